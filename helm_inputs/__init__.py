@@ -1,0 +1,239 @@
+"""Seeded synthetic inputs for the ECS Helmholtz solver and its oracle.
+
+This module is shared by the CUDA path's tests/bench and by the CPU oracle's tests.
+It holds no arithmetic of the method itself: it only describes problems (grid sizes,
+layer widths, angles, wave-number fields phi = k(x)^2 sampled at the real node
+positions, right-hand sides, Krylov shadow vectors) and draws the random numbers
+those descriptions need, from numpy's seeded PCG64 generator.
+
+Node positions follow the problem statement of the paper (Section 2, the ECS map
+z(x) = (x - r) e^{i theta} + r on the layers, and Section 3's vertex-centred grid):
+interior nodes sit at x = 0, h, ..., L (h = L / (n_int - 1)); a layer of n_l nodes
+continues past each end with real positions -m h and L + m h (m = 1..n_l); a side with
+n_l = 0 is a Dirichlet wall, whose end node is not an unknown.  The wave number is
+evaluated at these real positions (the layers continue the coordinate, not the
+potential; Section 1 on ECS and non-analytic potentials).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+BASE_SEED = 20091201
+
+# Preconditioner kinds and solver codes, mirrored by both the C-ABI and the oracle.
+PC_NONE, PC_CSL, PC_CSG_UNIFORM, PC_CSG_INTERIOR = 0, 1, 2, 3
+SM_JACOBI, SM_RBGS = 0, 1
+BICGSTAB, IDR = 0, 1
+
+
+@dataclasses.dataclass
+class Problem:
+    """One ECS Helmholtz instance: grid, layers, wave-number field and RHS."""
+
+    dim: int
+    n_int: Tuple[int, int, int]
+    n_layer: Tuple[Tuple[int, int], Tuple[int, int], Tuple[int, int]]
+    extent: Tuple[float, float, float]
+    theta_gamma: float
+    phi: Optional[np.ndarray]  # k(x)^2 at the unknowns (float64, x fastest) or None for constant
+    k0: float                  # constant wave number when phi is None
+    b: np.ndarray              # right-hand side (complex128, x fastest)
+    name: str = ""
+
+    @property
+    def shape(self) -> Tuple[int, ...]:
+        """Unknowns per axis, x first."""
+        return tuple(axis_unknowns(self.n_int[a], self.n_layer[a]) for a in range(self.dim))
+
+    @property
+    def n(self) -> int:
+        return int(np.prod(self.shape))
+
+    def h(self, axis: int = 0) -> float:
+        return self.extent[axis] / (self.n_int[axis] - 1)
+
+
+def axis_unknowns(n_int: int, nl: Tuple[int, int]) -> int:
+    """Number of unknowns along one axis (interior nodes, minus Dirichlet walls, plus layers)."""
+    lo, hi = nl
+    return n_int - 2 + (lo + 1 if lo > 0 else 0) + (hi + 1 if hi > 0 else 0)
+
+
+def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray:
+    """Real coordinates of the unknowns along one axis (layers continue the real axis)."""
+    h = extent / (n_int - 1)
+    lo, hi = nl
+    xs: List[float] = []
+    xs += [-m * h for m in range(lo, 0, -1)]
+    first = 0 if lo > 0 else 1
+    last = n_int - 1 if hi > 0 else n_int - 2
+    xs += [j * h for j in range(first, last + 1)]
+    xs += [extent + m * h for m in range(1, hi + 1)]
+    return np.asarray(xs, dtype=np.float64)
+
+
+def mesh(p: Problem) -> List[np.ndarray]:
+    """Broadcastable real coordinate arrays, ordered so that arr.ravel() is x-fastest."""
+    axes = [axis_positions(p.n_int[a], p.n_layer[a], p.extent[a]) for a in range(p.dim)]
+    # index order (z, y, x) so that C-order ravel is x-fastest
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return grids[::-1]
+
+
+def interior_node_index(p: Problem, axis: int, j: int) -> int:
+    """0-based unknown index along `axis` of interior grid node j (0..n_int-1)."""
+    lo = p.n_layer[axis][0]
+    return j + lo if lo > 0 else j - 1
+
+
+def _dims3(dim, v):
+    v = list(v) + [v[-1]] * (3 - len(v))
+    return tuple(v[:3])
+
+
+def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, extent=1.0,
+                 theta_gamma=0.5, k0: float = 0.0, phi_kind: str = "const", bump_amp=0.3,
+                 bump_width2=0.02, bump_centre=(0.5, 0.5, 0.5), rhs: str = "point",
+                 rhs_width_h: float = 2.0, seed: int = BASE_SEED, name: str = "") -> Problem:
+    """Build a seeded synthetic instance shaped like the paper's model problems.
+
+    n_l: int (all sides), one (lo, hi) pair for every axis, or per-axis (lo, hi) pairs.
+    phi_kind: "const" (k = k0), or "bump" (k = k0 (1 + amp exp(-|x - c|^2 / width2))).
+    rhs: "point" (value 1 at the interior node floor((n_int-1)/2) per axis, as in MP1),
+         "gauss" (exp(-|x - x_s|^2 / (2 sigma^2)), sigma = rhs_width_h * h, x_s uniform in
+         [0.1, 0.9]^d from the seed), "random" (complex normal entries), "zero".
+    """
+    rng = np.random.default_rng(seed)
+    ni = _dims3(dim, [n_int] if np.isscalar(n_int) else list(n_int))
+    if np.isscalar(n_l):
+        nl = tuple((int(n_l), int(n_l)) for _ in range(3))
+    elif len(n_l) == 2 and all(np.isscalar(v) for v in n_l):
+        nl = tuple((int(n_l[0]), int(n_l[1])) for _ in range(3))
+    else:
+        nl_list = [tuple(x) for x in n_l]
+        nl = _dims3(dim, nl_list)
+    ext = _dims3(dim, [extent] if np.isscalar(extent) else list(extent))
+    p = Problem(dim=dim, n_int=tuple(int(x) for x in ni), n_layer=nl,
+                extent=tuple(float(x) for x in ext), theta_gamma=float(theta_gamma),
+                phi=None, k0=float(k0), b=np.zeros(0, np.complex128), name=name)
+    shape = p.shape
+    X = mesh(p)
+    if phi_kind == "bump":
+        r2 = sum((X[a] - bump_centre[a] * ext[a]) ** 2 for a in range(dim))
+        k = k0 * (1.0 + bump_amp * np.exp(-r2 / bump_width2))
+        p.phi = np.ascontiguousarray((k * k).ravel(), dtype=np.float64)
+    elif phi_kind != "const":
+        raise ValueError(phi_kind)
+    n = int(np.prod(shape))
+    if rhs == "point":
+        b = np.zeros(shape[::-1], np.complex128)
+        idx = tuple(interior_node_index(p, a, (ni[a] - 1) // 2) for a in range(dim))
+        b[idx[::-1]] = 1.0
+        p.b = b.ravel()
+    elif rhs == "gauss":
+        xs = rng.uniform(0.1, 0.9, size=dim) * np.asarray(ext[:dim])
+        sig = rhs_width_h * p.h(0)
+        r2 = sum((X[a] - xs[a]) ** 2 for a in range(dim))
+        p.b = np.ascontiguousarray(np.exp(-r2 / (2 * sig * sig)).ravel().astype(np.complex128))
+    elif rhs == "random":
+        p.b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    elif rhs == "zero":
+        p.b = np.zeros(n, np.complex128)
+    else:
+        raise ValueError(rhs)
+    return p
+
+
+def shadow_space(n: int, s: int, seed: int = BASE_SEED + 17) -> np.ndarray:
+    """Raw random shadow vectors for IDR(s): an (s, n) complex128 array, row j = vector j.
+
+    Entries are independent with real and imaginary parts uniform in [-1, 1).  The solver
+    orthonormalises them itself; only the random draw lives here.
+    """
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1, 1, (s, n)) + 1j * rng.uniform(-1, 1, (s, n))).astype(np.complex128)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+# ---- the workloads the solver is measured on -------------------------------------------
+
+def workload_small_2d(seed: int = BASE_SEED) -> Problem:
+    """64^2 interior + 16-point ECS layer per side (theta_gamma 0.5), k = 20, centre point source."""
+    return make_problem(2, 64, 16, theta_gamma=0.5, k0=20.0, rhs="point", seed=seed,
+                        name="2d-64sq-L16-k20-point")
+
+
+def workload_2d_512(seed: int = BASE_SEED) -> Problem:
+    """512^2 interior + 64-point ECS layers, kh = 0.5, Gaussian-bump k(x), Gaussian source (sigma 2h)."""
+    h = 1.0 / 511.0
+    k0 = 0.5 / h
+    return make_problem(2, 512, 64, theta_gamma=0.5, k0=k0, phi_kind="bump", bump_amp=0.3,
+                        bump_width2=0.02, bump_centre=(0.5, 0.5), rhs="gauss", rhs_width_h=2.0,
+                        seed=seed, name="2d-512sq-L64-kh0.5-bump-gauss")
+
+
+def workload_3d_128(seed: int = BASE_SEED) -> Problem:
+    """128^3 interior + 16-point ECS layers, k = 40, centre point source."""
+    return make_problem(3, 128, 16, theta_gamma=0.5, k0=40.0, rhs="point", seed=seed,
+                        name="3d-128cube-L16-k40-point")
+
+
+def workload_batch_2d(count: int = 256, seed: int = BASE_SEED) -> List[Problem]:
+    """Uneven batch: n_int in {63,127,255,511}, layers 16..32, kh in [0.3,0.6], const or bump k."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n_int = int(rng.choice([63, 127, 255, 511]))
+        n_l = int(rng.integers(16, 33))
+        kh = float(rng.uniform(0.3, 0.6))
+        k0 = kh * (n_int - 1)
+        bump = bool(rng.integers(0, 2))
+        amp = float(rng.uniform(0.0, 0.4)) if bump else 0.0
+        cen = tuple(rng.uniform(0.2, 0.8, 2))
+        p = make_problem(2, n_int, n_l, theta_gamma=0.5, k0=k0,
+                         phi_kind="bump" if bump else "const", bump_amp=amp,
+                         bump_centre=(cen[0], cen[1]), rhs="point", seed=seed + 1 + i,
+                         name=f"batch{i}")
+        # point source at a random interior node instead of the centre
+        b = np.zeros(p.shape[::-1], np.complex128)
+        idx = tuple(interior_node_index(p, a, int(rng.integers(1, n_int - 1))) for a in range(2))
+        b[idx[::-1]] = 1.0
+        p.b = b.ravel()
+        out.append(p)
+    return out
+
+
+@dataclasses.dataclass
+class Precond:
+    """Description of the preconditioner (plain parameters, no arithmetic).
+
+    kind: PC_NONE (identity), PC_CSL (M = -(L + beta^2 k^2), beta^2 = shift),
+    PC_CSG_UNIFORM (every mesh width times e^{i theta_beta}), PC_CSG_INTERIOR (interior
+    widths only).  V(nu1, nu2) cycles with damped Jacobi (omega) or red-black Gauss-Seidel.
+    """
+
+    kind: int = PC_CSG_UNIFORM
+    theta_beta: float = 0.3
+    shift: complex = 1.0 + 0.5j
+    nu1: int = 1
+    nu2: int = 1
+    smoother: int = SM_RBGS
+    omega: float = 0.5
+    max_levels: int = 32
+    coarse_max: int = 8
+
+
+@dataclasses.dataclass
+class SolveOpts:
+    method: int = BICGSTAB
+    s: int = 4
+    tol: float = 1e-6
+    maxmv: int = 2000
+    max_restarts: int = 3

@@ -1,0 +1,6 @@
+"""FP64 CPU oracle for the ECS Helmholtz solver -- test infrastructure only.
+
+Only the test suite, the package smoke check and the benchmark's CPU-baseline leg use this
+package.  It shares no code with the CUDA library.
+"""
+from .oracle import Oracle, build_oracle, lib_path  # noqa: F401

@@ -1,0 +1,777 @@
+/*
+ * helm_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for the preconditioned
+ * Krylov solve of the ECS-discretised indefinite Helmholtz equation of
+ * Reps, Vanroose & bin Zubair, "On the indefinite Helmholtz equation: complex stretched
+ * absorbing boundary layers, iterative analysis, and preconditioning" (arXiv 0912.0180).
+ *
+ * TEST INFRASTRUCTURE ONLY.  It exists to check the CUDA path; only the test suite, the
+ * package smoke check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or helper with the CUDA library, and the CUDA library never calls it.
+ *
+ * Everything is written as loops over the definitions, in the paper's order:
+ *   - grid and complex mesh widths: Section 2 (ECS map z = (x - r) e^{i theta} + r, mesh width
+ *     h_gamma = h e^{i theta}) and Section 3 (vertex-centred ECS grid, eq. "ecsgrid");
+ *   - Shortley-Weller second difference on non-uniform (complex) widths: Section 3, eq.
+ *     "shortwell"; H = -(Laplacian + phi) with phi = k(x)^2: eq. "helmctu0" / "Helgen";
+ *   - preconditioners: CSL M = -(L + beta^2 k^2), eq. "helmctucsl" (Section 5.2); CSG, every
+ *     (or only the interior) mesh width multiplied by beta = e^{i theta_beta}, eq. "CSL-CSG"
+ *     and eq. "lapctucsg" (Section 5.3);
+ *   - geometric multigrid on the preconditioner (Section 5.1, Section 6.1 components: full
+ *     weighting restriction, bilinear prolongation, rediscretised ("direct") coarse operators,
+ *     omega-Jacobi; red-black Gauss-Seidel as a second smoother; direct coarsest solve);
+ *   - right-preconditioned Bi-CGSTAB (van der Vorst 1992) and IDR(s) (Sonneveld & van Gijzen
+ *     2008), the Krylov methods of Section 6.2, stopped on ||d_m|| / ||d_0|| < tol (the
+ *     stopping rule of Section 6.2), followed by a true-residual check.
+ *
+ * Readings where the paper is silent (documented in the design notes): hierarchy by
+ * index-even coarsening with summed complex gaps; phi injected at the coarse nodes; FW and
+ * linear interpolation weights in index space; red = even (i + j + l), red first; Hermitian
+ * inner products conjugating the first argument; zero initial guess.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ---- public structs (mirrored by the ctypes wrapper in oracle.py) -------------------- */
+typedef struct {
+  int dim;              /* 1, 2 or 3 */
+  int n_int[3];         /* interior grid nodes per axis, both ends (turning points) included */
+  int n_layer[3][2];    /* ECS layer nodes on the low / high side; 0 = Dirichlet wall */
+  double extent[3];     /* length of the real interior along each axis */
+  double theta_gamma;   /* ECS angle */
+} orc_grid;
+
+typedef struct {
+  int kind;             /* 0 identity, 1 CSL, 2 CSG on every width, 3 CSG on interior widths */
+  double theta_beta;    /* CSG angle */
+  double shift_re, shift_im; /* CSL: beta^2 */
+  int nu1, nu2;         /* pre / post smoothing sweeps */
+  int smoother;         /* 0 damped Jacobi, 1 red-black Gauss-Seidel */
+  double omega;         /* Jacobi damping */
+  int max_levels;       /* cap on the number of levels (>= 1) */
+  int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
+} orc_precond;
+
+typedef struct {
+  int method;           /* 0 Bi-CGSTAB, 1 IDR(s) */
+  int s;                /* IDR shadow dimension */
+  double tol;           /* stop on ||r|| / ||b|| < tol */
+  int maxmv;            /* cap on preconditioned matvecs */
+  int max_restarts;     /* true-residual restarts allowed */
+} orc_solve_opts;
+
+typedef struct {
+  int status;           /* 0 ok, 4 breakdown, 5 max matvecs, 6 not finite */
+  int iters;            /* Bi-CGSTAB iterations, or IDR steps */
+  int matvecs;          /* preconditioned matvecs (one V-cycle + one H apply each) */
+  int restarts;
+  double rel_res_recur; /* last recurrence residual / ||b|| */
+  double rel_res_true;  /* ||b - H x|| / ||b|| of the returned x */
+} orc_info;
+
+/* ---- grid ---------------------------------------------------------------------------- */
+typedef struct {
+  int n;          /* unknowns on this axis */
+  cplx* gap;      /* n + 1 widths: gap[j] = z(node j+1) - z(node j), nodes 0 and n+1 Dirichlet */
+  double* pos;    /* n real positions of the unknowns (only used to sample phi) */
+  cplx *am, *a0, *ap; /* Shortley-Weller row of -d^2/dz^2 at each unknown */
+} axis_t;
+
+typedef struct {
+  int dim;
+  int n[3];
+  long ntot;
+  axis_t ax[3];
+  double* phi;    /* k(x)^2 at every unknown */
+  cplx s;         /* sigma = s * phi; 1 for H and CSG, beta^2 for CSL */
+} level_t;
+
+typedef struct orc_ctx {
+  orc_grid grid;
+  orc_precond pc;
+  level_t H;      /* the Helmholtz operator itself */
+  int nlev;
+  level_t* M;     /* preconditioner hierarchy, M[0] on the finest grid */
+  cplx* lu;       /* dense LU (partial pivoting) of the coarsest M */
+  int* piv;
+  long nco;
+} orc_ctx;
+
+static long imax(long a, long b) { return a > b ? a : b; }
+
+/* Complex mesh widths of one axis (Section 2: h_gamma = h e^{i theta_gamma} on the layers;
+ * Section 5.3: CSG multiplies widths by beta).  scale_in multiplies the interior widths,
+ * scale_ly the layer widths. */
+static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, double theta_g,
+                       cplx scale_in, cplx scale_ly) {
+  double h = extent / (n_int - 1);
+  cplx hg = h * cexp(I * theta_g);
+  int lo = nl[0], hi = nl[1];
+  int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+  a->n = ngap - 1;
+  a->gap = malloc(sizeof(cplx) * ngap);
+  a->pos = malloc(sizeof(double) * imax(a->n, 1));
+  int g = 0;
+  if (lo > 0)
+    for (int m = 0; m < lo + 1; ++m) a->gap[g++] = hg * scale_ly;
+  for (int m = 0; m < n_int - 1; ++m) a->gap[g++] = h * scale_in;
+  if (hi > 0)
+    for (int m = 0; m < hi + 1; ++m) a->gap[g++] = hg * scale_ly;
+  /* real positions: the layers continue the real coordinate */
+  int u = 0;
+  for (int m = lo; m >= 1; --m) a->pos[u++] = -m * h;
+  int first = lo > 0 ? 0 : 1, last = hi > 0 ? n_int - 1 : n_int - 2;
+  for (int j = first; j <= last; ++j) a->pos[u++] = j * h;
+  for (int m = 1; m <= hi; ++m) a->pos[u++] = extent + m * h;
+}
+
+/* Shortley-Weller (Section 3, eq. "shortwell"): with left width hl = gap[j], right width
+ * hr = gap[j+1],  -u'' ~ -2/(hl+hr) (u_{j-1}/hl - (1/hl + 1/hr) u_j + u_{j+1}/hr). */
+static void axis_coeffs(axis_t* a) {
+  a->am = malloc(sizeof(cplx) * imax(a->n, 1));
+  a->a0 = malloc(sizeof(cplx) * imax(a->n, 1));
+  a->ap = malloc(sizeof(cplx) * imax(a->n, 1));
+  for (int j = 0; j < a->n; ++j) {
+    cplx hl = a->gap[j], hr = a->gap[j + 1];
+    cplx f = 2.0 / (hl + hr);
+    a->am[j] = -f / hl;
+    a->a0[j] = f * (1.0 / hl + 1.0 / hr);
+    a->ap[j] = -f / hr;
+  }
+}
+
+/* Index-even coarsening: coarse unknown c is fine unknown 2c+1 (0-based), i.e. coarse node
+ * c+1 is fine node 2(c+1); coarse widths are the sums of the fine widths between coarse
+ * nodes; the last one reaches the fine Dirichlet node and spans one or two fine widths. */
+static void axis_coarsen(const axis_t* f, axis_t* c) {
+  c->n = f->n / 2;
+  c->gap = malloc(sizeof(cplx) * (c->n + 1));
+  c->pos = malloc(sizeof(double) * imax(c->n, 1));
+  for (int ci = 0; ci < c->n; ++ci) {
+    c->gap[ci] = f->gap[2 * ci] + f->gap[2 * ci + 1];
+    c->pos[ci] = f->pos[2 * ci + 1];
+  }
+  cplx last = 0;
+  for (int j = 2 * c->n; j <= f->n; ++j) last += f->gap[j];
+  c->gap[c->n] = last;
+  axis_coeffs(c);
+}
+
+static void axis_free(axis_t* a) {
+  free(a->gap); free(a->pos); free(a->am); free(a->a0); free(a->ap);
+}
+
+static void level_free(level_t* L) {
+  for (int d = 0; d < L->dim; ++d) axis_free(&L->ax[d]);
+  free(L->phi);
+}
+
+static long lidx(const level_t* L, int i, int j, int l) {
+  return i + (long)L->n[0] * (j + (long)L->n[1] * l);
+}
+
+/* Fine level: gaps for the requested operator, phi sampled (or constant). */
+static void level_fine(level_t* L, const orc_grid* g, const double* phi, double k0,
+                       cplx scale_in, cplx scale_ly, cplx s) {
+  memset(L, 0, sizeof(*L));
+  L->dim = g->dim;
+  L->ntot = 1;
+  for (int d = 0; d < 3; ++d) L->n[d] = 1;
+  for (int d = 0; d < g->dim; ++d) {
+    axis_build(&L->ax[d], g->n_int[d], g->n_layer[d], g->extent[d], g->theta_gamma,
+               scale_in, scale_ly);
+    axis_coeffs(&L->ax[d]);
+    L->n[d] = L->ax[d].n;
+    L->ntot *= L->n[d];
+  }
+  L->phi = malloc(sizeof(double) * imax(L->ntot, 1));
+  for (long p = 0; p < L->ntot; ++p) L->phi[p] = phi ? phi[p] : k0 * k0;
+  L->s = s;
+}
+
+/* Coarse level: coarsened axes, phi injected at the coarse nodes. */
+static void level_coarse(const level_t* F, level_t* C) {
+  memset(C, 0, sizeof(*C));
+  C->dim = F->dim;
+  C->ntot = 1;
+  for (int d = 0; d < 3; ++d) C->n[d] = 1;
+  for (int d = 0; d < F->dim; ++d) {
+    axis_coarsen(&F->ax[d], &C->ax[d]);
+    C->n[d] = C->ax[d].n;
+    C->ntot *= C->n[d];
+  }
+  C->phi = malloc(sizeof(double) * imax(C->ntot, 1));
+  for (int l = 0; l < C->n[2]; ++l)
+    for (int j = 0; j < C->n[1]; ++j)
+      for (int i = 0; i < C->n[0]; ++i) {
+        int fi = 2 * i + 1, fj = F->dim > 1 ? 2 * j + 1 : 0, fl = F->dim > 2 ? 2 * l + 1 : 0;
+        C->phi[lidx(C, i, j, l)] = F->phi[lidx(F, fi, fj, fl)];
+      }
+  C->s = F->s;
+}
+
+/* Diagonal of the operator at point (i,j,l): sum of the per-axis centre weights - s*phi. */
+static cplx diag_at(const level_t* L, int i, int j, int l) {
+  int ix[3] = {i, j, l};
+  cplx d = 0;
+  for (int a = 0; a < L->dim; ++a) d += L->ax[a].a0[ix[a]];
+  return d - L->s * L->phi[lidx(L, i, j, l)];
+}
+
+/* Off-diagonal part of row (i,j,l) applied to x (Dirichlet neighbours contribute 0). */
+static cplx offdiag_at(const level_t* L, const cplx* x, int i, int j, int l) {
+  int ix[3] = {i, j, l};
+  cplx acc = 0;
+  for (int a = 0; a < L->dim; ++a) {
+    int k = ix[a];
+    int lo[3] = {i, j, l}, hi[3] = {i, j, l};
+    lo[a] = k - 1;
+    hi[a] = k + 1;
+    if (k > 0) acc += L->ax[a].am[k] * x[lidx(L, lo[0], lo[1], lo[2])];
+    if (k < L->n[a] - 1) acc += L->ax[a].ap[k] * x[lidx(L, hi[0], hi[1], hi[2])];
+  }
+  return acc;
+}
+
+/* y = A x for the operator of a level: the d-fold sum of Shortley-Weller rows minus
+ * sigma = s * phi (eq. "helmctu0" / "Helgen"; CSL eq. "helmctucsl"). */
+static void level_apply(const level_t* L, const cplx* x, cplx* y) {
+  for (int l = 0; l < L->n[2]; ++l)
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int i = 0; i < L->n[0]; ++i) {
+        long p = lidx(L, i, j, l);
+        y[p] = diag_at(L, i, j, l) * x[p] + offdiag_at(L, x, i, j, l);
+      }
+}
+
+/* ---- dense LU with partial pivoting (the "direct" coarsest solve) ---------------------- */
+static int lu_factor(cplx* A, int* piv, long n) {
+  for (long k = 0; k < n; ++k) {
+    long p = k;
+    double best = cabs(A[k * n + k]);
+    for (long r = k + 1; r < n; ++r)
+      if (cabs(A[r * n + k]) > best) { best = cabs(A[r * n + k]); p = r; }
+    piv[k] = (int)p;
+    if (best == 0.0) return -1;
+    if (p != k)
+      for (long c = 0; c < n; ++c) { cplx t = A[k * n + c]; A[k * n + c] = A[p * n + c]; A[p * n + c] = t; }
+    for (long r = k + 1; r < n; ++r) {
+      cplx m = A[r * n + k] / A[k * n + k];
+      A[r * n + k] = m;
+      for (long c = k + 1; c < n; ++c) A[r * n + c] -= m * A[k * n + c];
+    }
+  }
+  return 0;
+}
+
+static void lu_solve(const cplx* A, const int* piv, long n, const cplx* b, cplx* x) {
+  if (x != b) memcpy(x, b, sizeof(cplx) * n);
+  for (long k = 0; k < n; ++k)
+    if (piv[k] != k) { cplx t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+  for (long r = 0; r < n; ++r)
+    for (long c = 0; c < r; ++c) x[r] -= A[r * n + c] * x[c];
+  for (long r = n - 1; r >= 0; --r) {
+    for (long c = r + 1; c < n; ++c) x[r] -= A[r * n + c] * x[c];
+    x[r] /= A[r * n + r];
+  }
+}
+
+/* Dense matrix of a level's operator, row-major, assembled entry by entry. */
+static void level_dense(const level_t* L, cplx* A) {
+  long n = L->ntot;
+  memset(A, 0, sizeof(cplx) * n * n);
+  for (int l = 0; l < L->n[2]; ++l)
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int i = 0; i < L->n[0]; ++i) {
+        long p = lidx(L, i, j, l);
+        A[p * n + p] = diag_at(L, i, j, l);
+        int ix[3] = {i, j, l};
+        for (int a = 0; a < L->dim; ++a) {
+          int k = ix[a];
+          long stride = a == 0 ? 1 : (a == 1 ? L->n[0] : (long)L->n[0] * L->n[1]);
+          if (k > 0) A[p * n + p - stride] = L->ax[a].am[k];
+          if (k < L->n[a] - 1) A[p * n + p + stride] = L->ax[a].ap[k];
+        }
+      }
+}
+
+/* ---- context ------------------------------------------------------------------------- */
+orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_precond* pc) {
+  orc_ctx* c = calloc(1, sizeof(orc_ctx));
+  c->grid = *g;
+  c->pc = *pc;
+  level_fine(&c->H, g, phi, k0, 1.0, 1.0, 1.0);
+  if (pc->kind == 0) return c; /* identity preconditioner: no hierarchy */
+  cplx beta = cexp(I * pc->theta_beta);
+  cplx scale_in = 1.0, scale_ly = 1.0, s = 1.0;
+  if (pc->kind == 1) s = pc->shift_re + I * pc->shift_im;           /* CSL: sigma = beta^2 phi */
+  else if (pc->kind == 2) { scale_in = beta; scale_ly = beta; }      /* CSG, every width */
+  else if (pc->kind == 3) { scale_in = beta; }                       /* CSG, interior widths */
+  int maxl = pc->max_levels < 1 ? 1 : pc->max_levels;
+  c->M = calloc(maxl, sizeof(level_t));
+  level_fine(&c->M[0], g, phi, k0, scale_in, scale_ly, s);
+  c->nlev = 1;
+  while (c->nlev < maxl) {
+    const level_t* F = &c->M[c->nlev - 1];
+    int all_small = 1, min_n = 1 << 30;
+    for (int d = 0; d < F->dim; ++d) {
+      if (F->n[d] > pc->coarse_max) all_small = 0;
+      if (F->n[d] < min_n) min_n = F->n[d];
+    }
+    if (all_small || min_n < 3) break;
+    level_coarse(F, &c->M[c->nlev]);
+    c->nlev++;
+  }
+  level_t* C = &c->M[c->nlev - 1];
+  c->nco = C->ntot;
+  c->lu = malloc(sizeof(cplx) * c->nco * c->nco);
+  c->piv = malloc(sizeof(int) * c->nco);
+  level_dense(C, c->lu);
+  if (lu_factor(c->lu, c->piv, c->nco) != 0) { /* singular coarsest operator */ }
+  return c;
+}
+
+void orc_destroy(orc_ctx* c) {
+  if (!c) return;
+  level_free(&c->H);
+  for (int k = 0; k < c->nlev; ++k) level_free(&c->M[k]);
+  free(c->M); free(c->lu); free(c->piv); free(c);
+}
+
+int orc_num_levels(const orc_ctx* c) { return c->nlev; }
+
+static const level_t* pick(const orc_ctx* c, int which, int lvl) {
+  return which == 0 ? &c->H : &c->M[lvl];
+}
+
+void orc_level_shape(const orc_ctx* c, int which, int lvl, int* n_out) {
+  const level_t* L = pick(c, which, lvl);
+  for (int d = 0; d < 3; ++d) n_out[d] = L->n[d];
+}
+
+/* Per-axis tables of a level: gaps (n+1), am, a0, ap (n each), real positions (n). */
+void orc_axis_tables(const orc_ctx* c, int which, int lvl, int axis, cplx* gap, cplx* am,
+                     cplx* a0, cplx* ap, double* pos) {
+  const axis_t* a = &pick(c, which, lvl)->ax[axis];
+  memcpy(gap, a->gap, sizeof(cplx) * (a->n + 1));
+  memcpy(am, a->am, sizeof(cplx) * a->n);
+  memcpy(a0, a->a0, sizeof(cplx) * a->n);
+  memcpy(ap, a->ap, sizeof(cplx) * a->n);
+  memcpy(pos, a->pos, sizeof(double) * a->n);
+}
+
+void orc_level_phi(const orc_ctx* c, int which, int lvl, double* phi, cplx* s) {
+  const level_t* L = pick(c, which, lvl);
+  memcpy(phi, L->phi, sizeof(double) * L->ntot);
+  *s = L->s;
+}
+
+/* y = H x (which = 0) or y = M_lvl x (which = 1). */
+void orc_apply(const orc_ctx* c, int which, int lvl, const cplx* x, cplx* y) {
+  level_apply(pick(c, which, lvl), x, y);
+}
+
+void orc_dense(const orc_ctx* c, int which, int lvl, cplx* A) { level_dense(pick(c, which, lvl), A); }
+
+/* ---- multigrid components (Section 5.1 / 6.1) ----------------------------------------- */
+
+/* One damped-Jacobi sweep: u <- u + omega D^{-1} (f - A u). */
+static void jacobi_sweep(const level_t* L, double omega, cplx* u, const cplx* f, cplx* tmp) {
+  level_apply(L, u, tmp);
+  for (int l = 0; l < L->n[2]; ++l)
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int i = 0; i < L->n[0]; ++i) {
+        long p = lidx(L, i, j, l);
+        tmp[p] = u[p] + omega * (f[p] - tmp[p]) / diag_at(L, i, j, l);
+      }
+  memcpy(u, tmp, sizeof(cplx) * L->ntot);
+}
+
+/* One red-black Gauss-Seidel sweep: red points ((i+j+l) even) then black points, each
+ * solving its own row with the current neighbour values. */
+static void rbgs_sweep(const level_t* L, cplx* u, const cplx* f) {
+  for (int colour = 0; colour < 2; ++colour)
+    for (int l = 0; l < L->n[2]; ++l)
+      for (int j = 0; j < L->n[1]; ++j)
+        for (int i = 0; i < L->n[0]; ++i) {
+          if (((i + j + l) & 1) != colour) continue;
+          long p = lidx(L, i, j, l);
+          u[p] = (f[p] - offdiag_at(L, u, i, j, l)) / diag_at(L, i, j, l);
+        }
+}
+
+static void smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps, cplx* tmp) {
+  const level_t* L = &c->M[lvl];
+  for (int k = 0; k < sweeps; ++k) {
+    if (c->pc.smoother == 0) jacobi_sweep(L, c->pc.omega, u, f, tmp);
+    else rbgs_sweep(L, u, f);
+  }
+}
+
+/* Full weighting in index space: coarse unknown c gathers fine unknowns 2c, 2c+1, 2c+2
+ * with weights 1/4, 1/2, 1/4 per axis (tensor product); missing neighbours are Dirichlet. */
+static void restrict_fw(const level_t* F, const level_t* C, const cplx* r, cplx* fc) {
+  static const double w[3] = {0.25, 0.5, 0.25};
+  for (int cl = 0; cl < C->n[2]; ++cl)
+    for (int cj = 0; cj < C->n[1]; ++cj)
+      for (int Ii = 0; Ii < C->n[0]; ++Ii) {
+        cplx acc = 0;
+        for (int dl = (F->dim > 2 ? -1 : 0); dl <= (F->dim > 2 ? 1 : 0); ++dl)
+          for (int dj = (F->dim > 1 ? -1 : 0); dj <= (F->dim > 1 ? 1 : 0); ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              int fi = 2 * Ii + 1 + di;
+              int fj = F->dim > 1 ? 2 * cj + 1 + dj : 0;
+              int fl = F->dim > 2 ? 2 * cl + 1 + dl : 0;
+              if (fi < 0 || fi >= F->n[0] || fj < 0 || fj >= F->n[1] || fl < 0 || fl >= F->n[2]) continue;
+              double wt = w[di + 1] * (F->dim > 1 ? w[dj + 1] : 1.0) * (F->dim > 2 ? w[dl + 1] : 1.0);
+              acc += wt * r[lidx(F, fi, fj, fl)];
+            }
+        fc[lidx(C, Ii, cj, cl)] = acc;
+      }
+}
+
+/* Linear interpolation weights of fine index i from coarse indices (per axis). */
+static int interp1(int i, int nc, int* ci, double* w) {
+  if (i & 1) { ci[0] = (i - 1) / 2; w[0] = 1.0; return 1; }
+  int k = 0;
+  if (i / 2 - 1 >= 0) { ci[k] = i / 2 - 1; w[k] = 0.5; ++k; }
+  if (i / 2 < nc) { ci[k] = i / 2; w[k] = 0.5; ++k; }
+  return k;
+}
+
+/* u_f += P e_c, bilinear / trilinear interpolation (tensor product of 1D linear). */
+static void prolong_add(const level_t* F, const level_t* C, const cplx* ec, cplx* u) {
+  for (int l = 0; l < F->n[2]; ++l)
+    for (int j = 0; j < F->n[1]; ++j)
+      for (int i = 0; i < F->n[0]; ++i) {
+        int ci[2], cj[2] = {0}, cl[2] = {0};
+        double wi[2], wj[2] = {1.0}, wl[2] = {1.0};
+        int ni = interp1(i, C->n[0], ci, wi);
+        int nj = F->dim > 1 ? interp1(j, C->n[1], cj, wj) : 1;
+        int nl = F->dim > 2 ? interp1(l, C->n[2], cl, wl) : 1;
+        cplx acc = 0;
+        for (int c3 = 0; c3 < nl; ++c3)
+          for (int c2 = 0; c2 < nj; ++c2)
+            for (int c1 = 0; c1 < ni; ++c1)
+              acc += wi[c1] * wj[c2] * wl[c3] * ec[lidx(C, ci[c1], cj[c2], cl[c3])];
+        u[lidx(F, i, j, l)] += acc;
+      }
+}
+
+/* V(nu1, nu2) cycle for M_lvl u = f from a zero initial guess (recursive). */
+static void vcycle_rec(const orc_ctx* c, int lvl, const cplx* f, cplx* u) {
+  const level_t* L = &c->M[lvl];
+  if (lvl == c->nlev - 1) { lu_solve(c->lu, c->piv, c->nco, f, u); return; }
+  const level_t* C = &c->M[lvl + 1];
+  long n = L->ntot;
+  cplx* tmp = malloc(sizeof(cplx) * n);
+  cplx* r = malloc(sizeof(cplx) * n);
+  cplx* fc = malloc(sizeof(cplx) * C->ntot);
+  cplx* ec = malloc(sizeof(cplx) * C->ntot);
+  memset(u, 0, sizeof(cplx) * n);
+  smooth(c, lvl, u, f, c->pc.nu1, tmp);
+  level_apply(L, u, tmp);
+  for (long p = 0; p < n; ++p) r[p] = f[p] - tmp[p];
+  restrict_fw(L, C, r, fc);
+  vcycle_rec(c, lvl + 1, fc, ec);
+  prolong_add(L, C, ec, u);
+  smooth(c, lvl, u, f, c->pc.nu2, tmp);
+  free(tmp); free(r); free(fc); free(ec);
+}
+
+/* z ~ M^{-1} r: one V-cycle (identity when there is no preconditioner). */
+void orc_vcycle(const orc_ctx* c, const cplx* r, cplx* z) {
+  if (c->pc.kind == 0) { memcpy(z, r, sizeof(cplx) * c->H.ntot); return; }
+  vcycle_rec(c, 0, r, z);
+}
+
+/* Component entry points for tests. */
+void orc_smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps) {
+  cplx* tmp = malloc(sizeof(cplx) * c->M[lvl].ntot);
+  smooth(c, lvl, u, f, sweeps, tmp);
+  free(tmp);
+}
+void orc_restrict(const orc_ctx* c, int lvl, const cplx* r, cplx* fc) {
+  restrict_fw(&c->M[lvl], &c->M[lvl + 1], r, fc);
+}
+void orc_prolong_add(const orc_ctx* c, int lvl, const cplx* ec, cplx* u) {
+  prolong_add(&c->M[lvl], &c->M[lvl + 1], ec, u);
+}
+void orc_coarse_solve(const orc_ctx* c, const cplx* f, cplx* z) { lu_solve(c->lu, c->piv, c->nco, f, z); }
+
+/* Direct solve of H x = b by dense LU (plain definition of the discrete solution). */
+int orc_dense_solve(const orc_ctx* c, const cplx* b, cplx* x) {
+  long n = c->H.ntot;
+  cplx* A = malloc(sizeof(cplx) * n * n);
+  int* piv = malloc(sizeof(int) * n);
+  level_dense(&c->H, A);
+  int rc = lu_factor(A, piv, n);
+  if (rc == 0) lu_solve(A, piv, n, b, x);
+  free(A); free(piv);
+  return rc;
+}
+
+/* ---- Krylov ---------------------------------------------------------------------------- */
+static cplx dotc(const cplx* x, const cplx* y, long n) { /* x^H y */
+  cplx s = 0;
+  for (long i = 0; i < n; ++i) s += conj(x[i]) * y[i];
+  return s;
+}
+static double nrm2(const cplx* x, long n) {
+  double s = 0;
+  for (long i = 0; i < n; ++i) s += creal(x[i]) * creal(x[i]) + cimag(x[i]) * cimag(x[i]);
+  return sqrt(s);
+}
+static int finite_c(cplx z) { return isfinite(creal(z)) && isfinite(cimag(z)); }
+
+enum { ST_OK = 0, ST_BREAKDOWN = 4, ST_MAXMV = 5, ST_NAN = 6 };
+
+/* Right-preconditioned Bi-CGSTAB (van der Vorst 1992) from the current x with residual r.
+ * Returns ST_OK when the recurrence residual meets tol.  2 preconditioned matvecs per
+ * iteration; the half-step exit after s counts one. */
+static int bicgstab_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
+                        const orc_solve_opts* o, orc_info* info, double* hist, int hist_cap) {
+  long n = c->H.ntot;
+  cplx *rh = malloc(sizeof(cplx) * n), *p = calloc(n, sizeof(cplx)), *v = calloc(n, sizeof(cplx));
+  cplx *ph = malloc(sizeof(cplx) * n), *sv = malloc(sizeof(cplx) * n), *sh = malloc(sizeof(cplx) * n);
+  cplx *t = malloc(sizeof(cplx) * n);
+  memcpy(rh, r, sizeof(cplx) * n);
+  cplx rho_old = 1, alpha = 1, omega = 1;
+  int st = ST_MAXMV;
+  for (;;) {
+    if (info->matvecs >= o->maxmv) { st = ST_MAXMV; break; }
+    cplx rho = dotc(rh, r, n);
+    if (!finite_c(rho)) { st = ST_NAN; break; }
+    if (rho == 0) { st = ST_BREAKDOWN; break; }
+    cplx beta = (rho / rho_old) * (alpha / omega);
+    for (long i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    orc_vcycle(c, p, ph);
+    level_apply(&c->H, ph, v);
+    info->matvecs++;
+    info->iters++;
+    cplx rv = dotc(rh, v, n);
+    if (!finite_c(rv)) { st = ST_NAN; break; }
+    if (rv == 0) { st = ST_BREAKDOWN; break; }
+    alpha = rho / rv;
+    for (long i = 0; i < n; ++i) sv[i] = r[i] - alpha * v[i];
+    double sn = nrm2(sv, n) / bn;
+    if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = sn;
+    info->rel_res_recur = sn;
+    if (!isfinite(sn)) { st = ST_NAN; break; }
+    if (sn < o->tol) {
+      for (long i = 0; i < n; ++i) x[i] += alpha * ph[i];
+      memcpy(r, sv, sizeof(cplx) * n);
+      st = ST_OK;
+      break;
+    }
+    if (info->matvecs >= o->maxmv) {
+      for (long i = 0; i < n; ++i) x[i] += alpha * ph[i];
+      memcpy(r, sv, sizeof(cplx) * n);
+      st = ST_MAXMV;
+      break;
+    }
+    orc_vcycle(c, sv, sh);
+    level_apply(&c->H, sh, t);
+    info->matvecs++;
+    cplx ts = dotc(t, sv, n);
+    double tt = creal(dotc(t, t, n));
+    if (!isfinite(tt) || !finite_c(ts)) { st = ST_NAN; break; }
+    if (tt == 0) { st = ST_BREAKDOWN; break; }
+    omega = ts / tt;
+    for (long i = 0; i < n; ++i) {
+      x[i] += alpha * ph[i] + omega * sh[i];
+      r[i] = sv[i] - omega * t[i];
+    }
+    double rn = nrm2(r, n) / bn;
+    if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = rn;
+    info->rel_res_recur = rn;
+    if (!isfinite(rn)) { st = ST_NAN; break; }
+    if (rn < o->tol) { st = ST_OK; break; }
+    if (omega == 0) { st = ST_BREAKDOWN; break; }
+    rho_old = rho;
+  }
+  free(rh); free(p); free(v); free(ph); free(sv); free(sh); free(t);
+  return st;
+}
+
+/* Solve the s x s system Mk c = m (column-major Mk[row + s*col]) by Gaussian elimination
+ * with partial pivoting; returns -1 when singular. */
+static int small_solve(const cplx* Mk, const cplx* m, cplx* out, int s) {
+  cplx A[64 * 64], rhs[64];
+  for (int i = 0; i < s; ++i) {
+    rhs[i] = m[i];
+    for (int j = 0; j < s; ++j) A[i * s + j] = Mk[i + s * j];
+  }
+  for (int k = 0; k < s; ++k) {
+    int p = k;
+    for (int r = k + 1; r < s; ++r) if (cabs(A[r * s + k]) > cabs(A[p * s + k])) p = r;
+    if (A[p * s + k] == 0) return -1;
+    if (p != k) {
+      for (int j = 0; j < s; ++j) { cplx tt = A[k * s + j]; A[k * s + j] = A[p * s + j]; A[p * s + j] = tt; }
+      cplx tt = rhs[k]; rhs[k] = rhs[p]; rhs[p] = tt;
+    }
+    for (int r = k + 1; r < s; ++r) {
+      cplx f = A[r * s + k] / A[k * s + k];
+      for (int j = k; j < s; ++j) A[r * s + j] -= f * A[k * s + j];
+      rhs[r] -= f * rhs[k];
+    }
+  }
+  for (int r = s - 1; r >= 0; --r) {
+    cplx acc = rhs[r];
+    for (int j = r + 1; j < s; ++j) acc -= A[r * s + j] * out[j];
+    out[r] = acc / A[r * s + r];
+  }
+  return 0;
+}
+
+/* Right-preconditioned IDR(s) (Sonneveld & van Gijzen 2008): the residual is pushed through
+ * nested spaces G_j; s differences dR (with their x-space twins dX) are kept, the next
+ * residual is made orthogonal to the shadow space P by an s x s solve, and each step costs
+ * one preconditioned matvec.  P holds s orthonormal columns (row-major P[j*n + i]). */
+static int idr_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn, const cplx* P,
+                   const orc_solve_opts* o, orc_info* info, double* hist, int hist_cap) {
+  long n = c->H.ntot;
+  int s = o->s;
+  cplx* dR = calloc((size_t)s * n, sizeof(cplx));
+  cplx* dX = calloc((size_t)s * n, sizeof(cplx));
+  cplx *v = malloc(sizeof(cplx) * n), *z = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+  cplx *q = malloc(sizeof(cplx) * n), *xs = malloc(sizeof(cplx) * n);
+  cplx Mk[64 * 64], m[64], cc[64], dm[64];
+  cplx omega = 1;
+  int st = ST_MAXMV;
+  double rn = nrm2(r, n) / bn;
+  /* s minimal-residual steps build the first difference vectors */
+  for (int k = 0; k < s; ++k) {
+    if (info->matvecs >= o->maxmv) { st = ST_MAXMV; goto done; }
+    orc_vcycle(c, r, z);
+    level_apply(&c->H, z, t);
+    info->matvecs++;
+    info->iters++;
+    double tt = creal(dotc(t, t, n));
+    if (!isfinite(tt)) { st = ST_NAN; goto done; }
+    if (tt == 0) { st = ST_BREAKDOWN; goto done; }
+    omega = dotc(t, r, n) / tt;
+    for (long i = 0; i < n; ++i) {
+      dX[k * n + i] = omega * z[i];
+      dR[k * n + i] = -omega * t[i];
+      x[i] += dX[k * n + i];
+      r[i] += dR[k * n + i];
+    }
+    rn = nrm2(r, n) / bn;
+    if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = rn;
+    info->rel_res_recur = rn;
+    if (!isfinite(rn)) { st = ST_NAN; goto done; }
+    if (rn < o->tol) { st = ST_OK; goto done; }
+  }
+  for (int j = 0; j < s; ++j) {
+    for (int i = 0; i < s; ++i) Mk[i + s * j] = dotc(&P[(long)i * n], &dR[(long)j * n], n);
+    m[j] = dotc(&P[(long)j * n], r, n);
+  }
+  int oldest = 0;
+  for (;;) {
+    for (int k = 0; k <= s; ++k) {
+      if (info->matvecs >= o->maxmv) { st = ST_MAXMV; goto done; }
+      if (small_solve(Mk, m, cc, s) != 0) { st = ST_BREAKDOWN; goto done; }
+      for (long i = 0; i < n; ++i) {
+        cplx acc = 0;
+        for (int j = 0; j < s; ++j) acc -= dR[(long)j * n + i] * cc[j];
+        q[i] = acc;
+        v[i] = r[i] + acc;
+      }
+      orc_vcycle(c, v, z);
+      /* new x-space difference: -dX c + omega z */
+      for (long i = 0; i < n; ++i) {
+        cplx acc = 0;
+        for (int j = 0; j < s; ++j) acc -= dX[(long)j * n + i] * cc[j];
+        xs[i] = acc; /* -dX c, combined below */
+      }
+      cplx* dRo = &dR[(long)oldest * n];
+      cplx* dXo = &dX[(long)oldest * n];
+      if (k == 0) {
+        level_apply(&c->H, z, t);
+        double tt = creal(dotc(t, t, n));
+        if (!isfinite(tt)) { st = ST_NAN; goto done; }
+        if (tt == 0) { st = ST_BREAKDOWN; goto done; }
+        omega = dotc(t, v, n) / tt;
+        for (long i = 0; i < n; ++i) {
+          dRo[i] = q[i] - omega * t[i];
+          dXo[i] = xs[i] + omega * z[i];
+        }
+      } else {
+        for (long i = 0; i < n; ++i) dXo[i] = xs[i] + omega * z[i];
+        level_apply(&c->H, dXo, t);
+        for (long i = 0; i < n; ++i) dRo[i] = -t[i];
+      }
+      info->matvecs++;
+      info->iters++;
+      for (long i = 0; i < n; ++i) { r[i] += dRo[i]; x[i] += dXo[i]; }
+      rn = nrm2(r, n) / bn;
+      if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = rn;
+      info->rel_res_recur = rn;
+      if (!isfinite(rn)) { st = ST_NAN; goto done; }
+      if (rn < o->tol) { st = ST_OK; goto done; }
+      for (int i = 0; i < s; ++i) dm[i] = dotc(&P[(long)i * n], dRo, n);
+      for (int i = 0; i < s; ++i) { Mk[i + s * oldest] = dm[i]; m[i] += dm[i]; }
+      oldest = (oldest + 1) % s;
+    }
+  }
+done:
+  free(dR); free(dX); free(v); free(z); free(t); free(q); free(xs);
+  return st;
+}
+
+/* Modified Gram-Schmidt on the s rows of P (in place). */
+static void orthonormalise(cplx* P, int s, long n) {
+  for (int j = 0; j < s; ++j) {
+    cplx* pj = &P[(long)j * n];
+    for (int i = 0; i < j; ++i) {
+      cplx* pi = &P[(long)i * n];
+      cplx h = dotc(pi, pj, n);
+      for (long k = 0; k < n; ++k) pj[k] -= h * pi[k];
+    }
+    double nn = nrm2(pj, n);
+    for (long k = 0; k < n; ++k) pj[k] /= nn;
+  }
+}
+
+/* Full solve H x = b from x = 0 (the stopping rule of Section 6.2 is relative to d_0 = b),
+ * then the true residual b - H x is recomputed; if it misses tol the method restarts from
+ * the current x (at most max_restarts times).  shadow: s x n raw random vectors for IDR. */
+int orc_solve(const orc_ctx* c, const cplx* b, cplx* x, const orc_solve_opts* o,
+              const cplx* shadow, orc_info* info, double* hist, int hist_cap) {
+  long n = c->H.ntot;
+  memset(info, 0, sizeof(*info));
+  memset(x, 0, sizeof(cplx) * n);
+  double bn = nrm2(b, n);
+  if (!isfinite(bn)) { info->status = ST_NAN; return ST_NAN; }
+  if (bn == 0) { info->status = ST_OK; return ST_OK; }
+  if (o->method == 1 && (o->s < 1 || o->s > 64 || !shadow)) { info->status = 1; return 1; }
+  cplx* r = malloc(sizeof(cplx) * n);
+  cplx* P = NULL;
+  if (o->method == 1) {
+    P = malloc(sizeof(cplx) * (size_t)o->s * n);
+    memcpy(P, shadow, sizeof(cplx) * (size_t)o->s * n);
+    orthonormalise(P, o->s, n);
+  }
+  memcpy(r, b, sizeof(cplx) * n);
+  int st;
+  for (;;) {
+    st = o->method == 0 ? bicgstab_run(c, b, x, r, bn, o, info, hist, hist_cap)
+                        : idr_run(c, b, x, r, bn, P, o, info, hist, hist_cap);
+    /* true residual */
+    level_apply(&c->H, x, r);
+    for (long i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    info->rel_res_true = nrm2(r, n) / bn;
+    if (st != ST_OK) break;
+    if (info->rel_res_true < o->tol) break;
+    if (info->restarts >= o->max_restarts) { st = ST_MAXMV; break; }
+    info->restarts++;
+  }
+  info->status = st;
+  free(r); free(P);
+  return st;
+}

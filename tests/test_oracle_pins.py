@@ -1,0 +1,486 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's formulas: each compares it with a closed form,
+an invariant, a value the paper prints, a textbook special case or a library routine.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import helm_inputs as hi
+from oracle import Oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _prob(dim, n_int, n_l, theta=0.5, k0=0.0, extent=1.0, phi=None, rhs="random", seed=1):
+    p = hi.make_problem(dim, n_int, n_l, theta_gamma=theta, k0=k0, extent=extent, rhs=rhs, seed=seed)
+    if phi is not None:
+        p.phi = phi
+    return p
+
+
+def _node_z(n_int, nl, extent, theta):
+    """Complex coordinates of the unknowns and of the two Dirichlet ends, written from the
+    ECS map of Section 2 (layer width h e^{i theta}), independently of the oracle."""
+    h = extent / (n_int - 1)
+    hg = h * np.exp(1j * theta)
+    lo, hi_ = nl
+    z = [-m * hg for m in range(lo, 0, -1)]
+    first = 0 if lo > 0 else 1
+    last = n_int - 1 if hi_ > 0 else n_int - 2
+    z += [j * h for j in range(first, last + 1)]
+    z += [extent + m * hg for m in range(1, hi_ + 1)]
+    zlo = -(lo + 1) * hg if lo > 0 else 0.0
+    zhi = extent + (hi_ + 1) * hg if hi_ > 0 else extent
+    return np.asarray(z, np.complex128), zlo, zhi
+
+
+# ---- stencil -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n_int", [(1, 17), (2, 12), (3, 7)])
+def test_dirichlet_laplacian_eigenpairs(dim, n_int):
+    """theta = 0, k = 0, Dirichlet walls: sine modes are eigenvectors of the 5/7-point
+    Laplacian with lambda = sum_a (4/h^2) sin^2(l_a pi / (2(N+1)))."""
+    p = _prob(dim, n_int, 0, theta=0.0)
+    o = Oracle(p)
+    N = n_int - 2
+    h = 1.0 / (n_int - 1)
+    idx = np.arange(1, N + 1)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        ls = rng.integers(1, N + 1, size=dim)
+        vecs = [np.sin(l * np.pi * idx / (N + 1)) for l in ls]
+        v = vecs[0]
+        for a in range(1, dim):
+            v = np.multiply.outer(vecs[a], v)  # outer order (z, y, x) so ravel is x-fastest
+        v = v.ravel().astype(np.complex128)
+        lam = sum(4 / h**2 * np.sin(l * np.pi / (2 * (N + 1))) ** 2 for l in ls)
+        Hv = o.apply(v)
+        assert np.abs(Hv - lam * v).max() <= 1e-12 * lam * np.abs(v).max()
+
+
+def test_real_layers_are_a_longer_uniform_grid():
+    """theta = 0 layers are plain real grid points: with n_l layer nodes per side the 1D
+    operator is the Dirichlet Laplacian on N = n_int + 2 n_l unknowns with the same h."""
+    n_int, nl = 10, 3
+    p = _prob(1, n_int, nl, theta=0.0)
+    A = Oracle(p).dense()
+    N = n_int + 2 * nl
+    h = 1.0 / (n_int - 1)
+    ref = (np.diag(2 * np.ones(N)) - np.diag(np.ones(N - 1), 1) - np.diag(np.ones(N - 1), -1)) / h**2
+    assert np.abs(A - ref).max() <= 1e-12 / h**2
+
+
+def test_turning_point_rows_match_lemma31_matrix():
+    """The rows of -h^2 L_h printed in the proof of Lemma 3.1 (Section 3), golden fixture."""
+    rows = {}
+    with open(os.path.join(GOLDEN, "lemma31_scaled_operator.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *ex = line.split()
+            rows[name] = ex
+    theta, n_int, nl = 0.4, 9, 5
+    gamma = np.exp(1j * theta)
+    p = _prob(1, n_int, (0, nl), theta=theta)  # Dirichlet at x = 0, layer on the right
+    A = Oracle(p).dense()
+    h = 1.0 / (n_int - 1)
+    S = -h * h * (-A)  # -h^2 L_h with L_h = -A (k = 0)
+    S = h * h * A
+    ev = {k: [complex(eval(e, {"gamma": gamma})) for e in v] for k, v in rows.items()}
+    t = n_int - 2  # unknown index of the turning point x = 1 (first unknown is x = h)
+    assert np.allclose([S[3, 2], S[3, 3], S[3, 4]], ev["interior"], atol=1e-13)
+    assert np.allclose([S[t, t - 1], S[t, t], S[t, t + 1]], ev["turning"], atol=1e-13)
+    assert np.allclose([S[t + 2, t + 1], S[t + 2, t + 2], S[t + 2, t + 3]], ev["layer"], atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_shortley_weller_exact_for_quadratics(dim):
+    """SW (Section 3) is exact for quadratics in z on non-uniform complex widths, the
+    turning points included: for u = prod_a (z_a - zlo_a)(z_a - zhi_a) (zero on the
+    Dirichlet ends), H u = -Laplacian u - k^2 u exactly."""
+    n_int, nl, theta, k0 = (11, 4, 0.5, 3.0) if dim < 3 else (7, 2, 0.5, 3.0)
+    p = _prob(dim, n_int, nl, theta=theta, k0=k0)
+    o = Oracle(p)
+    zs = [_node_z(n_int, (nl, nl), 1.0, theta) for _ in range(dim)]
+    q = [(z - zlo) * (z - zhi) for (z, zlo, zhi) in zs]  # per-axis quadratic, q'' = 2
+
+    def outer(vs):
+        v = vs[0]
+        for a in range(1, dim):
+            v = np.multiply.outer(vs[a], v)
+        return v.ravel()
+
+    u = outer(q)
+    lap = np.zeros_like(u)
+    for a in range(dim):
+        vs = [q[b] if b != a else 2 * np.ones_like(q[a]) for b in range(dim)]
+        lap += outer(vs)
+    expect = -lap - k0 * k0 * u
+    assert np.abs(o.apply(u) - expect).max() <= 1e-10 * np.abs(expect).max()
+
+
+def test_weighted_operator_is_complex_symmetric():
+    """With w_j = (g_j + g_{j+1}) / 2 per axis, W H is complex symmetric (transpose, not
+    adjoint): x^T W H y = y^T W H x."""
+    p = _prob(2, 9, (2, 3), theta=0.5, k0=4.0)
+    o = Oracle(p)
+    w = []
+    for a in range(2):
+        g = o.axis_tables(0, 0, a)["gap"]
+        w.append((g[:-1] + g[1:]) / 2)
+    W = np.multiply.outer(w[1], w[0]).ravel()
+    x = hi.random_vector(p.n, 5)
+    y = hi.random_vector(p.n, 6)
+    lhs = x @ (W * o.apply(y))
+    rhs = y @ (W * o.apply(x))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _lemma_grid(n, m, theta):
+    """Lemma 3.2's 1D grid: Dirichlet at z = 0, n real widths h = 1/n, m layer widths."""
+    return _prob(1, n + 1, (0, m - 1), theta=theta)
+
+
+@pytest.mark.parametrize("n,m,theta", [(16, 8, 0.5), (24, 12, np.pi / 6), (10, 10, 0.3)])
+def test_eigenvalues_satisfy_lemma32(n, m, theta):
+    """Lemma 3.2 (Section 3): every eigenvalue of -L_h is a root of the turning-point
+    condition.  Written branch-free: with cos a = 1 - lambda h^2/2 and
+    cos b = 1 - lambda gamma^2 h^2 / 2,  sin(b) cot(m b) + gamma sin(a) cot(n a) = 0;
+    the paper's F(lambda) = tan(n a)/tan(m b) + cos(a/2)/cos(b/2) (with sin(b/2) =
+    gamma sin(a/2)) vanishes as well."""
+    A = Oracle(_lemma_grid(n, m, theta)).dense()
+    lam = np.linalg.eigvals(A)
+    h = 1.0 / n
+    gamma = np.exp(1j * theta)
+    a = np.arccos(1 - lam * h * h / 2)
+    b = np.arccos(1 - lam * (gamma * h) ** 2 / 2)
+    G = np.sin(b) / np.tan(m * b) + gamma * np.sin(a) / np.tan(n * a)
+    scale = np.abs(np.sin(b) / np.tan(m * b)) + np.abs(gamma * np.sin(a) / np.tan(n * a))
+    assert np.all(np.abs(G) <= 1e-7 * np.maximum(scale, 1.0))
+    # paper's form with a consistent branch for b/2
+    half_a = a / 2
+    half_b = np.arcsin(gamma * np.sin(half_a))
+    F = np.tan(n * 2 * half_a) / np.tan(m * 2 * half_b) + np.cos(half_a) / np.cos(half_b)
+    ok = np.abs(F) <= 1e-6 * (np.abs(np.tan(n * a) / np.tan(m * 2 * half_b)) + 1)
+    assert ok.mean() > 0.95  # a handful of near-poles of tan are ill-conditioned
+
+
+@pytest.mark.parametrize("theta", [np.pi / 12, np.pi / 8, np.pi / 6])
+def test_spectrum_inside_lemma31_rectangle(theta):
+    """Lemma 3.1 (Section 3): h^2 sigma(-L_h) lies in the rectangle derived from the field
+    of values; checked with the bounds as stated for 0 < theta <= pi/6."""
+    n, m = 20, 10
+    A = Oracle(_lemma_grid(n, m, theta)).dense()
+    h = 1.0 / n
+    mu = np.linalg.eigvals(A) * h * h
+    g = np.exp(1j * theta)
+    gb = np.conj(g)
+    re_lo = np.real(1 / g**2) - abs(1 / (2 * g**2) + 1 / (gb * (1 + gb)))
+    re_hi = max(4.0, 3 + 0.5 * abs((3 + gb) / (1 + gb)))
+    im_lo = np.imag(4 / g**2)
+    im_hi = 0.5 * abs((1 - gb) / (1 + gb))
+    eps = 1e-10
+    assert np.all(mu.real >= re_lo - eps) and np.all(mu.real <= re_hi + eps)
+    assert np.all(mu.imag >= im_lo - eps) and np.all(mu.imag <= im_hi + eps)
+
+
+def test_smallest_eigenvalues_near_continuous_ecs_line():
+    """Section 2 / Lemma 3.3 (third case): the smoothest modes have eigenvalues close to the
+    continuous ECS values (j pi / R_z)^2, R_z = 1 + m h e^{i theta}."""
+    n, m, theta = 200, 100, 0.3
+    A = Oracle(_lemma_grid(n, m, theta)).dense()
+    lam = np.linalg.eigvals(A)
+    h = 1.0 / n
+    Rz = 1 + m * h * np.exp(1j * theta)
+    for j in (1, 2, 3):
+        target = (j * np.pi / Rz) ** 2
+        near = lam[np.argmin(np.abs(lam - target))]
+        assert abs(near - target) / abs(target) < 2e-3
+
+
+def test_outgoing_wave_through_layers_1d():
+    """Constant k, unit source at node j0, ECS layers both sides: in the real interior the
+    discrete solution is the outgoing free-space wave A xi^{|j-j0|} (xi + 1/xi = 2 - k^2 h^2,
+    |xi| = 1, Im xi > 0, A = h^2 xi / (1 - xi^2)) up to the small reflections of the two
+    turning points and layer ends; inside a layer it decays by |eta| per node
+    (eta + 1/eta = 2 - k^2 gamma^2 h^2, |eta| < 1) (Section 2, ECS as absorbing layer)."""
+    n_int, nl, theta, kh = 201, 60, np.pi / 4, 0.3
+    h = 1.0 / (n_int - 1)
+    k = kh / h
+    p = _prob(1, n_int, nl, theta=theta, k0=k, rhs="zero")
+    j0 = nl + (n_int - 1) // 2
+    p.b[j0] = 1.0
+    u = Oracle(p).dense_solve(p.b)
+    c = 2 - (k * h) ** 2
+    xi = np.roots([1, -c, 1])
+    xi = xi[np.argmax(xi.imag)]
+    A = h * h * xi / (1 - xi * xi)
+    j = np.arange(nl, nl + n_int)
+    free = A * xi ** np.abs(j - j0)
+    err = np.abs(u[nl:nl + n_int] - free).max() / abs(A)
+    # reflection at a SW turning point: the discrete interface coefficient, computed from the
+    # two-sided recurrences (amplitudes 1 + R = T, turning-row equation).
+    g = np.exp(1j * theta)
+    eta = np.roots([1, -(2 - (k * h * g) ** 2), 1])
+    eta = eta[np.argmin(np.abs(eta))]
+    am, a0, ap = -2 / (h * h * (1 + g)), 2 / (g * h * h), -2 / (g * h * h * (1 + g))
+    # incoming xi^j from the left (node 0 = turning point), transmitted T eta^j on the right
+    # a_m (xi^-1 + R xi) + (a0 - k^2)(1 + R) + a_p (1 + R) eta = 0
+    R = -(am / xi + (a0 - k * k) + ap * eta) / (am * xi + (a0 - k * k) + ap * eta)
+    bound = 3 * (abs(R) + abs(eta) ** (2 * (nl + 1)))
+    assert err < bound
+    assert err < 0.05
+    # decay inside the right layer
+    lay = np.abs(u[nl + n_int: nl + n_int + 20])
+    ratios = lay[1:] / lay[:-1]
+    assert np.all(np.abs(ratios - abs(eta)) < 0.02)
+
+
+@pytest.mark.parametrize("n_int,nl", [(8, 2), (12, 3), (16, 0)])
+def test_dense_solve_matches_numpy(n_int, nl):
+    p = _prob(2, n_int, nl, theta=0.5, k0=7.0)
+    o = Oracle(p)
+    x = o.dense_solve(p.b)
+    ref = np.linalg.solve(o.dense(), p.b)
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_csl_csg_equivalence_operator_and_vcycle():
+    """Eq. "CSL-CSG" (Section 5.3): scaling every width by beta gives
+    M^CSG = beta^-2 M^CSL(beta^2), so one V-cycle on M^CSG is beta^2 times one V-cycle on
+    M^CSL with shift beta^2 = e^{2 i theta_beta} (phi sampled at real positions)."""
+    p = _prob(2, 20, 5, theta=0.5, k0=12.0)
+    tb = 0.3
+    beta2 = np.exp(2j * tb)
+    for sm in (hi.SM_JACOBI, hi.SM_RBGS):
+        og = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=tb, smoother=sm))
+        ol = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=beta2, smoother=sm))
+        x = hi.random_vector(p.n, 9)
+        assert np.allclose(og.apply(x, 1, 0), ol.apply(x, 1, 0) / beta2, rtol=1e-12, atol=1e-9)
+        zg, zl = og.vcycle(x), ol.vcycle(x)
+        assert np.linalg.norm(zg - beta2 * zl) <= 1e-12 * np.linalg.norm(zg)
+
+
+# ---- multigrid ---------------------------------------------------------------------------
+
+def test_hierarchy_sizes_and_total_length():
+    """Index-even coarsening: N -> floor(N/2) per axis; the complex widths of every level add
+    up to the same contour end-to-end length z_hi - z_lo."""
+    p = _prob(2, 33, (5, 6), theta=0.5, k0=1.0)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.2, coarse_max=3))
+    beta = np.exp(0.2j)
+    z, zlo, zhi = _node_z(33, (5, 6), 1.0, 0.5)
+    for lvl in range(o.nlev):
+        g = o.axis_tables(1, lvl, 0)["gap"]
+        assert np.isclose(g.sum(), beta * (zhi - zlo), rtol=1e-13)
+        if lvl:
+            assert o.level_shape(1, lvl)[0] == o.level_shape(1, lvl - 1)[0] // 2
+
+
+def test_transfer_operators_reproduce_linear_functions():
+    """FW restriction maps an index-linear fine field to the coarse samples at the coarse
+    nodes (away from the Dirichlet ends) and bilinear interpolation reproduces index-linear
+    coarse fields; P = 2^d R^T (the textbook FW / linear-interpolation pair)."""
+    p = _prob(2, 15, 3, theta=0.5, k0=1.0)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, coarse_max=4))
+    nx, ny = o.level_shape(1, 0)
+    cx, cy = o.level_shape(1, 1)
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny))  # (y, x)
+    f = (2.0 + 0.5 * I - 0.25j * J).ravel()
+    fc = o.restrict(0, f).reshape(cy, cx)
+    CI, CJ = np.meshgrid(np.arange(cx), np.arange(cy))
+    expect = 2.0 + 0.5 * (2 * CI + 1) - 0.25j * (2 * CJ + 1)
+    inner = (CI >= 0) & (2 * CI + 2 < nx) & (2 * CJ + 2 < ny)
+    assert np.allclose(fc[inner], expect[inner], atol=1e-13)
+    ec = expect.ravel()
+    u = o.prolong_add(0, ec, np.zeros(nx * ny)).reshape(ny, nx)
+    ok = (I >= 1) & (I <= 2 * cx - 1) & (J >= 1) & (J <= 2 * cy - 1)
+    assert np.allclose(u[ok], (2.0 + 0.5 * I - 0.25j * J)[ok], atol=1e-13)
+    # P = 4 R^T
+    R = np.stack([o.restrict(0, e) for e in np.eye(nx * ny)], axis=1)
+    P = np.stack([o.prolong_add(0, e, np.zeros(nx * ny)) for e in np.eye(cx * cy)], axis=1)
+    assert np.allclose(P, 4 * R.T, atol=1e-14)
+
+
+def test_rbgs_half_sweeps_zero_their_residuals():
+    """Gauss-Seidel: after the red half-sweep the red rows hold exactly; after the black
+    half-sweep the black rows hold (5-point coupling links only opposite colours)."""
+    p = _prob(2, 10, 2, theta=0.5, k0=5.0)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_RBGS))
+    f = hi.random_vector(p.n, 3)
+    u = o.smooth(0, np.zeros(p.n), f, 1)
+    r = f - o.apply(u, 1, 0)
+    nx, ny = o.level_shape(1, 0)
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny))
+    black = ((I + J) % 2 == 1).ravel()
+    assert np.abs(r[black]).max() <= 1e-12 * np.abs(f).max()
+    assert np.abs(r[~black]).max() > 1e-3 * np.abs(f).max()
+
+
+def _twogrid_fourier_rho(N, omega, nu1, nu2):
+    """Rigorous Fourier two-grid factor for the 2D Dirichlet Laplacian (k = 0), vertex grid
+    with N = 2^p - 1 unknowns per axis, omega-Jacobi, FW restriction, bilinear interpolation
+    and the rediscretised coarse operator: the sine harmonics {(k,l),(N+1-k,l),(k,N+1-l),
+    (N+1-k,N+1-l)} span invariant subspaces (textbook analysis, e.g. Trottenberg,
+    Oosterlee & Schueller, Multigrid, chapter 3)."""
+    h = 1.0 / (N + 1)
+    rho = 0.0
+    n2 = (N + 1) // 2
+
+    def s2(k):
+        return np.sin(k * np.pi * h / 2) ** 2
+
+    def lam(k, l):
+        return 4 / h**2 * (s2(k) + s2(l))
+
+    for k in range(1, n2 + 1):
+        for l in range(1, n2 + 1):
+            modes = [(k, l), (N + 1 - k, l), (k, N + 1 - l), (N + 1 - k, N + 1 - l)]
+            # keep distinct modes (k = n2 maps onto itself)
+            uniq = []
+            for md in modes:
+                if md not in uniq:
+                    uniq.append(md)
+            m = len(uniq)
+            S = np.diag([1 - omega * h * h / 4 * lam(*md) for md in uniq])
+            A = np.diag([lam(*md) for md in uniq])
+            if k < n2 and l < n2:
+                # restriction: 1D R phi_k = c_k phi^c_k, R phi_{N+1-k} = -s_k phi^c_k
+                ck, sk, cl, sl = 1 - s2(k), s2(k), 1 - s2(l), s2(l)
+                r = np.array([ck * cl, -sk * cl, -ck * sl, sk * sl])[:m]
+                pvec = r.copy()  # P phi^c = c phi_k - s phi_{N+1-k} per axis (same weights)
+                Ac = 4 / (2 * h) ** 2 * (np.sin(k * np.pi * h) ** 2 + np.sin(l * np.pi * h) ** 2)
+                CGC = np.eye(m) - np.outer(pvec, r) @ A / Ac
+            else:
+                CGC = np.eye(m)  # modes with no coarse counterpart are killed by R
+            E = np.linalg.matrix_power(S, nu2) @ CGC @ np.linalg.matrix_power(S, nu1)
+            rho = max(rho, np.abs(np.linalg.eigvals(E)).max())
+    return rho
+
+
+@pytest.mark.parametrize("omega,nu", [(0.5, (1, 1)), (0.8, (1, 1)), (0.8, (2, 1))])
+def test_twogrid_factor_matches_fourier_analysis(omega, nu):
+    """k = 0, theta = 0, Dirichlet walls, two levels (exact coarse solve): the spectral
+    radius of the oracle's two-grid error operator I - V A equals the closed-form Fourier
+    two-grid factor."""
+    N = 15
+    p = _prob(2, N + 2, 0, theta=0.0, k0=0.0)
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.0, smoother=hi.SM_JACOBI, omega=omega,
+                    nu1=nu[0], nu2=nu[1], max_levels=2, coarse_max=1)
+    o = Oracle(p, pc)
+    assert o.nlev == 2
+    n = p.n
+    A = o.dense()
+    B = np.stack([o.vcycle(e) for e in np.eye(n)], axis=1)
+    rho = np.abs(np.linalg.eigvals(np.eye(n) - B @ A)).max()
+    ref = _twogrid_fourier_rho(N, omega, *nu)
+    assert abs(rho - ref) < 1e-8, (rho, ref)
+
+
+def test_vcycle_is_linear_and_single_level_is_direct():
+    p = _prob(2, 18, 4, theta=0.5, k0=10.0)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3))
+    x, y = hi.random_vector(p.n, 1), hi.random_vector(p.n, 2)
+    a, b = 0.3 - 1.2j, 2.0 + 0.1j
+    lhs = o.vcycle(a * x + b * y)
+    assert np.linalg.norm(lhs - (a * o.vcycle(x) + b * o.vcycle(y))) <= 1e-12 * np.linalg.norm(lhs)
+    o1 = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, max_levels=1))
+    M = o1.dense(1, 0)
+    assert np.allclose(o1.vcycle(x), np.linalg.solve(M, x), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("sm", [hi.SM_JACOBI, hi.SM_RBGS])
+def test_vcycle_contracts_on_ecs_laplacian(sm):
+    """k = 0 with ECS layers (theta 0.5): the multilevel V(1,1) cycle contracts about as fast
+    as the Fourier two-grid factor of the real Poisson problem predicts (Jacobi), and much
+    faster with red-black Gauss-Seidel."""
+    p = _prob(2, 32, 8, theta=0.5, k0=0.0)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.0, smoother=sm))
+    f = np.zeros(p.n, np.complex128)
+    u = hi.random_vector(p.n, 4)
+    e0 = np.linalg.norm(u)
+    for _ in range(6):  # error iteration u <- u - V(A u) for A u = 0
+        u = u - o.vcycle(o.apply(u, 1, 0) - f)
+    factor = (np.linalg.norm(u) / e0) ** (1 / 6)
+    if sm == hi.SM_JACOBI:
+        assert factor < _twogrid_fourier_rho(31, 0.5, 1, 1) + 0.05
+    else:
+        assert factor < 0.25
+
+
+# ---- Krylov ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+def test_unpreconditioned_krylov_reaches_direct_solution(method):
+    p = _prob(2, 8, 2, theta=0.5, k0=6.0)
+    o = Oracle(p)
+    x_ref = o.dense_solve(p.b)
+    opts = hi.SolveOpts(method=method, s=4, tol=1e-12, maxmv=5000)
+    x, info = o.solve(p.b, opts, shadow=hi.shadow_space(p.n, 4))
+    assert info["status"] == 0
+    assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    assert info["rel_res_true"] < 1e-11
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 8])
+def test_idr_finite_termination(s):
+    """IDR(s) reaches the exact solution within N + N/s matvecs in exact arithmetic
+    (Sonneveld & van Gijzen 2008).  A small, well-conditioned system keeps the rounding
+    drift from the exact-arithmetic property to a couple of matvecs (on larger non-normal
+    systems finite precision loses termination, as it does for Bi-CGSTAB)."""
+    p = _prob(1, 18, 3, theta=0.2, k0=1.0)  # N = 24 unknowns
+    o = Oracle(p)
+    opts = hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=400)
+    x, info = o.solve(p.b, opts, shadow=hi.shadow_space(p.n, s))
+    n = p.n
+    assert info["status"] == 0
+    assert info["matvecs"] <= n + n / s + 3
+
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+def test_mg_preconditioned_solve_reaches_direct_solution(method):
+    p = _prob(2, 24, 6, theta=0.5, k0=12.0, rhs="point")
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3))
+    x_ref = o.dense_solve(p.b)
+    opts = hi.SolveOpts(method=method, s=4, tol=1e-11, maxmv=500)
+    x, info = o.solve(p.b, opts, shadow=hi.shadow_space(p.n, 4))
+    assert info["status"] == 0 and info["rel_res_true"] < 1e-11
+    assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+def test_scaling_the_preconditioner_leaves_iterates_unchanged(method):
+    """Right preconditioning by c M^{-1} gives the same x-iterates; CSG(theta) is beta^2 times
+    CSL(e^{2 i theta}), so both runs follow the same residual history (compare the MP1 ECS
+    rows of Table MP1, where the two preconditioners tie).  In floating point the two
+    histories agree to rounding at first and then drift apart geometrically, as any two
+    Bi-CGSTAB/IDR runs with different rounding do; the counts stay within 2 and both
+    solutions meet the tolerance."""
+    p = _prob(2, 32, 8, theta=0.5, k0=20.0, rhs="point")
+    tb = 0.3
+    og = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=tb))
+    ol = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=np.exp(2j * tb)))
+    opts = hi.SolveOpts(method=method, s=4, tol=1e-8)
+    sh = hi.shadow_space(p.n, 4)
+    xg, ig = og.solve(p.b, opts, shadow=sh, history=True)
+    xl, il = ol.solve(p.b, opts, shadow=sh, history=True)
+    assert np.allclose(ig["history"][:8], il["history"][:8], rtol=1e-12, atol=0)
+    assert abs(ig["matvecs"] - il["matvecs"]) <= 2
+    assert ig["rel_res_true"] < 1e-8 and il["rel_res_true"] < 1e-8
+    assert np.linalg.norm(xg - xl) <= 1e-7 * np.linalg.norm(xg)
+
+
+def test_zero_rhs_and_stopping_rule():
+    p = _prob(2, 16, 4, theta=0.5, k0=8.0, rhs="zero")
+    o = Oracle(p, hi.Precond())
+    x, info = o.solve(p.b, hi.SolveOpts())
+    assert info["status"] == 0 and info["matvecs"] == 0 and not np.any(x)
+    p = _prob(2, 16, 4, theta=0.5, k0=8.0, rhs="point")
+    o = Oracle(p, hi.Precond())
+    x, info = o.solve(p.b, hi.SolveOpts(tol=1e-6), history=True)
+    h = info["history"]
+    assert h[-1] < 1e-6 and np.all(h[:-1] >= 1e-6)  # stops at the first recurrence hit
+    assert info["rel_res_true"] < 1e-6
