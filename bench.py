@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the ECS Helmholtz solver on the 512^2 + 64-layer workload.
+
+Workload (one "step"): the 2D ECS Helmholtz problem with a 512 x 512 interior grid and a
+64-node ECS layer on every side (640 x 640 = 409,600 unknowns), theta_gamma = 0.5, kh = 0.5
+(k0 = 255.5), k(x) = k0 (1 + 0.3 exp(-|x - c|^2 / 0.02)), Gaussian source of width 2h at a
+seeded position, solved to a relative residual of 1e-6 four times:
+{Bi-CGSTAB, IDR(4)} x {CSG theta_beta = 0.3, CSL shift 1 + 0.5i}, one V(1,1) cycle with
+omega-Jacobi (0.5) per preconditioned matvec.  Every solve is certified by the FP64 true
+residual ||b - H x|| / ||b|| < 1e-6 recomputed on the device.
+
+`value` is the all-FP64 path (FP64 V-cycle and Krylov); the FP32-multigrid path (FP32 V-cycle,
+FP64 Krylov and true residual) is measured on the same step and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own copy (replicas, no data
+exchange); the barrier and the max over ranks time the job.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import helm_inputs as hi  # noqa: E402
+
+METRIC = "solves/s at 1e-6 true rel. residual, FP32-MG vs FP64; p50/p99 latency; HBM %peak"
+TOL = 1e-6
+SOLVES = [("bicgstab", hi.BICGSTAB, "csg"), ("bicgstab", hi.BICGSTAB, "csl"),
+          ("idr4", hi.IDR, "csg"), ("idr4", hi.IDR, "csl")]
+
+
+def precond(name: str) -> hi.Precond:
+    if name == "csg":
+        return hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    return hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+
+
+def config(p) -> dict:
+    return {"workload": p.name, "grid": "512^2 interior + 64 ECS nodes per side (640^2 unknowns)",
+            "n_unknowns": p.n, "solves_per_step": len(SOLVES),
+            "solves": "{Bi-CGSTAB, IDR(4)} x {CSG theta_beta=0.3, CSL shift 1+0.5i}",
+            "multigrid": "V(1,1), omega-Jacobi 0.5, FW, bilinear, rediscretised levels, dense coarsest",
+            "tol": TOL, "l2": "flushed (512 MiB device write) before every timed step"}
+
+
+# ---- clocks ------------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- CPU oracle ---------------------------------------------------------------------------
+
+def oracle_counts():
+    path = os.path.join(ROOT, "oracle", "workload_counts.json")
+    with open(path) as fh:
+        d = json.load(fh)
+    return {(s["method"], s["precond"]): s["matvecs"] for s in d["solves"]}
+
+
+def oracle_sample(p, mv_per_method: int) -> dict:
+    """Times the oracle (single thread) on a bounded sample: mv_per_method preconditioned
+    matvecs of Bi-CGSTAB and of IDR(4) on the workload (CSG); returns seconds per matvec."""
+    import oracle
+    o = oracle.Oracle(p, precond("csg"))
+    sh = hi.shadow_space(p.n, 4)
+    out = {}
+    for name, method in (("bicgstab", hi.BICGSTAB), ("idr4", hi.IDR)):
+        t = time.perf_counter()
+        _, info = o.solve(p.b, hi.SolveOpts(method=method, s=4, tol=1e-30, maxmv=mv_per_method, max_restarts=0),
+                          shadow=sh)
+        out[name] = (time.perf_counter() - t) / max(info["matvecs"], 1)
+    return out
+
+
+def oracle_step_seconds(per_mv: dict, counts: dict) -> float:
+    return sum(counts[(m, pc)] * per_mv[m] for (m, _, pc) in SOLVES)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = hi.workload_2d_512()
+    counts = oracle_counts()
+    mv = int(os.environ.get("HELM_REF_SAMPLE_MV", "24"))
+    step_s = []
+    for k in range(args.warmup + args.steps):
+        per = oracle_sample(p, mv)
+        if k >= args.warmup:
+            step_s.append(oracle_step_seconds(per, counts))
+    ms = 1000 * statistics.mean(step_s)
+    value = len(SOLVES) / (ms / 1000)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config(p),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {mv} preconditioned matvecs each of Bi-CGSTAB and IDR(4) "
+                                       f"(CSG) on the full 640^2 workload, single thread; seconds per matvec "
+                                       f"x the oracle's own matvec counts of the four solves "
+                                       f"(oracle/workload_counts.json)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU ------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    g.build()
+    from paper_0912_0180_gb300 import _lib as L
+    from paper_0912_0180_gb300.helm import Helm
+
+    p = hi.workload_2d_512()
+    sh = hi.shadow_space(p.n, 4)
+    dev = torch.device("cuda", local)
+    b_dev = torch.from_numpy(p.b).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ctxs = {}
+    for mg in ("c128", "c64"):
+        for pcn in ("csg", "csl"):
+            ctxs[(mg, pcn)] = Helm(p, precond(pcn), mg_dtype=mg)
+
+    def one_step(mg: str, lat: list, infos: list, e2e_host=None):
+        x = None
+        for (mname, method, pcn) in SOLVES:
+            h = ctxs[(mg, pcn)]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if e2e_host is not None:
+                b_in = e2e_host["b"].to(dev, non_blocking=True)
+                x, info = h.solve(b_in, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh)
+                e2e_host["x"].copy_(x, non_blocking=True)
+            else:
+                x, info = h.solve(b_dev, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh)
+            e1.record()
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return x
+
+    def timed(mg: str, e2e=False):
+        host = None
+        if e2e:
+            host = {"b": torch.from_numpy(p.b).pin_memory(), "x": torch.empty(p.n, dtype=torch.complex128).pin_memory()}
+        for _ in range(args.warmup):
+            one_step(mg, [], [], host)
+        lat, infos, step_ms = [], [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            one_step(mg, lat, infos, host)
+            s1.record()
+            barrier()
+            step_ms.append(s0.elapsed_time(s1))
+        return step_ms, lat, infos
+
+    with ClockSampler(local) as clk:
+        ms64, lat64, inf64 = timed("c128")
+        ms32, lat32, inf32 = timed("c64")
+    e2e_ms, _, _ = timed("c128", e2e=True)
+
+    for info in inf64 + inf32:
+        if info.status != 0 or not info.rel_res_true < TOL:
+            raise SystemExit(f"a timed solve did not converge: {info}")
+
+    step64 = max_over_ranks(statistics.mean(ms64))
+    step32 = max_over_ranks(statistics.mean(ms32))
+    stepe2e = max_over_ranks(statistics.mean(e2e_ms))
+    nsol = len(SOLVES) * world
+    value = nsol / (step64 / 1000)
+
+    # ---- per-kernel rooflines, measured with CUDA events on the launching stream ----
+    kern = kernel_rooflines(torch, L, ctxs, p, dev)
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v), q))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config(p),
+        "latency_ms": {"p50": pct(lat64, 50), "p99": pct(lat64, 99)},
+        "matvecs": {f"{m}-{pc}": inf64[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)},
+        "fp32_mg": {"value": nsol / (step32 / 1000), "unit": "solves/s", "ms_per_step": step32,
+                    "dtype": "c64 V-cycle, c128 Krylov and true residual",
+                    "latency_ms": {"p50": pct(lat32, 50), "p99": pct(lat32, 99)},
+                    "matvecs": {f"{m}-{pc}": inf32[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)},
+                    "max_true_rel_res": max(i.rel_res_true for i in inf32)},
+        "max_true_rel_res": max(i.rel_res_true for i in inf64),
+        "clocks": clk.summary(),
+        "e2e": {"value": nsol / (stepe2e / 1000), "unit": "solves/s",
+                "h2d_bytes_per_step": len(SOLVES) * p.n * 16, "d2h_bytes_per_step": len(SOLVES) * p.n * 16},
+        "gpu_launches": int(sum(i.kernels for i in inf64[: len(SOLVES) * args.steps]) +
+                            sum(i.kernels for i in inf32)),
+        "roofline": kern["dominant"],
+        "kernels": kern["table"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            per = oracle_sample(p, int(os.environ.get("HELM_CPU_SAMPLE_MV", "60")))
+            sec = oracle_step_seconds(per, oracle_counts())
+            line["cpu_baseline"] = {"value": len(SOLVES) / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": "60 preconditioned matvecs each of Bi-CGSTAB and IDR(4) (CSG) on "
+                                              "the full workload, single thread; seconds per matvec x the "
+                                              "oracle's own matvec counts of the four solves"}
+        except Exception as e:  # the oracle is a reported baseline; never fail the GPU line on it
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"unavailable: {e}"}
+    for h in ctxs.values():
+        h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_rooflines(torch, L, ctxs, p, dev) -> dict:
+    """Average duration of the hot kernels on the finest level, CUDA events on the launching
+    stream, achieved = algorithmic bytes (or FLOPs) per launch / duration."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (unit count inferred from a
+    # measured 1.2 TFLOP/s FP64 FMA loop; nominal 1.25 TFLOP/s)
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    n = p.n
+    reps = 50
+    table = {}
+    st = torch.cuda.current_stream()
+
+    def time_it(fn):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0  # seconds
+
+    for mg, dt, esz, psz in (("c64", torch.complex64, 8, 4), ("c128", torch.complex128, 16, 8)):
+        h = ctxs[(mg, "csg")]
+        u = torch.randn(n, dtype=dt, device=dev)
+        f = torch.randn(n, dtype=dt, device=dev)
+        out = torch.empty(n, dtype=dt, device=dev)
+        # damped-Jacobi sweeps from a guess: each reads u, f, phi and writes u' (two sweeps per
+        # call so that the result lands back in the caller's buffer without a copy)
+        t = time_it(lambda: h.level_op(L.HELM_OP_SMOOTH, 0, u, f, None, count=2)) / 2
+        byt = n * (3 * esz + psz)
+        table[f"jacobi_sweep_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
+        t = time_it(lambda: h.level_op(L.HELM_OP_RESIDUAL, 0, u, f, out))
+        table[f"residual_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
+    h = ctxs[("c128", "csg")]
+    x = torch.randn(n, dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    t = time_it(lambda: h.apply(x, out=y))
+    byt = n * (16 + 16 + 8)
+    flops = n * 48
+    table["h_apply_c128"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9, "TFLOP/s": flops / t / 1e12}
+    dom = table["jacobi_sweep_c128"]
+    # FP64 sweep: ~ 56 flops per unknown (diagonal, 4 complex FMAs, residual, complex divide, update)
+    fl = n * 56
+    ach = fl / (dom["us"] * 1e-6) / 1e12
+    dominant = {"kernel": "k_jacobi<double,2> (finest level, FP64 path)", "bound": "alu", "achieved": ach,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)",
+                "hbm_GBs_achieved": dom["GB/s"], "hbm_peak_GBs": hbm, "hbm_peak_source": hbm_src}
+    for k, v in table.items():
+        v["frac_hbm"] = v["GB/s"] / hbm
+    return {"dominant": dominant, "table": table}
+
+
+if __name__ == "__main__":
+    main()

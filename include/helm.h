@@ -1,0 +1,184 @@
+/*
+ * helm.h -- C ABI of the GB300 ECS-Helmholtz solver (libhelm.so).
+ *
+ * The library solves H u = b for the indefinite Helmholtz operator
+ *     H u = -(Laplacian + phi(x)) u,  phi = k(x)^2                 (Section 2, eq. "helmctu0";
+ *                                                                  variable k: Section 4, eq. "Helgen")
+ * discretised by the Shortley-Weller second difference (Section 3, eq. "shortwell") on a
+ * vertex-centred grid whose ends are continued by exterior-complex-scaled (ECS) layers with
+ * mesh width h e^{i theta_gamma} (Section 2, the linear ECS map; Section 3, eq. "ecsgrid").
+ * It uses right-preconditioned Bi-CGSTAB or IDR(s) (Section 6.2) with one multigrid V-cycle
+ * on a complex-shifted-Laplacian (CSL, Section 5.2, eq. "helmctucsl") or complex-stretched-
+ * grid (CSG, Section 5.3, eqs. "CSL-CSG" and "lapctucsg") preconditioner per matvec.
+ *
+ * Conventions for every entry point:
+ *   - Vectors are DEVICE pointers on the current CUDA device, complex interleaved
+ *     (re, im) of the element type given by helm_dtype, holding every unknown (interior and
+ *     layer nodes; Dirichlet nodes are not stored), index i + Nx*(j + Ny*l), x fastest.
+ *     They must be 16-byte aligned (8-byte for HELM_C64) and must not alias unless stated.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued on it;
+ *     calls return before the GPU finishes unless stated.  helm_solve synchronises the
+ *     stream once at the end to return its statistics.
+ *   - The caller owns b, x and every array it passes.  The library owns the context, the
+ *     multigrid hierarchy and all workspace, released by helm_destroy.  helm_create allocates
+ *     the operator and the hierarchy; the first helm_solve with a given (method, s) allocates
+ *     its Krylov workspace and captures its graphs (a different (method, s) replaces them).
+ *     Nothing else allocates device memory.
+ *   - No call aborts, traps or throws: every call returns a helm_status.  Argument errors are
+ *     detected on the host before anything is launched.  A context is not thread-safe.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_ERR_ARG = 1,       /* invalid argument (sizes, kinds, NULL pointers, misalignment) */
+  HELM_ERR_OOM = 2,       /* device allocation failed in helm_create */
+  HELM_ERR_CUDA = 3,      /* a CUDA runtime call failed; see helm_last_error() */
+  HELM_ERR_BREAKDOWN = 4, /* Krylov breakdown: rho, (r^, v), |t|^2 or omega became zero */
+  HELM_ERR_MAXIT = 5,     /* matvec cap reached (or true-residual restarts exhausted) */
+  HELM_ERR_NAN = 6,       /* a norm or inner product was not finite */
+  HELM_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up */
+  HELM_ERR_BUSY = 8       /* reserved */
+} helm_status;
+
+typedef enum { HELM_C64 = 0 /* complex float32 */, HELM_C128 = 1 /* complex float64 */ } helm_dtype;
+
+enum { HELM_PC_NONE = 0, HELM_PC_CSL = 1, HELM_PC_CSG_UNIFORM = 2, HELM_PC_CSG_INTERIOR = 3 };
+enum { HELM_SM_JACOBI = 0, HELM_SM_RBGS = 1 };
+enum { HELM_BICGSTAB = 0, HELM_IDR = 1 };
+
+/* Grid of one instance (Section 3, eq. "ecsgrid", extended per axis).  Along axis a the
+ * interior holds n_int[a] nodes at 0, h, ..., extent[a] (h = extent/(n_int-1)); a side with
+ * n_layer[a][side] = m > 0 continues with m ECS nodes of width h e^{i theta_gamma} and a
+ * Dirichlet node after them; a side with m = 0 is a Dirichlet wall (its end node is not an
+ * unknown).  Unknowns per axis: n_int - 2 + (m_lo ? m_lo + 1 : 0) + (m_hi ? m_hi + 1 : 0). */
+typedef struct {
+  int dim;              /* 1, 2 or 3 */
+  int n_int[3];         /* >= 2 (>= 3 for a side without layer); unused axes ignored */
+  int n_layer[3][2];    /* >= 0 */
+  double extent[3];     /* > 0 */
+  double theta_gamma;   /* ECS angle in radians, 0 <= theta_gamma < pi/2 */
+} helm_grid;
+
+/* Wave number: phi = k(x)^2 at the real node positions (the layers continue the real
+ * coordinate).  phi == NULL means the constant k0. */
+typedef struct {
+  double k0;
+  const double* phi;    /* HOST pointer to N real values (x fastest), read during helm_create only */
+} helm_kspec;
+
+/* Preconditioner M and the V(nu1, nu2)-cycle that approximates M^{-1} (Section 5;
+ * components of Section 6.1: full-weighting restriction, bilinear/trilinear prolongation,
+ * rediscretised coarse operators, damped Jacobi or red-black Gauss-Seidel smoothing, and a
+ * direct solve on the coarsest level). */
+typedef struct {
+  int kind;             /* HELM_PC_*: NONE = identity; CSL: M = -(L + shift * phi);
+                           CSG_UNIFORM: every width times e^{i theta_beta}, M = -(L_beta + phi);
+                           CSG_INTERIOR: only interior widths scaled */
+  double theta_beta;    /* CSG angle */
+  double shift_re, shift_im; /* CSL shift beta^2 */
+  int nu1, nu2;         /* 0..8 sweeps */
+  int smoother;         /* HELM_SM_JACOBI or HELM_SM_RBGS */
+  double omega;         /* Jacobi damping, 0 < omega <= 1 */
+  int max_levels;       /* >= 1 */
+  int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
+  helm_dtype mg_dtype;  /* HELM_C64: whole V-cycle in complex FP32; HELM_C128: FP64 */
+} helm_precond;
+
+/* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
+ * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;
+ * if it misses tol the method restarts from x (at most max_restarts times). */
+typedef struct {
+  int method;           /* HELM_BICGSTAB or HELM_IDR */
+  int s;                /* IDR shadow dimension, 1..8 */
+  double tol;           /* > 0 */
+  int maxmv;            /* cap on preconditioned matvecs (V-cycle + H apply), >= 1 */
+  int max_restarts;     /* >= 0 */
+  const void* shadow;   /* IDR: HOST pointer to s x N complex128 raw random vectors (row j =
+                           vector j), orthonormalised by the library; required for IDR.  The
+                           orthonormalised copy is cached per context and keyed on this
+                           pointer: pass a different pointer to change the shadow space */
+  double* history;      /* optional DEVICE array of maxmv doubles: entry m-1 receives the
+                           recurrence residual / ||b|| after preconditioned matvec m (the
+                           convergence history of the paper's Figure "krylov"); NULL = off */
+} helm_solve_opts;
+
+typedef struct {
+  helm_status status;
+  int iters;            /* Bi-CGSTAB iterations or IDR steps */
+  int matvecs;          /* preconditioned matvecs */
+  int restarts;
+  double rel_res_recur; /* last recurrence residual / ||b|| */
+  double rel_res_true;  /* ||b - H x|| / ||b|| recomputed in FP64 */
+  long kernels;         /* kernel launches the solve executed on the device */
+} helm_solve_info;
+
+typedef struct helm_ctx helm_ctx;
+
+/* Builds the grid, the FP64 operator H and the preconditioner hierarchy on the current
+ * device (setup kernels on `stream`, then synchronises).  Returns HELM_ERR_ARG for invalid
+ * sizes/kinds, HELM_ERR_OOM if device memory runs out (nothing is leaked). */
+helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_precond* pc,
+                        void* stream, helm_ctx** out);
+
+/* Number of unknowns N of the instance (0 if ctx is NULL). */
+long helm_size(const helm_ctx* ctx);
+
+/* Device bytes held by the context. */
+size_t helm_workspace_bytes(const helm_ctx* ctx);
+
+/* y = H x (eq. "helmctu0" discretised by eq. "shortwell").  dtype HELM_C128: x, y complex128,
+ * FP64 arithmetic.  dtype HELM_C64: x complex64 read and y complex128 written, FP64
+ * arithmetic (the upcast is exact).  x and y must not alias. */
+helm_status helm_apply(helm_ctx* ctx, helm_dtype dtype, const void* x, void* y, void* stream);
+
+/* z = one V(nu1, nu2)-cycle on the preconditioner from a zero initial guess, z ~ M^{-1} r
+ * (Section 5.1).  r is complex128; z has the hierarchy's mg_dtype.  For HELM_PC_NONE, z = r
+ * (converted).  r and z must not alias. */
+helm_status helm_vcycle(helm_ctx* ctx, const void* r, void* z, void* stream);
+
+/* Single multigrid component on level `lvl` of the hierarchy (element type = mg_dtype), for
+ * testing each kernel against a reference:
+ *   HELM_OP_APPLY     out = M_lvl a
+ *   HELM_OP_RESIDUAL  out = b - M_lvl a
+ *   HELM_OP_SMOOTH    a <- `count` smoothing sweeps on M_lvl a = b (in place; out unused)
+ *   HELM_OP_SMOOTH0   a <- the first sweep from a zero guess, then count-1 sweeps
+ *   HELM_OP_RESTRICT  out (level lvl+1) = full weighting of a (level lvl)
+ *   HELM_OP_PROLONG   a (level lvl) += bilinear interpolation of b (level lvl+1)
+ *   HELM_OP_COARSE    out = M_coarsest^{-1} a (lvl must be the coarsest level) */
+enum { HELM_OP_APPLY = 0, HELM_OP_RESIDUAL = 1, HELM_OP_SMOOTH = 2, HELM_OP_SMOOTH0 = 3,
+       HELM_OP_RESTRICT = 4, HELM_OP_PROLONG = 5, HELM_OP_COARSE = 6 };
+helm_status helm_level_op(helm_ctx* ctx, int op, int lvl, void* a, const void* b, void* out,
+                          int count, void* stream);
+
+/* Number of multigrid levels and the unknowns per axis of level lvl (n[3]). */
+int helm_num_levels(const helm_ctx* ctx);
+helm_status helm_level_shape(const helm_ctx* ctx, int lvl, int* n);
+
+/* Solves H x = b from x = 0 (b, x complex128, device, no aliasing).  Returns the final
+ * status (also in info->status); x always holds the last iterate.  The whole Krylov loop runs
+ * on the device (one graph launch per solve, a conditional WHILE node around one iteration);
+ * the host synchronises once at the end to read the statistics. */
+helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, const helm_solve_opts* opts,
+                       helm_solve_info* info, void* stream);
+
+/* Releases everything the context holds (synchronises the device first).  NULL is a no-op. */
+void helm_destroy(helm_ctx* ctx);
+
+const char* helm_status_str(helm_status s);
+
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

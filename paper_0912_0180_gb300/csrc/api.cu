@@ -1,0 +1,200 @@
+// api.cu -- the extern "C" entry points declared in include/helm.h: argument validation on
+// the host, context lifetime, and dispatch to the setup, multigrid and Krylov code.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+helm_status cuda_check(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA;
+}
+
+helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HELM_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return HELM_ERR_OOM;
+  }
+  c->allocs.push_back(*p);
+  c->bytes += bytes;
+  return HELM_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static helm_status check_grid(const helm_grid* g) {
+  if (!g || g->dim < 1 || g->dim > 3) { set_error("grid.dim must be 1, 2 or 3"); return HELM_ERR_ARG; }
+  if (!(g->theta_gamma >= 0.0 && g->theta_gamma < M_PI / 2)) { set_error("theta_gamma out of [0, pi/2)"); return HELM_ERR_ARG; }
+  long total = 1;
+  for (int a = 0; a < g->dim; ++a) {
+    int lo = g->n_layer[a][0], hi = g->n_layer[a][1];
+    if (lo < 0 || hi < 0 || g->n_int[a] < 2 || !(g->extent[a] > 0.0) || !std::isfinite(g->extent[a])) {
+      set_error("invalid n_int / n_layer / extent");
+      return HELM_ERR_ARG;
+    }
+    long n = (long)g->n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+    if (n < 1 || n > (1L << 24)) { set_error("axis has no unknowns or too many"); return HELM_ERR_ARG; }
+    total *= n;
+    if (total > (1L << 34)) { set_error("grid too large"); return HELM_ERR_ARG; }
+  }
+  return HELM_OK;
+}
+
+static helm_status check_precond(const helm_precond* p) {
+  if (!p) { set_error("precond is NULL"); return HELM_ERR_ARG; }
+  if (p->kind < HELM_PC_NONE || p->kind > HELM_PC_CSG_INTERIOR) { set_error("precond.kind"); return HELM_ERR_ARG; }
+  if (p->kind == HELM_PC_NONE) return HELM_OK;
+  if (p->nu1 < 0 || p->nu1 > 8 || p->nu2 < 0 || p->nu2 > 8) { set_error("nu1/nu2 must be in 0..8"); return HELM_ERR_ARG; }
+  if (p->smoother != HELM_SM_JACOBI && p->smoother != HELM_SM_RBGS) { set_error("smoother"); return HELM_ERR_ARG; }
+  if (p->smoother == HELM_SM_JACOBI && !(p->omega > 0.0 && p->omega <= 1.0)) { set_error("omega must be in (0, 1]"); return HELM_ERR_ARG; }
+  if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
+  if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
+  if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
+  if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {
+    set_error("non-finite preconditioner parameter");
+    return HELM_ERR_ARG;
+  }
+  return HELM_OK;
+}
+
+static void ctx_release(helm_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  krylov_free(c);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" {
+
+helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_precond* pc, void* stream,
+                        helm_ctx** out) {
+  if (!out) { set_error("out is NULL"); return HELM_ERR_ARG; }
+  *out = nullptr;
+  helm_status s;
+  if ((s = check_grid(grid)) != HELM_OK) return s;
+  if ((s = check_precond(pc)) != HELM_OK) return s;
+  if (!k || !std::isfinite(k->k0)) { set_error("kspec missing or k0 not finite"); return HELM_ERR_ARG; }
+  helm_ctx* c = new helm_ctx();
+  c->grid = *grid;
+  c->pc = *pc;
+  for (int a = grid->dim; a < 3; ++a) {
+    c->grid.n_int[a] = 3;
+    c->grid.n_layer[a][0] = c->grid.n_layer[a][1] = 0;
+    c->grid.extent[a] = 1.0;
+  }
+  cudaGetDevice(&c->dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (k->phi) {
+    long n = 1;
+    for (int a = 0; a < grid->dim; ++a) {
+      int lo = grid->n_layer[a][0], hi = grid->n_layer[a][1];
+      n *= (long)grid->n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+    }
+    for (long i = 0; i < n; ++i)
+      if (!std::isfinite(k->phi[i])) { delete c; set_error("phi has a non-finite entry"); return HELM_ERR_ARG; }
+  }
+  if ((s = build_operator(c, k, st)) != HELM_OK) { ctx_release(c); return s; }
+  if ((s = build_hierarchy(c, st)) != HELM_OK) { ctx_release(c); return s; }
+  if (pc->kind != HELM_PC_NONE && pc->mg_dtype == HELM_C64) {
+    if ((s = ctx_alloc(c, &c->scratch, sizeof(float2) * c->n)) != HELM_OK) { ctx_release(c); return s; }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { ctx_release(c); return cuda_check(e, "helm_create"); }
+  *out = c;
+  return HELM_OK;
+}
+
+long helm_size(const helm_ctx* c) { return c ? c->n : 0; }
+
+size_t helm_workspace_bytes(const helm_ctx* c) { return c ? c->bytes : 0; }
+
+int helm_num_levels(const helm_ctx* c) { return c ? (int)c->lv.size() : 0; }
+
+helm_status helm_level_shape(const helm_ctx* c, int lvl, int* n) {
+  if (!c || !n || lvl < 0 || lvl >= (int)c->lv.size()) { set_error("bad level"); return HELM_ERR_ARG; }
+  for (int a = 0; a < 3; ++a) n[a] = c->lv[lvl].n[a];
+  return HELM_OK;
+}
+
+helm_status helm_apply(helm_ctx* c, helm_dtype dtype, const void* x, void* y, void* stream) {
+  if (!c || !x || !y || x == y) { set_error("helm_apply: NULL or aliased arguments"); return HELM_ERR_ARG; }
+  if (dtype != HELM_C64 && dtype != HELM_C128) { set_error("helm_apply: dtype"); return HELM_ERR_ARG; }
+  if (!aligned(x, dtype == HELM_C64 ? 8 : 16) || !aligned(y, 16)) { set_error("helm_apply: misaligned"); return HELM_ERR_ARG; }
+  return h_apply(c, dtype == HELM_C64, x, (double2*)y, (cudaStream_t)stream);
+}
+
+helm_status helm_vcycle(helm_ctx* c, const void* r, void* z, void* stream) {
+  if (!c || !r || !z || r == z) { set_error("helm_vcycle: NULL or aliased arguments"); return HELM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  bool f32 = c->pc.mg_dtype == HELM_C64;
+  if (!aligned(r, 16) || !aligned(z, f32 ? 8 : 16)) { set_error("helm_vcycle: misaligned"); return HELM_ERR_ARG; }
+  if (c->pc.kind == HELM_PC_NONE) {
+    if (f32) return convert_c128_to_mg(c, (const double2*)r, z, st);
+    cudaError_t e = cudaMemcpyAsync(z, r, sizeof(double2) * c->n, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HELM_OK : cuda_check(e, "helm_vcycle copy");
+  }
+  if (f32) {
+    helm_status s = convert_c128_to_mg(c, (const double2*)r, c->scratch, st);
+    if (s != HELM_OK) return s;
+    return mg_vcycle<float>(c, (const float2*)c->scratch, (float2*)z, nullptr, st);
+  }
+  return mg_vcycle<double>(c, (const double2*)r, (double2*)z, nullptr, st);
+}
+
+helm_status helm_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, void* out, int count,
+                          void* stream) {
+  if (!c) { set_error("ctx is NULL"); return HELM_ERR_ARG; }
+  return mg_level_op(c, op, lvl, a, b, out, count, (cudaStream_t)stream);
+}
+
+helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opts* o, helm_solve_info* info,
+                       void* stream) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!c || !b || !x || !o || b == x) { set_error("helm_solve: NULL or aliased arguments"); return HELM_ERR_ARG; }
+  if (!aligned(b, 16) || !aligned(x, 16)) { set_error("helm_solve: misaligned"); return HELM_ERR_ARG; }
+  if (o->method != HELM_BICGSTAB && o->method != HELM_IDR) { set_error("method"); return HELM_ERR_ARG; }
+  if (o->method == HELM_IDR && (o->s < 1 || o->s > 8 || !o->shadow)) { set_error("IDR needs 1 <= s <= 8 and a shadow array"); return HELM_ERR_ARG; }
+  if (!(o->tol > 0.0) || o->maxmv < 1 || o->max_restarts < 0) { set_error("tol / maxmv / max_restarts"); return HELM_ERR_ARG; }
+  helm_status s = krylov_solve(c, (const double2*)b, (double2*)x, o, info, (cudaStream_t)stream);
+  if (info) info->status = s;
+  return s;
+}
+
+void helm_destroy(helm_ctx* c) { ctx_release(c); }
+
+const char* helm_status_str(helm_status s) {
+  switch (s) {
+    case HELM_OK: return "ok";
+    case HELM_ERR_ARG: return "invalid argument";
+    case HELM_ERR_OOM: return "out of device memory";
+    case HELM_ERR_CUDA: return "CUDA error";
+    case HELM_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HELM_ERR_MAXIT: return "matvec cap reached";
+    case HELM_ERR_NAN: return "non-finite value";
+    case HELM_ERR_TIMEOUT: return "device wait timed out";
+    case HELM_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* helm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

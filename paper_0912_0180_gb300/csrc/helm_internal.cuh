@@ -1,0 +1,145 @@
+// helm_internal.cuh -- types shared by the translation units of libhelm (device views of
+// the operators, the multigrid hierarchy, the Krylov state, complex helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+// ---- complex arithmetic on float2 / double2 ------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <typename T> using cx = typename cvec<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mkc(T re, T im) {
+  cx<T> z; z.x = re; z.y = im; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mkc<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mkc<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * b + c
+template <typename T> __host__ __device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> c) {
+  return mkc<T>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mkc<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mkc<T>(s * a.x, s * a.y); }
+template <typename T> __host__ __device__ __forceinline__ T cabs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
+  T d = b.x * b.x + b.y * b.y;
+  return mkc<T>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> crecip(cx<T> b) {
+  T d = b.x * b.x + b.y * b.y;
+  return mkc<T>(b.x / d, -b.y / d);
+}
+template <typename TO, typename TI> __host__ __device__ __forceinline__ cx<TO> cconv(cx<TI> a) {
+  return mkc<TO>((TO)a.x, (TO)a.y);
+}
+
+// ---- operator view ---------------------------------------------------------------------
+// A level operator: per-axis Shortley-Weller rows (am, a0, ap) and sigma = s * phi.
+template <typename T> struct OpView {
+  int n[3];
+  const cx<T>* am[3];
+  const cx<T>* a0[3];
+  const cx<T>* ap[3];
+  const T* phi;   // nullptr -> phi0 everywhere
+  T phi0;
+  cx<T> s;
+};
+
+// ---- owned device storage of one level ---------------------------------------------------
+struct LevelHost {
+  int dim = 0;
+  int n[3] = {1, 1, 1};
+  long ntot = 0;
+  // FP64 tables (always), FP32 copies (MG in FP32)
+  double2* gap[3] = {nullptr, nullptr, nullptr};   // n+1 widths
+  double* pos[3] = {nullptr, nullptr, nullptr};    // n real positions
+  double2* coef64[3][3] = {};                      // [axis][am,a0,ap]
+  float2* coef32[3][3] = {};
+  double* phi64 = nullptr;   // nullptr when constant
+  float* phi32 = nullptr;
+  double phi0 = 0.0;
+  double2 s = {1.0, 0.0};
+  // work vectors (MG type), allocated for multigrid levels
+  void* u = nullptr;
+  void* f = nullptr;
+  void* w = nullptr;
+
+  template <typename T> OpView<T> view() const;
+};
+
+struct KrylovState;  // device-side scalars, defined in krylov.cu
+
+struct Workspace;    // Krylov vectors, defined in krylov.cu
+
+}  // namespace helm
+
+struct helm_ctx {
+  helm_grid grid{};
+  helm_precond pc{};
+  int dev = 0;
+  long n = 0;
+  helm::LevelHost H;                 // the FP64 Helmholtz operator
+  std::vector<helm::LevelHost> lv;   // preconditioner hierarchy
+  void* coarse_inv = nullptr;        // dense inverse of the coarsest M (mg dtype)
+  int nco = 0;
+  size_t bytes = 0;                  // device bytes held
+  std::vector<void*> allocs;         // everything to free
+  helm::Workspace* ws = nullptr;     // Krylov workspace (lazily created)
+  void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
+};
+
+namespace helm {
+
+// error bookkeeping (per thread)
+void set_error(const std::string& msg);
+helm_status cuda_check(cudaError_t e, const char* what);
+#define HELM_CUDA(call)                                            \
+  do {                                                             \
+    cudaError_t _e = (call);                                       \
+    if (_e != cudaSuccess) return ::helm::cuda_check(_e, #call);   \
+  } while (0)
+
+// device allocation owned by the context
+helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes);
+
+// setup.cu
+helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st);
+helm_status build_hierarchy(helm_ctx* c, cudaStream_t st);
+
+// mg.cu
+template <typename T>
+helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, cx<T>* u0, const int* skip, cudaStream_t st);
+helm_status mg_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, void* out, int count,
+                        cudaStream_t st);
+// y = H x (FP64 arithmetic); x of type TX; optional fused partial inner products handled in krylov.cu
+helm_status h_apply(helm_ctx* c, bool x_is_f32, const void* x, double2* y, cudaStream_t st);
+helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st);
+
+// krylov.cu
+helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
+                         helm_solve_info* info, cudaStream_t st);
+void krylov_free(helm_ctx* c);
+
+inline int grid_blocks(long work, int threads, int cap) {
+  long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace helm

@@ -1,0 +1,960 @@
+// krylov.cu -- right-preconditioned Bi-CGSTAB (van der Vorst 1992) and IDR(s) (Sonneveld &
+// van Gijzen 2008), the Krylov methods of Section 6.2, run entirely on the device.
+//
+// FP64 vectors and inner products; the V-cycle runs in the hierarchy's precision: the vector
+// entering it is written in that precision by the update kernel that produces it (fused
+// precision boundary), and its FP32 output is read directly by the FP64 matvec (exact upcast).
+//
+// Scalars (rho, alpha, omega, norms, status) live in a device struct.  Every inner product is
+// reduced in the producing kernel: per-block partials, then the last block to finish (atomic
+// ticket) sums the partials in a fixed order -- deterministic -- and updates the scalars.
+// One iteration is captured once into a CUDA graph and driven by a conditional WHILE node
+// whose condition the last kernel of the iteration sets, so a whole solve is one graph launch.
+// No kernel waits on another: there is no device-side spin anywhere.
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "stencil.cuh"
+
+namespace helm {
+
+constexpr int KT = 256;      // threads per block of the vector kernels
+constexpr int SMAX = 8;      // largest IDR shadow dimension
+constexpr int NRED = SMAX + 2;
+
+struct KrylovState {
+  double2 rho, rho_old, alpha, omega, beta;
+  double bnorm, tol, rel_recur, rel_true;
+  int done, status, half, matvecs, iters, maxmv;
+  int k, oldest, s, loops;  // loops: body executions of the WHILE node in this solve
+  double2 M[SMAX * SMAX];  // IDR: P^H dR, column-major M[i + s*j]
+  double2 m[SMAX];         // IDR: P^H r
+  double2 c[SMAX];         // IDR: M^{-1} m
+  unsigned int ticket[8];  // last-block counters, one per reduction site
+  double* hist;            // optional residual history (device), capacity maxmv
+};
+
+struct Workspace {
+  int method = -1, s = 0;
+  int G = 0;                   // blocks of the vector kernels (fixed -> fixed reduction order)
+  KrylovState* st = nullptr;   // device
+  KrylovState* hst = nullptr;  // pinned host copy
+  double2* partials = nullptr; // [NRED][G]
+  double2 *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *sv = nullptr, *t = nullptr, *q = nullptr;
+  void *pmg = nullptr, *smg = nullptr, *ph = nullptr, *sh = nullptr;  // mg precision
+  double2 *P = nullptr, *dR = nullptr, *dX = nullptr;                  // IDR, s vectors each
+  const void* shadow_key = nullptr;
+  cudaGraphExec_t loop = nullptr;
+  cudaGraphExec_t idr_init = nullptr;
+  cudaGraph_t loop_graph = nullptr, init_graph = nullptr;
+  size_t body_nodes = 0, init_nodes = 0;  // kernels per loop body / IDR start graph
+  std::vector<void*> mem;
+};
+
+// ---- block reductions -------------------------------------------------------------------
+
+template <int K>
+__device__ __forceinline__ void warp_sum(double2 (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      v[k].x += __shfl_down_sync(0xffffffffu, v[k].x, o);
+      v[k].y += __shfl_down_sync(0xffffffffu, v[k].y, o);
+    }
+}
+
+// Sum K values over the block; thread 0 gets the totals.
+template <int K>
+__device__ __forceinline__ void block_sum(double2 (&v)[K]) {
+  __shared__ double2 sm[K][KT / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  warp_sum<K>(v);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k][w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = lane < KT / 32 ? sm[k][lane] : mkc<double>(0.0, 0.0);
+    warp_sum<K>(v);
+  }
+  __syncthreads();
+}
+
+// Stores this block's K partial sums, then returns true in the last block to arrive, where
+// `tot` holds the grand totals (summed in a fixed order) on every thread.
+template <int K>
+__device__ bool reduce_last(double2 (&v)[K], double2* partials, unsigned int* ticket, double2 (&tot)[K]) {
+  __shared__ bool last;
+  __shared__ double2 res[K];
+  block_sum<K>(v);
+  int G = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * G + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == (unsigned int)G - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double2 a[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    a[k] = mkc<double>(0.0, 0.0);
+    for (int b = threadIdx.x; b < G; b += KT) {
+      double2 pv = __ldcg(&partials[k * G + b]);
+      a[k].x += pv.x;
+      a[k].y += pv.y;
+    }
+  }
+  block_sum<K>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) res[k] = a[k];
+    *ticket = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = res[k];
+  return true;
+}
+
+__device__ __forceinline__ bool finite2(double2 z) { return isfinite(z.x) && isfinite(z.y); }
+__device__ __forceinline__ bool is_zero(double2 z) { return z.x == 0.0 && z.y == 0.0; }
+
+__device__ __forceinline__ void record(KrylovState* S, double rn) {
+  S->rel_recur = rn;
+  if (S->hist && S->matvecs >= 1 && S->matvecs <= S->maxmv) S->hist[S->matvecs - 1] = rn;
+}
+
+__device__ __forceinline__ void finish(KrylovState* S, int status) {
+  S->status = status;
+  S->done = 1;
+}
+
+template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i, double2 v) {
+  if (dst) reinterpret_cast<cx<TM>*>(dst)[i] = cconv<TM, double>(v);
+}
+
+#define GRID_LOOP(i, n) for (long i = blockIdx.x * (long)KT + threadIdx.x; i < (n); i += (long)gridDim.x * KT)
+
+// ---- shared kernels ----------------------------------------------------------------------
+
+// Start (or restart) from the current residual r: ||r||, shadow r^ = r, p = v = 0 and
+// rho = r^H r.  first: r = b and ||b|| sets the scale of the stopping rule.
+__global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* r, double2* rh,
+                        double2* p, double2* v, void* rmg, int mg32, long n, int first,
+                        double2* partials) {
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) {
+    double2 ri = first ? b[i] : r[i];
+    if (first) r[i] = ri;
+    if (rh) rh[i] = ri;
+    if (p) { p[i] = mkc<double>(0.0, 0.0); v[i] = mkc<double>(0.0, 0.0); }
+    if (rmg) { if (mg32) put_mg<float>(rmg, i, ri); else put_mg<double>(rmg, i, ri); }
+    acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot)) return;
+  if (threadIdx.x) return;
+  double rr = tot[0].x;
+  if (first) {
+    S->bnorm = sqrt(rr);
+    S->matvecs = 0; S->iters = 0;
+  }
+  S->done = 0; S->half = 0; S->status = HELM_ERR_MAXIT;
+  S->rho = mkc<double>(rr, 0.0);
+  S->rho_old = S->alpha = S->omega = mkc<double>(1.0, 0.0);
+  S->beta = S->rho;  // p = v = 0, so beta only multiplies zeros on the first step
+  S->k = 0; S->oldest = 0;
+  S->loops = 0;
+  S->rel_recur = sqrt(rr) / S->bnorm;
+  if (!isfinite(rr)) finish(S, HELM_ERR_NAN);
+  else if (S->bnorm == 0.0) { S->rel_recur = 0.0; finish(S, HELM_OK); }
+  else if (S->matvecs >= S->maxmv) finish(S, HELM_ERR_MAXIT);
+}
+
+// r = b - H x and ||r|| / ||b|| (the FP64 true residual that certifies convergence).
+template <int DIM>
+__global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __restrict__ b,
+                           const double2* __restrict__ x, double2* __restrict__ r, long n, double2* partials) {
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    double2 ri = csub<double>(b[p], op_row<double, double, DIM>(H, x, i, j, l, p));
+    r[p] = ri;
+    acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[1], tot)) return;
+  if (threadIdx.x) return;
+  S->rel_true = S->bnorm > 0.0 ? sqrt(tot[0].x) / S->bnorm : 0.0;
+}
+
+// Sets the WHILE condition from `done`.  At the end of the body it also counts the body
+// executions and, as a guard against a logic error, stops a loop that has run more bodies than
+// the matvec cap allows (status HELM_ERR_TIMEOUT) -- every live body costs at least one matvec.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, KrylovState* S, int in_body) {
+  if (in_body) {
+    S->loops += 1;
+    if (!S->done && S->loops > S->maxmv + 16) finish(S, HELM_ERR_TIMEOUT);
+  }
+  cudaGraphSetConditional(h, S->done ? 0u : 1u);
+}
+
+// ---- Bi-CGSTAB -----------------------------------------------------------------------------
+
+// p = r + beta (p - omega v); its copy in multigrid precision feeds the V-cycle.
+template <typename TM>
+__global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ p,
+                         const double2* __restrict__ v, void* pmg, long n) {
+  if (S->done) return;
+  double2 beta = S->beta, om = S->omega;
+  GRID_LOOP(i, n) {
+    double2 pi = cadd<double>(r[i], cmul<double>(beta, csub<double>(p[i], cmul<double>(om, v[i]))));
+    p[i] = pi;
+    put_mg<TM>(pmg, i, pi);
+  }
+}
+
+// v = H p^ and alpha = rho / (r^H v).
+template <typename TM, int DIM>
+__global__ void k_bicg_v(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ ph,
+                         const double2* __restrict__ rh, double2* __restrict__ v, long n, double2* partials) {
+  if (S->done) return;
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    double2 vi = op_row<double, TM, DIM>(H, ph, i, j, l, p);
+    v[p] = vi;
+    acc[0] = cadd<double>(acc[0], cmulc<double>(rh[p], vi));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[2], tot)) return;
+  if (threadIdx.x) return;
+  S->matvecs += 1;
+  S->iters += 1;
+  double2 rv = tot[0];
+  if (!finite2(rv)) { finish(S, HELM_ERR_NAN); return; }
+  if (is_zero(rv)) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  S->alpha = cdiv<double>(S->rho, rv);
+}
+
+// s = r - alpha v, ||s||; stop after the half step if ||s|| / ||b|| < tol (or at the cap).
+template <typename TM>
+__global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const double2* __restrict__ v,
+                         double2* __restrict__ sv, void* smg, long n, double2* partials) {
+  if (S->done) return;
+  double2 al = S->alpha;
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) {
+    double2 si = csub<double>(r[i], cmul<double>(al, v[i]));
+    sv[i] = si;
+    put_mg<TM>(smg, i, si);
+    acc[0].x = fma(si.x, si.x, fma(si.y, si.y, acc[0].x));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot)) return;
+  if (threadIdx.x) return;
+  double sn = sqrt(tot[0].x) / S->bnorm;
+  record(S, sn);
+  if (!isfinite(sn)) { finish(S, HELM_ERR_NAN); return; }
+  if (sn < S->tol) { S->half = 1; finish(S, HELM_OK); return; }
+  if (S->matvecs >= S->maxmv) { S->half = 1; finish(S, HELM_ERR_MAXIT); }
+}
+
+// x += alpha p^ after a half-step exit.
+template <typename TM>
+__global__ void k_bicg_xhalf(KrylovState* S, const cx<TM>* __restrict__ ph, double2* __restrict__ x, long n) {
+  if (!S->half) return;
+  double2 al = S->alpha;
+  GRID_LOOP(i, n) x[i] = cfma<double>(al, cconv<double, TM>(ph[i]), x[i]);
+}
+
+// t = H s^, omega = (t^H s) / (t^H t).
+template <typename TM, int DIM>
+__global__ void k_bicg_t(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ sh,
+                         const double2* __restrict__ sv, double2* __restrict__ t, long n, double2* partials) {
+  if (S->done) return;
+  double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    double2 ti = op_row<double, TM, DIM>(H, sh, i, j, l, p);
+    t[p] = ti;
+    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, sv[p]));
+    acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
+  }
+  double2 tot[2];
+  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot)) return;
+  if (threadIdx.x) return;
+  S->matvecs += 1;
+  double tt = tot[1].x;
+  if (!isfinite(tt) || !finite2(tot[0])) { finish(S, HELM_ERR_NAN); return; }
+  if (tt == 0.0) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  S->omega = cscale<double>(1.0 / tt, tot[0]);
+}
+
+// x += alpha p^ + omega s^; r = s - omega t; ||r||, rho = r^H r and the next beta.
+template <typename TM>
+__global__ void k_bicg_xr(KrylovState* S, const cx<TM>* __restrict__ ph, const cx<TM>* __restrict__ sh,
+                          const double2* __restrict__ sv, const double2* __restrict__ t,
+                          const double2* __restrict__ rh, double2* __restrict__ x, double2* __restrict__ r,
+                          long n, double2* partials) {
+  if (S->done) return;
+  double2 al = S->alpha, om = S->omega;
+  double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) {
+    x[i] = cfma<double>(om, cconv<double, TM>(sh[i]), cfma<double>(al, cconv<double, TM>(ph[i]), x[i]));
+    double2 ri = csub<double>(sv[i], cmul<double>(om, t[i]));
+    r[i] = ri;
+    acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
+    acc[1] = cadd<double>(acc[1], cmulc<double>(rh[i], ri));
+  }
+  double2 tot[2];
+  if (!reduce_last<2>(acc, partials, &S->ticket[5], tot)) return;
+  if (threadIdx.x) return;
+  double rn = sqrt(tot[0].x) / S->bnorm;
+  record(S, rn);
+  if (!isfinite(rn)) { finish(S, HELM_ERR_NAN); return; }
+  if (rn < S->tol) { finish(S, HELM_OK); return; }
+  if (is_zero(om)) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  if (S->matvecs >= S->maxmv) { finish(S, HELM_ERR_MAXIT); return; }
+  double2 rho = tot[1];
+  if (!finite2(rho)) { finish(S, HELM_ERR_NAN); return; }
+  if (is_zero(rho)) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  S->rho_old = S->rho;
+  S->rho = rho;
+  S->beta = cmul<double>(cdiv<double>(rho, S->rho_old), cdiv<double>(S->alpha, om));
+}
+
+// ---- IDR(s) -------------------------------------------------------------------------------
+
+// out_i = P_i^H y for i < s (one pass over y).  Used for the shadow-space projections.
+template <int S_>
+__device__ __forceinline__ void proj_acc(const double2* __restrict__ P, long n, long i, double2 y, double2* acc) {
+#pragma unroll
+  for (int k = 0; k < S_; ++k) acc[k] = cadd<double>(acc[k], cmulc<double>(P[k * n + i], y));
+}
+
+// Minimal-residual start step k: t = H z, omega = (t^H r) / (t^H t).
+template <typename TM, int DIM>
+__global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ z,
+                           const double2* __restrict__ r, double2* __restrict__ t, long n, double2* partials) {
+  if (S->done) return;
+  double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    double2 ti = op_row<double, TM, DIM>(H, z, i, j, l, p);
+    t[p] = ti;
+    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, r[p]));
+    acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
+  }
+  double2 tot[2];
+  if (!reduce_last<2>(acc, partials, &S->ticket[2], tot)) return;
+  if (threadIdx.x) return;
+  S->matvecs += 1;
+  S->iters += 1;
+  double tt = tot[1].x;
+  if (!isfinite(tt)) { finish(S, HELM_ERR_NAN); return; }
+  if (tt == 0.0) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  S->omega = cscale<double>(1.0 / tt, tot[0]);
+}
+
+// dX_k = omega z, dR_k = -omega t, x += dX_k, r += dR_k, ||r||.
+template <typename TM>
+__global__ void k_idr_mr_upd(KrylovState* S, int kcol, const cx<TM>* __restrict__ z, const double2* __restrict__ t,
+                             double2* __restrict__ dX, double2* __restrict__ dR, double2* __restrict__ x,
+                             double2* __restrict__ r, void* rmg, long n, double2* partials) {
+  if (S->done) return;
+  double2 om = S->omega;
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) {
+    double2 dx = cmul<double>(om, cconv<double, TM>(z[i]));
+    double2 dr = cmul<double>(om, t[i]);
+    dr = mkc<double>(-dr.x, -dr.y);
+    dX[kcol * n + i] = dx;
+    dR[kcol * n + i] = dr;
+    x[i] = cadd<double>(x[i], dx);
+    double2 ri = cadd<double>(r[i], dr);
+    r[i] = ri;
+    put_mg<TM>(rmg, i, ri);
+    acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot)) return;
+  if (threadIdx.x) return;
+  double rn = sqrt(tot[0].x) / S->bnorm;
+  record(S, rn);
+  if (!isfinite(rn)) { finish(S, HELM_ERR_NAN); return; }
+  if (rn < S->tol) { finish(S, HELM_OK); return; }
+  if (S->matvecs >= S->maxmv) finish(S, HELM_ERR_MAXIT);
+}
+
+// Projections onto the shadow space: column `col` of M = P^H dR_col, or m = P^H r (col < 0).
+template <int S_>
+__global__ void k_idr_proj(KrylovState* S, const double2* __restrict__ P, const double2* __restrict__ y,
+                           int col, long n, double2* partials) {
+  if (S->done) return;
+  double2 acc[S_];
+#pragma unroll
+  for (int k = 0; k < S_; ++k) acc[k] = mkc<double>(0.0, 0.0);
+  GRID_LOOP(i, n) proj_acc<S_>(P, n, i, y[i], acc);
+  double2 tot[S_];
+  if (!reduce_last<S_>(acc, partials, &S->ticket[6], tot)) return;
+  if (threadIdx.x) return;
+  for (int k = 0; k < S_; ++k) {
+    if (col >= 0) S->M[k + S_ * col] = tot[k];
+    else S->m[k] = tot[k];
+  }
+}
+
+// c = M^{-1} m (s x s, Gaussian elimination with partial pivoting, one thread).
+__global__ void k_idr_small(KrylovState* S) {
+  if (S->done || threadIdx.x) return;
+  if (S->matvecs >= S->maxmv) { finish(S, HELM_ERR_MAXIT); return; }
+  int s = S->s;
+  double2 A[SMAX][SMAX], b[SMAX];
+  for (int i = 0; i < s; ++i) {
+    b[i] = S->m[i];
+    for (int j = 0; j < s; ++j) A[i][j] = S->M[i + s * j];
+  }
+  for (int k = 0; k < s; ++k) {
+    int pv = k;
+    for (int rr = k + 1; rr < s; ++rr)
+      if (cabs2<double>(A[rr][k]) > cabs2<double>(A[pv][k])) pv = rr;
+    if (is_zero(A[pv][k])) { finish(S, HELM_ERR_BREAKDOWN); return; }
+    if (pv != k) {
+      for (int j = 0; j < s; ++j) { double2 tt = A[k][j]; A[k][j] = A[pv][j]; A[pv][j] = tt; }
+      double2 tt = b[k]; b[k] = b[pv]; b[pv] = tt;
+    }
+    for (int rr = k + 1; rr < s; ++rr) {
+      double2 f = cdiv<double>(A[rr][k], A[k][k]);
+      for (int j = k; j < s; ++j) A[rr][j] = csub<double>(A[rr][j], cmul<double>(f, A[k][j]));
+      b[rr] = csub<double>(b[rr], cmul<double>(f, b[k]));
+    }
+  }
+  for (int rr = s - 1; rr >= 0; --rr) {
+    double2 acc = b[rr];
+    for (int j = rr + 1; j < s; ++j) acc = csub<double>(acc, cmul<double>(A[rr][j], S->c[j]));
+    S->c[rr] = cdiv<double>(acc, A[rr][rr]);
+  }
+}
+
+// q = -dR c, v = r + q (and v in multigrid precision).
+template <typename TM, int S_>
+__global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, const double2* __restrict__ r,
+                        double2* __restrict__ q, void* vmg, long n) {
+  if (S->done) return;
+  double2 c[S_];
+#pragma unroll
+  for (int k = 0; k < S_; ++k) c[k] = S->c[k];
+  GRID_LOOP(i, n) {
+    double2 acc = mkc<double>(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < S_; ++k) acc = csub<double>(acc, cmul<double>(dR[k * n + i], c[k]));
+    q[i] = acc;
+    put_mg<TM>(vmg, i, cadd<double>(r[i], acc));
+  }
+}
+
+// First step of a cycle (k == 0): t = H z, omega = (t^H v) / (t^H t), v = r + q.
+template <typename TM, int DIM>
+__global__ void k_idr_t0(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ z,
+                         const double2* __restrict__ r, const double2* __restrict__ q,
+                         double2* __restrict__ t, long n, double2* partials) {
+  if (S->done || S->k != 0) return;
+  double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    double2 ti = op_row<double, TM, DIM>(H, z, i, j, l, p);
+    t[p] = ti;
+    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, cadd<double>(r[p], q[p])));
+    acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
+  }
+  double2 tot[2];
+  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot)) return;
+  if (threadIdx.x) return;
+  double tt = tot[1].x;
+  if (!isfinite(tt) || !finite2(tot[0])) { finish(S, HELM_ERR_NAN); return; }
+  if (tt == 0.0) { finish(S, HELM_ERR_BREAKDOWN); return; }
+  S->omega = cscale<double>(1.0 / tt, tot[0]);
+}
+
+// dX_oldest = -dX c + omega z (in place: each entry reads its row of dX before writing).
+template <typename TM, int S_>
+__global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const cx<TM>* __restrict__ z, long n) {
+  if (S->done) return;
+  double2 c[S_];
+#pragma unroll
+  for (int k = 0; k < S_; ++k) c[k] = S->c[k];
+  double2 om = S->omega;
+  int o = S->oldest;
+  GRID_LOOP(i, n) {
+    double2 acc = cmul<double>(om, cconv<double, TM>(z[i]));
+#pragma unroll
+    for (int k = 0; k < S_; ++k) acc = csub<double>(acc, cmul<double>(dX[k * n + i], c[k]));
+    dX[o * n + i] = acc;
+  }
+}
+
+// Later steps (k > 0): t = H dX_oldest.
+template <int DIM>
+__global__ void k_idr_tk(const KrylovState* S, OpView<double> H, const double2* __restrict__ dX,
+                         double2* __restrict__ t, long n) {
+  if (S->done || S->k == 0) return;
+  const double2* d = dX + S->oldest * n;
+  GRID_LOOP(p, n) {
+    int i, j, l;
+    unflatten(p, H.n, i, j, l);
+    t[p] = op_row<double, double, DIM>(H, d, i, j, l, p);
+  }
+}
+
+// dR_oldest = (k == 0 ? q - omega t : -t); r += dR_oldest; x += dX_oldest; ||r||;
+// dm = P^H dR_oldest updates M and m; advance oldest and k.
+template <int S_>
+__global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2* __restrict__ dR,
+                          const double2* __restrict__ dX, const double2* __restrict__ q,
+                          const double2* __restrict__ t, double2* __restrict__ x, double2* __restrict__ r,
+                          long n, double2* partials) {
+  if (S->done) return;
+  int o = S->oldest;
+  bool first = S->k == 0;
+  double2 om = S->omega;
+  double2 acc[S_ + 1];
+#pragma unroll
+  for (int k = 0; k <= S_; ++k) acc[k] = mkc<double>(0.0, 0.0);
+  GRID_LOOP(i, n) {
+    double2 ti = t[i];
+    double2 dr = first ? csub<double>(q[i], cmul<double>(om, ti)) : mkc<double>(-ti.x, -ti.y);
+    dR[o * n + i] = dr;
+    double2 ri = cadd<double>(r[i], dr);
+    r[i] = ri;
+    x[i] = cadd<double>(x[i], dX[o * n + i]);
+    acc[S_].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[S_].x));
+    proj_acc<S_>(P, n, i, dr, acc);
+  }
+  double2 tot[S_ + 1];
+  if (!reduce_last<S_ + 1>(acc, partials, &S->ticket[5], tot)) return;
+  if (threadIdx.x) return;
+  S->matvecs += 1;
+  S->iters += 1;
+  double rn = sqrt(tot[S_].x) / S->bnorm;
+  record(S, rn);
+  if (!isfinite(rn)) { finish(S, HELM_ERR_NAN); return; }
+  if (rn < S->tol) { finish(S, HELM_OK); return; }
+  for (int k = 0; k < S_; ++k) {
+    S->M[k + S_ * o] = tot[k];
+    S->m[k] = cadd<double>(S->m[k], tot[k]);
+  }
+  S->oldest = (o + 1) % S_;
+  S->k = (S->k + 1) % (S_ + 1);
+}
+
+// Modified Gram-Schmidt on the shadow vectors: h = P_i^H P_j ...
+__global__ void k_dot1(KrylovState* S, const double2* __restrict__ a, const double2* __restrict__ b,
+                       long n, double2* partials, double2* out) {
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) acc[0] = cadd<double>(acc[0], cmulc<double>(a[i], b[i]));
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[7], tot)) return;
+  if (threadIdx.x == 0) *out = tot[0];
+}
+// ... P_j -= h P_i  (mode 0)  or  P_j /= sqrt(h)  (mode 1, h = P_j^H P_j)
+__global__ void k_mgs_upd(double2* __restrict__ pj, const double2* __restrict__ pi, const double2* h, int mode, long n) {
+  double2 hv = *h;
+  double sc = mode ? 1.0 / sqrt(hv.x) : 0.0;
+  GRID_LOOP(i, n) {
+    if (mode) pj[i] = cscale<double>(sc, pj[i]);
+    else pj[i] = csub<double>(pj[i], cmul<double>(hv, pi[i]));
+  }
+}
+
+// ---- host orchestration ---------------------------------------------------------------------
+
+static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc failed for the Krylov workspace");
+    return HELM_ERR_OOM;
+  }
+  w->mem.push_back(*p);
+  c->bytes += bytes;
+  return HELM_OK;
+}
+
+void krylov_free(helm_ctx* c) {
+  Workspace* w = c->ws;
+  if (!w) return;
+  if (w->loop) cudaGraphExecDestroy(w->loop);
+  if (w->idr_init) cudaGraphExecDestroy(w->idr_init);
+  if (w->loop_graph) cudaGraphDestroy(w->loop_graph);
+  if (w->init_graph) cudaGraphDestroy(w->init_graph);
+  for (void* p : w->mem) cudaFree(p);
+  if (w->hst) cudaFreeHost(w->hst);
+  delete w;
+  c->ws = nullptr;
+}
+
+struct Ctx {
+  helm_ctx* c;
+  Workspace* w;
+  long n;
+  bool mg32;
+  bool pc;
+  int dim;
+  int G;
+};
+
+template <typename TM>
+static helm_status precondition(const Ctx& k, const void* in_mg, void* out_mg, cudaStream_t st) {
+  return mg_vcycle<TM>(k.c, (const cx<TM>*)in_mg, (cx<TM>*)out_mg, &k.w->st->done, st);
+}
+
+template <typename TM, int DIM>
+static helm_status enqueue_bicg_iter(const Ctx& k, cudaStream_t st) {
+  Workspace* w = k.w;
+  OpView<double> H = k.c->H.view<double>();
+  helm_status s;
+  // In FP32 multigrid the update kernels also write the vector in FP32 (the V-cycle input);
+  // in FP64 the V-cycle reads the Krylov vector itself.
+  const bool f32 = std::is_same<TM, float>::value;
+  void* pcopy = f32 ? w->pmg : nullptr;
+  void* scopy = f32 ? w->smg : nullptr;
+  const cx<TM>* pin = f32 ? (const cx<TM>*)w->pmg : (const cx<TM>*)(const void*)w->p;
+  const cx<TM>* sin_ = f32 ? (const cx<TM>*)w->smg : (const cx<TM>*)(const void*)w->sv;
+  k_bicg_p<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->p, w->v, pcopy, k.n);
+  const cx<TM>* ph = pin;
+  if (k.pc) {
+    if ((s = precondition<TM>(k, pin, w->ph, st)) != HELM_OK) return s;
+    ph = (const cx<TM>*)w->ph;
+  }
+  k_bicg_v<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, ph, w->rh, w->v, k.n, w->partials);
+  k_bicg_s<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->v, w->sv, scopy, k.n, w->partials);
+  k_bicg_xhalf<TM><<<k.G, KT, 0, st>>>(w->st, ph, w->x, k.n);
+  const cx<TM>* sh = sin_;
+  if (k.pc) {
+    if ((s = precondition<TM>(k, sin_, w->sh, st)) != HELM_OK) return s;
+    sh = (const cx<TM>*)w->sh;
+  }
+  k_bicg_t<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, sh, w->sv, w->t, k.n, w->partials);
+  k_bicg_xr<TM><<<k.G, KT, 0, st>>>(w->st, ph, sh, w->sv, w->t, w->rh, w->x, w->r, k.n, w->partials);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename TM, int DIM, int S_>
+static helm_status enqueue_idr_step(const Ctx& k, cudaStream_t st) {
+  Workspace* w = k.w;
+  OpView<double> H = k.c->H.view<double>();
+  helm_status s;
+  k_idr_small<<<1, 32, 0, st>>>(w->st);
+  void* vin = w->pmg;  // v in multigrid precision (always materialised)
+  k_idr_v<TM, S_><<<k.G, KT, 0, st>>>(w->st, w->dR, w->r, w->q, vin, k.n);
+  const cx<TM>* z;
+  if (k.pc) {
+    if ((s = precondition<TM>(k, vin, w->ph, st)) != HELM_OK) return s;
+    z = (const cx<TM>*)w->ph;
+  } else {
+    z = (const cx<TM>*)vin;
+  }
+  k_idr_t0<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->q, w->t, k.n, w->partials);
+  k_idr_dx<TM, S_><<<k.G, KT, 0, st>>>(w->st, w->dX, z, k.n);
+  k_idr_tk<DIM><<<k.G, KT, 0, st>>>(w->st, H, w->dX, w->t, k.n);
+  k_idr_upd<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR, w->dX, w->q, w->t, w->x, w->r, k.n, w->partials);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename TM, int DIM, int S_>
+static helm_status enqueue_idr_init(const Ctx& k, cudaStream_t st) {
+  Workspace* w = k.w;
+  OpView<double> H = k.c->H.view<double>();
+  helm_status s;
+  for (int kc = 0; kc < S_; ++kc) {
+    const cx<TM>* z;
+    if (k.pc) {
+      if ((s = precondition<TM>(k, w->pmg, w->ph, st)) != HELM_OK) return s;
+      z = (const cx<TM>*)w->ph;
+    } else {
+      z = (const cx<TM>*)w->pmg;
+    }
+    k_idr_mr_t<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->t, k.n, w->partials);
+    k_idr_mr_upd<TM><<<k.G, KT, 0, st>>>(w->st, kc, z, w->t, w->dX, w->dR, w->x, w->r, w->pmg, k.n, w->partials);
+  }
+  for (int j = 0; j < S_; ++j) k_idr_proj<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR + (long)j * k.n, j, k.n, w->partials);
+  k_idr_proj<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->r, -1, k.n, w->partials);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename TM, int DIM>
+static helm_status enqueue_body(const Ctx& k, int method, int s, cudaStream_t st) {
+  if (method == HELM_BICGSTAB) return enqueue_bicg_iter<TM, DIM>(k, st);
+  switch (s) {
+    case 1: return enqueue_idr_step<TM, DIM, 1>(k, st);
+    case 2: return enqueue_idr_step<TM, DIM, 2>(k, st);
+    case 3: return enqueue_idr_step<TM, DIM, 3>(k, st);
+    case 4: return enqueue_idr_step<TM, DIM, 4>(k, st);
+    case 5: return enqueue_idr_step<TM, DIM, 5>(k, st);
+    case 6: return enqueue_idr_step<TM, DIM, 6>(k, st);
+    case 7: return enqueue_idr_step<TM, DIM, 7>(k, st);
+    default: return enqueue_idr_step<TM, DIM, 8>(k, st);
+  }
+}
+
+template <typename TM, int DIM>
+static helm_status enqueue_init(const Ctx& k, int s, cudaStream_t st) {
+  switch (s) {
+    case 1: return enqueue_idr_init<TM, DIM, 1>(k, st);
+    case 2: return enqueue_idr_init<TM, DIM, 2>(k, st);
+    case 3: return enqueue_idr_init<TM, DIM, 3>(k, st);
+    case 4: return enqueue_idr_init<TM, DIM, 4>(k, st);
+    case 5: return enqueue_idr_init<TM, DIM, 5>(k, st);
+    case 6: return enqueue_idr_init<TM, DIM, 6>(k, st);
+    case 7: return enqueue_idr_init<TM, DIM, 7>(k, st);
+    default: return enqueue_idr_init<TM, DIM, 8>(k, st);
+  }
+}
+
+template <typename TM>
+static helm_status enqueue_body_any(const Ctx& k, int method, int s, cudaStream_t st) {
+  if (k.dim == 1) return enqueue_body<TM, 1>(k, method, s, st);
+  if (k.dim == 2) return enqueue_body<TM, 2>(k, method, s, st);
+  return enqueue_body<TM, 3>(k, method, s, st);
+}
+template <typename TM>
+static helm_status enqueue_init_any(const Ctx& k, int s, cudaStream_t st) {
+  if (k.dim == 1) return enqueue_init<TM, 1>(k, s, st);
+  if (k.dim == 2) return enqueue_init<TM, 2>(k, s, st);
+  return enqueue_init<TM, 3>(k, s, st);
+}
+
+// Captures the straight-line enqueue into a graph.
+template <typename F>
+static helm_status capture(cudaStream_t st, cudaGraph_t* g, F&& fn) {
+  cudaStream_t cs;
+  HELM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_check(e, "cudaStreamBeginCapture"); }
+  helm_status s = fn(cs);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (s != HELM_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+  if (e != cudaSuccess) return cuda_check(e, "cudaStreamEndCapture");
+  *g = graph;
+  (void)st;
+  return HELM_OK;
+}
+
+// Loop graph: [set condition from `done`] -> WHILE(cond) { one iteration; set condition }.
+template <typename TM>
+static helm_status build_loop(const Ctx& k, int method, int s) {
+  Workspace* w = k.w;
+  cudaGraph_t g;
+  HELM_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaGraphConditionalHandleCreate"); }
+  // head node: sets the condition from the current state
+  cudaKernelNodeParams kp = {};
+  int head_flag = 0;
+  void* args[3] = {&h, &w->st, &head_flag};
+  kp.func = (void*)k_set_cond;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = args;
+  cudaGraphNode_t head;
+  e = cudaGraphAddKernelNode(&head, g, nullptr, 0, &kp);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaGraphAddKernelNode"); }
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t cn;
+  e = cudaGraphAddNode(&cn, g, &head, nullptr, 1, &np);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaGraphAddNode(conditional)"); }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaStreamCreate"); }
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); return cuda_check(e, "cudaStreamBeginCaptureToGraph"); }
+  helm_status s2 = enqueue_body_any<TM>(k, method, s, cs);
+  k_set_cond<<<1, 1, 0, cs>>>(h, w->st, 1);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(cs, &out);
+  cudaStreamDestroy(cs);
+  if (s2 != HELM_OK) { cudaGraphDestroy(g); return s2; }
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaStreamEndCapture(body)"); }
+  size_t nb = 0;
+  cudaGraphGetNodes(body, nullptr, &nb);
+  w->body_nodes = nb;
+  e = cudaGraphInstantiate(&w->loop, g, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_check(e, "cudaGraphInstantiate(loop)"); }
+  w->loop_graph = g;
+  return HELM_OK;
+}
+
+template <typename TM>
+static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st) {
+  Workspace*& w = c->ws;
+  if (w && (w->method != o->method || (o->method == HELM_IDR && w->s != o->s))) krylov_free(c);
+  bool fresh = w == nullptr;
+  if (fresh) {
+    w = new Workspace();
+    w->method = o->method;
+    w->s = o->s;
+    long n = c->n;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+    w->G = grid_blocks(n, KT, sms * 4);
+    size_t v64 = sizeof(double2) * n;
+    bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
+    size_t vmg = (f32 ? sizeof(float2) : sizeof(double2)) * n;
+    helm_status s;
+    if ((s = ws_alloc(c, w, (void**)&w->st, sizeof(KrylovState))) != HELM_OK) return s;
+    HELM_CUDA(cudaMemset(w->st, 0, sizeof(KrylovState)));
+    HELM_CUDA(cudaMallocHost(&w->hst, sizeof(KrylovState)));
+    if ((s = ws_alloc(c, w, (void**)&w->partials, sizeof(double2) * NRED * w->G)) != HELM_OK) return s;
+    double2** vecs[] = {&w->x, &w->r, &w->t};
+    for (auto pp : vecs) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, &w->pmg, vmg)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, &w->ph, vmg)) != HELM_OK) return s;
+    if (o->method == HELM_BICGSTAB) {
+      double2** more[] = {&w->rh, &w->p, &w->v, &w->sv};
+      for (auto pp : more) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, &w->smg, vmg)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, &w->sh, vmg)) != HELM_OK) return s;
+    } else {
+      if ((s = ws_alloc(c, w, (void**)&w->q, v64)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->P, v64 * o->s)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->dR, v64 * o->s)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->dX, v64 * o->s)) != HELM_OK) return s;
+    }
+  }
+  k.c = c;
+  k.w = w;
+  k.n = c->n;
+  k.mg32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
+  k.pc = c->pc.kind != HELM_PC_NONE;
+  k.dim = c->grid.dim;
+  k.G = w->G;
+  if (fresh) {
+    helm_status s = build_loop<TM>(k, o->method, o->s);
+    if (s != HELM_OK) return s;
+    if (o->method == HELM_IDR) {
+      s = capture(st, &w->init_graph, [&](cudaStream_t cs) { return enqueue_init_any<TM>(k, o->s, cs); });
+      if (s != HELM_OK) return s;
+      HELM_CUDA(cudaGraphInstantiate(&w->idr_init, w->init_graph, 0));
+      size_t ni = 0;
+      cudaGraphGetNodes(w->init_graph, nullptr, &ni);
+      w->init_nodes = ni;
+    }
+  }
+  return HELM_OK;
+}
+
+static helm_status upload_shadow(const Ctx& k, const helm_solve_opts* o, cudaStream_t st) {
+  Workspace* w = k.w;
+  if (w->shadow_key == o->shadow) return HELM_OK;
+  long n = k.n;
+  HELM_CUDA(cudaMemcpyAsync(w->P, o->shadow, sizeof(double2) * n * o->s, cudaMemcpyHostToDevice, st));
+  // modified Gram-Schmidt; the scalar goes through the partial-sum slot after the reductions
+  double2* h = w->partials + (NRED - 1) * w->G;  // last slot, unused by k_dot1's own partials
+  for (int j = 0; j < o->s; ++j) {
+    double2* pj = w->P + (long)j * n;
+    for (int i = 0; i < j; ++i) {
+      double2* pi = w->P + (long)i * n;
+      k_dot1<<<k.G, KT, 0, st>>>(w->st, pi, pj, n, w->partials, h);
+      k_mgs_upd<<<k.G, KT, 0, st>>>(pj, pi, h, 0, n);
+    }
+    k_dot1<<<k.G, KT, 0, st>>>(w->st, pj, pj, n, w->partials, h);
+    k_mgs_upd<<<k.G, KT, 0, st>>>(pj, pj, h, 1, n);
+  }
+  HELM_CUDA(cudaGetLastError());
+  w->shadow_key = o->shadow;
+  return HELM_OK;
+}
+
+template <typename TM>
+static helm_status solve_t(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
+                           helm_solve_info* info, cudaStream_t st) {
+  Ctx k;
+  helm_status s = prepare<TM>(c, o, k, st);
+  if (s != HELM_OK) return s;
+  Workspace* w = k.w;
+  if (o->method == HELM_IDR && (s = upload_shadow(k, o, st)) != HELM_OK) return s;
+  // scalars fixed for this solve
+  KrylovState init{};
+  init.tol = o->tol;
+  init.maxmv = o->maxmv;
+  init.s = o->s;
+  HELM_CUDA(cudaMemcpyAsync(&w->st->tol, &init.tol, sizeof(double), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemcpyAsync(&w->st->maxmv, &init.maxmv, sizeof(int), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemcpyAsync(&w->st->s, &init.s, sizeof(int), cudaMemcpyHostToDevice, st));
+  double* hist = o->history;
+  HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * k.n, st));
+  bool bicg = o->method == HELM_BICGSTAB;
+  // the first V-cycle input: Bi-CGSTAB builds p itself; IDR needs r in multigrid precision
+  void* rmg = bicg ? nullptr : w->pmg;
+  OpView<double> H = c->H.view<double>();
+  int restarts = 0;
+  long kernels = 0;
+  for (;;) {
+    k_start<<<k.G, KT, 0, st>>>(w->st, b, w->r, bicg ? w->rh : nullptr, bicg ? w->p : nullptr,
+                                bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n, restarts == 0 ? 1 : 0,
+                                w->partials);
+    if (!bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
+    HELM_CUDA(cudaGraphLaunch(w->loop, st));
+    switch (k.dim) {
+      case 1: k_true_res<1><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
+      case 2: k_true_res<2><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
+      default: k_true_res<3><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials);
+    }
+    HELM_CUDA(cudaGetLastError());
+    HELM_CUDA(cudaMemcpyAsync(w->hst, w->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaStreamSynchronize(st));
+    const KrylovState& hs = *w->hst;
+    // k_start, the loop head, loops x body, k_true_res (+ the IDR start graph)
+    kernels += 3 + (long)hs.loops * (long)w->body_nodes + (bicg ? 0 : (long)w->init_nodes);
+    if (hs.status != HELM_OK || hs.rel_true < o->tol) break;
+    if (restarts >= o->max_restarts) break;
+    ++restarts;
+  }
+  const KrylovState& hs = *w->hst;
+  HELM_CUDA(cudaMemcpyAsync(x, w->x, sizeof(double2) * k.n, cudaMemcpyDeviceToDevice, st));
+  helm_status final_status = (helm_status)hs.status;
+  if (final_status == HELM_OK && !(hs.rel_true < o->tol)) final_status = HELM_ERR_MAXIT;
+  if (info) {
+    info->status = final_status;
+    info->iters = hs.iters;
+    info->matvecs = hs.matvecs;
+    info->restarts = restarts;
+    info->rel_res_recur = hs.rel_recur;
+    info->rel_res_true = hs.rel_true;
+    info->kernels = kernels;
+  }
+  HELM_CUDA(cudaStreamSynchronize(st));
+  return final_status;
+}
+
+helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
+                         helm_solve_info* info, cudaStream_t st) {
+  if (c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64) return solve_t<float>(c, b, x, o, info, st);
+  return solve_t<double>(c, b, x, o, info, st);
+}
+
+}  // namespace helm

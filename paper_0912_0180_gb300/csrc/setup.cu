@@ -1,0 +1,371 @@
+// setup.cu -- grid, coefficient and hierarchy setup kernels (run once per context).
+//
+// Grid: Section 3, eq. "ecsgrid" (vertex-centred, turning points are nodes) with the ECS
+// layer width h e^{i theta_gamma} of Section 2; CSG scales widths by beta = e^{i theta_beta}
+// (Section 5.3, eqs. "CSL-CSG", "lapctucsg").  Coefficients: Shortley-Weller, Section 3,
+// eq. "shortwell".  Hierarchy: coarse unknown c <-> fine unknown 2c+1 (0-based), coarse widths
+// are sums of fine widths, phi is injected; the coarsest operator is inverted densely in FP64
+// (Gauss-Jordan with partial pivoting) and stored in the multigrid precision.
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+// One thread per width: layer widths (first nlo and last nhi) are h e^{i theta} * scale_ly,
+// interior widths h * scale_in.
+__global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_layer,
+                            double2 w_int) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ngap) return;
+  bool interior = (j >= nlo) && (j < nlo + nin);
+  gap[j] = interior ? w_int : w_layer;
+}
+
+// coarse width c = fine widths 2c and 2c+1; the last coarse width reaches the fine Dirichlet
+// node and gathers the remaining one or two fine widths.
+__global__ void k_axis_coarsen(const double2* __restrict__ gf, int nf, double2* __restrict__ gc,
+                               int nc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > nc) return;
+  if (c < nc) {
+    gc[c] = cadd<double>(gf[2 * c], gf[2 * c + 1]);
+  } else {
+    double2 acc = mkc<double>(0.0, 0.0);
+    for (int j = 2 * nc; j <= nf; ++j) acc = cadd<double>(acc, gf[j]);
+    gc[c] = acc;
+  }
+}
+
+// Shortley-Weller row of -d^2/dz^2 at unknown j with left width hl, right width hr:
+//   am = -2 / (hl (hl + hr)),  a0 = 2 / (hl hr),  ap = -2 / (hr (hl + hr)).
+__global__ void k_axis_coeffs(const double2* __restrict__ gap, int n, double2* am, double2* a0,
+                              double2* ap, float2* am32, float2* a032, float2* ap32) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double2 hl = gap[j], hr = gap[j + 1];
+  double2 sum = cadd<double>(hl, hr);
+  double2 two = mkc<double>(2.0, 0.0);
+  double2 m = cdiv<double>(two, cmul<double>(hl, sum));
+  double2 p = cdiv<double>(two, cmul<double>(hr, sum));
+  double2 c = cdiv<double>(two, cmul<double>(hl, hr));
+  am[j] = mkc<double>(-m.x, -m.y);
+  a0[j] = c;
+  ap[j] = mkc<double>(-p.x, -p.y);
+  if (am32) {
+    am32[j] = cconv<float, double>(am[j]);
+    a032[j] = cconv<float, double>(c);
+    ap32[j] = cconv<float, double>(ap[j]);
+  }
+}
+
+// phi on the coarse level: value of the fine node that coincides with the coarse node.
+__global__ void k_phi_inject(const double* __restrict__ pf, int f0, int f1, int dim,
+                             double* __restrict__ pc, float* __restrict__ pc32, int c0, int c1,
+                             int c2) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long nc = (long)c0 * c1 * c2;
+  if (p >= nc) return;
+  int i = (int)(p % c0);
+  long q = p / c0;
+  int j = (int)(q % c1);
+  int l = (int)(q / c1);
+  int fi = 2 * i + 1, fj = dim > 1 ? 2 * j + 1 : 0, fl = dim > 2 ? 2 * l + 1 : 0;
+  double v = pf[fi + (long)f0 * (fj + (long)f1 * fl)];
+  pc[p] = v;
+  if (pc32) pc32[p] = (float)v;
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (p < n) b[p] = (float)a[p];
+}
+
+__global__ void k_c128_to_c64(const double2* __restrict__ a, float2* __restrict__ b, long n) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (p < n) b[p] = cconv<float, double>(a[p]);
+}
+
+// Dense matrix of the coarsest operator (row-major, FP64), one thread per row.
+__global__ void k_dense_assemble(OpView<double> op, int dim, double2* A, int n) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = p % op.n[0];
+  int j = (p / op.n[0]) % op.n[1];
+  int l = p / (op.n[0] * op.n[1]);
+  double2* row = A + (long)p * n;
+  for (int c = 0; c < n; ++c) row[c] = mkc<double>(0.0, 0.0);
+  double ph = op.phi ? op.phi[p] : op.phi0;
+  double2 d = op.a0[0][i];
+  if (dim > 1) d = cadd<double>(d, op.a0[1][j]);
+  if (dim > 2) d = cadd<double>(d, op.a0[2][l]);
+  d = csub<double>(d, cscale<double>(ph, op.s));
+  row[p] = d;
+  if (i > 0) row[p - 1] = op.am[0][i];
+  if (i < op.n[0] - 1) row[p + 1] = op.ap[0][i];
+  if (dim > 1) {
+    if (j > 0) row[p - op.n[0]] = op.am[1][j];
+    if (j < op.n[1] - 1) row[p + op.n[0]] = op.ap[1][j];
+  }
+  if (dim > 2) {
+    int st = op.n[0] * op.n[1];
+    if (l > 0) row[p - st] = op.am[2][l];
+    if (l < op.n[2] - 1) row[p + st] = op.ap[2][l];
+  }
+}
+
+// Gauss-Jordan inversion with partial pivoting, one block.  A (n x n) is destroyed; X = A^{-1}.
+// status[0] = 1 if a pivot is exactly zero.
+__global__ void k_gauss_jordan(double2* A, double2* X, int n, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  double* best = reinterpret_cast<double*>(smem_raw);
+  int* bidx = reinterpret_cast<int*>(best + blockDim.x);
+  __shared__ int piv;
+  __shared__ double2 inv_p;
+  int tid = threadIdx.x, nt = blockDim.x;
+  for (long e = tid; e < (long)n * n; e += nt) X[e] = mkc<double>((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double b = -1.0;
+    int bi = k;
+    for (int r = k + tid; r < n; r += nt) {
+      double v = cabs2<double>(A[(long)r * n + k]);
+      if (v > b) { b = v; bi = r; }
+    }
+    best[tid] = b;
+    bidx[tid] = bi;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        if (best[tid + s] > best[tid] || (best[tid + s] == best[tid] && bidx[tid + s] < bidx[tid])) {
+          best[tid] = best[tid + s];
+          bidx[tid] = bidx[tid + s];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      piv = bidx[0];
+      if (best[0] <= 0.0) status[0] = 1;
+    }
+    __syncthreads();
+    int p = piv;
+    if (p != k) {
+      for (int c = tid; c < n; c += nt) {
+        double2 t = A[(long)k * n + c]; A[(long)k * n + c] = A[(long)p * n + c]; A[(long)p * n + c] = t;
+        t = X[(long)k * n + c]; X[(long)k * n + c] = X[(long)p * n + c]; X[(long)p * n + c] = t;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) inv_p = crecip<double>(A[(long)k * n + k]);
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+      A[(long)k * n + c] = cmul<double>(A[(long)k * n + c], inv_p);
+      X[(long)k * n + c] = cmul<double>(X[(long)k * n + c], inv_p);
+    }
+    __syncthreads();
+    for (long e = tid; e < (long)n * n; e += nt) {
+      int r = (int)(e / n), c = (int)(e % n);
+      if (r == k) continue;
+      double2 f = A[(long)r * n + k];
+      if (c != k) A[e] = csub<double>(A[e], cmul<double>(f, A[(long)k * n + c]));
+      X[e] = csub<double>(X[e], cmul<double>(f, X[(long)k * n + c]));
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt)
+      if (r != k) A[(long)r * n + k] = mkc<double>(0.0, 0.0);
+    __syncthreads();
+  }
+}
+
+static int ceil_div(long a, int b) { return (int)((a + b - 1) / b); }
+
+static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, double2 scale_ly,
+                              bool want32, cudaStream_t st) {
+  const helm_grid& g = c->grid;
+  L.dim = g.dim;
+  L.ntot = 1;
+  for (int a = 0; a < 3; ++a) L.n[a] = 1;
+  for (int a = 0; a < g.dim; ++a) {
+    int lo = g.n_layer[a][0], hi = g.n_layer[a][1];
+    int nlo = lo > 0 ? lo + 1 : 0, nhi = hi > 0 ? hi + 1 : 0;
+    int nin = g.n_int[a] - 1;
+    int ngap = nlo + nin + nhi;
+    int n = ngap - 1;
+    double h = g.extent[a] / (g.n_int[a] - 1);
+    double2 hg = mkc<double>(h * cos(g.theta_gamma), h * sin(g.theta_gamma));
+    double2 wl = cmul<double>(hg, scale_ly);
+    double2 wi = cscale<double>(h, scale_in);
+    helm_status s;
+    if ((s = ctx_alloc(c, (void**)&L.gap[a], sizeof(double2) * ngap)) != HELM_OK) return s;
+    for (int k = 0; k < 3; ++k) {
+      if ((s = ctx_alloc(c, (void**)&L.coef64[a][k], sizeof(double2) * n)) != HELM_OK) return s;
+      if (want32 && (s = ctx_alloc(c, (void**)&L.coef32[a][k], sizeof(float2) * n)) != HELM_OK) return s;
+    }
+    k_axis_gaps<<<ceil_div(ngap, 256), 256, 0, st>>>(L.gap[a], ngap, nlo, nin, wl, wi);
+    k_axis_coeffs<<<ceil_div(n, 256), 256, 0, st>>>(L.gap[a], n, L.coef64[a][0], L.coef64[a][1],
+                                                    L.coef64[a][2], L.coef32[a][0], L.coef32[a][1],
+                                                    L.coef32[a][2]);
+    HELM_CUDA(cudaGetLastError());
+    L.n[a] = n;
+    L.ntot *= n;
+  }
+  return HELM_OK;
+}
+
+template <typename T> OpView<T> LevelHost::view() const {
+  OpView<T> v{};
+  for (int a = 0; a < 3; ++a) {
+    v.n[a] = n[a];
+    for (int k = 0; k < 3; ++k) {
+      const void* src = nullptr;
+      if (a < dim) src = std::is_same<T, double>::value ? (const void*)coef64[a][k] : (const void*)coef32[a][k];
+      const cx<T>* p = reinterpret_cast<const cx<T>*>(src);
+      if (k == 0) v.am[a] = p;
+      if (k == 1) v.a0[a] = p;
+      if (k == 2) v.ap[a] = p;
+    }
+  }
+  v.phi = std::is_same<T, double>::value ? (const T*)(const void*)phi64 : (const T*)(const void*)phi32;
+  v.phi0 = (T)phi0;
+  v.s = mkc<T>((T)s.x, (T)s.y);
+  return v;
+}
+template OpView<double> LevelHost::view<double>() const;
+template OpView<float> LevelHost::view<float>() const;
+
+helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
+  LevelHost& H = c->H;
+  helm_status s = build_axes(c, H, mkc<double>(1, 0), mkc<double>(1, 0), false, st);
+  if (s != HELM_OK) return s;
+  c->n = H.ntot;
+  H.s = mkc<double>(1.0, 0.0);
+  H.phi0 = k->k0 * k->k0;
+  if (k->phi) {
+    if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
+    HELM_CUDA(cudaMemcpyAsync(H.phi64, k->phi, sizeof(double) * H.ntot, cudaMemcpyHostToDevice, st));
+  }
+  return HELM_OK;
+}
+
+helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
+  const helm_precond& pc = c->pc;
+  if (pc.kind == HELM_PC_NONE) return HELM_OK;
+  bool f32 = pc.mg_dtype == HELM_C64;
+  size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  double2 beta = mkc<double>(cos(pc.theta_beta), sin(pc.theta_beta));
+  double2 one = mkc<double>(1.0, 0.0);
+  double2 sc_in = one, sc_ly = one, s = one;
+  if (pc.kind == HELM_PC_CSL) s = mkc<double>(pc.shift_re, pc.shift_im);
+  if (pc.kind == HELM_PC_CSG_UNIFORM) { sc_in = beta; sc_ly = beta; }
+  if (pc.kind == HELM_PC_CSG_INTERIOR) sc_in = beta;
+  helm_status rc;
+  c->lv.clear();
+  c->lv.reserve(pc.max_levels);
+  c->lv.emplace_back();
+  {
+    LevelHost& L0 = c->lv[0];
+    if ((rc = build_axes(c, L0, sc_in, sc_ly, f32, st)) != HELM_OK) return rc;
+    L0.s = s;
+    L0.phi0 = c->H.phi0;
+    L0.phi64 = c->H.phi64;  // same field, shared
+    if (L0.phi64 && f32) {
+      if ((rc = ctx_alloc(c, (void**)&L0.phi32, sizeof(float) * L0.ntot)) != HELM_OK) return rc;
+      k_to_f32<<<ceil_div(L0.ntot, 256), 256, 0, st>>>(L0.phi64, L0.phi32, L0.ntot);
+    }
+  }
+  while ((int)c->lv.size() < pc.max_levels) {
+    const LevelHost& F = c->lv.back();
+    bool all_small = true;
+    int min_n = 1 << 30;
+    for (int a = 0; a < F.dim; ++a) {
+      if (F.n[a] > pc.coarse_max) all_small = false;
+      if (F.n[a] < min_n) min_n = F.n[a];
+    }
+    if (all_small || min_n < 3) break;
+    LevelHost C;
+    C.dim = F.dim;
+    C.ntot = 1;
+    for (int a = 0; a < F.dim; ++a) {
+      int nf = F.n[a], nc = nf / 2;
+      if ((rc = ctx_alloc(c, (void**)&C.gap[a], sizeof(double2) * (nc + 1))) != HELM_OK) return rc;
+      for (int k = 0; k < 3; ++k) {
+        if ((rc = ctx_alloc(c, (void**)&C.coef64[a][k], sizeof(double2) * nc)) != HELM_OK) return rc;
+        if (f32 && (rc = ctx_alloc(c, (void**)&C.coef32[a][k], sizeof(float2) * nc)) != HELM_OK) return rc;
+      }
+      k_axis_coarsen<<<ceil_div(nc + 1, 256), 256, 0, st>>>(F.gap[a], nf, C.gap[a], nc);
+      k_axis_coeffs<<<ceil_div(nc, 256), 256, 0, st>>>(C.gap[a], nc, C.coef64[a][0], C.coef64[a][1],
+                                                       C.coef64[a][2], C.coef32[a][0],
+                                                       C.coef32[a][1], C.coef32[a][2]);
+      C.n[a] = nc;
+      C.ntot *= nc;
+    }
+    C.s = F.s;
+    C.phi0 = F.phi0;
+    if (F.phi64) {
+      if ((rc = ctx_alloc(c, (void**)&C.phi64, sizeof(double) * C.ntot)) != HELM_OK) return rc;
+      if (f32 && (rc = ctx_alloc(c, (void**)&C.phi32, sizeof(float) * C.ntot)) != HELM_OK) return rc;
+      k_phi_inject<<<ceil_div(C.ntot, 256), 256, 0, st>>>(F.phi64, F.n[0], F.n[1], F.dim, C.phi64,
+                                                          C.phi32, C.n[0], C.n[1], C.n[2]);
+    }
+    HELM_CUDA(cudaGetLastError());
+    c->lv.push_back(C);
+  }
+  // work vectors: level 0 needs one spare buffer (its f and u are the caller's); coarser
+  // levels need u, f and a spare.
+  for (size_t l = 0; l < c->lv.size(); ++l) {
+    LevelHost& L = c->lv[l];
+    if ((rc = ctx_alloc(c, &L.w, esz * L.ntot)) != HELM_OK) return rc;
+    if (l > 0) {
+      if ((rc = ctx_alloc(c, &L.u, esz * L.ntot)) != HELM_OK) return rc;
+      if ((rc = ctx_alloc(c, &L.f, esz * L.ntot)) != HELM_OK) return rc;
+    }
+  }
+  // dense inverse of the coarsest operator, computed in FP64
+  LevelHost& Cst = c->lv.back();
+  if (Cst.ntot > 4096) {
+    set_error("coarsest level too large for the dense direct solve (> 4096 unknowns); raise max_levels");
+    return HELM_ERR_ARG;
+  }
+  int n = (int)Cst.ntot;
+  c->nco = n;
+  double2 *A = nullptr, *X = nullptr;
+  int* flag = nullptr;
+  HELM_CUDA(cudaMalloc(&A, sizeof(double2) * (size_t)n * n));
+  cudaError_t e1 = cudaMalloc(&X, sizeof(double2) * (size_t)n * n);
+  cudaError_t e2 = cudaMalloc(&flag, sizeof(int));
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaFree(A); cudaFree(X); cudaFree(flag);
+    return cuda_check(e1 != cudaSuccess ? e1 : e2, "cudaMalloc(coarse)");
+  }
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
+  int thr = 1024;
+  k_gauss_jordan<<<1, thr, thr * (sizeof(double) + sizeof(int)), st>>>(A, X, n, flag);
+  if ((rc = ctx_alloc(c, &c->coarse_inv, esz * (size_t)n * n)) != HELM_OK) {
+    cudaFree(A); cudaFree(X); cudaFree(flag);
+    return rc;
+  }
+  if (f32) k_c128_to_c64<<<ceil_div((long)n * n, 256), 256, 0, st>>>(X, (float2*)c->coarse_inv, (long)n * n);
+  else cudaMemcpyAsync(c->coarse_inv, X, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+  int hflag = 0;
+  cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(A); cudaFree(X); cudaFree(flag);
+  HELM_CUDA(e);
+  if (hflag) {
+    set_error("coarsest operator is singular");
+    return HELM_ERR_ARG;
+  }
+  return HELM_OK;
+}
+
+helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st) {
+  k_c128_to_c64<<<ceil_div(c->n, 256), 256, 0, st>>>(in, (float2*)out, c->n);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+}  // namespace helm

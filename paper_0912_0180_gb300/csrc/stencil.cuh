@@ -1,0 +1,54 @@
+// stencil.cuh -- the Shortley-Weller row of a level operator evaluated at one grid point.
+//   (A x)_P = sum_axes (am x_{P-e} + a0 x_P + ap x_{P+e}) - s * phi_P * x_P
+// Section 3, eq. "shortwell", summed over axes; sigma = s * phi with s = 1 for H and CSG
+// (eqs. "helmctu0", "lapctucsg") and s = beta^2 for CSL (eq. "helmctucsl").  Neighbours
+// outside the grid are Dirichlet nodes and contribute nothing.
+#pragma once
+#include "helm_internal.cuh"
+
+namespace helm {
+
+template <typename T, int DIM>
+__device__ __forceinline__ cx<T> op_diag(const OpView<T>& op, int i, int j, int l, long p) {
+  cx<T> d = op.a0[0][i];
+  if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
+  if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
+  T ph = op.phi ? op.phi[p] : op.phi0;
+  return csub<T>(d, cscale<T>(ph, op.s));
+}
+
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* __restrict__ x,
+                                            int i, int j, int l, long p) {
+  cx<T> acc = mkc<T>(T(0), T(0));
+  if (i > 0) acc = cfma<T>(op.am[0][i], cconv<T, TX>(x[p - 1]), acc);
+  if (i < op.n[0] - 1) acc = cfma<T>(op.ap[0][i], cconv<T, TX>(x[p + 1]), acc);
+  if (DIM > 1) {
+    long st = op.n[0];
+    if (j > 0) acc = cfma<T>(op.am[1][j], cconv<T, TX>(x[p - st]), acc);
+    if (j < op.n[1] - 1) acc = cfma<T>(op.ap[1][j], cconv<T, TX>(x[p + st]), acc);
+  }
+  if (DIM > 2) {
+    long st = (long)op.n[0] * op.n[1];
+    if (l > 0) acc = cfma<T>(op.am[2][l], cconv<T, TX>(x[p - st]), acc);
+    if (l < op.n[2] - 1) acc = cfma<T>(op.ap[2][l], cconv<T, TX>(x[p + st]), acc);
+  }
+  return acc;
+}
+
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __restrict__ x, int i,
+                                        int j, int l, long p) {
+  cx<T> d = op_diag<T, DIM>(op, i, j, l, p);
+  return cfma<T>(d, cconv<T, TX>(x[p]), op_offdiag<T, TX, DIM>(op, x, i, j, l, p));
+}
+
+// point coordinates from a linear index
+__device__ __forceinline__ void unflatten(long p, const int n[3], int& i, int& j, int& l) {
+  i = (int)(p % n[0]);
+  long q = p / n[0];
+  j = (int)(q % n[1]);
+  l = (int)(q / n[1]);
+}
+
+}  // namespace helm

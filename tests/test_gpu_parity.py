@@ -1,0 +1,299 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element.
+
+Tolerances, derived from the arithmetic:
+  - FP64 kernels: the same formulas summed in a different order differ by a few ulps of the
+    largest term; relative 1e-12 of the vector norm (stencil terms cancel up to ~1/h^2 * |x|
+    against |H x|, so the bound is taken against |coefficients| * |x|).
+  - FP32 multigrid: one sweep rounds every term to 2^-24 ~ 6e-8 relative; a V-cycle chains a
+    few dozen such operations through the levels, so 2e-5 relative.
+  - Krylov: two FP64 runs with different rounding follow the same residual history for the
+    first steps and then drift; the solutions both satisfy ||b - Hx|| <= tol ||b||, so they
+    agree to about cond * tol; at tol 1e-10 the bar is 1e-9 relative, matvec counts within 2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import helm_inputs as hi
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+from paper_0912_0180_gb300 import _lib as L  # noqa: E402
+from paper_0912_0180_gb300.helm import Helm  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def cu(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [
+    # dim, n_int, layers, theta, k0, phi kind
+    (1, 50, (7, 5), 0.5, 9.0, "const"),
+    (2, 33, 6, 0.5, 15.0, "const"),
+    (2, (40, 29), ((5, 0), (3, 8)), 0.4, 12.0, "bump"),
+    (2, 64, 16, 0.5, 20.0, "const"),
+    (3, 13, 3, 0.5, 6.0, "const"),
+    (3, (12, 9, 10), ((2, 3), (0, 2), (3, 0)), 0.5, 5.0, "bump"),
+]
+
+
+def _problem(case, rhs="random", seed=11):
+    dim, n_int, nl, th, k0, kind = case
+    return hi.make_problem(dim, n_int, nl, theta_gamma=th, k0=k0, phi_kind=kind, rhs=rhs, seed=seed,
+                           bump_centre=(0.4, 0.6, 0.5))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_helmholtz_apply_fp64(case):
+    p = _problem(case)
+    o = Oracle(p)
+    h = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+    x = hi.random_vector(p.n, 3)
+    y = h.apply(cu(x)).cpu().numpy()
+    ref = o.apply(x)
+    assert rel(y, ref) < 1e-12
+    # complex64 input: exact upcast, then FP64 arithmetic
+    x32 = x.astype(np.complex64)
+    y32 = h.apply(cu(x32, torch.complex64)).cpu().numpy()
+    assert rel(y32, o.apply(x32.astype(np.complex128))) < 1e-12
+    h.close()
+
+
+PCS = [
+    hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS),
+    hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5, nu1=2, nu2=1),
+    hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.8),
+    hi.Precond(kind=hi.PC_CSG_INTERIOR, theta_beta=0.25, smoother=hi.SM_RBGS, nu1=0, nu2=2),
+]
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("pci", range(len(PCS)))
+@pytest.mark.parametrize("case", CASES)
+def test_multigrid_components(case, pci, mg):
+    """Every level: operator, residual, smoothing (from zero and from a guess), restriction,
+    prolongation and the coarsest direct solve."""
+    p = _problem(case)
+    pc = PCS[pci]
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype=mg)
+    assert h.nlev == o.nlev
+    dt = torch.complex128 if mg == "c128" else torch.complex64
+    tol = 1e-11 if mg == "c128" else 2e-5
+    rng = np.random.default_rng(5)
+    for lvl in range(o.nlev):
+        assert h.level_shape(lvl) == o.level_shape(1, lvl)
+        n = o.level_size(1, lvl)
+        a = (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        b = (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        if mg == "c64":
+            a = a.astype(np.complex64).astype(np.complex128)
+            b = b.astype(np.complex64).astype(np.complex128)
+        if lvl == o.nlev - 1:
+            out = torch.empty(n, dtype=dt, device="cuda")
+            h.level_op(L.HELM_OP_COARSE, lvl, cu(a, dt), None, out)
+            assert rel(out.cpu().numpy(), o.coarse_solve(a)) < (1e-10 if mg == "c128" else 1e-4)
+            continue
+        out = torch.empty(n, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
+        assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+        h.level_op(L.HELM_OP_RESIDUAL, lvl, cu(a, dt), cu(b, dt), out)
+        assert rel(out.cpu().numpy(), b - o.apply(a, 1, lvl)) < tol
+        u = cu(a, dt)
+        h.level_op(L.HELM_OP_SMOOTH, lvl, u, cu(b, dt), None, count=2)
+        assert rel(u.cpu().numpy(), o.smooth(lvl, a, b, 2)) < tol
+        u = cu(a, dt)
+        h.level_op(L.HELM_OP_SMOOTH0, lvl, u, cu(b, dt), None, count=2)
+        assert rel(u.cpu().numpy(), o.smooth(lvl, np.zeros(n), b, 2)) < tol
+        nc = o.level_size(1, lvl + 1)
+        fc = torch.empty(nc, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_RESTRICT, lvl, cu(a, dt), None, fc)
+        assert rel(fc.cpu().numpy(), o.restrict(lvl, a)) < tol
+        ec = rng.standard_normal(nc) + 1j * rng.standard_normal(nc)
+        if mg == "c64":
+            ec = ec.astype(np.complex64).astype(np.complex128)
+        u = cu(a, dt)
+        h.level_op(L.HELM_OP_PROLONG, lvl, u, cu(ec, dt))
+        assert rel(u.cpu().numpy(), o.prolong_add(lvl, ec, a)) < tol
+    h.close()
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("pci", range(len(PCS)))
+@pytest.mark.parametrize("case", CASES)
+def test_vcycle(case, pci, mg):
+    p = _problem(case)
+    pc = PCS[pci]
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype=mg)
+    r = hi.random_vector(p.n, 21)
+    z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
+    ref = o.vcycle(r)
+    assert rel(z, ref) < (1e-10 if mg == "c128" else 5e-5)
+    h.close()
+
+
+SOLVE_CASES = [
+    (2, 33, 6, 0.5, 15.0, "const"),
+    (2, (40, 29), ((5, 0), (3, 8)), 0.4, 12.0, "bump"),
+    (2, 64, 16, 0.5, 20.0, "const"),
+    (3, (12, 9, 10), ((2, 3), (0, 2), (3, 0)), 0.5, 5.0, "bump"),
+]
+
+
+def _oracle_counts(o, b, opts, sh, n_perturb=2):
+    """Matvec counts of the oracle on b and on rounding-level perturbations of b (relative
+    1e-14): the spread is the method's own sensitivity to rounding."""
+    counts = []
+    rng = np.random.default_rng(99)
+    for k in range(n_perturb):
+        bp = b * (1 + 1e-14 * rng.standard_normal(b.shape))
+        counts.append(o.solve(bp, opts, shadow=sh)[1]["matvecs"])
+    return counts
+
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+@pytest.mark.parametrize("pci", [0, 2])
+@pytest.mark.parametrize("case", SOLVE_CASES)
+def test_fp64_solve_matches_oracle(case, pci, method):
+    """FP64 path vs the oracle at tol 1e-10: the same residual history until rounding drift
+    (first 8 matvecs to 1e-9 relative), relative solution difference <= 1e-9, and a matvec
+    count within 2 of the oracle's (on b, or on b perturbed at rounding level when the
+    oracle's own count moves by more than that)."""
+    p = _problem(case, rhs="point")
+    pc = PCS[pci]
+    o = Oracle(p, pc)
+    sh = hi.shadow_space(p.n, 4)
+    opts = hi.SolveOpts(method=method, s=4, tol=1e-10, maxmv=1500)
+    x_ref, info_ref = o.solve(p.b, opts, shadow=sh, history=True)
+    h = Helm(p, pc, mg_dtype="c128")
+    x, info = h.solve(cu(p.b), method=method, s=4, tol=1e-10, maxmv=1500, shadow=sh, history=True)
+    assert info.status == 0 and info_ref["status"] == 0
+    assert info.rel_res_true < 1e-10
+    m = min(8, info.matvecs, info_ref["matvecs"])
+    assert np.allclose(info.history[:m], info_ref["history"][:m], rtol=1e-9, atol=0)
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
+    if abs(info.matvecs - info_ref["matvecs"]) > 2:
+        counts = _oracle_counts(o, p.b, opts, sh)
+        assert min(abs(info.matvecs - c) for c in counts) <= 2, (info.matvecs, info_ref["matvecs"], counts)
+    h.close()
+
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+@pytest.mark.parametrize("case", SOLVE_CASES)
+def test_mixed_precision_solve_error(case, method):
+    """FP32 V-cycle, FP64 Krylov: true residual below tol and the error against the oracle's
+    solution at 1e-12 within 1e-5 (at tol 1e-7)."""
+    p = _problem(case, rhs="point")
+    pc = PCS[0]
+    o = Oracle(p, pc)
+    sh = hi.shadow_space(p.n, 4)
+    x_ref, _ = o.solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-12, maxmv=3000))
+    h = Helm(p, pc, mg_dtype="c64")
+    x, info = h.solve(cu(p.b), method=method, s=4, tol=1e-7, maxmv=1500, shadow=sh)
+    assert info.status == 0 and info.rel_res_true < 1e-7
+    assert rel(x.cpu().numpy(), x_ref) < 1e-5
+    h.close()
+
+
+@pytest.mark.parametrize("s", [1, 2, 8])
+def test_idr_other_shadow_dimensions(s):
+    p = _problem(SOLVE_CASES[0], rhs="point")
+    pc = PCS[0]
+    o = Oracle(p, pc)
+    sh = hi.shadow_space(p.n, s, seed=77)
+    x_ref, info_ref = o.solve(p.b, hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=1500), shadow=sh)
+    h = Helm(p, pc, mg_dtype="c128")
+    x, info = h.solve(cu(p.b), method=hi.IDR, s=s, tol=1e-10, maxmv=1500, shadow=sh)
+    assert info.status == 0
+    if abs(info.matvecs - info_ref["matvecs"]) > 2:
+        counts = _oracle_counts(o, p.b, hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=1500), sh)
+        assert min(abs(info.matvecs - c) for c in counts) <= 2
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
+    h.close()
+
+
+def test_unpreconditioned_and_edge_cases():
+    p = _problem((2, 12, 3, 0.5, 6.0, "const"), rhs="point")
+    o = Oracle(p)
+    x_ref = o.dense_solve(p.b)
+    h = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+    for method in (hi.BICGSTAB, hi.IDR):
+        x, info = h.solve(cu(p.b), method=method, tol=1e-12, maxmv=5000, shadow=hi.shadow_space(p.n, 4))
+        assert info.status == 0 and rel(x.cpu().numpy(), x_ref) < 1e-9
+    # zero right-hand side: x = 0 without a matvec
+    x, info = h.solve(torch.zeros(p.n, dtype=torch.complex128, device="cuda"))
+    assert info.status == 0 and info.matvecs == 0 and not torch.any(x)
+    # non-finite right-hand side
+    b = cu(p.b)
+    b[3] = float("nan")
+    x, info = h.solve(b)
+    assert info.status == L.HELM_ERR_NAN
+    # matvec cap: status MAXIT, x holds the last iterate (matches the oracle's iterate)
+    x, info = h.solve(cu(p.b), tol=1e-14, maxmv=7)
+    assert info.status == L.HELM_ERR_MAXIT and info.matvecs == 7
+    xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-14, maxmv=7, max_restarts=0))
+    assert io["status"] == 5 and rel(x.cpu().numpy(), xo) < 1e-10
+    h.close()
+
+
+def test_single_unknown_and_single_level():
+    # one unknown per axis: the hierarchy is one level, the V-cycle is the direct solve
+    p = hi.make_problem(2, 3, 0, theta_gamma=0.0, k0=1.0, rhs="random", seed=2)
+    assert p.n == 1
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3)
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype="c128")
+    assert h.nlev == 1
+    assert rel(h.vcycle(cu(p.b)).cpu().numpy(), o.vcycle(p.b)) < 1e-13
+    x, info = h.solve(cu(p.b), tol=1e-12)
+    assert info.status == 0 and info.matvecs <= 2
+    h.close()
+
+
+def test_bad_arguments_are_rejected_on_the_host():
+    p = _problem(CASES[1])
+    h = Helm(p, PCS[0], mg_dtype="c64")
+    b = cu(p.b)
+    from paper_0912_0180_gb300.helm import HelmError
+    with pytest.raises(HelmError):
+        h.solve(b, x=b)  # aliasing
+    with pytest.raises(HelmError):
+        h.solve(b, method=hi.IDR, s=9, shadow=hi.shadow_space(p.n, 9))
+    with pytest.raises(HelmError):
+        h.level_op(L.HELM_OP_COARSE, 0, b, None, b)  # level 0 is not the coarsest
+    h.close()
+
+
+def test_large_2d_workload_sampled():
+    """The 512^2 + 64-layer workload (kh = 0.5, bump k, Gaussian source) at full size: the
+    matvec and one V-cycle element by element, and the full mixed-precision solves through the
+    same entry point the benchmark times, certified by the oracle's own true residual."""
+    p = hi.workload_2d_512()
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype="c64")
+    x = hi.random_vector(p.n, 4)
+    assert rel(h.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
+    assert rel(z, o.vcycle(x)) < 5e-5
+    for method in (hi.BICGSTAB, hi.IDR):
+        xs, info = h.solve(cu(p.b), method=method, s=4, tol=1e-6, maxmv=3000,
+                           shadow=hi.shadow_space(p.n, 4))
+        assert info.status == 0
+        r = p.b - o.apply(xs.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(p.b) < 1e-6
+    h.close()
