@@ -54,6 +54,35 @@ def config(p) -> dict:
             "tol": TOL, "l2": "flushed (512 MiB device write) before every timed step"}
 
 
+# ---- ranks -------------------------------------------------------------------------------
+
+class Ranks:
+    """Replica bookkeeping for N > 1: every rank solves its own copy of the workload (no data
+    exchange); the only collectives are the timing barrier and the max over ranks."""
+
+    def __init__(self, dist=None, device=None):
+        self.dist = dist
+        self.device = device
+        self.world = dist.get_world_size() if dist is not None else 1
+        self.rank = dist.get_rank() if dist is not None else 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_rate(self, units_per_rank: int, ms_per_rank: float) -> float:
+        """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+        return units_per_rank * self.world / (self.max(ms_per_rank) / 1000.0)
+
+
 # ---- clocks ------------------------------------------------------------------------------
 
 class ClockSampler:
@@ -173,6 +202,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phase", default="all", choices=["all", "fp64", "fp32"],
+                    help="which timed paths to run: all (FP64 value, FP32-multigrid, e2e), or only the "
+                         "FP64 / FP32-multigrid device-timed path (for kernel profiling)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the Krylov loop from the host (one graph launch per iteration) so that "
+                         "a kernel profiler sees every launch; slower, for profiling only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -203,17 +238,11 @@ def main():
     b_dev = torch.from_numpy(p.b).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+    ranks = Ranks(dist if world > 1 else None, dev)
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def barrier():
+        ranks.barrier()
+        torch.cuda.synchronize()
 
     ctxs = {}
     for mg in ("c128", "c64"):
@@ -229,10 +258,12 @@ def main():
             e0.record()
             if e2e_host is not None:
                 b_in = e2e_host["b"].to(dev, non_blocking=True)
-                x, info = h.solve(b_in, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh)
+                x, info = h.solve(b_in, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh,
+                                  host_loop=args.host_loop)
                 e2e_host["x"].copy_(x, non_blocking=True)
             else:
-                x, info = h.solve(b_dev, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh)
+                x, info = h.solve(b_dev, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh,
+                                  host_loop=args.host_loop)
             e1.record()
             e1.synchronize()
             lat.append(e0.elapsed_time(e1))
@@ -258,20 +289,42 @@ def main():
             step_ms.append(s0.elapsed_time(s1))
         return step_ms, lat, infos
 
+    run64 = args.phase in ("all", "fp64")
+    run32 = args.phase in ("all", "fp32")
+    ms64 = lat64 = inf64 = ms32 = lat32 = inf32 = None
     with ClockSampler(local) as clk:
-        ms64, lat64, inf64 = timed("c128")
-        ms32, lat32, inf32 = timed("c64")
+        if run64:
+            ms64, lat64, inf64 = timed("c128")
+        if run32:
+            ms32, lat32, inf32 = timed("c64")
+    if args.phase != "all":
+        ms, lat, inf = (ms64, lat64, inf64) if run64 else (ms32, lat32, inf32)
+        step = ranks.max(statistics.mean(ms))
+        line = {"metric": METRIC, "phase": args.phase, "value": ranks.job_rate(len(SOLVES), step),
+                "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": step, "higher_is_better": True, "scaling": "weak",
+                "dtype": "c128" if run64 else "c64 V-cycle, c128 Krylov", "data": "synthetic",
+                "config": config(p), "host_loop": bool(args.host_loop), "clocks": clk.summary(),
+                "gpu_launches": int(sum(i.kernels for i in inf)),
+                "matvecs": {f"{m}-{pc}": inf[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)}}
+        for h in ctxs.values():
+            h.close()
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     e2e_ms, _, _ = timed("c128", e2e=True)
 
     for info in inf64 + inf32:
         if info.status != 0 or not info.rel_res_true < TOL:
             raise SystemExit(f"a timed solve did not converge: {info}")
 
-    step64 = max_over_ranks(statistics.mean(ms64))
-    step32 = max_over_ranks(statistics.mean(ms32))
-    stepe2e = max_over_ranks(statistics.mean(e2e_ms))
+    step64 = ranks.max(statistics.mean(ms64))
+    step32 = ranks.max(statistics.mean(ms32))
+    stepe2e = ranks.max(statistics.mean(e2e_ms))
     nsol = len(SOLVES) * world
-    value = nsol / (step64 / 1000)
+    value = ranks.job_rate(len(SOLVES), step64)
 
     # ---- per-kernel rooflines, measured with CUDA events on the launching stream ----
     kern = kernel_rooflines(torch, L, ctxs, p, dev)

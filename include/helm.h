@@ -91,7 +91,12 @@ typedef struct {
   int max_levels;       /* >= 1 */
   int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
   helm_dtype mg_dtype;  /* HELM_C64: whole V-cycle in complex FP32; HELM_C128: FP64 */
+  int flags;            /* HELM_PF_*; 0 = defaults */
 } helm_precond;
+
+/* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
+ * same arithmetic as the default fused kernels; for testing the fusion) */
+enum { HELM_PF_UNFUSED = 1 };
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
  * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;
@@ -109,6 +114,11 @@ typedef struct {
   double* history;      /* optional DEVICE array of maxmv doubles: entry m-1 receives the
                            recurrence residual / ||b|| after preconditioned matvec m (the
                            convergence history of the paper's Figure "krylov"); NULL = off */
+  int host_loop;        /* 0: the loop runs on the device (conditional WHILE graph node);
+                           1: the host launches the captured iteration once per iteration and
+                           reads the convergence flag after each (same kernels, one
+                           synchronisation per iteration; lets kernel profilers see every
+                           launch of the loop) */
 } helm_solve_opts;
 
 typedef struct {

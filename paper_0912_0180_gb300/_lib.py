@@ -12,6 +12,7 @@ HELM_ERR_BREAKDOWN, HELM_ERR_MAXIT, HELM_ERR_NAN, HELM_ERR_TIMEOUT, HELM_ERR_BUS
 HELM_C64, HELM_C128 = 0, 1
 HELM_OP_APPLY, HELM_OP_RESIDUAL, HELM_OP_SMOOTH, HELM_OP_SMOOTH0 = 0, 1, 2, 3
 HELM_OP_RESTRICT, HELM_OP_PROLONG, HELM_OP_COARSE = 4, 5, 6
+HELM_PF_UNFUSED = 1
 
 
 class Grid(C.Structure):
@@ -27,12 +28,13 @@ class Precond(C.Structure):
     _fields_ = [("kind", C.c_int), ("theta_beta", C.c_double), ("shift_re", C.c_double),
                 ("shift_im", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int), ("smoother", C.c_int),
                 ("omega", C.c_double), ("max_levels", C.c_int), ("coarse_max", C.c_int),
-                ("mg_dtype", C.c_int)]
+                ("mg_dtype", C.c_int), ("flags", C.c_int)]
 
 
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("s", C.c_int), ("tol", C.c_double), ("maxmv", C.c_int),
-                ("max_restarts", C.c_int), ("shadow", C.c_void_p), ("history", C.c_void_p)]
+                ("max_restarts", C.c_int), ("shadow", C.c_void_p), ("history", C.c_void_p),
+                ("host_loop", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -46,7 +46,7 @@ static helm_status check_grid(const helm_grid* g) {
       return HELM_ERR_ARG;
     }
     long n = (long)g->n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
-    if (n < 1 || n > (1L << 24)) { set_error("axis has no unknowns or too many"); return HELM_ERR_ARG; }
+    if (n < 1 || n > 65535) { set_error("an axis has no unknowns or more than 65535"); return HELM_ERR_ARG; }
     total *= n;
     if (total > (1L << 34)) { set_error("grid too large"); return HELM_ERR_ARG; }
   }
@@ -63,6 +63,7 @@ static helm_status check_precond(const helm_precond* p) {
   if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
   if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
   if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
+  if (p->flags & ~HELM_PF_UNFUSED) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
   if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {
     set_error("non-finite preconditioner parameter");
     return HELM_ERR_ARG;
@@ -154,9 +155,9 @@ helm_status helm_vcycle(helm_ctx* c, const void* r, void* z, void* stream) {
   if (f32) {
     helm_status s = convert_c128_to_mg(c, (const double2*)r, c->scratch, st);
     if (s != HELM_OK) return s;
-    return mg_vcycle<float>(c, (const float2*)c->scratch, (float2*)z, nullptr, st);
+    return mg_vcycle<float>(c, (const float2*)c->scratch, z, false, nullptr, st);
   }
-  return mg_vcycle<double>(c, (const double2*)r, (double2*)z, nullptr, st);
+  return mg_vcycle<double>(c, (const double2*)r, z, false, nullptr, st);
 }
 
 helm_status helm_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, void* out, int count,

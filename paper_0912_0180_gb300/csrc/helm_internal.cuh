@@ -50,6 +50,9 @@ template <typename TO, typename TI> __host__ __device__ __forceinline__ cx<TO> c
 
 // ---- operator view ---------------------------------------------------------------------
 // A level operator: per-axis Shortley-Weller rows (am, a0, ap) and sigma = s * phi.
+// Uniform interior: on axis a, unknowns ulo[a]..uhi[a] share one row (am = ap = ua[a], a0 equal);
+// a point inside all the ranges has the row ud x_P + sum_a ua[a] (x_{P-e_a} + x_{P+e_a}) - s phi x_P,
+// evaluated with fewer operations (uniform_real: ua and s real, as for H).
 template <typename T> struct OpView {
   int n[3];
   const cx<T>* am[3];
@@ -58,6 +61,12 @@ template <typename T> struct OpView {
   const T* phi;   // nullptr -> phi0 everywhere
   T phi0;
   cx<T> s;
+  int ulo[3], uhi[3];
+  cx<T> ua[3];
+  cx<T> ud;
+  int uniform_real;
+  const cx<T>* dinv;  // 1 / diagonal at every point (multigrid levels; nullptr otherwise)
+  const cx<T>* dg;    // the diagonal itself (multigrid levels; nullptr otherwise)
 };
 
 // ---- owned device storage of one level ---------------------------------------------------
@@ -74,6 +83,15 @@ struct LevelHost {
   float* phi32 = nullptr;
   double phi0 = 0.0;
   double2 s = {1.0, 0.0};
+  // uniform interior (see OpView), found at setup from the FP64 tables
+  int ulo[3] = {1, 1, 1}, uhi[3] = {0, 0, 0};
+  double2 ua[3] = {};
+  double2 ud = {0.0, 0.0};
+  // reciprocal of the diagonal, multigrid precision (multigrid levels only)
+  double2* dinv64 = nullptr;
+  float2* dinv32 = nullptr;
+  double2* dg64 = nullptr;   // the diagonal itself, same precision
+  float2* dg32 = nullptr;
   // work vectors (MG type), allocated for multigrid levels
   void* u = nullptr;
   void* f = nullptr;
@@ -101,6 +119,7 @@ struct helm_ctx {
   std::vector<void*> allocs;         // everything to free
   helm::Workspace* ws = nullptr;     // Krylov workspace (lazily created)
   void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
+  int tail_first = 1 << 30;          // first level run by the single-block tail kernel
 };
 
 namespace helm {
@@ -122,13 +141,26 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st);
 helm_status build_hierarchy(helm_ctx* c, cudaStream_t st);
 
 // mg.cu
+// z = V-cycle(f0); u0 is cx<T> or, with u0_f64, complex128 (the multigrid result widened in the
+// kernel that writes it -- the precision boundary into the FP64 Krylov vectors)
 template <typename T>
-helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, cx<T>* u0, const int* skip, cudaStream_t st);
+helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, void* u0, bool u0_f64, const int* skip, cudaStream_t st);
 helm_status mg_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, void* out, int count,
                         cudaStream_t st);
 // y = H x (FP64 arithmetic); x of type TX; optional fused partial inner products handled in krylov.cu
 helm_status h_apply(helm_ctx* c, bool x_is_f32, const void* x, double2* y, cudaStream_t st);
 helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st);
+
+// mg_fused.cu
+template <typename T> int tail_first_level(const helm_ctx* c);
+template <typename T>
+helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,
+                        cudaStream_t st);
+template <typename T>
+void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>* fc, const int* skip, cudaStream_t st);
+template <typename T>
+void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, const cx<T>* f, void* out,
+                bool out_f64, const int* skip, cudaStream_t st);
 
 // krylov.cu
 helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,

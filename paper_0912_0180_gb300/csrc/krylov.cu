@@ -42,12 +42,14 @@ struct Workspace {
   KrylovState* hst = nullptr;  // pinned host copy
   double2* partials = nullptr; // [NRED][G]
   double2 *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *sv = nullptr, *t = nullptr, *q = nullptr;
-  void *pmg = nullptr, *smg = nullptr, *ph = nullptr, *sh = nullptr;  // mg precision
+  void *pmg = nullptr, *smg = nullptr;  // V-cycle inputs in the multigrid precision
+  double2 *ph = nullptr, *sh = nullptr; // V-cycle outputs, widened to complex128
   double2 *P = nullptr, *dR = nullptr, *dX = nullptr;                  // IDR, s vectors each
   const void* shadow_key = nullptr;
   cudaGraphExec_t loop = nullptr;
+  cudaGraphExec_t body = nullptr;       // host-driven loop: one iteration per launch
   cudaGraphExec_t idr_init = nullptr;
-  cudaGraph_t loop_graph = nullptr, init_graph = nullptr;
+  cudaGraph_t loop_graph = nullptr, init_graph = nullptr, body_graph = nullptr;
   size_t body_nodes = 0, init_nodes = 0;  // kernels per loop body / IDR start graph
   std::vector<void*> mem;
 };
@@ -141,6 +143,14 @@ template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i,
 
 #define GRID_LOOP(i, n) for (long i = blockIdx.x * (long)KT + threadIdx.x; i < (n); i += (long)gridDim.x * KT)
 
+// Stencil kernels walk whole grid rows (fixed j, l): one div/mod per row, not per point.
+#define ROW_LOOP(H, i, j, l, p)                                                   \
+  for (long row_ = blockIdx.x, nrows_ = (long)(H).n[1] * (H).n[2]; row_ < nrows_;  \
+       row_ += gridDim.x)                                                         \
+    for (int j = (int)(row_ % (H).n[1]), l = (int)(row_ / (H).n[1]), i = threadIdx.x; \
+         i < (H).n[0]; i += KT)                                                    \
+      if (const long p = i + row_ * (H).n[0]; true)
+
 // ---- shared kernels ----------------------------------------------------------------------
 
 // Start (or restart) from the current residual r: ||r||, shadow r^ = r, p = v = 0 and
@@ -182,9 +192,7 @@ template <int DIM>
 __global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __restrict__ b,
                            const double2* __restrict__ x, double2* __restrict__ r, long n, double2* partials) {
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
+  ROW_LOOP(H, i, j, l, p) {
     double2 ri = csub<double>(b[p], op_row<double, double, DIM>(H, x, i, j, l, p));
     r[p] = ri;
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
@@ -222,15 +230,13 @@ __global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, do
 }
 
 // v = H p^ and alpha = rho / (r^H v).
-template <typename TM, int DIM>
-__global__ void k_bicg_v(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ ph,
+template <int DIM>
+__global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __restrict__ ph,
                          const double2* __restrict__ rh, double2* __restrict__ v, long n, double2* partials) {
   if (S->done) return;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
-    double2 vi = op_row<double, TM, DIM>(H, ph, i, j, l, p);
+  ROW_LOOP(H, i, j, l, p) {
+    double2 vi = op_row<double, double, DIM>(H, ph, i, j, l, p);
     v[p] = vi;
     acc[0] = cadd<double>(acc[0], cmulc<double>(rh[p], vi));
   }
@@ -269,23 +275,20 @@ __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const do
 }
 
 // x += alpha p^ after a half-step exit.
-template <typename TM>
-__global__ void k_bicg_xhalf(KrylovState* S, const cx<TM>* __restrict__ ph, double2* __restrict__ x, long n) {
+__global__ void k_bicg_xhalf(KrylovState* S, const double2* __restrict__ ph, double2* __restrict__ x, long n) {
   if (!S->half) return;
   double2 al = S->alpha;
-  GRID_LOOP(i, n) x[i] = cfma<double>(al, cconv<double, TM>(ph[i]), x[i]);
+  GRID_LOOP(i, n) x[i] = cfma<double>(al, ph[i], x[i]);
 }
 
 // t = H s^, omega = (t^H s) / (t^H t).
-template <typename TM, int DIM>
-__global__ void k_bicg_t(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ sh,
+template <int DIM>
+__global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __restrict__ sh,
                          const double2* __restrict__ sv, double2* __restrict__ t, long n, double2* partials) {
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
-    double2 ti = op_row<double, TM, DIM>(H, sh, i, j, l, p);
+  ROW_LOOP(H, i, j, l, p) {
+    double2 ti = op_row<double, double, DIM>(H, sh, i, j, l, p);
     t[p] = ti;
     acc[0] = cadd<double>(acc[0], cmulc<double>(ti, sv[p]));
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
@@ -301,8 +304,7 @@ __global__ void k_bicg_t(KrylovState* S, OpView<double> H, const cx<TM>* __restr
 }
 
 // x += alpha p^ + omega s^; r = s - omega t; ||r||, rho = r^H r and the next beta.
-template <typename TM>
-__global__ void k_bicg_xr(KrylovState* S, const cx<TM>* __restrict__ ph, const cx<TM>* __restrict__ sh,
+__global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const double2* __restrict__ sh,
                           const double2* __restrict__ sv, const double2* __restrict__ t,
                           const double2* __restrict__ rh, double2* __restrict__ x, double2* __restrict__ r,
                           long n, double2* partials) {
@@ -310,7 +312,7 @@ __global__ void k_bicg_xr(KrylovState* S, const cx<TM>* __restrict__ ph, const c
   double2 al = S->alpha, om = S->omega;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
-    x[i] = cfma<double>(om, cconv<double, TM>(sh[i]), cfma<double>(al, cconv<double, TM>(ph[i]), x[i]));
+    x[i] = cfma<double>(om, sh[i], cfma<double>(al, ph[i], x[i]));
     double2 ri = csub<double>(sv[i], cmul<double>(om, t[i]));
     r[i] = ri;
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
@@ -343,15 +345,13 @@ __device__ __forceinline__ void proj_acc(const double2* __restrict__ P, long n, 
 }
 
 // Minimal-residual start step k: t = H z, omega = (t^H r) / (t^H t).
-template <typename TM, int DIM>
-__global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ z,
+template <int DIM>
+__global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                            const double2* __restrict__ r, double2* __restrict__ t, long n, double2* partials) {
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
-    double2 ti = op_row<double, TM, DIM>(H, z, i, j, l, p);
+  ROW_LOOP(H, i, j, l, p) {
+    double2 ti = op_row<double, double, DIM>(H, z, i, j, l, p);
     t[p] = ti;
     acc[0] = cadd<double>(acc[0], cmulc<double>(ti, r[p]));
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
@@ -369,14 +369,14 @@ __global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const cx<TM>* __res
 
 // dX_k = omega z, dR_k = -omega t, x += dX_k, r += dR_k, ||r||.
 template <typename TM>
-__global__ void k_idr_mr_upd(KrylovState* S, int kcol, const cx<TM>* __restrict__ z, const double2* __restrict__ t,
+__global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict__ z, const double2* __restrict__ t,
                              double2* __restrict__ dX, double2* __restrict__ dR, double2* __restrict__ x,
                              double2* __restrict__ r, void* rmg, long n, double2* partials) {
   if (S->done) return;
   double2 om = S->omega;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
-    double2 dx = cmul<double>(om, cconv<double, TM>(z[i]));
+    double2 dx = cmul<double>(om, z[i]);
     double2 dr = cmul<double>(om, t[i]);
     dr = mkc<double>(-dr.x, -dr.y);
     dX[kcol * n + i] = dx;
@@ -465,16 +465,14 @@ __global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, co
 }
 
 // First step of a cycle (k == 0): t = H z, omega = (t^H v) / (t^H t), v = r + q.
-template <typename TM, int DIM>
-__global__ void k_idr_t0(KrylovState* S, OpView<double> H, const cx<TM>* __restrict__ z,
+template <int DIM>
+__global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                          const double2* __restrict__ r, const double2* __restrict__ q,
                          double2* __restrict__ t, long n, double2* partials) {
   if (S->done || S->k != 0) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
-    double2 ti = op_row<double, TM, DIM>(H, z, i, j, l, p);
+  ROW_LOOP(H, i, j, l, p) {
+    double2 ti = op_row<double, double, DIM>(H, z, i, j, l, p);
     t[p] = ti;
     acc[0] = cadd<double>(acc[0], cmulc<double>(ti, cadd<double>(r[p], q[p])));
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
@@ -489,8 +487,8 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const cx<TM>* __restr
 }
 
 // dX_oldest = -dX c + omega z (in place: each entry reads its row of dX before writing).
-template <typename TM, int S_>
-__global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const cx<TM>* __restrict__ z, long n) {
+template <int S_>
+__global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const double2* __restrict__ z, long n) {
   if (S->done) return;
   double2 c[S_];
 #pragma unroll
@@ -498,7 +496,7 @@ __global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const c
   double2 om = S->omega;
   int o = S->oldest;
   GRID_LOOP(i, n) {
-    double2 acc = cmul<double>(om, cconv<double, TM>(z[i]));
+    double2 acc = cmul<double>(om, z[i]);
 #pragma unroll
     for (int k = 0; k < S_; ++k) acc = csub<double>(acc, cmul<double>(dX[k * n + i], c[k]));
     dX[o * n + i] = acc;
@@ -511,9 +509,7 @@ __global__ void k_idr_tk(const KrylovState* S, OpView<double> H, const double2* 
                          double2* __restrict__ t, long n) {
   if (S->done || S->k == 0) return;
   const double2* d = dX + S->oldest * n;
-  GRID_LOOP(p, n) {
-    int i, j, l;
-    unflatten(p, H.n, i, j, l);
+  ROW_LOOP(H, i, j, l, p) {
     t[p] = op_row<double, double, DIM>(H, d, i, j, l, p);
   }
 }
@@ -596,6 +592,8 @@ void krylov_free(helm_ctx* c) {
   Workspace* w = c->ws;
   if (!w) return;
   if (w->loop) cudaGraphExecDestroy(w->loop);
+  if (w->body) cudaGraphExecDestroy(w->body);
+  if (w->body_graph) cudaGraphDestroy(w->body_graph);
   if (w->idr_init) cudaGraphExecDestroy(w->idr_init);
   if (w->loop_graph) cudaGraphDestroy(w->loop_graph);
   if (w->init_graph) cudaGraphDestroy(w->init_graph);
@@ -615,9 +613,10 @@ struct Ctx {
   int G;
 };
 
+// one V-cycle on the precision-boundary copy `in_mg`; the result is written in FP64
 template <typename TM>
-static helm_status precondition(const Ctx& k, const void* in_mg, void* out_mg, cudaStream_t st) {
-  return mg_vcycle<TM>(k.c, (const cx<TM>*)in_mg, (cx<TM>*)out_mg, &k.w->st->done, st);
+static helm_status precondition(const Ctx& k, const void* in_mg, double2* out, cudaStream_t st) {
+  return mg_vcycle<TM>(k.c, (const cx<TM>*)in_mg, out, true, &k.w->st->done, st);
 }
 
 template <typename TM, int DIM>
@@ -630,24 +629,24 @@ static helm_status enqueue_bicg_iter(const Ctx& k, cudaStream_t st) {
   const bool f32 = std::is_same<TM, float>::value;
   void* pcopy = f32 ? w->pmg : nullptr;
   void* scopy = f32 ? w->smg : nullptr;
-  const cx<TM>* pin = f32 ? (const cx<TM>*)w->pmg : (const cx<TM>*)(const void*)w->p;
-  const cx<TM>* sin_ = f32 ? (const cx<TM>*)w->smg : (const cx<TM>*)(const void*)w->sv;
+  const void* pin = f32 ? (const void*)w->pmg : (const void*)w->p;
+  const void* sin_ = f32 ? (const void*)w->smg : (const void*)w->sv;
   k_bicg_p<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->p, w->v, pcopy, k.n);
-  const cx<TM>* ph = pin;
+  const double2* ph = w->p;
   if (k.pc) {
     if ((s = precondition<TM>(k, pin, w->ph, st)) != HELM_OK) return s;
-    ph = (const cx<TM>*)w->ph;
+    ph = w->ph;
   }
-  k_bicg_v<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, ph, w->rh, w->v, k.n, w->partials);
+  k_bicg_v<DIM><<<k.G, KT, 0, st>>>(w->st, H, ph, w->rh, w->v, k.n, w->partials);
   k_bicg_s<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->v, w->sv, scopy, k.n, w->partials);
-  k_bicg_xhalf<TM><<<k.G, KT, 0, st>>>(w->st, ph, w->x, k.n);
-  const cx<TM>* sh = sin_;
+  k_bicg_xhalf<<<k.G, KT, 0, st>>>(w->st, ph, w->x, k.n);
+  const double2* sh = w->sv;
   if (k.pc) {
     if ((s = precondition<TM>(k, sin_, w->sh, st)) != HELM_OK) return s;
-    sh = (const cx<TM>*)w->sh;
+    sh = w->sh;
   }
-  k_bicg_t<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, sh, w->sv, w->t, k.n, w->partials);
-  k_bicg_xr<TM><<<k.G, KT, 0, st>>>(w->st, ph, sh, w->sv, w->t, w->rh, w->x, w->r, k.n, w->partials);
+  k_bicg_t<DIM><<<k.G, KT, 0, st>>>(w->st, H, sh, w->sv, w->t, k.n, w->partials);
+  k_bicg_xr<<<k.G, KT, 0, st>>>(w->st, ph, sh, w->sv, w->t, w->rh, w->x, w->r, k.n, w->partials);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
@@ -660,15 +659,13 @@ static helm_status enqueue_idr_step(const Ctx& k, cudaStream_t st) {
   k_idr_small<<<1, 32, 0, st>>>(w->st);
   void* vin = w->pmg;  // v in multigrid precision (always materialised)
   k_idr_v<TM, S_><<<k.G, KT, 0, st>>>(w->st, w->dR, w->r, w->q, vin, k.n);
-  const cx<TM>* z;
+  const double2* z = (const double2*)vin;  // identity preconditioner: TM is double
   if (k.pc) {
     if ((s = precondition<TM>(k, vin, w->ph, st)) != HELM_OK) return s;
-    z = (const cx<TM>*)w->ph;
-  } else {
-    z = (const cx<TM>*)vin;
+    z = w->ph;
   }
-  k_idr_t0<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->q, w->t, k.n, w->partials);
-  k_idr_dx<TM, S_><<<k.G, KT, 0, st>>>(w->st, w->dX, z, k.n);
+  k_idr_t0<DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->q, w->t, k.n, w->partials);
+  k_idr_dx<S_><<<k.G, KT, 0, st>>>(w->st, w->dX, z, k.n);
   k_idr_tk<DIM><<<k.G, KT, 0, st>>>(w->st, H, w->dX, w->t, k.n);
   k_idr_upd<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR, w->dX, w->q, w->t, w->x, w->r, k.n, w->partials);
   HELM_CUDA(cudaGetLastError());
@@ -681,14 +678,12 @@ static helm_status enqueue_idr_init(const Ctx& k, cudaStream_t st) {
   OpView<double> H = k.c->H.view<double>();
   helm_status s;
   for (int kc = 0; kc < S_; ++kc) {
-    const cx<TM>* z;
+    const double2* z = (const double2*)w->pmg;
     if (k.pc) {
       if ((s = precondition<TM>(k, w->pmg, w->ph, st)) != HELM_OK) return s;
-      z = (const cx<TM>*)w->ph;
-    } else {
-      z = (const cx<TM>*)w->pmg;
+      z = w->ph;
     }
-    k_idr_mr_t<TM, DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->t, k.n, w->partials);
+    k_idr_mr_t<DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->t, k.n, w->partials);
     k_idr_mr_upd<TM><<<k.G, KT, 0, st>>>(w->st, kc, z, w->t, w->dX, w->dR, w->x, w->r, w->pmg, k.n, w->partials);
   }
   for (int j = 0; j < S_; ++j) k_idr_proj<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR + (long)j * k.n, j, k.n, w->partials);
@@ -819,7 +814,9 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
     long n = c->n;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
-    w->G = grid_blocks(n, KT, sms * 4);
+    // two blocks per SM: each thread then reduces several points before the (FP64, shuffle)
+    // block reduction, whose cost is per thread, not per point
+    w->G = grid_blocks(n, KT, sms * 2);
     size_t v64 = sizeof(double2) * n;
     bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
     size_t vmg = (f32 ? sizeof(float2) : sizeof(double2)) * n;
@@ -831,12 +828,12 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
     double2** vecs[] = {&w->x, &w->r, &w->t};
     for (auto pp : vecs) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
     if ((s = ws_alloc(c, w, &w->pmg, vmg)) != HELM_OK) return s;
-    if ((s = ws_alloc(c, w, &w->ph, vmg)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, (void**)&w->ph, v64)) != HELM_OK) return s;
     if (o->method == HELM_BICGSTAB) {
       double2** more[] = {&w->rh, &w->p, &w->v, &w->sv};
       for (auto pp : more) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
       if ((s = ws_alloc(c, w, &w->smg, vmg)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, &w->sh, vmg)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->sh, v64)) != HELM_OK) return s;
     } else {
       if ((s = ws_alloc(c, w, (void**)&w->q, v64)) != HELM_OK) return s;
       if ((s = ws_alloc(c, w, (void**)&w->P, v64 * o->s)) != HELM_OK) return s;
@@ -862,6 +859,11 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
       cudaGraphGetNodes(w->init_graph, nullptr, &ni);
       w->init_nodes = ni;
     }
+  }
+  if (o->host_loop && !w->body) {
+    helm_status s = capture(st, &w->body_graph, [&](cudaStream_t cs) { return enqueue_body_any<TM>(k, o->method, o->s, cs); });
+    if (s != HELM_OK) return s;
+    HELM_CUDA(cudaGraphInstantiate(&w->body, w->body_graph, 0));
   }
   return HELM_OK;
 }
@@ -918,7 +920,19 @@ static helm_status solve_t(helm_ctx* c, const double2* b, double2* x, const helm
                                 bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n, restarts == 0 ? 1 : 0,
                                 w->partials);
     if (!bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
-    HELM_CUDA(cudaGraphLaunch(w->loop, st));
+    long host_loops = -1;
+    if (o->host_loop) {
+      host_loops = 0;
+      for (;;) {
+        HELM_CUDA(cudaMemcpyAsync(&w->hst->done, &w->st->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA(cudaStreamSynchronize(st));
+        if (w->hst->done || host_loops > o->maxmv + 16) break;
+        HELM_CUDA(cudaGraphLaunch(w->body, st));
+        ++host_loops;
+      }
+    } else {
+      HELM_CUDA(cudaGraphLaunch(w->loop, st));
+    }
     switch (k.dim) {
       case 1: k_true_res<1><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
       case 2: k_true_res<2><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
@@ -929,7 +943,8 @@ static helm_status solve_t(helm_ctx* c, const double2* b, double2* x, const helm
     HELM_CUDA(cudaStreamSynchronize(st));
     const KrylovState& hs = *w->hst;
     // k_start, the loop head, loops x body, k_true_res (+ the IDR start graph)
-    kernels += 3 + (long)hs.loops * (long)w->body_nodes + (bicg ? 0 : (long)w->init_nodes);
+    if (host_loops >= 0) kernels += 2 + host_loops * (long)(w->body_nodes - 1) + (bicg ? 0 : (long)w->init_nodes);
+    else kernels += 3 + (long)hs.loops * (long)w->body_nodes + (bicg ? 0 : (long)w->init_nodes);
     if (hs.status != HELM_OK || hs.rel_true < o->tol) break;
     if (restarts >= o->max_restarts) break;
     ++restarts;

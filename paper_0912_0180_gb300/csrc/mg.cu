@@ -6,6 +6,8 @@
 // Kernels take an optional `skip` flag: when it points to a non-zero word the kernel returns
 // at once.  Inside a captured Krylov iteration this lets the remaining work of a converged
 // solve cost one flag read per thread.
+#include <type_traits>
+
 #include "stencil.cuh"
 
 namespace helm {
@@ -37,20 +39,22 @@ __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T
   y[p] = f ? csub<T>(f[p], v) : v;
 }
 
-// One damped-Jacobi sweep un = u + omega D^{-1} (f - M u); u == nullptr is the zero guess.
+// One damped-Jacobi sweep un = u + omega D^{-1} (f - M u), evaluated as
+// (1 - omega) u + omega D^{-1} (f - offdiag(u)) with the stored D^{-1}; u == nullptr is the
+// zero guess (un = omega D^{-1} f).
 template <typename T, int DIM>
 __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ un, T omega, const int* skip) {
   if (skip && *skip) return;
   POINT_INDEX(op);
-  cx<T> d = op_diag<T, DIM>(op, i, j, l, p);
-  cx<T> r = f[p];
-  cx<T> u0 = mkc<T>(T(0), T(0));
-  if (u) {
-    u0 = u[p];
-    r = csub<T>(r, cfma<T>(d, u0, op_offdiag<T, T, DIM>(op, u, i, j, l, p)));
+  cx<T> di = op.dinv[p];
+  if (!u) {
+    un[p] = cscale<T>(omega, cmul<T>(f[p], di));
+    return;
   }
-  un[p] = cadd<T>(u0, cscale<T>(omega, cdiv<T>(r, d)));
+  cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
+  cx<T> u0 = u[p];
+  un[p] = mkc<T>(fma(omega, g.x, (T(1) - omega) * u0.x), fma(omega, g.y, (T(1) - omega) * u0.y));
 }
 
 // Red-black Gauss-Seidel half-sweep on points with (i + j + l) % 2 == colour, in place:
@@ -63,13 +67,12 @@ __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restr
   POINT_INDEX(op);
   int c = (i + j + l) & 1;
   if (zero_guess) {
-    if (c == 0) u[p] = cdiv<T>(f[p], op_diag<T, DIM>(op, i, j, l, p));
+    if (c == 0) u[p] = cmul<T>(f[p], op.dinv[p]);
     else u[p] = mkc<T>(T(0), T(0));
     return;
   }
   if (c != colour) return;
-  cx<T> d = op_diag<T, DIM>(op, i, j, l, p);
-  u[p] = cdiv<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), d);
+  u[p] = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), op.dinv[p]);
 }
 
 struct Dims { int f[3]; int c[3]; };
@@ -165,7 +168,20 @@ __global__ void k_h_apply(OpView<double> op, const cx<TX>* __restrict__ x, doubl
   y[p] = op_row<double, TX, DIM>(op, x, i, j, l, p);
 }
 
+__global__ void k_widen(const float2* __restrict__ a, double2* __restrict__ b, long n, const int* skip) {
+  if (skip && *skip) return;
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (p < n) b[p] = cconv<double, float>(a[p]);
+}
+
 // ---- host side -------------------------------------------------------------------------
+
+static void widen_c64(const helm_ctx*, const float2* a, double2* b, long n, const int* skip, cudaStream_t st) {
+  k_widen<<<(int)((n + 255) / 256), 256, 0, st>>>(a, b, n, skip);
+}
+
+template <typename T>
+static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st);
 
 template <typename T, int DIM> struct Launch {
   static void apply(const LevelHost& L, const cx<T>* x, const cx<T>* f, cx<T>* y, const int* skip, cudaStream_t st) {
@@ -249,9 +265,44 @@ static void smooth(helm_ctx* c, const LevelHost& L, cx<T>* b[2], int* cur, const
   }
 }
 
-// V-cycle on level l for M_l u = f from u = 0; the result lands in `out`.
 template <typename T>
-static void vcycle_level(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st) {
+static bool fused_applies(const helm_ctx* c, int l) {
+  const helm_precond& pcf = c->pc;
+  if (pcf.flags & HELM_PF_UNFUSED) return false;
+  if (l >= c->tail_first) return true;
+  return c->lv[l].dim == 2 && pcf.nu1 == 1 && pcf.nu2 == 1 && l < (int)c->lv.size() - 1;
+}
+
+// V-cycle on level l for M_l u = f from u = 0; the result lands in `out` (complex128 when
+// out_f64, else cx<T>; only level 0 is ever asked for complex128 with T = float).
+template <typename T>
+static void vcycle_level(helm_ctx* c, int l, const cx<T>* f, void* out, bool out_f64, const int* skip,
+                         cudaStream_t st) {
+  const LevelHost& L = c->lv[l];
+  int nl = (int)c->lv.size();
+  if (fused_applies<T>(c, l)) {
+    if (l >= c->tail_first) {  // this level and all coarser ones in one block
+      tail_vcycle<T>(c, l, f, out, out_f64, skip, st);
+      return;
+    }
+    const LevelHost& C = c->lv[l + 1];
+    fused_down2d<T>(c, l, f, (cx<T>*)L.w, (cx<T>*)C.f, skip, st);
+    vcycle_level<T>(c, l + 1, (const cx<T>*)C.f, C.u, false, skip, st);
+    fused_up2d<T>(c, l, (const cx<T>*)L.w, (const cx<T>*)C.u, f, out, out_f64, skip, st);
+    return;
+  }
+  if (out_f64 && !std::is_same<T, double>::value) {
+    // one-kernel-per-component path: run in the multigrid precision, then widen
+    vcycle_level<T>(c, l, f, c->scratch, false, skip, st);
+    widen_c64(c, (const float2*)c->scratch, (double2*)out, L.ntot, skip, st);
+    return;
+  }
+  vcycle_unfused<T>(c, l, f, (cx<T>*)out, skip, st);
+}
+
+// the one-kernel-per-component V-cycle on level l (below it, fused levels may take over)
+template <typename T>
+static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st) {
   const LevelHost& L = c->lv[l];
   int nl = (int)c->lv.size();
   if (l == nl - 1) {
@@ -272,19 +323,19 @@ static void vcycle_level(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const i
   } else {
     restrict_any<T>(L, C, f, fc, skip, st);
   }
-  vcycle_level<T>(c, l + 1, fc, (cx<T>*)C.u, skip, st);
+  vcycle_level<T>(c, l + 1, fc, C.u, false, skip, st);
   prolong_any<T>(L, C, (const cx<T>*)C.u, b[cur], pc.nu1 > 0 ? 0 : 1, skip, st);
   smooth<T>(c, L, b, &cur, f, pc.nu2, false, skip, st);
 }
 
 template <typename T>
-helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, cx<T>* u0, const int* skip, cudaStream_t st) {
-  vcycle_level<T>(c, 0, f0, u0, skip, st);
+helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, void* u0, bool u0_f64, const int* skip, cudaStream_t st) {
+  vcycle_level<T>(c, 0, f0, u0, u0_f64 && !std::is_same<T, double>::value, skip, st);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
-template helm_status mg_vcycle<float>(helm_ctx*, const float2*, float2*, const int*, cudaStream_t);
-template helm_status mg_vcycle<double>(helm_ctx*, const double2*, double2*, const int*, cudaStream_t);
+template helm_status mg_vcycle<float>(helm_ctx*, const float2*, void*, bool, const int*, cudaStream_t);
+template helm_status mg_vcycle<double>(helm_ctx*, const double2*, void*, bool, const int*, cudaStream_t);
 
 template <typename T>
 static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void* bb, void* out, int count,

@@ -1,0 +1,515 @@
+// mg_fused.cu -- the V(1,1) cycle restructured for the GPU: the arithmetic of the per-component
+// kernels of mg.cu (Section 5.1 / 6.1 components), fused so that a cycle costs few launches and
+// little HBM traffic, and free of divisions (every level stores 1/D).
+//
+//  k_down2d  pre-smoothing sweep from the zero guess + residual + full-weighting restriction.
+//            One block per 16 x 8 tile of coarse points; f of the fine tile plus a halo is
+//            staged in shared memory, u is computed there and written once, and the residual
+//            never leaves shared memory.  After a sweep from the zero guess the residual needs
+//            no diagonal: D u = omega f for Jacobi, so r = (1 - omega) f - offdiag(u); for
+//            red-black Gauss-Seidel r = -offdiag(u) on red points and r = 0 on black points.
+//  k_up2d    bilinear prolongation of the coarse correction + the post-smoothing sweep, out of
+//            place (reads u, writes the next iterate), halo staged in shared memory; the
+//            finest level may write its result widened to complex128 (the precision boundary
+//            into the FP64 Krylov vectors).
+//  k_tail    the coarsest levels (a few thousand unknowns in FP32, about a hundred in FP64) in
+//            ONE block: smoothing, residual, restriction, the dense coarsest solve,
+//            prolongation and post-smoothing, with __syncthreads() between phases instead of
+//            kernel launches.
+//
+// Outside the grid every value is a Dirichlet zero, as in the unfused kernels.
+#include <type_traits>
+
+#include "stencil.cuh"
+
+namespace helm {
+
+constexpr int DN_CX = 16, DN_CY = 8;         // coarse tile of k_down2d
+constexpr int UP_FX = 32, UP_FY = 8;         // fine tile of k_up2d
+constexpr int FUSED_THREADS = 256;
+
+// ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
+// HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
+template <typename T, bool RBGS>
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
+         cx<T>* __restrict__ fc, T omega, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int HF = RBGS ? 2 : 1;
+  constexpr int RX = 2 * DN_CX + 1, RY = 2 * DN_CY + 1;  // residual region
+  constexpr int FX = RX + 2 * HF, FY = RY + 2 * HF;      // staged f / u region
+  __shared__ cx<T> sf[FY][FX];
+  __shared__ cx<T> su[FY][FX];
+  __shared__ cx<T> sr[RY][RX];
+  const int n0 = op.n[0], n1 = op.n[1];
+  const int I0 = blockIdx.x * DN_CX, J0 = blockIdx.y * DN_CY;
+  const int fx0 = 2 * I0 - HF, fy0 = 2 * J0 - HF;  // origin of the staged region
+  const int tid = threadIdx.x;
+  // stage f; Jacobi: u = omega D^-1 f; RB-GS: red u = D^-1 f, black 0
+  for (int e = tid; e < FX * FY; e += FUSED_THREADS) {
+    int x = e % FX, y = e / FX;
+    int i = fx0 + x, j = fy0 + y;
+    cx<T> fv = mkc<T>(T(0), T(0)), uv = mkc<T>(T(0), T(0));
+    if (i >= 0 && i < n0 && j >= 0 && j < n1) {
+      int p = i + n0 * j;
+      fv = f[p];
+      if (!RBGS) uv = cscale<T>(omega, cmul<T>(fv, op.dinv[p]));
+      else if (((i + j) & 1) == 0) uv = cmul<T>(fv, op.dinv[p]);
+    }
+    sf[y][x] = fv;
+    su[y][x] = uv;
+  }
+  __syncthreads();
+  if (RBGS) {  // black points of the inner region from the red values just computed
+    for (int e = tid; e < (FX - 2) * (FY - 2); e += FUSED_THREADS) {
+      int x = 1 + e % (FX - 2), y = 1 + e / (FX - 2);
+      int i = fx0 + x, j = fy0 + y;
+      if (i < 0 || i >= n0 || j < 0 || j >= n1 || ((i + j) & 1) == 0) continue;
+      cx<T> acc = off2d<T>(op, i, j, su[y][x - 1], su[y][x + 1], su[y - 1][x], su[y + 1][x]);
+      su[y][x] = cmul<T>(csub<T>(sf[y][x], acc), op.dinv[i + n0 * j]);
+    }
+    __syncthreads();
+  }
+  // write the smoothed iterate of the points this tile owns (the last tile also owns the
+  // fine point past the last coarse node when n is odd)
+  {
+    const int oi1 = (I0 + DN_CX >= nc0) ? n0 : 2 * (I0 + DN_CX);
+    const int oj1 = (J0 + DN_CY >= nc1) ? n1 : 2 * (J0 + DN_CY);
+    const int wx = oi1 - 2 * I0, wy = oj1 - 2 * J0;
+    for (int e = tid; e < wx * wy; e += FUSED_THREADS) {
+      int x = e % wx, y = e / wx;
+      int i = 2 * I0 + x, j = 2 * J0 + y;
+      u_out[i + n0 * j] = su[y + HF][x + HF];
+    }
+  }
+  // residual on the restriction region (fine 2I0 .. 2I0 + 2CX), zero outside the grid
+  for (int e = tid; e < RX * RY; e += FUSED_THREADS) {
+    int x = e % RX, y = e / RX;
+    int i = 2 * I0 + x, j = 2 * J0 + y;
+    cx<T> rv = mkc<T>(T(0), T(0));
+    if (i < n0 && j < n1) {
+      int sx = x + HF, sy = y + HF;
+      if (!RBGS || ((i + j) & 1) == 0) {
+        cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
+        rv = RBGS ? mkc<T>(-acc.x, -acc.y) : csub<T>(cscale<T>(T(1) - omega, sf[sy][sx]), acc);
+      }
+    }
+    sr[y][x] = rv;
+  }
+  __syncthreads();
+  // full weighting (1/4, 1/2, 1/4 per axis)
+  for (int e = tid; e < DN_CX * DN_CY; e += FUSED_THREADS) {
+    int cx_ = e % DN_CX, cy = e / DN_CX;
+    int I = I0 + cx_, J = J0 + cy;
+    if (I >= nc0 || J >= nc1) continue;
+    const T w[3] = {T(0.25), T(0.5), T(0.25)};
+    cx<T> acc = mkc<T>(T(0), T(0));
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) acc = cadd<T>(acc, cscale<T>(w[di] * w[dj], sr[2 * cy + dj][2 * cx_ + di]));
+    fc[I + nc0 * J] = acc;
+  }
+}
+
+// ---- up: prolongation + correction + post-smoothing (2D, nu2 = 1), out of place --------------
+template <typename T, bool RBGS, typename TO>
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
+       const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int HU = RBGS ? 2 : 1;                 // halo of the corrected iterate
+  constexpr int UX = UP_FX + 2 * HU, UY = UP_FY + 2 * HU;
+  constexpr int CXN = UX / 2 + 3, CYN = UY / 2 + 3;  // coarse values covering the region
+  __shared__ cx<T> su[UY][UX];
+  __shared__ cx<T> se[CYN][CXN];
+  const int n0 = op.n[0], n1 = op.n[1];
+  const int i0 = blockIdx.x * UP_FX, j0 = blockIdx.y * UP_FY;
+  const int ux0 = i0 - HU, uy0 = j0 - HU;
+  const int cx0 = (ux0 >> 1) - 1, cy0 = (uy0 >> 1) - 1;  // floor division for negatives
+  const int tid = threadIdx.x;
+  for (int e = tid; e < CXN * CYN; e += FUSED_THREADS) {
+    int x = e % CXN, y = e / CXN;
+    int I = cx0 + x, J = cy0 + y;
+    se[y][x] = (I >= 0 && I < nc0 && J >= 0 && J < nc1) ? ec[I + nc0 * J] : mkc<T>(T(0), T(0));
+  }
+  __syncthreads();
+  // corrected iterate u + P e on the tile and its halo
+  for (int e = tid; e < UX * UY; e += FUSED_THREADS) {
+    int x = e % UX, y = e / UX;
+    int i = ux0 + x, j = uy0 + y;
+    cx<T> v = mkc<T>(T(0), T(0));
+    if (i >= 0 && i < n0 && j >= 0 && j < n1) {
+      // per axis: odd fine index -> one coarse node, even -> the two around it (coarse index k
+      // is se[.][k - c0]; indices outside the coarse grid read zero)
+      int ia = (i & 1) ? (i - 1) >> 1 : (i >> 1) - 1, ib = (i & 1) ? ia : (i >> 1);
+      int ja = (j & 1) ? (j - 1) >> 1 : (j >> 1) - 1, jb = (j & 1) ? ja : (j >> 1);
+      T w = ((i & 1) ? T(1) : T(0.5)) * ((j & 1) ? T(1) : T(0.5));
+      cx<T> acc = se[ja - cy0][ia - cx0];
+      if (ib != ia) acc = cadd<T>(acc, se[ja - cy0][ib - cx0]);
+      if (jb != ja) {
+        acc = cadd<T>(acc, se[jb - cy0][ia - cx0]);
+        if (ib != ia) acc = cadd<T>(acc, se[jb - cy0][ib - cx0]);
+      }
+      v = cadd<T>(u_in[i + n0 * j], cscale<T>(w, acc));
+    }
+    su[y][x] = v;
+  }
+  __syncthreads();
+  if (!RBGS) {
+    for (int e = tid; e < UP_FX * UP_FY; e += FUSED_THREADS) {
+      int x = e % UP_FX, y = e / UP_FX;
+      int i = i0 + x, j = j0 + y;
+      if (i >= n0 || j >= n1) continue;
+      int p = i + n0 * j;
+      int sx = x + HU, sy = y + HU;
+      cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
+      cx<T> g = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
+      cx<T> uc = su[sy][sx];
+      u_out[p] = cconv<TO, T>(mkc<T>(fma(omega, g.x, (T(1) - omega) * uc.x), fma(omega, g.y, (T(1) - omega) * uc.y)));
+    }
+  } else {
+    // red points of the tile and one ring around it, from the corrected black values
+    __shared__ cx<T> sred[UP_FY + 2][UP_FX + 2];
+    for (int e = tid; e < (UP_FX + 2) * (UP_FY + 2); e += FUSED_THREADS) {
+      int x = e % (UP_FX + 2), y = e / (UP_FX + 2);
+      int i = i0 - 1 + x, j = j0 - 1 + y;
+      int sx = x + 1, sy = y + 1;  // position in su (HU = 2)
+      cx<T> v = su[sy][sx];
+      if (i >= 0 && i < n0 && j >= 0 && j < n1 && ((i + j) & 1) == 0) {
+        int p = i + n0 * j;
+        cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
+        v = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
+      }
+      sred[y][x] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < UP_FX * UP_FY; e += FUSED_THREADS) {
+      int x = e % UP_FX, y = e / UP_FX;
+      int i = i0 + x, j = j0 + y;
+      if (i >= n0 || j >= n1) continue;
+      int p = i + n0 * j;
+      int sx = x + 1, sy = y + 1;  // position in sred
+      cx<T> v = sred[sy][sx];
+      if ((i + j) & 1) {
+        cx<T> acc = off2d<T>(op, i, j, sred[sy][sx - 1], sred[sy][sx + 1], sred[sy - 1][sx], sred[sy + 1][sx]);
+        v = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
+      }
+      u_out[p] = cconv<TO, T>(v);
+    }
+  }
+}
+
+// ---- tail: the coarsest levels in one block ------------------------------------------------
+constexpr int TAIL_MAX_LEVELS = 12;
+constexpr int TAIL_THREADS = 1024;
+
+template <typename T> struct TailArgs {
+  int count;                        // levels in the tail (the last is the coarsest)
+  OpView<T> op[TAIL_MAX_LEVELS];
+  int n[TAIL_MAX_LEVELS];
+  int off[TAIL_MAX_LEVELS];         // offset (elements) of each level's vectors in shared memory
+  const cx<T>* ainv;
+  int nco;
+  int nu1, nu2, smoother;
+  T omega;
+};
+
+// Level k keeps five vectors in shared memory at base + off[k]: two iterate buffers (which one
+// holds u is bit k of `swap`; a Jacobi sweep writes the other and flips it), f, 1/D and D
+// (the last two copied in once, so that no phase waits on a global load).
+constexpr int TAIL_VECS = 5;
+template <typename T> struct TailMem {
+  cx<T>* base;
+  const TailArgs<T>* a;
+  unsigned swap;
+  __device__ cx<T>* U(int k) const { return base + a->off[k] + (((swap >> k) & 1u) ? a->n[k] : 0); }
+  __device__ cx<T>* W(int k) const { return base + a->off[k] + (((swap >> k) & 1u) ? 0 : a->n[k]); }
+  __device__ cx<T>* F(int k) const { return base + a->off[k] + 2 * a->n[k]; }
+  __device__ cx<T>* DI(int k) const { return base + a->off[k] + 3 * a->n[k]; }
+  __device__ cx<T>* DG(int k) const { return base + a->off[k] + 4 * a->n[k]; }
+};
+
+__device__ __forceinline__ void tail_coords(int p, const int n[3], int& i, int& j, int& l) {
+  i = p % n[0];
+  int q = p / n[0];
+  j = q % n[1];
+  l = q / n[1];
+}
+
+template <typename T, int DIM>
+__device__ void tail_smooth(const TailArgs<T>& a, TailMem<T>& m, int k, bool zero) {
+  const OpView<T>& op = a.op[k];
+  const int n = a.n[k];
+  cx<T>* u = m.U(k);
+  const cx<T>* f = m.F(k);
+  const cx<T>* dinv = m.DI(k);
+  const T om = a.omega;
+  if (a.smoother == HELM_SM_JACOBI) {
+    cx<T>* w = m.W(k);
+    for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
+      cx<T> di = dinv[p];
+      if (zero) {
+        w[p] = cscale<T>(om, cmul<T>(f[p], di));
+        continue;
+      }
+      int i, j, l;
+      tail_coords(p, op.n, i, j, l);
+      cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
+      cx<T> u0 = u[p];
+      w[p] = mkc<T>(fma(om, g.x, (T(1) - om) * u0.x), fma(om, g.y, (T(1) - om) * u0.y));
+    }
+    __syncthreads();
+    m.swap ^= 1u << k;
+  } else {
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
+        int i, j, l;
+        tail_coords(p, op.n, i, j, l);
+        int c = (i + j + l) & 1;
+        if (zero && colour == 0) {
+          u[p] = c == 0 ? cmul<T>(f[p], dinv[p]) : mkc<T>(T(0), T(0));
+          continue;
+        }
+        if (c != colour) continue;
+        u[p] = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), dinv[p]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// linear interpolation weights of fine index x from coarse indices (at most 2)
+template <typename T>
+__device__ __forceinline__ int tail_lin(int x, int nc, int* c, T* w) {
+  if (x & 1) { c[0] = (x - 1) >> 1; w[0] = T(1); return 1; }
+  int m = 0;
+  if ((x >> 1) - 1 >= 0) { c[m] = (x >> 1) - 1; w[m] = T(0.5); ++m; }
+  if ((x >> 1) < nc) { c[m] = x >> 1; w[m] = T(0.5); ++m; }
+  return m;
+}
+
+template <typename T, int DIM, typename TO>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ TailArgs<T> a,
+                                                       const cx<T>* __restrict__ f_in,
+                                                       cx<TO>* __restrict__ u_outg, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ unsigned char tail_smem[];
+  TailMem<T> m{reinterpret_cast<cx<T>*>(tail_smem), &a, 0u};
+  {
+    cx<T>* F0 = m.F(0);
+    for (int p = threadIdx.x; p < a.n[0]; p += TAIL_THREADS) F0[p] = f_in[p];
+    for (int k = 0; k < a.count; ++k) {
+      cx<T>* di = m.DI(k);
+      cx<T>* dg = m.DG(k);
+      for (int p = threadIdx.x; p < a.n[k]; p += TAIL_THREADS) {
+        di[p] = a.op[k].dinv[p];
+        dg[p] = a.op[k].dg[p];
+      }
+    }
+  }
+  __syncthreads();
+  const int last = a.count - 1;
+  // down: smooth, residual, full weighting into the next level's f
+  for (int k = 0; k < last; ++k) {
+    const OpView<T>& op = a.op[k];
+    const int n = a.n[k];
+    if (a.nu1 > 0) {
+      for (int s = 0; s < a.nu1; ++s) tail_smooth<T, DIM>(a, m, k, s == 0);
+      cx<T>* u = m.U(k);
+      cx<T>* w = m.W(k);
+      const cx<T>* f = m.F(k);
+      const cx<T>* dg = m.DG(k);
+      for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
+        int i, j, l;
+        tail_coords(p, op.n, i, j, l);
+        w[p] = csub<T>(f[p], cfma<T>(dg[p], u[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)));
+      }
+    } else {
+      cx<T>* u = m.U(k);
+      cx<T>* w = m.W(k);
+      const cx<T>* f = m.F(k);
+      for (int p = threadIdx.x; p < n; p += TAIL_THREADS) { w[p] = f[p]; u[p] = mkc<T>(T(0), T(0)); }
+    }
+    __syncthreads();
+    const OpView<T>& oc = a.op[k + 1];
+    const cx<T>* r = m.W(k);
+    cx<T>* fc = m.F(k + 1);
+    const T wts[3] = {T(0.25), T(0.5), T(0.25)};
+    for (int q = threadIdx.x; q < a.n[k + 1]; q += TAIL_THREADS) {
+      int I, J, Lz;
+      tail_coords(q, oc.n, I, J, Lz);
+      cx<T> acc = mkc<T>(T(0), T(0));
+      for (int dl = (DIM > 2 ? -1 : 0); dl <= (DIM > 2 ? 1 : 0); ++dl) {
+        int fl = DIM > 2 ? 2 * Lz + 1 + dl : 0;
+        if (fl >= op.n[2]) continue;
+        for (int dj = (DIM > 1 ? -1 : 0); dj <= (DIM > 1 ? 1 : 0); ++dj) {
+          int fj = DIM > 1 ? 2 * J + 1 + dj : 0;
+          if (fj >= op.n[1]) continue;
+          for (int di = -1; di <= 1; ++di) {
+            int fi = 2 * I + 1 + di;
+            if (fi >= op.n[0]) continue;
+            T wt = wts[di + 1] * (DIM > 1 ? wts[dj + 1] : T(1)) * (DIM > 2 ? wts[dl + 1] : T(1));
+            acc = cadd<T>(acc, cscale<T>(wt, r[fi + op.n[0] * (fj + op.n[1] * fl)]));
+          }
+        }
+      }
+      fc[q] = acc;
+    }
+    __syncthreads();
+  }
+  // coarsest: dense inverse, one warp per row
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const cx<T>* fl = m.F(last);
+    cx<T>* ul = m.U(last);
+    for (int row = warp; row < a.nco; row += TAIL_THREADS / 32) {
+      cx<T> acc = mkc<T>(T(0), T(0));
+      for (int c = lane; c < a.nco; c += 32) acc = cfma<T>(a.ainv[row * a.nco + c], fl[c], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) ul[row] = acc;
+    }
+    __syncthreads();
+  }
+  // up: prolongation + correction, post-smoothing
+  for (int k = last - 1; k >= 0; --k) {
+    const OpView<T>& op = a.op[k];
+    const OpView<T>& oc = a.op[k + 1];
+    cx<T>* u = m.U(k);
+    const cx<T>* e = m.U(k + 1);
+    for (int p = threadIdx.x; p < a.n[k]; p += TAIL_THREADS) {
+      int i, j, l;
+      tail_coords(p, op.n, i, j, l);
+      int ci[2], cj[2] = {0, 0}, cl[2] = {0, 0};
+      T wi[2], wj[2] = {T(1), T(1)}, wl[2] = {T(1), T(1)};
+      int ni = tail_lin<T>(i, oc.n[0], ci, wi);
+      int nj = DIM > 1 ? tail_lin<T>(j, oc.n[1], cj, wj) : 1;
+      int nl = DIM > 2 ? tail_lin<T>(l, oc.n[2], cl, wl) : 1;
+      cx<T> acc = mkc<T>(T(0), T(0));
+      for (int c3 = 0; c3 < nl; ++c3)
+        for (int c2 = 0; c2 < nj; ++c2)
+          for (int c1 = 0; c1 < ni; ++c1)
+            acc = cadd<T>(acc, cscale<T>(wi[c1] * wj[c2] * wl[c3], e[ci[c1] + oc.n[0] * (cj[c2] + oc.n[1] * cl[c3])]));
+      u[p] = cadd<T>(u[p], acc);
+    }
+    __syncthreads();
+    for (int s = 0; s < a.nu2; ++s) tail_smooth<T, DIM>(a, m, k, false);
+  }
+  {
+    const cx<T>* u0 = m.U(0);
+    for (int p = threadIdx.x; p < a.n[0]; p += TAIL_THREADS) u_outg[p] = cconv<TO, T>(u0[p]);
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------
+
+// Points handled by the single block: its phases cost a fraction of a microsecond each only while
+// the block's threads have a few points each; FP64 runs at about a sixtieth of the FP32 rate, so
+// its tail stays tiny.
+template <typename T> static long tail_point_budget() { return std::is_same<T, double>::value ? 160 : 2400; }
+constexpr size_t TAIL_SMEM_BUDGET = 200 * 1024;
+
+template <typename T> int tail_first_level(const helm_ctx* c) {
+  int nl = (int)c->lv.size();
+  long pts = c->lv[nl - 1].ntot;
+  size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
+  if (bytes > TAIL_SMEM_BUDGET) return nl;  // the coarsest level alone is too big: no tail
+  int first = nl - 1;
+  while (first > 0 && nl - (first - 1) <= TAIL_MAX_LEVELS) {
+    long np = pts + c->lv[first - 1].ntot;
+    size_t nb = bytes + TAIL_VECS * sizeof(cx<T>) * c->lv[first - 1].ntot;
+    if (np > tail_point_budget<T>() || nb > TAIL_SMEM_BUDGET) break;
+    pts = np;
+    bytes = nb;
+    --first;
+  }
+  return first;
+}
+
+template <typename T, typename TO>
+static helm_status tail_launch(const TailArgs<T>& a, int dim, size_t smem, const cx<T>* f, cx<TO>* out,
+                               const int* skip, cudaStream_t st) {
+  switch (dim) {
+    case 1:
+      HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 1, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tail<T, 1, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+      break;
+    case 2:
+      HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 2, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tail<T, 2, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+      break;
+    default:
+      HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 3, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tail<T, 3, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+  }
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename T>
+helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,
+                        cudaStream_t st) {
+  TailArgs<T> a{};
+  int nl = (int)c->lv.size();
+  a.count = nl - first;
+  int off = 0;
+  for (int k = 0; k < a.count; ++k) {
+    const LevelHost& L = c->lv[first + k];
+    a.op[k] = L.view<T>();
+    a.n[k] = (int)L.ntot;
+    a.off[k] = off;
+    off += TAIL_VECS * (int)L.ntot;
+  }
+  a.ainv = (const cx<T>*)c->coarse_inv;
+  a.nco = c->nco;
+  a.nu1 = c->pc.nu1;
+  a.nu2 = c->pc.nu2;
+  a.smoother = c->pc.smoother;
+  a.omega = (T)c->pc.omega;
+  size_t smem = (size_t)off * sizeof(cx<T>);
+  if (out_f64) return tail_launch<T, double>(a, c->grid.dim, smem, f, (double2*)out, skip, st);
+  return tail_launch<T, T>(a, c->grid.dim, smem, f, (cx<T>*)out, skip, st);
+}
+
+template <typename T>
+void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>* fc, const int* skip, cudaStream_t st) {
+  const LevelHost& F = c->lv[l];
+  const LevelHost& C = c->lv[l + 1];
+  dim3 g((C.n[0] + DN_CX - 1) / DN_CX, (C.n[1] + DN_CY - 1) / DN_CY);
+  if (c->pc.smoother == HELM_SM_RBGS)
+    k_down2d<T, true><<<g, FUSED_THREADS, 0, st>>>(F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
+  else
+    k_down2d<T, false><<<g, FUSED_THREADS, 0, st>>>(F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
+}
+
+template <typename T>
+void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, const cx<T>* f, void* out,
+                bool out_f64, const int* skip, cudaStream_t st) {
+  const LevelHost& F = c->lv[l];
+  const LevelHost& C = c->lv[l + 1];
+  dim3 g((F.n[0] + UP_FX - 1) / UP_FX, (F.n[1] + UP_FY - 1) / UP_FY);
+  OpView<T> v = F.view<T>();
+  T om = (T)c->pc.omega;
+  bool rb = c->pc.smoother == HELM_SM_RBGS;
+  if (out_f64) {
+    if (rb) k_up2d<T, true, double><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
+    else k_up2d<T, false, double><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
+  } else {
+    if (rb) k_up2d<T, true, T><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
+    else k_up2d<T, false, T><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
+  }
+}
+
+template int tail_first_level<float>(const helm_ctx*);
+template int tail_first_level<double>(const helm_ctx*);
+template helm_status tail_vcycle<float>(helm_ctx*, int, const float2*, void*, bool, const int*, cudaStream_t);
+template helm_status tail_vcycle<double>(helm_ctx*, int, const double2*, void*, bool, const int*, cudaStream_t);
+template void fused_down2d<float>(const helm_ctx*, int, const float2*, float2*, float2*, const int*, cudaStream_t);
+template void fused_down2d<double>(const helm_ctx*, int, const double2*, double2*, double2*, const int*, cudaStream_t);
+template void fused_up2d<float>(const helm_ctx*, int, const float2*, const float2*, const float2*, void*, bool, const int*, cudaStream_t);
+template void fused_up2d<double>(const helm_ctx*, int, const double2*, const double2*, const double2*, void*, bool, const int*, cudaStream_t);
+
+}  // namespace helm

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "helm_internal.cuh"
 
@@ -76,6 +77,25 @@ __global__ void k_phi_inject(const double* __restrict__ pf, int f0, int f1, int 
   double v = pf[fi + (long)f0 * (fj + (long)f1 * fl)];
   pc[p] = v;
   if (pc32) pc32[p] = (float)v;
+}
+
+// 1 / D at every point of a level, D = sum_axes a0 - s * phi, computed in FP64 and stored in
+// the multigrid precision (the smoothers multiply instead of dividing).
+template <int DIM>
+__global__ void k_dinv(OpView<double> op, double2* d64, float2* d32, double2* g64, float2* g32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  int l = blockIdx.z;
+  if (i >= op.n[0]) return;
+  long p = i + (long)op.n[0] * (j + (long)op.n[1] * l);
+  double2 d = op.a0[0][i];
+  if (DIM > 1) d = cadd<double>(d, op.a0[1][j]);
+  if (DIM > 2) d = cadd<double>(d, op.a0[2][l]);
+  double ph = op.phi ? op.phi[p] : op.phi0;
+  d = csub<double>(d, cscale<double>(ph, op.s));
+  double2 r = crecip<double>(d);
+  if (d64) { d64[p] = r; g64[p] = d; }
+  if (d32) { d32[p] = cconv<float, double>(r); g32[p] = cconv<float, double>(d); }
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
@@ -215,6 +235,44 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
   return HELM_OK;
 }
 
+// Finds, per axis, the longest run of unknowns around the middle whose Shortley-Weller rows are
+// bitwise identical with am == ap (the uniform interior); rows are copied from the device once.
+static helm_status find_uniform(LevelHost& L, cudaStream_t st) {
+  L.ud = mkc<double>(0.0, 0.0);
+  for (int a = 0; a < 3; ++a) { L.ulo[a] = 1; L.uhi[a] = 0; L.ua[a] = mkc<double>(0.0, 0.0); }
+  bool all = true;
+  double2 ud = mkc<double>(0.0, 0.0);
+  for (int a = 0; a < L.dim; ++a) {
+    int n = L.n[a];
+    std::vector<double2> am(n), a0(n), ap(n);
+    HELM_CUDA(cudaMemcpyAsync(am.data(), L.coef64[a][0], sizeof(double2) * n, cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaMemcpyAsync(a0.data(), L.coef64[a][1], sizeof(double2) * n, cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaMemcpyAsync(ap.data(), L.coef64[a][2], sizeof(double2) * n, cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaStreamSynchronize(st));
+    auto same = [&](int j, int m) {
+      return std::memcmp(&am[j], &am[m], sizeof(double2)) == 0 && std::memcmp(&a0[j], &a0[m], sizeof(double2)) == 0 &&
+             std::memcmp(&ap[j], &ap[m], sizeof(double2)) == 0 && std::memcmp(&am[j], &ap[j], sizeof(double2)) == 0;
+    };
+    int mid = n / 2;
+    if (n < 3 || !same(mid, mid)) { all = false; break; }
+    int lo = mid, hi = mid;
+    while (lo - 1 >= 0 && same(lo - 1, mid)) --lo;
+    while (hi + 1 < n && same(hi + 1, mid)) ++hi;
+    // the row must also read both neighbours inside the grid to use the uniform formula
+    if (lo < 1) lo = 1;
+    if (hi > n - 2) hi = n - 2;
+    if (hi < lo) { all = false; break; }
+    L.ulo[a] = lo;
+    L.uhi[a] = hi;
+    L.ua[a] = am[mid];
+    ud = cadd<double>(ud, a0[mid]);
+  }
+  if (!all)
+    for (int a = 0; a < 3; ++a) { L.ulo[a] = 1; L.uhi[a] = 0; }
+  L.ud = ud;
+  return HELM_OK;
+}
+
 template <typename T> OpView<T> LevelHost::view() const {
   OpView<T> v{};
   for (int a = 0; a < 3; ++a) {
@@ -231,6 +289,18 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.phi = std::is_same<T, double>::value ? (const T*)(const void*)phi64 : (const T*)(const void*)phi32;
   v.phi0 = (T)phi0;
   v.s = mkc<T>((T)s.x, (T)s.y);
+  bool real = s.y == 0.0;
+  for (int a = 0; a < 3; ++a) {
+    v.ulo[a] = a < dim ? ulo[a] : 0;
+    v.uhi[a] = a < dim ? uhi[a] : 0;
+    v.ua[a] = mkc<T>((T)ua[a].x, (T)ua[a].y);
+    if (a < dim && ua[a].y != 0.0) real = false;
+  }
+  v.ud = mkc<T>((T)ud.x, (T)ud.y);
+  if (ud.y != 0.0) real = false;
+  v.uniform_real = real ? 1 : 0;
+  v.dinv = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dinv64 : (const cx<T>*)(const void*)dinv32;
+  v.dg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dg64 : (const cx<T>*)(const void*)dg32;
   return v;
 }
 template OpView<double> LevelHost::view<double>() const;
@@ -240,6 +310,7 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
   LevelHost& H = c->H;
   helm_status s = build_axes(c, H, mkc<double>(1, 0), mkc<double>(1, 0), false, st);
   if (s != HELM_OK) return s;
+  if ((s = find_uniform(H, st)) != HELM_OK) return s;
   c->n = H.ntot;
   H.s = mkc<double>(1.0, 0.0);
   H.phi0 = k->k0 * k->k0;
@@ -268,6 +339,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   {
     LevelHost& L0 = c->lv[0];
     if ((rc = build_axes(c, L0, sc_in, sc_ly, f32, st)) != HELM_OK) return rc;
+    if ((rc = find_uniform(L0, st)) != HELM_OK) return rc;
     L0.s = s;
     L0.phi0 = c->H.phi0;
     L0.phi64 = c->H.phi64;  // same field, shared
@@ -311,12 +383,28 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
                                                           C.phi32, C.n[0], C.n[1], C.n[2]);
     }
     HELM_CUDA(cudaGetLastError());
+    if ((rc = find_uniform(C, st)) != HELM_OK) return rc;
     c->lv.push_back(C);
   }
   // work vectors: level 0 needs one spare buffer (its f and u are the caller's); coarser
-  // levels need u, f and a spare.
+  // levels need u, f and a spare.  Every level gets its reciprocal diagonal.
   for (size_t l = 0; l < c->lv.size(); ++l) {
     LevelHost& L = c->lv[l];
+    if (f32) {
+      if ((rc = ctx_alloc(c, (void**)&L.dinv32, sizeof(float2) * L.ntot)) != HELM_OK) return rc;
+      if ((rc = ctx_alloc(c, (void**)&L.dg32, sizeof(float2) * L.ntot)) != HELM_OK) return rc;
+    } else {
+      if ((rc = ctx_alloc(c, (void**)&L.dinv64, sizeof(double2) * L.ntot)) != HELM_OK) return rc;
+      if ((rc = ctx_alloc(c, (void**)&L.dg64, sizeof(double2) * L.ntot)) != HELM_OK) return rc;
+    }
+    {
+      OpView<double> v = L.view<double>();
+      dim3 g((L.n[0] + 127) / 128, L.n[1], L.n[2]);
+      if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      else if (L.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      else k_dinv<3><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      HELM_CUDA(cudaGetLastError());
+    }
     if ((rc = ctx_alloc(c, &L.w, esz * L.ntot)) != HELM_OK) return rc;
     if (l > 0) {
       if ((rc = ctx_alloc(c, &L.u, esz * L.ntot)) != HELM_OK) return rc;
@@ -359,6 +447,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     set_error("coarsest operator is singular");
     return HELM_ERR_ARG;
   }
+  c->tail_first = f32 ? tail_first_level<float>(c) : tail_first_level<double>(c);
   return HELM_OK;
 }
 

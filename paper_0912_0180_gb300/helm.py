@@ -56,7 +56,7 @@ class Helm:
     or "c128" (FP64 V-cycle).  Vectors are torch complex tensors on the current CUDA device.
     """
 
-    def __init__(self, problem, precond, mg_dtype: str = "c64", stream=None):
+    def __init__(self, problem, precond, mg_dtype: str = "c64", stream=None, fused: bool = True):
         lib = L.load()
         self._lib = lib
         g = L.Grid()
@@ -75,7 +75,8 @@ class Helm:
         pc = L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
                        complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
                        precond.omega, precond.max_levels, precond.coarse_max,
-                       L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128)
+                       L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
+                       0 if fused else L.HELM_PF_UNFUSED)
         h = C.c_void_p()
         _check(lib.helm_create(C.byref(g), C.byref(k), C.byref(pc), C.c_void_p(_stream(stream)), C.byref(h)),
                "helm_create")
@@ -129,12 +130,12 @@ class Helm:
     def solve(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, *, method: int = 0, s: int = 4,
               tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3,
               shadow: Optional[np.ndarray] = None, stream=None, raise_on_error: bool = False,
-              history: bool = False):
+              history: bool = False, host_loop: bool = False):
         """Solve H x = b from x = 0; returns (x, Info).  Krylov statuses (breakdown, cap, NaN) are
         reported in Info; CUDA and argument errors raise."""
         if x is None:
             x = torch.empty(self.n, dtype=torch.complex128, device=b.device)
-        o = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None)
+        o = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None, 1 if host_loop else 0)
         hist = None
         if history:
             hist = torch.full((maxmv,), float("nan"), dtype=torch.float64, device=b.device)
