@@ -180,6 +180,24 @@ helm_status helm_level_shape(const helm_ctx* ctx, int lvl, int* n);
 helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, const helm_solve_opts* opts,
                        helm_solve_info* info, void* stream);
 
+/* r = b - H x and *rel_out = ||r|| / ||b|| (0 when b = 0), FP64, without allocating anything.
+ * The paper has no counterpart: this is the true-residual computation that helm_solve runs
+ * after its Krylov loop, offered to callers that cannot allocate device memory -- processes
+ * whose device memory belongs to another allocator that reserved the device up front, and
+ * latency-critical loops that cannot afford cudaMalloc, which may synchronise the device.
+ * The caller passes every input and output: b, x, r (complex128, N entries) and rel_out (one
+ * double), all DEVICE pointers, 16-byte aligned (rel_out 8), r aliasing neither b nor x.
+ * Its scratch (per-block partial sums and a completion counter) is a file-scope static
+ * device array of 64 KiB + 256 B that every device which loads libhelm.so keeps until the
+ * process exits; it bounds N to at most 4,194,304 unknowns (HELM_ERR_ARG beyond).
+ * The first call on each device looks up that array's device address with the device
+ * current (cudaGetSymbolAddress); make this first call before any stream capture.
+ * Every call shares the one array and zeroes its counter on `stream` before the kernel:
+ * calls whose kernels overlap on the GPU (two streams, or two host threads) race and give
+ * wrong results; serialise them.  Asynchronous: *rel_out is valid once `stream` reaches it. */
+helm_status helm_residual_noalloc(helm_ctx* ctx, const void* b, const void* x, void* r,
+                                  double* rel_out, void* stream);
+
 /* Releases everything the context holds (synchronises the device first).  NULL is a no-op. */
 void helm_destroy(helm_ctx* ctx);
 

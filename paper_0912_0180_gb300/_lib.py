@@ -72,6 +72,8 @@ def load() -> C.CDLL:
     lib.helm_level_op.restype = ip
     lib.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.helm_solve.restype = ip
+    lib.helm_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.helm_residual_noalloc.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_status_str.argtypes = [ip]
