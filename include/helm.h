@@ -95,8 +95,9 @@ typedef struct {
 } helm_precond;
 
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
- * same arithmetic as the default fused kernels; for testing the fusion) */
-enum { HELM_PF_UNFUSED = 1 };
+ * same arithmetic as the default fused kernels; for testing the fusion); HELM_PF_NO_PDL
+ * launches the solve-path kernels without programmatic dependent launch (same kernels) */
+enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2 };
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
  * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;

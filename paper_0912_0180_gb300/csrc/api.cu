@@ -10,6 +10,14 @@
 namespace helm {
 
 static thread_local std::string g_last_error;
+thread_local bool g_use_pdl = true;
+
+// Sets the launch mode of the solve-path kernels for the calls made on this context.
+struct PdlScope {
+  bool saved;
+  explicit PdlScope(const helm_ctx* c) : saved(g_use_pdl) { g_use_pdl = !(c->pc.flags & HELM_PF_NO_PDL); }
+  ~PdlScope() { g_use_pdl = saved; }
+};
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -63,7 +71,7 @@ static helm_status check_precond(const helm_precond* p) {
   if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
   if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
   if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
-  if (p->flags & ~HELM_PF_UNFUSED) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
+  if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
   if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {
     set_error("non-finite preconditioner parameter");
     return HELM_ERR_ARG;
@@ -139,12 +147,14 @@ helm_status helm_apply(helm_ctx* c, helm_dtype dtype, const void* x, void* y, vo
   if (!c || !x || !y || x == y) { set_error("helm_apply: NULL or aliased arguments"); return HELM_ERR_ARG; }
   if (dtype != HELM_C64 && dtype != HELM_C128) { set_error("helm_apply: dtype"); return HELM_ERR_ARG; }
   if (!aligned(x, dtype == HELM_C64 ? 8 : 16) || !aligned(y, 16)) { set_error("helm_apply: misaligned"); return HELM_ERR_ARG; }
+  PdlScope pdl(c);
   return h_apply(c, dtype == HELM_C64, x, (double2*)y, (cudaStream_t)stream);
 }
 
 helm_status helm_vcycle(helm_ctx* c, const void* r, void* z, void* stream) {
   if (!c || !r || !z || r == z) { set_error("helm_vcycle: NULL or aliased arguments"); return HELM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
+  PdlScope pdl(c);
   bool f32 = c->pc.mg_dtype == HELM_C64;
   if (!aligned(r, 16) || !aligned(z, f32 ? 8 : 16)) { set_error("helm_vcycle: misaligned"); return HELM_ERR_ARG; }
   if (c->pc.kind == HELM_PC_NONE) {
@@ -163,6 +173,7 @@ helm_status helm_vcycle(helm_ctx* c, const void* r, void* z, void* stream) {
 helm_status helm_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, void* out, int count,
                           void* stream) {
   if (!c) { set_error("ctx is NULL"); return HELM_ERR_ARG; }
+  PdlScope pdl(c);
   return mg_level_op(c, op, lvl, a, b, out, count, (cudaStream_t)stream);
 }
 
@@ -174,6 +185,7 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opt
   if (o->method != HELM_BICGSTAB && o->method != HELM_IDR) { set_error("method"); return HELM_ERR_ARG; }
   if (o->method == HELM_IDR && (o->s < 1 || o->s > 8 || !o->shadow)) { set_error("IDR needs 1 <= s <= 8 and a shadow array"); return HELM_ERR_ARG; }
   if (!(o->tol > 0.0) || o->maxmv < 1 || o->max_restarts < 0) { set_error("tol / maxmv / max_restarts"); return HELM_ERR_ARG; }
+  PdlScope pdl(c);
   helm_status s = krylov_solve(c, (const double2*)b, (double2*)x, o, info, (cudaStream_t)stream);
   if (info) info->status = s;
   return s;

@@ -167,6 +167,38 @@ helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_s
                          helm_solve_info* info, cudaStream_t st);
 void krylov_free(helm_ctx* c);
 
+// Programmatic dependent launch: kernels on the solve path are launched so that the next kernel's
+// blocks may be scheduled while the previous one drains; every such kernel starts with
+// pdl_entry(), which waits for the previous kernel's completion and memory (griddepcontrol.wait)
+// before anything is read, then lets its own dependent launch proceed.  A kernel launched
+// without the attribute passes the wait at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// process-wide switch read by launch_pdl (set per call chain by the entry points)
+extern thread_local bool g_use_pdl;
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  if (!g_use_pdl) {
+    kernel<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline int grid_blocks(long work, int threads, int cap) {
   long b = (work + threads - 1) / threads;
   if (b < 1) b = 1;

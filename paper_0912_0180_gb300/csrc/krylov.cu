@@ -158,6 +158,7 @@ template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i,
 __global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* r, double2* rh,
                         double2* p, double2* v, void* rmg, int mg32, long n, int first,
                         double2* partials) {
+  pdl_entry();
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
     double2 ri = first ? b[i] : r[i];
@@ -191,6 +192,7 @@ __global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* 
 template <int DIM>
 __global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __restrict__ b,
                            const double2* __restrict__ x, double2* __restrict__ r, long n, double2* partials) {
+  pdl_entry();
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
     double2 ri = csub<double>(b[p], op_row<double, double, DIM>(H, x, i, j, l, p));
@@ -207,6 +209,7 @@ __global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __re
 // executions and, as a guard against a logic error, stops a loop that has run more bodies than
 // the matvec cap allows (status HELM_ERR_TIMEOUT) -- every live body costs at least one matvec.
 __global__ void k_set_cond(cudaGraphConditionalHandle h, KrylovState* S, int in_body) {
+  pdl_entry();
   if (in_body) {
     S->loops += 1;
     if (!S->done && S->loops > S->maxmv + 16) finish(S, HELM_ERR_TIMEOUT);
@@ -220,6 +223,7 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, KrylovState* S, int in_
 template <typename TM>
 __global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ p,
                          const double2* __restrict__ v, void* pmg, long n) {
+  pdl_entry();
   if (S->done) return;
   double2 beta = S->beta, om = S->omega;
   GRID_LOOP(i, n) {
@@ -233,6 +237,7 @@ __global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, do
 template <int DIM>
 __global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __restrict__ ph,
                          const double2* __restrict__ rh, double2* __restrict__ v, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -255,6 +260,7 @@ __global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __rest
 template <typename TM>
 __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const double2* __restrict__ v,
                          double2* __restrict__ sv, void* smg, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 al = S->alpha;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
@@ -276,6 +282,7 @@ __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const do
 
 // x += alpha p^ after a half-step exit.
 __global__ void k_bicg_xhalf(KrylovState* S, const double2* __restrict__ ph, double2* __restrict__ x, long n) {
+  pdl_entry();
   if (!S->half) return;
   double2 al = S->alpha;
   GRID_LOOP(i, n) x[i] = cfma<double>(al, ph[i], x[i]);
@@ -285,6 +292,7 @@ __global__ void k_bicg_xhalf(KrylovState* S, const double2* __restrict__ ph, dou
 template <int DIM>
 __global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __restrict__ sh,
                          const double2* __restrict__ sv, double2* __restrict__ t, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -308,6 +316,7 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
                           const double2* __restrict__ sv, const double2* __restrict__ t,
                           const double2* __restrict__ rh, double2* __restrict__ x, double2* __restrict__ r,
                           long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 al = S->alpha, om = S->omega;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
@@ -348,6 +357,7 @@ __device__ __forceinline__ void proj_acc(const double2* __restrict__ P, long n, 
 template <int DIM>
 __global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                            const double2* __restrict__ r, double2* __restrict__ t, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -372,6 +382,7 @@ template <typename TM>
 __global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict__ z, const double2* __restrict__ t,
                              double2* __restrict__ dX, double2* __restrict__ dR, double2* __restrict__ x,
                              double2* __restrict__ r, void* rmg, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 om = S->omega;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
@@ -401,6 +412,7 @@ __global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict
 template <int S_>
 __global__ void k_idr_proj(KrylovState* S, const double2* __restrict__ P, const double2* __restrict__ y,
                            int col, long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   double2 acc[S_];
 #pragma unroll
@@ -417,6 +429,7 @@ __global__ void k_idr_proj(KrylovState* S, const double2* __restrict__ P, const 
 
 // c = M^{-1} m (s x s, Gaussian elimination with partial pivoting, one thread).
 __global__ void k_idr_small(KrylovState* S) {
+  pdl_entry();
   if (S->done || threadIdx.x) return;
   if (S->matvecs >= S->maxmv) { finish(S, HELM_ERR_MAXIT); return; }
   int s = S->s;
@@ -451,6 +464,7 @@ __global__ void k_idr_small(KrylovState* S) {
 template <typename TM, int S_>
 __global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, const double2* __restrict__ r,
                         double2* __restrict__ q, void* vmg, long n) {
+  pdl_entry();
   if (S->done) return;
   double2 c[S_];
 #pragma unroll
@@ -469,6 +483,7 @@ template <int DIM>
 __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                          const double2* __restrict__ r, const double2* __restrict__ q,
                          double2* __restrict__ t, long n, double2* partials) {
+  pdl_entry();
   if (S->done || S->k != 0) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -489,6 +504,7 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __rest
 // dX_oldest = -dX c + omega z (in place: each entry reads its row of dX before writing).
 template <int S_>
 __global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const double2* __restrict__ z, long n) {
+  pdl_entry();
   if (S->done) return;
   double2 c[S_];
 #pragma unroll
@@ -507,6 +523,7 @@ __global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const d
 template <int DIM>
 __global__ void k_idr_tk(const KrylovState* S, OpView<double> H, const double2* __restrict__ dX,
                          double2* __restrict__ t, long n) {
+  pdl_entry();
   if (S->done || S->k == 0) return;
   const double2* d = dX + S->oldest * n;
   ROW_LOOP(H, i, j, l, p) {
@@ -521,6 +538,7 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
                           const double2* __restrict__ dX, const double2* __restrict__ q,
                           const double2* __restrict__ t, double2* __restrict__ x, double2* __restrict__ r,
                           long n, double2* partials) {
+  pdl_entry();
   if (S->done) return;
   int o = S->oldest;
   bool first = S->k == 0;
@@ -558,6 +576,7 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
 // Modified Gram-Schmidt on the shadow vectors: h = P_i^H P_j ...
 __global__ void k_dot1(KrylovState* S, const double2* __restrict__ a, const double2* __restrict__ b,
                        long n, double2* partials, double2* out) {
+  pdl_entry();
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) acc[0] = cadd<double>(acc[0], cmulc<double>(a[i], b[i]));
   double2 tot[1];
@@ -566,6 +585,7 @@ __global__ void k_dot1(KrylovState* S, const double2* __restrict__ a, const doub
 }
 // ... P_j -= h P_i  (mode 0)  or  P_j /= sqrt(h)  (mode 1, h = P_j^H P_j)
 __global__ void k_mgs_upd(double2* __restrict__ pj, const double2* __restrict__ pi, const double2* h, int mode, long n) {
+  pdl_entry();
   double2 hv = *h;
   double sc = mode ? 1.0 / sqrt(hv.x) : 0.0;
   GRID_LOOP(i, n) {
@@ -631,22 +651,22 @@ static helm_status enqueue_bicg_iter(const Ctx& k, cudaStream_t st) {
   void* scopy = f32 ? w->smg : nullptr;
   const void* pin = f32 ? (const void*)w->pmg : (const void*)w->p;
   const void* sin_ = f32 ? (const void*)w->smg : (const void*)w->sv;
-  k_bicg_p<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->p, w->v, pcopy, k.n);
+  launch_pdl(k_bicg_p<TM>, dim3(k.G), dim3(KT), 0, st, w->st, w->r, w->p, w->v, pcopy, k.n);
   const double2* ph = w->p;
   if (k.pc) {
     if ((s = precondition<TM>(k, pin, w->ph, st)) != HELM_OK) return s;
     ph = w->ph;
   }
-  k_bicg_v<DIM><<<k.G, KT, 0, st>>>(w->st, H, ph, w->rh, w->v, k.n, w->partials);
-  k_bicg_s<TM><<<k.G, KT, 0, st>>>(w->st, w->r, w->v, w->sv, scopy, k.n, w->partials);
-  k_bicg_xhalf<<<k.G, KT, 0, st>>>(w->st, ph, w->x, k.n);
+  launch_pdl(k_bicg_v<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, ph, w->rh, w->v, k.n, w->partials);
+  launch_pdl(k_bicg_s<TM>, dim3(k.G), dim3(KT), 0, st, w->st, w->r, w->v, w->sv, scopy, k.n, w->partials);
+  launch_pdl(k_bicg_xhalf, dim3(k.G), dim3(KT), 0, st, w->st, ph, w->x, k.n);
   const double2* sh = w->sv;
   if (k.pc) {
     if ((s = precondition<TM>(k, sin_, w->sh, st)) != HELM_OK) return s;
     sh = w->sh;
   }
-  k_bicg_t<DIM><<<k.G, KT, 0, st>>>(w->st, H, sh, w->sv, w->t, k.n, w->partials);
-  k_bicg_xr<<<k.G, KT, 0, st>>>(w->st, ph, sh, w->sv, w->t, w->rh, w->x, w->r, k.n, w->partials);
+  launch_pdl(k_bicg_t<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, sh, w->sv, w->t, k.n, w->partials);
+  launch_pdl(k_bicg_xr, dim3(k.G), dim3(KT), 0, st, w->st, ph, sh, w->sv, w->t, w->rh, w->x, w->r, k.n, w->partials);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
@@ -656,18 +676,18 @@ static helm_status enqueue_idr_step(const Ctx& k, cudaStream_t st) {
   Workspace* w = k.w;
   OpView<double> H = k.c->H.view<double>();
   helm_status s;
-  k_idr_small<<<1, 32, 0, st>>>(w->st);
+  launch_pdl(k_idr_small, dim3(1), dim3(32), 0, st, w->st);
   void* vin = w->pmg;  // v in multigrid precision (always materialised)
-  k_idr_v<TM, S_><<<k.G, KT, 0, st>>>(w->st, w->dR, w->r, w->q, vin, k.n);
+  launch_pdl(k_idr_v<TM, S_>, dim3(k.G), dim3(KT), 0, st, w->st, w->dR, w->r, w->q, vin, k.n);
   const double2* z = (const double2*)vin;  // identity preconditioner: TM is double
   if (k.pc) {
     if ((s = precondition<TM>(k, vin, w->ph, st)) != HELM_OK) return s;
     z = w->ph;
   }
-  k_idr_t0<DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->q, w->t, k.n, w->partials);
-  k_idr_dx<S_><<<k.G, KT, 0, st>>>(w->st, w->dX, z, k.n);
-  k_idr_tk<DIM><<<k.G, KT, 0, st>>>(w->st, H, w->dX, w->t, k.n);
-  k_idr_upd<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR, w->dX, w->q, w->t, w->x, w->r, k.n, w->partials);
+  launch_pdl(k_idr_t0<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, z, w->r, w->q, w->t, k.n, w->partials);
+  launch_pdl(k_idr_dx<S_>, dim3(k.G), dim3(KT), 0, st, w->st, w->dX, z, k.n);
+  launch_pdl(k_idr_tk<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, w->dX, w->t, k.n);
+  launch_pdl(k_idr_upd<S_>, dim3(k.G), dim3(KT), 0, st, w->st, w->P, w->dR, w->dX, w->q, w->t, w->x, w->r, k.n, w->partials);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
@@ -683,11 +703,11 @@ static helm_status enqueue_idr_init(const Ctx& k, cudaStream_t st) {
       if ((s = precondition<TM>(k, w->pmg, w->ph, st)) != HELM_OK) return s;
       z = w->ph;
     }
-    k_idr_mr_t<DIM><<<k.G, KT, 0, st>>>(w->st, H, z, w->r, w->t, k.n, w->partials);
-    k_idr_mr_upd<TM><<<k.G, KT, 0, st>>>(w->st, kc, z, w->t, w->dX, w->dR, w->x, w->r, w->pmg, k.n, w->partials);
+    launch_pdl(k_idr_mr_t<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, z, w->r, w->t, k.n, w->partials);
+    launch_pdl(k_idr_mr_upd<TM>, dim3(k.G), dim3(KT), 0, st, w->st, kc, z, w->t, w->dX, w->dR, w->x, w->r, w->pmg, k.n, w->partials);
   }
-  for (int j = 0; j < S_; ++j) k_idr_proj<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->dR + (long)j * k.n, j, k.n, w->partials);
-  k_idr_proj<S_><<<k.G, KT, 0, st>>>(w->st, w->P, w->r, -1, k.n, w->partials);
+  for (int j = 0; j < S_; ++j) launch_pdl(k_idr_proj<S_>, dim3(k.G), dim3(KT), 0, st, w->st, w->P, w->dR + (long)j * k.n, j, k.n, w->partials);
+  launch_pdl(k_idr_proj<S_>, dim3(k.G), dim3(KT), 0, st, w->st, w->P, w->r, -1, k.n, w->partials);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
@@ -787,7 +807,7 @@ static helm_status build_loop(const Ctx& k, int method, int s) {
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); return cuda_check(e, "cudaStreamBeginCaptureToGraph"); }
   helm_status s2 = enqueue_body_any<TM>(k, method, s, cs);
-  k_set_cond<<<1, 1, 0, cs>>>(h, w->st, 1);
+  launch_pdl(k_set_cond, dim3(1), dim3(1), 0, cs, h, w->st, 1);
   cudaGraph_t out = nullptr;
   e = cudaStreamEndCapture(cs, &out);
   cudaStreamDestroy(cs);

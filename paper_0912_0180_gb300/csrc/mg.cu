@@ -33,6 +33,7 @@ template <int DIM> static void cfg(const int n[3], dim3& g, dim3& b) {
 template <typename T, int DIM>
 __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ f,
                            cx<T>* __restrict__ y, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
   cx<T> v = op_row<T, T, DIM>(op, x, i, j, l, p);
@@ -45,6 +46,7 @@ __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T
 template <typename T, int DIM>
 __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ un, T omega, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
   cx<T> di = op.dinv[p];
@@ -63,6 +65,7 @@ __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
 template <typename T, int DIM>
 __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restrict__ f, int colour,
                        int zero_guess, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
   int c = (i + j + l) & 1;
@@ -81,6 +84,7 @@ struct Dims { int f[3]; int c[3]; };
 // axis with weights 1/4, 1/2, 1/4 (tensor product); indices past the grid are Dirichlet.
 template <typename T, int DIM>
 __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restrict__ fc, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -122,6 +126,7 @@ __device__ __forceinline__ int interp1(int i, int nc, int* ci, float* w) {
 template <typename T, int DIM>
 __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restrict__ u, int overwrite,
                           const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -147,6 +152,7 @@ __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restric
 template <typename T>
 __global__ void k_coarse(const cx<T>* __restrict__ Ainv, int n, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ z, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -164,11 +170,13 @@ __global__ void k_coarse(const cx<T>* __restrict__ Ainv, int n, const cx<T>* __r
 // y = H x in FP64 arithmetic, x complex128 or complex64.
 template <typename TX, int DIM>
 __global__ void k_h_apply(OpView<double> op, const cx<TX>* __restrict__ x, double2* __restrict__ y) {
+  pdl_entry();
   POINT_INDEX(op);
   y[p] = op_row<double, TX, DIM>(op, x, i, j, l, p);
 }
 
 __global__ void k_widen(const float2* __restrict__ a, double2* __restrict__ b, long n, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (p < n) b[p] = cconv<double, float>(a[p]);
@@ -177,7 +185,7 @@ __global__ void k_widen(const float2* __restrict__ a, double2* __restrict__ b, l
 // ---- host side -------------------------------------------------------------------------
 
 static void widen_c64(const helm_ctx*, const float2* a, double2* b, long n, const int* skip, cudaStream_t st) {
-  k_widen<<<(int)((n + 255) / 256), 256, 0, st>>>(a, b, n, skip);
+  launch_pdl(k_widen, dim3((int)((n + 255) / 256)), dim3(256), 0, st, a, b, n, skip);
 }
 
 template <typename T>
@@ -186,25 +194,25 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
 template <typename T, int DIM> struct Launch {
   static void apply(const LevelHost& L, const cx<T>* x, const cx<T>* f, cx<T>* y, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
-    k_mg_apply<T, DIM><<<g, b, 0, st>>>(L.view<T>(), x, f, y, skip);
+    launch_pdl(k_mg_apply<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
   }
   static void jacobi(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* un, T omega, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
-    k_jacobi<T, DIM><<<g, b, 0, st>>>(L.view<T>(), u, f, un, omega, skip);
+    launch_pdl(k_jacobi<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, skip);
   }
   static void rbgs(const LevelHost& L, cx<T>* u, const cx<T>* f, int colour, int zero, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
-    k_rbgs<T, DIM><<<g, b, 0, st>>>(L.view<T>(), u, f, colour, zero, skip);
+    launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, skip);
   }
   static void restrict_(const LevelHost& F, const LevelHost& C, const cx<T>* r, cx<T>* fc, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; }
     dim3 g, b; cfg<DIM>(C.n, g, b);
-    k_restrict<T, DIM><<<g, b, 0, st>>>(d, r, fc, skip);
+    launch_pdl(k_restrict<T, DIM>, dim3(g), dim3(b), 0, st, d, r, fc, skip);
   }
   static void prolong(const LevelHost& F, const LevelHost& C, const cx<T>* ec, cx<T>* u, int overwrite, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; }
     dim3 g, b; cfg<DIM>(F.n, g, b);
-    k_prolong<T, DIM><<<g, b, 0, st>>>(d, ec, u, overwrite, skip);
+    launch_pdl(k_prolong<T, DIM>, dim3(g), dim3(b), 0, st, d, ec, u, overwrite, skip);
   }
 };
 
@@ -245,7 +253,7 @@ static void coarse_solve(helm_ctx* c, const cx<T>* f, cx<T>* z, const int* skip,
   int n = c->nco;
   int thr = 256;
   int blocks = (n * 32 + thr - 1) / thr;
-  k_coarse<T><<<blocks, thr, 0, st>>>((const cx<T>*)c->coarse_inv, n, f, z, skip);
+  launch_pdl(k_coarse<T>, dim3(blocks), dim3(thr), 0, st, (const cx<T>*)c->coarse_inv, n, f, z, skip);
 }
 
 // Smoothing sweeps on level L; buffers b[2] with *cur the index holding u.  zero: start from u = 0.
@@ -381,16 +389,16 @@ helm_status h_apply(helm_ctx* c, bool x_is_f32, const void* x, double2* y, cudaS
   dim3 g, b;
   switch (H.dim) {
     case 1: cfg<1>(H.n, g, b);
-      if (x_is_f32) k_h_apply<float, 1><<<g, b, 0, st>>>(v, (const float2*)x, y);
-      else k_h_apply<double, 1><<<g, b, 0, st>>>(v, (const double2*)x, y);
+      if (x_is_f32) launch_pdl(k_h_apply<float, 1>, dim3(g), dim3(b), 0, st, v, (const float2*)x, y);
+      else launch_pdl(k_h_apply<double, 1>, dim3(g), dim3(b), 0, st, v, (const double2*)x, y);
       break;
     case 2: cfg<2>(H.n, g, b);
-      if (x_is_f32) k_h_apply<float, 2><<<g, b, 0, st>>>(v, (const float2*)x, y);
-      else k_h_apply<double, 2><<<g, b, 0, st>>>(v, (const double2*)x, y);
+      if (x_is_f32) launch_pdl(k_h_apply<float, 2>, dim3(g), dim3(b), 0, st, v, (const float2*)x, y);
+      else launch_pdl(k_h_apply<double, 2>, dim3(g), dim3(b), 0, st, v, (const double2*)x, y);
       break;
     default: cfg<3>(H.n, g, b);
-      if (x_is_f32) k_h_apply<float, 3><<<g, b, 0, st>>>(v, (const float2*)x, y);
-      else k_h_apply<double, 3><<<g, b, 0, st>>>(v, (const double2*)x, y);
+      if (x_is_f32) launch_pdl(k_h_apply<float, 3>, dim3(g), dim3(b), 0, st, v, (const float2*)x, y);
+      else launch_pdl(k_h_apply<double, 3>, dim3(g), dim3(b), 0, st, v, (const double2*)x, y);
   }
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;

@@ -34,6 +34,7 @@ template <typename T, bool RBGS>
 __global__ void __launch_bounds__(FUSED_THREADS)
 k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
          cx<T>* __restrict__ fc, T omega, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   constexpr int HF = RBGS ? 2 : 1;
   constexpr int RX = 2 * DN_CX + 1, RY = 2 * DN_CY + 1;  // residual region
@@ -45,19 +46,36 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
   const int I0 = blockIdx.x * DN_CX, J0 = blockIdx.y * DN_CY;
   const int fx0 = 2 * I0 - HF, fy0 = 2 * J0 - HF;  // origin of the staged region
   const int tid = threadIdx.x;
-  // stage f; Jacobi: u = omega D^-1 f; RB-GS: red u = D^-1 f, black 0
-  for (int e = tid; e < FX * FY; e += FUSED_THREADS) {
-    int x = e % FX, y = e / FX;
-    int i = fx0 + x, j = fy0 + y;
-    cx<T> fv = mkc<T>(T(0), T(0)), uv = mkc<T>(T(0), T(0));
-    if (i >= 0 && i < n0 && j >= 0 && j < n1) {
-      int p = i + n0 * j;
-      fv = f[p];
-      if (!RBGS) uv = cscale<T>(omega, cmul<T>(fv, op.dinv[p]));
-      else if (((i + j) & 1) == 0) uv = cmul<T>(fv, op.dinv[p]);
+  // stage f; Jacobi: u = omega D^-1 f; RB-GS: red u = D^-1 f, black 0.  All loads of a
+  // thread are issued before any is used.
+  {
+    constexpr int NS = (FX * FY + FUSED_THREADS - 1) / FUSED_THREADS;
+    cx<T> fv[NS], dv[NS];
+#pragma unroll
+    for (int it = 0; it < NS; ++it) {
+      int e = tid + it * FUSED_THREADS;
+      int x = e % FX, y = e / FX;
+      int i = fx0 + x, j = fy0 + y;
+      fv[it] = mkc<T>(T(0), T(0));
+      dv[it] = mkc<T>(T(0), T(0));
+      if (e < FX * FY && i >= 0 && i < n0 && j >= 0 && j < n1) {
+        int p = i + n0 * j;
+        fv[it] = f[p];
+        dv[it] = op.dinv[p];
+      }
     }
-    sf[y][x] = fv;
-    su[y][x] = uv;
+#pragma unroll
+    for (int it = 0; it < NS; ++it) {
+      int e = tid + it * FUSED_THREADS;
+      if (e >= FX * FY) break;
+      int x = e % FX, y = e / FX;
+      int i = fx0 + x, j = fy0 + y;
+      cx<T> uv = mkc<T>(T(0), T(0));
+      if (!RBGS) uv = cscale<T>(omega, cmul<T>(fv[it], dv[it]));
+      else if (((i + j) & 1) == 0) uv = cmul<T>(fv[it], dv[it]);
+      sf[y][x] = fv[it];
+      su[y][x] = uv;
+    }
   }
   __syncthreads();
   if (RBGS) {  // black points of the inner region from the red values just computed
@@ -117,6 +135,7 @@ template <typename T, bool RBGS, typename TO>
 __global__ void __launch_bounds__(FUSED_THREADS)
 k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
        const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   constexpr int HU = RBGS ? 2 : 1;                 // halo of the corrected iterate
   constexpr int UX = UP_FX + 2 * HU, UY = UP_FY + 2 * HU;
@@ -134,8 +153,19 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
     se[y][x] = (I >= 0 && I < nc0 && J >= 0 && J < nc1) ? ec[I + nc0 * J] : mkc<T>(T(0), T(0));
   }
   __syncthreads();
-  // corrected iterate u + P e on the tile and its halo
-  for (int e = tid; e < UX * UY; e += FUSED_THREADS) {
+  // corrected iterate u + P e on the tile and its halo (u loads issued up front)
+  constexpr int NU = (UX * UY + FUSED_THREADS - 1) / FUSED_THREADS;
+  cx<T> uold[NU];
+#pragma unroll
+  for (int it = 0; it < NU; ++it) {
+    int e = tid + it * FUSED_THREADS;
+    int i = ux0 + e % UX, j = uy0 + e / UX;
+    uold[it] = (e < UX * UY && i >= 0 && i < n0 && j >= 0 && j < n1) ? u_in[i + n0 * j] : mkc<T>(T(0), T(0));
+  }
+#pragma unroll
+  for (int it = 0; it < NU; ++it) {
+    int e = tid + it * FUSED_THREADS;
+    if (e >= UX * UY) break;
     int x = e % UX, y = e / UX;
     int i = ux0 + x, j = uy0 + y;
     cx<T> v = mkc<T>(T(0), T(0));
@@ -151,7 +181,7 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
         acc = cadd<T>(acc, se[jb - cy0][ia - cx0]);
         if (ib != ia) acc = cadd<T>(acc, se[jb - cy0][ib - cx0]);
       }
-      v = cadd<T>(u_in[i + n0 * j], cscale<T>(w, acc));
+      v = cadd<T>(uold[it], cscale<T>(w, acc));
     }
     su[y][x] = v;
   }
@@ -293,6 +323,7 @@ template <typename T, int DIM, typename TO>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ TailArgs<T> a,
                                                        const cx<T>* __restrict__ f_in,
                                                        cx<TO>* __restrict__ u_outg, const int* skip) {
+  pdl_entry();
   if (skip && *skip) return;
   extern __shared__ unsigned char tail_smem[];
   TailMem<T> m{reinterpret_cast<cx<T>*>(tail_smem), &a, 0u};
@@ -435,15 +466,15 @@ static helm_status tail_launch(const TailArgs<T>& a, int dim, size_t smem, const
   switch (dim) {
     case 1:
       HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 1, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tail<T, 1, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+      launch_pdl(k_tail<T, 1, TO>, dim3(1), dim3(TAIL_THREADS), smem, st, a, f, out, skip);
       break;
     case 2:
       HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 2, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tail<T, 2, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+      launch_pdl(k_tail<T, 2, TO>, dim3(1), dim3(TAIL_THREADS), smem, st, a, f, out, skip);
       break;
     default:
       HELM_CUDA(cudaFuncSetAttribute(k_tail<T, 3, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tail<T, 3, TO><<<1, TAIL_THREADS, smem, st>>>(a, f, out, skip);
+      launch_pdl(k_tail<T, 3, TO>, dim3(1), dim3(TAIL_THREADS), smem, st, a, f, out, skip);
   }
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
@@ -480,9 +511,9 @@ void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>*
   const LevelHost& C = c->lv[l + 1];
   dim3 g((C.n[0] + DN_CX - 1) / DN_CX, (C.n[1] + DN_CY - 1) / DN_CY);
   if (c->pc.smoother == HELM_SM_RBGS)
-    k_down2d<T, true><<<g, FUSED_THREADS, 0, st>>>(F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
+    launch_pdl(k_down2d<T, true>, dim3(g), dim3(FUSED_THREADS), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
   else
-    k_down2d<T, false><<<g, FUSED_THREADS, 0, st>>>(F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
+    launch_pdl(k_down2d<T, false>, dim3(g), dim3(FUSED_THREADS), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
 }
 
 template <typename T>
@@ -495,11 +526,11 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
   T om = (T)c->pc.omega;
   bool rb = c->pc.smoother == HELM_SM_RBGS;
   if (out_f64) {
-    if (rb) k_up2d<T, true, double><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
-    else k_up2d<T, false, double><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
+    if (rb) launch_pdl(k_up2d<T, true, double>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
+    else launch_pdl(k_up2d<T, false, double>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
   } else {
-    if (rb) k_up2d<T, true, T><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
-    else k_up2d<T, false, T><<<g, FUSED_THREADS, 0, st>>>(v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
+    if (rb) launch_pdl(k_up2d<T, true, T>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
+    else launch_pdl(k_up2d<T, false, T>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
   }
 }
 
