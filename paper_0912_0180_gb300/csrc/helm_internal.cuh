@@ -65,7 +65,9 @@ template <typename T> struct OpView {
   cx<T> ua[3];
   cx<T> ud;
   int uniform_real;
-  const cx<T>* dinv;  // 1 / diagonal at every point (multigrid levels; nullptr otherwise)
+  int uniform_iso;    // every axis has the same uniform coefficient (square interior cells)
+  const cx<T>* dinv;  // omega/D (damped Jacobi) or 1/D (Gauss-Seidel) at every point of a
+                      // multigrid level; nullptr otherwise
   const cx<T>* dg;    // the diagonal itself (multigrid levels; nullptr otherwise)
 };
 

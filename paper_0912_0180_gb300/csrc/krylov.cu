@@ -225,9 +225,10 @@ __global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, do
                          const double2* __restrict__ v, void* pmg, long n) {
   pdl_entry();
   if (S->done) return;
-  double2 beta = S->beta, om = S->omega;
+  const double2 beta = S->beta;
+  const double2 mbw = cmul<double>(mkc<double>(-beta.x, -beta.y), S->omega);  // -beta omega
   GRID_LOOP(i, n) {
-    double2 pi = cadd<double>(r[i], cmul<double>(beta, csub<double>(p[i], cmul<double>(om, v[i]))));
+    double2 pi = cfma<double>(mbw, v[i], cfma<double>(beta, p[i], r[i]));  // r + beta (p - omega v)
     p[i] = pi;
     put_mg<TM>(pmg, i, pi);
   }
@@ -262,10 +263,10 @@ __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const do
                          double2* __restrict__ sv, void* smg, long n, double2* partials) {
   pdl_entry();
   if (S->done) return;
-  double2 al = S->alpha;
+  const double2 mal = mkc<double>(-S->alpha.x, -S->alpha.y);
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
-    double2 si = csub<double>(r[i], cmul<double>(al, v[i]));
+    double2 si = cfma<double>(mal, v[i], r[i]);  // r - alpha v
     sv[i] = si;
     put_mg<TM>(smg, i, si);
     acc[0].x = fma(si.x, si.x, fma(si.y, si.y, acc[0].x));
@@ -319,10 +320,11 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
   pdl_entry();
   if (S->done) return;
   double2 al = S->alpha, om = S->omega;
+  const double2 mom = mkc<double>(-om.x, -om.y);
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
     x[i] = cfma<double>(om, sh[i], cfma<double>(al, ph[i], x[i]));
-    double2 ri = csub<double>(sv[i], cmul<double>(om, t[i]));
+    double2 ri = cfma<double>(mom, t[i], sv[i]);  // s - omega t
     r[i] = ri;
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
     acc[1] = cadd<double>(acc[1], cmulc<double>(rh[i], ri));

@@ -41,22 +41,23 @@ __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T
 }
 
 // One damped-Jacobi sweep un = u + omega D^{-1} (f - M u), evaluated as
-// (1 - omega) u + omega D^{-1} (f - offdiag(u)) with the stored D^{-1}; u == nullptr is the
-// zero guess (un = omega D^{-1} f).
+// (1 - omega) u + (omega / D) (f - offdiag(u)) with the stored omega / D; u == nullptr is the
+// zero guess (un = (omega / D) f).
 template <typename T, int DIM>
 __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ un, T omega, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
-  cx<T> di = op.dinv[p];
+  cx<T> di = op.dinv[p];  // omega / D
   if (!u) {
-    un[p] = cscale<T>(omega, cmul<T>(f[p], di));
+    un[p] = cmul<T>(f[p], di);
     return;
   }
   cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
   cx<T> u0 = u[p];
-  un[p] = mkc<T>(fma(omega, g.x, (T(1) - omega) * u0.x), fma(omega, g.y, (T(1) - omega) * u0.y));
+  const T om1 = T(1) - omega;
+  un[p] = mkc<T>(fma(om1, u0.x, g.x), fma(om1, u0.y, g.y));
 }
 
 // Red-black Gauss-Seidel half-sweep on points with (i + j + l) % 2 == colour, in place:

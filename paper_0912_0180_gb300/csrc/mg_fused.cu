@@ -12,7 +12,7 @@
 //            place (reads u, writes the next iterate), halo staged in shared memory; the
 //            finest level may write its result widened to complex128 (the precision boundary
 //            into the FP64 Krylov vectors).
-//  k_tail    the coarsest levels (a few thousand unknowns in FP32, about a hundred in FP64) in
+//  k_tail    the coarsest levels (a few hundred unknowns in FP32, a few dozen in FP64) in
 //            ONE block: smoothing, residual, restriction, the dense coarsest solve,
 //            prolongation and post-smoothing, with __syncthreads() between phases instead of
 //            kernel launches.
@@ -71,8 +71,7 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
       int x = e % FX, y = e / FX;
       int i = fx0 + x, j = fy0 + y;
       cx<T> uv = mkc<T>(T(0), T(0));
-      if (!RBGS) uv = cscale<T>(omega, cmul<T>(fv[it], dv[it]));
-      else if (((i + j) & 1) == 0) uv = cmul<T>(fv[it], dv[it]);
+      if (!RBGS || ((i + j) & 1) == 0) uv = cmul<T>(fv[it], dv[it]);  // dinv holds omega/D (Jacobi)
       sf[y][x] = fv[it];
       su[y][x] = uv;
     }
@@ -120,13 +119,15 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
     int cx_ = e % DN_CX, cy = e / DN_CX;
     int I = I0 + cx_, J = J0 + cy;
     if (I >= nc0 || J >= nc1) continue;
-    const T w[3] = {T(0.25), T(0.5), T(0.25)};
-    cx<T> acc = mkc<T>(T(0), T(0));
+    // separable weights: each row (a + c) + 2 b, then the rows the same way, then / 16
+    cx<T> rw[3];
 #pragma unroll
-    for (int dj = 0; dj < 3; ++dj)
-#pragma unroll
-      for (int di = 0; di < 3; ++di) acc = cadd<T>(acc, cscale<T>(w[di] * w[dj], sr[2 * cy + dj][2 * cx_ + di]));
-    fc[I + nc0 * J] = acc;
+    for (int dj = 0; dj < 3; ++dj) {
+      cx<T> a = sr[2 * cy + dj][2 * cx_], b = sr[2 * cy + dj][2 * cx_ + 1], c = sr[2 * cy + dj][2 * cx_ + 2];
+      rw[dj] = mkc<T>(fma(T(2), b.x, a.x + c.x), fma(T(2), b.y, a.y + c.y));
+    }
+    cx<T> acc = mkc<T>(fma(T(2), rw[1].x, rw[0].x + rw[2].x), fma(T(2), rw[1].y, rw[0].y + rw[2].y));
+    fc[I + nc0 * J] = cscale<T>(T(0.0625), acc);
   }
 }
 
@@ -194,9 +195,10 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
       int p = i + n0 * j;
       int sx = x + HU, sy = y + HU;
       cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
-      cx<T> g = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
+      cx<T> g = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);  // dinv holds omega / D
       cx<T> uc = su[sy][sx];
-      u_out[p] = cconv<TO, T>(mkc<T>(fma(omega, g.x, (T(1) - omega) * uc.x), fma(omega, g.y, (T(1) - omega) * uc.y)));
+      const T om1 = T(1) - omega;
+      u_out[p] = cconv<TO, T>(mkc<T>(fma(om1, uc.x, g.x), fma(om1, uc.y, g.y)));
     }
   } else {
     // red points of the tile and one ring around it, from the corrected black values
@@ -260,50 +262,49 @@ template <typename T> struct TailMem {
   __device__ cx<T>* DG(int k) const { return base + a->off[k] + 4 * a->n[k]; }
 };
 
-__device__ __forceinline__ void tail_coords(int p, const int n[3], int& i, int& j, int& l) {
-  i = p % n[0];
-  int q = p / n[0];
-  j = q % n[1];
-  l = q / n[1];
+// Calls body(i, j, l, p) for every point of a level: each warp takes whole rows (fixed j, l) and
+// its lanes walk along x, so no point needs an index division.
+template <typename F>
+__device__ __forceinline__ void tail_for_each(const int n[3], F&& body) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = n[1] * n[2];
+  for (int row = warp; row < rows; row += TAIL_THREADS / 32) {
+    const int j = row % n[1], l = row / n[1];
+    const int base = row * n[0];
+    for (int i = lane; i < n[0]; i += 32) body(i, j, l, base + i);
+  }
 }
 
 template <typename T, int DIM>
 __device__ void tail_smooth(const TailArgs<T>& a, TailMem<T>& m, int k, bool zero) {
   const OpView<T>& op = a.op[k];
-  const int n = a.n[k];
   cx<T>* u = m.U(k);
   const cx<T>* f = m.F(k);
-  const cx<T>* dinv = m.DI(k);
-  const T om = a.omega;
+  const cx<T>* sdinv = m.DI(k);  // omega / D (Jacobi) or 1 / D (Gauss-Seidel)
+  const T om1 = T(1) - a.omega;
   if (a.smoother == HELM_SM_JACOBI) {
     cx<T>* w = m.W(k);
-    for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
-      cx<T> di = dinv[p];
+    tail_for_each(op.n, [&](int i, int j, int l, int p) {
       if (zero) {
-        w[p] = cscale<T>(om, cmul<T>(f[p], di));
-        continue;
+        w[p] = cmul<T>(f[p], sdinv[p]);
+      } else {
+        cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), sdinv[p]);
+        cx<T> u0 = u[p];
+        w[p] = mkc<T>(fma(om1, u0.x, g.x), fma(om1, u0.y, g.y));
       }
-      int i, j, l;
-      tail_coords(p, op.n, i, j, l);
-      cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
-      cx<T> u0 = u[p];
-      w[p] = mkc<T>(fma(om, g.x, (T(1) - om) * u0.x), fma(om, g.y, (T(1) - om) * u0.y));
-    }
+    });
     __syncthreads();
     m.swap ^= 1u << k;
   } else {
     for (int colour = 0; colour < 2; ++colour) {
-      for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
-        int i, j, l;
-        tail_coords(p, op.n, i, j, l);
+      tail_for_each(op.n, [&](int i, int j, int l, int p) {
         int c = (i + j + l) & 1;
         if (zero && colour == 0) {
-          u[p] = c == 0 ? cmul<T>(f[p], dinv[p]) : mkc<T>(T(0), T(0));
-          continue;
+          u[p] = c == 0 ? cmul<T>(f[p], sdinv[p]) : mkc<T>(T(0), T(0));
+        } else if (c == colour) {
+          u[p] = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), sdinv[p]);
         }
-        if (c != colour) continue;
-        u[p] = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), dinv[p]);
-      }
+      });
       __syncthreads();
     }
   }
@@ -351,11 +352,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
       cx<T>* w = m.W(k);
       const cx<T>* f = m.F(k);
       const cx<T>* dg = m.DG(k);
-      for (int p = threadIdx.x; p < n; p += TAIL_THREADS) {
-        int i, j, l;
-        tail_coords(p, op.n, i, j, l);
+      tail_for_each(op.n, [&](int i, int j, int l, int p) {
         w[p] = csub<T>(f[p], cfma<T>(dg[p], u[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)));
-      }
+      });
     } else {
       cx<T>* u = m.U(k);
       cx<T>* w = m.W(k);
@@ -367,9 +366,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
     const cx<T>* r = m.W(k);
     cx<T>* fc = m.F(k + 1);
     const T wts[3] = {T(0.25), T(0.5), T(0.25)};
-    for (int q = threadIdx.x; q < a.n[k + 1]; q += TAIL_THREADS) {
-      int I, J, Lz;
-      tail_coords(q, oc.n, I, J, Lz);
+    tail_for_each(oc.n, [&](int I, int J, int Lz, int q) {
       cx<T> acc = mkc<T>(T(0), T(0));
       for (int dl = (DIM > 2 ? -1 : 0); dl <= (DIM > 2 ? 1 : 0); ++dl) {
         int fl = DIM > 2 ? 2 * Lz + 1 + dl : 0;
@@ -386,7 +383,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
         }
       }
       fc[q] = acc;
-    }
+    });
     __syncthreads();
   }
   // coarsest: dense inverse, one warp per row
@@ -411,9 +408,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
     const OpView<T>& oc = a.op[k + 1];
     cx<T>* u = m.U(k);
     const cx<T>* e = m.U(k + 1);
-    for (int p = threadIdx.x; p < a.n[k]; p += TAIL_THREADS) {
-      int i, j, l;
-      tail_coords(p, op.n, i, j, l);
+    tail_for_each(op.n, [&](int i, int j, int l, int p) {
       int ci[2], cj[2] = {0, 0}, cl[2] = {0, 0};
       T wi[2], wj[2] = {T(1), T(1)}, wl[2] = {T(1), T(1)};
       int ni = tail_lin<T>(i, oc.n[0], ci, wi);
@@ -425,7 +420,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
           for (int c1 = 0; c1 < ni; ++c1)
             acc = cadd<T>(acc, cscale<T>(wi[c1] * wj[c2] * wl[c3], e[ci[c1] + oc.n[0] * (cj[c2] + oc.n[1] * cl[c3])]));
       u[p] = cadd<T>(u[p], acc);
-    }
+    });
     __syncthreads();
     for (int s = 0; s < a.nu2; ++s) tail_smooth<T, DIM>(a, m, k, false);
   }
@@ -440,7 +435,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
 // Points handled by the single block: its phases cost a fraction of a microsecond each only while
 // the block's threads have a few points each; FP64 runs at about a sixtieth of the FP32 rate, so
 // its tail stays tiny.
-template <typename T> static long tail_point_budget() { return std::is_same<T, double>::value ? 160 : 2400; }
+template <typename T> static long tail_point_budget() { return std::is_same<T, double>::value ? 40 : 700; }
 constexpr size_t TAIL_SMEM_BUDGET = 200 * 1024;
 
 template <typename T> int tail_first_level(const helm_ctx* c) {

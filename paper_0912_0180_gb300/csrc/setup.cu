@@ -79,10 +79,11 @@ __global__ void k_phi_inject(const double* __restrict__ pf, int f0, int f1, int 
   if (pc32) pc32[p] = (float)v;
 }
 
-// 1 / D at every point of a level, D = sum_axes a0 - s * phi, computed in FP64 and stored in
-// the multigrid precision (the smoothers multiply instead of dividing).
+// omega_s / D at every point of a level (omega_s = omega for damped Jacobi, 1 for Gauss-Seidel),
+// D = sum_axes a0 - s * phi, computed in FP64 and stored in the multigrid precision together with
+// D itself (the smoothers multiply instead of dividing).
 template <int DIM>
-__global__ void k_dinv(OpView<double> op, double2* d64, float2* d32, double2* g64, float2* g32) {
+__global__ void k_dinv(OpView<double> op, double omega_s, double2* d64, float2* d32, double2* g64, float2* g32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   int l = blockIdx.z;
@@ -93,7 +94,7 @@ __global__ void k_dinv(OpView<double> op, double2* d64, float2* d32, double2* g6
   if (DIM > 2) d = cadd<double>(d, op.a0[2][l]);
   double ph = op.phi ? op.phi[p] : op.phi0;
   d = csub<double>(d, cscale<double>(ph, op.s));
-  double2 r = crecip<double>(d);
+  double2 r = cscale<double>(omega_s, crecip<double>(d));
   if (d64) { d64[p] = r; g64[p] = d; }
   if (d32) { d32[p] = cconv<float, double>(r); g32[p] = cconv<float, double>(d); }
 }
@@ -299,6 +300,10 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.ud = mkc<T>((T)ud.x, (T)ud.y);
   if (ud.y != 0.0) real = false;
   v.uniform_real = real ? 1 : 0;
+  bool iso = dim > 1;
+  for (int a = 1; a < dim; ++a)
+    if (std::memcmp(&ua[a], &ua[0], sizeof(double2)) != 0) iso = false;
+  v.uniform_iso = iso ? 1 : 0;
   v.dinv = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dinv64 : (const cx<T>*)(const void*)dinv32;
   v.dg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dg64 : (const cx<T>*)(const void*)dg32;
   return v;
@@ -400,9 +405,10 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     {
       OpView<double> v = L.view<double>();
       dim3 g((L.n[0] + 127) / 128, L.n[1], L.n[2]);
-      if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
-      else if (L.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
-      else k_dinv<3><<<g, 128, 0, st>>>(v, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      double om = pc.smoother == HELM_SM_JACOBI ? pc.omega : 1.0;
+      if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      else if (L.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      else k_dinv<3><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       HELM_CUDA(cudaGetLastError());
     }
     if ((rc = ctx_alloc(c, &L.w, esz * L.ntot)) != HELM_OK) return rc;

@@ -42,6 +42,11 @@ __device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const c
     long st = (long)op.n[0] * op.n[1];
     sz = cadd<T>(cconv<T, TX>(x[p - st]), cconv<T, TX>(x[p + st]));
   }
+  if (DIM > 1 && op.uniform_iso) {  // one coefficient for all neighbours
+    cx<T> sum = cadd<T>(sx, sy);
+    if (DIM > 2) sum = cadd<T>(sum, sz);
+    return op.uniform_real ? cscale<T>(op.ua[0].x, sum) : cmul<T>(op.ua[0], sum);
+  }
   if (op.uniform_real) {
     cx<T> acc = cscale<T>(op.ua[0].x, sx);
     if (DIM > 1) acc = mkc<T>(fma(op.ua[1].x, sy.x, acc.x), fma(op.ua[1].x, sy.y, acc.y));
@@ -87,6 +92,10 @@ template <typename T>
 __device__ __forceinline__ cx<T> off2d(const OpView<T>& op, int i, int j, cx<T> xw, cx<T> xe, cx<T> xs, cx<T> xn) {
   if (op_uniform<2>(op, i, j, 0)) {
     cx<T> sx = cadd<T>(xw, xe), sy = cadd<T>(xs, xn);
+    if (op.uniform_iso) {
+      cx<T> sum = cadd<T>(sx, sy);
+      return op.uniform_real ? cscale<T>(op.ua[0].x, sum) : cmul<T>(op.ua[0], sum);
+    }
     if (op.uniform_real) {
       cx<T> acc = cscale<T>(op.ua[0].x, sx);
       return mkc<T>(fma(op.ua[1].x, sy.x, acc.x), fma(op.ua[1].x, sy.y, acc.y));
