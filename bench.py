@@ -202,9 +202,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--phase", default="all", choices=["all", "fp64", "fp32"],
-                    help="which timed paths to run: all (FP64 value, FP32-multigrid, e2e), or only the "
-                         "FP64 / FP32-multigrid device-timed path (for kernel profiling)")
+    ap.add_argument("--phase", default="all", choices=["all", "fp64", "fp32", "kernels"],
+                    help="which timed paths to run: all (FP64 value, FP32-multigrid, e2e), only the "
+                         "FP64 / FP32-multigrid device-timed path, or only the per-kernel rooflines "
+                         "(for kernel profiling)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the Krylov loop from the host (one graph launch per iteration) so that "
                          "a kernel profiler sees every launch; slower, for profiling only")
@@ -289,6 +290,17 @@ def main():
             step_ms.append(s0.elapsed_time(s1))
         return step_ms, lat, infos
 
+    if args.phase == "kernels":
+        kern = kernel_rooflines(torch, L, ctxs, p, dev, flush)
+        line = {"metric": METRIC, "phase": "kernels", "config": config(p), "roofline": kern["dominant"],
+                "roofline_fp32_mg": kern["fp32_mg"], "kernels": kern["table"]}
+        for h in ctxs.values():
+            h.close()
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     run64 = args.phase in ("all", "fp64")
     run32 = args.phase in ("all", "fp32")
     ms64 = lat64 = inf64 = ms32 = lat32 = inf32 = None
@@ -327,7 +339,7 @@ def main():
     value = ranks.job_rate(len(SOLVES), step64)
 
     # ---- per-kernel rooflines, measured with CUDA events on the launching stream ----
-    kern = kernel_rooflines(torch, L, ctxs, p, dev)
+    kern = kernel_rooflines(torch, L, ctxs, p, dev, flush)
 
     def pct(v, q):
         return float(np.percentile(np.asarray(v), q))
@@ -350,6 +362,7 @@ def main():
         "gpu_launches": int(sum(i.kernels for i in inf64[: len(SOLVES) * args.steps]) +
                             sum(i.kernels for i in inf32)),
         "roofline": kern["dominant"],
+        "roofline_fp32_mg": kern["fp32_mg"],
         "kernels": kern["table"],
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -371,9 +384,22 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_rooflines(torch, L, ctxs, p, dev) -> dict:
+# Algorithmic cost of the fused first half of a V(1,1) level (smoothing sweep from the zero guess,
+# residual, full weighting), per fine unknown: reads f and omega/D, writes u, writes a quarter of a
+# coarse value; flops: u = f (omega/D) (complex multiply, 6), residual (1 - omega) f - a (sum of
+# four neighbours) (3 complex adds, 1 complex multiply, 1 scale, 1 subtract: 16), full weighting
+# (8 complex adds and a scale per coarse unknown: 18 / 4).
+DOWN_FLOPS_PER_POINT = 6 + 16 + 18 / 4
+
+
+def down_bytes_per_point(esz: int) -> float:
+    return 3 * esz + esz / 4
+
+
+def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
     """Average duration of the hot kernels on the finest level, CUDA events on the launching
-    stream, achieved = algorithmic bytes (or FLOPs) per launch / duration."""
+    stream with L2 flushed before every launch; achieved = algorithmic bytes (or FLOPs) per
+    launch / duration."""
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -382,56 +408,61 @@ def kernel_rooflines(torch, L, ctxs, p, dev) -> dict:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    # FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (unit count inferred from a
-    # measured 1.2 TFLOP/s FP64 FMA loop; nominal 1.25 TFLOP/s)
+    # FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the unit count inferred from
+    # a measured 1.2 TFLOP/s FP64 FMA loop on this GB300)
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
     n = p.n
-    reps = 50
-    table = {}
     st = torch.cuda.current_stream()
+    table = {}
 
-    def time_it(fn):
-        for _ in range(3):
-            fn()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
+    def time_cold(fn, reps=20) -> float:
+        fn()
+        ts = []
         for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
             fn()
-        e1.record(st)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / reps / 1000.0  # seconds
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts) / 1000.0  # seconds
 
-    for mg, dt, esz, psz in (("c64", torch.complex64, 8, 4), ("c128", torch.complex128, 16, 8)):
+    for mg, dt, esz in (("c128", torch.complex128, 16), ("c64", torch.complex64, 8)):
         h = ctxs[(mg, "csg")]
-        u = torch.randn(n, dtype=dt, device=dev)
+        nc = h.level_shape(1)[0] * h.level_shape(1)[1]
         f = torch.randn(n, dtype=dt, device=dev)
-        out = torch.empty(n, dtype=dt, device=dev)
-        # damped-Jacobi sweeps from a guess: each reads u, f, phi and writes u' (two sweeps per
-        # call so that the result lands back in the caller's buffer without a copy)
-        t = time_it(lambda: h.level_op(L.HELM_OP_SMOOTH, 0, u, f, None, count=2)) / 2
-        byt = n * (3 * esz + psz)
-        table[f"jacobi_sweep_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
-        t = time_it(lambda: h.level_op(L.HELM_OP_RESIDUAL, 0, u, f, out))
-        table[f"residual_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
+        u = torch.empty(n, dtype=dt, device=dev)
+        fc = torch.empty(nc, dtype=dt, device=dev)
+        t = time_cold(lambda: h.level_op(L.HELM_OP_DOWN, 0, u, f, fc))
+        byt = n * down_bytes_per_point(esz)
+        fl = n * DOWN_FLOPS_PER_POINT
+        table[f"k_down2d_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9, "flops": fl,
+                                   "TFLOP/s": fl / t / 1e12}
+        r = torch.randn(n, dtype=torch.complex128, device=dev)
+        z = torch.empty(n, dtype=dt, device=dev)
+        t = time_cold(lambda: h.vcycle(r, out=z))
+        table[f"vcycle_{mg}"] = {"us": t * 1e6}
     h = ctxs[("c128", "csg")]
     x = torch.randn(n, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)
-    t = time_it(lambda: h.apply(x, out=y))
+    t = time_cold(lambda: h.apply(x, out=y))
     byt = n * (16 + 16 + 8)
-    flops = n * 48
-    table["h_apply_c128"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9, "TFLOP/s": flops / t / 1e12}
-    dom = table["jacobi_sweep_c128"]
-    # FP64 sweep: ~ 56 flops per unknown (diagonal, 4 complex FMAs, residual, complex divide, update)
-    fl = n * 56
-    ach = fl / (dom["us"] * 1e-6) / 1e12
-    dominant = {"kernel": "k_jacobi<double,2> (finest level, FP64 path)", "bound": "alu", "achieved": ach,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)",
-                "hbm_GBs_achieved": dom["GB/s"], "hbm_peak_GBs": hbm, "hbm_peak_source": hbm_src}
-    for k, v in table.items():
-        v["frac_hbm"] = v["GB/s"] / hbm
-    return {"dominant": dominant, "table": table}
+    table["k_h_apply_c128"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
+    for v in table.values():
+        if "GB/s" in v:
+            v["frac_hbm"] = v["GB/s"] / hbm
+    d64, d32 = table["k_down2d_c128"], table["k_down2d_c64"]
+    dominant = {"kernel": "k_down2d<double> (fused smooth + residual + full weighting, finest level, FP64 path)",
+                "bound": "alu", "achieved": d64["TFLOP/s"], "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": d64["TFLOP/s"] / fp64_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "flops_per_launch": d64["flops"], "launch_us": d64["us"]}
+    fp32 = {"kernel": "k_down2d<float> (same kernel in the FP32 V-cycle)", "bound": "hbm",
+            "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm, "traffic": None,
+            "peak_source": hbm_src, "bytes_per_launch": d32["bytes"], "launch_us": d32["us"]}
+    return {"dominant": dominant, "fp32_mg": fp32, "table": table}
 
 
 if __name__ == "__main__":

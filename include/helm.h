@@ -164,9 +164,12 @@ helm_status helm_vcycle(helm_ctx* ctx, const void* r, void* z, void* stream);
  *   HELM_OP_SMOOTH0   a <- the first sweep from a zero guess, then count-1 sweeps
  *   HELM_OP_RESTRICT  out (level lvl+1) = full weighting of a (level lvl)
  *   HELM_OP_PROLONG   a (level lvl) += bilinear interpolation of b (level lvl+1)
- *   HELM_OP_COARSE    out = M_coarsest^{-1} a (lvl must be the coarsest level) */
+ *   HELM_OP_COARSE    out = M_coarsest^{-1} a (lvl must be the coarsest level)
+ *   HELM_OP_DOWN      the fused first half of a V(1,1) level (2D, nu1 = 1, not the coarsest):
+ *                     a = one smoothing sweep from the zero guess on M_lvl a = b, and
+ *                     out (level lvl+1) = full weighting of b - M_lvl a, in one kernel */
 enum { HELM_OP_APPLY = 0, HELM_OP_RESIDUAL = 1, HELM_OP_SMOOTH = 2, HELM_OP_SMOOTH0 = 3,
-       HELM_OP_RESTRICT = 4, HELM_OP_PROLONG = 5, HELM_OP_COARSE = 6 };
+       HELM_OP_RESTRICT = 4, HELM_OP_PROLONG = 5, HELM_OP_COARSE = 6, HELM_OP_DOWN = 7 };
 helm_status helm_level_op(helm_ctx* ctx, int op, int lvl, void* a, const void* b, void* out,
                           int count, void* stream);
 

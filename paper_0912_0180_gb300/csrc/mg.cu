@@ -371,6 +371,10 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
     case HELM_OP_RESTRICT: if (lvl >= nl - 1 || !A || !O) return HELM_ERR_ARG; restrict_any<T>(L, c->lv[lvl + 1], A, O, nullptr, st); break;
     case HELM_OP_PROLONG: if (lvl >= nl - 1 || !A || !B) return HELM_ERR_ARG; prolong_any<T>(L, c->lv[lvl + 1], B, A, 0, nullptr, st); break;
     case HELM_OP_COARSE: if (lvl != nl - 1 || !A || !O) return HELM_ERR_ARG; coarse_solve<T>(c, A, O, nullptr, st); break;
+    case HELM_OP_DOWN:
+      if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || !A || !B || !O) return HELM_ERR_ARG;
+      fused_down2d<T>(c, lvl, B, A, O, nullptr, st);
+      break;
     default: return HELM_ERR_ARG;
   }
   HELM_CUDA(cudaGetLastError());

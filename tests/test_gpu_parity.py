@@ -131,6 +131,34 @@ def test_multigrid_components(case, pci, mg):
     h.close()
 
 
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("pci", [0, 2])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]])
+def test_fused_down_kernel(case, pci, mg):
+    """HELM_OP_DOWN (one kernel): smoothing from the zero guess, residual and full weighting,
+    against the oracle's three separate steps on every non-coarsest level."""
+    p = _problem(case)
+    pc = PCS[pci]
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype=mg)
+    dt = torch.complex128 if mg == "c128" else torch.complex64
+    tol = 1e-11 if mg == "c128" else 2e-5
+    rng = np.random.default_rng(7)
+    for lvl in range(o.nlev - 1):
+        n, nc = o.level_size(1, lvl), o.level_size(1, lvl + 1)
+        f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        if mg == "c64":
+            f = f.astype(np.complex64).astype(np.complex128)
+        u = torch.empty(n, dtype=dt, device="cuda")
+        fc = torch.empty(nc, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_DOWN, lvl, u, cu(f, dt), fc)
+        u_ref = o.smooth(lvl, np.zeros(n), f, 1)
+        fc_ref = o.restrict(lvl, f - o.apply(u_ref, 1, lvl))
+        assert rel(u.cpu().numpy(), u_ref) < tol
+        assert rel(fc.cpu().numpy(), fc_ref) < (10 * tol)
+    h.close()
+
+
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("mg", ["c128", "c64"])
 @pytest.mark.parametrize("pci", range(len(PCS)))
