@@ -184,6 +184,51 @@ helm_status helm_level_shape(const helm_ctx* ctx, int lvl, int* n);
 helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, const helm_solve_opts* opts,
                        helm_solve_info* info, void* stream);
 
+/* Solves n independent instances H_i x_i = b_i at once (a batch of uneven grids, k fields and
+ * preconditioners): every instance's device-resident solve (as in helm_solve, opts[i]) runs on
+ * its own stream, ordered after `stream` and joined back into it, so the instances overlap on the
+ * GPU; the host only reads each instance's statistics when its loop has finished.  ctxs must be n
+ * distinct contexts (a context holds one solve's workspace); b[i], x[i] follow helm_solve.
+ * infos (n entries, may be NULL) receives every instance's statistics.  Returns HELM_OK when all
+ * instances converged, else the first non-OK instance status (every x[i] still holds that
+ * instance's last iterate); argument errors are reported before anything is launched.  The result
+ * of each instance is bitwise the result helm_solve gives it alone. */
+helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* b, void* const* x, int n,
+                             const helm_solve_opts* opts, helm_solve_info* infos, void* stream);
+
+/* ---- serving --------------------------------------------------------------------------------
+ * A server admits solve requests of any grid, k field and preconditioner against a device-memory
+ * budget and runs up to max_active of them at once, each on its own stream with its own context
+ * (continuous batching: a request submitted while others run starts as soon as a slot and the
+ * budget allow, and its work overlaps theirs on the GPU).  Requests start in submission order.
+ * Each request's result is bitwise what helm_solve gives it alone.  A server is thread-safe for
+ * submit / poll / wait / stats; a worker thread owned by the server does the device work. */
+typedef struct {
+  helm_grid grid;
+  helm_kspec k;          /* k.phi (HOST) is copied at submit */
+  helm_precond pc;
+  helm_solve_opts opts;  /* opts.shadow (HOST, IDR) is copied at submit; history and host_loop ignored */
+  const void* b;         /* HOST complex128, N entries; copied at submit */
+  void* x;               /* HOST complex128, N entries; written before the request completes and
+                            must stay valid until then */
+} helm_request;
+typedef struct helm_server helm_server;
+
+/* Device bytes a request holds while it runs (operator, hierarchy, coarse inverse, Krylov
+ * workspace, b and x); the server admits against this estimate.  0 for invalid arguments. */
+size_t helm_estimate_bytes(const helm_grid* grid, const helm_precond* pc, const helm_solve_opts* opts);
+
+helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server** out);
+/* HELM_ERR_OOM if the request alone exceeds the budget; *ticket identifies it afterwards. */
+helm_status helm_server_submit(helm_server* s, const helm_request* req, uint64_t* ticket);
+/* HELM_ERR_BUSY while queued or running; otherwise the request's final status, with its
+ * statistics and the submission-to-completion latency in seconds. */
+helm_status helm_server_poll(helm_server* s, uint64_t ticket, helm_solve_info* info, double* latency_s);
+helm_status helm_server_wait(helm_server* s, uint64_t ticket, helm_solve_info* info, double* latency_s);
+helm_status helm_server_stats(helm_server* s, int* queued, int* active, size_t* used_bytes);
+/* Finishes every queued and running request, then releases the server. */
+void helm_server_destroy(helm_server* s);
+
 /* r = b - H x and *rel_out = ||r|| / ||b|| (0 when b = 0), FP64, without allocating anything.
  * The paper has no counterpart: this is the true-residual computation that helm_solve runs
  * after its Krylov loop, offered to callers that cannot allocate device memory -- processes

@@ -42,6 +42,11 @@ class SolveInfo(C.Structure):
                 ("rel_res_recur", C.c_double), ("rel_res_true", C.c_double), ("kernels", C.c_long)]
 
 
+class Request(C.Structure):
+    _fields_ = [("grid", Grid), ("k", KSpec), ("pc", Precond), ("opts", SolveOpts), ("b", C.c_void_p),
+                ("x", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -72,6 +77,22 @@ def load() -> C.CDLL:
     lib.helm_level_op.restype = ip
     lib.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.helm_solve.restype = ip
+    lib.helm_solve_batch.argtypes = [vp, vp, vp, ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+    lib.helm_solve_batch.restype = ip
+    lib.helm_estimate_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Precond), C.POINTER(SolveOpts)]
+    lib.helm_estimate_bytes.restype = C.c_size_t
+    lib.helm_server_create.argtypes = [C.c_size_t, ip, C.POINTER(vp)]
+    lib.helm_server_create.restype = ip
+    lib.helm_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+    lib.helm_server_submit.restype = ip
+    lib.helm_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]
+    lib.helm_server_poll.restype = ip
+    lib.helm_server_wait.argtypes = [vp, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]
+    lib.helm_server_wait.restype = ip
+    lib.helm_server_stats.argtypes = [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(C.c_size_t)]
+    lib.helm_server_stats.restype = ip
+    lib.helm_server_destroy.argtypes = [vp]
+    lib.helm_server_destroy.restype = None
     lib.helm_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.helm_residual_noalloc.restype = ip
     lib.helm_destroy.argtypes = [vp]

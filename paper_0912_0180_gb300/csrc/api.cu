@@ -3,7 +3,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "helm_internal.cuh"
 
@@ -29,7 +31,7 @@ helm_status cuda_check(cudaError_t e, const char* what) {
 helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return HELM_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, c->alloc_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -79,12 +81,42 @@ static helm_status check_precond(const helm_precond* p) {
   return HELM_OK;
 }
 
+void ctx_release_on(helm_ctx* c, cudaStream_t st) {
+  if (!c) return;
+  krylov_free(c, st);
+  for (void* p : c->allocs) cudaFreeAsync(p, st);
+  delete c;
+}
+
+// helm_destroy: the context may have been used on any stream, so wait for the device first.
 static void ctx_release(helm_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  krylov_free(c);
-  for (void* p : c->allocs) cudaFree(p);
-  delete c;
+  ctx_release_on(c, (cudaStream_t)0);
+  cudaStreamSynchronize((cudaStream_t)0);
+}
+
+static std::mutex g_pinned_mu;
+static std::vector<void*> g_pinned_free;
+
+void* pinned_slot_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      void* p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes < 4096 ? 4096 : bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void pinned_slot_put(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(p);
 }
 
 }  // namespace helm
@@ -111,6 +143,7 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   }
   cudaGetDevice(&c->dev);
   cudaStream_t st = (cudaStream_t)stream;
+  c->alloc_stream = st;
   if (k->phi) {
     long n = 1;
     for (int a = 0; a < grid->dim; ++a) {
@@ -177,14 +210,37 @@ helm_status helm_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, 
   return mg_level_op(c, op, lvl, a, b, out, count, (cudaStream_t)stream);
 }
 
-helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opts* o, helm_solve_info* info,
-                       void* stream) {
-  if (info) std::memset(info, 0, sizeof(*info));
+static helm_status check_solve_args(const helm_ctx* c, const void* b, const void* x, const helm_solve_opts* o) {
   if (!c || !b || !x || !o || b == x) { set_error("helm_solve: NULL or aliased arguments"); return HELM_ERR_ARG; }
   if (!aligned(b, 16) || !aligned(x, 16)) { set_error("helm_solve: misaligned"); return HELM_ERR_ARG; }
   if (o->method != HELM_BICGSTAB && o->method != HELM_IDR) { set_error("method"); return HELM_ERR_ARG; }
   if (o->method == HELM_IDR && (o->s < 1 || o->s > 8 || !o->shadow)) { set_error("IDR needs 1 <= s <= 8 and a shadow array"); return HELM_ERR_ARG; }
   if (!(o->tol > 0.0) || o->maxmv < 1 || o->max_restarts < 0) { set_error("tol / maxmv / max_restarts"); return HELM_ERR_ARG; }
+  return HELM_OK;
+}
+
+helm_status helm_solve_batch(helm_ctx* const* cs, const void* const* b, void* const* x, int n,
+                             const helm_solve_opts* o, helm_solve_info* infos, void* stream) {
+  if (infos && n > 0) std::memset(infos, 0, sizeof(*infos) * n);
+  if (n < 0 || (n > 0 && (!cs || !b || !x || !o))) { set_error("helm_solve_batch: bad arrays"); return HELM_ERR_ARG; }
+  for (int i = 0; i < n; ++i) {
+    helm_status s = check_solve_args(cs[i], b[i], x[i], &o[i]);
+    if (s != HELM_OK) return s;
+    for (int j = 0; j < i; ++j)
+      if (cs[j] == cs[i]) { set_error("helm_solve_batch: a context appears twice"); return HELM_ERR_ARG; }
+  }
+  if (n == 0) return HELM_OK;
+  PdlScope pdl(cs[0]);
+  helm_status s = krylov_solve_batch(cs, (const double2* const*)b, (double2* const*)x, n, o, infos,
+                                     (cudaStream_t)stream);
+  return s;
+}
+
+helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opts* o, helm_solve_info* info,
+                       void* stream) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  helm_status cs = check_solve_args(c, b, x, o);
+  if (cs != HELM_OK) return cs;
   PdlScope pdl(c);
   helm_status s = krylov_solve(c, (const double2*)b, (double2*)x, o, info, (cudaStream_t)stream);
   if (info) info->status = s;

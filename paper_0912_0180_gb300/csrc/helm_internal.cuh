@@ -121,6 +121,7 @@ struct helm_ctx {
   std::vector<void*> allocs;         // everything to free
   helm::Workspace* ws = nullptr;     // Krylov workspace (lazily created)
   void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
+  cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations of helm_create
   int tail_first = 1 << 30;          // first level run by the single-block tail kernel
 };
 
@@ -135,8 +136,15 @@ helm_status cuda_check(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::helm::cuda_check(_e, #call);   \
   } while (0)
 
-// device allocation owned by the context
+// device allocation owned by the context (stream-ordered, on the context's creation stream)
 helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes);
+// releases a context: every buffer is freed in order on `st` after the work already queued there
+// (no device-wide synchronisation); the caller guarantees all its work was queued on `st`
+void ctx_release_on(helm_ctx* c, cudaStream_t st);
+// pinned host buffers for the per-solve statistics, recycled (freeing pinned memory may
+// synchronise the device)
+void* pinned_slot_get(size_t bytes);
+void pinned_slot_put(void* p);
 
 // setup.cu
 helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st);
@@ -167,7 +175,11 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
 // krylov.cu
 helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
                          helm_solve_info* info, cudaStream_t st);
-void krylov_free(helm_ctx* c);
+helm_status krylov_solve_batch(helm_ctx* const* cs, const double2* const* b, double2* const* x, int n,
+                               const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t user);
+// resumable solves (used by the batch and the server)
+struct SolveJob;
+void krylov_free(helm_ctx* c, cudaStream_t st);
 
 // Programmatic dependent launch: kernels on the solve path are launched so that the next kernel's
 // blocks may be scheduled while the previous one drains; every such kernel starts with

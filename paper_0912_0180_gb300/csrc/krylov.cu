@@ -13,6 +13,7 @@
 // No kernel waits on another: there is no device-side spin anywhere.
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 
 #include "stencil.cuh"
@@ -598,8 +599,8 @@ __global__ void k_mgs_upd(double2* __restrict__ pj, const double2* __restrict__ 
 
 // ---- host orchestration ---------------------------------------------------------------------
 
-static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes, cudaStream_t st) {
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc failed for the Krylov workspace");
@@ -610,7 +611,7 @@ static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes) {
   return HELM_OK;
 }
 
-void krylov_free(helm_ctx* c) {
+void krylov_free(helm_ctx* c, cudaStream_t st) {
   Workspace* w = c->ws;
   if (!w) return;
   if (w->loop) cudaGraphExecDestroy(w->loop);
@@ -619,8 +620,8 @@ void krylov_free(helm_ctx* c) {
   if (w->idr_init) cudaGraphExecDestroy(w->idr_init);
   if (w->loop_graph) cudaGraphDestroy(w->loop_graph);
   if (w->init_graph) cudaGraphDestroy(w->init_graph);
-  for (void* p : w->mem) cudaFree(p);
-  if (w->hst) cudaFreeHost(w->hst);
+  for (void* p : w->mem) cudaFreeAsync(p, st);
+  pinned_slot_put(w->hst);
   delete w;
   c->ws = nullptr;
 }
@@ -827,7 +828,10 @@ static helm_status build_loop(const Ctx& k, int method, int s) {
 template <typename TM>
 static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st) {
   Workspace*& w = c->ws;
-  if (w && (w->method != o->method || (o->method == HELM_IDR && w->s != o->s))) krylov_free(c);
+  if (w && (w->method != o->method || (o->method == HELM_IDR && w->s != o->s))) {
+    HELM_CUDA(cudaStreamSynchronize(st));
+    krylov_free(c, st);
+  }
   bool fresh = w == nullptr;
   if (fresh) {
     w = new Workspace();
@@ -843,24 +847,25 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
     bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
     size_t vmg = (f32 ? sizeof(float2) : sizeof(double2)) * n;
     helm_status s;
-    if ((s = ws_alloc(c, w, (void**)&w->st, sizeof(KrylovState))) != HELM_OK) return s;
-    HELM_CUDA(cudaMemset(w->st, 0, sizeof(KrylovState)));
-    HELM_CUDA(cudaMallocHost(&w->hst, sizeof(KrylovState)));
-    if ((s = ws_alloc(c, w, (void**)&w->partials, sizeof(double2) * NRED * w->G)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, (void**)&w->st, sizeof(KrylovState), st)) != HELM_OK) return s;
+    HELM_CUDA(cudaMemsetAsync(w->st, 0, sizeof(KrylovState), st));
+    w->hst = (KrylovState*)pinned_slot_get(sizeof(KrylovState));
+    if (!w->hst) { set_error("pinned host buffer"); return HELM_ERR_OOM; }
+    if ((s = ws_alloc(c, w, (void**)&w->partials, sizeof(double2) * NRED * w->G, st)) != HELM_OK) return s;
     double2** vecs[] = {&w->x, &w->r, &w->t};
-    for (auto pp : vecs) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
-    if ((s = ws_alloc(c, w, &w->pmg, vmg)) != HELM_OK) return s;
-    if ((s = ws_alloc(c, w, (void**)&w->ph, v64)) != HELM_OK) return s;
+    for (auto pp : vecs) if ((s = ws_alloc(c, w, (void**)pp, v64, st)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, &w->pmg, vmg, st)) != HELM_OK) return s;
+    if ((s = ws_alloc(c, w, (void**)&w->ph, v64, st)) != HELM_OK) return s;
     if (o->method == HELM_BICGSTAB) {
       double2** more[] = {&w->rh, &w->p, &w->v, &w->sv};
-      for (auto pp : more) if ((s = ws_alloc(c, w, (void**)pp, v64)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, &w->smg, vmg)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, (void**)&w->sh, v64)) != HELM_OK) return s;
+      for (auto pp : more) if ((s = ws_alloc(c, w, (void**)pp, v64, st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, &w->smg, vmg, st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->sh, v64, st)) != HELM_OK) return s;
     } else {
-      if ((s = ws_alloc(c, w, (void**)&w->q, v64)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, (void**)&w->P, v64 * o->s)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, (void**)&w->dR, v64 * o->s)) != HELM_OK) return s;
-      if ((s = ws_alloc(c, w, (void**)&w->dX, v64 * o->s)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->q, v64, st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->P, v64 * o->s, st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->dR, v64 * o->s, st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->dX, v64 * o->s, st)) != HELM_OK) return s;
     }
   }
   k.c = c;
@@ -912,86 +917,213 @@ static helm_status upload_shadow(const Ctx& k, const helm_solve_opts* o, cudaStr
   return HELM_OK;
 }
 
+// A solve in flight: begin() enqueues everything up to the readback of the statistics, poll()
+// then finishes it or enqueues a true-residual restart.  A single solve, a batch and the server
+// all drive solves through this object; nothing here synchronises another stream.
+struct SolveJob {
+  helm_ctx* c = nullptr;
+  const double2* b = nullptr;
+  double2* x = nullptr;
+  helm_solve_opts o{};
+  helm_solve_info* info = nullptr;
+  cudaStream_t st = nullptr;
+  Ctx k{};
+  bool f32 = false, bicg = true;
+  int restarts = 0;
+  long kernels = 0;
+  long host_loops = -1;
+  cudaEvent_t ev = nullptr;
+  bool finished = false;
+  helm_status status = HELM_OK;
+};
+
 template <typename TM>
-static helm_status solve_t(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
-                           helm_solve_info* info, cudaStream_t st) {
-  Ctx k;
-  helm_status s = prepare<TM>(c, o, k, st);
+static helm_status job_pass(SolveJob& j) {
+  Workspace* w = j.k.w;
+  cudaStream_t st = j.st;
+  const Ctx& k = j.k;
+  void* rmg = j.bicg ? nullptr : w->pmg;  // IDR's first V-cycle input is r in multigrid precision
+  launch_pdl(k_start, dim3(k.G), dim3(KT), 0, st, w->st, j.b, w->r, j.bicg ? w->rh : nullptr,
+             j.bicg ? w->p : nullptr, j.bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n,
+             j.restarts == 0 ? 1 : 0, w->partials);
+  if (!j.bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
+  j.host_loops = -1;
+  if (j.o.host_loop) {
+    j.host_loops = 0;
+    for (;;) {
+      HELM_CUDA(cudaMemcpyAsync(&w->hst->done, &w->st->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      HELM_CUDA(cudaStreamSynchronize(st));
+      if (w->hst->done || j.host_loops > j.o.maxmv + 16) break;
+      HELM_CUDA(cudaGraphLaunch(w->body, st));
+      ++j.host_loops;
+    }
+  } else {
+    HELM_CUDA(cudaGraphLaunch(w->loop, st));
+  }
+  OpView<double> H = j.c->H.view<double>();
+  switch (k.dim) {
+    case 1: launch_pdl(k_true_res<1>, dim3(k.G), dim3(KT), 0, st, w->st, H, j.b, w->x, w->r, k.n, w->partials); break;
+    case 2: launch_pdl(k_true_res<2>, dim3(k.G), dim3(KT), 0, st, w->st, H, j.b, w->x, w->r, k.n, w->partials); break;
+    default: launch_pdl(k_true_res<3>, dim3(k.G), dim3(KT), 0, st, w->st, H, j.b, w->x, w->r, k.n, w->partials);
+  }
+  HELM_CUDA(cudaGetLastError());
+  HELM_CUDA(cudaMemcpyAsync(w->hst, w->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, st));
+  HELM_CUDA(cudaEventRecord(j.ev, st));
+  return HELM_OK;
+}
+
+template <typename TM>
+static helm_status job_begin_t(SolveJob& j) {
+  helm_status s = prepare<TM>(j.c, &j.o, j.k, j.st);
   if (s != HELM_OK) return s;
-  Workspace* w = k.w;
-  if (o->method == HELM_IDR && (s = upload_shadow(k, o, st)) != HELM_OK) return s;
-  // scalars fixed for this solve
+  Workspace* w = j.k.w;
+  cudaStream_t st = j.st;
+  if (j.o.method == HELM_IDR && (s = upload_shadow(j.k, &j.o, st)) != HELM_OK) return s;
+  // per-solve scalars
   KrylovState init{};
-  init.tol = o->tol;
-  init.maxmv = o->maxmv;
-  init.s = o->s;
+  init.tol = j.o.tol;
+  init.maxmv = j.o.maxmv;
+  init.s = j.o.s;
   HELM_CUDA(cudaMemcpyAsync(&w->st->tol, &init.tol, sizeof(double), cudaMemcpyHostToDevice, st));
   HELM_CUDA(cudaMemcpyAsync(&w->st->maxmv, &init.maxmv, sizeof(int), cudaMemcpyHostToDevice, st));
   HELM_CUDA(cudaMemcpyAsync(&w->st->s, &init.s, sizeof(int), cudaMemcpyHostToDevice, st));
-  double* hist = o->history;
+  double* hist = j.o.history;
   HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
-  HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * k.n, st));
-  bool bicg = o->method == HELM_BICGSTAB;
-  // the first V-cycle input: Bi-CGSTAB builds p itself; IDR needs r in multigrid precision
-  void* rmg = bicg ? nullptr : w->pmg;
-  OpView<double> H = c->H.view<double>();
-  int restarts = 0;
-  long kernels = 0;
-  for (;;) {
-    k_start<<<k.G, KT, 0, st>>>(w->st, b, w->r, bicg ? w->rh : nullptr, bicg ? w->p : nullptr,
-                                bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n, restarts == 0 ? 1 : 0,
-                                w->partials);
-    if (!bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
-    long host_loops = -1;
-    if (o->host_loop) {
-      host_loops = 0;
-      for (;;) {
-        HELM_CUDA(cudaMemcpyAsync(&w->hst->done, &w->st->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        HELM_CUDA(cudaStreamSynchronize(st));
-        if (w->hst->done || host_loops > o->maxmv + 16) break;
-        HELM_CUDA(cudaGraphLaunch(w->body, st));
-        ++host_loops;
-      }
-    } else {
-      HELM_CUDA(cudaGraphLaunch(w->loop, st));
-    }
-    switch (k.dim) {
-      case 1: k_true_res<1><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
-      case 2: k_true_res<2><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials); break;
-      default: k_true_res<3><<<k.G, KT, 0, st>>>(w->st, H, b, w->x, w->r, k.n, w->partials);
-    }
-    HELM_CUDA(cudaGetLastError());
-    HELM_CUDA(cudaMemcpyAsync(w->hst, w->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, st));
-    HELM_CUDA(cudaStreamSynchronize(st));
-    const KrylovState& hs = *w->hst;
-    // k_start, the loop head, loops x body, k_true_res (+ the IDR start graph)
-    if (host_loops >= 0) kernels += 2 + host_loops * (long)(w->body_nodes - 1) + (bicg ? 0 : (long)w->init_nodes);
-    else kernels += 3 + (long)hs.loops * (long)w->body_nodes + (bicg ? 0 : (long)w->init_nodes);
-    if (hs.status != HELM_OK || hs.rel_true < o->tol) break;
-    if (restarts >= o->max_restarts) break;
-    ++restarts;
-  }
-  const KrylovState& hs = *w->hst;
-  HELM_CUDA(cudaMemcpyAsync(x, w->x, sizeof(double2) * k.n, cudaMemcpyDeviceToDevice, st));
-  helm_status final_status = (helm_status)hs.status;
-  if (final_status == HELM_OK && !(hs.rel_true < o->tol)) final_status = HELM_ERR_MAXIT;
-  if (info) {
-    info->status = final_status;
-    info->iters = hs.iters;
-    info->matvecs = hs.matvecs;
-    info->restarts = restarts;
-    info->rel_res_recur = hs.rel_recur;
-    info->rel_res_true = hs.rel_true;
-    info->kernels = kernels;
-  }
-  HELM_CUDA(cudaStreamSynchronize(st));
-  return final_status;
+  HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * j.k.n, st));
+  if (!j.ev) HELM_CUDA(cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming));
+  return job_pass<TM>(j);
 }
+
+// Called once j.ev has completed: finish, or enqueue a restart from the true residual.
+template <typename TM>
+static helm_status job_step_t(SolveJob& j) {
+  Workspace* w = j.k.w;
+  const KrylovState& hs = *w->hst;
+  // k_start, the loop head, loops x body, k_true_res (+ the IDR start graph)
+  if (j.host_loops >= 0) j.kernels += 2 + j.host_loops * (long)(w->body_nodes - 1) + (j.bicg ? 0 : (long)w->init_nodes);
+  else j.kernels += 3 + (long)hs.loops * (long)w->body_nodes + (j.bicg ? 0 : (long)w->init_nodes);
+  if (hs.status == HELM_OK && !(hs.rel_true < j.o.tol) && j.restarts < j.o.max_restarts) {
+    ++j.restarts;
+    return job_pass<TM>(j);
+  }
+  HELM_CUDA(cudaMemcpyAsync(j.x, w->x, sizeof(double2) * j.k.n, cudaMemcpyDeviceToDevice, j.st));
+  helm_status fs = (helm_status)hs.status;
+  if (fs == HELM_OK && !(hs.rel_true < j.o.tol)) fs = HELM_ERR_MAXIT;
+  if (j.info) {
+    j.info->status = fs;
+    j.info->iters = hs.iters;
+    j.info->matvecs = hs.matvecs;
+    j.info->restarts = j.restarts;
+    j.info->rel_res_recur = hs.rel_recur;
+    j.info->rel_res_true = hs.rel_true;
+    j.info->kernels = j.kernels;
+  }
+  j.status = fs;
+  j.finished = true;
+  return HELM_OK;
+}
+
+static bool job_f32(const helm_ctx* c) { return c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64; }
+
+helm_status job_begin(SolveJob& j) {
+  j.f32 = job_f32(j.c);
+  j.bicg = j.o.method == HELM_BICGSTAB;
+  return j.f32 ? job_begin_t<float>(j) : job_begin_t<double>(j);
+}
+
+// Non-blocking when `block` is false: returns HELM_ERR_BUSY while the pass is still running.
+helm_status job_poll(SolveJob& j, bool block) {
+  if (j.finished) return HELM_OK;
+  if (block) HELM_CUDA(cudaEventSynchronize(j.ev));
+  else {
+    cudaError_t e = cudaEventQuery(j.ev);
+    if (e == cudaErrorNotReady) return HELM_ERR_BUSY;
+    if (e != cudaSuccess) return cuda_check(e, "cudaEventQuery(solve)");
+  }
+  return j.f32 ? job_step_t<float>(j) : job_step_t<double>(j);
+}
+
+void job_release(SolveJob& j) {
+  if (j.ev) cudaEventDestroy(j.ev);
+  j.ev = nullptr;
+}
+
+SolveJob* job_new() { return new SolveJob(); }
+void job_delete(SolveJob* j) { delete j; }
+void job_setup(SolveJob* j, helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
+               helm_solve_info* info, cudaStream_t st) {
+  j->c = c; j->b = b; j->x = x; j->o = *o; j->info = info; j->st = st;
+}
+bool job_finished(const SolveJob* j) { return j->finished; }
+helm_status job_status(const SolveJob* j) { return j->status; }
 
 helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
                          helm_solve_info* info, cudaStream_t st) {
-  if (c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64) return solve_t<float>(c, b, x, o, info, st);
-  return solve_t<double>(c, b, x, o, info, st);
+  SolveJob j;
+  j.c = c; j.b = b; j.x = x; j.o = *o; j.info = info; j.st = st;
+  helm_status s = job_begin(j);
+  while (s == HELM_OK && !j.finished) s = job_poll(j, true);
+  job_release(j);
+  if (s != HELM_OK) return s;
+  HELM_CUDA(cudaStreamSynchronize(st));
+  return j.status;
+}
+
+// Independent solves overlapped on the device: every instance runs on its own stream (ordered
+// after the caller's stream and joined back into it), its device-resident loop needing no host
+// involvement until its statistics are read.
+helm_status krylov_solve_batch(helm_ctx* const* cs, const double2* const* b, double2* const* x, int n,
+                               const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t user) {
+  std::vector<SolveJob> jobs(n);
+  std::vector<cudaStream_t> streams(n, nullptr);
+  cudaEvent_t start;
+  HELM_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  helm_status s = HELM_OK;
+  cudaError_t e = cudaEventRecord(start, user);
+  if (e != cudaSuccess) s = cuda_check(e, "cudaEventRecord(batch)");
+  for (int i = 0; i < n && s == HELM_OK; ++i) {
+    e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[i], start, 0);
+    if (e != cudaSuccess) { s = cuda_check(e, "batch stream"); break; }
+    SolveJob& j = jobs[i];
+    j.c = cs[i]; j.b = b[i]; j.x = x[i]; j.o = o[i]; j.info = infos ? &infos[i] : nullptr; j.st = streams[i];
+    if (j.o.host_loop) j.o.host_loop = 0;  // a batch always runs its loops on the device
+    s = job_begin(j);
+  }
+  // finish every job (restarts are enqueued as their first pass completes)
+  bool pending = s == HELM_OK;
+  while (pending && s == HELM_OK) {
+    pending = false;
+    for (int i = 0; i < n && s == HELM_OK; ++i) {
+      if (jobs[i].finished) continue;
+      helm_status r = job_poll(jobs[i], false);
+      if (r == HELM_ERR_BUSY) { pending = true; continue; }
+      if (r != HELM_OK) { s = r; break; }
+      if (!jobs[i].finished) pending = true;
+    }
+    if (pending) std::this_thread::yield();
+  }
+  // join the instance streams back into the caller's stream
+  for (int i = 0; i < n; ++i) {
+    if (!streams[i]) continue;
+    if (s == HELM_OK) {
+      cudaEvent_t done;
+      if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(done, streams[i]);
+        cudaStreamWaitEvent(user, done, 0);
+        cudaEventDestroy(done);
+      }
+    }
+    cudaStreamSynchronize(streams[i]);
+    cudaStreamDestroy(streams[i]);
+    job_release(jobs[i]);
+  }
+  cudaEventDestroy(start);
+  if (s != HELM_OK) return s;
+  helm_status worst = HELM_OK;
+  for (int i = 0; i < n; ++i)
+    if (jobs[i].status != HELM_OK && worst == HELM_OK) worst = jobs[i].status;
+  return worst;
 }
 
 }  // namespace helm

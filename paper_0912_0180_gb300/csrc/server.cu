@@ -1,0 +1,333 @@
+// server.cu -- a solve server with continuous batching.
+//
+// Requests (grid, k(x), preconditioner, solve options, right-hand side on the host) are queued by
+// helm_server_submit and admitted, in arrival order, as soon as both an execution slot and the
+// device-memory budget allow; every admitted request gets its own stream, context and
+// device-resident solve, so requests admitted while others run overlap with them on the GPU.  A
+// worker thread admits, starts and polls; nothing in its loop synchronises the device (allocations
+// and frees are stream-ordered), so a request's completion is noticed as soon as its own stream
+// reaches it.  Latency is measured from submission to the moment the solution is in host memory.
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+struct SolveJob;
+helm_status job_begin(SolveJob& j);
+helm_status job_poll(SolveJob& j, bool block);
+void job_release(SolveJob& j);
+SolveJob* job_new();
+void job_delete(SolveJob* j);
+void job_setup(SolveJob* j, helm_ctx* c, const double2* b, double2* x, const helm_solve_opts* o,
+               helm_solve_info* info, cudaStream_t st);
+bool job_finished(const SolveJob* j);
+helm_status job_status(const SolveJob* j);
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static long axis_n(const helm_grid& g, int a) {
+  int lo = g.n_layer[a][0], hi = g.n_layer[a][1];
+  return (long)g.n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+// Device bytes one request holds while it runs (operator, hierarchy, coarse inverse, Krylov
+// workspace, right-hand side and solution), mirroring the allocations of helm_create and of the
+// first helm_solve; an upper bound up to the few kilobytes of per-axis tables.
+extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc, const helm_solve_opts* o) {
+  if (!g || !pc || !o || g->dim < 1 || g->dim > 3) return 0;
+  long n[3] = {1, 1, 1};
+  long N = 1;
+  for (int a = 0; a < g->dim; ++a) { n[a] = axis_n(*g, a); N *= n[a]; }
+  size_t bytes = 0;
+  for (int a = 0; a < g->dim; ++a) bytes += (size_t)(n[a] + 1) * 16 * 4;  // H tables
+  bytes += (size_t)N * 8;                                                 // phi
+  bool pcon = pc->kind != HELM_PC_NONE;
+  size_t esz = pcon && pc->mg_dtype == HELM_C64 ? 8 : 16;
+  if (pcon) {
+    long m[3] = {n[0], n[1], n[2]};
+    long Nl = N;
+    int levels = 0;
+    long last = N;
+    for (;;) {
+      ++levels;
+      for (int a = 0; a < g->dim; ++a) bytes += (size_t)(m[a] + 1) * (16 * 4 + 8 * 3);
+      bytes += (size_t)Nl * (8 + 4 + 2 * esz + (levels == 1 ? 1 : 3) * esz);
+      last = Nl;
+      bool all_small = true;
+      long min_n = 1L << 40;
+      for (int a = 0; a < g->dim; ++a) {
+        if (m[a] > pc->coarse_max) all_small = false;
+        if (m[a] < min_n) min_n = m[a];
+      }
+      if (levels >= pc->max_levels || all_small || min_n < 3) break;
+      Nl = 1;
+      for (int a = 0; a < g->dim; ++a) { m[a] /= 2; Nl *= m[a]; }
+    }
+    bytes += (size_t)last * last * esz;     // coarse inverse
+    bytes += (size_t)last * last * 32 + 4;  // its FP64 factorisation (transient)
+    if (esz == 8) bytes += (size_t)N * 8;   // conversion buffer
+  }
+  // Krylov workspace
+  if (o->method == HELM_IDR) bytes += (size_t)N * ((5 + 3 * (size_t)o->s) * 16 + esz);
+  else bytes += (size_t)N * (9 * 16 + 2 * esz);
+  bytes += (size_t)N * 32;  // the request's own b and x on the device
+  bytes += 64 * 1024;       // state and partial sums
+  return bytes;
+}
+
+struct helm_server {
+  struct Req {
+    uint64_t id = 0;
+    helm_grid grid{};
+    helm_precond pc{};
+    helm_solve_opts opts{};
+    double k0 = 0.0;
+    std::vector<double> phi;
+    std::vector<std::complex<double>> b, shadow;
+    void* x_host = nullptr;
+    long n = 0;
+    size_t bytes = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    helm_solve_info info{};
+    helm_status status = HELM_OK;
+    // running
+    helm_ctx* ctx = nullptr;
+    void* bd = nullptr;
+    void* xd = nullptr;
+    SolveJob* job = nullptr;
+    int slot = -1;
+  };
+  size_t budget = 0, used = 0;
+  int max_active = 1;
+  int dev = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> queue;
+  std::vector<Req*> active;
+  std::unordered_map<uint64_t, Req*> reqs;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> slot_busy;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::string last_error;
+
+  void finish(Req* r, helm_status st) {
+    cudaStream_t s = r->slot >= 0 ? streams[r->slot] : (cudaStream_t)0;
+    if (r->ctx && r->xd && r->job && job_finished(r->job)) {  // the solution, or the last iterate
+      cudaMemcpyAsync(r->x_host, r->xd, sizeof(double2) * r->n, cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+    }
+    if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
+    if (r->bd) cudaFreeAsync(r->bd, s);
+    if (r->xd) cudaFreeAsync(r->xd, s);
+    if (r->ctx) ctx_release_on(r->ctx, s);
+    r->bd = r->xd = nullptr;
+    r->ctx = nullptr;
+    r->t_done = now_s();
+    std::lock_guard<std::mutex> lk(mu);
+    if (r->status == HELM_OK) r->status = st;
+    r->info.status = r->status;
+    r->state = 2;
+    used -= r->bytes;
+    if (r->slot >= 0) slot_busy[r->slot] = false;
+    active.erase(std::find(active.begin(), active.end(), r));
+    cv_done.notify_all();
+  }
+
+  helm_status start(Req* r) {
+    cudaStream_t s = streams[r->slot];
+    helm_kspec k{r->k0, r->phi.empty() ? nullptr : r->phi.data()};
+    helm_status st = helm_create(&r->grid, &k, &r->pc, (void*)s, &r->ctx);
+    if (st != HELM_OK) return st;
+    size_t vb = sizeof(double2) * r->n;
+    if (cudaMallocAsync(&r->bd, vb, s) != cudaSuccess || cudaMallocAsync(&r->xd, vb, s) != cudaSuccess) {
+      cudaGetLastError();
+      return HELM_ERR_OOM;
+    }
+    if (cudaMemcpyAsync(r->bd, r->b.data(), vb, cudaMemcpyHostToDevice, s) != cudaSuccess) return HELM_ERR_CUDA;
+    if (!r->shadow.empty()) r->opts.shadow = r->shadow.data();
+    r->opts.history = nullptr;
+    r->opts.host_loop = 0;
+    r->job = job_new();
+    job_setup(r->job, r->ctx, (const double2*)r->bd, (double2*)r->xd, &r->opts, &r->info, s);
+    r->t_start = now_s();
+    return job_begin(*r->job);
+  }
+
+  void run() {
+    cudaSetDevice(dev);
+    for (;;) {
+      std::vector<Req*> to_start;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        if (stop && queue.empty() && active.empty()) return;
+        while (!queue.empty() && (int)active.size() < max_active && used + queue.front()->bytes <= budget) {
+          Req* r = queue.front();
+          queue.pop_front();
+          for (int i = 0; i < (int)slot_busy.size(); ++i)
+            if (!slot_busy[i]) { slot_busy[i] = true; r->slot = i; break; }
+          used += r->bytes;
+          r->state = 1;
+          active.push_back(r);
+          to_start.push_back(r);
+        }
+        if (to_start.empty() && active.empty()) {
+          cv_work.wait_for(lk, std::chrono::milliseconds(5));
+          continue;
+        }
+      }
+      for (Req* r : to_start) {
+        helm_status st = start(r);
+        if (st != HELM_OK) finish(r, st);
+      }
+      bool progressed = !to_start.empty();
+      std::vector<Req*> snapshot;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        snapshot = active;
+      }
+      for (Req* r : snapshot) {
+        if (!r->job) continue;
+        helm_status st = job_poll(*r->job, false);
+        if (st == HELM_ERR_BUSY) continue;
+        progressed = true;
+        if (st != HELM_OK) { finish(r, st); continue; }
+        if (job_finished(r->job)) finish(r, job_status(r->job));
+      }
+      if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+};
+
+extern "C" {
+
+helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server** out) {
+  if (!out || max_active < 1 || max_active > 256 || budget_bytes == 0) {
+    set_error("helm_server_create: bad arguments");
+    return HELM_ERR_ARG;
+  }
+  helm_server* s = new helm_server();
+  s->budget = budget_bytes;
+  s->max_active = max_active;
+  cudaGetDevice(&s->dev);
+  s->streams.resize(max_active);
+  s->slot_busy.assign(max_active, false);
+  for (int i = 0; i < max_active; ++i) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
+      delete s;
+      return cuda_check(e, "helm_server_create: stream");
+    }
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return HELM_OK;
+}
+
+helm_status helm_server_submit(helm_server* s, const helm_request* rq, uint64_t* ticket) {
+  if (!s || !rq || !ticket || !rq->b || !rq->x) { set_error("helm_server_submit: NULL argument"); return HELM_ERR_ARG; }
+  if (rq->grid.dim < 1 || rq->grid.dim > 3) { set_error("helm_server_submit: grid.dim"); return HELM_ERR_ARG; }
+  auto* r = new helm_server::Req();
+  r->grid = rq->grid;
+  r->pc = rq->pc;
+  r->opts = rq->opts;
+  r->k0 = rq->k.k0;
+  r->n = 1;
+  for (int a = 0; a < rq->grid.dim; ++a) r->n *= axis_n(rq->grid, a);
+  if (r->n < 1) { delete r; set_error("helm_server_submit: empty grid"); return HELM_ERR_ARG; }
+  if (rq->k.phi) r->phi.assign(rq->k.phi, rq->k.phi + r->n);
+  const std::complex<double>* b = (const std::complex<double>*)rq->b;
+  r->b.assign(b, b + r->n);
+  if (rq->opts.method == HELM_IDR) {
+    if (!rq->opts.shadow || rq->opts.s < 1 || rq->opts.s > 8) { delete r; set_error("helm_server_submit: IDR shadow"); return HELM_ERR_ARG; }
+    const std::complex<double>* sh = (const std::complex<double>*)rq->opts.shadow;
+    r->shadow.assign(sh, sh + (size_t)rq->opts.s * r->n);
+  }
+  r->x_host = rq->x;
+  r->bytes = helm_estimate_bytes(&rq->grid, &rq->pc, &rq->opts);
+  if (r->bytes > s->budget) {
+    delete r;
+    set_error("helm_server_submit: the request needs more device memory than the whole budget");
+    return HELM_ERR_OOM;
+  }
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+  }
+  s->cv_work.notify_one();
+  *ticket = r->id;
+  return HELM_OK;
+}
+
+helm_status helm_server_poll(helm_server* s, uint64_t ticket, helm_solve_info* info, double* latency_s) {
+  if (!s) { set_error("helm_server_poll: NULL server"); return HELM_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) { set_error("helm_server_poll: unknown ticket"); return HELM_ERR_ARG; }
+  helm_server::Req* r = it->second;
+  if (r->state != 2) return HELM_ERR_BUSY;
+  if (info) *info = r->info;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  return r->status;
+}
+
+helm_status helm_server_wait(helm_server* s, uint64_t ticket, helm_solve_info* info, double* latency_s) {
+  if (!s) { set_error("helm_server_wait: NULL server"); return HELM_ERR_ARG; }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) { set_error("helm_server_wait: unknown ticket"); return HELM_ERR_ARG; }
+  helm_server::Req* r = it->second;
+  s->cv_done.wait(lk, [r] { return r->state == 2; });
+  if (info) *info = r->info;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  return r->status;
+}
+
+helm_status helm_server_stats(helm_server* s, int* queued, int* active, size_t* used_bytes) {
+  if (!s) return HELM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (queued) *queued = (int)s->queue.size();
+  if (active) *active = (int)s->active.size();
+  if (used_bytes) *used_bytes = s->used;
+  return HELM_OK;
+}
+
+void helm_server_destroy(helm_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (cudaStream_t st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

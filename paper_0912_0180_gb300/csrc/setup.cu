@@ -427,27 +427,29 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   c->nco = n;
   double2 *A = nullptr, *X = nullptr;
   int* flag = nullptr;
-  HELM_CUDA(cudaMalloc(&A, sizeof(double2) * (size_t)n * n));
-  cudaError_t e1 = cudaMalloc(&X, sizeof(double2) * (size_t)n * n);
-  cudaError_t e2 = cudaMalloc(&flag, sizeof(int));
+  HELM_CUDA(cudaMallocAsync(&A, sizeof(double2) * (size_t)n * n, st));
+  cudaError_t e1 = cudaMallocAsync(&X, sizeof(double2) * (size_t)n * n, st);
+  cudaError_t e2 = cudaMallocAsync(&flag, sizeof(int), st);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    cudaFree(A); cudaFree(X); cudaFree(flag);
-    return cuda_check(e1 != cudaSuccess ? e1 : e2, "cudaMalloc(coarse)");
+    if (X) cudaFreeAsync(X, st);
+    if (flag) cudaFreeAsync(flag, st);
+    cudaFreeAsync(A, st);
+    return cuda_check(e1 != cudaSuccess ? e1 : e2, "cudaMallocAsync(coarse)");
   }
   cudaMemsetAsync(flag, 0, sizeof(int), st);
   k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
   int thr = 1024;
   k_gauss_jordan<<<1, thr, thr * (sizeof(double) + sizeof(int)), st>>>(A, X, n, flag);
   if ((rc = ctx_alloc(c, &c->coarse_inv, esz * (size_t)n * n)) != HELM_OK) {
-    cudaFree(A); cudaFree(X); cudaFree(flag);
+    cudaFreeAsync(A, st); cudaFreeAsync(X, st); cudaFreeAsync(flag, st);
     return rc;
   }
   if (f32) k_c128_to_c64<<<ceil_div((long)n * n, 256), 256, 0, st>>>(X, (float2*)c->coarse_inv, (long)n * n);
   else cudaMemcpyAsync(c->coarse_inv, X, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
   int hflag = 0;
   cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(A, st); cudaFreeAsync(X, st); cudaFreeAsync(flag, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(A); cudaFree(X); cudaFree(flag);
   HELM_CUDA(e);
   if (hflag) {
     set_error("coarsest operator is singular");

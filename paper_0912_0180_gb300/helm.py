@@ -152,3 +152,114 @@ class Helm:
         h = hist[: info.matvecs].cpu().numpy() if hist is not None else None
         return x, Info(info.status, info.iters, info.matvecs, info.restarts, info.rel_res_recur,
                        info.rel_res_true, info.kernels, h)
+
+
+def solve_batch(instances, bs, *, method: int = 0, s: int = 4, tol: float = 1e-6, maxmv: int = 2000,
+                max_restarts: int = 3, shadows=None, stream=None):
+    """helm_solve_batch: solve every (Helm instance, rhs) pair at once; returns (xs, infos)."""
+    lib = L.load()
+    n = len(instances)
+    xs = [torch.empty(h.n, dtype=torch.complex128, device=b.device) for h, b in zip(instances, bs)]
+    opts = (L.SolveOpts * max(n, 1))()
+    keep = []
+    for i in range(n):
+        o = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None, 0)
+        if shadows is not None and shadows[i] is not None:
+            arr = np.ascontiguousarray(shadows[i], dtype=np.complex128)
+            keep.append(arr)
+            o.shadow = arr.ctypes.data
+        opts[i] = o
+    infos = (L.SolveInfo * max(n, 1))()
+    cs = (C.c_void_p * max(n, 1))(*[h._h.value for h in instances])
+    bp = (C.c_void_p * max(n, 1))(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * max(n, 1))(*[x.data_ptr() for x in xs])
+    st = lib.helm_solve_batch(cs, bp, xp, n, opts, infos, C.c_void_p(_stream(stream)))
+    _check(st, "helm_solve_batch", (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN))
+    out = [Info(infos[i].status, infos[i].iters, infos[i].matvecs, infos[i].restarts, infos[i].rel_res_recur,
+                infos[i].rel_res_true, infos[i].kernels) for i in range(n)]
+    return xs, out
+
+
+class Server:
+    """helm_server_*: continuous-batching solve server (requests from host memory)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 4):
+        self._lib = L.load()
+        h = C.c_void_p()
+        _check(self._lib.helm_server_create(int(budget_bytes), int(max_active), C.byref(h)), "helm_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, problem, precond, *, mg_dtype: str = "c64", method: int = 0, s: int = 4,
+               tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3, shadow=None) -> int:
+        rq = L.Request()
+        g = rq.grid
+        g.dim = problem.dim
+        for a in range(3):
+            g.n_int[a] = problem.n_int[a]
+            g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
+            g.extent[a] = problem.extent[a]
+        g.theta_gamma = problem.theta_gamma
+        rq.k.k0 = problem.k0
+        phi = None
+        if problem.phi is not None:
+            phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
+            rq.k.phi = phi.ctypes.data
+        rq.pc = L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
+                          complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
+                          precond.omega, precond.max_levels, precond.coarse_max,
+                          L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128, 0)
+        rq.opts = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None, 0)
+        sh = None
+        if shadow is not None:
+            sh = np.ascontiguousarray(shadow, dtype=np.complex128)
+            rq.opts.shadow = sh.ctypes.data
+        b = np.ascontiguousarray(problem.b, dtype=np.complex128)
+        x = np.zeros_like(b)
+        rq.b = b.ctypes.data
+        rq.x = x.ctypes.data
+        t = C.c_uint64()
+        _check(self._lib.helm_server_submit(self._h, C.byref(rq), C.byref(t)), "helm_server_submit")
+        self._keep[t.value] = x
+        return t.value
+
+    def wait(self, ticket: int):
+        """Blocks until the request is done; returns (x, Info, latency_s)."""
+        info = L.SolveInfo()
+        lat = C.c_double()
+        st = self._lib.helm_server_wait(self._h, ticket, C.byref(info), C.byref(lat))
+        _check(st, "helm_server_wait", (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN))
+        x = self._keep.pop(ticket)
+        return x, Info(info.status, info.iters, info.matvecs, info.restarts, info.rel_res_recur,
+                       info.rel_res_true, info.kernels), lat.value
+
+    def stats(self):
+        q, a, u = C.c_int(), C.c_int(), C.c_size_t()
+        self._lib.helm_server_stats(self._h, C.byref(q), C.byref(a), C.byref(u))
+        return q.value, a.value, u.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.helm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(problem, precond, mg_dtype: str = "c64", method: int = 0, s: int = 4) -> int:
+    lib = L.load()
+    g = L.Grid()
+    g.dim = problem.dim
+    for a in range(3):
+        g.n_int[a] = problem.n_int[a]
+        g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
+        g.extent[a] = problem.extent[a]
+    pc = L.Precond(precond.kind, precond.theta_beta, 0.0, 0.0, precond.nu1, precond.nu2, precond.smoother,
+                   precond.omega, precond.max_levels, precond.coarse_max,
+                   L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128, 0)
+    o = L.SolveOpts(method, s, 1e-6, 1000, 3, None, None, 0)
+    return int(lib.helm_estimate_bytes(C.byref(g), C.byref(pc), C.byref(o)))

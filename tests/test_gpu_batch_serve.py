@@ -1,0 +1,112 @@
+"""Batched and served execution: many uneven instances at once give, instance by instance, the
+result of a lone solve (bitwise: every solve's reductions have a fixed order and instances share
+nothing), and the server admits requests against its device-memory budget."""
+import numpy as np
+import pytest
+import torch
+
+import helm_inputs as hi
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _instances():
+    """Uneven 2D and 3D instances: sizes, layers, k fields, preconditioners and smoothers differ."""
+    out = []
+    specs = [
+        (2, 47, 8, 10.0, "const", hi.PC_CSG_UNIFORM, hi.SM_JACOBI),
+        (2, 96, 16, 25.0, "bump", hi.PC_CSL, hi.SM_JACOBI),
+        (2, (70, 33), ((6, 0), (4, 9)), 12.0, "bump", hi.PC_CSG_UNIFORM, hi.SM_RBGS),
+        (3, 15, 3, 6.0, "const", hi.PC_CSG_UNIFORM, hi.SM_RBGS),
+        (2, 130, 20, 30.0, "const", hi.PC_CSG_INTERIOR, hi.SM_JACOBI),
+        (3, (14, 11, 13), ((2, 3), (0, 2), (3, 0)), 5.0, "bump", hi.PC_CSL, hi.SM_JACOBI),
+    ]
+    for i, (dim, n_int, nl, k0, kind, pck, sm) in enumerate(specs):
+        p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=k0, phi_kind=kind, rhs="gauss", seed=100 + i,
+                            bump_centre=(0.45, 0.55, 0.5))
+        pc = hi.Precond(kind=pck, theta_beta=0.3, shift=1 + 0.5j, smoother=sm, omega=0.5)
+        out.append((p, pc))
+    return out
+
+
+@pytest.mark.parametrize("mg", ["c64", "c128"])
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
+def test_batch_equals_lone_solves(mg, method):
+    from paper_0912_0180_gb300.helm import Helm, solve_batch
+    inst = _instances()
+    hs = [Helm(p, pc, mg_dtype=mg) for p, pc in inst]
+    bs = [torch.from_numpy(p.b).cuda() for p, _ in inst]
+    shadows = [hi.shadow_space(p.n, 4, seed=5 + i) for i, (p, _) in enumerate(inst)]
+    alone = []
+    for h, b, sh in zip(hs, bs, shadows):
+        x, info = h.solve(b, method=method, tol=1e-8, maxmv=3000, shadow=sh)
+        alone.append((x.clone(), info))
+    xs, infos = solve_batch(hs, bs, method=method, tol=1e-8, maxmv=3000, shadows=shadows)
+    for (xa, ia), xb, ib in zip(alone, xs, infos):
+        assert ib.status == 0 and ia.status == 0
+        assert torch.equal(xa, xb)
+        assert ia.matvecs == ib.matvecs and ia.rel_res_true == ib.rel_res_true
+    # and the batch is right: the FP64 multigrid batch against the oracle's solutions
+    if mg == "c128":
+        for (p, pc), xb in zip(inst, xs):
+            xo, io = Oracle(p, pc).solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-12, maxmv=4000))
+            assert np.linalg.norm(xb.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
+    for h in hs:
+        h.close()
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    from paper_0912_0180_gb300.helm import Helm, Server, estimate_bytes
+    inst = _instances()
+    alone = []
+    for p, pc in inst:
+        h = Helm(p, pc, mg_dtype="c64")
+        x, info = h.solve(torch.from_numpy(p.b).cuda(), tol=1e-7, maxmv=3000)
+        alone.append((x.cpu().numpy(), info))
+        h.close()
+    sizes = [estimate_bytes(p, pc) for p, pc in inst]
+    budget = int(max(sizes) + sorted(sizes)[0])  # at most two of the requests fit at once
+    srv = Server(budget, max_active=3)
+    tickets = [srv.submit(p, pc, tol=1e-7, maxmv=3000) for p, pc in inst]
+    queued, active, used = srv.stats()
+    assert used <= budget
+    results = [srv.wait(t) for t in tickets]
+    for (xa, ia), (xs, info, lat) in zip(alone, results):
+        assert info.status == 0 and lat > 0
+        assert np.array_equal(xa, xs)
+        assert info.matvecs == ia.matvecs
+    assert srv.stats()[2] == 0  # every byte admitted has been returned
+    # a request bigger than the whole budget is refused at submission
+    from paper_0912_0180_gb300.helm import HelmError
+    with pytest.raises(HelmError):
+        Server(1000, 1).submit(*inst[0])
+    srv.close()
+
+
+def test_server_overlaps_requests():
+    """Continuous batching: with room for all of them, requests run concurrently (the server's
+    active count exceeds one while they run) and all complete."""
+    import time
+    from paper_0912_0180_gb300.helm import Server
+    inst = _instances()
+    srv = Server(64 << 30, max_active=8)
+    tickets = [srv.submit(p, pc, tol=1e-7, maxmv=3000) for p, pc in inst]
+    seen = 0
+    for _ in range(2000):
+        seen = max(seen, srv.stats()[1])
+        if seen > 1:
+            break
+        time.sleep(0.0005)
+    res = [srv.wait(t) for t in tickets]
+    assert all(r[1].status == 0 for r in res)
+    assert seen > 1
+    srv.close()
