@@ -1,0 +1,370 @@
+"""The other workloads of bench.py (`--workload`): each prints one JSON line of its own.
+
+  3d160     128^3 interior + 16-node ECS layers (160^3 = 4,096,000 unknowns), k = 40 constant,
+            centre point source; one Bi-CGSTAB solve to 1e-6 per step, preconditioned by one CSG
+            (theta_beta = 0.3) V(1,1) cycle with red-black Gauss-Seidel on 4 levels (coarsest
+            20^3 = 8000 unknowns, dense inverse).  `value` is the all-FP64 path; `fp32_mg` is the
+            complex-FP32 V-cycle under FP64 Bi-CGSTAB and FP64 true residual, with its solution's
+            relative difference from the FP64 path's.
+  batch256  256 independent 2D instances (interior 63..511 per axis, 16..32-node layers, kh in
+            [0.3, 0.6], constant or bump k, seeded point sources); one step solves all of them with
+            helm_solve_batch (Bi-CGSTAB, CSG omega-Jacobi V(1,1), 1e-6).
+  serve     a Poisson-arrival stream (mean 200 requests/s) of 2D (127^2 .. 1023^2 interior) and 3D
+            (64^3 .. 160^3 interior) requests with 1..8 point-source right-hand sides each, submitted
+            at their arrival times to the solve server (150 GB budget); reports right-hand-side
+            solves/s and the server's submit-to-completion latencies.
+
+Every timed solve is certified by the FP64 true residual; a step whose solves did not all reach
+1e-6 aborts the run.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import time
+
+import numpy as np
+
+import helm_inputs as hi
+
+TOL = 1e-6
+
+
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q))
+
+
+def _base(args, metric_value, ms_step, world, cfg, dtype):
+    import bench
+    return {"metric": bench.METRIC, "value": metric_value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg}
+
+
+def _check(infos, what):
+    for i in infos:
+        if i.status != 0 or not i.rel_res_true < TOL:
+            raise SystemExit(f"{what}: a timed solve did not converge: {i}")
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    g.build()
+    dev = torch.device("cuda", local)
+    ranks = bench.Ranks(dist if world > 1 else None, dev)
+    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve}[args.workload]
+    line = fn(args, torch, ranks, dev, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---- 3D ------------------------------------------------------------------------------------
+
+def _pc3d():
+    return hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS, max_levels=4)
+
+
+def run_3d(args, torch, ranks, dev, local):
+    import bench
+    from paper_0912_0180_gb300 import _lib as L
+    from paper_0912_0180_gb300.helm import Helm
+    p = hi.workload_3d_128()
+    b_dev = torch.from_numpy(p.b).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx, create_s = {}, {}
+    for mg in ("c128", "c64"):
+        t = time.perf_counter()
+        ctx[mg] = Helm(p, _pc3d(), mg_dtype=mg)
+        torch.cuda.synchronize()
+        create_s[mg] = time.perf_counter() - t
+
+    def step(mg, host=None):
+        h = ctx[mg]
+        if host is not None:
+            x, info = h.solve(host["b"].to(dev, non_blocking=True), tol=TOL, maxmv=3000)
+            host["x"].copy_(x, non_blocking=True)
+        else:
+            x, info = h.solve(b_dev, tol=TOL, maxmv=3000)
+        return x, info
+
+    def timed(mg, e2e=False):
+        host = None
+        if e2e:
+            host = {"b": torch.from_numpy(p.b).pin_memory(),
+                    "x": torch.empty(p.n, dtype=torch.complex128).pin_memory()}
+        for _ in range(args.warmup):
+            step(mg, host)
+        ms, infos, x = [], [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ranks.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, info = step(mg, host)
+            e1.record()
+            ranks.barrier()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return ms, infos, x
+
+    with bench.ClockSampler(local) as clk:
+        ms64, inf64, x64 = timed("c128")
+        ms32, inf32, x32 = timed("c64")
+    e2e_ms, _, _ = timed("c64", e2e=True)
+    _check(inf64 + inf32, "3d160")
+    diff = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    step64 = ranks.max(statistics.mean(ms64))
+    step32 = ranks.max(statistics.mean(ms32))
+    kern = _kernels_3d(torch, L, ctx, p, dev, flush)
+    cfg = {"workload": p.name, "grid": "128^3 interior + 16 ECS nodes per side (160^3 unknowns)",
+           "n_unknowns": p.n, "solves_per_step": 1, "solver": "Bi-CGSTAB, tol 1e-6 (FP64 true residual)",
+           "multigrid": "CSG theta_beta=0.3, V(1,1) red-black Gauss-Seidel, 4 levels, FW, trilinear, "
+                        "dense inverse of the 20^3 coarsest level",
+           "l2": "flushed (512 MiB device write) before every timed step"}
+    line = _base(args, ranks.job_rate(1, step64), step64, ranks.world, cfg, "c128")
+    line.update({
+        "latency_ms": {"p50": _pct(ms64, 50), "p99": _pct(ms64, 99)},
+        "matvecs": inf64[-1].matvecs, "max_true_rel_res": max(i.rel_res_true for i in inf64),
+        "fp32_mg": {"value": ranks.world / (step32 / 1000), "unit": "solves/s", "ms_per_step": step32,
+                    "dtype": "c64 V-cycle, c128 Bi-CGSTAB and true residual",
+                    "latency_ms": {"p50": _pct(ms32, 50), "p99": _pct(ms32, 99)},
+                    "matvecs": inf32[-1].matvecs, "max_true_rel_res": max(i.rel_res_true for i in inf32),
+                    "rel_diff_vs_fp64_solution": diff},
+        "create_s": create_s,
+        "clocks": clk.summary(),
+        "e2e": {"value": ranks.world / (ranks.max(statistics.mean(e2e_ms)) / 1000), "unit": "solves/s",
+                "path": "fp32_mg through helm_solve with pinned host b and x",
+                "h2d_bytes_per_step": p.n * 16, "d2h_bytes_per_step": p.n * 16},
+        "gpu_launches": int(sum(i.kernels for i in inf64) + sum(i.kernels for i in inf32)),
+        "roofline": kern["dominant"], "kernels": kern["table"],
+    })
+    for h in ctx.values():
+        h.close()
+    return line
+
+
+def _time_cold(torch, flush, fn, reps=10):
+    st = torch.cuda.current_stream()
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts) / 1000.0
+
+
+# FP64 operations of one Helmholtz matvec point in the 3D uniform interior (k_h_apply): six
+# neighbour additions (10), the scale (2), the diagonal 6/h^2 - k^2 (1) and its complex product
+# with x added to the neighbour sum (4); counted as operations, not FMA-doubled flops.
+H3D_FP64_OPS_PER_POINT = 17
+
+
+def _kernels_3d(torch, L, ctx, p, dev, flush):
+    n = p.n
+    fp64_ops_peak = 152 * 2 * 2.07e9 / 1e12  # FP64 operations per second (2 per clock per SM), in T/s
+    table = {}
+    x = torch.randn(n, dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    h = ctx["c128"]
+    t = _time_cold(torch, flush, lambda: h.apply(x, out=y))
+    table["k_h_apply_c128"] = {"us": t * 1e6, "bytes": n * 40, "GB/s": n * 40 / t / 1e9,
+                               "fp64_ops": n * H3D_FP64_OPS_PER_POINT}
+    for mg, dt, esz in (("c128", torch.complex128, 16), ("c64", torch.complex64, 8)):
+        hh = ctx[mg]
+        f = torch.randn(n, dtype=dt, device=dev)
+        u = torch.zeros(n, dtype=dt, device=dev)
+        t = _time_cold(torch, flush, lambda: hh.level_op(L.HELM_OP_SMOOTH, 0, u, f, u))
+        table[f"rbgs_sweep_{mg}"] = {"us": t * 1e6, "bytes": n * 4 * esz, "GB/s": n * 4 * esz / t / 1e9}
+        r = torch.randn(n, dtype=torch.complex128, device=dev)
+        z = torch.empty(n, dtype=dt, device=dev)
+        t = _time_cold(torch, flush, lambda: hh.vcycle(r, out=z))
+        table[f"vcycle_{mg}"] = {"us": t * 1e6}
+    a = table["k_h_apply_c128"]
+    achieved = a["fp64_ops"] / (a["us"] / 1e6) / 1e12
+    dom = {"kernel": "k_h_apply<double, 3> (FP64 Helmholtz matvec; the stencil of the Krylov kernels)",
+           "bound": "alu", "achieved": achieved, "peak": fp64_ops_peak, "unit": "T FP64 op/s",
+           "frac": achieved / fp64_ops_peak, "traffic": None,
+           "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
+           "launch_us": a["us"]}
+    return {"dominant": dom, "table": table}
+
+
+# ---- batch ---------------------------------------------------------------------------------
+
+def _pc2d():
+    return hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+
+
+def run_batch(args, torch, ranks, dev, local):
+    import bench
+    from paper_0912_0180_gb300.helm import Helm, solve_batch
+    inst = hi.workload_batch_2d(256)
+    bs = [torch.from_numpy(p.b).to(dev) for p in inst]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    with bench.ClockSampler(local) as clk:
+        for mg in ("c128", "c64"):
+            hs = [Helm(p, _pc2d(), mg_dtype=mg) for p in inst]
+            for _ in range(args.warmup):
+                solve_batch(hs, bs, tol=TOL, maxmv=4000)
+            ms, infos = [], []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                ranks.barrier()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                xs, inf = solve_batch(hs, bs, tol=TOL, maxmv=4000)
+                e1.record()
+                ranks.barrier()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                infos += inf
+            _check(infos, "batch256")
+            one = None
+            if mg == "c64":  # the same instances one after another, for the batching gain
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for h, b in zip(hs, bs):
+                    h.solve(b, tol=TOL, maxmv=4000)
+                e1.record()
+                torch.cuda.synchronize()
+                one = e0.elapsed_time(e1)
+                # e2e: host right-hand sides in, host solutions out, through the public calls
+                hb = [torch.from_numpy(p.b).pin_memory() for p in inst]
+                hx = [torch.empty(p.n, dtype=torch.complex128).pin_memory() for p in inst]
+                e2e = []
+                for _ in range(max(1, args.steps)):
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    bd = [b.to(dev, non_blocking=True) for b in hb]
+                    xs2, _ = solve_batch(hs, bd, tol=TOL, maxmv=4000)
+                    for xh, xd in zip(hx, xs2):
+                        xh.copy_(xd, non_blocking=True)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    e2e.append(e0.elapsed_time(e1))
+                res["e2e_ms"] = statistics.mean(e2e)
+            res[mg] = {"ms": ranks.max(statistics.mean(ms)), "infos": infos, "one_by_one_ms": one}
+            for h in hs:
+                h.close()
+    nb = len(inst)
+    r64, r32 = res["c128"], res["c64"]
+    cfg = {"workload": "batch-2d-256", "instances": nb, "n_unknowns_total": int(sum(p.n for p in inst)),
+           "sizes": "interior {63,127,255,511}^2, 16..32-node layers, kh 0.3..0.6, const or bump k",
+           "solver": "helm_solve_batch: Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
+           "l2": "flushed (512 MiB device write) before every timed step"}
+    line = _base(args, ranks.job_rate(nb, r64["ms"]), r64["ms"], ranks.world, cfg, "c128")
+    lat64 = [i.matvecs for i in r64["infos"]]
+    line.update({
+        "matvecs_total_per_step": int(sum(lat64) / max(1, args.steps)),
+        "fp32_mg": {"value": nb * ranks.world / (r32["ms"] / 1000), "unit": "solves/s", "ms_per_step": r32["ms"],
+                    "dtype": "c64 V-cycle, c128 Krylov and true residual",
+                    "one_by_one_solves_per_s": nb / (r32["one_by_one_ms"] / 1000),
+                    "max_true_rel_res": max(i.rel_res_true for i in r32["infos"])},
+        "max_true_rel_res": max(i.rel_res_true for i in r64["infos"]),
+        "clocks": clk.summary(),
+        "e2e": {"value": nb / (res["e2e_ms"] / 1000), "unit": "solves/s",
+                "path": "fp32_mg batch with pinned host right-hand sides and solutions",
+                "h2d_bytes_per_step": int(sum(p.n for p in inst) * 16),
+                "d2h_bytes_per_step": int(sum(p.n for p in inst) * 16)},
+        "gpu_launches": int(sum(i.kernels for i in r64["infos"]) + sum(i.kernels for i in r32["infos"])),
+    })
+    return line
+
+
+# ---- serve ---------------------------------------------------------------------------------
+
+def _stream(torch, reqs, mg, budget):
+    """Submits every request at its arrival time; returns wall seconds, per-request results."""
+    from paper_0912_0180_gb300.helm import Server
+    srv = Server(budget, max_active=8)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(srv.submit(r.problem, _pc2d(), mg_dtype=mg, tol=TOL, maxmv=4000, rhs=r.rhs))
+    out = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    srv.close()
+    return wall, out
+
+
+def run_serve(args, torch, ranks, dev, local):
+    import bench
+    reqs = hi.workload_serve()
+    budget = 150 * 10**9
+    nsol = int(sum(r.rhs.shape[0] for r in reqs))
+    res = {}
+    with bench.ClockSampler(local) as clk:
+        for mg in ("c128", "c64"):
+            _stream(torch, reqs[:4], mg, budget)  # warm-up: the first requests of the stream
+            walls, outs = [], None
+            for _ in range(args.steps):
+                wall, outs = _stream(torch, reqs, mg, budget)
+                walls.append(wall)
+                for x, info, lat in outs:
+                    if info.status != 0 or not info.rel_res_true < TOL:
+                        raise SystemExit(f"serve: a request did not converge: {info}")
+            res[mg] = (ranks.max(statistics.mean(walls)), outs)
+    w64, o64 = res["c128"]
+    w32, o32 = res["c64"]
+    diff = max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(o32, o64))
+    lat64 = [o[2] * 1000 for o in o64]
+    lat32 = [o[2] * 1000 for o in o32]
+    cfg = {"workload": "serve-stream-32", "requests": len(reqs), "rhs_solves": nsol,
+           "arrivals": "Poisson, mean 200 requests/s", "mix": "3/4 2D (127..1023 interior, 32-node layers), "
+           "1/4 3D (64..160 interior, 16-node layers), 1..8 point-source right-hand sides each",
+           "server": "150 GB budget, 8 slots", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
+           "timing": "wall clock from the first arrival to the last completion (host in, host out)"}
+    line = _base(args, ranks.job_rate(nsol, w64 * 1000), w64 * 1000, ranks.world, cfg, "c128")
+    line.update({
+        "latency_ms": {"p50": _pct(lat64, 50), "p99": _pct(lat64, 99)},
+        "requests_per_s": len(reqs) / w64,
+        "fp32_mg": {"value": nsol / w32, "unit": "solves/s", "ms_per_step": w32 * 1000,
+                    "requests_per_s": len(reqs) / w32,
+                    "latency_ms": {"p50": _pct(lat32, 50), "p99": _pct(lat32, 99)},
+                    "max_rel_diff_vs_fp64_solution": diff,
+                    "max_true_rel_res": max(o[1].rel_res_true for o in o32)},
+        "max_true_rel_res": max(o[1].rel_res_true for o in o64),
+        "clocks": clk.summary(),
+        "e2e": {"value": nsol / w32, "unit": "solves/s",
+                "path": "the served fp32_mg stream itself: host right-hand sides in, host solutions out",
+                "h2d_bytes_per_step": int(sum(r.rhs.nbytes for r in reqs)),
+                "d2h_bytes_per_step": int(sum(r.rhs.nbytes for r in reqs))},
+        "gpu_launches": int(sum(o[1].kernels for o in o64) + sum(o[1].kernels for o in o32)),
+    })
+    return line

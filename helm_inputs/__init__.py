@@ -211,6 +211,44 @@ def workload_batch_2d(count: int = 256, seed: int = BASE_SEED) -> List[Problem]:
 
 
 @dataclasses.dataclass
+class ServeRequest:
+    arrival_s: float          # offset from the start of the stream
+    problem: Problem
+    rhs: np.ndarray           # nrhs x N complex128 point sources
+
+
+def workload_serve(count: int = 32, rate_hz: float = 200.0, frac_3d: float = 0.25,
+                   seed: int = BASE_SEED + 5) -> List[ServeRequest]:
+    """Poisson-arrival request stream: exponential gaps of mean 1/rate_hz; 2D requests with
+    n_int in {127, 255, 511, 1023} and 32-node layers, 3D requests with n_int uniform in
+    [64, 160] and 16-node layers; kh uniform in [0.3, 0.6] (2D) or [0.25, 0.4] (3D); k constant or
+    a Gaussian bump (amplitude 0..0.4, seeded centre); 1..8 right-hand sides per request, each a
+    unit point source at a seeded interior node."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate_hz))
+        dim = 3 if rng.uniform() < frac_3d else 2
+        if dim == 2:
+            n_int, n_l, kh = int(rng.choice([127, 255, 511, 1023])), 32, float(rng.uniform(0.3, 0.6))
+        else:
+            n_int, n_l, kh = int(rng.integers(64, 161)), 16, float(rng.uniform(0.25, 0.4))
+        bump = bool(rng.integers(0, 2))
+        amp = float(rng.uniform(0.0, 0.4)) if bump else 0.0
+        cen = tuple(rng.uniform(0.2, 0.8, 3))
+        p = make_problem(dim, n_int, n_l, theta_gamma=0.5, k0=kh * (n_int - 1),
+                         phi_kind="bump" if bump else "const", bump_amp=amp, bump_centre=cen[:dim],
+                         rhs="point", seed=seed + 1 + i, name=f"serve{i}-{dim}d-{n_int}")
+        nrhs = int(rng.integers(1, 9))
+        rhs = np.zeros((nrhs,) + p.shape[::-1], np.complex128)
+        for k in range(nrhs):
+            idx = tuple(interior_node_index(p, a, int(rng.integers(1, n_int - 1))) for a in range(dim))
+            rhs[(k,) + idx[::-1]] = 1.0
+        out.append(ServeRequest(t, p, rhs.reshape(nrhs, -1)))
+    return out
+
+
+@dataclasses.dataclass
 class Precond:
     """Description of the preconditioner (plain parameters, no arithmetic).
 

@@ -88,11 +88,17 @@ typedef struct {
   int nu1, nu2;         /* 0..8 sweeps */
   int smoother;         /* HELM_SM_JACOBI or HELM_SM_RBGS */
   double omega;         /* Jacobi damping, 0 < omega <= 1 */
-  int max_levels;       /* >= 1 */
+  int max_levels;       /* >= 1; the coarsest level reached must have at most
+                           HELM_COARSE_MAX_UNKNOWNS unknowns (else helm_create: HELM_ERR_ARG) */
   int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
   helm_dtype mg_dtype;  /* HELM_C64: whole V-cycle in complex FP32; HELM_C128: FP64 */
   int flags;            /* HELM_PF_*; 0 = defaults */
 } helm_precond;
+
+/* Largest coarsest level: its dense inverse is built at helm_create by Gauss-Jordan in FP64
+ * (one block up to 512 unknowns, the whole GPU above) and applied as a dense matrix-vector
+ * product in the V-cycle precision; 16384 unknowns take 4 GiB in FP64 during create. */
+#define HELM_COARSE_MAX_UNKNOWNS 16384
 
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
  * same arithmetic as the default fused kernels; for testing the fusion); HELM_PF_NO_PDL
@@ -208,10 +214,18 @@ typedef struct {
   helm_kspec k;          /* k.phi (HOST) is copied at submit */
   helm_precond pc;
   helm_solve_opts opts;  /* opts.shadow (HOST, IDR) is copied at submit; history and host_loop ignored */
-  const void* b;         /* HOST complex128, N entries; copied at submit */
-  void* x;               /* HOST complex128, N entries; written before the request completes and
-                            must stay valid until then */
+  const void* b;         /* HOST complex128, nrhs x N entries (right-hand side after right-hand
+                            side); copied at submit */
+  void* x;               /* HOST complex128, nrhs x N entries; written before the request
+                            completes and must stay valid until then */
+  int nrhs;              /* right-hand sides, 1 .. HELM_MAX_RHS (0 counts as 1); they are solved
+                            one after another on the request's context, whose operator,
+                            hierarchy and Krylov workspace stay on the device in between.  The
+                            completed request's statistics add up iterations, matvecs, restarts
+                            and kernels over its right-hand sides and keep the largest residuals;
+                            a failing right-hand side ends the request with its status */
 } helm_request;
+#define HELM_MAX_RHS 64
 typedef struct helm_server helm_server;
 
 /* Device bytes a request holds while it runs (operator, hierarchy, coarse inverse, Krylov

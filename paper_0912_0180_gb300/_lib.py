@@ -44,7 +44,7 @@ class SolveInfo(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("grid", Grid), ("k", KSpec), ("pc", Precond), ("opts", SolveOpts), ("b", C.c_void_p),
-                ("x", C.c_void_p)]
+                ("x", C.c_void_p), ("nrhs", C.c_int)]
 
 
 _lib = None

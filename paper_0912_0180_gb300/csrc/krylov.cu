@@ -21,6 +21,9 @@
 namespace helm {
 
 constexpr int KT = 256;      // threads per block of the vector kernels
+#ifndef KRYLOV_BLOCKS_PER_SM
+#define KRYLOV_BLOCKS_PER_SM 2
+#endif
 constexpr int SMAX = 8;      // largest IDR shadow dimension
 constexpr int NRED = SMAX + 2;
 
@@ -144,13 +147,18 @@ template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i,
 
 #define GRID_LOOP(i, n) for (long i = blockIdx.x * (long)KT + threadIdx.x; i < (n); i += (long)gridDim.x * KT)
 
-// Stencil kernels walk whole grid rows (fixed j, l): one div/mod per row, not per point.
-#define ROW_LOOP(H, i, j, l, p)                                                   \
-  for (long row_ = blockIdx.x, nrows_ = (long)(H).n[1] * (H).n[2]; row_ < nrows_;  \
-       row_ += gridDim.x)                                                         \
-    for (int j = (int)(row_ % (H).n[1]), l = (int)(row_ / (H).n[1]), i = threadIdx.x; \
-         i < (H).n[0]; i += KT)                                                    \
-      if (const long p = i + row_ * (H).n[0]; true)
+// Stencil kernels walk warp-sized chunks of grid rows: a warp takes 32 consecutive points of
+// one row (fixed j, l), so its loads are coalesced, only the last chunk of a row has idle lanes,
+// and the index arithmetic costs one div/mod per chunk.
+#define ROW_LOOP(H, i, j, l, p)                                                              \
+  for (long ch_ = (blockIdx.x * (long)KT + threadIdx.x) >> 5, nch_ = ((H).n[0] + 31) >> 5,    \
+            nc_ = nch_ * (H).n[1] * (H).n[2];                                                 \
+       ch_ < nc_; ch_ += ((long)gridDim.x * KT) >> 5)                                         \
+    for (long row_ = ch_ / nch_, once_ = 1; once_; once_ = 0)                                 \
+      for (int i = (int)(ch_ - row_ * nch_) * 32 + (threadIdx.x & 31), j = (int)(row_ % (H).n[1]), \
+               l = (int)(row_ / (H).n[1]);                                                    \
+           i < (H).n[0]; i = (H).n[0])                                                        \
+        if (const long p = i + row_ * (H).n[0]; true)
 
 // ---- shared kernels ----------------------------------------------------------------------
 
@@ -840,9 +848,9 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
     long n = c->n;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
-    // two blocks per SM: each thread then reduces several points before the (FP64, shuffle)
+    // a few blocks per SM: each thread then reduces several points before the (FP64, shuffle)
     // block reduction, whose cost is per thread, not per point
-    w->G = grid_blocks(n, KT, sms * 2);
+    w->G = grid_blocks(n, KT, sms * KRYLOV_BLOCKS_PER_SM);
     size_t v64 = sizeof(double2) * n;
     bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
     size_t vmg = (f32 ? sizeof(float2) : sizeof(double2)) * n;

@@ -437,12 +437,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
 // its tail stays tiny.
 template <typename T> static long tail_point_budget() { return std::is_same<T, double>::value ? 40 : 700; }
 constexpr size_t TAIL_SMEM_BUDGET = 200 * 1024;
+constexpr size_t TAIL_INVERSE_BYTES = 1 << 20;
 
 template <typename T> int tail_first_level(const helm_ctx* c) {
   int nl = (int)c->lv.size();
   long pts = c->lv[nl - 1].ntot;
   size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
   if (bytes > TAIL_SMEM_BUDGET) return nl;  // the coarsest level alone is too big: no tail
+  // one block streaming the dense coarsest inverse is slower than the whole-GPU product
+  if ((size_t)pts * pts * sizeof(cx<T>) > TAIL_INVERSE_BYTES) return nl;
   int first = nl - 1;
   while (first > 0 && nl - (first - 1) <= TAIL_MAX_LEVELS) {
     long np = pts + c->lv[first - 1].ntot;

@@ -105,7 +105,9 @@ struct helm_server {
     size_t bytes = 0;
     double t_submit = 0, t_start = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running, 2 done
-    helm_solve_info info{};
+    int nrhs = 1, cur = 0;      // right-hand sides, the one being solved
+    helm_solve_info info{};     // summed over the right-hand sides solved so far
+    helm_solve_info one{};      // the current right-hand side
     helm_status status = HELM_OK;
     // running
     helm_ctx* ctx = nullptr;
@@ -129,12 +131,47 @@ struct helm_server {
   uint64_t next_id = 1;
   std::string last_error;
 
+  // Statistics of the right-hand side just finished, folded into the request's: counts add up,
+  // residuals take the worst, the status the first failure.
+  static void accumulate(Req* r) {
+    helm_solve_info& a = r->info;
+    const helm_solve_info& o = r->one;
+    if (r->cur == 0) a = o;
+    else {
+      a.iters += o.iters; a.matvecs += o.matvecs; a.restarts += o.restarts; a.kernels += o.kernels;
+      if (o.rel_res_recur > a.rel_res_recur) a.rel_res_recur = o.rel_res_recur;
+      if (o.rel_res_true > a.rel_res_true) a.rel_res_true = o.rel_res_true;
+      if (a.status == HELM_OK) a.status = o.status;
+    }
+  }
+
+  // Copies the finished right-hand side's solution (or last iterate) to the host and folds its
+  // statistics in.
+  void collect(Req* r) {
+    cudaStream_t s = streams[r->slot];
+    cudaMemcpyAsync((double2*)r->x_host + (size_t)r->cur * r->n, r->xd, sizeof(double2) * r->n,
+                    cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    accumulate(r);
+  }
+
+  // Starts the solve of right-hand side r->cur on the request's context (its hierarchy and
+  // Krylov workspace stay resident between right-hand sides).
+  helm_status begin_rhs(Req* r) {
+    cudaStream_t s = streams[r->slot];
+    if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
+    size_t vb = sizeof(double2) * r->n;
+    if (cudaMemcpyAsync(r->bd, r->b.data() + (size_t)r->cur * r->n, vb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return HELM_ERR_CUDA;
+    r->one = helm_solve_info{};
+    r->job = job_new();
+    job_setup(r->job, r->ctx, (const double2*)r->bd, (double2*)r->xd, &r->opts, &r->one, s);
+    return job_begin(*r->job);
+  }
+
   void finish(Req* r, helm_status st) {
     cudaStream_t s = r->slot >= 0 ? streams[r->slot] : (cudaStream_t)0;
-    if (r->ctx && r->xd && r->job && job_finished(r->job)) {  // the solution, or the last iterate
-      cudaMemcpyAsync(r->x_host, r->xd, sizeof(double2) * r->n, cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-    }
+    if (r->ctx && r->xd && r->job && job_finished(r->job)) collect(r);  // the solution, or the last iterate
     if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
     if (r->bd) cudaFreeAsync(r->bd, s);
     if (r->xd) cudaFreeAsync(r->xd, s);
@@ -162,14 +199,12 @@ struct helm_server {
       cudaGetLastError();
       return HELM_ERR_OOM;
     }
-    if (cudaMemcpyAsync(r->bd, r->b.data(), vb, cudaMemcpyHostToDevice, s) != cudaSuccess) return HELM_ERR_CUDA;
     if (!r->shadow.empty()) r->opts.shadow = r->shadow.data();
     r->opts.history = nullptr;
     r->opts.host_loop = 0;
-    r->job = job_new();
-    job_setup(r->job, r->ctx, (const double2*)r->bd, (double2*)r->xd, &r->opts, &r->info, s);
     r->t_start = now_s();
-    return job_begin(*r->job);
+    r->cur = 0;
+    return begin_rhs(r);
   }
 
   void run() {
@@ -210,7 +245,12 @@ struct helm_server {
         if (st == HELM_ERR_BUSY) continue;
         progressed = true;
         if (st != HELM_OK) { finish(r, st); continue; }
-        if (job_finished(r->job)) finish(r, job_status(r->job));
+        if (!job_finished(r->job)) continue;
+        helm_status js = job_status(r->job);
+        if (js != HELM_OK || r->cur + 1 >= r->nrhs) { finish(r, js); continue; }
+        collect(r);
+        r->cur += 1;
+        if ((st = begin_rhs(r)) != HELM_OK) finish(r, st);
       }
       if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
@@ -255,8 +295,10 @@ helm_status helm_server_submit(helm_server* s, const helm_request* rq, uint64_t*
   for (int a = 0; a < rq->grid.dim; ++a) r->n *= axis_n(rq->grid, a);
   if (r->n < 1) { delete r; set_error("helm_server_submit: empty grid"); return HELM_ERR_ARG; }
   if (rq->k.phi) r->phi.assign(rq->k.phi, rq->k.phi + r->n);
+  r->nrhs = rq->nrhs < 1 ? 1 : rq->nrhs;
+  if (r->nrhs > HELM_MAX_RHS) { delete r; set_error("helm_server_submit: nrhs"); return HELM_ERR_ARG; }
   const std::complex<double>* b = (const std::complex<double>*)rq->b;
-  r->b.assign(b, b + r->n);
+  r->b.assign(b, b + (size_t)r->nrhs * r->n);
   if (rq->opts.method == HELM_IDR) {
     if (!rq->opts.shadow || rq->opts.s < 1 || rq->opts.s > 8) { delete r; set_error("helm_server_submit: IDR shadow"); return HELM_ERR_ARG; }
     const std::complex<double>* sh = (const std::complex<double>*)rq->opts.shadow;

@@ -203,6 +203,91 @@ __global__ void k_gauss_jordan(double2* A, double2* X, int n, int* status) {
 
 static int ceil_div(long a, int b) { return (int)((a + b - 1) / b); }
 
+// In-place Gauss-Jordan with partial pivoting over the whole GPU, for coarsest levels too
+// large for one block: A (n x n, row-major) is overwritten with A^{-1}.  Step k: one block picks
+// the pivot row p >= k of column k; rows k and p are exchanged while the pivot row is scaled
+// into `prow` (prow[k] = 1 / a_pk) and column k is saved into `fcol`; every other row r then
+// becomes A[r, :] - fcol[r] prow, column k being replaced by -fcol[r] / a_pk.  The row exchanges
+// are undone on the columns at the end, last step first.
+constexpr int GJ_ONE_BLOCK_MAX = 512;
+
+struct GjPivot {
+  double2 apk, akk;
+  int p;
+};
+
+__global__ void k_gj_pivot(const double2* __restrict__ A, int n, int k, GjPivot* pv, int* perm, int* status) {
+  __shared__ double best[1024];
+  __shared__ int bidx[1024];
+  int tid = threadIdx.x, nt = blockDim.x;
+  double b = -1.0;
+  int bi = k;
+  for (int r = k + tid; r < n; r += nt) {
+    double v = cabs2<double>(A[(long)r * n + k]);
+    if (v > b) { b = v; bi = r; }
+  }
+  best[tid] = b;
+  bidx[tid] = bi;
+  __syncthreads();
+  for (int s = nt / 2; s > 0; s >>= 1) {
+    if (tid < s && (best[tid + s] > best[tid] || (best[tid + s] == best[tid] && bidx[tid + s] < bidx[tid]))) {
+      best[tid] = best[tid + s];
+      bidx[tid] = bidx[tid + s];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int p = bidx[0];
+    if (best[0] <= 0.0) status[0] = 1;
+    pv->p = p;
+    pv->apk = A[(long)p * n + k];
+    pv->akk = A[(long)k * n + k];
+    perm[k] = p;
+  }
+}
+
+// thread t owns column t of rows k and p, and row t of column k
+__global__ void k_gj_swap(double2* __restrict__ A, int n, int k, const GjPivot* pv, double2* __restrict__ prow,
+                          double2* __restrict__ fcol) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int p = pv->p;
+  double2 ip = crecip<double>(pv->apk);
+  double2 ak = A[(long)k * n + t], ap = A[(long)p * n + t];
+  double2 pr = t == k ? ip : cmul<double>(ap, ip);
+  prow[t] = pr;
+  A[(long)k * n + t] = pr;
+  if (p != k) A[(long)p * n + t] = ak;
+  fcol[t] = t == k ? mkc<double>(0.0, 0.0) : (t == p ? pv->akk : A[(long)t * n + k]);
+}
+
+__global__ void k_gj_update(double2* __restrict__ A, int n, int k, const double2* __restrict__ prow,
+                            const double2* __restrict__ fcol) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (c >= n || r == k) return;
+  double2 f = fcol[r];
+  if (f.x == 0.0 && f.y == 0.0) return;  // the row does not change
+  long e = (long)r * n + c;
+  double2 a = c == k ? mkc<double>(0.0, 0.0) : A[e];
+  A[e] = csub<double>(a, cmul<double>(f, prow[c]));
+}
+
+__global__ void k_gj_unpermute(double2* __restrict__ A, int n, const int* __restrict__ perm) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double2* row = A + (long)r * n;
+  for (int k = n - 1; k >= 0; --k) {
+    int p = perm[k];
+    if (p != k) {
+      double2 t = row[k];
+      row[k] = row[p];
+      row[p] = t;
+    }
+  }
+}
+
+
 static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, double2 scale_ly,
                               bool want32, cudaStream_t st) {
   const helm_grid& g = c->grid;
@@ -417,38 +502,64 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       if ((rc = ctx_alloc(c, &L.f, esz * L.ntot)) != HELM_OK) return rc;
     }
   }
-  // dense inverse of the coarsest operator, computed in FP64
+  // dense inverse of the coarsest operator, computed in FP64: one block for small levels,
+  // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
-  if (Cst.ntot > 4096) {
-    set_error("coarsest level too large for the dense direct solve (> 4096 unknowns); raise max_levels");
+  if (Cst.ntot > HELM_COARSE_MAX_UNKNOWNS) {
+    set_error("coarsest level too large for the dense direct solve (> 16384 unknowns); raise max_levels");
     return HELM_ERR_ARG;
   }
   int n = (int)Cst.ntot;
   c->nco = n;
-  double2 *A = nullptr, *X = nullptr;
-  int* flag = nullptr;
-  HELM_CUDA(cudaMallocAsync(&A, sizeof(double2) * (size_t)n * n, st));
-  cudaError_t e1 = cudaMallocAsync(&X, sizeof(double2) * (size_t)n * n, st);
-  cudaError_t e2 = cudaMallocAsync(&flag, sizeof(int), st);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  const bool one_block = n <= GJ_ONE_BLOCK_MAX;
+  double2 *A = nullptr, *X = nullptr, *prow = nullptr, *fcol = nullptr;
+  int *flag = nullptr, *perm = nullptr;
+  GjPivot* pv = nullptr;
+  auto free_all = [&]() {
+    if (A) cudaFreeAsync(A, st);
     if (X) cudaFreeAsync(X, st);
     if (flag) cudaFreeAsync(flag, st);
-    cudaFreeAsync(A, st);
-    return cuda_check(e1 != cudaSuccess ? e1 : e2, "cudaMallocAsync(coarse)");
+  };
+  // X holds the inverse (one block) or the pivot row, saved column, pivots and pivot order
+  size_t xbytes = one_block ? sizeof(double2) * (size_t)n * n
+                            : sizeof(double2) * 2 * (size_t)n + sizeof(GjPivot) + sizeof(int) * (size_t)n + 256;
+  cudaError_t e0 = cudaMallocAsync(&A, sizeof(double2) * (size_t)n * n, st);
+  cudaError_t e1 = e0 == cudaSuccess ? cudaMallocAsync(&X, xbytes, st) : e0;
+  cudaError_t e2 = e1 == cudaSuccess ? cudaMallocAsync(&flag, sizeof(int), st) : e1;
+  if (e2 != cudaSuccess) {
+    free_all();
+    return cuda_check(e2, "cudaMallocAsync(coarse)");
   }
   cudaMemsetAsync(flag, 0, sizeof(int), st);
   k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
-  int thr = 1024;
-  k_gauss_jordan<<<1, thr, thr * (sizeof(double) + sizeof(int)), st>>>(A, X, n, flag);
+  const double2* inv = X;
+  if (one_block) {
+    int thr = 1024;
+    k_gauss_jordan<<<1, thr, thr * (sizeof(double) + sizeof(int)), st>>>(A, X, n, flag);
+  } else {
+    prow = X;
+    fcol = X + n;
+    pv = reinterpret_cast<GjPivot*>(X + 2 * (size_t)n);
+    perm = reinterpret_cast<int*>(reinterpret_cast<char*>(pv) + 256);
+    dim3 ug(ceil_div(n, 256), n);
+    for (int k = 0; k < n; ++k) {
+      k_gj_pivot<<<1, 1024, 0, st>>>(A, n, k, pv, perm, flag);
+      k_gj_swap<<<ceil_div(n, 256), 256, 0, st>>>(A, n, k, pv, prow, fcol);
+      k_gj_update<<<ug, 256, 0, st>>>(A, n, k, prow, fcol);
+    }
+    k_gj_unpermute<<<ceil_div(n, 128), 128, 0, st>>>(A, n, perm);
+    inv = A;
+  }
+  HELM_CUDA(cudaGetLastError());
   if ((rc = ctx_alloc(c, &c->coarse_inv, esz * (size_t)n * n)) != HELM_OK) {
-    cudaFreeAsync(A, st); cudaFreeAsync(X, st); cudaFreeAsync(flag, st);
+    free_all();
     return rc;
   }
-  if (f32) k_c128_to_c64<<<ceil_div((long)n * n, 256), 256, 0, st>>>(X, (float2*)c->coarse_inv, (long)n * n);
-  else cudaMemcpyAsync(c->coarse_inv, X, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+  if (f32) k_c128_to_c64<<<ceil_div((long)n * n, 256), 256, 0, st>>>(inv, (float2*)c->coarse_inv, (long)n * n);
+  else cudaMemcpyAsync(c->coarse_inv, inv, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
   int hflag = 0;
   cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaFreeAsync(A, st); cudaFreeAsync(X, st); cudaFreeAsync(flag, st);
+  free_all();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   HELM_CUDA(e);
   if (hflag) {

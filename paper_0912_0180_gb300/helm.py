@@ -191,7 +191,9 @@ class Server:
         self._keep = {}
 
     def submit(self, problem, precond, *, mg_dtype: str = "c64", method: int = 0, s: int = 4,
-               tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3, shadow=None) -> int:
+               tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3, shadow=None, rhs=None) -> int:
+        """Queues one request; `rhs` (nrhs x N complex128) replaces problem.b when given, and
+        wait() then returns x with the same shape."""
         rq = L.Request()
         g = rq.grid
         g.dim = problem.dim
@@ -214,10 +216,11 @@ class Server:
         if shadow is not None:
             sh = np.ascontiguousarray(shadow, dtype=np.complex128)
             rq.opts.shadow = sh.ctypes.data
-        b = np.ascontiguousarray(problem.b, dtype=np.complex128)
+        b = np.ascontiguousarray(problem.b if rhs is None else rhs, dtype=np.complex128)
         x = np.zeros_like(b)
         rq.b = b.ctypes.data
         rq.x = x.ctypes.data
+        rq.nrhs = 1 if b.ndim == 1 else int(b.shape[0])
         t = C.c_uint64()
         _check(self._lib.helm_server_submit(self._h, C.byref(rq), C.byref(t)), "helm_server_submit")
         self._keep[t.value] = x

@@ -110,3 +110,28 @@ def test_server_overlaps_requests():
     assert all(r[1].status == 0 for r in res)
     assert seen > 1
     srv.close()
+
+
+def test_server_multiple_right_hand_sides():
+    """A request with several right-hand sides: every column is what a lone helm_solve gives it
+    (bitwise), and the request's statistics add up the per-right-hand-side counts."""
+    from paper_0912_0180_gb300.helm import Helm, Server
+    inst = _instances()
+    srv = Server(64 << 30, max_active=4)
+    jobs = []
+    for i, (p, pc) in enumerate(inst[:4]):
+        nrhs = 1 + (i * 3) % 5
+        rhs = np.stack([hi.random_vector(p.n, 40 + 7 * i + k) for k in range(nrhs)])
+        jobs.append((p, pc, rhs, srv.submit(p, pc, tol=1e-7, maxmv=3000, rhs=rhs)))
+    for p, pc, rhs, t in jobs:
+        x, info, lat = srv.wait(t)
+        assert info.status == 0 and x.shape == rhs.shape
+        h = Helm(p, pc, mg_dtype="c64")
+        mv = 0
+        for k in range(rhs.shape[0]):
+            xa, ia = h.solve(torch.from_numpy(rhs[k]).cuda(), tol=1e-7, maxmv=3000)
+            assert np.array_equal(xa.cpu().numpy(), x[k])
+            mv += ia.matvecs
+        assert info.matvecs == mv
+        h.close()
+    srv.close()

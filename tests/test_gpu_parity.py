@@ -373,3 +373,22 @@ def test_device_loop_is_deterministic_and_matches_host_loop(method):
     bodies = i1.iters if method == hi.BICGSTAB else i1.iters - 4
     assert i1.kernels == i3.kernels + 1 + bodies
     h.close()
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("shape", [(2, (44, 50), ((4, 3), (5, 0)), 1), (3, 17, 2, 1), (3, (30, 34, 32), 2, 2)])
+def test_vcycle_large_coarsest(shape, mg):
+    """Coarsest levels above 512 unknowns: their dense inverse comes from the whole-GPU
+    Gauss-Jordan (one pivot step per launch sequence) instead of the one-block kernel."""
+    dim, n_int, nl, levels = shape
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=0.4 * (np.max(n_int) - 1), phi_kind="bump",
+                        rhs="random", seed=5, bump_centre=(0.3, 0.6, 0.5))
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS, max_levels=levels + 1)
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype=mg)
+    shp = h.level_shape(h.nlev - 1)
+    assert int(np.prod(shp[:dim])) > 512
+    r = hi.random_vector(p.n, 4)
+    z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
+    assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+    h.close()
