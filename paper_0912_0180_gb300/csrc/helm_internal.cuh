@@ -31,6 +31,14 @@ template <typename T> __host__ __device__ __forceinline__ cx<T> cfma(cx<T> a, cx
   return mkc<T>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 // conj(a) * b
+// c - a b, four FMAs
+template <typename T> __host__ __device__ __forceinline__ cx<T> cfms(cx<T> a, cx<T> b, cx<T> c) {
+  return mkc<T>(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c + conj(a) b, four FMAs (the accumulation step of a complex inner product a^H b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cfmac(cx<T> a, cx<T> b, cx<T> c) {
+  return mkc<T>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
 template <typename T> __host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
   return mkc<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }

@@ -253,7 +253,7 @@ __global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __rest
   ROW_LOOP(H, i, j, l, p) {
     double2 vi = op_row<double, double, DIM>(H, ph, i, j, l, p);
     v[p] = vi;
-    acc[0] = cadd<double>(acc[0], cmulc<double>(rh[p], vi));
+    acc[0] = cfmac<double>(rh[p], vi, acc[0]);
   }
   double2 tot[1];
   if (!reduce_last<1>(acc, partials, &S->ticket[2], tot)) return;
@@ -308,7 +308,7 @@ __global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __rest
   ROW_LOOP(H, i, j, l, p) {
     double2 ti = op_row<double, double, DIM>(H, sh, i, j, l, p);
     t[p] = ti;
-    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, sv[p]));
+    acc[0] = cfmac<double>(ti, sv[p], acc[0]);
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
@@ -336,7 +336,7 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
     double2 ri = cfma<double>(mom, t[i], sv[i]);  // s - omega t
     r[i] = ri;
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
-    acc[1] = cadd<double>(acc[1], cmulc<double>(rh[i], ri));
+    acc[1] = cfmac<double>(rh[i], ri, acc[1]);
   }
   double2 tot[2];
   if (!reduce_last<2>(acc, partials, &S->ticket[5], tot)) return;
@@ -361,7 +361,7 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
 template <int S_>
 __device__ __forceinline__ void proj_acc(const double2* __restrict__ P, long n, long i, double2 y, double2* acc) {
 #pragma unroll
-  for (int k = 0; k < S_; ++k) acc[k] = cadd<double>(acc[k], cmulc<double>(P[k * n + i], y));
+  for (int k = 0; k < S_; ++k) acc[k] = cfmac<double>(P[k * n + i], y, acc[k]);
 }
 
 // Minimal-residual start step k: t = H z, omega = (t^H r) / (t^H t).
@@ -374,7 +374,7 @@ __global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const double2* __re
   ROW_LOOP(H, i, j, l, p) {
     double2 ti = op_row<double, double, DIM>(H, z, i, j, l, p);
     t[p] = ti;
-    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, r[p]));
+    acc[0] = cfmac<double>(ti, r[p], acc[0]);
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
@@ -483,7 +483,7 @@ __global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, co
   GRID_LOOP(i, n) {
     double2 acc = mkc<double>(0.0, 0.0);
 #pragma unroll
-    for (int k = 0; k < S_; ++k) acc = csub<double>(acc, cmul<double>(dR[k * n + i], c[k]));
+    for (int k = 0; k < S_; ++k) acc = cfms<double>(dR[k * n + i], c[k], acc);
     q[i] = acc;
     put_mg<TM>(vmg, i, cadd<double>(r[i], acc));
   }
@@ -500,7 +500,7 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __rest
   ROW_LOOP(H, i, j, l, p) {
     double2 ti = op_row<double, double, DIM>(H, z, i, j, l, p);
     t[p] = ti;
-    acc[0] = cadd<double>(acc[0], cmulc<double>(ti, cadd<double>(r[p], q[p])));
+    acc[0] = cfmac<double>(ti, cadd<double>(r[p], q[p]), acc[0]);
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
@@ -525,7 +525,7 @@ __global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const d
   GRID_LOOP(i, n) {
     double2 acc = cmul<double>(om, z[i]);
 #pragma unroll
-    for (int k = 0; k < S_; ++k) acc = csub<double>(acc, cmul<double>(dX[k * n + i], c[k]));
+    for (int k = 0; k < S_; ++k) acc = cfms<double>(dX[k * n + i], c[k], acc);
     dX[o * n + i] = acc;
   }
 }
@@ -559,7 +559,7 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
   for (int k = 0; k <= S_; ++k) acc[k] = mkc<double>(0.0, 0.0);
   GRID_LOOP(i, n) {
     double2 ti = t[i];
-    double2 dr = first ? csub<double>(q[i], cmul<double>(om, ti)) : mkc<double>(-ti.x, -ti.y);
+    double2 dr = first ? cfms<double>(om, ti, q[i]) : mkc<double>(-ti.x, -ti.y);
     dR[o * n + i] = dr;
     double2 ri = cadd<double>(r[i], dr);
     r[i] = ri;
@@ -589,7 +589,7 @@ __global__ void k_dot1(KrylovState* S, const double2* __restrict__ a, const doub
                        long n, double2* partials, double2* out) {
   pdl_entry();
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
-  GRID_LOOP(i, n) acc[0] = cadd<double>(acc[0], cmulc<double>(a[i], b[i]));
+  GRID_LOOP(i, n) acc[0] = cfmac<double>(a[i], b[i], acc[0]);
   double2 tot[1];
   if (!reduce_last<1>(acc, partials, &S->ticket[7], tot)) return;
   if (threadIdx.x == 0) *out = tot[0];

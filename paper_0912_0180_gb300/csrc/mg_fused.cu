@@ -24,36 +24,40 @@
 
 namespace helm {
 
-constexpr int DN_CX = 16, DN_CY = 8;         // coarse tile of k_down2d
-constexpr int UP_FX = 32, UP_FY = 8;         // fine tile of k_up2d
-constexpr int FUSED_THREADS = 256;
+// Tiles: the large ones (coarse 16 x 8 for k_down2d, fine 32 x 8 for k_up2d, 256 threads) on
+// levels with at least two blocks per SM; otherwise quarter / half tiles of 128 threads, so
+// that a small level still spreads over most SMs (in FP64 one block's arithmetic on one SM
+// otherwise sets the level's time).
+constexpr int DN_CX = 16, DN_CY = 8, DN_SCX = 8, DN_SCY = 4;
+constexpr int UP_FX = 32, UP_FY = 8, UP_SFX = 16, UP_SFY = 8;
+constexpr int FUSED_THREADS = 256, FUSED_SMALL_THREADS = 128;
 
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
-template <typename T, bool RBGS>
-__global__ void __launch_bounds__(FUSED_THREADS)
+template <typename T, bool RBGS, int CX, int CY, int NT>
+__global__ void __launch_bounds__(NT)
 k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
          cx<T>* __restrict__ fc, T omega, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
   constexpr int HF = RBGS ? 2 : 1;
-  constexpr int RX = 2 * DN_CX + 1, RY = 2 * DN_CY + 1;  // residual region
+  constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;  // residual region
   constexpr int FX = RX + 2 * HF, FY = RY + 2 * HF;      // staged f / u region
   __shared__ cx<T> sf[FY][FX];
   __shared__ cx<T> su[FY][FX];
   __shared__ cx<T> sr[RY][RX];
   const int n0 = op.n[0], n1 = op.n[1];
-  const int I0 = blockIdx.x * DN_CX, J0 = blockIdx.y * DN_CY;
+  const int I0 = blockIdx.x * CX, J0 = blockIdx.y * CY;
   const int fx0 = 2 * I0 - HF, fy0 = 2 * J0 - HF;  // origin of the staged region
   const int tid = threadIdx.x;
   // stage f; Jacobi: u = omega D^-1 f; RB-GS: red u = D^-1 f, black 0.  All loads of a
   // thread are issued before any is used.
   {
-    constexpr int NS = (FX * FY + FUSED_THREADS - 1) / FUSED_THREADS;
+    constexpr int NS = (FX * FY + NT - 1) / NT;
     cx<T> fv[NS], dv[NS];
 #pragma unroll
     for (int it = 0; it < NS; ++it) {
-      int e = tid + it * FUSED_THREADS;
+      int e = tid + it * NT;
       int x = e % FX, y = e / FX;
       int i = fx0 + x, j = fy0 + y;
       fv[it] = mkc<T>(T(0), T(0));
@@ -66,7 +70,7 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
     }
 #pragma unroll
     for (int it = 0; it < NS; ++it) {
-      int e = tid + it * FUSED_THREADS;
+      int e = tid + it * NT;
       if (e >= FX * FY) break;
       int x = e % FX, y = e / FX;
       int i = fx0 + x, j = fy0 + y;
@@ -78,7 +82,7 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
   }
   __syncthreads();
   if (RBGS) {  // black points of the inner region from the red values just computed
-    for (int e = tid; e < (FX - 2) * (FY - 2); e += FUSED_THREADS) {
+    for (int e = tid; e < (FX - 2) * (FY - 2); e += NT) {
       int x = 1 + e % (FX - 2), y = 1 + e / (FX - 2);
       int i = fx0 + x, j = fy0 + y;
       if (i < 0 || i >= n0 || j < 0 || j >= n1 || ((i + j) & 1) == 0) continue;
@@ -90,17 +94,17 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
   // write the smoothed iterate of the points this tile owns (the last tile also owns the
   // fine point past the last coarse node when n is odd)
   {
-    const int oi1 = (I0 + DN_CX >= nc0) ? n0 : 2 * (I0 + DN_CX);
-    const int oj1 = (J0 + DN_CY >= nc1) ? n1 : 2 * (J0 + DN_CY);
+    const int oi1 = (I0 + CX >= nc0) ? n0 : 2 * (I0 + CX);
+    const int oj1 = (J0 + CY >= nc1) ? n1 : 2 * (J0 + CY);
     const int wx = oi1 - 2 * I0, wy = oj1 - 2 * J0;
-    for (int e = tid; e < wx * wy; e += FUSED_THREADS) {
+    for (int e = tid; e < wx * wy; e += NT) {
       int x = e % wx, y = e / wx;
       int i = 2 * I0 + x, j = 2 * J0 + y;
       u_out[i + n0 * j] = su[y + HF][x + HF];
     }
   }
   // residual on the restriction region (fine 2I0 .. 2I0 + 2CX), zero outside the grid
-  for (int e = tid; e < RX * RY; e += FUSED_THREADS) {
+  for (int e = tid; e < RX * RY; e += NT) {
     int x = e % RX, y = e / RX;
     int i = 2 * I0 + x, j = 2 * J0 + y;
     cx<T> rv = mkc<T>(T(0), T(0));
@@ -115,8 +119,8 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
   }
   __syncthreads();
   // full weighting (1/4, 1/2, 1/4 per axis)
-  for (int e = tid; e < DN_CX * DN_CY; e += FUSED_THREADS) {
-    int cx_ = e % DN_CX, cy = e / DN_CX;
+  for (int e = tid; e < CX * CY; e += NT) {
+    int cx_ = e % CX, cy = e / CX;
     int I = I0 + cx_, J = J0 + cy;
     if (I >= nc0 || J >= nc1) continue;
     // separable weights: each row (a + c) + 2 b, then the rows the same way, then / 16
@@ -132,40 +136,40 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
 }
 
 // ---- up: prolongation + correction + post-smoothing (2D, nu2 = 1), out of place --------------
-template <typename T, bool RBGS, typename TO>
-__global__ void __launch_bounds__(FUSED_THREADS)
+template <typename T, bool RBGS, typename TO, int FX, int FY, int NT>
+__global__ void __launch_bounds__(NT)
 k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
        const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
   constexpr int HU = RBGS ? 2 : 1;                 // halo of the corrected iterate
-  constexpr int UX = UP_FX + 2 * HU, UY = UP_FY + 2 * HU;
+  constexpr int UX = FX + 2 * HU, UY = FY + 2 * HU;
   constexpr int CXN = UX / 2 + 3, CYN = UY / 2 + 3;  // coarse values covering the region
   __shared__ cx<T> su[UY][UX];
   __shared__ cx<T> se[CYN][CXN];
   const int n0 = op.n[0], n1 = op.n[1];
-  const int i0 = blockIdx.x * UP_FX, j0 = blockIdx.y * UP_FY;
+  const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY;
   const int ux0 = i0 - HU, uy0 = j0 - HU;
   const int cx0 = (ux0 >> 1) - 1, cy0 = (uy0 >> 1) - 1;  // floor division for negatives
   const int tid = threadIdx.x;
-  for (int e = tid; e < CXN * CYN; e += FUSED_THREADS) {
+  for (int e = tid; e < CXN * CYN; e += NT) {
     int x = e % CXN, y = e / CXN;
     int I = cx0 + x, J = cy0 + y;
     se[y][x] = (I >= 0 && I < nc0 && J >= 0 && J < nc1) ? ec[I + nc0 * J] : mkc<T>(T(0), T(0));
   }
   __syncthreads();
   // corrected iterate u + P e on the tile and its halo (u loads issued up front)
-  constexpr int NU = (UX * UY + FUSED_THREADS - 1) / FUSED_THREADS;
+  constexpr int NU = (UX * UY + NT - 1) / NT;
   cx<T> uold[NU];
 #pragma unroll
   for (int it = 0; it < NU; ++it) {
-    int e = tid + it * FUSED_THREADS;
+    int e = tid + it * NT;
     int i = ux0 + e % UX, j = uy0 + e / UX;
     uold[it] = (e < UX * UY && i >= 0 && i < n0 && j >= 0 && j < n1) ? u_in[i + n0 * j] : mkc<T>(T(0), T(0));
   }
 #pragma unroll
   for (int it = 0; it < NU; ++it) {
-    int e = tid + it * FUSED_THREADS;
+    int e = tid + it * NT;
     if (e >= UX * UY) break;
     int x = e % UX, y = e / UX;
     int i = ux0 + x, j = uy0 + y;
@@ -188,8 +192,8 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
   }
   __syncthreads();
   if (!RBGS) {
-    for (int e = tid; e < UP_FX * UP_FY; e += FUSED_THREADS) {
-      int x = e % UP_FX, y = e / UP_FX;
+    for (int e = tid; e < FX * FY; e += NT) {
+      int x = e % FX, y = e / FX;
       int i = i0 + x, j = j0 + y;
       if (i >= n0 || j >= n1) continue;
       int p = i + n0 * j;
@@ -202,9 +206,9 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
     }
   } else {
     // red points of the tile and one ring around it, from the corrected black values
-    __shared__ cx<T> sred[UP_FY + 2][UP_FX + 2];
-    for (int e = tid; e < (UP_FX + 2) * (UP_FY + 2); e += FUSED_THREADS) {
-      int x = e % (UP_FX + 2), y = e / (UP_FX + 2);
+    __shared__ cx<T> sred[FY + 2][FX + 2];
+    for (int e = tid; e < (FX + 2) * (FY + 2); e += NT) {
+      int x = e % (FX + 2), y = e / (FX + 2);
       int i = i0 - 1 + x, j = j0 - 1 + y;
       int sx = x + 1, sy = y + 1;  // position in su (HU = 2)
       cx<T> v = su[sy][sx];
@@ -216,8 +220,8 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
       sred[y][x] = v;
     }
     __syncthreads();
-    for (int e = tid; e < UP_FX * UP_FY; e += FUSED_THREADS) {
-      int x = e % UP_FX, y = e / UP_FX;
+    for (int e = tid; e < FX * FY; e += NT) {
+      int x = e % FX, y = e / FX;
       int i = i0 + x, j = j0 + y;
       if (i >= n0 || j >= n1) continue;
       int p = i + n0 * j;
@@ -503,15 +507,57 @@ helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool 
   return tail_launch<T, T>(a, c->grid.dim, smem, f, (cx<T>*)out, skip, st);
 }
 
+static bool big_tiles(const helm_ctx* c, long blocks) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  return blocks >= 2L * sms;
+}
+
+template <typename T, bool RB, int CX, int CY, int NT>
+static void down_launch(const LevelHost& F, const LevelHost& C, const cx<T>* f, cx<T>* u_out, cx<T>* fc, T om,
+                        const int* skip, cudaStream_t st) {
+  dim3 g((C.n[0] + CX - 1) / CX, (C.n[1] + CY - 1) / CY);
+  launch_pdl(k_down2d<T, RB, CX, CY, NT>, dim3(g), dim3(NT), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, om, skip);
+}
+
 template <typename T>
 void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>* fc, const int* skip, cudaStream_t st) {
   const LevelHost& F = c->lv[l];
   const LevelHost& C = c->lv[l + 1];
-  dim3 g((C.n[0] + DN_CX - 1) / DN_CX, (C.n[1] + DN_CY - 1) / DN_CY);
-  if (c->pc.smoother == HELM_SM_RBGS)
-    launch_pdl(k_down2d<T, true>, dim3(g), dim3(FUSED_THREADS), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
-  else
-    launch_pdl(k_down2d<T, false>, dim3(g), dim3(FUSED_THREADS), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, (T)c->pc.omega, skip);
+  long nb = (long)((C.n[0] + DN_CX - 1) / DN_CX) * ((C.n[1] + DN_CY - 1) / DN_CY);
+  bool big = big_tiles(c, nb);
+  T om = (T)c->pc.omega;
+  if (c->pc.smoother == HELM_SM_RBGS) {
+    if (big) down_launch<T, true, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
+    else down_launch<T, true, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  } else {
+    if (big) down_launch<T, false, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
+    else down_launch<T, false, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  }
+}
+
+template <typename T, bool RB, typename TO, int FX, int FY, int NT>
+static void up_launch(const LevelHost& F, const LevelHost& C, const cx<T>* u_in, const cx<T>* ec, const cx<T>* f,
+                      TO* out, T om, const int* skip, cudaStream_t st) {
+  dim3 g((F.n[0] + FX - 1) / FX, (F.n[1] + FY - 1) / FY);
+  launch_pdl(k_up2d<T, RB, TO, FX, FY, NT>, dim3(g), dim3(NT), 0, st, F.view<T>(), C.n[0], C.n[1], u_in, ec, f,
+             (cx<TO>*)out, om, skip);
+}
+
+template <typename T, typename TO>
+static void up_dispatch(const helm_ctx* c, const LevelHost& F, const LevelHost& C, const cx<T>* u_in, const cx<T>* ec,
+                        const cx<T>* f, void* out, const int* skip, cudaStream_t st) {
+  long nb = (long)((F.n[0] + UP_FX - 1) / UP_FX) * ((F.n[1] + UP_FY - 1) / UP_FY);
+  bool big = big_tiles(c, nb);
+  T om = (T)c->pc.omega;
+  TO* o = (TO*)out;
+  if (c->pc.smoother == HELM_SM_RBGS) {
+    if (big) up_launch<T, true, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+    else up_launch<T, true, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  } else {
+    if (big) up_launch<T, false, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+    else up_launch<T, false, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  }
 }
 
 template <typename T>
@@ -519,17 +565,8 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
                 bool out_f64, const int* skip, cudaStream_t st) {
   const LevelHost& F = c->lv[l];
   const LevelHost& C = c->lv[l + 1];
-  dim3 g((F.n[0] + UP_FX - 1) / UP_FX, (F.n[1] + UP_FY - 1) / UP_FY);
-  OpView<T> v = F.view<T>();
-  T om = (T)c->pc.omega;
-  bool rb = c->pc.smoother == HELM_SM_RBGS;
-  if (out_f64) {
-    if (rb) launch_pdl(k_up2d<T, true, double>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
-    else launch_pdl(k_up2d<T, false, double>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (double2*)out, om, skip);
-  } else {
-    if (rb) launch_pdl(k_up2d<T, true, T>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
-    else launch_pdl(k_up2d<T, false, T>, dim3(g), dim3(FUSED_THREADS), 0, st, v, C.n[0], C.n[1], u_in, ec, f, (cx<T>*)out, om, skip);
-  }
+  if (out_f64) up_dispatch<T, double>(c, F, C, u_in, ec, f, out, skip, st);
+  else up_dispatch<T, T>(c, F, C, u_in, ec, f, out, skip, st);
 }
 
 template int tail_first_level<float>(const helm_ctx*);

@@ -16,20 +16,6 @@ __device__ __forceinline__ bool op_uniform(const OpView<T>& op, int i, int j, in
   return u;
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ cx<T> op_diag(const OpView<T>& op, int i, int j, int l, long p) {
-  if (op_uniform<DIM>(op, i, j, l)) {
-    T ph = op.phi ? op.phi[p] : op.phi0;
-    if (op.uniform_real) return mkc<T>(op.ud.x - ph * op.s.x, op.ud.y);
-    return csub<T>(op.ud, cscale<T>(ph, op.s));
-  }
-  cx<T> d = op.a0[0][i];
-  if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
-  if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
-  T ph = op.phi ? op.phi[p] : op.phi0;
-  return csub<T>(d, cscale<T>(ph, op.s));
-}
-
 template <typename T, typename TX, int DIM>
 __device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const cx<TX>* __restrict__ x, long p) {
   cx<T> sx = cadd<T>(cconv<T, TX>(x[p - 1]), cconv<T, TX>(x[p + 1]));
@@ -59,31 +45,57 @@ __device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const c
   return acc;
 }
 
+// Off-diagonal sum of a point outside the uniform interior.  Axes along which the point still
+// lies in the uniform run take the shared coefficient on the neighbour pair (one product instead
+// of two); the others read their Shortley-Weller row, skipping Dirichlet neighbours.
 template <typename T, typename TX, int DIM>
-__device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* __restrict__ x,
-                                            int i, int j, int l, long p) {
-  if (op_uniform<DIM>(op, i, j, l)) return op_offdiag_uniform<T, TX, DIM>(op, x, p);
+__device__ __forceinline__ cx<T> op_offdiag_general(const OpView<T>& op, const cx<TX>* __restrict__ x,
+                                                    int i, int j, int l, long p) {
   cx<T> acc = mkc<T>(T(0), T(0));
-  if (i > 0) acc = cfma<T>(op.am[0][i], cconv<T, TX>(x[p - 1]), acc);
-  if (i < op.n[0] - 1) acc = cfma<T>(op.ap[0][i], cconv<T, TX>(x[p + 1]), acc);
-  if (DIM > 1) {
-    long st = op.n[0];
-    if (j > 0) acc = cfma<T>(op.am[1][j], cconv<T, TX>(x[p - st]), acc);
-    if (j < op.n[1] - 1) acc = cfma<T>(op.ap[1][j], cconv<T, TX>(x[p + st]), acc);
-  }
-  if (DIM > 2) {
-    long st = (long)op.n[0] * op.n[1];
-    if (l > 0) acc = cfma<T>(op.am[2][l], cconv<T, TX>(x[p - st]), acc);
-    if (l < op.n[2] - 1) acc = cfma<T>(op.ap[2][l], cconv<T, TX>(x[p + st]), acc);
+  const int idx[3] = {i, j, l};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const long st = a == 0 ? 1 : (a == 1 ? (long)op.n[0] : (long)op.n[0] * op.n[1]);
+    const int q = idx[a];
+    if (q >= op.ulo[a] && q <= op.uhi[a]) {
+      cx<T> pr = cadd<T>(cconv<T, TX>(x[p - st]), cconv<T, TX>(x[p + st]));
+      acc = op.uniform_real ? mkc<T>(fma(op.ua[a].x, pr.x, acc.x), fma(op.ua[a].x, pr.y, acc.y))
+                            : cfma<T>(op.ua[a], pr, acc);
+    } else {
+      if (q > 0) acc = cfma<T>(op.am[a][q], cconv<T, TX>(x[p - st]), acc);
+      if (q < op.n[a] - 1) acc = cfma<T>(op.ap[a][q], cconv<T, TX>(x[p + st]), acc);
+    }
   }
   return acc;
 }
 
 template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* __restrict__ x,
+                                            int i, int j, int l, long p) {
+  if (op_uniform<DIM>(op, i, j, l)) return op_offdiag_uniform<T, TX, DIM>(op, x, p);
+  return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p);
+}
+
+// (A x)_P.  In the uniform interior of an operator with real coefficients (H) the diagonal
+// ud - s phi_P is real and multiplies x_P with two FMAs.
+template <typename T, typename TX, int DIM>
 __device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __restrict__ x, int i,
                                         int j, int l, long p) {
-  cx<T> d = op_diag<T, DIM>(op, i, j, l, p);
-  return cfma<T>(d, cconv<T, TX>(x[p]), op_offdiag<T, TX, DIM>(op, x, i, j, l, p));
+  const cx<T> xp = cconv<T, TX>(x[p]);
+  const T ph = op.phi ? op.phi[p] : op.phi0;
+  if (op_uniform<DIM>(op, i, j, l)) {
+    const cx<T> off = op_offdiag_uniform<T, TX, DIM>(op, x, p);
+    if (op.uniform_real) {
+      const T d = fma(-ph, op.s.x, op.ud.x);
+      return mkc<T>(fma(d, xp.x, off.x), fma(d, xp.y, off.y));
+    }
+    return cfma<T>(csub<T>(op.ud, cscale<T>(ph, op.s)), xp, off);
+  }
+  cx<T> d = op.a0[0][i];
+  if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
+  if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
+  d = csub<T>(d, cscale<T>(ph, op.s));
+  return cfma<T>(d, xp, op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p));
 }
 
 // 2D off-diagonal part from the four neighbour values (staged in shared memory by the fused
@@ -102,10 +114,20 @@ __device__ __forceinline__ cx<T> off2d(const OpView<T>& op, int i, int j, cx<T> 
     }
     return cfma<T>(op.ua[1], sy, cmul<T>(op.ua[0], sx));
   }
-  cx<T> acc = cmul<T>(op.am[0][i], xw);
-  acc = cfma<T>(op.ap[0][i], xe, acc);
-  acc = cfma<T>(op.am[1][j], xs, acc);
-  return cfma<T>(op.ap[1][j], xn, acc);
+  // per axis: the shared coefficient on the pair where the axis is still uniform
+  cx<T> acc;
+  if (i >= op.ulo[0] && i <= op.uhi[0]) {
+    cx<T> pr = cadd<T>(xw, xe);
+    acc = op.uniform_real ? cscale<T>(op.ua[0].x, pr) : cmul<T>(op.ua[0], pr);
+  } else {
+    acc = cfma<T>(op.ap[0][i], xe, cmul<T>(op.am[0][i], xw));
+  }
+  if (j >= op.ulo[1] && j <= op.uhi[1]) {
+    cx<T> pr = cadd<T>(xs, xn);
+    return op.uniform_real ? mkc<T>(fma(op.ua[1].x, pr.x, acc.x), fma(op.ua[1].x, pr.y, acc.y))
+                           : cfma<T>(op.ua[1], pr, acc);
+  }
+  return cfma<T>(op.ap[1][j], xn, cfma<T>(op.am[1][j], xs, acc));
 }
 
 // point coordinates from a linear index

@@ -180,10 +180,12 @@ def test_vcycle(case, pci, mg, fused):
 
 @pytest.mark.parametrize("mg", ["c128", "c64"])
 @pytest.mark.parametrize("sm", [hi.SM_JACOBI, hi.SM_RBGS])
-@pytest.mark.parametrize("shape", [(300, 8), (97, 3), (161, 0), ((130, 70), ((0, 9), (5, 5)))])
+@pytest.mark.parametrize("shape", [(300, 8), (97, 3), (161, 0), ((130, 70), ((0, 9), (5, 5))),
+                                   ((561, 300), ((8, 7), (4, 4)))])
 def test_vcycle_fused_levels_large(shape, sm, mg):
     """Grids large enough that several levels run the fused 2D kernels with many tiles and
-    ragged edges (odd and even sizes, one-sided layers) before the tail takes over."""
+    ragged edges (odd and even sizes, one-sided layers) before the tail takes over; the last
+    shape is big enough for the large tiles on its finest level and the small ones below."""
     n_int, nl = shape
     p = hi.make_problem(2, n_int, nl, theta_gamma=0.5, k0=0.3 * (np.max(n_int) - 1), phi_kind="bump",
                         rhs="random", seed=8, bump_centre=(0.3, 0.6))
