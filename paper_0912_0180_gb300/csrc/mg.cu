@@ -45,44 +45,94 @@ __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T
 // zero guess (un = (omega / D) f).
 template <typename T, int DIM>
 __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
-                         cx<T>* __restrict__ un, T omega, const int* skip) {
+                         cx<T>* __restrict__ un, T omega, double2* __restrict__ wide, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
   cx<T> di = op.dinv[p];  // omega / D
+  cx<T> v;
   if (!u) {
-    un[p] = cmul<T>(f[p], di);
-    return;
+    v = cmul<T>(f[p], di);
+  } else {
+    cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
+    cx<T> u0 = u[p];
+    const T om1 = T(1) - omega;
+    v = mkc<T>(fma(om1, u0.x, g.x), fma(om1, u0.y, g.y));
   }
-  cx<T> g = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), di);
-  cx<T> u0 = u[p];
-  const T om1 = T(1) - omega;
-  un[p] = mkc<T>(fma(om1, u0.x, g.x), fma(om1, u0.y, g.y));
+  if (wide) wide[p] = cconv<double, T>(v);  // the last sweep of a V-cycle that ends in complex128
+  else un[p] = v;
 }
 
-// Red-black Gauss-Seidel half-sweep on points with (i + j + l) % 2 == colour, in place:
-// u_P = (f_P - offdiag(u)_P) / D_P.  zero_guess with colour 0 writes the red points from a
-// zero guess (f / D) and zeroes the black points.
+// Red-black Gauss-Seidel half-sweep on the points with (i + j + l) % 2 == colour, in place:
+// u_P = (f_P - offdiag(u)_P) / D_P.  Along a row the colours alternate, so the grid holds one
+// thread per point of the colour (thread t of a row takes i = 2t or 2t + 1) and every lane of a
+// warp does arithmetic.  zero_guess (colour 0) writes the red points from a zero guess, f / D; the
+// black sweep that always follows it reads only red neighbours and writes every black point.
+// `wide` (black sweeps only): also write the pair of points of this thread, widened to complex128.
 template <typename T, int DIM>
 __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restrict__ f, int colour,
-                       int zero_guess, const int* skip) {
+                       int zero_guess, double2* __restrict__ wide, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
-  POINT_INDEX(op);
-  int c = (i + j + l) & 1;
-  if (zero_guess) {
-    if (c == 0) u[p] = cmul<T>(f[p], op.dinv[p]);
-    else u[p] = mkc<T>(T(0), T(0));
-    return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int l = blockIdx.z;
+  if (j >= op.n[1]) return;
+  const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
+  const int i = 2 * t + ((j + l + colour) & 1);
+  if (i < op.n[0]) {
+    const long p = row + i;
+    if (zero_guess) {
+      u[p] = cmul<T>(f[p], op.dinv[p]);
+      return;
+    }
+    cx<T> v = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), op.dinv[p]);
+    u[p] = v;
+    if (wide) wide[p] = cconv<double, T>(v);
   }
-  if (c != colour) return;
-  u[p] = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), op.dinv[p]);
+  // the other point of the pair [2t, 2t + 1] is already final; it is in the grid even when this
+  // thread's point lies past an odd row end
+  const int i2 = 2 * t + ((j + l + colour + 1) & 1);
+  if (wide && i2 < op.n[0]) wide[row + i2] = cconv<double, T>(u[row + i2]);
+}
+
+// Residual right after the single pre-smoothing sweep from the zero guess, without the diagonal:
+// damped Jacobi left D u = omega f, so r = (1 - omega) f - offdiag(u); red-black Gauss-Seidel
+// left r = 0 on the black points and r = -offdiag(u) on the red ones (their neighbours are all
+// black and were updated last).  RB: one thread per red/black pair of a row.
+template <typename T, int DIM, bool RB>
+__global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
+                         cx<T>* __restrict__ r, T omega, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int l = blockIdx.z;
+  if (j >= op.n[1]) return;
+  const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
+  if (RB) {
+    int par = (j + l) & 1;
+    int ir = 2 * t + par, ib = 2 * t + 1 - par;
+    if (ib < op.n[0]) r[row + ib] = mkc<T>(T(0), T(0));
+    if (ir < op.n[0]) {
+      cx<T> acc = op_offdiag<T, T, DIM>(op, u, ir, j, l, row + ir);
+      r[row + ir] = mkc<T>(-acc.x, -acc.y);
+    }
+  } else {
+    if (t >= op.n[0]) return;
+    long p = row + t;
+    cx<T> acc = op_offdiag<T, T, DIM>(op, u, t, j, l, p);
+    cx<T> fv = f[p];
+    const T om1 = T(1) - omega;
+    r[p] = mkc<T>(fma(om1, fv.x, -acc.x), fma(om1, fv.y, -acc.y));
+  }
 }
 
 struct Dims { int f[3]; int c[3]; };
 
 // Full weighting in index space: coarse unknown c gathers fine unknowns 2c, 2c+1, 2c+2 per
-// axis with weights 1/4, 1/2, 1/4 (tensor product); indices past the grid are Dirichlet.
+// axis with weights 1/4, 1/2, 1/4 (tensor product); indices past the grid are Dirichlet.  The
+// weights are applied one axis at a time, (a + c) + 2 b, and the factor 4^-DIM once at the end.
 template <typename T, int DIM>
 __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restrict__ fc, const int* skip) {
   pdl_entry();
@@ -91,39 +141,41 @@ __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restric
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   int L = blockIdx.z;
   if (I >= d.c[0] || J >= d.c[1]) return;
-  const T w[3] = {T(0.25), T(0.5), T(0.25)};
-  cx<T> acc = mkc<T>(T(0), T(0));
-  int dl0 = DIM > 2 ? -1 : 0, dl1 = DIM > 2 ? 1 : 0;
-  int dj0 = DIM > 1 ? -1 : 0, dj1 = DIM > 1 ? 1 : 0;
-  for (int dl = dl0; dl <= dl1; ++dl) {
-    int fl = DIM > 2 ? 2 * L + 1 + dl : 0;
-    if (fl >= d.f[2]) continue;
-    T wl = DIM > 2 ? w[dl + 1] : T(1);
-    for (int dj = dj0; dj <= dj1; ++dj) {
-      int fj = DIM > 1 ? 2 * J + 1 + dj : 0;
-      if (fj >= d.f[1]) continue;
-      T wj = DIM > 1 ? w[dj + 1] : T(1);
-      const cx<T>* row = r + (long)d.f[0] * (fj + (long)d.f[1] * fl);
-      for (int di = -1; di <= 1; ++di) {
-        int fi = 2 * I + 1 + di;
-        if (fi >= d.f[0]) continue;
-        acc = cadd<T>(acc, cscale<T>(w[di + 1] * wj * wl, row[fi]));
-      }
-    }
-  }
-  fc[I + (long)d.c[0] * (J + (long)d.c[1] * L)] = acc;
+  const cx<T> zero = mkc<T>(T(0), T(0));
+  auto w3 = [](cx<T> a, cx<T> b, cx<T> c) {
+    return mkc<T>(fma(T(2), b.x, a.x + c.x), fma(T(2), b.y, a.y + c.y));
+  };
+  const int fi = 2 * I;  // fine 2I .. 2I+2; 2I+2 may lie past a ragged edge
+  auto row_sum = [&](int fj, int fl) -> cx<T> {
+    if ((DIM > 1 && fj >= d.f[1]) || (DIM > 2 && fl >= d.f[2])) return zero;
+    const cx<T>* row = r + (long)d.f[0] * (fj + (long)d.f[1] * fl);
+    return w3(row[fi], row[fi + 1], fi + 2 < d.f[0] ? row[fi + 2] : zero);
+  };
+  auto plane_sum = [&](int fl) -> cx<T> {
+    if (DIM == 1) return row_sum(0, 0);
+    const int fj = 2 * J;
+    return w3(row_sum(fj, fl), row_sum(fj + 1, fl), row_sum(fj + 2, fl));
+  };
+  cx<T> acc;
+  if (DIM < 3) acc = plane_sum(0);
+  else acc = w3(plane_sum(2 * L), plane_sum(2 * L + 1), plane_sum(2 * L + 2));
+  const T sc = DIM == 1 ? T(0.25) : (DIM == 2 ? T(0.0625) : T(0.015625));
+  fc[I + (long)d.c[0] * (J + (long)d.c[1] * L)] = cscale<T>(sc, acc);
 }
 
-// linear interpolation weights of fine index i from coarse indices (at most 2)
-__device__ __forceinline__ int interp1(int i, int nc, int* ci, float* w) {
-  if (i & 1) { ci[0] = (i - 1) >> 1; w[0] = 1.f; return 1; }
+// Linear interpolation along one axis: an odd fine index i takes coarse node (i - 1) / 2 with
+// weight 1, an even one the coarse nodes i/2 - 1 and i/2 with weight 1/2 each (nodes outside
+// the coarse grid are Dirichlet zeros).  Returns the count of coarse nodes and their indices.
+__device__ __forceinline__ int interp1(int i, int nc, int* ci) {
+  if (i & 1) { ci[0] = (i - 1) >> 1; return 1; }
   int k = 0;
-  if ((i >> 1) - 1 >= 0) { ci[k] = (i >> 1) - 1; w[k] = 0.5f; ++k; }
-  if ((i >> 1) < nc) { ci[k] = i >> 1; w[k] = 0.5f; ++k; }
+  if ((i >> 1) - 1 >= 0) ci[k++] = (i >> 1) - 1;
+  if ((i >> 1) < nc) ci[k++] = i >> 1;
   return k;
 }
 
-// u += P ec (or u = P ec when overwrite), bilinear / trilinear interpolation.
+// u += P ec (or u = P ec when overwrite), bilinear / trilinear interpolation.  All terms of a fine
+// point carry the same weight (1/2 per even axis), so they are summed first and scaled once.
 template <typename T, int DIM>
 __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restrict__ u, int overwrite,
                           const int* skip) {
@@ -134,19 +186,24 @@ __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restric
   int l = blockIdx.z;
   if (i >= d.f[0] || j >= d.f[1]) return;
   int ci[2], cj[2] = {0, 0}, cl[2] = {0, 0};
-  float wi[2], wj[2] = {1.f, 1.f}, wl[2] = {1.f, 1.f};
-  int ni = interp1(i, d.c[0], ci, wi);
-  int nj = DIM > 1 ? interp1(j, d.c[1], cj, wj) : 1;
-  int nl = DIM > 2 ? interp1(l, d.c[2], cl, wl) : 1;
+  int ni = interp1(i, d.c[0], ci);
+  int nj = DIM > 1 ? interp1(j, d.c[1], cj) : 1;
+  int nl = DIM > 2 ? interp1(l, d.c[2], cl) : 1;
+  T w = (i & 1) ? T(1) : T(0.5);
+  if (DIM > 1 && !(j & 1)) w *= T(0.5);
+  if (DIM > 2 && !(l & 1)) w *= T(0.5);
   cx<T> acc = mkc<T>(T(0), T(0));
   for (int c3 = 0; c3 < nl; ++c3)
-    for (int c2 = 0; c2 < nj; ++c2)
-      for (int c1 = 0; c1 < ni; ++c1) {
-        T wt = (T)wi[c1] * (T)wj[c2] * (T)wl[c3];
-        acc = cadd<T>(acc, cscale<T>(wt, ec[ci[c1] + (long)d.c[0] * (cj[c2] + (long)d.c[1] * cl[c3])]));
-      }
+    for (int c2 = 0; c2 < nj; ++c2) {
+      const cx<T>* row = ec + (long)d.c[0] * (cj[c2] + (long)d.c[1] * cl[c3]);
+      for (int c1 = 0; c1 < ni; ++c1) acc = cadd<T>(acc, row[ci[c1]]);
+    }
   long p = i + (long)d.f[0] * (j + (long)d.f[1] * l);
-  u[p] = overwrite ? acc : cadd<T>(u[p], acc);
+  if (overwrite) u[p] = cscale<T>(w, acc);
+  else {
+    cx<T> uo = u[p];
+    u[p] = mkc<T>(fma(w, acc.x, uo.x), fma(w, acc.y, uo.y));
+  }
 }
 
 // z = Ainv f, one warp per row of the dense inverse of the coarsest operator.
@@ -190,20 +247,36 @@ static void widen_c64(const helm_ctx*, const float2* a, double2* b, long n, cons
 }
 
 template <typename T>
-static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st);
+static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st,
+                           double2* wide = nullptr);
 
 template <typename T, int DIM> struct Launch {
   static void apply(const LevelHost& L, const cx<T>* x, const cx<T>* f, cx<T>* y, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
     launch_pdl(k_mg_apply<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
   }
-  static void jacobi(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* un, T omega, const int* skip, cudaStream_t st) {
+  static void jacobi(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* un, T omega, double2* wide,
+                     const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
-    launch_pdl(k_jacobi<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, skip);
+    launch_pdl(k_jacobi<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, wide, skip);
   }
-  static void rbgs(const LevelHost& L, cx<T>* u, const cx<T>* f, int colour, int zero, const int* skip, cudaStream_t st) {
-    dim3 g, b; cfg<DIM>(L.n, g, b);
-    launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, skip);
+  static void rbgs(const LevelHost& L, cx<T>* u, const cx<T>* f, int colour, int zero, double2* wide,
+                   const int* skip, cudaStream_t st) {
+    int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
+    dim3 g, b; cfg<DIM>(half, g, b);
+    launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
+  }
+  static void resid0(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* r, T omega, bool rb, const int* skip,
+                     cudaStream_t st) {
+    int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
+    dim3 g, b;
+    if (rb) {
+      cfg<DIM>(half, g, b);
+      launch_pdl(k_resid0<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+    } else {
+      cfg<DIM>(L.n, g, b);
+      launch_pdl(k_resid0<T, DIM, false>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+    }
   }
   static void restrict_(const LevelHost& F, const LevelHost& C, const cx<T>* r, cx<T>* fc, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; }
@@ -225,15 +298,22 @@ template <typename T> struct Ops {
     else if (dim == 2) Launch<T, 2>::apply(L, x, f, y, skip, st);
     else Launch<T, 3>::apply(L, x, f, y, skip, st);
   }
-  void jacobi(const cx<T>* u, const cx<T>* f, cx<T>* un, T om, const int* skip, cudaStream_t st) const {
-    if (dim == 1) Launch<T, 1>::jacobi(L, u, f, un, om, skip, st);
-    else if (dim == 2) Launch<T, 2>::jacobi(L, u, f, un, om, skip, st);
-    else Launch<T, 3>::jacobi(L, u, f, un, om, skip, st);
+  void jacobi(const cx<T>* u, const cx<T>* f, cx<T>* un, T om, const int* skip, cudaStream_t st,
+              double2* wide = nullptr) const {
+    if (dim == 1) Launch<T, 1>::jacobi(L, u, f, un, om, wide, skip, st);
+    else if (dim == 2) Launch<T, 2>::jacobi(L, u, f, un, om, wide, skip, st);
+    else Launch<T, 3>::jacobi(L, u, f, un, om, wide, skip, st);
   }
-  void rbgs(cx<T>* u, const cx<T>* f, int colour, int zero, const int* skip, cudaStream_t st) const {
-    if (dim == 1) Launch<T, 1>::rbgs(L, u, f, colour, zero, skip, st);
-    else if (dim == 2) Launch<T, 2>::rbgs(L, u, f, colour, zero, skip, st);
-    else Launch<T, 3>::rbgs(L, u, f, colour, zero, skip, st);
+  void rbgs(cx<T>* u, const cx<T>* f, int colour, int zero, const int* skip, cudaStream_t st,
+            double2* wide = nullptr) const {
+    if (dim == 1) Launch<T, 1>::rbgs(L, u, f, colour, zero, wide, skip, st);
+    else if (dim == 2) Launch<T, 2>::rbgs(L, u, f, colour, zero, wide, skip, st);
+    else Launch<T, 3>::rbgs(L, u, f, colour, zero, wide, skip, st);
+  }
+  void resid0(const cx<T>* u, const cx<T>* f, cx<T>* r, T om, bool rb, const int* skip, cudaStream_t st) const {
+    if (dim == 1) Launch<T, 1>::resid0(L, u, f, r, om, rb, skip, st);
+    else if (dim == 2) Launch<T, 2>::resid0(L, u, f, r, om, rb, skip, st);
+    else Launch<T, 3>::resid0(L, u, f, r, om, rb, skip, st);
   }
 };
 
@@ -258,18 +338,20 @@ static void coarse_solve(helm_ctx* c, const cx<T>* f, cx<T>* z, const int* skip,
 }
 
 // Smoothing sweeps on level L; buffers b[2] with *cur the index holding u.  zero: start from u = 0.
+// wide (optional): the last sweep also writes the result widened to complex128.
 template <typename T>
 static void smooth(helm_ctx* c, const LevelHost& L, cx<T>* b[2], int* cur, const cx<T>* f, int sweeps,
-                   bool zero, const int* skip, cudaStream_t st) {
+                   bool zero, const int* skip, cudaStream_t st, double2* wide = nullptr) {
   Ops<T> op{L, L.dim};
   for (int k = 0; k < sweeps; ++k) {
     bool z0 = zero && k == 0;
+    double2* w = k == sweeps - 1 ? wide : nullptr;
     if (c->pc.smoother == HELM_SM_JACOBI) {
-      op.jacobi(z0 ? nullptr : b[*cur], f, b[1 - *cur], (T)c->pc.omega, skip, st);
+      op.jacobi(z0 ? nullptr : b[*cur], f, b[1 - *cur], (T)c->pc.omega, skip, st, w);
       *cur = 1 - *cur;
     } else {
       op.rbgs(b[*cur], f, 0, z0 ? 1 : 0, skip, st);
-      op.rbgs(b[*cur], f, 1, 0, skip, st);
+      op.rbgs(b[*cur], f, 1, 0, skip, st, w);
     }
   }
 }
@@ -301,21 +383,24 @@ static void vcycle_level(helm_ctx* c, int l, const cx<T>* f, void* out, bool out
     return;
   }
   if (out_f64 && !std::is_same<T, double>::value) {
-    // one-kernel-per-component path: run in the multigrid precision, then widen
-    vcycle_level<T>(c, l, f, c->scratch, false, skip, st);
-    widen_c64(c, (const float2*)c->scratch, (double2*)out, L.ntot, skip, st);
+    // one-kernel-per-component path in the multigrid precision; the last sweep writes the
+    // complex128 result (or, without one, a separate widening pass)
+    vcycle_unfused<T>(c, l, f, (cx<T>*)c->scratch, skip, st, (double2*)out);
     return;
   }
   vcycle_unfused<T>(c, l, f, (cx<T>*)out, skip, st);
 }
 
-// the one-kernel-per-component V-cycle on level l (below it, fused levels may take over)
+// the one-kernel-per-component V-cycle on level l (below it, fused levels may take over); with
+// `wide` the result goes there as complex128 instead of to `out` (which is then scratch)
 template <typename T>
-static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st) {
+static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st,
+                           double2* wide) {
   const LevelHost& L = c->lv[l];
   int nl = (int)c->lv.size();
   if (l == nl - 1) {
     coarse_solve<T>(c, f, out, skip, st);
+    if (wide) widen_c64(c, (const float2*)out, wide, L.ntot, skip, st);
     return;
   }
   const LevelHost& C = c->lv[l + 1];
@@ -327,14 +412,17 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
   cx<T>* fc = (cx<T>*)C.f;
   if (pc.nu1 > 0) {
     smooth<T>(c, L, b, &cur, f, pc.nu1, true, skip, st);
-    op.apply(b[cur], f, b[1 - cur], skip, st);  // residual into the spare buffer
+    // residual into the spare buffer; after a single sweep from zero without the diagonal
+    if (pc.nu1 == 1) op.resid0(b[cur], f, b[1 - cur], (T)pc.omega, !jac, skip, st);
+    else op.apply(b[cur], f, b[1 - cur], skip, st);
     restrict_any<T>(L, C, b[1 - cur], fc, skip, st);
   } else {
     restrict_any<T>(L, C, f, fc, skip, st);
   }
   vcycle_level<T>(c, l + 1, fc, C.u, false, skip, st);
   prolong_any<T>(L, C, (const cx<T>*)C.u, b[cur], pc.nu1 > 0 ? 0 : 1, skip, st);
-  smooth<T>(c, L, b, &cur, f, pc.nu2, false, skip, st);
+  smooth<T>(c, L, b, &cur, f, pc.nu2, false, skip, st, wide);
+  if (wide && pc.nu2 == 0) widen_c64(c, (const float2*)b[cur], wide, L.ntot, skip, st);
 }
 
 template <typename T>
