@@ -102,8 +102,12 @@ typedef struct {
 
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
  * same arithmetic as the default fused kernels; for testing the fusion); HELM_PF_NO_PDL
- * launches the solve-path kernels without programmatic dependent launch (same kernels) */
-enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2 };
+ * launches the solve-path kernels without programmatic dependent launch (same kernels);
+ * HELM_PF_NO_AUTOTUNE skips the tile autotuner of helm_create (which times the large and small
+ * tiles of the fused 2D kernels on every fused level, keeps the faster, and caches the choice for
+ * the process by precision, smoother and level shape) and picks tiles by a block-count rule.
+ * Tiles change the speed only: every point is computed by the same formulas. */
+enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4 };
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
  * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;

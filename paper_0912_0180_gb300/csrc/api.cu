@@ -73,7 +73,7 @@ static helm_status check_precond(const helm_precond* p) {
   if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
   if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
   if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
-  if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
+  if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL | HELM_PF_NO_AUTOTUNE)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
   if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {
     set_error("non-finite preconditioner parameter");
     return HELM_ERR_ARG;

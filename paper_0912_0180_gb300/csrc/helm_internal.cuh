@@ -102,6 +102,8 @@ struct LevelHost {
   float2* dinv32 = nullptr;
   double2* dg64 = nullptr;   // the diagonal itself, same precision
   float2* dg32 = nullptr;
+  // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, -1 by the block-count rule
+  int tile_down = -1, tile_up = -1;
   // work vectors (MG type), allocated for multigrid levels
   void* u = nullptr;
   void* f = nullptr;
@@ -170,6 +172,7 @@ helm_status h_apply(helm_ctx* c, bool x_is_f32, const void* x, double2* y, cudaS
 helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st);
 
 // mg_fused.cu
+helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);
 template <typename T> int tail_first_level(const helm_ctx* c);
 template <typename T>
 helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,

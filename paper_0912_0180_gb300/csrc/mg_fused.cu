@@ -18,6 +18,9 @@
 //            kernel launches.
 //
 // Outside the grid every value is a Dirichlet zero, as in the unfused kernels.
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "stencil.cuh"
@@ -525,7 +528,7 @@ void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>*
   const LevelHost& F = c->lv[l];
   const LevelHost& C = c->lv[l + 1];
   long nb = (long)((C.n[0] + DN_CX - 1) / DN_CX) * ((C.n[1] + DN_CY - 1) / DN_CY);
-  bool big = big_tiles(c, nb);
+  bool big = F.tile_down >= 0 ? F.tile_down == 1 : big_tiles(c, nb);
   T om = (T)c->pc.omega;
   if (c->pc.smoother == HELM_SM_RBGS) {
     if (big) down_launch<T, true, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
@@ -548,7 +551,7 @@ template <typename T, typename TO>
 static void up_dispatch(const helm_ctx* c, const LevelHost& F, const LevelHost& C, const cx<T>* u_in, const cx<T>* ec,
                         const cx<T>* f, void* out, const int* skip, cudaStream_t st) {
   long nb = (long)((F.n[0] + UP_FX - 1) / UP_FX) * ((F.n[1] + UP_FY - 1) / UP_FY);
-  bool big = big_tiles(c, nb);
+  bool big = F.tile_up >= 0 ? F.tile_up == 1 : big_tiles(c, nb);
   T om = (T)c->pc.omega;
   TO* o = (TO*)out;
   if (c->pc.smoother == HELM_SM_RBGS) {
@@ -567,6 +570,88 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
   const LevelHost& C = c->lv[l + 1];
   if (out_f64) up_dispatch<T, double>(c, F, C, u_in, ec, f, out, skip, st);
   else up_dispatch<T, T>(c, F, C, u_in, ec, f, out, skip, st);
+}
+
+// ---- tile autotuner -------------------------------------------------------------------------
+// On every fused 2D level the large and the small tiles of k_down2d and k_up2d are timed with
+// CUDA events (mean of three launches after one warm-up) on zeroed buffers of the level's shape,
+// and the faster is kept.  Choices are cached for the process by (precision, smoother, level
+// shape), so contexts of shapes seen before skip the timing.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+}
+
+template <typename F_>
+static float time_variant(F_ launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  launch();
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < 3; ++r) launch();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms;
+}
+
+template <typename T, bool RB>
+static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
+  int nl = (int)c->lv.size();
+  int last = c->tail_first < nl - 1 ? c->tail_first : nl - 1;  // fused 2D levels: [0, last)
+  if (last <= 0 || c->lv[0].dim != 2 || c->pc.nu1 != 1 || c->pc.nu2 != 1) return HELM_OK;
+  std::vector<int> todo;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int l = 0; l < last; ++l) {
+      auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
+      if (it != g_tune.end()) {
+        c->lv[l].tile_down = it->second.first;
+        c->lv[l].tile_up = it->second.second;
+      } else {
+        todo.push_back(l);
+      }
+    }
+  }
+  if (todo.empty()) return HELM_OK;
+  size_t nf = (size_t)c->lv[todo.front()].ntot, ncs = (size_t)c->lv[todo.front() + 1].ntot;
+  void* buf = nullptr;
+  size_t bytes = sizeof(cx<T>) * (4 * nf + ncs);
+  HELM_CUDA(cudaMallocAsync(&buf, bytes, st));
+  HELM_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
+  cx<T>* f = (cx<T>*)buf;
+  cx<T>* u = f + nf;
+  cx<T>* o = u + nf;
+  cx<T>* w = o + nf;
+  cx<T>* fc = w + nf;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  T om = (T)c->pc.omega;
+  for (int l : todo) {
+    const LevelHost& F = c->lv[l];
+    const LevelHost& C = c->lv[l + 1];
+    float db = time_variant([&] { down_launch<T, RB, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
+    float ds = time_variant([&] { down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
+    float ub = time_variant([&] { up_launch<T, RB, T, UP_FX, UP_FY, FUSED_THREADS>(F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
+    float us = time_variant([&] { up_launch<T, RB, T, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
+    c->lv[l].tile_down = db <= ds ? 1 : 0;
+    c->lv[l].tile_up = ub <= us ? 1 : 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple((int)sizeof(T), (int)RB, F.n[0], F.n[1])] = {c->lv[l].tile_down, c->lv[l].tile_up};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, st);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status autotune_tiles(helm_ctx* c, cudaStream_t st) {
+  if ((c->pc.flags & (HELM_PF_NO_AUTOTUNE | HELM_PF_UNFUSED)) || c->pc.kind == HELM_PC_NONE || c->lv.empty())
+    return HELM_OK;
+  bool f32 = c->pc.mg_dtype == HELM_C64, rb = c->pc.smoother == HELM_SM_RBGS;
+  if (f32) return rb ? autotune_t<float, true>(c, st) : autotune_t<float, false>(c, st);
+  return rb ? autotune_t<double, true>(c, st) : autotune_t<double, false>(c, st);
 }
 
 template int tail_first_level<float>(const helm_ctx*);

@@ -567,7 +567,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     return HELM_ERR_ARG;
   }
   c->tail_first = f32 ? tail_first_level<float>(c) : tail_first_level<double>(c);
-  return HELM_OK;
+  return autotune_tiles(c, st);
 }
 
 helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st) {

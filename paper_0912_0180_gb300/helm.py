@@ -57,7 +57,7 @@ class Helm:
     """
 
     def __init__(self, problem, precond, mg_dtype: str = "c64", stream=None, fused: bool = True,
-                 pdl: bool = True):
+                 pdl: bool = True, autotune: bool = True):
         lib = L.load()
         self._lib = lib
         g = L.Grid()
@@ -77,7 +77,8 @@ class Helm:
                        complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
                        precond.omega, precond.max_levels, precond.coarse_max,
                        L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
-                       (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL))
+                       (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL)
+                       | (0 if autotune else L.HELM_PF_NO_AUTOTUNE))
         h = C.c_void_p()
         _check(lib.helm_create(C.byref(g), C.byref(k), C.byref(pc), C.c_void_p(_stream(stream)), C.byref(h)),
                "helm_create")

@@ -394,3 +394,22 @@ def test_vcycle_large_coarsest(shape, mg):
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
     assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
     h.close()
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("sm", [hi.SM_JACOBI, hi.SM_RBGS])
+def test_autotuned_tiles_give_the_same_vcycle(sm, mg):
+    """The tile autotuner changes speed only: the V-cycle with autotuned tiles equals, bitwise, the
+    one with tiles from the block-count rule, and both match the oracle."""
+    p = hi.make_problem(2, (561, 300), ((8, 7), (4, 4)), theta_gamma=0.5, k0=168.0, phi_kind="bump",
+                        rhs="random", seed=9, bump_centre=(0.3, 0.6))
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=sm)
+    r = cu(hi.random_vector(p.n, 6))
+    ha = Helm(p, pc, mg_dtype=mg, autotune=True)
+    hb = Helm(p, pc, mg_dtype=mg, autotune=False)
+    za, zb = ha.vcycle(r), hb.vcycle(r)
+    assert torch.equal(za, zb)
+    ref = Oracle(p, pc).vcycle(r.cpu().numpy())
+    assert rel(za.cpu().numpy().astype(np.complex128), ref) < (1e-10 if mg == "c128" else 5e-5)
+    ha.close()
+    hb.close()
