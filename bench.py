@@ -399,6 +399,11 @@ def main():
 # (8 complex adds and a scale per coarse unknown: 18 / 4).
 DOWN_FLOPS_PER_POINT = 6 + 16 + 18 / 4
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level launch of the fused
+# down kernel on this workload, from an ncu --set full capture of the current kernels (FP64, FP32);
+# set back to None whenever k_down2d changes.
+DOWN_TRAFFIC_BYTES = {"c128": 13132800, "c64": 6569728}
+
 
 def down_bytes_per_point(esz: int) -> float:
     return 3 * esz + esz / 4
@@ -423,7 +428,10 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
     st = torch.cuda.current_stream()
     table = {}
 
-    def time_cold(fn, reps=20) -> float:
+    def time_cold(fn, reps=20, name=None) -> float:
+        # an NVTX range per kernel, so that a profiler can select exactly these launches
+        if name:
+            torch.cuda.nvtx.range_push(name)
         fn()
         ts = []
         for _ in range(reps):
@@ -435,6 +443,8 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
             e1.record(st)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
+        if name:
+            torch.cuda.nvtx.range_pop()
         return statistics.median(ts) / 1000.0  # seconds
 
     for mg, dt, esz in (("c128", torch.complex128, 16), ("c64", torch.complex64, 8)):
@@ -443,19 +453,19 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
         f = torch.randn(n, dtype=dt, device=dev)
         u = torch.empty(n, dtype=dt, device=dev)
         fc = torch.empty(nc, dtype=dt, device=dev)
-        t = time_cold(lambda: h.level_op(L.HELM_OP_DOWN, 0, u, f, fc))
+        t = time_cold(lambda: h.level_op(L.HELM_OP_DOWN, 0, u, f, fc), name=f"k_down2d_{mg}")
         byt = n * down_bytes_per_point(esz)
         fl = n * DOWN_FLOPS_PER_POINT
         table[f"k_down2d_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9, "flops": fl,
                                    "TFLOP/s": fl / t / 1e12}
         r = torch.randn(n, dtype=torch.complex128, device=dev)
         z = torch.empty(n, dtype=dt, device=dev)
-        t = time_cold(lambda: h.vcycle(r, out=z))
+        t = time_cold(lambda: h.vcycle(r, out=z), name=f"vcycle_{mg}")
         table[f"vcycle_{mg}"] = {"us": t * 1e6}
     h = ctxs[("c128", "csg")]
     x = torch.randn(n, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)
-    t = time_cold(lambda: h.apply(x, out=y))
+    t = time_cold(lambda: h.apply(x, out=y), name="k_h_apply_c128")
     byt = n * (16 + 16 + 8)
     table["k_h_apply_c128"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9}
     for v in table.values():
@@ -464,11 +474,12 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
     d64, d32 = table["k_down2d_c128"], table["k_down2d_c64"]
     dominant = {"kernel": "k_down2d<double> (fused smooth + residual + full weighting, finest level, FP64 path)",
                 "bound": "alu", "achieved": d64["TFLOP/s"], "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": d64["TFLOP/s"] / fp64_peak, "traffic": None,
+                "frac": d64["TFLOP/s"] / fp64_peak, "traffic": DOWN_TRAFFIC_BYTES["c128"],
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "flops_per_launch": d64["flops"], "launch_us": d64["us"]}
     fp32 = {"kernel": "k_down2d<float> (same kernel in the FP32 V-cycle)", "bound": "hbm",
-            "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm, "traffic": None,
+            "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm,
+            "traffic": DOWN_TRAFFIC_BYTES["c64"],
             "peak_source": hbm_src, "bytes_per_launch": d32["bytes"], "launch_us": d32["us"]}
     return {"dominant": dominant, "fp32_mg": fp32, "table": table}
 
