@@ -103,10 +103,13 @@ typedef struct {
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
  * same arithmetic as the default fused kernels; for testing the fusion); HELM_PF_NO_PDL
  * launches the solve-path kernels without programmatic dependent launch (same kernels);
- * HELM_PF_NO_AUTOTUNE skips the tile autotuner of helm_create (which times the large and small
- * tiles of the fused 2D kernels on every fused level, keeps the faster, and caches the choice for
- * the process by precision, smoother and level shape) and picks tiles by a block-count rule.
- * Tiles change the speed only: every point is computed by the same formulas. */
+ * HELM_PF_NO_AUTOTUNE skips the autotuner of helm_create, which times the large, small and
+ * one-warp tiles of the fused 2D kernels on every fused level and then whole V-cycles for every
+ * admissible depth of the one-block tail kernel, keeps the fastest, and caches the choices for the
+ * process (tiles by precision, smoother and level shape; depth by precision, smoother and
+ * hierarchy); without it tiles follow a block-count rule and the tail a point budget.  Tiles
+ * change the speed only (every point is computed by the same formulas); the tail depth also
+ * changes the summation order inside the small levels, i.e. the rounding. */
 enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4 };
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence

@@ -30,10 +30,13 @@ namespace helm {
 // Tiles: the large ones (coarse 16 x 8 for k_down2d, fine 32 x 8 for k_up2d, 256 threads) on
 // levels with at least two blocks per SM; otherwise quarter / half tiles of 128 threads, so
 // that a small level still spreads over most SMs (in FP64 one block's arithmetic on one SM
-// otherwise sets the level's time).
-constexpr int DN_CX = 16, DN_CY = 8, DN_SCX = 8, DN_SCY = 4;
-constexpr int UP_FX = 32, UP_FY = 8, UP_SFX = 16, UP_SFY = 8;
-constexpr int FUSED_THREADS = 256, FUSED_SMALL_THREADS = 128;
+// otherwise sets the level's time).  The autotuner chooses among these and a one-warp tile.
+constexpr int DN_CX = 16, DN_CY = 8, DN_SCX = 8, DN_SCY = 4, DN_TCX = 4, DN_TCY = 2;
+constexpr int UP_FX = 32, UP_FY = 8, UP_SFX = 16, UP_SFY = 8, UP_TFX = 8, UP_TFY = 4;
+constexpr int FUSED_THREADS = 256, FUSED_SMALL_THREADS = 128, FUSED_TINY_THREADS = 32;
+// tile choices (LevelHost::tile_down / tile_up): the autotuner also tries a tiny tile of one warp,
+// which spreads a small FP64 level over many more SMs
+enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2 };
 
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
@@ -248,6 +251,8 @@ template <typename T> struct TailArgs {
   OpView<T> op[TAIL_MAX_LEVELS];
   int n[TAIL_MAX_LEVELS];
   int off[TAIL_MAX_LEVELS];         // offset (elements) of each level's vectors in shared memory
+  int toff[TAIL_MAX_LEVELS];        // offset of its coefficient tables (am, a0, ap per axis)
+  int aoff;                         // offset of the staged coarsest inverse, -1: read from global
   const cx<T>* ainv;
   int nco;
   int nu1, nu2, smoother;
@@ -283,8 +288,7 @@ __device__ __forceinline__ void tail_for_each(const int n[3], F&& body) {
 }
 
 template <typename T, int DIM>
-__device__ void tail_smooth(const TailArgs<T>& a, TailMem<T>& m, int k, bool zero) {
-  const OpView<T>& op = a.op[k];
+__device__ void tail_smooth(const TailArgs<T>& a, const OpView<T>& op, TailMem<T>& m, int k, bool zero) {
   cx<T>* u = m.U(k);
   const cx<T>* f = m.F(k);
   const cx<T>* sdinv = m.DI(k);  // omega / D (Jacobi) or 1 / D (Gauss-Seidel)
@@ -334,6 +338,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
   pdl_entry();
   if (skip && *skip) return;
   extern __shared__ unsigned char tail_smem[];
+  // every level's operator with its coefficient tables redirected to shared-memory copies, so
+  // that no phase waits on a global load
+  __shared__ OpView<T> sop[TAIL_MAX_LEVELS];
   TailMem<T> m{reinterpret_cast<cx<T>*>(tail_smem), &a, 0u};
   {
     cx<T>* F0 = m.F(0);
@@ -345,16 +352,43 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
         di[p] = a.op[k].dinv[p];
         dg[p] = a.op[k].dg[p];
       }
+      cx<T>* tb = m.base + a.toff[k];
+      for (int ax = 0; ax < DIM; ++ax) {
+        const int na = a.op[k].n[ax];
+        for (int q = threadIdx.x; q < 3 * na; q += TAIL_THREADS) {
+          const int which = q / na, idx = q - which * na;
+          const cx<T>* src = which == 0 ? a.op[k].am[ax] : (which == 1 ? a.op[k].a0[ax] : a.op[k].ap[ax]);
+          tb[q] = src[idx];
+        }
+        tb += 3 * na;
+      }
+    }
+    if (a.aoff >= 0) {
+      cx<T>* ai = m.base + a.aoff;
+      for (int q = threadIdx.x; q < a.nco * a.nco; q += TAIL_THREADS) ai[q] = a.ainv[q];
+    }
+    if (threadIdx.x < a.count) {
+      const int k = threadIdx.x;
+      OpView<T> v = a.op[k];
+      cx<T>* tb = m.base + a.toff[k];
+      for (int ax = 0; ax < DIM; ++ax) {
+        const int na = v.n[ax];
+        v.am[ax] = tb;
+        v.a0[ax] = tb + na;
+        v.ap[ax] = tb + 2 * na;
+        tb += 3 * na;
+      }
+      sop[k] = v;
     }
   }
   __syncthreads();
   const int last = a.count - 1;
   // down: smooth, residual, full weighting into the next level's f
   for (int k = 0; k < last; ++k) {
-    const OpView<T>& op = a.op[k];
+    const OpView<T>& op = sop[k];
     const int n = a.n[k];
     if (a.nu1 > 0) {
-      for (int s = 0; s < a.nu1; ++s) tail_smooth<T, DIM>(a, m, k, s == 0);
+      for (int s = 0; s < a.nu1; ++s) tail_smooth<T, DIM>(a, op, m, k, s == 0);
       cx<T>* u = m.U(k);
       cx<T>* w = m.W(k);
       const cx<T>* f = m.F(k);
@@ -369,7 +403,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
       for (int p = threadIdx.x; p < n; p += TAIL_THREADS) { w[p] = f[p]; u[p] = mkc<T>(T(0), T(0)); }
     }
     __syncthreads();
-    const OpView<T>& oc = a.op[k + 1];
+    const OpView<T>& oc = sop[k + 1];
     const cx<T>* r = m.W(k);
     cx<T>* fc = m.F(k + 1);
     const T wts[3] = {T(0.25), T(0.5), T(0.25)};
@@ -398,9 +432,10 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const cx<T>* fl = m.F(last);
     cx<T>* ul = m.U(last);
+    const cx<T>* ainv = a.aoff >= 0 ? m.base + a.aoff : a.ainv;
     for (int row = warp; row < a.nco; row += TAIL_THREADS / 32) {
       cx<T> acc = mkc<T>(T(0), T(0));
-      for (int c = lane; c < a.nco; c += 32) acc = cfma<T>(a.ainv[row * a.nco + c], fl[c], acc);
+      for (int c = lane; c < a.nco; c += 32) acc = cfma<T>(ainv[row * a.nco + c], fl[c], acc);
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
@@ -411,8 +446,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
   }
   // up: prolongation + correction, post-smoothing
   for (int k = last - 1; k >= 0; --k) {
-    const OpView<T>& op = a.op[k];
-    const OpView<T>& oc = a.op[k + 1];
+    const OpView<T>& op = sop[k];
+    const OpView<T>& oc = sop[k + 1];
     cx<T>* u = m.U(k);
     const cx<T>* e = m.U(k + 1);
     tail_for_each(op.n, [&](int i, int j, int l, int p) {
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
       u[p] = cadd<T>(u[p], acc);
     });
     __syncthreads();
-    for (int s = 0; s < a.nu2; ++s) tail_smooth<T, DIM>(a, m, k, false);
+    for (int s = 0; s < a.nu2; ++s) tail_smooth<T, DIM>(a, op, m, k, false);
   }
   {
     const cx<T>* u0 = m.U(0);
@@ -446,7 +481,7 @@ template <typename T> static long tail_point_budget() { return std::is_same<T, d
 constexpr size_t TAIL_SMEM_BUDGET = 200 * 1024;
 constexpr size_t TAIL_INVERSE_BYTES = 1 << 20;
 
-template <typename T> int tail_first_level(const helm_ctx* c) {
+template <typename T> int tail_first_level(const helm_ctx* c, long point_budget) {
   int nl = (int)c->lv.size();
   long pts = c->lv[nl - 1].ntot;
   size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
@@ -457,7 +492,7 @@ template <typename T> int tail_first_level(const helm_ctx* c) {
   while (first > 0 && nl - (first - 1) <= TAIL_MAX_LEVELS) {
     long np = pts + c->lv[first - 1].ntot;
     size_t nb = bytes + TAIL_VECS * sizeof(cx<T>) * c->lv[first - 1].ntot;
-    if (np > tail_point_budget<T>() || nb > TAIL_SMEM_BUDGET) break;
+    if (np > point_budget || nb > TAIL_SMEM_BUDGET) break;
     pts = np;
     bytes = nb;
     --first;
@@ -499,8 +534,18 @@ helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool 
     a.off[k] = off;
     off += TAIL_VECS * (int)L.ntot;
   }
+  for (int k = 0; k < a.count; ++k) {
+    const LevelHost& L = c->lv[first + k];
+    a.toff[k] = off;
+    for (int ax = 0; ax < L.dim; ++ax) off += 3 * L.n[ax];
+  }
   a.ainv = (const cx<T>*)c->coarse_inv;
   a.nco = c->nco;
+  a.aoff = -1;
+  if ((size_t)(off + c->nco * c->nco) * sizeof(cx<T>) <= TAIL_SMEM_BUDGET) {
+    a.aoff = off;
+    off += c->nco * c->nco;
+  }
   a.nu1 = c->pc.nu1;
   a.nu2 = c->pc.nu2;
   a.smoother = c->pc.smoother;
@@ -523,20 +568,23 @@ static void down_launch(const LevelHost& F, const LevelHost& C, const cx<T>* f, 
   launch_pdl(k_down2d<T, RB, CX, CY, NT>, dim3(g), dim3(NT), 0, st, F.view<T>(), C.n[0], C.n[1], f, u_out, fc, om, skip);
 }
 
+template <typename T, bool RB>
+static void down_tile(int tile, const LevelHost& F, const LevelHost& C, const cx<T>* f, cx<T>* u_out, cx<T>* fc, T om,
+                      const int* skip, cudaStream_t st) {
+  if (tile == TILE_BIG) down_launch<T, RB, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  else if (tile == TILE_TINY) down_launch<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  else down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
+}
+
 template <typename T>
 void fused_down2d(const helm_ctx* c, int l, const cx<T>* f, cx<T>* u_out, cx<T>* fc, const int* skip, cudaStream_t st) {
   const LevelHost& F = c->lv[l];
   const LevelHost& C = c->lv[l + 1];
   long nb = (long)((C.n[0] + DN_CX - 1) / DN_CX) * ((C.n[1] + DN_CY - 1) / DN_CY);
-  bool big = F.tile_down >= 0 ? F.tile_down == 1 : big_tiles(c, nb);
+  int tile = F.tile_down >= 0 ? F.tile_down : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
   T om = (T)c->pc.omega;
-  if (c->pc.smoother == HELM_SM_RBGS) {
-    if (big) down_launch<T, true, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
-    else down_launch<T, true, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
-  } else {
-    if (big) down_launch<T, false, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
-    else down_launch<T, false, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
-  }
+  if (c->pc.smoother == HELM_SM_RBGS) down_tile<T, true>(tile, F, C, f, u_out, fc, om, skip, st);
+  else down_tile<T, false>(tile, F, C, f, u_out, fc, om, skip, st);
 }
 
 template <typename T, bool RB, typename TO, int FX, int FY, int NT>
@@ -547,20 +595,23 @@ static void up_launch(const LevelHost& F, const LevelHost& C, const cx<T>* u_in,
              (cx<TO>*)out, om, skip);
 }
 
+template <typename T, bool RB, typename TO>
+static void up_tile(int tile, const LevelHost& F, const LevelHost& C, const cx<T>* u_in, const cx<T>* ec,
+                    const cx<T>* f, TO* o, T om, const int* skip, cudaStream_t st) {
+  if (tile == TILE_BIG) up_launch<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  else if (tile == TILE_TINY) up_launch<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  else up_launch<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+}
+
 template <typename T, typename TO>
 static void up_dispatch(const helm_ctx* c, const LevelHost& F, const LevelHost& C, const cx<T>* u_in, const cx<T>* ec,
                         const cx<T>* f, void* out, const int* skip, cudaStream_t st) {
   long nb = (long)((F.n[0] + UP_FX - 1) / UP_FX) * ((F.n[1] + UP_FY - 1) / UP_FY);
-  bool big = F.tile_up >= 0 ? F.tile_up == 1 : big_tiles(c, nb);
+  int tile = F.tile_up >= 0 ? F.tile_up : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
   T om = (T)c->pc.omega;
   TO* o = (TO*)out;
-  if (c->pc.smoother == HELM_SM_RBGS) {
-    if (big) up_launch<T, true, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
-    else up_launch<T, true, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
-  } else {
-    if (big) up_launch<T, false, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
-    else up_launch<T, false, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
-  }
+  if (c->pc.smoother == HELM_SM_RBGS) up_tile<T, true, TO>(tile, F, C, u_in, ec, f, o, om, skip, st);
+  else up_tile<T, false, TO>(tile, F, C, u_in, ec, f, o, om, skip, st);
 }
 
 template <typename T>
@@ -572,15 +623,20 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
   else up_dispatch<T, T>(c, F, C, u_in, ec, f, out, skip, st);
 }
 
-// ---- tile autotuner -------------------------------------------------------------------------
-// On every fused 2D level the large and the small tiles of k_down2d and k_up2d are timed with
+// ---- autotuner ------------------------------------------------------------------------------
+// On every fused 2D level the large, small and one-warp tiles of k_down2d and k_up2d are timed with
 // CUDA events (mean of three launches after one warm-up) on zeroed buffers of the level's shape,
-// and the faster is kept.  Choices are cached for the process by (precision, smoother, level
-// shape), so contexts of shapes seen before skip the timing.
+// and the fastest is kept; then whole V-cycles are timed for every admissible depth of the
+// one-block tail (from the deepest that fits its budgets to none) and the fastest depth is kept.
+// Choices are cached for the process (tiles by precision, smoother and level shape; depth by
+// precision, smoother and hierarchy), so contexts of shapes seen before skip the timing.
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;       // tiles per level shape
+std::map<std::tuple<int, int, int, int, int, int, int>, int> g_depth;       // tail depth per hierarchy
 }
+// the tail depths the autotuner tries are bounded by this many points (and by shared memory)
+constexpr long TAIL_TUNE_POINTS = 700;
 
 template <typename F_>
 static float time_variant(F_ launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
@@ -597,12 +653,13 @@ static float time_variant(F_ launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_
 template <typename T, bool RB>
 static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   int nl = (int)c->lv.size();
-  int last = c->tail_first < nl - 1 ? c->tail_first : nl - 1;  // fused 2D levels: [0, last)
-  if (last <= 0 || c->lv[0].dim != 2 || c->pc.nu1 != 1 || c->pc.nu2 != 1) return HELM_OK;
+  if (nl < 2) return HELM_OK;
+  const bool fused2d = c->lv[0].dim == 2 && c->pc.nu1 == 1 && c->pc.nu2 == 1;
+  // 1. tiles of every level that can run the fused 2D kernels
   std::vector<int> todo;
-  {
+  if (fused2d) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (int l = 0; l < last; ++l) {
+    for (int l = 0; l < nl - 1; ++l) {
       auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
       if (it != g_tune.end()) {
         c->lv[l].tile_down = it->second.first;
@@ -612,8 +669,20 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
       }
     }
   }
-  if (todo.empty()) return HELM_OK;
-  size_t nf = (size_t)c->lv[todo.front()].ntot, ncs = (size_t)c->lv[todo.front() + 1].ntot;
+  // 2. depth of the one-block tail: from the deepest the shared-memory and point budgets admit to none
+  const int deepest = tail_first_level<T>(c, TAIL_TUNE_POINTS);
+  auto dkey = std::make_tuple((int)sizeof(T), (int)RB, c->lv[0].dim, c->lv[0].n[0], c->lv[0].n[1], c->lv[0].n[2], nl);
+  bool tune_depth = deepest < nl;
+  if (tune_depth) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_depth.find(dkey);
+    if (it != g_depth.end()) {
+      c->tail_first = it->second;
+      tune_depth = false;
+    }
+  }
+  if (todo.empty() && !tune_depth) return HELM_OK;
+  size_t nf = (size_t)c->lv[0].ntot, ncs = (size_t)c->lv[1].ntot;
   void* buf = nullptr;
   size_t bytes = sizeof(cx<T>) * (4 * nf + ncs);
   HELM_CUDA(cudaMallocAsync(&buf, bytes, st));
@@ -623,6 +692,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   cx<T>* o = u + nf;
   cx<T>* w = o + nf;
   cx<T>* fc = w + nf;
+  (void)w;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -630,14 +700,30 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   for (int l : todo) {
     const LevelHost& F = c->lv[l];
     const LevelHost& C = c->lv[l + 1];
-    float db = time_variant([&] { down_launch<T, RB, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
-    float ds = time_variant([&] { down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
-    float ub = time_variant([&] { up_launch<T, RB, T, UP_FX, UP_FY, FUSED_THREADS>(F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
-    float us = time_variant([&] { up_launch<T, RB, T, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
-    c->lv[l].tile_down = db <= ds ? 1 : 0;
-    c->lv[l].tile_up = ub <= us ? 1 : 0;
+    int best_d = TILE_BIG, best_u = TILE_BIG;
+    float td = 1e30f, tu = 1e30f;
+    for (int tile : {TILE_BIG, TILE_SMALL, TILE_TINY}) {
+      float a = time_variant([&] { down_tile<T, RB>(tile, F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
+      float b = time_variant([&] { up_tile<T, RB, T>(tile, F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
+      if (a < td) { td = a; best_d = tile; }
+      if (b < tu) { tu = b; best_u = tile; }
+    }
+    c->lv[l].tile_down = best_d;
+    c->lv[l].tile_up = best_u;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[std::make_tuple((int)sizeof(T), (int)RB, F.n[0], F.n[1])] = {c->lv[l].tile_down, c->lv[l].tile_up};
+  }
+  if (tune_depth) {
+    int best = c->tail_first;
+    float tb = 1e30f;
+    for (int first = deepest; first <= nl; ++first) {
+      c->tail_first = first;
+      float t = time_variant([&] { mg_vcycle<T>(c, f, (void*)u, false, nullptr, st); }, st, e0, e1);
+      if (t < tb) { tb = t; best = first; }
+    }
+    c->tail_first = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_depth[dkey] = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -654,6 +740,7 @@ helm_status autotune_tiles(helm_ctx* c, cudaStream_t st) {
   return rb ? autotune_t<double, true>(c, st) : autotune_t<double, false>(c, st);
 }
 
+template <typename T> int tail_first_level(const helm_ctx* c) { return tail_first_level<T>(c, tail_point_budget<T>()); }
 template int tail_first_level<float>(const helm_ctx*);
 template int tail_first_level<double>(const helm_ctx*);
 template helm_status tail_vcycle<float>(helm_ctx*, int, const float2*, void*, bool, const int*, cudaStream_t);

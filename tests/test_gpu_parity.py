@@ -399,8 +399,9 @@ def test_vcycle_large_coarsest(shape, mg):
 @pytest.mark.parametrize("mg", ["c128", "c64"])
 @pytest.mark.parametrize("sm", [hi.SM_JACOBI, hi.SM_RBGS])
 def test_autotuned_tiles_give_the_same_vcycle(sm, mg):
-    """The tile autotuner changes speed only: the V-cycle with autotuned tiles equals, bitwise, the
-    one with tiles from the block-count rule, and both match the oracle."""
+    """The autotuner changes speed, not the method: its tiles regroup identical per-point formulas
+    and its tail depth moves levels between kernels that sum in different orders, so the V-cycle
+    equals the rule-chosen one to rounding, and both match the oracle."""
     p = hi.make_problem(2, (561, 300), ((8, 7), (4, 4)), theta_gamma=0.5, k0=168.0, phi_kind="bump",
                         rhs="random", seed=9, bump_centre=(0.3, 0.6))
     pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=sm)
@@ -408,7 +409,7 @@ def test_autotuned_tiles_give_the_same_vcycle(sm, mg):
     ha = Helm(p, pc, mg_dtype=mg, autotune=True)
     hb = Helm(p, pc, mg_dtype=mg, autotune=False)
     za, zb = ha.vcycle(r), hb.vcycle(r)
-    assert torch.equal(za, zb)
+    assert rel(za.cpu().numpy(), zb.cpu().numpy()) < (1e-13 if mg == "c128" else 2e-6)
     ref = Oracle(p, pc).vcycle(r.cpu().numpy())
     assert rel(za.cpu().numpy().astype(np.complex128), ref) < (1e-10 if mg == "c128" else 5e-5)
     ha.close()
