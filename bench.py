@@ -348,6 +348,9 @@ def main():
 
     # ---- per-kernel rooflines, measured with CUDA events on the launching stream ----
     kern = kernel_rooflines(torch, L, ctxs, p, dev, flush)
+    # ---- solution error per tolerance against a tight FP64 solve (untimed; Bi-CGSTAB, CSG) ----
+    import bench_workloads
+    err = bench_workloads._errors_vs_reference(torch, {mg: ctxs[(mg, "csg")] for mg in ("c128", "c64")}, b_dev)
 
     def pct(v, q):
         return float(np.percentile(np.asarray(v), q))
@@ -364,6 +367,7 @@ def main():
                     "matvecs": {f"{m}-{pc}": inf32[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)},
                     "max_true_rel_res": max(i.rel_res_true for i in inf32)},
         "max_true_rel_res": max(i.rel_res_true for i in inf64),
+        "error_vs_reference": err,
         "clocks": clk.summary(),
         "e2e": {"value": nsol / (stepe2e / 1000), "unit": "solves/s",
                 "h2d_bytes_per_step": len(SOLVES) * p.n * 16, "d2h_bytes_per_step": len(SOLVES) * p.n * 16},

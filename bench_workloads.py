@@ -133,6 +133,7 @@ def run_3d(args, torch, ranks, dev, local):
     e2e_ms, _, _ = timed("c64", e2e=True)
     _check(inf64 + inf32, "3d160")
     diff = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    err = _errors_vs_reference(torch, ctx, b_dev)
     step64 = ranks.max(statistics.mean(ms64))
     step32 = ranks.max(statistics.mean(ms32))
     kern = _kernels_3d(torch, L, ctx, p, dev, flush)
@@ -150,6 +151,7 @@ def run_3d(args, torch, ranks, dev, local):
                     "latency_ms": {"p50": _pct(ms32, 50), "p99": _pct(ms32, 99)},
                     "matvecs": inf32[-1].matvecs, "max_true_rel_res": max(i.rel_res_true for i in inf32),
                     "rel_diff_vs_fp64_solution": diff},
+        "error_vs_reference": err,
         "create_s": create_s,
         "clocks": clk.summary(),
         "e2e": {"value": ranks.world / (ranks.max(statistics.mean(e2e_ms)) / 1000), "unit": "solves/s",
@@ -161,6 +163,21 @@ def run_3d(args, torch, ranks, dev, local):
     for h in ctx.values():
         h.close()
     return line
+
+
+def _errors_vs_reference(torch, ctx, b, method=0, shadow=None):
+    """Relative error of both paths' solutions at tol 1e-6 and 1e-7 against the FP64 path's
+    solution at tol 1e-10 (untimed): two solutions that each meet a 1e-6 residual differ by up to
+    cond(H) x 1e-6 whatever the V-cycle precision, so the error is reported per tolerance."""
+    xr, ir = ctx["c128"].solve(b, method=method, s=4, tol=1e-10, maxmv=8000, shadow=shadow)
+    nr = torch.linalg.vector_norm(xr)
+    out = {"reference": "FP64 path at tol 1e-10", "reference_true_rel_res": ir.rel_res_true}
+    for mg in ("c128", "c64"):
+        for tol in (1e-6, 1e-7):
+            x, info = ctx[mg].solve(b, method=method, s=4, tol=tol, maxmv=8000, shadow=shadow)
+            key = ("fp64" if mg == "c128" else "fp32_mg") + f"_tol{tol:.0e}"
+            out[key] = float(torch.linalg.vector_norm(x - xr) / nr)
+    return out
 
 
 def _time_cold(torch, flush, fn, reps=10):

@@ -57,6 +57,7 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
   size_t bytes = 0;
   for (int a = 0; a < g->dim; ++a) bytes += (size_t)(n[a] + 1) * 16 * 4;  // H tables
   bytes += (size_t)N * 8;                                                 // phi
+  bytes += (size_t)N * 16;                                                // diagonal of H
   bool pcon = pc->kind != HELM_PC_NONE;
   size_t esz = pcon && pc->mg_dtype == HELM_C64 ? 8 : 16;
   if (pcon) {

@@ -95,8 +95,10 @@ __global__ void k_dinv(OpView<double> op, double omega_s, double2* d64, float2* 
   double ph = op.phi ? op.phi[p] : op.phi0;
   d = csub<double>(d, cscale<double>(ph, op.s));
   double2 r = cscale<double>(omega_s, crecip<double>(d));
-  if (d64) { d64[p] = r; g64[p] = d; }
-  if (d32) { d32[p] = cconv<float, double>(r); g32[p] = cconv<float, double>(d); }
+  if (d64) d64[p] = r;
+  if (g64) g64[p] = d;
+  if (d32) d32[p] = cconv<float, double>(r);
+  if (g32) g32[p] = cconv<float, double>(d);
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
@@ -407,6 +409,18 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
   if (k->phi) {
     if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
     HELM_CUDA(cudaMemcpyAsync(H.phi64, k->phi, sizeof(double) * H.ntot, cudaMemcpyHostToDevice, st));
+  }
+  // the diagonal of H at every point: outside the uniform interior the stencil kernels read it
+  // instead of summing the axes' centre coefficients and subtracting phi (FP64 operations are
+  // what bound them; the 16 B per point are cheap)
+  if ((s = ctx_alloc(c, (void**)&H.dg64, sizeof(double2) * H.ntot)) != HELM_OK) return s;
+  {
+    OpView<double> v = H.view<double>();
+    dim3 g((H.n[0] + 127) / 128, H.n[1], H.n[2]);
+    if (H.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, 1.0, nullptr, nullptr, H.dg64, nullptr);
+    else if (H.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, 1.0, nullptr, nullptr, H.dg64, nullptr);
+    else k_dinv<3><<<g, 128, 0, st>>>(v, 1.0, nullptr, nullptr, H.dg64, nullptr);
+    HELM_CUDA(cudaGetLastError());
   }
   return HELM_OK;
 }

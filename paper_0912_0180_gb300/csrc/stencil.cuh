@@ -77,7 +77,8 @@ __device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* _
 }
 
 // (A x)_P.  In the uniform interior of an operator with real coefficients (H) the diagonal
-// ud - s phi_P is real and multiplies x_P with two FMAs.
+// ud - s phi_P is real and multiplies x_P with two FMAs; elsewhere the stored diagonal is read
+// when the operator has one.
 template <typename T, typename TX, int DIM>
 __device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __restrict__ x, int i,
                                         int j, int l, long p) {
@@ -91,10 +92,15 @@ __device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __res
     }
     return cfma<T>(csub<T>(op.ud, cscale<T>(ph, op.s)), xp, off);
   }
-  cx<T> d = op.a0[0][i];
-  if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
-  if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
-  d = csub<T>(d, cscale<T>(ph, op.s));
+  cx<T> d;
+  if (op.dg) {
+    d = op.dg[p];  // the stored diagonal
+  } else {
+    d = op.a0[0][i];
+    if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
+    if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
+    d = csub<T>(d, cscale<T>(ph, op.s));
+  }
   return cfma<T>(d, xp, op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p));
 }
 
