@@ -213,6 +213,8 @@ def main():
                     help="2d640 (default): the 512^2 + 64-layer four-solve step; 3d160: 128^3 + 16-layer "
                          "k = 40 mixed-precision solve; batch256: 256 uneven 2D instances per step; "
                          "serve: a Poisson-arrival request stream through the solve server")
+    ap.add_argument("--serve-requests", type=int, default=32, help="serve: requests in the stream")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: mean arrival rate (requests/s)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

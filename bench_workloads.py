@@ -9,10 +9,11 @@
   batch256  256 independent 2D instances (interior 63..511 per axis, 16..32-node layers, kh in
             [0.3, 0.6], constant or bump k, seeded point sources); one step solves all of them with
             helm_solve_batch (Bi-CGSTAB, CSG omega-Jacobi V(1,1), 1e-6).
-  serve     a Poisson-arrival stream (mean 200 requests/s) of 2D (127^2 .. 1023^2 interior) and 3D
-            (64^3 .. 160^3 interior) requests with 1..8 point-source right-hand sides each, submitted
-            at their arrival times to the solve server (150 GB budget); reports right-hand-side
-            solves/s and the server's submit-to-completion latencies.
+  serve     a Poisson-arrival stream (--serve-requests, default 32, at --serve-rate, default 200
+            requests/s) of 2D (127^2 .. 1023^2 interior) and 3D (64^3 .. 160^3 interior) requests
+            with 1..8 point-source right-hand sides each, submitted at their arrival times to the
+            solve server (150 GB budget); reports right-hand-side solves/s and the server's
+            submit-to-completion latencies.
 
 Every timed solve is certified by the FP64 true residual; a step whose solves did not all reach
 1e-6 aborts the run.
@@ -342,7 +343,7 @@ def _stream(torch, reqs, mg, budget):
 
 def run_serve(args, torch, ranks, dev, local):
     import bench
-    reqs = hi.workload_serve()
+    reqs = hi.workload_serve(args.serve_requests, args.serve_rate)
     budget = 150 * 10**9
     nsol = int(sum(r.rhs.shape[0] for r in reqs))
     res = {}
@@ -362,15 +363,18 @@ def run_serve(args, torch, ranks, dev, local):
     diff = max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(o32, o64))
     lat64 = [o[2] * 1000 for o in o64]
     lat32 = [o[2] * 1000 for o in o32]
-    cfg = {"workload": "serve-stream-32", "requests": len(reqs), "rhs_solves": nsol,
-           "arrivals": "Poisson, mean 200 requests/s", "mix": "3/4 2D (127..1023 interior, 32-node layers), "
-           "1/4 3D (64..160 interior, 16-node layers), 1..8 point-source right-hand sides each",
+    cfg = {"workload": f"serve-stream-{len(reqs)}", "requests": len(reqs), "rhs_solves": nsol,
+           "arrivals": f"Poisson, mean {args.serve_rate:g} requests/s (offered)",
+           "mix": "1/2 2D (interior 127..1023), 1/2 3D (interior 64..160), 16..32-node layers, kh 0.3..0.6, "
+                  "1..8 point-source right-hand sides each",
+           "n_unknowns_total": int(sum(r.problem.n * r.rhs.shape[0] for r in reqs)),
            "server": "150 GB budget, 8 slots", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
            "timing": "wall clock from the first arrival to the last completion (host in, host out)"}
     line = _base(args, ranks.job_rate(nsol, w64 * 1000), w64 * 1000, ranks.world, cfg, "c128")
     line.update({
         "latency_ms": {"p50": _pct(lat64, 50), "p99": _pct(lat64, 99)},
         "requests_per_s": len(reqs) / w64,
+        "offered_requests_per_s": args.serve_rate,
         "fp32_mg": {"value": nsol / w32, "unit": "solves/s", "ms_per_step": w32 * 1000,
                     "requests_per_s": len(reqs) / w32,
                     "latency_ms": {"p50": _pct(lat32, 50), "p99": _pct(lat32, 99)},

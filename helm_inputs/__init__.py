@@ -217,22 +217,21 @@ class ServeRequest:
     rhs: np.ndarray           # nrhs x N complex128 point sources
 
 
-def workload_serve(count: int = 32, rate_hz: float = 200.0, frac_3d: float = 0.25,
+def workload_serve(count: int = 32, rate_hz: float = 200.0, frac_3d: float = 0.5,
                    seed: int = BASE_SEED + 5) -> List[ServeRequest]:
     """Poisson-arrival request stream: exponential gaps of mean 1/rate_hz; 2D requests with
-    n_int in {127, 255, 511, 1023} and 32-node layers, 3D requests with n_int uniform in
-    [64, 160] and 16-node layers; kh uniform in [0.3, 0.6] (2D) or [0.25, 0.4] (3D); k constant or
-    a Gaussian bump (amplitude 0..0.4, seeded centre); 1..8 right-hand sides per request, each a
-    unit point source at a seeded interior node."""
+    n_int in {127, 255, 511, 1023}, 3D requests with n_int in {64, 96, 128, 160} (3D with
+    probability frac_3d); layers of 16..32 nodes per side; kh uniform in [0.3, 0.6]; k constant
+    or (probability 1/2) a Gaussian bump of amplitude 0..0.4 at a seeded centre; 1..8 right-hand
+    sides per request, each a unit point source at a seeded interior node."""
     rng = np.random.default_rng(seed)
     out, t = [], 0.0
     for i in range(count):
         t += float(rng.exponential(1.0 / rate_hz))
         dim = 3 if rng.uniform() < frac_3d else 2
-        if dim == 2:
-            n_int, n_l, kh = int(rng.choice([127, 255, 511, 1023])), 32, float(rng.uniform(0.3, 0.6))
-        else:
-            n_int, n_l, kh = int(rng.integers(64, 161)), 16, float(rng.uniform(0.25, 0.4))
+        n_int = int(rng.choice([127, 255, 511, 1023] if dim == 2 else [64, 96, 128, 160]))
+        n_l = int(rng.integers(16, 33))
+        kh = float(rng.uniform(0.3, 0.6))
         bump = bool(rng.integers(0, 2))
         amp = float(rng.uniform(0.0, 0.4)) if bump else 0.0
         cen = tuple(rng.uniform(0.2, 0.8, 3))
