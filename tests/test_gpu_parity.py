@@ -414,3 +414,49 @@ def test_autotuned_tiles_give_the_same_vcycle(sm, mg):
     assert rel(za.cpu().numpy().astype(np.complex128), ref) < (1e-10 if mg == "c128" else 5e-5)
     ha.close()
     hb.close()
+
+
+def test_large_3d_workload_sampled():
+    """The 128^3 + 16-layer, k = 40 workload at full size in the benchmark's configuration (CSG,
+    red-black Gauss-Seidel V(1,1) on 4 levels, coarsest 20^3 inverted densely): the matvec element
+    by element against the oracle; the V-cycle by properties that hold at any size (linearity, and
+    the FP32 cycle against the FP64 one); both solves certified by the oracle's own residual."""
+    p = hi.workload_3d_128()
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS, max_levels=4)
+    o = Oracle(p, hi.Precond(kind=hi.PC_NONE))
+    h64 = Helm(p, pc, mg_dtype="c128")
+    h32 = Helm(p, pc, mg_dtype="c64")
+    assert h64.nlev == 4 and tuple(h64.level_shape(3)[:3]) == (20, 20, 20)
+    x = hi.random_vector(p.n, 4)
+    y = hi.random_vector(p.n, 5)
+    assert rel(h64.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    a, b = 0.7 - 0.2j, -1.3 + 0.4j
+    vx, vy = h64.vcycle(cu(x)), h64.vcycle(cu(y))
+    vxy = h64.vcycle(cu(a * x + b * y))
+    assert rel(vxy.cpu().numpy(), (a * vx + b * vy).cpu().numpy()) < 1e-12
+    assert rel(h32.vcycle(cu(x)).cpu().numpy().astype(np.complex128), vx.cpu().numpy()) < 5e-5
+    for h in (h64, h32):
+        xs, info = h.solve(cu(p.b), tol=1e-6, maxmv=3000)
+        assert info.status == 0 and info.rel_res_true < 1e-6
+        r = p.b - o.apply(xs.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(p.b) < 1e-6
+    h64.close()
+    h32.close()
+
+
+def test_batch256_workload_sampled():
+    """All 256 instances of the uneven batch in one helm_solve_batch call (FP32 multigrid, the
+    benchmark's configuration); a seeded sample of them certified by the oracle's own residual."""
+    from paper_0912_0180_gb300.helm import solve_batch
+    inst = hi.workload_batch_2d(256)
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    hs = [Helm(p, pc, mg_dtype="c64") for p in inst]
+    xs, infos = solve_batch(hs, [cu(p.b) for p in inst], tol=1e-6, maxmv=4000)
+    assert all(i.status == 0 and i.rel_res_true < 1e-6 for i in infos)
+    rng = np.random.default_rng(7)
+    for k in rng.choice(len(inst), 8, replace=False):
+        p = inst[k]
+        r = p.b - Oracle(p, hi.Precond(kind=hi.PC_NONE)).apply(xs[k].cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(p.b) < 1e-6
+    for h in hs:
+        h.close()
