@@ -213,6 +213,10 @@ def _time_cold(torch, flush, fn, reps=10, name=None):
 # with x added to the neighbour sum (4); counted as operations, not FMA-doubled flops.
 H3D_FP64_OPS_PER_POINT = 17
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_h_apply<double, 3> launch on
+# this workload, from an ncu --set full capture of the current kernel; None whenever it changes.
+H3D_TRAFFIC_BYTES = 102660864 + 35742720
+
 
 def _kernels_3d(torch, L, ctx, p, dev, flush):
     n = p.n
@@ -238,7 +242,7 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
     achieved = a["fp64_ops"] / (a["us"] / 1e6) / 1e12
     dom = {"kernel": "k_h_apply<double, 3> (FP64 Helmholtz matvec; the stencil of the Krylov kernels)",
            "bound": "alu", "achieved": achieved, "peak": fp64_ops_peak, "unit": "T FP64 op/s",
-           "frac": achieved / fp64_ops_peak, "traffic": None,
+           "frac": achieved / fp64_ops_peak, "traffic": H3D_TRAFFIC_BYTES,
            "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
            "launch_us": a["us"]}
     return {"dominant": dom, "table": table}
