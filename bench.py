@@ -7,7 +7,10 @@ Workload (one "step"): the 2D ECS Helmholtz problem with a 512 x 512 interior gr
 seeded position, solved to a relative residual of 1e-6 four times:
 {Bi-CGSTAB, IDR(4)} x {CSG theta_beta = 0.3, CSL shift 1 + 0.5i}, one V(1,1) cycle with
 omega-Jacobi (0.5) per preconditioned matvec.  Every solve is certified by the FP64 true
-residual ||b - H x|| / ||b|| < 1e-6 recomputed on the device.
+residual ||b - H x|| / ||b|| < 1e-6 recomputed on the device.  The four solves of a step run at
+once through helm_solve_batch (one context and one stream each; a lone 640^2 solve leaves much of
+the GPU idle in its small multigrid levels and reductions); the same solves one after another
+give each solve's latency (`latency_ms`) and the `sequential` throughput.
 
 `value` is the all-FP64 path (FP64 V-cycle and Krylov); the FP32-multigrid path (FP32 V-cycle,
 FP64 Krylov and true residual) is measured on the same step and reported beside it.
@@ -46,10 +49,12 @@ def precond(name: str) -> hi.Precond:
     return hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
 
 
-def config(p) -> dict:
+def config(p, concurrent=True) -> dict:
     return {"workload": p.name, "grid": "512^2 interior + 64 ECS nodes per side (640^2 unknowns)",
             "n_unknowns": p.n, "solves_per_step": len(SOLVES),
             "solves": "{Bi-CGSTAB, IDR(4)} x {CSG theta_beta=0.3, CSL shift 1+0.5i}",
+            "execution": ("the four solves at once through helm_solve_batch (one context and stream each)"
+                          if concurrent else "the four solves one after another (host-driven loop)"),
             "multigrid": "V(1,1), omega-Jacobi 0.5, FW, bilinear, rediscretised levels, dense coarsest",
             "tol": TOL, "l2": "flushed (512 MiB device write) before every timed step"}
 
@@ -241,7 +246,7 @@ def main():
         dist.barrier()
     g.build()
     from paper_0912_0180_gb300 import _lib as L
-    from paper_0912_0180_gb300.helm import Helm
+    from paper_0912_0180_gb300.helm import Helm, solve_batch
 
     p = hi.workload_2d_512()
     sh = hi.shadow_space(p.n, 4)
@@ -255,38 +260,49 @@ def main():
         ranks.barrier()
         torch.cuda.synchronize()
 
+    # one context per solve of the step (a context holds one solve's workspace), per precision
     ctxs = {}
     for mg in ("c128", "c64"):
-        for pcn in ("csg", "csl"):
-            ctxs[(mg, pcn)] = Helm(p, precond(pcn), mg_dtype=mg)
+        for i, (_, _, pcn) in enumerate(SOLVES):
+            ctxs[(mg, i)] = Helm(p, precond(pcn), mg_dtype=mg)
+    methods = [m for (_, m, _) in SOLVES]
+    shadows = [sh if m == hi.IDR else None for m in methods]
+    xs_dev = {mg: [torch.empty(p.n, dtype=torch.complex128, device=dev) for _ in SOLVES] for mg in ("c128", "c64")}
+    concurrent = not args.host_loop  # the host-driven loop (profiling) runs the solves one by one
 
-    def one_step(mg: str, lat: list, infos: list, e2e_host=None):
-        x = None
-        for (mname, method, pcn) in SOLVES:
-            h = ctxs[(mg, pcn)]
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            if e2e_host is not None:
-                b_in = e2e_host["b"].to(dev, non_blocking=True)
-                x, info = h.solve(b_in, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh,
-                                  host_loop=args.host_loop)
-                e2e_host["x"].copy_(x, non_blocking=True)
-            else:
-                x, info = h.solve(b_dev, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh,
-                                  host_loop=args.host_loop)
-            e1.record()
-            e1.synchronize()
-            lat.append(e0.elapsed_time(e1))
-            infos.append(info)
-        return x
+    def one_step(mg: str, lat: list, infos: list, e2e_host=None, together=True):
+        """The step: the four solves of the workload, at once through helm_solve_batch (one stream
+        per solve) or one after another (then `lat` gets each solve's latency)."""
+        b_in = e2e_host["b"].to(dev, non_blocking=True) if e2e_host is not None else b_dev
+        if together:
+            hs = [ctxs[(mg, i)] for i in range(len(SOLVES))]
+            xs, inf = solve_batch(hs, [b_in] * len(SOLVES), method=methods, s=4, tol=TOL, maxmv=4000,
+                                  shadows=shadows, xs=xs_dev[mg])
+            infos.extend(inf)
+        else:
+            xs = []
+            for i, method in enumerate(methods):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                x, info = ctxs[(mg, i)].solve(b_in, method=method, s=4, tol=TOL, maxmv=4000, shadow=sh,
+                                              host_loop=args.host_loop)
+                e1.record()
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+                infos.append(info)
+                xs.append(x)
+        if e2e_host is not None:
+            for k, x in enumerate(xs):
+                e2e_host["x"][k].copy_(x, non_blocking=True)
 
-    def timed(mg: str, e2e=False):
+    def timed(mg: str, e2e=False, together=True):
         host = None
         if e2e:
-            host = {"b": torch.from_numpy(p.b).pin_memory(), "x": torch.empty(p.n, dtype=torch.complex128).pin_memory()}
+            host = {"b": torch.from_numpy(p.b).pin_memory(),
+                    "x": [torch.empty(p.n, dtype=torch.complex128).pin_memory() for _ in SOLVES]}
         for _ in range(args.warmup):
-            one_step(mg, [], [], host)
+            one_step(mg, [], [], host, together)
         lat, infos, step_ms = [], [], []
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -294,7 +310,7 @@ def main():
             s0 = torch.cuda.Event(enable_timing=True)
             s1 = torch.cuda.Event(enable_timing=True)
             s0.record()
-            one_step(mg, lat, infos, host)
+            one_step(mg, lat, infos, host, together)
             s1.record()
             barrier()
             step_ms.append(s0.elapsed_time(s1))
@@ -316,9 +332,13 @@ def main():
     ms64 = lat64 = inf64 = ms32 = lat32 = inf32 = None
     with ClockSampler(local) as clk:
         if run64:
-            ms64, lat64, inf64 = timed("c128")
+            ms64, lat64, inf64 = timed("c128", together=concurrent)
         if run32:
-            ms32, lat32, inf32 = timed("c64")
+            ms32, lat32, inf32 = timed("c64", together=concurrent)
+        if args.phase == "all":
+            # the same four solves one after another: each solve's latency on an otherwise idle GPU
+            sq64, lat64, _ = timed("c128", together=False)
+            sq32, lat32, _ = timed("c64", together=False)
     if args.phase != "all":
         ms, lat, inf = (ms64, lat64, inf64) if run64 else (ms32, lat32, inf32)
         step = ranks.max(statistics.mean(ms))
@@ -326,7 +346,7 @@ def main():
                 "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": step, "higher_is_better": True, "scaling": "weak",
                 "dtype": "c128" if run64 else "c64 V-cycle, c128 Krylov", "data": "synthetic",
-                "config": config(p), "host_loop": bool(args.host_loop), "clocks": clk.summary(),
+                "config": config(p, concurrent), "host_loop": bool(args.host_loop), "clocks": clk.summary(),
                 "gpu_launches": int(sum(i.kernels for i in inf)),
                 "matvecs": {f"{m}-{pc}": inf[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)}}
         for h in ctxs.values():
@@ -352,7 +372,7 @@ def main():
     kern = kernel_rooflines(torch, L, ctxs, p, dev, flush)
     # ---- solution error per tolerance against a tight FP64 solve (untimed; Bi-CGSTAB, CSG) ----
     import bench_workloads
-    err = bench_workloads._errors_vs_reference(torch, {mg: ctxs[(mg, "csg")] for mg in ("c128", "c64")}, b_dev)
+    err = bench_workloads._errors_vs_reference(torch, {mg: ctxs[(mg, 0)] for mg in ("c128", "c64")}, b_dev)
 
     def pct(v, q):
         return float(np.percentile(np.asarray(v), q))
@@ -360,19 +380,27 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step64, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config(p),
-        "latency_ms": {"p50": pct(lat64, 50), "p99": pct(lat64, 99)},
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config(p, concurrent),
+        "latency_ms": {"p50": pct(lat64, 50), "p99": pct(lat64, 99),
+                       "what": "one solve alone on the GPU (the step's solves run one after another)"},
+        "step_latency_ms": {"p50": pct(ms64, 50), "p99": pct(ms64, 99)},
+        "sequential": {"value": nsol / (ranks.max(statistics.mean(sq64)) / 1000), "unit": "solves/s",
+                       "fp32_mg": nsol / (ranks.max(statistics.mean(sq32)) / 1000),
+                       "what": "the same four solves one after another"},
         "matvecs": {f"{m}-{pc}": inf64[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)},
         "fp32_mg": {"value": nsol / (step32 / 1000), "unit": "solves/s", "ms_per_step": step32,
                     "dtype": "c64 V-cycle, c128 Krylov and true residual",
                     "latency_ms": {"p50": pct(lat32, 50), "p99": pct(lat32, 99)},
+                    "step_latency_ms": {"p50": pct(ms32, 50), "p99": pct(ms32, 99)},
                     "matvecs": {f"{m}-{pc}": inf32[i].matvecs for i, (m, _, pc) in enumerate(SOLVES)},
                     "max_true_rel_res": max(i.rel_res_true for i in inf32)},
         "max_true_rel_res": max(i.rel_res_true for i in inf64),
         "error_vs_reference": err,
         "clocks": clk.summary(),
         "e2e": {"value": nsol / (stepe2e / 1000), "unit": "solves/s",
-                "h2d_bytes_per_step": len(SOLVES) * p.n * 16, "d2h_bytes_per_step": len(SOLVES) * p.n * 16},
+                "path": "FP64 path, helm_solve_batch with the right-hand side copied in from pinned host "
+                        "memory and the four solutions copied out, every step",
+                "h2d_bytes_per_step": p.n * 16, "d2h_bytes_per_step": len(SOLVES) * p.n * 16},
         "gpu_launches": int(sum(i.kernels for i in inf64[: len(SOLVES) * args.steps]) +
                             sum(i.kernels for i in inf32)),
         "roofline": kern["dominant"],
@@ -454,7 +482,7 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
         return statistics.median(ts) / 1000.0  # seconds
 
     for mg, dt, esz in (("c128", torch.complex128, 16), ("c64", torch.complex64, 8)):
-        h = ctxs[(mg, "csg")]
+        h = ctxs[(mg, 0)]  # Bi-CGSTAB with CSG
         nc = h.level_shape(1)[0] * h.level_shape(1)[1]
         f = torch.randn(n, dtype=dt, device=dev)
         u = torch.empty(n, dtype=dt, device=dev)
@@ -468,7 +496,7 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
         z = torch.empty(n, dtype=dt, device=dev)
         t = time_cold(lambda: h.vcycle(r, out=z), name=f"vcycle_{mg}")
         table[f"vcycle_{mg}"] = {"us": t * 1e6}
-    h = ctxs[("c128", "csg")]
+    h = ctxs[("c128", 0)]
     x = torch.randn(n, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)
     t = time_cold(lambda: h.apply(x, out=y), name="k_h_apply_c128")
