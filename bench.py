@@ -432,6 +432,11 @@ def main():
 # four neighbours) (3 complex adds, 1 complex multiply, 1 scale, 1 subtract: 16), full weighting
 # (8 complex adds and a scale per coarse unknown: 18 / 4).
 DOWN_FLOPS_PER_POINT = 6 + 16 + 18 / 4
+# The same work in FP64-pipe operations (DADD, DMUL and DFMA each one issue slot of the FP64 pipe;
+# interior point, complex CSG coefficients): u = f (omega/D) 4, residual 12 (neighbour pair sums 4,
+# their sum 2, the complex coefficient 4, (1 - omega) f - a 2), full weighting 18 per coarse
+# unknown = 4.5 per fine one.
+DOWN_FP64_OPS_PER_POINT = 4 + 12 + 18 / 4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level launch of the fused
 # down kernel on this workload, from an ncu --set full capture of the current kernels (FP64, FP32);
@@ -455,9 +460,8 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    # FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the unit count inferred from
-    # a measured 1.2 TFLOP/s FP64 FMA loop on this GB300)
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    # FP64 pipe peak: 152 SMs x 2 FP64 operations per clock per SM (ncu's peak_sustained) x 2.07 GHz
+    fp64_ops_peak = 152 * 2 * 2.07e9 / 1e12  # T operations/s
     n = p.n
     st = torch.cuda.current_stream()
     table = {}
@@ -490,8 +494,9 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
         t = time_cold(lambda: h.level_op(L.HELM_OP_DOWN, 0, u, f, fc), name=f"k_down2d_{mg}")
         byt = n * down_bytes_per_point(esz)
         fl = n * DOWN_FLOPS_PER_POINT
+        ops = n * DOWN_FP64_OPS_PER_POINT
         table[f"k_down2d_{mg}"] = {"us": t * 1e6, "bytes": byt, "GB/s": byt / t / 1e9, "flops": fl,
-                                   "TFLOP/s": fl / t / 1e12}
+                                   "TFLOP/s": fl / t / 1e12, "fp64_ops": ops, "T_op/s": ops / t / 1e12}
         r = torch.randn(n, dtype=torch.complex128, device=dev)
         z = torch.empty(n, dtype=dt, device=dev)
         t = time_cold(lambda: h.vcycle(r, out=z), name=f"vcycle_{mg}")
@@ -507,10 +512,11 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
             v["frac_hbm"] = v["GB/s"] / hbm
     d64, d32 = table["k_down2d_c128"], table["k_down2d_c64"]
     dominant = {"kernel": "k_down2d<double> (fused smooth + residual + full weighting, finest level, FP64 path)",
-                "bound": "alu", "achieved": d64["TFLOP/s"], "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": d64["TFLOP/s"] / fp64_peak, "traffic": DOWN_TRAFFIC_BYTES["c128"],
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "flops_per_launch": d64["flops"], "launch_us": d64["us"]}
+                "bound": "alu", "achieved": d64["T_op/s"], "peak": fp64_ops_peak, "unit": "T FP64 op/s",
+                "frac": d64["T_op/s"] / fp64_ops_peak, "traffic": DOWN_TRAFFIC_BYTES["c128"],
+                "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
+                "fp64_ops_per_launch": d64["fp64_ops"], "launch_us": d64["us"],
+                "note": "DADD, DMUL and DFMA each take one FP64-pipe slot; ncu: the pipe is 82% busy"}
     fp32 = {"kernel": "k_down2d<float> (same kernel in the FP32 V-cycle)", "bound": "hbm",
             "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm,
             "traffic": DOWN_TRAFFIC_BYTES["c64"],
