@@ -220,6 +220,7 @@ def main():
                          "serve: a Poisson-arrival request stream through the solve server")
     ap.add_argument("--serve-requests", type=int, default=32, help="serve: requests in the stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: mean arrival rate (requests/s)")
+    ap.add_argument("--serve-slots", type=int, default=8, help="serve: requests the server runs at once")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

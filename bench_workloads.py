@@ -339,10 +339,10 @@ def run_batch(args, torch, ranks, dev, local):
 
 # ---- serve ---------------------------------------------------------------------------------
 
-def _stream(torch, reqs, mg, budget):
+def _stream(torch, reqs, mg, budget, slots=8):
     """Submits every request at its arrival time; returns wall seconds, per-request results."""
     from paper_0912_0180_gb300.helm import Server
-    srv = Server(budget, max_active=8)
+    srv = Server(budget, max_active=slots)
     t0 = time.perf_counter()
     tickets = []
     for r in reqs:
@@ -364,10 +364,10 @@ def run_serve(args, torch, ranks, dev, local):
     res = {}
     with bench.ClockSampler(local) as clk:
         for mg in ("c128", "c64"):
-            _stream(torch, reqs[:4], mg, budget)  # warm-up: the first requests of the stream
+            _stream(torch, reqs[:4], mg, budget, args.serve_slots)  # warm-up: the first requests
             walls, outs = [], None
             for _ in range(args.steps):
-                wall, outs = _stream(torch, reqs, mg, budget)
+                wall, outs = _stream(torch, reqs, mg, budget, args.serve_slots)
                 walls.append(wall)
                 for x, info, lat in outs:
                     if info.status != 0 or not info.rel_res_true < TOL:
@@ -383,7 +383,7 @@ def run_serve(args, torch, ranks, dev, local):
            "mix": "1/2 2D (interior 127..1023), 1/2 3D (interior 64..160), 16..32-node layers, kh 0.3..0.6, "
                   "1..8 point-source right-hand sides each",
            "n_unknowns_total": int(sum(r.problem.n * r.rhs.shape[0] for r in reqs)),
-           "server": "150 GB budget, 8 slots", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
+           "server": f"150 GB budget, {args.serve_slots} slots", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
            "timing": "wall clock from the first arrival to the last completion (host in, host out)"}
     line = _base(args, ranks.job_rate(nsol, w64 * 1000), w64 * 1000, ranks.world, cfg, "c128")
     line.update({
