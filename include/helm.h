@@ -88,16 +88,20 @@ typedef struct {
   int nu1, nu2;         /* 0..8 sweeps */
   int smoother;         /* HELM_SM_JACOBI or HELM_SM_RBGS */
   double omega;         /* Jacobi damping, 0 < omega <= 1 */
-  int max_levels;       /* >= 1; the coarsest level reached must have at most
-                           HELM_COARSE_MAX_UNKNOWNS unknowns (else helm_create: HELM_ERR_ARG) */
+  int max_levels;       /* >= 1; a coarsest level that needs the dense inverse (variable k) must
+                           have at most HELM_COARSE_MAX_UNKNOWNS unknowns (else helm_create:
+                           HELM_ERR_ARG) */
   int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
   helm_dtype mg_dtype;  /* HELM_C64: whole V-cycle in complex FP32; HELM_C128: FP64 */
   int flags;            /* HELM_PF_*; 0 = defaults */
 } helm_precond;
 
-/* Largest coarsest level: its dense inverse is built at helm_create by Gauss-Jordan in FP64
- * (one block up to 512 unknowns, the whole GPU above) and applied as a dense matrix-vector
- * product in the V-cycle precision; 16384 unknowns take 4 GiB in FP64 during create. */
+/* The coarsest level is solved exactly.  With a constant k there and more than 512 unknowns, by
+ * separation of variables: per-axis eigendecompositions of the Shortley-Weller matrices, computed
+ * in FP64 on the host at helm_create, applied as one transform per axis (any size).  Otherwise its
+ * dense inverse is built at helm_create by Gauss-Jordan in FP64 (one block up to 512 unknowns, the
+ * whole GPU above) and applied as a dense matrix-vector product in the V-cycle precision; this
+ * limits such levels to HELM_COARSE_MAX_UNKNOWNS unknowns (4 GiB in FP64 during create). */
 #define HELM_COARSE_MAX_UNKNOWNS 16384
 
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the

@@ -118,6 +118,19 @@ struct Workspace;    // Krylov vectors, defined in krylov.cu
 
 }  // namespace helm
 
+// Separable exact solve of the coarsest level (see coarse_fdm.cu): per axis the eigenvector
+// matrices V_a and V_a^{-1} (n_a x n_a, row-major) and the pointwise 1 / (eigenvalue sums), in the
+// V-cycle precision, and two scratch vectors of the level's size.
+struct FdmCoarse {
+  bool on = false;
+  int dim = 0;
+  int n[3] = {1, 1, 1};
+  void* V[3] = {nullptr, nullptr, nullptr};
+  void* Vi[3] = {nullptr, nullptr, nullptr};
+  void* dinv = nullptr;
+  void* scr = nullptr;
+};
+
 struct helm_ctx {
   helm_grid grid{};
   helm_precond pc{};
@@ -133,6 +146,7 @@ struct helm_ctx {
   void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations of helm_create
   int tail_first = 1 << 30;          // first level run by the single-block tail kernel
+  FdmCoarse fdm;                     // separable coarsest solve (constant phi there), or off
 };
 
 namespace helm {
@@ -173,6 +187,10 @@ helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaSt
 
 // mg_fused.cu
 helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);
+// coarse_fdm.cu
+helm_status fdm_build(helm_ctx* c, const LevelHost& L, bool f32, cudaStream_t st);
+template <typename T>
+void fdm_apply(const helm_ctx* c, const cx<T>* f, cx<T>* z, const int* skip, cudaStream_t st);
 template <typename T> int tail_first_level(const helm_ctx* c);
 template <typename T>
 helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,

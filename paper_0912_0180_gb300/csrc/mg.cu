@@ -331,6 +331,10 @@ static void prolong_any(const LevelHost& F, const LevelHost& C, const cx<T>* ec,
 }
 template <typename T>
 static void coarse_solve(helm_ctx* c, const cx<T>* f, cx<T>* z, const int* skip, cudaStream_t st) {
+  if (c->fdm.on) {
+    fdm_apply<T>(c, f, z, skip, st);
+    return;
+  }
   int n = c->nco;
   int thr = 256;
   int blocks = (n * 32 + thr - 1) / thr;

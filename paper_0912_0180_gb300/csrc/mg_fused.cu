@@ -483,6 +483,7 @@ constexpr size_t TAIL_INVERSE_BYTES = 1 << 20;
 
 template <typename T> int tail_first_level(const helm_ctx* c, long point_budget) {
   int nl = (int)c->lv.size();
+  if (c->fdm.on) return nl;  // the one-block tail needs the dense coarsest inverse
   long pts = c->lv[nl - 1].ntot;
   size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
   if (bytes > TAIL_SMEM_BUDGET) return nl;  // the coarsest level alone is too big: no tail

@@ -212,6 +212,8 @@ static int ceil_div(long a, int b) { return (int)((a + b - 1) / b); }
 // becomes A[r, :] - fcol[r] prow, column k being replaced by -fcol[r] / a_pk.  The row exchanges
 // are undone on the columns at the end, last step first.
 constexpr int GJ_ONE_BLOCK_MAX = 512;
+// coarsest levels above this size with a constant phi use the separable solve of coarse_fdm.cu
+constexpr long FDM_MIN_UNKNOWNS = 512;
 
 struct GjPivot {
   double2 apk, akk;
@@ -519,6 +521,15 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   // dense inverse of the coarsest operator, computed in FP64: one block for small levels,
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
+  // constant phi on a large coarsest level: the separable exact solve, no dense inverse
+  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64) {
+    if ((rc = fdm_build(c, Cst, f32, st)) != HELM_OK) return rc;
+    if (c->fdm.on) {
+      c->nco = 0;
+      c->tail_first = (int)c->lv.size();  // the one-block tail needs the dense inverse
+      return autotune_tiles(c, st);
+    }
+  }
   if (Cst.ntot > HELM_COARSE_MAX_UNKNOWNS) {
     set_error("coarsest level too large for the dense direct solve (> 16384 unknowns); raise max_levels");
     return HELM_ERR_ARG;

@@ -378,12 +378,14 @@ def test_device_loop_is_deterministic_and_matches_host_loop(method):
 
 
 @pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("kind", ["bump", "const"])
 @pytest.mark.parametrize("shape", [(2, (44, 50), ((4, 3), (5, 0)), 1), (3, 17, 2, 1), (3, (30, 34, 32), 2, 2)])
-def test_vcycle_large_coarsest(shape, mg):
-    """Coarsest levels above 512 unknowns: their dense inverse comes from the whole-GPU
-    Gauss-Jordan (one pivot step per launch sequence) instead of the one-block kernel."""
+def test_vcycle_large_coarsest(shape, kind, mg):
+    """Coarsest levels above 512 unknowns: with a variable k their dense inverse comes from the
+    whole-GPU Gauss-Jordan (one pivot step per launch sequence) instead of the one-block kernel;
+    with a constant k they are solved by separation of variables (per-axis eigendecompositions)."""
     dim, n_int, nl, levels = shape
-    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=0.4 * (np.max(n_int) - 1), phi_kind="bump",
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=0.4 * (np.max(n_int) - 1), phi_kind=kind,
                         rhs="random", seed=5, bump_centre=(0.3, 0.6, 0.5))
     pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS, max_levels=levels + 1)
     o = Oracle(p, pc)
