@@ -135,3 +135,24 @@ def test_server_multiple_right_hand_sides():
         assert info.matvecs == mv
         h.close()
     srv.close()
+
+
+@pytest.mark.parametrize("mg", ["c64", "c128"])
+def test_batch_with_a_method_per_instance(mg):
+    """One batch mixing Bi-CGSTAB and IDR(s) instances (opts has one entry per instance, as the
+    benchmark's four-solve step uses it): each instance equals its lone solve bitwise."""
+    from paper_0912_0180_gb300.helm import Helm, solve_batch
+    inst = _instances()
+    methods = [hi.BICGSTAB if i % 2 == 0 else hi.IDR for i in range(len(inst))]
+    hs = [Helm(p, pc, mg_dtype=mg) for p, pc in inst]
+    bs = [torch.from_numpy(p.b).cuda() for p, _ in inst]
+    shadows = [hi.shadow_space(p.n, 4, seed=9 + i) if m == hi.IDR else None
+               for i, ((p, _), m) in enumerate(zip(inst, methods))]
+    alone = [h.solve(b, method=m, tol=1e-8, maxmv=3000, shadow=sh) for h, b, m, sh in zip(hs, bs, methods, shadows)]
+    alone = [(x.clone(), info) for x, info in alone]
+    xs, infos = solve_batch(hs, bs, method=methods, tol=1e-8, maxmv=3000, shadows=shadows)
+    for (xa, ia), xb, ib in zip(alone, xs, infos):
+        assert ia.status == 0 and ib.status == 0
+        assert torch.equal(xa, xb) and ia.matvecs == ib.matvecs
+    for h in hs:
+        h.close()
