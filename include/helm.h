@@ -206,7 +206,9 @@ helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, const helm_solve_o
  * its own stream, ordered after `stream` and joined back into it, so the instances overlap on the
  * GPU; the host only reads each instance's statistics when its loop has finished.  ctxs must be n
  * distinct contexts (a context holds one solve's workspace); b[i], x[i] follow helm_solve; opts
- * has n entries, so every instance has its own method, shadow space and tolerances.
+ * has n entries, so every instance has its own method, shadow space and tolerances.  Streams get
+ * priorities longest work first (unknowns x the method's cost per matvec), so that the instances
+ * that finish last start first and the short ones fill the gaps.
  * infos (n entries, may be NULL) receives every instance's statistics.  Returns HELM_OK when all
  * instances converged, else the first non-OK instance status (every x[i] still holds that
  * instance's last iterate); argument errors are reported before anything is launched.  The result

@@ -12,6 +12,7 @@
 // whose condition the last kernel of the iteration sets, so a whole solve is one graph launch.
 // No kernel waits on another: there is no device-side spin anywhere.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <thread>
 #include <type_traits>
@@ -1084,13 +1085,26 @@ helm_status krylov_solve_batch(helm_ctx* const* cs, const double2* const* b, dou
                                const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t user) {
   std::vector<SolveJob> jobs(n);
   std::vector<cudaStream_t> streams(n, nullptr);
+  // longest work first: stream priorities by the estimated work of each instance (unknowns x a
+  // per-matvec cost of its method; IDR(s) does about 1.8 times Bi-CGSTAB's vector work per
+  // matvec), ranked and spread over the device's priority range, the largest highest
+  std::vector<int> prio(n, 0);
+  {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    std::vector<std::pair<double, int>> w(n);
+    for (int i = 0; i < n; ++i) w[i] = {(double)cs[i]->n * (o[i].method == HELM_IDR ? 1.8 : 1.0), i};
+    std::sort(w.begin(), w.end());
+    const int levels = least - greatest + 1;
+    for (int r = 0; r < n; ++r) prio[w[r].second] = least - (int)((long)r * levels / (n > 0 ? n : 1));
+  }
   cudaEvent_t start;
   HELM_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   helm_status s = HELM_OK;
   cudaError_t e = cudaEventRecord(start, user);
   if (e != cudaSuccess) s = cuda_check(e, "cudaEventRecord(batch)");
   for (int i = 0; i < n && s == HELM_OK; ++i) {
-    e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&streams[i], cudaStreamNonBlocking, prio[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[i], start, 0);
     if (e != cudaSuccess) { s = cuda_check(e, "batch stream"); break; }
     SolveJob& j = jobs[i];
