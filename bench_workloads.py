@@ -342,7 +342,7 @@ def run_batch(args, torch, ranks, dev, local):
 def _stream(torch, reqs, mg, budget, slots=8):
     """Submits every request at its arrival time; returns wall seconds, per-request results."""
     from paper_0912_0180_gb300.helm import Server
-    srv = Server(budget, max_active=slots)
+    srv = Server(budget, max_active=slots, smallest_first=True)
     t0 = time.perf_counter()
     tickets = []
     for r in reqs:
@@ -383,7 +383,7 @@ def run_serve(args, torch, ranks, dev, local):
            "mix": "1/2 2D (interior 127..1023), 1/2 3D (interior 64..160), 16..32-node layers, kh 0.3..0.6, "
                   "1..8 point-source right-hand sides each",
            "n_unknowns_total": int(sum(r.problem.n * r.rhs.shape[0] for r in reqs)),
-           "server": f"150 GB budget, {args.serve_slots} slots", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
+           "server": f"150 GB budget, {args.serve_slots} slots, smallest work admitted first", "solver": "Bi-CGSTAB, CSG theta_beta=0.3 omega-Jacobi V(1,1), tol 1e-6",
            "timing": "wall clock from the first arrival to the last completion (host in, host out)"}
     line = _base(args, ranks.job_rate(nsol, w64 * 1000), w64 * 1000, ranks.world, cfg, "c128")
     line.update({

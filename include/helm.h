@@ -220,7 +220,8 @@ helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* b, void* 
  * A server admits solve requests of any grid, k field and preconditioner against a device-memory
  * budget and runs up to max_active of them at once, each on its own stream with its own context
  * (continuous batching: a request submitted while others run starts as soon as a slot and the
- * budget allow, and its work overlaps theirs on the GPU).  Requests start in submission order.
+ * budget allow, and its work overlaps theirs on the GPU).  Requests start in submission order
+ * unless helm_server_set_policy says otherwise.
  * Each request's result is bitwise what helm_solve gives it alone.  A server is thread-safe for
  * submit / poll / wait / stats; a worker thread owned by the server does the device work. */
 typedef struct {
@@ -247,6 +248,14 @@ typedef struct helm_server helm_server;
 size_t helm_estimate_bytes(const helm_grid* grid, const helm_precond* pc, const helm_solve_opts* opts);
 
 helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server** out);
+/* Admission order.  HELM_SERVE_FIFO (the default): submission order, a request that does not fit
+ * the free budget waits and so do the ones behind it.  HELM_SERVE_SMALLEST_FIRST: the queued
+ * request with the least work (unknowns x right-hand sides) that fits the free budget, except that
+ * a request passed over 2 x max_active times is admitted next.  Either way the requests running at
+ * once get stream priorities smallest work first.  The policy changes when requests run, never
+ * their results. */
+enum { HELM_SERVE_FIFO = 0, HELM_SERVE_SMALLEST_FIRST = 1 };
+helm_status helm_server_set_policy(helm_server* s, int policy);
 /* HELM_ERR_OOM if the request alone exceeds the budget; *ticket identifies it afterwards. */
 helm_status helm_server_submit(helm_server* s, const helm_request* req, uint64_t* ticket);
 /* HELM_ERR_BUSY while queued or running; otherwise the request's final status, with its

@@ -13,6 +13,7 @@ HELM_C64, HELM_C128 = 0, 1
 HELM_OP_APPLY, HELM_OP_RESIDUAL, HELM_OP_SMOOTH, HELM_OP_SMOOTH0 = 0, 1, 2, 3
 HELM_OP_RESTRICT, HELM_OP_PROLONG, HELM_OP_COARSE, HELM_OP_DOWN = 4, 5, 6, 7
 HELM_PF_UNFUSED, HELM_PF_NO_PDL, HELM_PF_NO_AUTOTUNE = 1, 2, 4
+HELM_SERVE_FIFO, HELM_SERVE_SMALLEST_FIRST = 0, 1
 
 
 class Grid(C.Structure):
@@ -83,6 +84,8 @@ def load() -> C.CDLL:
     lib.helm_estimate_bytes.restype = C.c_size_t
     lib.helm_server_create.argtypes = [C.c_size_t, ip, C.POINTER(vp)]
     lib.helm_server_create.restype = ip
+    lib.helm_server_set_policy.argtypes = [vp, ip]
+    lib.helm_server_set_policy.restype = ip
     lib.helm_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
     lib.helm_server_submit.restype = ip
     lib.helm_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]

@@ -8,6 +8,7 @@
 // and frees are stream-ordered), so a request's completion is noticed as soon as its own stream
 // reaches it.  Latency is measured from submission to the moment the solution is in host memory.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <complex>
 #include <condition_variable>
@@ -107,6 +108,7 @@ struct helm_server {
     double t_submit = 0, t_start = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running, 2 done
     int nrhs = 1, cur = 0;      // right-hand sides, the one being solved
+    int bypassed = 0;           // times a later request was admitted before this one
     helm_solve_info info{};     // summed over the right-hand sides solved so far
     helm_solve_info one{};      // the current right-hand side
     helm_status status = HELM_OK;
@@ -116,16 +118,20 @@ struct helm_server {
     void* xd = nullptr;
     SolveJob* job = nullptr;
     int slot = -1;
+    cudaStream_t stream = nullptr;  // the slot's stream at this request's priority
   };
   size_t budget = 0, used = 0;
   int max_active = 1;
+  int policy = HELM_SERVE_FIFO;
   int dev = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req*> queue;
   std::vector<Req*> active;
   std::unordered_map<uint64_t, Req*> reqs;
+  // per slot, one stream per priority level (greatest .. least): requests run smallest work first
   std::vector<cudaStream_t> streams;
+  int prio_levels = 1, prio_greatest = 0;
   std::vector<bool> slot_busy;
   std::thread worker;
   bool stop = false;
@@ -149,7 +155,7 @@ struct helm_server {
   // Copies the finished right-hand side's solution (or last iterate) to the host and folds its
   // statistics in.
   void collect(Req* r) {
-    cudaStream_t s = streams[r->slot];
+    cudaStream_t s = r->stream;
     cudaMemcpyAsync((double2*)r->x_host + (size_t)r->cur * r->n, r->xd, sizeof(double2) * r->n,
                     cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -159,7 +165,7 @@ struct helm_server {
   // Starts the solve of right-hand side r->cur on the request's context (its hierarchy and
   // Krylov workspace stay resident between right-hand sides).
   helm_status begin_rhs(Req* r) {
-    cudaStream_t s = streams[r->slot];
+    cudaStream_t s = r->stream;
     if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
     size_t vb = sizeof(double2) * r->n;
     if (cudaMemcpyAsync(r->bd, r->b.data() + (size_t)r->cur * r->n, vb, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -171,7 +177,7 @@ struct helm_server {
   }
 
   void finish(Req* r, helm_status st) {
-    cudaStream_t s = r->slot >= 0 ? streams[r->slot] : (cudaStream_t)0;
+    cudaStream_t s = r->stream;
     if (r->ctx && r->xd && r->job && job_finished(r->job)) collect(r);  // the solution, or the last iterate
     if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
     if (r->bd) cudaFreeAsync(r->bd, s);
@@ -190,8 +196,40 @@ struct helm_server {
     cv_done.notify_all();
   }
 
+  // Index in the queue of the request to admit next, or queue.size() if none fits the free
+  // budget.  FIFO: the head (a request that does not fit blocks the ones behind it, so admission
+  // order is submission order).  SMALLEST_FIRST: a request bypassed 2 x max_active times goes
+  // first (no starvation); otherwise the one with the least work (unknowns x right-hand sides)
+  // among those that fit, the earliest on ties.
+  size_t next_admission() const {
+    const size_t none = queue.size();
+    if (policy == HELM_SERVE_FIFO) return used + queue.front()->bytes <= budget ? 0 : none;
+    for (size_t q = 0; q < queue.size(); ++q)
+      if (queue[q]->bypassed >= 2 * max_active) return used + queue[q]->bytes <= budget ? q : none;
+    size_t best = none;
+    double bw = 0.0;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      if (used + queue[q]->bytes > budget) continue;
+      double w = (double)queue[q]->n * queue[q]->nrhs;
+      if (best == none || w < bw) { best = q; bw = w; }
+    }
+    return best;
+  }
+
+  // Priority bucket of a request: one level per decade of unknowns x right-hand sides above 1e4,
+  // the smallest work at the greatest priority, so that short requests overtake long ones on the
+  // GPU while admission stays first come, first served.
+  int prio_level(const Req* r) const {
+    double work = (double)r->n * r->nrhs;
+    int b = (int)std::floor(std::log10(work > 1.0 ? work : 1.0)) - 4;
+    if (b < 0) b = 0;
+    if (b > prio_levels - 1) b = prio_levels - 1;
+    return b;
+  }
+
   helm_status start(Req* r) {
-    cudaStream_t s = streams[r->slot];
+    r->stream = streams[(size_t)r->slot * prio_levels + prio_level(r)];
+    cudaStream_t s = r->stream;
     helm_kspec k{r->k0, r->phi.empty() ? nullptr : r->phi.data()};
     helm_status st = helm_create(&r->grid, &k, &r->pc, (void*)s, &r->ctx);
     if (st != HELM_OK) return st;
@@ -215,9 +253,12 @@ struct helm_server {
       {
         std::unique_lock<std::mutex> lk(mu);
         if (stop && queue.empty() && active.empty()) return;
-        while (!queue.empty() && (int)active.size() < max_active && used + queue.front()->bytes <= budget) {
-          Req* r = queue.front();
-          queue.pop_front();
+        while (!queue.empty() && (int)active.size() < max_active) {
+          const size_t k = next_admission();
+          if (k >= queue.size()) break;  // nothing fits the free budget yet
+          Req* r = queue[k];
+          for (size_t q = 0; q < k; ++q) queue[q]->bypassed += 1;
+          queue.erase(queue.begin() + (long)k);
           for (int i = 0; i < (int)slot_busy.size(); ++i)
             if (!slot_busy[i]) { slot_busy[i] = true; r->slot = i; break; }
           used += r->bytes;
@@ -269,10 +310,16 @@ helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server*
   s->budget = budget_bytes;
   s->max_active = max_active;
   cudaGetDevice(&s->dev);
-  s->streams.resize(max_active);
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  s->prio_levels = least - greatest + 1;
+  s->prio_greatest = greatest;
+  const int ns = max_active * s->prio_levels;
+  s->streams.assign(ns, nullptr);
   s->slot_busy.assign(max_active, false);
-  for (int i = 0; i < max_active; ++i) {
-    cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+  for (int i = 0; i < ns; ++i) {
+    int level = i % s->prio_levels;
+    cudaError_t e = cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, greatest + level);
     if (e != cudaSuccess) {
       for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
       delete s;
@@ -281,6 +328,16 @@ helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server*
   }
   s->worker = std::thread([s] { s->run(); });
   *out = s;
+  return HELM_OK;
+}
+
+helm_status helm_server_set_policy(helm_server* s, int policy) {
+  if (!s || (policy != HELM_SERVE_FIFO && policy != HELM_SERVE_SMALLEST_FIRST)) {
+    set_error("helm_server_set_policy: bad arguments");
+    return HELM_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->policy = policy;
   return HELM_OK;
 }
 

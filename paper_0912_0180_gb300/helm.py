@@ -188,12 +188,14 @@ def solve_batch(instances, bs, *, method=0, s: int = 4, tol: float = 1e-6, maxmv
 class Server:
     """helm_server_*: continuous-batching solve server (requests from host memory)."""
 
-    def __init__(self, budget_bytes: int, max_active: int = 4):
+    def __init__(self, budget_bytes: int, max_active: int = 4, smallest_first: bool = False):
         self._lib = L.load()
         h = C.c_void_p()
         _check(self._lib.helm_server_create(int(budget_bytes), int(max_active), C.byref(h)), "helm_server_create")
         self._h = h
         self._keep = {}
+        if smallest_first:
+            _check(self._lib.helm_server_set_policy(h, L.HELM_SERVE_SMALLEST_FIRST), "helm_server_set_policy")
 
     def submit(self, problem, precond, *, mg_dtype: str = "c64", method: int = 0, s: int = 4,
                tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3, shadow=None, rhs=None) -> int:

@@ -156,3 +156,34 @@ def test_batch_with_a_method_per_instance(mg):
         assert torch.equal(xa, xb) and ia.matvecs == ib.matvecs
     for h in hs:
         h.close()
+
+
+def test_server_smallest_first_admission():
+    """With one slot busy on a long request, a large and several small requests wait; the
+    smallest-first policy admits the small ones before the large one submitted ahead of them, and
+    every result still equals the lone solve bitwise."""
+    from paper_0912_0180_gb300.helm import Helm, Server
+    inst = _instances()
+    sizes = [p.n for p, _ in inst]
+    order = sorted(range(len(inst)), key=lambda i: sizes[i])
+    big, smalls = order[-1], order[:2]  # with one slot a request can be passed over twice
+    blocker = (hi.make_problem(2, 383, 64, theta_gamma=0.5, k0=150.0, phi_kind="bump", rhs="gauss", seed=4),
+               hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5))
+    srv = Server(64 << 30, max_active=1, smallest_first=True)
+    tb = srv.submit(*blocker, tol=1e-10, maxmv=8000)
+    import time
+    time.sleep(0.05)  # the blocker (several hundred matvecs on 511^2 unknowns) is running
+    tbig = srv.submit(*inst[big], tol=1e-7, maxmv=3000)
+    tsm = [srv.submit(*inst[i], tol=1e-7, maxmv=3000) for i in smalls]
+    srv.wait(tb)
+    xb, ib, lat_big = srv.wait(tbig)
+    res = [srv.wait(t) for t in tsm]
+    assert ib.status == 0 and all(r[1].status == 0 for r in res)
+    assert max(r[2] for r in res) < lat_big
+    for i, (x, info, _) in zip(smalls + [big], res + [(xb, ib, lat_big)]):
+        p, pc = inst[i]
+        h = Helm(p, pc, mg_dtype="c64")
+        xa, ia = h.solve(torch.from_numpy(p.b).cuda(), tol=1e-7, maxmv=3000)
+        assert np.array_equal(xa.cpu().numpy(), x) and ia.matvecs == info.matvecs
+        h.close()
+    srv.close()
