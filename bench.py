@@ -214,10 +214,11 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the Krylov loop from the host (one graph launch per iteration) so that "
                          "a kernel profiler sees every launch; slower, for profiling only")
-    ap.add_argument("--workload", default="2d640", choices=["2d640", "3d160", "batch256", "serve"],
+    ap.add_argument("--workload", default="2d640", choices=["2d640", "3d160", "batch256", "serve", "mp2", "mp3"],
                     help="2d640 (default): the 512^2 + 64-layer four-solve step; 3d160: 128^3 + 16-layer "
                          "k = 40 mixed-precision solve; batch256: 256 uneven 2D instances per step; "
-                         "serve: a Poisson-arrival request stream through the solve server")
+                         "serve: a Poisson-arrival request stream through the solve server; mp2 / mp3: "
+                         "the paper's model problems 2 and 3 with ECS layers on the north / east edges")
     ap.add_argument("--serve-requests", type=int, default=32, help="serve: requests in the stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--serve-slots", type=int, default=8, help="serve: requests the server runs at once")

@@ -97,14 +97,17 @@ def _dims3(dim, v):
 def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, extent=1.0,
                  theta_gamma=0.5, k0: float = 0.0, phi_kind: str = "const", bump_amp=0.3,
                  bump_width2=0.02, bump_centre=(0.5, 0.5, 0.5), rhs: str = "point",
-                 rhs_width_h: float = 2.0, seed: int = BASE_SEED, name: str = "") -> Problem:
+                 rhs_width_h: float = 2.0, seed: int = BASE_SEED, name: str = "",
+                 phi_fn=None, rhs_fn=None) -> Problem:
     """Build a seeded synthetic instance shaped like the paper's model problems.
 
     n_l: int (all sides), one (lo, hi) pair for every axis, or per-axis (lo, hi) pairs.
-    phi_kind: "const" (k = k0), or "bump" (k = k0 (1 + amp exp(-|x - c|^2 / width2))).
+    phi_kind: "const" (k = k0), "bump" (k = k0 (1 + amp exp(-|x - c|^2 / width2))), or "field"
+         (phi = phi_fn(x, y[, z]) at the real node positions).
     rhs: "point" (value 1 at the interior node floor((n_int-1)/2) per axis, as in MP1),
          "gauss" (exp(-|x - x_s|^2 / (2 sigma^2)), sigma = rhs_width_h * h, x_s uniform in
-         [0.1, 0.9]^d from the seed), "random" (complex normal entries), "zero".
+         [0.1, 0.9]^d from the seed), "random" (complex normal entries), "zero", "field"
+         (rhs_fn(x, y[, z]) at the real node positions).
     """
     rng = np.random.default_rng(seed)
     ni = _dims3(dim, [n_int] if np.isscalar(n_int) else list(n_int))
@@ -125,6 +128,8 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
         r2 = sum((X[a] - bump_centre[a] * ext[a]) ** 2 for a in range(dim))
         k = k0 * (1.0 + bump_amp * np.exp(-r2 / bump_width2))
         p.phi = np.ascontiguousarray((k * k).ravel(), dtype=np.float64)
+    elif phi_kind == "field":
+        p.phi = np.ascontiguousarray(np.broadcast_to(phi_fn(*X[:dim]), shape[::-1]).ravel(), dtype=np.float64)
     elif phi_kind != "const":
         raise ValueError(phi_kind)
     n = int(np.prod(shape))
@@ -142,6 +147,8 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
         p.b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     elif rhs == "zero":
         p.b = np.zeros(n, np.complex128)
+    elif rhs == "field":
+        p.b = np.ascontiguousarray(np.broadcast_to(rhs_fn(*X[:dim]), shape[::-1]).ravel().astype(np.complex128))
     else:
         raise ValueError(rhs)
     return p
@@ -183,6 +190,30 @@ def workload_3d_128(seed: int = BASE_SEED) -> Problem:
     """128^3 interior + 16-point ECS layers, k = 40, centre point source."""
     return make_problem(3, 128, 16, theta_gamma=0.5, k0=40.0, rhs="point", seed=seed,
                         name="3d-128cube-L16-k40-point")
+
+
+def workload_mp2(nu: float = 7.0, k: float = 2.0, n_int: int = 385, n_l: int = 128, r: float = 50.0,
+                 theta_gamma: float = np.pi / 6) -> Problem:
+    """The paper's model problem 2 (Section 4, eq. "MP2"): phi = nu (e^{-x^2} + e^{-y^2}) + k^2,
+    source chi = e^{-(x^2 + y^2)} on [0, r]^2, Dirichlet on the south / west edges (x = 0, y = 0) and
+    ECS layers of n_l nodes on the east / north edges.  Defaults: the paper's 384^2 interior grid
+    with 128 layer nodes (512^2 unknowns)."""
+    return make_problem(2, n_int, ((0, n_l), (0, n_l)), extent=r, theta_gamma=theta_gamma, k0=k,
+                        phi_kind="field", rhs="field", name=f"mp2-nu{nu:g}-k{k:g}-{n_int - 1}sq-L{n_l}",
+                        phi_fn=lambda x, y: nu * (np.exp(-x * x) + np.exp(-y * y)) + k * k,
+                        rhs_fn=lambda x, y: np.exp(-(x * x + y * y)))
+
+
+def workload_mp3(r: float = 90.0, k: float = 2.0, n_int: int = 1025, n_l: int = 256,
+                 theta_gamma: float = np.pi / 6) -> Problem:
+    """The paper's model problem 3 (Section 4, eq. "MP3"): phi = 1/x + 1/y + k^2 (singular at the
+    origin, which is a Dirichlet node here, so no unknown sits on it), chi = e^{-(x^2 + y^2)} on
+    [0, r]^2, Dirichlet south / west, ECS layers east / north.  Defaults: r = 90 with the paper's
+    1024^2 interior grid and 256 layer nodes (1280^2 unknowns)."""
+    return make_problem(2, n_int, ((0, n_l), (0, n_l)), extent=r, theta_gamma=theta_gamma, k0=k,
+                        phi_kind="field", rhs="field", name=f"mp3-r{r:g}-k{k:g}-{n_int - 1}sq-L{n_l}",
+                        phi_fn=lambda x, y: 1.0 / x + 1.0 / y + k * k,
+                        rhs_fn=lambda x, y: np.exp(-(x * x + y * y)))
 
 
 def workload_batch_2d(count: int = 256, seed: int = BASE_SEED) -> List[Problem]:

@@ -155,20 +155,21 @@ class Helm:
                        info.rel_res_true, info.kernels, h)
 
 
-def solve_batch(instances, bs, *, method=0, s: int = 4, tol: float = 1e-6, maxmv: int = 2000,
+def solve_batch(instances, bs, *, method=0, s=4, tol: float = 1e-6, maxmv: int = 2000,
                 max_restarts: int = 3, shadows=None, stream=None, xs=None):
     """helm_solve_batch: solve every (Helm instance, rhs) pair at once; returns (xs, infos).
-    `method` is one method for all instances or a sequence of one per instance; `xs` (optional)
-    receives the solutions."""
+    `method` and `s` are one value for all instances or a sequence of one per instance; `xs`
+    (optional) receives the solutions."""
     lib = L.load()
     n = len(instances)
     if xs is None:
         xs = [torch.empty(h.n, dtype=torch.complex128, device=b.device) for h, b in zip(instances, bs)]
     methods = list(method) if isinstance(method, (list, tuple)) else [method] * n
+    ss = list(s) if isinstance(s, (list, tuple)) else [s] * n
     opts = (L.SolveOpts * max(n, 1))()
     keep = []
     for i in range(n):
-        o = L.SolveOpts(methods[i], s, tol, maxmv, max_restarts, None, None, 0)
+        o = L.SolveOpts(methods[i], ss[i], tol, maxmv, max_restarts, None, None, 0)
         if shadows is not None and shadows[i] is not None:
             arr = np.ascontiguousarray(shadows[i], dtype=np.complex128)
             keep.append(arr)

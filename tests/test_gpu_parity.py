@@ -462,3 +462,31 @@ def test_batch256_workload_sampled():
         assert np.linalg.norm(r) / np.linalg.norm(p.b) < 1e-6
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("which", ["mp2", "mp3"])
+def test_model_problems_small(which):
+    """The paper's model problems 2 and 3 (analytic phi and source, Dirichlet south / west, ECS
+    north / east) on small grids with the paper's mesh width: V-cycle and FP64 solve against the
+    oracle, and the FP32-multigrid solve certified by the oracle's own residual."""
+    if which == "mp2":
+        p = hi.workload_mp2(n_int=49, n_l=16, r=50.0 * 48 / 384)
+        pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=np.pi / 20, smoother=hi.SM_JACOBI, omega=0.5)
+    else:
+        p = hi.workload_mp3(n_int=65, n_l=16, r=90.0 * 64 / 1024)
+        pc = hi.Precond(kind=hi.PC_CSL, shift=1 + 0.38j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    r = hi.random_vector(p.n, 3)
+    h64 = Helm(p, pc, mg_dtype="c128")
+    assert rel(h64.apply(cu(r)).cpu().numpy(), o.apply(r)) < 1e-12
+    assert rel(h64.vcycle(cu(r)).cpu().numpy(), o.vcycle(r)) < 1e-10
+    x, info = h64.solve(cu(p.b), tol=1e-10, maxmv=4000)
+    xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=4000))
+    assert info.status == 0 and io["status"] == 0
+    assert rel(x.cpu().numpy(), xo) < 1e-9
+    h32 = Helm(p, pc, mg_dtype="c64")
+    x32, i32 = h32.solve(cu(p.b), tol=1e-7, maxmv=4000)
+    assert i32.status == 0
+    assert np.linalg.norm(p.b - o.apply(x32.cpu().numpy())) / np.linalg.norm(p.b) < 1e-7
+    h64.close()
+    h32.close()
