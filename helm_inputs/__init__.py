@@ -296,6 +296,7 @@ class Precond:
     omega: float = 0.5
     max_levels: int = 32
     coarse_max: int = 8
+    galerkin: bool = False   # 2D, omega-Jacobi: coarse operators R A P instead of rediscretised
 
 
 @dataclasses.dataclass

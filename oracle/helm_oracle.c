@@ -17,8 +17,9 @@
  *     (or only the interior) mesh width multiplied by beta = e^{i theta_beta}, eq. "CSL-CSG"
  *     and eq. "lapctucsg" (Section 5.3);
  *   - geometric multigrid on the preconditioner (Section 5.1, Section 6.1 components: full
- *     weighting restriction, bilinear prolongation, rediscretised ("direct") coarse operators,
- *     omega-Jacobi; red-black Gauss-Seidel as a second smoother; direct coarsest solve);
+ *     weighting restriction, bilinear prolongation, rediscretised ("direct") coarse operators
+ *     or (2D) Galerkin coarse operators R A P, omega-Jacobi; red-black Gauss-Seidel as a
+ *     second smoother; direct coarsest solve);
  *   - right-preconditioned Bi-CGSTAB (van der Vorst 1992) and IDR(s) (Sonneveld & van Gijzen
  *     2008), the Krylov methods of Section 6.2, stopped on ||d_m|| / ||d_0|| < tol (the
  *     stopping rule of Section 6.2), followed by a true-residual check.
@@ -54,6 +55,7 @@ typedef struct {
   double omega;         /* Jacobi damping */
   int max_levels;       /* cap on the number of levels (>= 1) */
   int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
+  int galerkin;         /* 1: coarse operators R A P (2D, 9-point) instead of rediscretised */
 } orc_precond;
 
 typedef struct {
@@ -88,6 +90,8 @@ typedef struct {
   axis_t ax[3];
   double* phi;    /* k(x)^2 at every unknown */
   cplx s;         /* sigma = s * phi; 1 for H and CSG, beta^2 for CSL */
+  cplx* st9;      /* Galerkin levels (2D): row p is st9[9p + 3(dj+1) + (di+1)], the weight of the
+                     unknown (i+di, j+dj); NULL for a Shortley-Weller level */
 } level_t;
 
 typedef struct orc_ctx {
@@ -166,6 +170,7 @@ static void axis_free(axis_t* a) {
 }
 
 static void level_free(level_t* L) {
+  free(L->st9);
   for (int d = 0; d < L->dim; ++d) axis_free(&L->ax[d]);
   free(L->phi);
 }
@@ -214,8 +219,10 @@ static void level_coarse(const level_t* F, level_t* C) {
   C->s = F->s;
 }
 
-/* Diagonal of the operator at point (i,j,l): sum of the per-axis centre weights - s*phi. */
+/* Diagonal of the operator at point (i,j,l): sum of the per-axis centre weights - s*phi
+ * (a Galerkin level: its stencil's centre weight). */
 static cplx diag_at(const level_t* L, int i, int j, int l) {
+  if (L->st9) return L->st9[9 * lidx(L, i, j, l) + 4];
   int ix[3] = {i, j, l};
   cplx d = 0;
   for (int a = 0; a < L->dim; ++a) d += L->ax[a].a0[ix[a]];
@@ -224,6 +231,18 @@ static cplx diag_at(const level_t* L, int i, int j, int l) {
 
 /* Off-diagonal part of row (i,j,l) applied to x (Dirichlet neighbours contribute 0). */
 static cplx offdiag_at(const level_t* L, const cplx* x, int i, int j, int l) {
+  if (L->st9) {  /* the eight neighbours of a Galerkin stencil */
+    cplx acc = 0;
+    const cplx* w = L->st9 + 9 * lidx(L, i, j, l);
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        if (di == 0 && dj == 0) continue;
+        int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) continue;
+        acc += w[3 * (dj + 1) + (di + 1)] * x[lidx(L, ii, jj, 0)];
+      }
+    return acc;
+  }
   int ix[3] = {i, j, l};
   cplx acc = 0;
   for (int a = 0; a < L->dim; ++a) {
@@ -284,6 +303,17 @@ static void lu_solve(const cplx* A, const int* piv, long n, const cplx* b, cplx*
 static void level_dense(const level_t* L, cplx* A) {
   long n = L->ntot;
   memset(A, 0, sizeof(cplx) * n * n);
+  if (L->st9) {
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int i = 0; i < L->n[0]; ++i)
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            int ii = i + di, jj = j + dj;
+            if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) continue;
+            A[lidx(L, i, j, 0) * n + lidx(L, ii, jj, 0)] = L->st9[9 * lidx(L, i, j, 0) + 3 * (dj + 1) + (di + 1)];
+          }
+    return;
+  }
   for (int l = 0; l < L->n[2]; ++l)
     for (int j = 0; j < L->n[1]; ++j)
       for (int i = 0; i < L->n[0]; ++i) {
@@ -297,6 +327,65 @@ static void level_dense(const level_t* L, cplx* A) {
           if (k < L->n[a] - 1) A[p * n + p + stride] = L->ax[a].ap[k];
         }
       }
+}
+
+/* Weight of fine unknown `fine` in the full-weighting row of coarse unknown `coarse` along one
+ * axis: the row gathers fine 2c, 2c+1, 2c+2 with 1/4, 1/2, 1/4. */
+static double fw_weight(int fine, int coarse) {
+  int d = fine - (2 * coarse + 1);
+  return d == 0 ? 0.5 : (d == 1 || d == -1 ? 0.25 : 0.0);
+}
+
+/* Weight of coarse unknown `coarse` in the linear interpolation of fine unknown `fine` along
+ * one axis: 1 at fine 2c+1, 1/2 at fine 2c and 2c+2. */
+static double lin_weight(int fine, int coarse) {
+  int d = fine - (2 * coarse + 1);
+  return d == 0 ? 1.0 : (d == 1 || d == -1 ? 0.5 : 0.0);
+}
+
+/* Entry (row p, column q) of a 2D level's operator, by its definition. */
+static cplx entry2d(const level_t* L, int i, int j, int ii, int jj) {
+  if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) return 0;
+  if (L->st9) {
+    int di = ii - i, dj = jj - j;
+    if (di < -1 || di > 1 || dj < -1 || dj > 1) return 0;
+    return L->st9[9 * lidx(L, i, j, 0) + 3 * (dj + 1) + (di + 1)];
+  }
+  if (ii == i && jj == j) return diag_at(L, i, j, 0);
+  if (jj == j && ii == i - 1) return L->ax[0].am[i];
+  if (jj == j && ii == i + 1) return L->ax[0].ap[i];
+  if (ii == i && jj == j - 1) return L->ax[1].am[j];
+  if (ii == i && jj == j + 1) return L->ax[1].ap[j];
+  return 0;
+}
+
+/* Galerkin coarse operator (2D): C = R F P with R the full weighting and P the linear
+ * interpolation of the V-cycle, entry by entry:
+ *   C[(I,J), (K,M)] = sum_{fine a,b} R[(I,J),(a,b)] sum_{fine c,d} F[(a,b),(c,d)] P[(c,d),(K,M)],
+ * where only |K - I| <= 1, |M - J| <= 1 can be non-zero (the 9-point result); in the loops
+ * (I, J) is (ci, cj) and (K, M) is (ck, cm). */
+static void level_galerkin(const level_t* F, level_t* C) {
+  C->st9 = calloc(9 * (size_t)imax(C->ntot, 1), sizeof(cplx));
+  for (int cj = 0; cj < C->n[1]; ++cj)
+    for (int ci = 0; ci < C->n[0]; ++ci)
+      for (int dm = -1; dm <= 1; ++dm)
+        for (int dk = -1; dk <= 1; ++dk) {
+          int ck = ci + dk, cm = cj + dm;
+          if (ck < 0 || ck >= C->n[0] || cm < 0 || cm >= C->n[1]) continue;
+          cplx acc = 0;
+          for (int b = 2 * cj; b <= 2 * cj + 2; ++b)
+            for (int a = 2 * ci; a <= 2 * ci + 2; ++a) {
+              if (a >= F->n[0] || b >= F->n[1]) continue;
+              double r = fw_weight(a, ci) * fw_weight(b, cj);
+              for (int d = b - 1; d <= b + 1; ++d)
+                for (int c2 = a - 1; c2 <= a + 1; ++c2) {
+                  double pw = lin_weight(c2, ck) * lin_weight(d, cm);
+                  if (pw == 0.0) continue;
+                  acc += r * entry2d(F, a, b, c2, d) * pw;
+                }
+            }
+          C->st9[9 * lidx(C, ci, cj, 0) + 3 * (dm + 1) + (dk + 1)] = acc;
+        }
 }
 
 /* ---- context ------------------------------------------------------------------------- */
@@ -324,6 +413,7 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_p
     }
     if (all_small || min_n < 3) break;
     level_coarse(F, &c->M[c->nlev]);
+    if (pc->galerkin && g->dim == 2) level_galerkin(F, &c->M[c->nlev]);
     c->nlev++;
   }
   level_t* C = &c->M[c->nlev - 1];
@@ -371,6 +461,12 @@ void orc_level_phi(const orc_ctx* c, int which, int lvl, double* phi, cplx* s) {
 }
 
 /* y = H x (which = 0) or y = M_lvl x (which = 1). */
+void orc_level_st9(const orc_ctx* c, int lvl, cplx* out) {
+  const level_t* L = pick(c, 1, lvl);
+  if (L->st9) memcpy(out, L->st9, sizeof(cplx) * 9 * L->ntot);
+  else memset(out, 0, sizeof(cplx) * 9 * L->ntot);
+}
+
 void orc_apply(const orc_ctx* c, int which, int lvl, const cplx* x, cplx* y) {
   level_apply(pick(c, which, lvl), x, y);
 }

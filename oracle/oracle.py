@@ -43,7 +43,7 @@ class _Precond(C.Structure):
     _fields_ = [("kind", C.c_int), ("theta_beta", C.c_double), ("shift_re", C.c_double),
                 ("shift_im", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("smoother", C.c_int), ("omega", C.c_double), ("max_levels", C.c_int),
-                ("coarse_max", C.c_int)]
+                ("coarse_max", C.c_int), ("galerkin", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -69,6 +69,7 @@ def _load():
         lib.orc_level_shape.argtypes = [vp, ip, ip, vp]
         lib.orc_axis_tables.argtypes = [vp, ip, ip, ip, vp, vp, vp, vp, vp]
         lib.orc_level_phi.argtypes = [vp, ip, ip, vp, vp]
+        lib.orc_level_st9.argtypes = [vp, ip, vp]
         lib.orc_apply.argtypes = [vp, ip, ip, vp, vp]
         lib.orc_dense.argtypes = [vp, ip, ip, vp]
         lib.orc_vcycle.argtypes = [vp, vp, vp]
@@ -112,7 +113,8 @@ class Oracle:
             g.extent[a] = problem.extent[a]
         g.theta_gamma = problem.theta_gamma
         p = _Precond(pc.kind, pc.theta_beta, complex(pc.shift).real, complex(pc.shift).imag,
-                     pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max)
+                     pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max,
+                     1 if getattr(pc, "galerkin", False) else 0)
         self._phi = None
         if problem.phi is not None:
             self._phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
@@ -147,6 +149,14 @@ class Oracle:
         s = np.zeros(1, np.complex128)
         _lib.orc_level_phi(self._h, which, lvl, _ptr(phi), _ptr(s))
         return phi, complex(s[0])
+
+    def level_stencil9(self, lvl):
+        """Galerkin 9-point stencil of preconditioner level lvl, shape (ntot, 3, 3) indexed
+        [p, dj+1, di+1]; zeros for a Shortley-Weller level."""
+        m = self.level_size(1, lvl)
+        out = np.zeros(9 * m, np.complex128)
+        _lib.orc_level_st9(self._h, lvl, _ptr(out))
+        return out.reshape(m, 3, 3)
 
     def apply(self, x, which=0, lvl=0):
         x = _c128(x)

@@ -484,3 +484,78 @@ def test_zero_rhs_and_stopping_rule():
     h = info["history"]
     assert h[-1] < 1e-6 and np.all(h[:-1] >= 1e-6)  # stops at the first recurrence hit
     assert info["rel_res_true"] < 1e-6
+
+
+# ---- Galerkin coarse operators (2D) ------------------------------------------------------------
+
+def _fw_matrix(nf, nc):
+    """Full weighting in index space from its definition: coarse c gathers fine 2c, 2c+1, 2c+2
+    with 1/4, 1/2, 1/4 (fine indices past the grid are Dirichlet)."""
+    R = np.zeros((nc, nf))
+    for c in range(nc):
+        for d, w in ((-1, 0.25), (0, 0.5), (1, 0.25)):
+            f = 2 * c + 1 + d
+            if 0 <= f < nf:
+                R[c, f] = w
+    return R
+
+
+def _lin_matrix(nf, nc):
+    """Linear interpolation in index space: fine 2c+1 takes coarse c, fine 2c and 2c+2 half."""
+    P = np.zeros((nf, nc))
+    for c in range(nc):
+        for d, w in ((-1, 0.5), (0, 1.0), (1, 0.5)):
+            f = 2 * c + 1 + d
+            if 0 <= f < nf:
+                P[f, c] = w
+    return P
+
+
+def _stencil_to_dense(st, n0, n1):
+    A = np.zeros((n0 * n1, n0 * n1), np.complex128)
+    for j in range(n1):
+        for i in range(n0):
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    ii, jj = i + di, j + dj
+                    if 0 <= ii < n0 and 0 <= jj < n1:
+                        A[i + n0 * j, ii + n0 * jj] = st[i + n0 * j, dj + 1, di + 1]
+    return A
+
+
+def test_galerkin_coarse_operator_is_R_A_P():
+    """Every Galerkin level equals R A P formed from dense matrices (R, P from the definitions of
+    full weighting and linear interpolation, A the finer level's dense operator) on a complex
+    CSG / ECS grid with one-sided layers and a variable k."""
+    p = hi.make_problem(2, (29, 22), ((3, 0), (2, 4)), theta_gamma=0.5, k0=9.0, phi_kind="bump", rhs="zero")
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, galerkin=True)
+    o = Oracle(p, pc)
+    assert o.nlev >= 3  # level 2 is the Galerkin operator of a Galerkin operator
+    for lvl in range(1, o.nlev):
+        nf = o.level_shape(1, lvl - 1)
+        nc = o.level_shape(1, lvl)
+        R = np.kron(_fw_matrix(nf[1], nc[1]), _fw_matrix(nf[0], nc[0]))
+        P = np.kron(_lin_matrix(nf[1], nc[1]), _lin_matrix(nf[0], nc[0]))
+        A = o.dense(1, lvl - 1)
+        C = _stencil_to_dense(o.level_stencil9(lvl), nc[0], nc[1])
+        assert np.abs(C - R @ A @ P).max() <= 1e-12 * np.abs(R @ A @ P).max()
+        assert np.abs(o.dense(1, lvl) - C).max() == 0.0  # the level's operator is that stencil
+
+
+def test_galerkin_laplacian_closed_form():
+    """Uniform Dirichlet grid, k = 0: the Galerkin operator of the 2D Laplacian is the Kronecker
+    form A_x (x) M_y + M_x (x) A_y with the 1D Galerkin rows; in the interior those rows are the
+    rediscretised (-1, 2, -1) / (2h)^2 and the mass (1/8, 3/4, 1/8)."""
+    n = 15
+    p = hi.make_problem(2, n + 2, 0, theta_gamma=0.0, k0=0.0, rhs="zero")
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1.0, smoother=hi.SM_JACOBI, galerkin=True, max_levels=2)
+    o = Oracle(p, pc)
+    h = 1.0 / (n + 1)
+    a1 = (np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)) / h ** 2
+    R, P = _fw_matrix(n, n // 2), _lin_matrix(n, n // 2)
+    ac, mc = R @ a1 @ P, R @ P
+    mid = (n // 2) // 2
+    assert np.allclose(ac[mid, mid - 1: mid + 2], np.array([-1, 2, -1]) / (2 * h) ** 2, rtol=1e-13)
+    assert np.allclose(mc[mid, mid - 1: mid + 2], [0.125, 0.75, 0.125], rtol=1e-14)
+    C = o.dense(1, 1)
+    assert np.allclose(C, np.kron(mc, ac) + np.kron(ac, mc), rtol=1e-12, atol=1e-9)
