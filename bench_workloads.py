@@ -13,8 +13,8 @@
             the north / east edges, Dirichlet south / west; 512^2 unknowns) and 3 (r = 90, k = 2:
             1024^2 + 256; 1280^2 unknowns), theta_gamma = pi/6; one step solves them six times at
             once, {Bi-CGSTAB, IDR(4), IDR(8)} x {CSL, CSG} with the shift and angle of the paper's
-            ECS rows (omega-Jacobi V(1,1) here, not the paper's ILU(0) / Galerkin V(0,1), so the
-            paper's matvec counts, reported beside ours, are context).
+            ECS rows and its Galerkin coarse operators (omega-Jacobi V(1,1) here, not the paper's
+            ILU(0) V(0,1), so the paper's matvec counts, reported beside ours, are context).
   serve     a Poisson-arrival stream (--serve-requests, default 32, at --serve-rate, default 200
             requests/s) of 2D (127^2 .. 1023^2 interior) and 3D (64^3 .. 160^3 interior) requests
             with 1..8 point-source right-hand sides each, submitted at their arrival times to the
@@ -437,8 +437,9 @@ def run_mp(args, torch, ranks, dev, local):
     b_dev = torch.from_numpy(p.b).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     solves = [(m, s, pcn) for pcn in ("csl", "csg") for (m, s) in (("bicgstab", 0), ("idr4", 4), ("idr8", 8))]
-    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], smoother=hi.SM_JACOBI, omega=0.5),
-           "csg": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=case["csg"], smoother=hi.SM_JACOBI, omega=0.5)}
+    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], smoother=hi.SM_JACOBI, omega=0.5, galerkin=True),
+           "csg": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=case["csg"], smoother=hi.SM_JACOBI, omega=0.5,
+                             galerkin=True)}
     methods = [hi.BICGSTAB if s == 0 else hi.IDR for (_, s, _) in solves]
     svals = [max(s, 1) for (_, s, _) in solves]
     shadows = [hi.shadow_space(p.n, s) if s else None for (_, s, _) in solves]
@@ -473,7 +474,7 @@ def run_mp(args, torch, ranks, dev, local):
     cfg = {"workload": p.name, "n_unknowns": p.n, "solves_per_step": ns,
            "solves": "{Bi-CGSTAB, IDR(4), IDR(8)} x {CSL shift %s, CSG theta_beta %.4f}, run at once"
                      % (case["csl"], case["csg"]),
-           "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, rediscretised coarse operators",
+           "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, Galerkin coarse operators R A P",
            "boundaries": "Dirichlet south / west, ECS layers east / north (theta_gamma = pi/6)",
            "l2": "flushed (512 MiB device write) before every timed step"}
     line = _base(args, ranks.job_rate(done(res["c128"][1]), res["c128"][0]), res["c128"][0], ranks.world, cfg, "c128")

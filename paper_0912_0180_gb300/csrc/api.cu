@@ -73,7 +73,11 @@ static helm_status check_precond(const helm_precond* p) {
   if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
   if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
   if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
-  if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL | HELM_PF_NO_AUTOTUNE)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
+  if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL | HELM_PF_NO_AUTOTUNE | HELM_PF_GALERKIN)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
+  if ((p->flags & HELM_PF_GALERKIN) && p->smoother != HELM_SM_JACOBI) {
+    set_error("Galerkin coarse operators need the damped-Jacobi smoother");
+    return HELM_ERR_ARG;
+  }
   if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {
     set_error("non-finite preconditioner parameter");
     return HELM_ERR_ARG;
@@ -132,6 +136,10 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   helm_status s;
   if ((s = check_grid(grid)) != HELM_OK) return s;
   if ((s = check_precond(pc)) != HELM_OK) return s;
+  if ((pc->flags & HELM_PF_GALERKIN) && pc->kind != HELM_PC_NONE && grid->dim != 2) {
+    set_error("Galerkin coarse operators need a 2D grid");
+    return HELM_ERR_ARG;
+  }
   if (!k || !std::isfinite(k->k0)) { set_error("kspec missing or k0 not finite"); return HELM_ERR_ARG; }
   helm_ctx* c = new helm_ctx();
   c->grid = *grid;

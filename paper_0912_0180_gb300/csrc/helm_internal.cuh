@@ -77,6 +77,9 @@ template <typename T> struct OpView {
   const cx<T>* dinv;  // omega/D (damped Jacobi) or 1/D (Gauss-Seidel) at every point of a
                       // multigrid level; nullptr otherwise
   const cx<T>* dg;    // the diagonal itself (multigrid levels; nullptr otherwise)
+  const cx<T>* st9;   // Galerkin level (2D): weight k = 3 (dj + 1) + (di + 1) of unknown p at
+                      // st9[k * ntot + p]; nullptr for a Shortley-Weller level
+  long ntot;
 };
 
 // ---- owned device storage of one level ---------------------------------------------------
@@ -102,6 +105,9 @@ struct LevelHost {
   float2* dinv32 = nullptr;
   double2* dg64 = nullptr;   // the diagonal itself, same precision
   float2* dg32 = nullptr;
+  // Galerkin coarse operator (2D, 9-point), [9][ntot]; FP64 always, FP32 copy for FP32 multigrid
+  double2* st9_64 = nullptr;
+  float2* st9_32 = nullptr;
   // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, -1 by the block-count rule
   int tile_down = -1, tile_up = -1;
   // work vectors (MG type), allocated for multigrid levels

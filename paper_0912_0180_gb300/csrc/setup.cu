@@ -205,6 +205,102 @@ __global__ void k_gauss_jordan(double2* A, double2* X, int n, int* status) {
 
 static int ceil_div(long a, int b) { return (int)((a + b - 1) / b); }
 
+// ---- Galerkin coarse operators (2D) ---------------------------------------------------------
+// Entry of the finer operator between fine unknowns (i, j) and (ii, jj): its 9-point stencil when
+// it is a Galerkin level, else its Shortley-Weller row (centre: axis centre weights - s phi).
+__device__ double2 fine_entry(const OpView<double>& F, int i, int j, int ii, int jj) {
+  if (ii < 0 || ii >= F.n[0] || jj < 0 || jj >= F.n[1]) return mkc<double>(0.0, 0.0);
+  const int di = ii - i, dj = jj - j;
+  const long p = i + (long)F.n[0] * j;
+  if (F.st9) return F.st9[(long)(3 * (dj + 1) + (di + 1)) * F.ntot + p];
+  if (di == 0 && dj == 0) {
+    double ph = F.phi ? F.phi[p] : F.phi0;
+    return csub<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), cscale<double>(ph, F.s));
+  }
+  if (di != 0 && dj != 0) return mkc<double>(0.0, 0.0);  // a 5-point row has no corner weights
+  if (dj == 0) return di < 0 ? F.am[0][i] : F.ap[0][i];
+  return dj < 0 ? F.am[1][j] : F.ap[1][j];
+}
+
+// C = R F P for one coarse unknown per thread: R gathers fine 2I+{0,1,2} x 2J+{0,1,2} with the
+// full-weighting weights, P spreads coarse (K, M) over fine 2K+{0,1,2} x 2M+{0,1,2} with the
+// linear-interpolation weights; only |K - I|, |M - J| <= 1 survive.
+__global__ void k_galerkin2d(OpView<double> F, int nc0, int nc1, double2* __restrict__ c64, float2* __restrict__ c32) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y;
+  if (I >= nc0) return;
+  const long ncs = (long)nc0 * nc1;
+  const long q = I + (long)nc0 * J;
+  const double wr[3] = {0.25, 0.5, 0.25};
+  double2 acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = mkc<double>(0.0, 0.0);
+  for (int b = 0; b < 3; ++b) {
+    const int fj = 2 * J + b;
+    if (fj >= F.n[1]) continue;
+    for (int a = 0; a < 3; ++a) {
+      const int fi = 2 * I + a;
+      if (fi >= F.n[0]) continue;
+      const double r = wr[a] * wr[b];
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const double2 e = fine_entry(F, fi, fj, fi + di, fj + dj);
+          if (e.x == 0.0 && e.y == 0.0) continue;
+          const int gi = fi + di, gj = fj + dj;  // the fine unknown the entry reaches
+          // coarse (K, M) with |gi - (2K+1)| <= 1 and |gj - (2M+1)| <= 1
+          for (int dM = -1; dM <= 1; ++dM) {
+            const int M = J + dM;
+            const int ty = gj - (2 * M + 1);
+            if (M < 0 || M >= nc1 || ty < -1 || ty > 1) continue;
+            const double py = ty == 0 ? 1.0 : 0.5;
+            for (int dK = -1; dK <= 1; ++dK) {
+              const int K = I + dK;
+              const int tx = gi - (2 * K + 1);
+              if (K < 0 || K >= nc0 || tx < -1 || tx > 1) continue;
+              const double w = r * py * (tx == 0 ? 1.0 : 0.5);
+              double2& o = acc[3 * (dM + 1) + (dK + 1)];
+              o = mkc<double>(fma(w, e.x, o.x), fma(w, e.y, o.y));
+            }
+          }
+        }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    c64[k * ncs + q] = acc[k];
+    if (c32) c32[k * ncs + q] = cconv<float, double>(acc[k]);
+  }
+}
+
+// omega / D and D of a Galerkin level (D = the stencil's centre weight).
+__global__ void k_dinv9(const double2* __restrict__ st9, long n, double omega_s, double2* d64, float2* d32,
+                        double2* g64, float2* g32) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double2 d = st9[4 * n + p];
+  double2 r = cscale<double>(omega_s, crecip<double>(d));
+  if (d64) d64[p] = r;
+  if (g64) g64[p] = d;
+  if (d32) d32[p] = cconv<float, double>(r);
+  if (g32) g32[p] = cconv<float, double>(d);
+}
+
+// Dense matrix of a Galerkin coarsest level (row-major, FP64), one thread per row.
+__global__ void k_dense_assemble9(const double2* __restrict__ st9, int n0, int n1, double2* A, int n) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = p % n0, j = p / n0;
+  double2* row = A + (long)p * n;
+  for (int c = 0; c < n; ++c) row[c] = mkc<double>(0.0, 0.0);
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      int ii = i + di, jj = j + dj;
+      if (ii < 0 || ii >= n0 || jj < 0 || jj >= n1) continue;
+      row[ii + n0 * jj] = st9[(long)(3 * (dj + 1) + (di + 1)) * n + p];
+    }
+}
+
+
 // In-place Gauss-Jordan with partial pivoting over the whole GPU, for coarsest levels too
 // large for one block: A (n x n, row-major) is overwritten with A^{-1}.  Step k: one block picks
 // the pivot row p >= k of column k; rows k and p are exchanged while the pivot row is scaled
@@ -395,6 +491,8 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.uniform_iso = iso ? 1 : 0;
   v.dinv = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dinv64 : (const cx<T>*)(const void*)dinv32;
   v.dg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dg64 : (const cx<T>*)(const void*)dg32;
+  v.st9 = std::is_same<T, double>::value ? (const cx<T>*)(const void*)st9_64 : (const cx<T>*)(const void*)st9_32;
+  v.ntot = ntot;
   return v;
 }
 template OpView<double> LevelHost::view<double>() const;
@@ -441,6 +539,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   helm_status rc;
   c->lv.clear();
   c->lv.reserve(pc.max_levels);
+  const bool galerkin = (pc.flags & HELM_PF_GALERKIN) != 0;
   c->lv.emplace_back();
   {
     LevelHost& L0 = c->lv[0];
@@ -490,6 +589,15 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     }
     HELM_CUDA(cudaGetLastError());
     if ((rc = find_uniform(C, st)) != HELM_OK) return rc;
+    if (galerkin) {
+      // R F P replaces the rediscretised row; its uniform-interior shortcut does not apply
+      for (int a = 0; a < 3; ++a) { C.ulo[a] = 1; C.uhi[a] = 0; }
+      if ((rc = ctx_alloc(c, (void**)&C.st9_64, sizeof(double2) * 9 * C.ntot)) != HELM_OK) return rc;
+      if (f32 && (rc = ctx_alloc(c, (void**)&C.st9_32, sizeof(float2) * 9 * C.ntot)) != HELM_OK) return rc;
+      dim3 gg(ceil_div(C.n[0], 128), C.n[1]);
+      k_galerkin2d<<<gg, 128, 0, st>>>(F.view<double>(), C.n[0], C.n[1], C.st9_64, C.st9_32);
+      HELM_CUDA(cudaGetLastError());
+    }
     c->lv.push_back(C);
   }
   // work vectors: level 0 needs one spare buffer (its f and u are the caller's); coarser
@@ -507,7 +615,8 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       OpView<double> v = L.view<double>();
       dim3 g((L.n[0] + 127) / 128, L.n[1], L.n[2]);
       double om = pc.smoother == HELM_SM_JACOBI ? pc.omega : 1.0;
-      if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      if (L.st9_64) k_dinv9<<<ceil_div(L.ntot, 256), 256, 0, st>>>(L.st9_64, L.ntot, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      else if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       else if (L.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       else k_dinv<3><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       HELM_CUDA(cudaGetLastError());
@@ -522,7 +631,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
   // constant phi on a large coarsest level: the separable exact solve, no dense inverse
-  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64) {
+  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.st9_64) {
     if ((rc = fdm_build(c, Cst, f32, st)) != HELM_OK) return rc;
     if (c->fdm.on) {
       c->nco = 0;
@@ -556,7 +665,8 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     return cuda_check(e2, "cudaMallocAsync(coarse)");
   }
   cudaMemsetAsync(flag, 0, sizeof(int), st);
-  k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
+  if (Cst.st9_64) k_dense_assemble9<<<ceil_div(n, 128), 128, 0, st>>>(Cst.st9_64, Cst.n[0], Cst.n[1], A, n);
+  else k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
   const double2* inv = X;
   if (one_block) {
     int thr = 1024;
@@ -592,6 +702,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     return HELM_ERR_ARG;
   }
   c->tail_first = f32 ? tail_first_level<float>(c) : tail_first_level<double>(c);
+  if (galerkin) c->tail_first = (int)c->lv.size();  // the one-block tail runs 5-point rows only
   return autotune_tiles(c, st);
 }
 

@@ -78,7 +78,8 @@ class Helm:
                        precond.omega, precond.max_levels, precond.coarse_max,
                        L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
                        (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL)
-                       | (0 if autotune else L.HELM_PF_NO_AUTOTUNE))
+                       | (0 if autotune else L.HELM_PF_NO_AUTOTUNE)
+                       | (L.HELM_PF_GALERKIN if getattr(precond, "galerkin", False) else 0))
         h = C.c_void_p()
         _check(lib.helm_create(C.byref(g), C.byref(k), C.byref(pc), C.c_void_p(_stream(stream)), C.byref(h)),
                "helm_create")
@@ -218,7 +219,8 @@ class Server:
         rq.pc = L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
                           complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
                           precond.omega, precond.max_levels, precond.coarse_max,
-                          L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128, 0)
+                          L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
+                          L.HELM_PF_GALERKIN if getattr(precond, "galerkin", False) else 0)
         rq.opts = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None, 0)
         sh = None
         if shadow is not None:
