@@ -111,7 +111,9 @@ typedef struct {
  * one-warp tiles of the fused 2D kernels on every fused level and then whole V-cycles for every
  * admissible depth of the one-block tail kernel, keeps the fastest, and caches the choices for the
  * process (tiles by precision, smoother and level shape; depth by precision, smoother and
- * hierarchy); without it tiles follow a block-count rule and the tail a point budget.  Tiles
+ * hierarchy); without it tiles follow a block-count rule and the tail a point budget.  When the
+ * environment variable HELM_TUNE_CACHE names a file, the process reads earlier decisions from it
+ * and appends its new ones, so that another process (say, one under a profiler) makes the same.  Tiles
  * change the speed only (every point is computed by the same formulas); the tail depth also
  * changes the summation order inside the small levels, i.e. the rounding. */
 enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4, HELM_PF_GALERKIN = 8 };

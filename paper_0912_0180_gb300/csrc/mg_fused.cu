@@ -18,6 +18,9 @@
 //            kernel launches.
 //
 // Outside the grid every value is a Dirichlet zero, as in the unfused kernels.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -640,6 +643,47 @@ std::map<std::tuple<int, int, int, int, int, int, int>, int> g_depth;       // t
 // the tail depths the autotuner tries are bounded by this many points (and by shared memory)
 constexpr long TAIL_TUNE_POINTS = 700;
 
+// Decisions persist across processes when HELM_TUNE_CACHE names a file: it is read once (lines
+// "tile <bytes> <rbgs> <n0> <n1> <down> <up>" and "depth <bytes> <rbgs> <dim> <n0> <n1> <n2> <levels>
+// <first>") and every new decision is appended, so that a later process -- one under a profiler,
+// whose serialised launches would distort the timings -- makes the same choices.
+static const char* tune_cache_path() {
+  const char* p = std::getenv("HELM_TUNE_CACHE");
+  return p && *p ? p : nullptr;
+}
+static void tune_cache_load_locked() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return;
+  char kind[16];
+  while (std::fscanf(fp, "%15s", kind) == 1) {
+    if (!std::strcmp(kind, "tile")) {
+      int b, rb, n0, n1, d, u;
+      if (std::fscanf(fp, "%d %d %d %d %d %d", &b, &rb, &n0, &n1, &d, &u) != 6) break;
+      g_tune[std::make_tuple(b, rb, n0, n1)] = {d, u};
+    } else if (!std::strcmp(kind, "depth")) {
+      int b, rb, dim, n0, n1, n2, nl, first;
+      if (std::fscanf(fp, "%d %d %d %d %d %d %d %d", &b, &rb, &dim, &n0, &n1, &n2, &nl, &first) != 8) break;
+      g_depth[std::make_tuple(b, rb, dim, n0, n1, n2, nl)] = first;
+    } else {
+      break;
+    }
+  }
+  std::fclose(fp);
+}
+static void tune_cache_append(const char* line) {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* fp = std::fopen(path, "a");
+  if (!fp) return;
+  std::fputs(line, fp);
+  std::fclose(fp);
+}
+
 template <typename F_>
 static float time_variant(F_ launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   launch();
@@ -659,12 +703,17 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   const bool fused2d = c->lv[0].dim == 2 && c->pc.nu1 == 1 && c->pc.nu2 == 1;
   // 1. tiles of every level that can run the fused 2D kernels
   std::vector<int> todo;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load_locked();
+  }
   if (fused2d) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (int l = 0; l < nl - 1; ++l) {
       if (c->lv[l].st9_64) continue;  // Galerkin levels do not run the fused kernels
       auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
-      if (it != g_tune.end()) {
+      auto valid = [](int t) { return t == TILE_BIG || t == TILE_SMALL || t == TILE_TINY; };
+      if (it != g_tune.end() && valid(it->second.first) && valid(it->second.second)) {
         c->lv[l].tile_down = it->second.first;
         c->lv[l].tile_up = it->second.second;
       } else {
@@ -679,7 +728,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   if (tune_depth) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_depth.find(dkey);
-    if (it != g_depth.end()) {
+    if (it != g_depth.end() && it->second >= deepest && it->second <= nl) {  // a cached depth must fit
       c->tail_first = it->second;
       tune_depth = false;
     }
@@ -715,6 +764,10 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     c->lv[l].tile_up = best_u;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[std::make_tuple((int)sizeof(T), (int)RB, F.n[0], F.n[1])] = {c->lv[l].tile_down, c->lv[l].tile_up};
+    char line[128];
+    std::snprintf(line, sizeof line, "tile %d %d %d %d %d %d\n", (int)sizeof(T), (int)RB, F.n[0], F.n[1],
+                  c->lv[l].tile_down, c->lv[l].tile_up);
+    tune_cache_append(line);
   }
   if (tune_depth) {
     int best = c->tail_first;
@@ -727,6 +780,10 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     c->tail_first = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_depth[dkey] = best;
+    char line[160];
+    std::snprintf(line, sizeof line, "depth %d %d %d %d %d %d %d %d\n", (int)sizeof(T), (int)RB, c->lv[0].dim,
+                  c->lv[0].n[0], c->lv[0].n[1], c->lv[0].n[2], nl, best);
+    tune_cache_append(line);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
