@@ -42,6 +42,7 @@ class Problem:
     k0: float                  # constant wave number when phi is None
     b: np.ndarray              # right-hand side (complex128, x fastest)
     name: str = ""
+    ecs_ramp: int = 0          # > 1: the layer contour turns over this many widths (smooth ECS)
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -98,12 +99,14 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
                  theta_gamma=0.5, k0: float = 0.0, phi_kind: str = "const", bump_amp=0.3,
                  bump_width2=0.02, bump_centre=(0.5, 0.5, 0.5), rhs: str = "point",
                  rhs_width_h: float = 2.0, seed: int = BASE_SEED, name: str = "",
-                 phi_fn=None, rhs_fn=None) -> Problem:
+                 phi_fn=None, rhs_fn=None, ecs_ramp: int = 0) -> Problem:
     """Build a seeded synthetic instance shaped like the paper's model problems.
 
     n_l: int (all sides), one (lo, hi) pair for every axis, or per-axis (lo, hi) pairs.
     phi_kind: "const" (k = k0), "bump" (k = k0 (1 + amp exp(-|x - c|^2 / width2))), or "field"
          (phi = phi_fn(x, y[, z]) at the real node positions).
+    ecs_ramp: 0 = sharp ECS contour; R > 1 = the contour turns by theta_gamma / R per layer width
+         over the first R widths (the smooth transition of the paper's Section 7 remark).
     rhs: "point" (value 1 at the interior node floor((n_int-1)/2) per axis, as in MP1),
          "gauss" (exp(-|x - x_s|^2 / (2 sigma^2)), sigma = rhs_width_h * h, x_s uniform in
          [0.1, 0.9]^d from the seed), "random" (complex normal entries), "zero", "field"
@@ -121,7 +124,8 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
     ext = _dims3(dim, [extent] if np.isscalar(extent) else list(extent))
     p = Problem(dim=dim, n_int=tuple(int(x) for x in ni), n_layer=nl,
                 extent=tuple(float(x) for x in ext), theta_gamma=float(theta_gamma),
-                phi=None, k0=float(k0), b=np.zeros(0, np.complex128), name=name)
+                phi=None, k0=float(k0), b=np.zeros(0, np.complex128), name=name,
+                ecs_ramp=int(ecs_ramp))
     shape = p.shape
     X = mesh(p)
     if phi_kind == "bump":

@@ -44,6 +44,9 @@ typedef struct {
   int n_layer[3][2];    /* ECS layer nodes on the low / high side; 0 = Dirichlet wall */
   double extent[3];     /* length of the real interior along each axis */
   double theta_gamma;   /* ECS angle */
+  int ecs_ramp;         /* R > 1: the m-th layer width from the turning point has angle
+                           theta_gamma * min(m, R) / R (smooth ECS transition, Section 7);
+                           0 or 1: the sharp contour */
 } orc_grid;
 
 typedef struct {
@@ -110,21 +113,28 @@ static long imax(long a, long b) { return a > b ? a : b; }
 /* Complex mesh widths of one axis (Section 2: h_gamma = h e^{i theta_gamma} on the layers;
  * Section 5.3: CSG multiplies widths by beta).  scale_in multiplies the interior widths,
  * scale_ly the layer widths. */
+/* Width of the m-th layer gap counted outwards from the turning point (m >= 1): h e^{i theta},
+ * theta = theta_gamma for the sharp contour, theta_gamma * min(m, R) / R for a ramp of R widths. */
+static cplx layer_width(double h, double theta_g, int ramp, int m) {
+  double th = theta_g;
+  if (ramp > 1 && m < ramp) th = theta_g * m / ramp;
+  return h * cexp(I * th);
+}
+
 static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, double theta_g,
-                       cplx scale_in, cplx scale_ly) {
+                       int ramp, cplx scale_in, cplx scale_ly) {
   double h = extent / (n_int - 1);
-  cplx hg = h * cexp(I * theta_g);
   int lo = nl[0], hi = nl[1];
   int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
   a->n = ngap - 1;
   a->gap = malloc(sizeof(cplx) * ngap);
   a->pos = malloc(sizeof(double) * imax(a->n, 1));
   int g = 0;
-  if (lo > 0)
-    for (int m = 0; m < lo + 1; ++m) a->gap[g++] = hg * scale_ly;
+  if (lo > 0)  /* outermost first: gap m = lo + 1 down to 1 */
+    for (int m = lo + 1; m >= 1; --m) a->gap[g++] = layer_width(h, theta_g, ramp, m) * scale_ly;
   for (int m = 0; m < n_int - 1; ++m) a->gap[g++] = h * scale_in;
   if (hi > 0)
-    for (int m = 0; m < hi + 1; ++m) a->gap[g++] = hg * scale_ly;
+    for (int m = 1; m <= hi + 1; ++m) a->gap[g++] = layer_width(h, theta_g, ramp, m) * scale_ly;
   /* real positions: the layers continue the real coordinate */
   int u = 0;
   for (int m = lo; m >= 1; --m) a->pos[u++] = -m * h;
@@ -187,7 +197,7 @@ static void level_fine(level_t* L, const orc_grid* g, const double* phi, double 
   L->ntot = 1;
   for (int d = 0; d < 3; ++d) L->n[d] = 1;
   for (int d = 0; d < g->dim; ++d) {
-    axis_build(&L->ax[d], g->n_int[d], g->n_layer[d], g->extent[d], g->theta_gamma,
+    axis_build(&L->ax[d], g->n_int[d], g->n_layer[d], g->extent[d], g->theta_gamma, g->ecs_ramp,
                scale_in, scale_ly);
     axis_coeffs(&L->ax[d]);
     L->n[d] = L->ax[d].n;

@@ -36,7 +36,8 @@ def build_oracle(force: bool = False) -> str:
 
 class _Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_int", C.c_int * 3), ("n_layer", (C.c_int * 2) * 3),
-                ("extent", C.c_double * 3), ("theta_gamma", C.c_double)]
+                ("extent", C.c_double * 3), ("theta_gamma", C.c_double),
+                ("ecs_ramp", C.c_int)]
 
 
 class _Precond(C.Structure):
@@ -112,6 +113,7 @@ class Oracle:
             g.n_layer[a][1] = problem.n_layer[a][1]
             g.extent[a] = problem.extent[a]
         g.theta_gamma = problem.theta_gamma
+        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
         p = _Precond(pc.kind, pc.theta_beta, complex(pc.shift).real, complex(pc.shift).imag,
                      pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max,
                      1 if getattr(pc, "galerkin", False) else 0)

@@ -21,19 +21,27 @@ def _prob(dim, n_int, n_l, theta=0.5, k0=0.0, extent=1.0, phi=None, rhs="random"
     return p
 
 
-def _node_z(n_int, nl, extent, theta):
+def _node_z(n_int, nl, extent, theta, ramp=0):
     """Complex coordinates of the unknowns and of the two Dirichlet ends, written from the
-    ECS map of Section 2 (layer width h e^{i theta}), independently of the oracle."""
+    ECS map of Section 2 (layer width h e^{i theta}), independently of the oracle.  With a
+    ramp of R > 1 widths the contour instead turns by theta / R at each of the first R layer
+    nodes (the smooth transition of the Section 7 remark): the node m steps into the layer
+    sits at the turning point plus sum_{q <= m} h e^{i theta min(q, R) / R}."""
     h = extent / (n_int - 1)
-    hg = h * np.exp(1j * theta)
     lo, hi_ = nl
-    z = [-m * hg for m in range(lo, 0, -1)]
+
+    def depth(m):  # complex distance of the m-th layer node from the turning point
+        if ramp > 1:
+            return sum(h * np.exp(1j * theta * min(q, ramp) / ramp) for q in range(1, m + 1))
+        return m * h * np.exp(1j * theta)
+
+    z = [-depth(m) for m in range(lo, 0, -1)]
     first = 0 if lo > 0 else 1
     last = n_int - 1 if hi_ > 0 else n_int - 2
     z += [j * h for j in range(first, last + 1)]
-    z += [extent + m * hg for m in range(1, hi_ + 1)]
-    zlo = -(lo + 1) * hg if lo > 0 else 0.0
-    zhi = extent + (hi_ + 1) * hg if hi_ > 0 else extent
+    z += [extent + depth(m) for m in range(1, hi_ + 1)]
+    zlo = -depth(lo + 1) if lo > 0 else 0.0
+    zhi = extent + depth(hi_ + 1) if hi_ > 0 else extent
     return np.asarray(z, np.complex128), zlo, zhi
 
 
@@ -96,15 +104,17 @@ def test_turning_point_rows_match_lemma31_matrix():
     assert np.allclose([S[t + 2, t + 1], S[t + 2, t + 2], S[t + 2, t + 3]], ev["layer"], atol=1e-13)
 
 
-@pytest.mark.parametrize("dim", [1, 2, 3])
-def test_shortley_weller_exact_for_quadratics(dim):
+@pytest.mark.parametrize("dim,ramp", [(1, 0), (2, 0), (3, 0), (1, 3), (2, 5)])
+def test_shortley_weller_exact_for_quadratics(dim, ramp):
     """SW (Section 3) is exact for quadratics in z on non-uniform complex widths, the
     turning points included: for u = prod_a (z_a - zlo_a)(z_a - zhi_a) (zero on the
-    Dirichlet ends), H u = -Laplacian u - k^2 u exactly."""
+    Dirichlet ends), H u = -Laplacian u - k^2 u exactly -- on the sharp contour and on the
+    smooth one, whose node positions are built independently above."""
     n_int, nl, theta, k0 = (11, 4, 0.5, 3.0) if dim < 3 else (7, 2, 0.5, 3.0)
     p = _prob(dim, n_int, nl, theta=theta, k0=k0)
+    p.ecs_ramp = ramp
     o = Oracle(p)
-    zs = [_node_z(n_int, (nl, nl), 1.0, theta) for _ in range(dim)]
+    zs = [_node_z(n_int, (nl, nl), 1.0, theta, ramp) for _ in range(dim)]
     q = [(z - zlo) * (z - zhi) for (z, zlo, zhi) in zs]  # per-axis quadratic, q'' = 2
 
     def outer(vs):
@@ -122,10 +132,12 @@ def test_shortley_weller_exact_for_quadratics(dim):
     assert np.abs(o.apply(u) - expect).max() <= 1e-10 * np.abs(expect).max()
 
 
-def test_weighted_operator_is_complex_symmetric():
+@pytest.mark.parametrize("ramp", [0, 3])
+def test_weighted_operator_is_complex_symmetric(ramp):
     """With w_j = (g_j + g_{j+1}) / 2 per axis, W H is complex symmetric (transpose, not
     adjoint): x^T W H y = y^T W H x."""
     p = _prob(2, 9, (2, 3), theta=0.5, k0=4.0)
+    p.ecs_ramp = ramp
     o = Oracle(p)
     w = []
     for a in range(2):
@@ -237,6 +249,33 @@ def test_outgoing_wave_through_layers_1d():
     lay = np.abs(u[nl + n_int: nl + n_int + 20])
     ratios = lay[1:] / lay[:-1]
     assert np.all(np.abs(ratios - abs(eta)) < 0.02)
+
+
+def test_smooth_contour_reduces_turning_point_reflection():
+    """Section 7 remark (smooth ECS transition): turning the contour gradually keeps the layer
+    absorbing while the reflection of the outgoing wave at the turning point falls with the
+    ramp length (a slowly varying medium reflects less); a ramp of one width is the sharp
+    contour, bit for bit."""
+    n_int, nl, theta, kh = 201, 60, np.pi / 4, 0.3
+    h = 1.0 / (n_int - 1)
+    k = kh / h
+    xi = np.roots([1, -(2 - kh * kh), 1])
+    xi = xi[np.argmax(xi.imag)]
+    A = h * h * xi / (1 - xi * xi)
+    j0 = nl + (n_int - 1) // 2
+    j = np.arange(nl, nl + n_int)
+    free = A * xi ** np.abs(j - j0)
+    errs, sols = {}, {}
+    for R in (0, 1, 10, 20):
+        p = _prob(1, n_int, nl, theta=theta, k0=k, rhs="zero")
+        p.ecs_ramp = R
+        p.b[j0] = 1.0
+        u = Oracle(p).dense_solve(p.b)
+        sols[R] = u
+        errs[R] = np.abs(u[nl:nl + n_int] - free).max() / abs(A)
+        assert abs(u[0]) < 1e-4 * abs(A) and abs(u[-1]) < 1e-4 * abs(A)  # still absorbed
+    assert np.array_equal(sols[0], sols[1])
+    assert errs[10] < 0.5 * errs[0] and errs[20] < errs[10]
 
 
 @pytest.mark.parametrize("n_int,nl", [(8, 2), (12, 3), (16, 0)])
