@@ -59,13 +59,18 @@ enum { HELM_BICGSTAB = 0, HELM_IDR = 1 };
  * interior holds n_int[a] nodes at 0, h, ..., extent[a] (h = extent/(n_int-1)); a side with
  * n_layer[a][side] = m > 0 continues with m ECS nodes of width h e^{i theta_gamma} and a
  * Dirichlet node after them; a side with m = 0 is a Dirichlet wall (its end node is not an
- * unknown).  Unknowns per axis: n_int - 2 + (m_lo ? m_lo + 1 : 0) + (m_hi ? m_hi + 1 : 0). */
+ * unknown).  Unknowns per axis: n_int - 2 + (m_lo ? m_lo + 1 : 0) + (m_hi ? m_hi + 1 : 0).
+ * ecs_ramp = R > 1 replaces the sharp turn by a gradual one (the smooth ECS transition of the
+ * paper's remark in Section 7): the m-th layer width counted from the turning point (m = 1, 2,
+ * ...) is h e^{i theta_gamma min(m, R) / R}, so the contour turns by theta_gamma / R per width over
+ * the first R widths; R = 0 or 1 is the sharp contour. */
 typedef struct {
   int dim;              /* 1, 2 or 3 */
   int n_int[3];         /* >= 2 (>= 3 for a side without layer); unused axes ignored */
   int n_layer[3][2];    /* >= 0 */
   double extent[3];     /* > 0 */
   double theta_gamma;   /* ECS angle in radians, 0 <= theta_gamma < pi/2 */
+  int ecs_ramp;         /* 0..1048576 */
 } helm_grid;
 
 /* Wave number: phi = k(x)^2 at the real node positions (the layers continue the real

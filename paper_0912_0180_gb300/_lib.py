@@ -18,7 +18,8 @@ HELM_SERVE_FIFO, HELM_SERVE_SMALLEST_FIRST = 0, 1
 
 class Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_int", C.c_int * 3), ("n_layer", (C.c_int * 2) * 3),
-                ("extent", C.c_double * 3), ("theta_gamma", C.c_double)]
+                ("extent", C.c_double * 3), ("theta_gamma", C.c_double),
+                ("ecs_ramp", C.c_int)]
 
 
 class KSpec(C.Structure):

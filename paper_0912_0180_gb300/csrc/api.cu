@@ -48,6 +48,7 @@ static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 static helm_status check_grid(const helm_grid* g) {
   if (!g || g->dim < 1 || g->dim > 3) { set_error("grid.dim must be 1, 2 or 3"); return HELM_ERR_ARG; }
   if (!(g->theta_gamma >= 0.0 && g->theta_gamma < M_PI / 2)) { set_error("theta_gamma out of [0, pi/2)"); return HELM_ERR_ARG; }
+  if (g->ecs_ramp < 0 || g->ecs_ramp > (1 << 20)) { set_error("ecs_ramp out of [0, 2^20]"); return HELM_ERR_ARG; }
   long total = 1;
   for (int a = 0; a < g->dim; ++a) {
     int lo = g->n_layer[a][0], hi = g->n_layer[a][1];

@@ -15,14 +15,24 @@
 
 namespace helm {
 
-// One thread per width: layer widths (first nlo and last nhi) are h e^{i theta} * scale_ly,
-// interior widths h * scale_in.
+// One thread per width: interior widths are h * scale_in; layer widths (the first nlo and the
+// last ones) are h e^{i theta_gamma} * scale_ly, except, with a ramp of R > 1 widths, the m-th
+// layer width from the turning point for m < R, which turns by only theta_gamma * m / R.
 __global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_layer,
-                            double2 w_int) {
+                            double2 w_int, int ramp, double h, double theta_g, double2 scale_ly) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ngap) return;
-  bool interior = (j >= nlo) && (j < nlo + nin);
-  gap[j] = interior ? w_int : w_layer;
+  if (j >= nlo && j < nlo + nin) {
+    gap[j] = w_int;
+    return;
+  }
+  int m = j < nlo ? nlo - j : j - (nlo + nin) + 1;  // 1 = the width next to the turning point
+  if (ramp > 1 && m < ramp) {
+    double th = theta_g * m / ramp;
+    gap[j] = cmul<double>(mkc<double>(h * cos(th), h * sin(th)), scale_ly);
+  } else {
+    gap[j] = w_layer;
+  }
 }
 
 // coarse width c = fine widths 2c and 2c+1; the last coarse width reaches the fine Dirichlet
@@ -410,7 +420,8 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
       if ((s = ctx_alloc(c, (void**)&L.coef64[a][k], sizeof(double2) * n)) != HELM_OK) return s;
       if (want32 && (s = ctx_alloc(c, (void**)&L.coef32[a][k], sizeof(float2) * n)) != HELM_OK) return s;
     }
-    k_axis_gaps<<<ceil_div(ngap, 256), 256, 0, st>>>(L.gap[a], ngap, nlo, nin, wl, wi);
+    k_axis_gaps<<<ceil_div(ngap, 256), 256, 0, st>>>(L.gap[a], ngap, nlo, nin, wl, wi, g.ecs_ramp, h,
+                                                     g.theta_gamma, scale_ly);
     k_axis_coeffs<<<ceil_div(n, 256), 256, 0, st>>>(L.gap[a], n, L.coef64[a][0], L.coef64[a][1],
                                                     L.coef64[a][2], L.coef32[a][0], L.coef32[a][1],
                                                     L.coef32[a][2]);

@@ -67,6 +67,7 @@ class Helm:
             g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
             g.extent[a] = problem.extent[a]
         g.theta_gamma = problem.theta_gamma
+        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
         k = L.KSpec()
         k.k0 = problem.k0
         self._phi = None
@@ -211,6 +212,7 @@ class Server:
             g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
             g.extent[a] = problem.extent[a]
         g.theta_gamma = problem.theta_gamma
+        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
         rq.k.k0 = problem.k0
         phi = None
         if problem.phi is not None:
