@@ -3,4 +3,4 @@
 Only the test suite, the package smoke check and the benchmark's CPU-baseline leg use this
 package.  It shares no code with the CUDA library.
 """
-from .oracle import Oracle, build_oracle, lib_path  # noqa: F401
+from .oracle import Oracle, build_oracle, lib_path, select_precond  # noqa: F401

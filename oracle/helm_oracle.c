@@ -881,3 +881,71 @@ int orc_solve(const orc_ctx* c, const cplx* b, cplx* x, const orc_solve_opts* o,
   free(r); free(P);
   return st;
 }
+
+/* ---- choosing the CSL shift / CSG angle (Section 7, remark on choosing the parameters) --- */
+
+/* Multigrid as a stationary solver of M u = f (M = the preconditioner's finest operator) from
+ * u = 0: each cycle u <- u + V(f - M u).  Returns the number of cycles after which
+ * ||f - M u|| <= reduction ||f|| (0 when f = 0), or -1 when that does not happen within
+ * max_cycles, or the residual grows past 1e6 ||f|| or stops being finite.  hist[k-1] (if
+ * given) receives ||f - M u|| / ||f|| after cycle k, for the cycles run. */
+int orc_mg_iterate(const orc_ctx* c, const cplx* f, int max_cycles, double reduction, cplx* u,
+                   double* hist) {
+  long n = c->H.ntot;
+  memset(u, 0, sizeof(cplx) * n);
+  if (c->pc.kind == 0) return -1;
+  double fn = nrm2(f, n);
+  if (fn == 0) return 0;
+  cplx* r = malloc(sizeof(cplx) * n);
+  cplx* z = malloc(sizeof(cplx) * n);
+  memcpy(r, f, sizeof(cplx) * n);
+  int result = -1;
+  for (int k = 1; k <= max_cycles; ++k) {
+    vcycle_rec(c, 0, r, z);
+    for (long i = 0; i < n; ++i) u[i] += z[i];
+    level_apply(&c->M[0], u, r);
+    for (long i = 0; i < n; ++i) r[i] = f[i] - r[i];
+    double rel = nrm2(r, n) / fn;
+    if (hist) hist[k - 1] = rel;
+    if (rel <= reduction) { result = k; break; }
+    if (!(rel <= 1e6)) break; /* diverging or not finite */
+  }
+  free(r); free(z);
+  return result;
+}
+
+/* From the starting preconditioner (CSL: its imaginary shift is the parameter; CSG: its angle
+ * theta_beta), the parameter is multiplied by `factor` (0 < factor < 1) from one trial to the
+ * next for as long as multigrid on the resulting M converges within max_cycles (orc_mg_iterate
+ * with right-hand side f); *out receives the last preconditioner that converged.  params[t] and
+ * cycles[t] record each trial (cycles -1 = did not converge).  Returns the number of trials run;
+ * *status = 0 when the start converged, else 5 and *out = the start. */
+int orc_select_precond(const orc_grid* g, const double* phi, double k0, const orc_precond* start,
+                       const cplx* f, int max_cycles, double reduction, double factor,
+                       int max_trials, orc_precond* out, double* params, int* cycles, int* status) {
+  *out = *start;
+  *status = 5;
+  long n = 1;
+  for (int d = 0; d < g->dim; ++d) {
+    int lo = g->n_layer[d][0], hi = g->n_layer[d][1];
+    n *= g->n_int[d] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+  }
+  cplx* u = malloc(sizeof(cplx) * n);
+  orc_precond pc = *start;
+  double p = start->kind == 1 ? start->shift_im : start->theta_beta;
+  int t = 0;
+  for (; t < max_trials; ++t) {
+    if (t > 0) p *= factor;
+    if (pc.kind == 1) pc.shift_im = p; else pc.theta_beta = p;
+    orc_ctx* c = orc_create(g, phi, k0, &pc);
+    int k = orc_mg_iterate(c, f, max_cycles, reduction, u, NULL);
+    orc_destroy(c);
+    params[t] = p;
+    cycles[t] = k;
+    if (k < 0) { ++t; break; }
+    *out = pc;
+    *status = 0;
+  }
+  free(u);
+  return t;
+}

@@ -82,6 +82,11 @@ def _load():
         lib.orc_dense_solve.restype = ip
         lib.orc_solve.argtypes = [vp, vp, vp, C.POINTER(_Opts), vp, C.POINTER(_Info), vp, ip]
         lib.orc_solve.restype = ip
+        lib.orc_mg_iterate.argtypes = [vp, vp, ip, dp, vp, vp]
+        lib.orc_mg_iterate.restype = ip
+        lib.orc_select_precond.argtypes = [C.POINTER(_Grid), vp, dp, C.POINTER(_Precond), vp, ip, dp, dp, ip,
+                                           C.POINTER(_Precond), vp, vp, C.POINTER(C.c_int)]
+        lib.orc_select_precond.restype = ip
         _lib = lib
     return _lib
 
@@ -92,6 +97,45 @@ def _c128(a) -> np.ndarray:
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def _grid(problem) -> "_Grid":
+    g = _Grid()
+    g.dim = problem.dim
+    for a in range(3):
+        g.n_int[a] = problem.n_int[a]
+        g.n_layer[a][0] = problem.n_layer[a][0]
+        g.n_layer[a][1] = problem.n_layer[a][1]
+        g.extent[a] = problem.extent[a]
+    g.theta_gamma = problem.theta_gamma
+    g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
+    return g
+
+
+def _precond(pc) -> "_Precond":
+    return _Precond(pc.kind, pc.theta_beta, complex(pc.shift).real, complex(pc.shift).imag,
+                    pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max,
+                    1 if getattr(pc, "galerkin", False) else 0)
+
+
+def select_precond(problem, start, f, max_cycles=20, reduction=1e-6, factor=0.8, max_trials=16):
+    """The parameter choice of Section 7's remark (orc_select_precond): returns the chosen
+    parameter (CSL imaginary shift or CSG angle), the status (0 = the start converged) and, per
+    trial, the parameter and the multigrid cycles it needed (-1 = did not converge)."""
+    lib = _load()
+    g = _grid(problem)
+    p = _precond(start)
+    phi = None if problem.phi is None else np.ascontiguousarray(problem.phi, dtype=np.float64)
+    f = _c128(f)
+    out = _Precond()
+    params = np.zeros(max_trials, np.float64)
+    cycles = np.zeros(max_trials, np.int32)
+    status = C.c_int(0)
+    t = lib.orc_select_precond(C.byref(g), _ptr(phi) if phi is not None else None, problem.k0, C.byref(p),
+                               _ptr(f), max_cycles, reduction, factor, max_trials, C.byref(out),
+                               _ptr(params), _ptr(cycles), C.byref(status))
+    chosen = out.shift_im if start.kind == 1 else out.theta_beta
+    return chosen, status.value, params[:t].copy(), cycles[:t].copy()
 
 
 class Oracle:
@@ -105,18 +149,8 @@ class Oracle:
         self.problem = problem
         pc = precond if precond is not None else Precond(kind=PC_NONE)
         self.precond = pc
-        g = _Grid()
-        g.dim = problem.dim
-        for a in range(3):
-            g.n_int[a] = problem.n_int[a]
-            g.n_layer[a][0] = problem.n_layer[a][0]
-            g.n_layer[a][1] = problem.n_layer[a][1]
-            g.extent[a] = problem.extent[a]
-        g.theta_gamma = problem.theta_gamma
-        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
-        p = _Precond(pc.kind, pc.theta_beta, complex(pc.shift).real, complex(pc.shift).imag,
-                     pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max,
-                     1 if getattr(pc, "galerkin", False) else 0)
+        g = _grid(problem)
+        p = _precond(pc)
         self._phi = None
         if problem.phi is not None:
             self._phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
@@ -201,6 +235,16 @@ class Oracle:
         z = np.empty_like(f)
         _lib.orc_coarse_solve(self._h, _ptr(f), _ptr(z))
         return z
+
+    def mg_iterate(self, f, max_cycles, reduction):
+        """Multigrid as a stationary solver of M u = f from u = 0 (orc_mg_iterate): returns
+        (cycles or -1, u, residual history)."""
+        f = _c128(f)
+        u = np.empty(self.n, np.complex128)
+        hist = np.zeros(max_cycles, np.float64)
+        k = _lib.orc_mg_iterate(self._h, _ptr(f), max_cycles, reduction, _ptr(u), _ptr(hist))
+        ran = k if k > 0 else int(np.count_nonzero(hist))
+        return k, u, hist[:ran].copy()
 
     def dense_solve(self, b):
         b = _c128(b)

@@ -3,6 +3,7 @@
 None of these checks re-types the oracle's formulas: each compares it with a closed form,
 an invariant, a value the paper prints, a textbook special case or a library routine.
 """
+import dataclasses
 import os
 
 import numpy as np
@@ -598,3 +599,85 @@ def test_galerkin_laplacian_closed_form():
     assert np.allclose(mc[mid, mid - 1: mid + 2], [0.125, 0.75, 0.125], rtol=1e-14)
     C = o.dense(1, 1)
     assert np.allclose(C, np.kron(mc, ac) + np.kron(ac, mc), rtol=1e-12, atol=1e-9)
+
+
+# ---- choosing the preconditioner parameter (Section 7 remark) -------------------------------
+
+def _dense_vcycle(o, n):
+    """The V-cycle is linear (pinned above), so its matrix is its action on unit vectors."""
+    V = np.zeros((n, n), np.complex128)
+    for j in range(n):
+        e = np.zeros(n, np.complex128)
+        e[j] = 1.0
+        V[:, j] = o.vcycle(e)
+    return V
+
+
+def _cycles_by_error_propagation(o, f, max_cycles, reduction):
+    """Brute force: u_k = u_{k-1} + V (f - M u_{k-1}) gives f - M u_k = (I - M V)^k f."""
+    n = len(f)
+    E = np.eye(n) - o.dense(1, 0) @ _dense_vcycle(o, n)
+    r, fn, hist = f.copy(), np.linalg.norm(f), []
+    for k in range(1, max_cycles + 1):
+        r = E @ r
+        hist.append(np.linalg.norm(r) / fn)
+        if hist[-1] <= reduction:
+            return k, np.asarray(hist)
+        if not hist[-1] <= 1e6:
+            break
+    return -1, np.asarray(hist)
+
+
+def test_mg_iteration_reaches_the_preconditioner_solution():
+    """Multigrid run as a solver of M u = f (the selection routine's inner loop) converges to
+    the dense solution of M u = f, and its residuals are (I - M V)^k f."""
+    p = _prob(2, 12, 3, theta=0.5, k0=4.0)
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    f = hi.random_vector(p.n, 21)
+    k, u, hist = o.mg_iterate(f, 80, 1e-10)
+    assert k > 0
+    ref = np.linalg.solve(o.dense(1, 0), f)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-8
+    kb, hb = _cycles_by_error_propagation(o, f, 80, 1e-10)
+    assert kb == k
+    assert np.allclose(hist, hb, rtol=1e-7, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [hi.PC_CSL, hi.PC_CSG_UNIFORM])
+def test_select_precond_picks_the_last_converging_parameter(kind):
+    """Section 7 remark: the parameter is reduced (x factor per trial) while multigrid on M still
+    converges within max_cycles; each trial's cycle count is checked by brute force and the
+    choice against the rule.  The start is chosen so that the sequence ends in a failure."""
+    from oracle import select_precond
+    p = _prob(2, 20, 4, theta=0.5, k0=8.0)
+    f = hi.random_vector(p.n, 22)
+    if kind == hi.PC_CSL:
+        start = hi.Precond(kind=kind, shift=1 + 1.2j, smoother=hi.SM_RBGS)
+    else:
+        start = hi.Precond(kind=kind, theta_beta=0.9, smoother=hi.SM_RBGS)
+    max_cycles, red, factor = 12, 1e-6, 0.7
+    chosen, status, params, cycles = select_precond(p, start, f, max_cycles, red, factor, 12)
+    assert status == 0 and cycles[0] > 0
+    assert cycles[-1] == -1, "the start should be large enough for the sequence to end in a failure"
+    expect = start.shift.imag if kind == hi.PC_CSL else start.theta_beta
+    for t, (pt, ct) in enumerate(zip(params, cycles)):
+        assert pt == expect
+        expect *= factor
+        pc = dataclasses.replace(start, shift=complex(start.shift.real, pt)) if kind == hi.PC_CSL else \
+            dataclasses.replace(start, theta_beta=pt)
+        kb, _ = _cycles_by_error_propagation(Oracle(p, pc), f, max_cycles, red)
+        assert kb == ct
+    assert chosen == params[-2]
+
+
+def test_select_precond_on_the_laplacian_never_fails():
+    """k = 0: multigrid contracts on the ECS Laplacian for every angle (pinned above), so every
+    trial converges and the smallest parameter tried is chosen."""
+    from oracle import select_precond
+    p = _prob(2, 14, 3, theta=0.5, k0=0.0)
+    f = hi.random_vector(p.n, 23)
+    start = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.5, smoother=hi.SM_RBGS)
+    chosen, status, params, cycles = select_precond(p, start, f, 20, 1e-6, 0.5, 6)
+    assert status == 0 and len(params) == 6 and np.all(cycles > 0)
+    assert chosen == params[-1] == 0.5 * 0.5 ** 5
