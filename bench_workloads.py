@@ -74,7 +74,7 @@ def run(args):
     g.build()
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
-    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp3": run_mp}[args.workload]
+    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp}[args.workload]
     line = fn(args, torch, ranks, dev, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -420,6 +420,10 @@ MP_CASES = {
     "mp2": {"problem": lambda: hi.workload_mp2(), "csl": 1 + 0.34j, "csg": np.pi / 20,
             "paper_matvecs": {"csl": {"bicgstab": 71, "idr4": 72, "idr8": 74},
                               "csg": {"bicgstab": 68, "idr4": 73, "idr8": 69}}},
+    # MP2 on the smooth contour of the Section 7 remark, turning over the whole 128-node layer
+    "mp2s": {"problem": lambda: hi.workload_mp2(ecs_ramp=128), "csl": 1 + 0.34j, "csg": np.pi / 20,
+             "paper_matvecs": {"csl": {"bicgstab": 71, "idr4": 72, "idr8": 74},
+                               "csg": {"bicgstab": 68, "idr4": 73, "idr8": 69}}},
     "mp3": {"problem": lambda: hi.workload_mp3(), "csl": 1 + 0.38j, "csg": np.pi / 17,
             "paper_matvecs": {"csl": {"bicgstab": 142, "idr4": 145, "idr8": 141},
                               "csg": {"bicgstab": 139, "idr4": 139, "idr8": 134}}},

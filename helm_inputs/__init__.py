@@ -197,13 +197,16 @@ def workload_3d_128(seed: int = BASE_SEED) -> Problem:
 
 
 def workload_mp2(nu: float = 7.0, k: float = 2.0, n_int: int = 385, n_l: int = 128, r: float = 50.0,
-                 theta_gamma: float = np.pi / 6) -> Problem:
+                 theta_gamma: float = np.pi / 6, ecs_ramp: int = 0) -> Problem:
     """The paper's model problem 2 (Section 4, eq. "MP2"): phi = nu (e^{-x^2} + e^{-y^2}) + k^2,
     source chi = e^{-(x^2 + y^2)} on [0, r]^2, Dirichlet on the south / west edges (x = 0, y = 0) and
     ECS layers of n_l nodes on the east / north edges.  Defaults: the paper's 384^2 interior grid
-    with 128 layer nodes (512^2 unknowns)."""
+    with 128 layer nodes (512^2 unknowns).  ecs_ramp > 1 turns the contour gradually (Section 7's
+    smooth ECS transition)."""
+    tag = f"-ramp{ecs_ramp}" if ecs_ramp > 1 else ""
     return make_problem(2, n_int, ((0, n_l), (0, n_l)), extent=r, theta_gamma=theta_gamma, k0=k,
-                        phi_kind="field", rhs="field", name=f"mp2-nu{nu:g}-k{k:g}-{n_int - 1}sq-L{n_l}",
+                        ecs_ramp=ecs_ramp,
+                        phi_kind="field", rhs="field", name=f"mp2-nu{nu:g}-k{k:g}-{n_int - 1}sq-L{n_l}{tag}",
                         phi_fn=lambda x, y: nu * (np.exp(-x * x) + np.exp(-y * y)) + k * k,
                         rhs_fn=lambda x, y: np.exp(-(x * x + y * y)))
 

@@ -295,6 +295,33 @@ void helm_server_destroy(helm_server* s);
 helm_status helm_residual_noalloc(helm_ctx* ctx, const void* b, const void* x, void* r,
                                   double* rel_out, void* stream);
 
+/* Multigrid as a stationary solver of the preconditioner's own equation M u = f (M = the
+ * finest preconditioner operator; Section 7, remark on choosing the CSL and CSG parameters):
+ * from u = 0, each cycle sets u <- u + V(f - M u) with one V-cycle V.  *cycles receives the
+ * number of cycles after which ||f - M u|| <= reduction ||f|| (0 when f = 0), or -1 when that
+ * does not happen within max_cycles or the ratio exceeds 1e6 or stops being finite.  hist
+ * (HOST, optional, max_cycles doubles) receives ||f - M u|| / ||f|| after each cycle run.
+ * f and u are complex128 DEVICE vectors of N (16-byte aligned, not aliased); the context needs a
+ * CSL or CSG preconditioner with an FP64 hierarchy (mg_dtype HELM_C128), else HELM_ERR_ARG.
+ * Allocates 2 N complex128 of scratch on `stream` and synchronises it once per cycle. */
+helm_status helm_mg_iterate(helm_ctx* ctx, const void* f, void* u, int max_cycles, double reduction,
+                            int* cycles, double* hist, void* stream);
+
+/* The automatic parameter choice of the same remark.  The parameter is the imaginary part of
+ * the CSL shift (start->kind HELM_PC_CSL) or the CSG angle theta_beta (the CSG kinds).  Trial t
+ * uses the parameter p_t = p_{t-1} * factor (p_0 = the start's, one multiplication per trial),
+ * builds the hierarchy with it in FP64 and runs helm_mg_iterate with right-hand side f (complex128
+ * DEVICE vector of N, seeded by the caller); trials continue while multigrid converges within
+ * max_cycles, up to max_trials (1..64).  *out = the start with the last converging parameter;
+ * params / cycles (HOST, optional, max_trials entries) record each trial's parameter and cycle
+ * count (-1 = did not converge); *trials = trials run.  Returns HELM_ERR_MAXIT (and *out = the
+ * start) when the start itself does not converge, HELM_ERR_ARG for factor outside (0, 1) or an
+ * identity preconditioner, or the error of helm_create. */
+helm_status helm_select_precond(const helm_grid* grid, const helm_kspec* k, const helm_precond* start,
+                                const void* f, int max_cycles, double reduction, double factor,
+                                int max_trials, helm_precond* out, double* params, int* cycles,
+                                int* trials, void* stream);
+
 /* Releases everything the context holds (synchronises the device first).  NULL is a no-op. */
 void helm_destroy(helm_ctx* ctx);
 

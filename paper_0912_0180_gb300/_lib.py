@@ -99,6 +99,12 @@ def load() -> C.CDLL:
     lib.helm_server_destroy.restype = None
     lib.helm_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.helm_residual_noalloc.restype = ip
+    dp = C.c_double
+    lib.helm_mg_iterate.argtypes = [vp, vp, vp, ip, dp, C.POINTER(ip), vp, vp]
+    lib.helm_mg_iterate.restype = ip
+    lib.helm_select_precond.argtypes = [C.POINTER(Grid), C.POINTER(KSpec), C.POINTER(Precond), vp, ip, dp, dp, ip,
+                                        C.POINTER(Precond), vp, vp, C.POINTER(ip), vp]
+    lib.helm_select_precond.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_status_str.argtypes = [ip]

@@ -49,6 +49,37 @@ class Info:
     history: Optional[np.ndarray] = None
 
 
+def _grid(problem) -> "L.Grid":
+    g = L.Grid()
+    g.dim = problem.dim
+    for a in range(3):
+        g.n_int[a] = problem.n_int[a]
+        g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
+        g.extent[a] = problem.extent[a]
+    g.theta_gamma = problem.theta_gamma
+    g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
+    return g
+
+
+def _kspec(problem):
+    """The k specification and the host array it points to (keep it alive while in use)."""
+    k = L.KSpec()
+    k.k0 = problem.k0
+    phi = None
+    if problem.phi is not None:
+        phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
+        k.phi = phi.ctypes.data
+    return k, phi
+
+
+def _precond(precond, mg_dtype: str = "c64", flags: int = 0) -> "L.Precond":
+    return L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
+                     complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
+                     precond.omega, precond.max_levels, precond.coarse_max,
+                     L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
+                     flags | (L.HELM_PF_GALERKIN if getattr(precond, "galerkin", False) else 0))
+
+
 class Helm:
     """One instance: grid, ECS layers, k(x), the FP64 operator H and a preconditioner hierarchy.
 
@@ -60,27 +91,10 @@ class Helm:
                  pdl: bool = True, autotune: bool = True):
         lib = L.load()
         self._lib = lib
-        g = L.Grid()
-        g.dim = problem.dim
-        for a in range(3):
-            g.n_int[a] = problem.n_int[a]
-            g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
-            g.extent[a] = problem.extent[a]
-        g.theta_gamma = problem.theta_gamma
-        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
-        k = L.KSpec()
-        k.k0 = problem.k0
-        self._phi = None
-        if problem.phi is not None:
-            self._phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
-            k.phi = self._phi.ctypes.data
-        pc = L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
-                       complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
-                       precond.omega, precond.max_levels, precond.coarse_max,
-                       L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
-                       (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL)
-                       | (0 if autotune else L.HELM_PF_NO_AUTOTUNE)
-                       | (L.HELM_PF_GALERKIN if getattr(precond, "galerkin", False) else 0))
+        g = _grid(problem)
+        k, self._phi = _kspec(problem)
+        pc = _precond(precond, mg_dtype, (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL)
+                      | (0 if autotune else L.HELM_PF_NO_AUTOTUNE))
         h = C.c_void_p()
         _check(lib.helm_create(C.byref(g), C.byref(k), C.byref(pc), C.c_void_p(_stream(stream)), C.byref(h)),
                "helm_create")
@@ -130,6 +144,17 @@ class Helm:
         _check(self._lib.helm_level_op(self._h, op, lvl, _ptr(a), _ptr(b), _ptr(out), count,
                                        C.c_void_p(_stream(stream))), "helm_level_op")
         return out
+
+    def mg_iterate(self, f: torch.Tensor, max_cycles: int = 20, reduction: float = 1e-6, stream=None):
+        """Multigrid as a stationary solver of M u = f (helm_mg_iterate; FP64 hierarchy): returns
+        (cycles or -1, u, per-cycle residual ratios)."""
+        u = torch.empty_like(f)
+        k = C.c_int(-1)
+        hist = np.zeros(max_cycles, np.float64)
+        _check(self._lib.helm_mg_iterate(self._h, _ptr(f), _ptr(u), max_cycles, reduction, C.byref(k),
+                                         hist.ctypes.data, C.c_void_p(_stream(stream))), "helm_mg_iterate")
+        ran = k.value if k.value > 0 else int(np.count_nonzero(hist))
+        return k.value, u, hist[:ran].copy()
 
     def solve(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, *, method: int = 0, s: int = 4,
               tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3,
@@ -263,6 +288,32 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def select_precond(problem, start, f: torch.Tensor, max_cycles: int = 20, reduction: float = 1e-6,
+                   factor: float = 0.8, max_trials: int = 16, stream=None):
+    """Automatic CSL shift / CSG angle (helm_select_precond): returns (the chosen preconditioner
+    as a helm_inputs.Precond, status, per-trial parameters, per-trial cycles)."""
+    import dataclasses
+    lib = L.load()
+    g = _grid(problem)
+    k, phi = _kspec(problem)
+    pc = _precond(start, "c128")
+    out = L.Precond()
+    params = np.zeros(max_trials, np.float64)
+    cycles = np.zeros(max_trials, np.int32)
+    trials = C.c_int(0)
+    st = lib.helm_select_precond(C.byref(g), C.byref(k), C.byref(pc), _ptr(f), max_cycles, reduction, factor,
+                                 max_trials, C.byref(out), params.ctypes.data, cycles.ctypes.data, C.byref(trials),
+                                 C.c_void_p(_stream(stream)))
+    _check(st, "helm_select_precond", ok=(L.HELM_OK, L.HELM_ERR_MAXIT))
+    del phi
+    if start.kind == 1:  # HELM_PC_CSL: the parameter is the imaginary shift
+        chosen = dataclasses.replace(start, shift=complex(complex(start.shift).real, out.shift_im))
+    else:
+        chosen = dataclasses.replace(start, theta_beta=out.theta_beta)
+    t = trials.value
+    return chosen, st, params[:t].copy(), cycles[:t].copy()
 
 
 def estimate_bytes(problem, precond, mg_dtype: str = "c64", method: int = 0, s: int = 4) -> int:

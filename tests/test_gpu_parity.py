@@ -528,3 +528,45 @@ def test_galerkin_solve_matches_oracle():
     with pytest.raises(Exception):  # Galerkin levels need the Jacobi smoother
         Helm(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_RBGS, galerkin=True))
     h.close()
+
+
+RAMP_CASES = [
+    # dim, n_int, layers, ramp, k0, phi kind
+    (2, (45, 38), ((12, 9), (0, 10)), 6, 14.0, "bump"),
+    (2, 64, 16, 16, 20.0, "const"),
+    (3, (14, 11, 12), ((4, 3), (0, 5), (3, 4)), 3, 6.0, "bump"),
+]
+
+
+@pytest.mark.parametrize("case", RAMP_CASES)
+def test_smooth_contour_parity(case):
+    """The smooth ECS contour (layer widths turning over `ramp` widths): the FP64 operator, every
+    level's operator and the V-cycle in both precisions, and an FP64 solve, against the oracle."""
+    dim, n_int, nl, ramp, k0, kind = case
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=k0, phi_kind=kind, rhs="gauss", seed=17,
+                        bump_centre=(0.4, 0.6, 0.5), ecs_ramp=ramp)
+    x = hi.random_vector(p.n, 8)
+    for mg in ("c128", "c64"):
+        pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3,
+                        smoother=hi.SM_RBGS if dim == 3 else hi.SM_JACOBI)
+        o = Oracle(p, pc)
+        h = Helm(p, pc, mg_dtype=mg)
+        assert h.nlev == o.nlev
+        if mg == "c128":
+            assert rel(h.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+        dt = torch.complex128 if mg == "c128" else torch.complex64
+        for lvl in range(o.nlev - 1):
+            n = o.level_size(1, lvl)
+            a = hi.random_vector(n, 9 + lvl).astype(np.complex64).astype(np.complex128)
+            out = torch.empty(n, dtype=dt, device="cuda")
+            h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
+            assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < (1e-12 if mg == "c128" else 2e-5)
+        z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
+        assert rel(z, o.vcycle(x)) < (1e-11 if mg == "c128" else 2e-5)
+        if mg == "c128":
+            xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=2000)
+            xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=2000))
+            assert info.status == 0 and io["status"] == 0
+            assert abs(info.matvecs - io["matvecs"]) <= 2
+            assert rel(xs.cpu().numpy(), xo) < 1e-9
+        h.close()
