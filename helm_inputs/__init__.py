@@ -26,7 +26,7 @@ BASE_SEED = 20091201
 # Preconditioner kinds and solver codes, mirrored by both the C-ABI and the oracle.
 PC_NONE, PC_CSL, PC_CSG_UNIFORM, PC_CSG_INTERIOR = 0, 1, 2, 3
 SM_JACOBI, SM_RBGS = 0, 1
-BICGSTAB, IDR = 0, 1
+BICGSTAB, IDR, GMRES = 0, 1, 2  # GMRES: SolveOpts.s is the restart length m
 
 
 @dataclasses.dataclass

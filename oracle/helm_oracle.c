@@ -62,8 +62,8 @@ typedef struct {
 } orc_precond;
 
 typedef struct {
-  int method;           /* 0 Bi-CGSTAB, 1 IDR(s) */
-  int s;                /* IDR shadow dimension */
+  int method;           /* 0 Bi-CGSTAB, 1 IDR(s), 2 GMRES(m) */
+  int s;                /* IDR shadow dimension; GMRES restart length m */
   double tol;           /* stop on ||r|| / ||b|| < tol */
   int maxmv;            /* cap on preconditioned matvecs */
   int max_restarts;     /* true-residual restarts allowed */
@@ -844,6 +844,106 @@ static void orthonormalise(cplx* P, int s, long n) {
   }
 }
 
+/* Right-preconditioned restarted GMRES(m) (Saad & Schultz; the paper's remark on testing GMRES
+ * in Section 7), from the current x with residual r = b - H x.  Each cycle builds an Arnoldi
+ * basis v_0 = r / ||r||, ..., orthogonalising w = H M^{-1} v_j against it by classical
+ * Gram-Schmidt applied twice (all inner products of a pass first, then one update), reduces the
+ * Hessenberg matrix by complex Givens rotations (the rotated right-hand side gives the residual
+ * norm |g_{j+1}| of the least-squares problem), and after m steps -- or when |g_{j+1}| / ||b||
+ * < tol -- sets x += M^{-1} (V y) with R y = g and recomputes r = b - H x.  One preconditioned
+ * matvec per Arnoldi step. */
+static int gmres_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
+                     const orc_solve_opts* o, orc_info* info, double* hist, int hist_cap) {
+  long n = c->H.ntot;
+  int m = o->s;
+  cplx* V = malloc(sizeof(cplx) * (size_t)(m + 1) * n);
+  cplx* Hs = calloc((size_t)(m + 1) * m, sizeof(cplx)); /* Hs[i + (m+1) j] */
+  double* cs = malloc(sizeof(double) * m);
+  cplx* sn = malloc(sizeof(cplx) * m);
+  cplx* g = malloc(sizeof(cplx) * (m + 1));
+  cplx* h = malloc(sizeof(cplx) * (m + 1));
+  cplx* y = malloc(sizeof(cplx) * m);
+  cplx *z = malloc(sizeof(cplx) * n), *w = malloc(sizeof(cplx) * n);
+  int st = ST_MAXMV;
+  for (;;) {
+    double beta = nrm2(r, n);
+    if (!isfinite(beta)) { st = ST_NAN; break; }
+    if (beta / bn < o->tol) { st = ST_OK; break; }
+    if (info->matvecs >= o->maxmv) { st = ST_MAXMV; break; }
+    for (long i = 0; i < n; ++i) V[i] = r[i] / beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0;
+    g[0] = beta;
+    int k = 0, done = 0;
+    st = ST_MAXMV;
+    for (int j = 0; j < m; ++j) {
+      if (info->matvecs >= o->maxmv) { st = ST_MAXMV; done = 1; break; }
+      cplx* vj = V + (size_t)j * n;
+      orc_vcycle(c, vj, z);
+      level_apply(&c->H, z, w);
+      info->matvecs++;
+      info->iters++;
+      cplx* col = Hs + (size_t)(m + 1) * j;
+      for (int i = 0; i <= j; ++i) col[i] = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i <= j; ++i) h[i] = dotc(V + (size_t)i * n, w, n);
+        for (long q = 0; q < n; ++q) {
+          cplx acc = 0;
+          for (int i = 0; i <= j; ++i) acc += h[i] * V[(size_t)i * n + q];
+          w[q] -= acc;
+        }
+        for (int i = 0; i <= j; ++i) col[i] += h[i];
+      }
+      double hn = nrm2(w, n);
+      /* earlier rotations on the new column, then the one that annihilates hn */
+      for (int i = 0; i < j; ++i) {
+        cplx a = col[i], bb = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * bb;
+        col[i + 1] = -conj(sn[i]) * a + cs[i] * bb;
+      }
+      cplx a = col[j];
+      double aa = cabs(a);
+      if (hn == 0) { cs[j] = 1; sn[j] = 0; }
+      else if (aa == 0) { cs[j] = 0; sn[j] = 1; col[j] = hn; }
+      else {
+        double t = hypot(aa, hn);
+        cs[j] = aa / t;
+        sn[j] = (a / aa) * (hn / t);
+        col[j] = (a / aa) * t;
+      }
+      col[j + 1] = 0;
+      g[j + 1] = -conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      double est = cabs(g[j + 1]) / bn;
+      if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = est;
+      info->rel_res_recur = est;
+      if (!isfinite(est) || !isfinite(hn)) { st = ST_NAN; done = 1; break; }
+      if (est < o->tol || hn == 0) { st = ST_OK; done = 1; break; }
+      for (long q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+    }
+    /* x += M^{-1} V y, R y = g (upper triangular k x k) */
+    for (int i = k - 1; i >= 0; --i) {
+      cplx acc = g[i];
+      for (int l = i + 1; l < k; ++l) acc -= Hs[i + (size_t)(m + 1) * l] * y[l];
+      y[i] = acc / Hs[i + (size_t)(m + 1) * i];
+    }
+    if (k > 0) {
+      for (long q = 0; q < n; ++q) {
+        cplx acc = 0;
+        for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * n + q];
+        w[q] = acc;
+      }
+      orc_vcycle(c, w, z);
+      for (long q = 0; q < n; ++q) x[q] += z[q];
+    }
+    level_apply(&c->H, x, r);
+    for (long q = 0; q < n; ++q) r[q] = b[q] - r[q];
+    if (done) break;
+  }
+  free(V); free(Hs); free(cs); free(sn); free(g); free(h); free(y); free(z); free(w);
+  return st;
+}
+
 /* Full solve H x = b from x = 0 (the stopping rule of Section 6.2 is relative to d_0 = b),
  * then the true residual b - H x is recomputed; if it misses tol the method restarts from
  * the current x (at most max_restarts times).  shadow: s x n raw random vectors for IDR. */
@@ -856,6 +956,7 @@ int orc_solve(const orc_ctx* c, const cplx* b, cplx* x, const orc_solve_opts* o,
   if (!isfinite(bn)) { info->status = ST_NAN; return ST_NAN; }
   if (bn == 0) { info->status = ST_OK; return ST_OK; }
   if (o->method == 1 && (o->s < 1 || o->s > 64 || !shadow)) { info->status = 1; return 1; }
+  if (o->method == 2 && (o->s < 1 || o->s > 128)) { info->status = 1; return 1; }
   cplx* r = malloc(sizeof(cplx) * n);
   cplx* P = NULL;
   if (o->method == 1) {
@@ -867,7 +968,8 @@ int orc_solve(const orc_ctx* c, const cplx* b, cplx* x, const orc_solve_opts* o,
   int st;
   for (;;) {
     st = o->method == 0 ? bicgstab_run(c, b, x, r, bn, o, info, hist, hist_cap)
-                        : idr_run(c, b, x, r, bn, P, o, info, hist, hist_cap);
+       : o->method == 1 ? idr_run(c, b, x, r, bn, P, o, info, hist, hist_cap)
+                        : gmres_run(c, b, x, r, bn, o, info, hist, hist_cap);
     /* true residual */
     level_apply(&c->H, x, r);
     for (long i = 0; i < n; ++i) r[i] = b[i] - r[i];

@@ -681,3 +681,64 @@ def test_select_precond_on_the_laplacian_never_fails():
     chosen, status, params, cycles = select_precond(p, start, f, 20, 1e-6, 0.5, 6)
     assert status == 0 and len(params) == 6 and np.all(cycles > 0)
     assert chosen == params[-1] == 0.5 * 0.5 ** 5
+
+
+# ---- GMRES(m) (Section 7, remark on testing GMRES) ---------------------------------------------
+
+def _krylov_lsq_residuals(A, b, steps):
+    """min_y ||b - A K_j y|| / ||b|| over the Krylov space K_j = span{b, A b, ..., A^{j-1} b},
+    with the basis orthonormalised by numpy's QR -- the definition of the GMRES iterate."""
+    out, cols, v = [], [], b.copy()
+    for j in range(steps):
+        cols.append(v)
+        Q, _ = np.linalg.qr(np.stack(cols, axis=1))
+        AQ = A @ Q
+        y, *_ = np.linalg.lstsq(AQ, b, rcond=None)
+        out.append(np.linalg.norm(b - AQ @ y) / np.linalg.norm(b))
+        v = A @ Q[:, -1]
+    return np.asarray(out)
+
+
+def test_gmres_residuals_are_the_krylov_least_squares_minimum():
+    """Without a preconditioner each GMRES residual is the minimum over the Krylov space (by
+    definition), computed here by numpy least squares; the full method ends at the dense solution."""
+    p = _prob(2, 7, 1, theta=0.5, k0=5.0)
+    o = Oracle(p)
+    A = o.dense()
+    steps = 8
+    ref = _krylov_lsq_residuals(A, p.b, steps)
+    x, info = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=steps, tol=1e-300, maxmv=steps, max_restarts=0),
+                      history=True)
+    assert np.allclose(info["history"], ref, rtol=1e-8)
+    # full GMRES: an N-step Krylov space holds the solution
+    n = p.n
+    x, info = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=n, tol=1e-11, maxmv=n + 2, max_restarts=0))
+    assert info["status"] == 0 and info["matvecs"] <= n
+    xd = o.dense_solve(p.b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_right_preconditioned_gmres_minimises_over_the_preconditioned_space():
+    """With right preconditioning the residual after j steps is the minimum of ||b - H V y|| over
+    y in the Krylov space of H V (V = the V-cycle's matrix, from unit vectors); restarted GMRES
+    preconditioned by multigrid reaches the dense solution, and within a cycle the residual
+    never grows."""
+    p = _prob(2, 10, 2, theta=0.5, k0=6.0)
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    n = p.n
+    V = _dense_vcycle(o, n)
+    AV = o.dense() @ V
+    steps = 7
+    ref = _krylov_lsq_residuals(AV, p.b, steps)
+    _, info = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=steps, tol=1e-300, maxmv=steps, max_restarts=0),
+                      history=True)
+    assert np.allclose(info["history"], ref, rtol=1e-7)
+    x, info = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=5, tol=1e-10, maxmv=400), history=True)
+    assert info["status"] == 0 and info["rel_res_true"] < 1e-10
+    h = info["history"]
+    for c0 in range(0, len(h), 5):
+        cyc = h[c0:c0 + 5]
+        assert np.all(np.diff(cyc) <= 1e-12 * cyc[0])
+    xd = o.dense_solve(p.b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
