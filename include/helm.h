@@ -53,7 +53,9 @@ typedef enum { HELM_C64 = 0 /* complex float32 */, HELM_C128 = 1 /* complex floa
 
 enum { HELM_PC_NONE = 0, HELM_PC_CSL = 1, HELM_PC_CSG_UNIFORM = 2, HELM_PC_CSG_INTERIOR = 3 };
 enum { HELM_SM_JACOBI = 0, HELM_SM_RBGS = 1 };
-enum { HELM_BICGSTAB = 0, HELM_IDR = 1 };
+enum { HELM_BICGSTAB = 0, HELM_IDR = 1, HELM_GMRES = 2 };
+/* largest GMRES restart length (helm_solve_opts.s) */
+#define HELM_GMRES_MAX_M 128
 
 /* Grid of one instance (Section 3, eq. "ecsgrid", extended per axis).  Along axis a the
  * interior holds n_int[a] nodes at 0, h, ..., extent[a] (h = extent/(n_int-1)); a side with
@@ -129,10 +131,18 @@ enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4, HELM_PF
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
  * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;
- * if it misses tol the method restarts from x (at most max_restarts times). */
+ * if it misses tol the method restarts from x (at most max_restarts times).
+ * HELM_GMRES is restarted right-preconditioned GMRES(m) (the paper's remark on testing GMRES,
+ * Section 7), m = s: each Arnoldi step is one preconditioned matvec, orthogonalised against the
+ * basis by classical Gram-Schmidt applied twice; the residual norm of the least-squares problem
+ * (from complex Givens rotations) plays the recurrence residual.  A cycle ends at m steps, when
+ * that norm meets tol, or at maxmv; then x += M^{-1} V y and the true residual starts the next
+ * cycle.  Cycles continue until the true residual meets tol or maxmv is reached; only a cycle
+ * whose estimate met tol while the true residual did not counts against max_restarts.  Device
+ * memory: m + 1 basis vectors besides the common work vectors. */
 typedef struct {
-  int method;           /* HELM_BICGSTAB or HELM_IDR */
-  int s;                /* IDR shadow dimension, 1..8 */
+  int method;           /* HELM_BICGSTAB, HELM_IDR or HELM_GMRES */
+  int s;                /* IDR shadow dimension, 1..8; GMRES restart length m, 1..HELM_GMRES_MAX_M */
   double tol;           /* > 0 */
   int maxmv;            /* cap on preconditioned matvecs (V-cycle + H apply), >= 1 */
   int max_restarts;     /* >= 0 */
@@ -310,7 +320,7 @@ helm_status helm_mg_iterate(helm_ctx* ctx, const void* f, void* u, int max_cycle
 /* The automatic parameter choice of the same remark.  The parameter is the imaginary part of
  * the CSL shift (start->kind HELM_PC_CSL) or the CSG angle theta_beta (the CSG kinds).  Trial t
  * uses the parameter p_t = p_{t-1} * factor (p_0 = the start's, one multiplication per trial),
- * builds the hierarchy with it in FP64 and runs helm_mg_iterate with right-hand side f (complex128
+ * builds the hierarchy with it in FP64 (without the autotuner) and runs helm_mg_iterate with right-hand side f (complex128
  * DEVICE vector of N, seeded by the caller); trials continue while multigrid converges within
  * max_cycles, up to max_trials (1..64).  *out = the start with the last converging parameter;
  * params / cycles (HOST, optional, max_trials entries) record each trial's parameter and cycle

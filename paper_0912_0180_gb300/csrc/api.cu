@@ -222,8 +222,9 @@ helm_status helm_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, 
 static helm_status check_solve_args(const helm_ctx* c, const void* b, const void* x, const helm_solve_opts* o) {
   if (!c || !b || !x || !o || b == x) { set_error("helm_solve: NULL or aliased arguments"); return HELM_ERR_ARG; }
   if (!aligned(b, 16) || !aligned(x, 16)) { set_error("helm_solve: misaligned"); return HELM_ERR_ARG; }
-  if (o->method != HELM_BICGSTAB && o->method != HELM_IDR) { set_error("method"); return HELM_ERR_ARG; }
+  if (o->method != HELM_BICGSTAB && o->method != HELM_IDR && o->method != HELM_GMRES) { set_error("method"); return HELM_ERR_ARG; }
   if (o->method == HELM_IDR && (o->s < 1 || o->s > 8 || !o->shadow)) { set_error("IDR needs 1 <= s <= 8 and a shadow array"); return HELM_ERR_ARG; }
+  if (o->method == HELM_GMRES && (o->s < 1 || o->s > HELM_GMRES_MAX_M)) { set_error("GMRES needs 1 <= m <= HELM_GMRES_MAX_M"); return HELM_ERR_ARG; }
   if (!(o->tol > 0.0) || o->maxmv < 1 || o->max_restarts < 0) { set_error("tol / maxmv / max_restarts"); return HELM_ERR_ARG; }
   return HELM_OK;
 }

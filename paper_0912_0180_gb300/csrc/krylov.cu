@@ -1,5 +1,6 @@
 // krylov.cu -- right-preconditioned Bi-CGSTAB (van der Vorst 1992) and IDR(s) (Sonneveld &
-// van Gijzen 2008), the Krylov methods of Section 6.2, run entirely on the device.
+// van Gijzen 2008), the Krylov methods of Section 6.2, and restarted GMRES(m) (Saad & Schultz
+// 1986; the paper's remark on testing GMRES in Section 7), run entirely on the device.
 //
 // FP64 vectors and inner products; the V-cycle runs in the hierarchy's precision: the vector
 // entering it is written in that precision by the update kernel that produces it (fused
@@ -27,6 +28,7 @@ constexpr int KT = 256;      // threads per block of the vector kernels
 #endif
 constexpr int SMAX = 8;      // largest IDR shadow dimension
 constexpr int NRED = SMAX + 2;
+constexpr int GMRES_MMAX = HELM_GMRES_MAX_M;  // largest GMRES restart length
 
 struct KrylovState {
   double2 rho, rho_old, alpha, omega, beta;
@@ -38,6 +40,9 @@ struct KrylovState {
   double2 c[SMAX];         // IDR: M^{-1} m
   unsigned int ticket[8];  // last-block counters, one per reduction site
   double* hist;            // optional residual history (device), capacity maxmv
+  double hn;               // GMRES: norm of the last orthogonalised vector, h_{j+1,j}
+  int gmm;                 // GMRES: restart length m
+  double2* gm;             // GMRES: Hessenberg matrix, rotations, g, y and the two h passes
 };
 
 struct Workspace {
@@ -50,6 +55,8 @@ struct Workspace {
   void *pmg = nullptr, *smg = nullptr;  // V-cycle inputs in the multigrid precision
   double2 *ph = nullptr, *sh = nullptr; // V-cycle outputs, widened to complex128
   double2 *P = nullptr, *dR = nullptr, *dX = nullptr;                  // IDR, s vectors each
+  double2 *V = nullptr, *gm = nullptr;  // GMRES: m + 1 basis vectors; its small dense arrays
+  int nred = NRED;                      // partial-sum slots per block
   const void* shadow_key = nullptr;
   cudaGraphExec_t loop = nullptr;
   cudaGraphExec_t body = nullptr;       // host-driven loop: one iteration per launch
@@ -606,6 +613,255 @@ __global__ void k_mgs_upd(double2* __restrict__ pj, const double2* __restrict__ 
   }
 }
 
+// ---- GMRES(m) --------------------------------------------------------------------------------
+// One loop body is one Arnoldi step j = S->k: z = M^{-1} v_j (V-cycle), w = H z, two classical
+// Gram-Schmidt passes (all inner products v_i^H w first, then one update), h_{j+1,j} = ||w||,
+// the complex Givens rotations that keep the Hessenberg matrix triangular, and v_{j+1} = w / h.
+// The cycle ends (done) when the rotated right-hand side shows ||r|| / ||b|| < tol, at step m or
+// at the matvec cap; then y solves R y = g and x += M^{-1} (V y), and the pass's true residual
+// starts the next cycle.
+
+struct GmView {
+  double2 *Hs, *cs, *sn, *g, *y, *hA, *hB;  // Hs[i + (m+1) j]; cs holds reals in .x
+};
+__host__ __device__ inline GmView gm_view(double2* base, int m) {
+  GmView v;
+  v.Hs = base;
+  v.cs = v.Hs + (size_t)(m + 1) * m;
+  v.sn = v.cs + m;
+  v.g = v.sn + m;
+  v.y = v.g + m + 1;
+  v.hA = v.y + m;
+  v.hB = v.hA + m + 1;
+  return v;
+}
+inline size_t gm_elems(int m) { return (size_t)(m + 1) * m + 6 * (size_t)m + 3; }
+
+// Cycle start from r (first pass: r = b, whose norm sets the scale): beta = ||r||, g = (beta, 0..).
+__global__ void k_gm_start(KrylovState* S, const double2* __restrict__ b, double2* r, long n, int first,
+                           double2* partials) {
+  pdl_entry();
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(i, n) {
+    double2 ri = first ? b[i] : r[i];
+    if (first) r[i] = ri;
+    acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
+  }
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot)) return;
+  if (threadIdx.x) return;
+  double beta = sqrt(tot[0].x);
+  if (first) {
+    S->bnorm = beta;
+    S->matvecs = 0; S->iters = 0;
+  }
+  S->done = 0; S->half = 0; S->status = HELM_ERR_MAXIT;
+  S->k = 0; S->loops = 0;
+  S->beta = mkc<double>(beta, 0.0);
+  GmView G = gm_view(S->gm, S->gmm);
+  G.g[0] = mkc<double>(beta, 0.0);
+  for (int i = 1; i <= S->gmm; ++i) G.g[i] = mkc<double>(0.0, 0.0);
+  S->rel_recur = S->bnorm > 0.0 ? beta / S->bnorm : 0.0;
+  if (!isfinite(beta)) finish(S, HELM_ERR_NAN);
+  else if (S->bnorm == 0.0) { S->rel_recur = 0.0; finish(S, HELM_OK); }
+  else if (beta / S->bnorm < S->tol) finish(S, HELM_OK);
+  else if (S->matvecs >= S->maxmv) finish(S, HELM_ERR_MAXIT);
+}
+
+// v_0 = r / beta, and its copy in multigrid precision (the first V-cycle's input)
+template <typename TM>
+__global__ void k_gm_v0(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ V, void* vmg,
+                        long n) {
+  pdl_entry();
+  if (S->done) return;
+  const double beta = S->beta.x;
+  GRID_LOOP(i, n) {
+    double2 v = mkc<double>(r[i].x / beta, r[i].y / beta);
+    V[i] = v;
+    put_mg<TM>(vmg, i, v);
+  }
+}
+
+// w = H z (z = M^{-1} v_j)
+template <int DIM>
+__global__ void k_gm_w(const KrylovState* S, OpView<double> H, const double2* __restrict__ z,
+                       double2* __restrict__ w, long n) {
+  pdl_entry();
+  if (S->done) return;
+  ROW_LOOP(H, i, j, l, p) w[p] = op_row<double, double, DIM>(H, z, i, j, l, p);
+}
+
+// h_i = v_i^H w for i = 0..j: each block takes a contiguous slice of the points, so that its
+// slice of w stays in cache over the chunks of 8 basis vectors; the last block to finish adds
+// the per-block partials in block order (deterministic).
+__global__ void k_gm_dots(KrylovState* S, const double2* __restrict__ V, const double2* __restrict__ w, long n,
+                          double2* partials, double2* h, int tk) {
+  pdl_entry();
+  if (S->done) return;
+  const int j = S->k;
+  const int G = gridDim.x;
+  const long L = (n + G - 1) / G;
+  const long beg = blockIdx.x * L, end = beg + L < n ? beg + L : n;
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    double2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = mkc<double>(0.0, 0.0);
+    for (long p = beg + threadIdx.x; p < end; p += KT) {
+      const double2 wp = w[p];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q <= j) acc[q] = cfmac<double>(V[(size_t)(i0 + q) * n + p], wp, acc[q]);
+    }
+    block_sum<8>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q <= j) partials[(size_t)(i0 + q) * G + blockIdx.x] = acc[q];
+  }
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&S->ticket[tk], 1u) == (unsigned int)G - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i <= j; i += KT) {
+    double2 t = mkc<double>(0.0, 0.0);
+    for (int bk = 0; bk < G; ++bk) {
+      double2 pv = __ldcg(&partials[(size_t)i * G + bk]);
+      t.x += pv.x;
+      t.y += pv.y;
+    }
+    h[i] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S->ticket[tk] = 0u;
+}
+
+// End of an Arnoldi step (one thread): the new Hessenberg column h = hA + hB, the earlier
+// rotations on it, the rotation that annihilates h_{j+1,j} = hn, the rotated right-hand side and
+// the stopping tests.
+__device__ void gm_step_end(KrylovState* S, double hn) {
+  const int j = S->k, m = S->gmm;
+  GmView G = gm_view(S->gm, m);
+  double2* col = G.Hs + (size_t)(m + 1) * j;
+  for (int i = 0; i <= j; ++i) col[i] = cadd<double>(G.hA[i], G.hB[i]);
+  for (int i = 0; i < j; ++i) {
+    const double c = G.cs[i].x;
+    const double2 sn = G.sn[i], a = col[i], b = col[i + 1];
+    col[i] = cfma<double>(sn, b, cscale<double>(c, a));                                   // c a + s b
+    col[i + 1] = csub<double>(cscale<double>(c, b), cmul<double>(mkc<double>(sn.x, -sn.y), a));  // -conj(s) a + c b
+  }
+  const double2 a = col[j];
+  const double aa = hypot(a.x, a.y);
+  if (hn == 0.0) {
+    G.cs[j] = mkc<double>(1.0, 0.0);
+    G.sn[j] = mkc<double>(0.0, 0.0);
+  } else if (aa == 0.0) {
+    G.cs[j] = mkc<double>(0.0, 0.0);
+    G.sn[j] = mkc<double>(1.0, 0.0);
+    col[j] = mkc<double>(hn, 0.0);
+  } else {
+    const double t = hypot(aa, hn);
+    const double2 ph = mkc<double>(a.x / aa, a.y / aa);
+    G.cs[j] = mkc<double>(aa / t, 0.0);
+    G.sn[j] = cscale<double>(hn / t, ph);
+    col[j] = cscale<double>(t, ph);
+  }
+  col[j + 1] = mkc<double>(0.0, 0.0);
+  const double2 sn = G.sn[j], gj = G.g[j];
+  G.g[j + 1] = cmul<double>(mkc<double>(-sn.x, sn.y), gj);  // -conj(s) g_j
+  G.g[j] = cscale<double>(G.cs[j].x, gj);
+  S->matvecs += 1;
+  S->iters += 1;
+  const double est = hypot(G.g[j + 1].x, G.g[j + 1].y) / S->bnorm;
+  record(S, est);
+  S->hn = hn;
+  S->k = j + 1;
+  if (!isfinite(est) || !isfinite(hn)) finish(S, HELM_ERR_NAN);
+  else if (est < S->tol || hn == 0.0) finish(S, HELM_OK);
+  else if (j + 1 == m || S->matvecs >= S->maxmv) finish(S, HELM_ERR_MAXIT);
+}
+
+// w -= sum_{i<=j} h_i v_i (one Gram-Schmidt update); after the second pass (`final`) also ||w||
+// and the end of the Arnoldi step.
+__global__ void k_gm_sub(KrylovState* S, const double2* __restrict__ V, double2* __restrict__ w,
+                         const double2* __restrict__ h, long n, int final, double2* partials) {
+  pdl_entry();
+  if (S->done) return;
+  __shared__ double2 hs[GMRES_MMAX + 1];
+  const int j = S->k;
+  for (int i = threadIdx.x; i <= j; i += KT) hs[i] = h[i];
+  __syncthreads();
+  double2 acc[1] = {mkc<double>(0.0, 0.0)};
+  GRID_LOOP(p, n) {
+    double2 u = mkc<double>(0.0, 0.0);
+    for (int i = 0; i <= j; ++i) u = cfma<double>(hs[i], V[(size_t)i * n + p], u);
+    const double2 wp = csub<double>(w[p], u);
+    w[p] = wp;
+    acc[0].x = fma(wp.x, wp.x, fma(wp.y, wp.y, acc[0].x));
+  }
+  if (!final) return;
+  double2 tot[1];
+  if (!reduce_last<1>(acc, partials, &S->ticket[5], tot)) return;
+  if (threadIdx.x) return;
+  gm_step_end(S, sqrt(tot[0].x));
+}
+
+// v_{j+1} = w / h_{j+1,j} and its copy in multigrid precision (the next step's V-cycle input)
+template <typename TM>
+__global__ void k_gm_next(const KrylovState* S, const double2* __restrict__ w, double2* __restrict__ V, void* vmg,
+                          long n) {
+  pdl_entry();
+  if (S->done) return;
+  const double hn = S->hn;
+  double2* vk = V + (size_t)S->k * n;
+  GRID_LOOP(i, n) {
+    double2 v = mkc<double>(w[i].x / hn, w[i].y / hn);
+    vk[i] = v;
+    put_mg<TM>(vmg, i, v);
+  }
+}
+
+// R y = g by back substitution over the k = S->k columns of the cycle (one thread)
+__global__ void k_gm_y(KrylovState* S) {
+  pdl_entry();
+  if (threadIdx.x) return;
+  const int k = S->k, m = S->gmm;
+  GmView G = gm_view(S->gm, m);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = G.g[i];
+    for (int l = i + 1; l < k; ++l) acc = cfms<double>(G.Hs[i + (size_t)(m + 1) * l], G.y[l], acc);
+    G.y[i] = cdiv<double>(acc, G.Hs[i + (size_t)(m + 1) * i]);
+  }
+}
+
+// u = sum_{i<k} y_i v_i, written in multigrid precision as the V-cycle input (and in FP64 when
+// there is no preconditioner, where it is the correction itself)
+template <typename TM>
+__global__ void k_gm_comb(const KrylovState* S, const double2* __restrict__ V, void* umg, double2* u64, long n) {
+  pdl_entry();
+  __shared__ double2 ys[GMRES_MMAX];
+  const int k = S->k;
+  GmView G = gm_view(S->gm, S->gmm);
+  for (int i = threadIdx.x; i < k; i += KT) ys[i] = G.y[i];
+  __syncthreads();
+  GRID_LOOP(p, n) {
+    double2 u = mkc<double>(0.0, 0.0);
+    for (int i = 0; i < k; ++i) u = cfma<double>(ys[i], V[(size_t)i * n + p], u);
+    put_mg<TM>(umg, p, u);
+    if (u64) u64[p] = u;
+  }
+}
+
+// x += z
+__global__ void k_gm_addx(const KrylovState* S, const double2* __restrict__ z, double2* __restrict__ x, long n) {
+  pdl_entry();
+  if (S->k == 0) return;
+  GRID_LOOP(i, n) x[i] = cadd<double>(x[i], z[i]);
+}
+
 // ---- host orchestration ---------------------------------------------------------------------
 
 static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes, cudaStream_t st) {
@@ -725,8 +981,30 @@ static helm_status enqueue_idr_init(const Ctx& k, cudaStream_t st) {
 }
 
 template <typename TM, int DIM>
+static helm_status enqueue_gm_step(const Ctx& k, cudaStream_t st) {
+  Workspace* w = k.w;
+  OpView<double> H = k.c->H.view<double>();
+  GmView G = gm_view(w->gm, w->s);
+  const double2* z = (const double2*)w->pmg;  // identity preconditioner: TM is double
+  if (k.pc) {
+    helm_status s = precondition<TM>(k, w->pmg, w->ph, st);
+    if (s != HELM_OK) return s;
+    z = w->ph;
+  }
+  launch_pdl(k_gm_w<DIM>, dim3(k.G), dim3(KT), 0, st, w->st, H, z, w->t, k.n);
+  launch_pdl(k_gm_dots, dim3(k.G), dim3(KT), 0, st, w->st, w->V, w->t, k.n, w->partials, G.hA, 2);
+  launch_pdl(k_gm_sub, dim3(k.G), dim3(KT), 0, st, w->st, w->V, w->t, G.hA, k.n, 0, w->partials);
+  launch_pdl(k_gm_dots, dim3(k.G), dim3(KT), 0, st, w->st, w->V, w->t, k.n, w->partials, G.hB, 3);
+  launch_pdl(k_gm_sub, dim3(k.G), dim3(KT), 0, st, w->st, w->V, w->t, G.hB, k.n, 1, w->partials);
+  launch_pdl(k_gm_next<TM>, dim3(k.G), dim3(KT), 0, st, w->st, w->t, w->V, w->pmg, k.n);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename TM, int DIM>
 static helm_status enqueue_body(const Ctx& k, int method, int s, cudaStream_t st) {
   if (method == HELM_BICGSTAB) return enqueue_bicg_iter<TM, DIM>(k, st);
+  if (method == HELM_GMRES) return enqueue_gm_step<TM, DIM>(k, st);
   switch (s) {
     case 1: return enqueue_idr_step<TM, DIM, 1>(k, st);
     case 2: return enqueue_idr_step<TM, DIM, 2>(k, st);
@@ -837,7 +1115,7 @@ static helm_status build_loop(const Ctx& k, int method, int s) {
 template <typename TM>
 static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st) {
   Workspace*& w = c->ws;
-  if (w && (w->method != o->method || (o->method == HELM_IDR && w->s != o->s))) {
+  if (w && (w->method != o->method || (o->method != HELM_BICGSTAB && w->s != o->s))) {
     HELM_CUDA(cudaStreamSynchronize(st));
     krylov_free(c, st);
   }
@@ -860,7 +1138,8 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
     HELM_CUDA(cudaMemsetAsync(w->st, 0, sizeof(KrylovState), st));
     w->hst = (KrylovState*)pinned_slot_get(sizeof(KrylovState));
     if (!w->hst) { set_error("pinned host buffer"); return HELM_ERR_OOM; }
-    if ((s = ws_alloc(c, w, (void**)&w->partials, sizeof(double2) * NRED * w->G, st)) != HELM_OK) return s;
+    w->nred = o->method == HELM_GMRES ? std::max(NRED, o->s + 1) : NRED;
+    if ((s = ws_alloc(c, w, (void**)&w->partials, sizeof(double2) * w->nred * w->G, st)) != HELM_OK) return s;
     double2** vecs[] = {&w->x, &w->r, &w->t};
     for (auto pp : vecs) if ((s = ws_alloc(c, w, (void**)pp, v64, st)) != HELM_OK) return s;
     if ((s = ws_alloc(c, w, &w->pmg, vmg, st)) != HELM_OK) return s;
@@ -870,6 +1149,9 @@ static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaSt
       for (auto pp : more) if ((s = ws_alloc(c, w, (void**)pp, v64, st)) != HELM_OK) return s;
       if ((s = ws_alloc(c, w, &w->smg, vmg, st)) != HELM_OK) return s;
       if ((s = ws_alloc(c, w, (void**)&w->sh, v64, st)) != HELM_OK) return s;
+    } else if (o->method == HELM_GMRES) {
+      if ((s = ws_alloc(c, w, (void**)&w->V, v64 * (o->s + 1), st)) != HELM_OK) return s;
+      if ((s = ws_alloc(c, w, (void**)&w->gm, sizeof(double2) * gm_elems(o->s), st)) != HELM_OK) return s;
     } else {
       if ((s = ws_alloc(c, w, (void**)&w->q, v64, st)) != HELM_OK) return s;
       if ((s = ws_alloc(c, w, (void**)&w->P, v64 * o->s, st)) != HELM_OK) return s;
@@ -937,7 +1219,8 @@ struct SolveJob {
   helm_solve_info* info = nullptr;
   cudaStream_t st = nullptr;
   Ctx k{};
-  bool f32 = false, bicg = true;
+  bool f32 = false, bicg = true, gm = false;
+  int gm_passes = 0;  // GMRES cycles run
   int restarts = 0;
   long kernels = 0;
   long host_loops = -1;
@@ -951,11 +1234,17 @@ static helm_status job_pass(SolveJob& j) {
   Workspace* w = j.k.w;
   cudaStream_t st = j.st;
   const Ctx& k = j.k;
-  void* rmg = j.bicg ? nullptr : w->pmg;  // IDR's first V-cycle input is r in multigrid precision
-  launch_pdl(k_start, dim3(k.G), dim3(KT), 0, st, w->st, j.b, w->r, j.bicg ? w->rh : nullptr,
-             j.bicg ? w->p : nullptr, j.bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n,
-             j.restarts == 0 ? 1 : 0, w->partials);
-  if (!j.bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
+  if (j.gm) {
+    launch_pdl(k_gm_start, dim3(k.G), dim3(KT), 0, st, w->st, j.b, w->r, k.n, j.gm_passes == 0 ? 1 : 0,
+               w->partials);
+    launch_pdl(k_gm_v0<TM>, dim3(k.G), dim3(KT), 0, st, w->st, w->r, w->V, w->pmg, k.n);
+  } else {
+    void* rmg = j.bicg ? nullptr : w->pmg;  // IDR's first V-cycle input is r in multigrid precision
+    launch_pdl(k_start, dim3(k.G), dim3(KT), 0, st, w->st, j.b, w->r, j.bicg ? w->rh : nullptr,
+               j.bicg ? w->p : nullptr, j.bicg ? w->v : nullptr, rmg, k.mg32 ? 1 : 0, k.n,
+               j.restarts == 0 ? 1 : 0, w->partials);
+    if (!j.bicg) HELM_CUDA(cudaGraphLaunch(w->idr_init, st));
+  }
   j.host_loops = -1;
   if (j.o.host_loop) {
     j.host_loops = 0;
@@ -968,6 +1257,16 @@ static helm_status job_pass(SolveJob& j) {
     }
   } else {
     HELM_CUDA(cudaGraphLaunch(w->loop, st));
+  }
+  if (j.gm) {  // end of the cycle: x += M^{-1} (V y)
+    launch_pdl(k_gm_y, dim3(1), dim3(32), 0, st, w->st);
+    launch_pdl(k_gm_comb<TM>, dim3(k.G), dim3(KT), 0, st, w->st, w->V, w->pmg, k.pc ? nullptr : w->ph, k.n);
+    if (k.pc) {
+      helm_status s = mg_vcycle<TM>(k.c, (const cx<TM>*)w->pmg, w->ph, true, nullptr, st);
+      if (s != HELM_OK) return s;
+    }
+    launch_pdl(k_gm_addx, dim3(k.G), dim3(KT), 0, st, w->st, w->ph, w->x, k.n);
+    ++j.gm_passes;
   }
   OpView<double> H = j.c->H.view<double>();
   switch (k.dim) {
@@ -998,6 +1297,13 @@ static helm_status job_begin_t(SolveJob& j) {
   HELM_CUDA(cudaMemcpyAsync(&w->st->s, &init.s, sizeof(int), cudaMemcpyHostToDevice, st));
   double* hist = j.o.history;
   HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
+  if (j.gm) {
+    init.gmm = j.o.s;
+    init.gm = w->gm;
+    HELM_CUDA(cudaMemcpyAsync(&w->st->gmm, &init.gmm, sizeof(int), cudaMemcpyHostToDevice, st));
+    HELM_CUDA(cudaMemcpyAsync(&w->st->gm, &init.gm, sizeof(double2*), cudaMemcpyHostToDevice, st));
+    j.gm_passes = 0;
+  }
   HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * j.k.n, st));
   if (!j.ev) HELM_CUDA(cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming));
   return job_pass<TM>(j);
@@ -1009,14 +1315,31 @@ static helm_status job_step_t(SolveJob& j) {
   Workspace* w = j.k.w;
   const KrylovState& hs = *w->hst;
   // k_start, the loop head, loops x body, k_true_res (+ the IDR start graph)
-  if (j.host_loops >= 0) j.kernels += 2 + j.host_loops * (long)(w->body_nodes - 1) + (j.bicg ? 0 : (long)w->init_nodes);
-  else j.kernels += 3 + (long)hs.loops * (long)w->body_nodes + (j.bicg ? 0 : (long)w->init_nodes);
-  if (hs.status == HELM_OK && !(hs.rel_true < j.o.tol) && j.restarts < j.o.max_restarts) {
-    ++j.restarts;
-    return job_pass<TM>(j);
+  if (j.gm) {
+    // k_gm_start, k_gm_v0, the loop head, loops x body, k_gm_y, k_gm_comb, the V-cycle (its
+    // kernels are the body's minus the 7 GMRES ones), k_gm_addx, k_true_res
+    long vc = j.k.pc ? (long)w->body_nodes - 7 : 0;
+    if (j.host_loops >= 0) j.kernels += 6 + vc + j.host_loops * (long)(w->body_nodes - 1);
+    else j.kernels += 7 + vc + (long)hs.loops * (long)w->body_nodes;
+    // a cycle that ended at m steps continues; one whose estimate met tol while the true
+    // residual did not counts as a restart
+    bool more = false;
+    if (!(hs.rel_true < j.o.tol) && hs.matvecs < j.o.maxmv) {
+      if (hs.status == HELM_ERR_MAXIT) more = true;
+      else if (hs.status == HELM_OK && j.restarts < j.o.max_restarts) { ++j.restarts; more = true; }
+    }
+    if (more) return job_pass<TM>(j);
+  } else {
+    if (j.host_loops >= 0) j.kernels += 2 + j.host_loops * (long)(w->body_nodes - 1) + (j.bicg ? 0 : (long)w->init_nodes);
+    else j.kernels += 3 + (long)hs.loops * (long)w->body_nodes + (j.bicg ? 0 : (long)w->init_nodes);
+    if (hs.status == HELM_OK && !(hs.rel_true < j.o.tol) && j.restarts < j.o.max_restarts) {
+      ++j.restarts;
+      return job_pass<TM>(j);
+    }
   }
   HELM_CUDA(cudaMemcpyAsync(j.x, w->x, sizeof(double2) * j.k.n, cudaMemcpyDeviceToDevice, j.st));
   helm_status fs = (helm_status)hs.status;
+  if (j.gm && (fs == HELM_OK || fs == HELM_ERR_MAXIT)) fs = hs.rel_true < j.o.tol ? HELM_OK : HELM_ERR_MAXIT;
   if (fs == HELM_OK && !(hs.rel_true < j.o.tol)) fs = HELM_ERR_MAXIT;
   if (j.info) {
     j.info->status = fs;
@@ -1037,6 +1360,7 @@ static bool job_f32(const helm_ctx* c) { return c->pc.kind != HELM_PC_NONE && c-
 helm_status job_begin(SolveJob& j) {
   j.f32 = job_f32(j.c);
   j.bicg = j.o.method == HELM_BICGSTAB;
+  j.gm = j.o.method == HELM_GMRES;
   return j.f32 ? job_begin_t<float>(j) : job_begin_t<double>(j);
 }
 
@@ -1093,7 +1417,8 @@ helm_status krylov_solve_batch(helm_ctx* const* cs, const double2* const* b, dou
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
     std::vector<std::pair<double, int>> w(n);
-    for (int i = 0; i < n; ++i) w[i] = {(double)cs[i]->n * (o[i].method == HELM_IDR ? 1.8 : 1.0), i};
+    for (int i = 0; i < n; ++i)
+      w[i] = {(double)cs[i]->n * (o[i].method == HELM_IDR ? 1.8 : o[i].method == HELM_GMRES ? 1.0 + 0.2 * o[i].s : 1.0), i};
     std::sort(w.begin(), w.end());
     const int levels = least - greatest + 1;
     for (int r = 0; r < n; ++r) prio[w[r].second] = least - (int)((long)r * levels / (n > 0 ? n : 1));

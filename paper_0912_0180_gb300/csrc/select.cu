@@ -166,7 +166,8 @@ helm_status helm_select_precond(const helm_grid* grid, const helm_kspec* k, cons
   cudaStream_t st = (cudaStream_t)stream;
   *out = *start;
   helm_precond pc = *start;
-  pc.mg_dtype = HELM_C128;  // the decision is taken on FP64 hierarchies
+  pc.mg_dtype = HELM_C128;            // the decision is taken on FP64 hierarchies
+  pc.flags |= HELM_PF_NO_AUTOTUNE;    // each trial's hierarchy runs a few cycles only
   double p = start->kind == HELM_PC_CSL ? start->shift_im : start->theta_beta;
   bool any = false;
   void* u = nullptr;

@@ -87,6 +87,7 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
   }
   // Krylov workspace
   if (o->method == HELM_IDR) bytes += (size_t)N * ((5 + 3 * (size_t)o->s) * 16 + esz);
+  else if (o->method == HELM_GMRES) bytes += (size_t)N * ((5 + 1 + (size_t)o->s) * 16 + esz) + (size_t)(o->s + 2) * o->s * 16;
   else bytes += (size_t)N * (9 * 16 + 2 * esz);
   bytes += (size_t)N * 32;  // the request's own b and x on the device
   bytes += 64 * 1024;       // state and partial sums

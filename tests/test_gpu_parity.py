@@ -570,3 +570,72 @@ def test_smooth_contour_parity(case):
             assert abs(info.matvecs - io["matvecs"]) <= 2
             assert rel(xs.cpu().numpy(), xo) < 1e-9
         h.close()
+
+
+GMRES_CASES = [
+    # case index into CASES, preconditioner, restart length m
+    (2, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5), 10),
+    (3, hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5), 40),
+    (5, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS), 7),
+    (0, hi.Precond(kind=hi.PC_NONE), 64),
+]
+
+
+@pytest.mark.parametrize("gi", range(len(GMRES_CASES)))
+def test_gmres_solve_matches_oracle(gi):
+    """Restarted right-preconditioned GMRES(m): the FP64 solve against the oracle's (matvecs within
+    2, same solution to 1e-9 at tol 1e-10, the same residual estimates step by step while they are
+    far above rounding), the host-driven loop bitwise equal to the device loop, and the FP32
+    V-cycle path certified by its FP64 true residual."""
+    ci, pc, m = GMRES_CASES[gi]
+    p = _problem(CASES[ci], rhs="gauss", seed=23)
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype="c128")
+    maxmv = 4000
+    xo, io = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=m, tol=1e-10, maxmv=maxmv), history=True)
+    x, info = h.solve(cu(p.b), method=hi.GMRES, s=m, tol=1e-10, maxmv=maxmv, history=True)
+    assert info.status == 0 and io["status"] == 0, (info, io)
+    assert info.rel_res_true < 1e-10
+    assert abs(info.matvecs - io["matvecs"]) <= 2
+    assert rel(x.cpu().numpy(), xo) < 1e-9
+    hg = info.history[: min(info.matvecs, io["matvecs"])]
+    ho = io["history"][: len(hg)]
+    far = ho > 1e-6
+    assert np.allclose(hg[far], ho[far], rtol=1e-6)
+    x2, info2 = h.solve(cu(p.b), method=hi.GMRES, s=m, tol=1e-10, maxmv=maxmv, host_loop=True)
+    assert info2.matvecs == info.matvecs and torch.equal(x2, x)
+    h.close()
+    if pc.kind != hi.PC_NONE:
+        h32 = Helm(p, pc, mg_dtype="c64")
+        x3, info3 = h32.solve(cu(p.b), method=hi.GMRES, s=m, tol=1e-8, maxmv=maxmv)
+        assert info3.status == 0 and info3.rel_res_true < 1e-8
+        xo8, io8 = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=m, tol=1e-8, maxmv=maxmv))
+        assert abs(info3.matvecs - io8["matvecs"]) <= max(3, io8["matvecs"] // 10)
+        h32.close()
+
+
+def test_gmres_full_and_batch():
+    """GMRES with m above the step count (no restart) equals the oracle; a batch mixing GMRES,
+    Bi-CGSTAB and IDR gives every instance its lone result bitwise."""
+    p = _problem(CASES[1], rhs="gauss", seed=24)
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    xo, io = o.solve(p.b, hi.SolveOpts(method=hi.GMRES, s=128, tol=1e-10, maxmv=128))
+    hs = [Helm(p, pc, mg_dtype="c128") for _ in range(3)]
+    x, info = hs[0].solve(cu(p.b), method=hi.GMRES, s=128, tol=1e-10, maxmv=128)
+    assert io["status"] == 0 and info.status == 0 and info.restarts == 0
+    assert abs(info.matvecs - io["matvecs"]) <= 1
+    assert rel(x.cpu().numpy(), xo) < 1e-9
+    from paper_0912_0180_gb300.helm import solve_batch
+    shadow = hi.shadow_space(p.n, 4)
+    lone = [hs[0].solve(cu(p.b), method=hi.GMRES, s=20, tol=1e-8)[0],
+            hs[1].solve(cu(p.b), method=hi.BICGSTAB, tol=1e-8)[0],
+            hs[2].solve(cu(p.b), method=hi.IDR, s=4, tol=1e-8, shadow=shadow)[0]]
+    xs, infos = solve_batch(hs, [cu(p.b)] * 3, method=[hi.GMRES, hi.BICGSTAB, hi.IDR], s=[20, 4, 4],
+                            tol=1e-8, shadows=[None, None, shadow])
+    for a, b_, inf in zip(xs, lone, infos):
+        assert inf.status == 0 and torch.equal(a, b_)
+    with pytest.raises(Exception):
+        hs[0].solve(cu(p.b), method=hi.GMRES, s=129)
+    for h in hs:
+        h.close()
