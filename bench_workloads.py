@@ -15,6 +15,12 @@
             once, {Bi-CGSTAB, IDR(4), IDR(8)} x {CSL, CSG} with the shift and angle of the paper's
             ECS rows and its Galerkin coarse operators (omega-Jacobi V(1,1) here, not the paper's
             ILU(0) V(0,1), so the paper's matvec counts, reported beside ours, are context).
+  mp2s      mp2 on the smooth ECS contour of the paper's Section 7 remark (the layer widths turn by
+            theta_gamma / 128 per width over the whole 128-node layer).
+  gmres     the paper's GMRES remark: MP2 (nu = 1, k = 4, ECS) to 1e-7 with GMRES(128), GMRES(30),
+            Bi-CGSTAB and IDR(4) under the CSG (pi/26) Galerkin multigrid preconditioner.
+  select    the automatic CSL shift / CSG angle choice of Section 7's remark on the 640^2 workload,
+            then a solve with the default and with the chosen parameter each.
   serve     a Poisson-arrival stream (--serve-requests, default 32, at --serve-rate, default 200
             requests/s) of 2D (127^2 .. 1023^2 interior) and 3D (64^3 .. 160^3 interior) requests
             with 1..8 point-source right-hand sides each, submitted at their arrival times to the
@@ -74,7 +80,8 @@ def run(args):
     g.build()
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
-    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp}[args.workload]
+    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+          "select": run_select, "gmres": run_gmres}[args.workload]
     line = fn(args, torch, ranks, dev, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -496,5 +503,130 @@ def run_mp(args, torch, ranks, dev, local):
         "e2e": {"value": None, "unit": "solves/s", "path": "not measured in this mode (see the default workload)",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": int(sum(i.kernels for i in res["c128"][1]) + sum(i.kernels for i in res["c64"][1])),
+    })
+    return line
+
+
+def run_select(args, torch, ranks, dev, local):
+    """The automatic parameter choice of Section 7's remark on the 640^2 workload: from a start
+    twice the default (CSL shift 1 + 1.0i, CSG angle 0.6), the parameter shrinks by 0.8 per trial
+    while omega-Jacobi V(1,1) multigrid, run as a solver of M u = f, still reaches 1e-6 within 20
+    cycles.  Then one Bi-CGSTAB solve (FP32 V-cycle, FP64 Krylov) with the default and with the
+    chosen parameter each, for their matvecs and times."""
+    import bench
+    from paper_0912_0180_gb300.helm import Helm, select_precond
+    p = hi.workload_2d_512()
+    f = torch.from_numpy(hi.random_vector(p.n, 20091202)).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    starts = {"csl": (hi.Precond(kind=hi.PC_CSL, shift=1 + 1.0j, smoother=hi.SM_JACOBI, omega=0.5),
+                      hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)),
+              "csg": (hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.6, smoother=hi.SM_JACOBI, omega=0.5),
+                      hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5))}
+    out, seconds, launches = {}, [], 0
+
+    def timed_solve(pc):
+        h = Helm(p, pc, mg_dtype="c64")
+        for _ in range(args.warmup):
+            h.solve(b, tol=TOL, maxmv=4000)
+        ms, info = [], None
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, info = h.solve(b, tol=TOL, maxmv=4000)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        h.close()
+        return statistics.mean(ms), info
+
+    with bench.ClockSampler(local) as clk:
+        for name, (start, default) in starts.items():
+            select_precond(p, start, f, 20, 1e-6, 0.8, 12)  # warm-up (module load, first allocations)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            chosen, st, params, cycles = select_precond(p, start, f, 20, 1e-6, 0.8, 12)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            seconds.append(sec)
+            ms_def, info_def = timed_solve(default)
+            ms_ch, info_ch = timed_solve(chosen)
+            _check([info_def, info_ch], f"select-{name}")
+            launches += info_def.kernels + info_ch.kernels
+            par = (lambda pc: complex(pc.shift).imag) if name == "csl" else (lambda pc: pc.theta_beta)
+            out[name] = {"start": par(start), "chosen": par(chosen), "status": int(st), "select_s": sec,
+                         "trials": [{"param": float(a), "cycles": int(c)} for a, c in zip(params, cycles)],
+                         "solve_default": {"param": par(default), "matvecs": info_def.matvecs, "ms": ms_def},
+                         "solve_chosen": {"param": par(chosen), "matvecs": info_ch.matvecs, "ms": ms_ch}}
+    total = sum(seconds)
+    cfg = {"workload": "select-" + p.name, "n_unknowns": p.n,
+           "rule": "parameter x 0.8 per trial while omega-Jacobi V(1,1) on M reaches 1e-6 in <= 20 cycles "
+                   "(FP64 hierarchy, seeded random f)",
+           "solves": "Bi-CGSTAB, FP32 V-cycle, FP64 Krylov, tol 1e-6, default vs chosen parameter"}
+    line = {"metric": "automatic preconditioner-parameter selections per second", "value": len(seconds) / total,
+            "unit": "selections/s", "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / len(seconds), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": cfg}
+    line.update({"csl": out["csl"], "csg": out["csg"], "clocks": clk.summary(),
+                 "e2e": {"value": None, "unit": "selections/s", "path": "not measured in this mode",
+                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                 "gpu_launches": int(launches)})
+    return line
+
+
+def run_gmres(args, torch, ranks, dev, local):
+    """The paper's GMRES remark (Section 7): multigrid-preconditioned GMRES on MP2 with nu = 1,
+    k = 4 and ECS layers, the CSG preconditioner of Table MP2's row for that case (theta_beta =
+    pi/26), residual reduced by seven orders of magnitude; beside it Bi-CGSTAB and IDR(4) on the
+    same preconditioner.  GMRES(128) (restarted only past 128 steps) and GMRES(30) are timed one
+    solve at a time, like the other two methods."""
+    import bench
+    from paper_0912_0180_gb300.helm import Helm
+    p = hi.workload_mp2(nu=1.0, k=4.0)
+    b = torch.from_numpy(p.b).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=np.pi / 26, smoother=hi.SM_JACOBI, omega=0.5, galerkin=True)
+    tol = 1e-7
+    methods = [("gmres128", hi.GMRES, 128), ("gmres30", hi.GMRES, 30), ("bicgstab", hi.BICGSTAB, 4),
+               ("idr4", hi.IDR, 4)]
+    shadow = hi.shadow_space(p.n, 4)
+    res, launches = {}, 0
+    with bench.ClockSampler(local) as clk:
+        for mg in ("c128", "c64"):
+            h = Helm(p, pc, mg_dtype=mg)
+            for name, meth, s in methods:
+                kw = dict(method=meth, s=s, tol=tol, maxmv=MP_MAXMV, shadow=shadow if meth == hi.IDR else None)
+                for _ in range(args.warmup):
+                    h.solve(b, **kw)
+                ms, info = [], None
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    x, info = h.solve(b, **kw)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                if info.status != 0 or not info.rel_res_true < tol:
+                    raise SystemExit(f"gmres workload: {name} ({mg}) did not converge: {info}")
+                launches += info.kernels
+                res[(mg, name)] = {"matvecs": info.matvecs, "ms": ranks.max(statistics.mean(ms)),
+                                   "restarts": info.restarts, "true_rel_res": info.rel_res_true}
+            h.close()
+    g = res[("c128", "gmres128")]
+    cfg = {"workload": "gmres-" + p.name, "n_unknowns": p.n, "tol": tol,
+           "preconditioner": "CSG theta_beta = pi/26, Galerkin omega-Jacobi V(1,1)",
+           "solves": "one at a time: GMRES(128), GMRES(30), Bi-CGSTAB, IDR(4)",
+           "l2": "flushed (512 MiB device write) before every timed solve"}
+    line = _base(args, ranks.job_rate(1, g["ms"]), g["ms"], ranks.world, cfg, "c128")
+    line.update({
+        "methods": {mg: {name: res[(mg, name)] for name, _, _ in methods} for mg in ("c128", "c64")},
+        "paper_context": {"gmres_iterations": 103, "bicgstab_matvecs": 115, "idr4_matvecs": 123,
+                          "gmres_time_over_bicgstab": "about 5 (175 s against 36 s, MATLAB on a Xeon)"},
+        "clocks": clk.summary(),
+        "e2e": {"value": None, "unit": "solves/s", "path": "not measured in this mode",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": int(launches),
     })
     return line
