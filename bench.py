@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32, help="serve: requests in the stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--serve-slots", type=int, default=8, help="serve: requests the server runs at once")
+    ap.add_argument("--serve-sweep", default="", help="serve: comma-separated further offered rates (requests/s), "
+                    "each run once on the FP32-multigrid path")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

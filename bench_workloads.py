@@ -416,6 +416,21 @@ def run_serve(args, torch, ranks, dev, local):
                 "d2h_bytes_per_step": int(sum(r.rhs.nbytes for r in reqs))},
         "gpu_launches": int(sum(o[1].kernels for o in o64) + sum(o[1].kernels for o in o32)),
     })
+    if args.serve_sweep:
+        # the same request mix at other offered rates (FP32-multigrid path, one stream each)
+        sweep = []
+        for rate in [float(v) for v in args.serve_sweep.split(",") if v]:
+            rq = hi.workload_serve(args.serve_requests, rate)
+            wall, outs = _stream(torch, rq, "c64", budget, args.serve_slots)
+            for x, info, lat in outs:
+                if info.status != 0 or not info.rel_res_true < TOL:
+                    raise SystemExit(f"serve sweep: a request did not converge: {info}")
+            lat = [o[2] * 1000 for o in outs]
+            ns = int(sum(r.rhs.shape[0] for r in rq))
+            sweep.append({"offered_requests_per_s": rate, "requests_per_s": len(rq) / wall,
+                          "rhs_solves_per_s": ns / wall, "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99)}})
+            line["gpu_launches"] += int(sum(o[1].kernels for o in outs))
+        line["fp32_mg"]["rate_sweep"] = sweep
     return line
 
 

@@ -187,3 +187,25 @@ def test_server_smallest_first_admission():
         assert np.array_equal(xa.cpu().numpy(), x) and ia.matvecs == info.matvecs
         h.close()
     srv.close()
+
+
+def test_gmres_in_batch_and_server():
+    """GMRES(30) instances batched and served give each instance its lone result bitwise."""
+    from paper_0912_0180_gb300.helm import Helm, Server, solve_batch
+    inst = _instances()[:4]
+    hs = [Helm(p, pc, mg_dtype="c64") for p, pc in inst]
+    bs = [torch.from_numpy(p.b).cuda() for p, _ in inst]
+    alone = [h.solve(b, method=hi.GMRES, s=30, tol=1e-7, maxmv=3000) for h, b in zip(hs, bs)]
+    alone = [(x.clone(), i) for x, i in alone]
+    xs, infos = solve_batch(hs, bs, method=hi.GMRES, s=30, tol=1e-7, maxmv=3000)
+    for (xa, ia), xb, ib in zip(alone, xs, infos):
+        assert ia.status == 0 and ib.status == 0
+        assert torch.equal(xa, xb) and ia.matvecs == ib.matvecs
+    srv = Server(64 << 30, max_active=4)
+    tickets = [srv.submit(p, pc, method=hi.GMRES, s=30, tol=1e-7, maxmv=3000) for p, pc in inst]
+    for (xa, ia), t in zip(alone, tickets):
+        x, info, lat = srv.wait(t)
+        assert info.status == 0 and np.array_equal(xa.cpu().numpy(), x) and info.matvecs == ia.matvecs
+    srv.close()
+    for h in hs:
+        h.close()
