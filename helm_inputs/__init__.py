@@ -58,9 +58,10 @@ class Problem:
 
 
 def axis_unknowns(n_int: int, nl: Tuple[int, int]) -> int:
-    """Number of unknowns along one axis (interior nodes, minus Dirichlet walls, plus layers)."""
+    """Number of unknowns along one axis (interior nodes, minus Dirichlet walls, plus layers; a
+    high side of -1 is a Sommerfeld boundary whose node is an unknown)."""
     lo, hi = nl
-    return n_int - 2 + (lo + 1 if lo > 0 else 0) + (hi + 1 if hi > 0 else 0)
+    return n_int - 2 + (lo + 1 if lo > 0 else 0) + (hi + 1 if hi > 0 else (1 if hi < 0 else 0))
 
 
 def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray:
@@ -70,7 +71,7 @@ def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray
     xs: List[float] = []
     xs += [-m * h for m in range(lo, 0, -1)]
     first = 0 if lo > 0 else 1
-    last = n_int - 1 if hi > 0 else n_int - 2
+    last = n_int - 1 if hi != 0 else n_int - 2
     xs += [j * h for j in range(first, last + 1)]
     xs += [extent + m * h for m in range(1, hi + 1)]
     return np.asarray(xs, dtype=np.float64)

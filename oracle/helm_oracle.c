@@ -41,7 +41,9 @@ typedef double complex cplx;
 typedef struct {
   int dim;              /* 1, 2 or 3 */
   int n_int[3];         /* interior grid nodes per axis, both ends (turning points) included */
-  int n_layer[3][2];    /* ECS layer nodes on the low / high side; 0 = Dirichlet wall */
+  int n_layer[3][2];    /* ECS layer nodes on the low / high side; 0 = Dirichlet wall; -1 on a
+                           high side = first-order Sommerfeld condition there (Section 2,
+                           eq. "sommerfeld1"): the boundary node is an unknown */
   double extent[3];     /* length of the real interior along each axis */
   double theta_gamma;   /* ECS angle */
   int ecs_ramp;         /* R > 1: the m-th layer width from the turning point has angle
@@ -81,9 +83,12 @@ typedef struct {
 /* ---- grid ---------------------------------------------------------------------------- */
 typedef struct {
   int n;          /* unknowns on this axis */
-  cplx* gap;      /* n + 1 widths: gap[j] = z(node j+1) - z(node j), nodes 0 and n+1 Dirichlet */
+  cplx* gap;      /* n + 1 widths: gap[j] = z(node j+1) - z(node j), nodes 0 and n+1 Dirichlet;
+                     with a Sommerfeld high side, gap[n] is the mirror width to the ghost node */
   double* pos;    /* n real positions of the unknowns (only used to sample phi) */
   cplx *am, *a0, *ap; /* Shortley-Weller row of -d^2/dz^2 at each unknown */
+  int somm;       /* 1: the last unknown is a Sommerfeld boundary node */
+  cplx bt;        /* its boundary weight 2i / h_l: the diagonal gains bt * k */
 } axis_t;
 
 typedef struct {
@@ -125,8 +130,10 @@ static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, dou
                        int ramp, cplx scale_in, cplx scale_ly) {
   double h = extent / (n_int - 1);
   int lo = nl[0], hi = nl[1];
-  int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+  /* a Sommerfeld high side adds one width: the mirror of the last one, to the ghost node */
+  int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
   a->n = ngap - 1;
+  a->somm = hi < 0;
   a->gap = malloc(sizeof(cplx) * ngap);
   a->pos = malloc(sizeof(double) * imax(a->n, 1));
   int g = 0;
@@ -135,10 +142,11 @@ static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, dou
   for (int m = 0; m < n_int - 1; ++m) a->gap[g++] = h * scale_in;
   if (hi > 0)
     for (int m = 1; m <= hi + 1; ++m) a->gap[g++] = layer_width(h, theta_g, ramp, m) * scale_ly;
+  if (hi < 0) a->gap[g++] = h * scale_in;
   /* real positions: the layers continue the real coordinate */
   int u = 0;
   for (int m = lo; m >= 1; --m) a->pos[u++] = -m * h;
-  int first = lo > 0 ? 0 : 1, last = hi > 0 ? n_int - 1 : n_int - 2;
+  int first = lo > 0 ? 0 : 1, last = hi != 0 ? n_int - 1 : n_int - 2;
   for (int j = first; j <= last; ++j) a->pos[u++] = j * h;
   for (int m = 1; m <= hi; ++m) a->pos[u++] = extent + m * h;
 }
@@ -156,6 +164,18 @@ static void axis_coeffs(axis_t* a) {
     a->a0[j] = f * (1.0 / hl + 1.0 / hr);
     a->ap[j] = -f / hr;
   }
+  a->bt = 0;
+  if (a->somm && a->n > 0) {
+    /* Sommerfeld node N (Section 2, eq. "sommerfeld1", du/dn = -i k u): the centred difference
+     * (u_g - u_{N-1}) / (2 h_l) = -i k u_N puts the ghost value u_g = u_{N-1} - 2 i k h_l u_N into
+     * the row: the left weight doubles, the right one vanishes, and the diagonal gains
+     * -2 i k h_l ap = 2 i k / h_l (the gap to the ghost mirrors h_l). */
+    int N = a->n - 1;
+    cplx hl = a->gap[N];
+    a->bt = -2.0 * I * hl * a->ap[N];
+    a->am[N] *= 2.0;
+    a->ap[N] = 0;
+  }
 }
 
 /* Index-even coarsening: coarse unknown c is fine unknown 2c+1 (0-based), i.e. coarse node
@@ -163,6 +183,7 @@ static void axis_coeffs(axis_t* a) {
  * nodes; the last one reaches the fine Dirichlet node and spans one or two fine widths. */
 static void axis_coarsen(const axis_t* f, axis_t* c) {
   c->n = f->n / 2;
+  c->somm = f->somm;
   c->gap = malloc(sizeof(cplx) * (c->n + 1));
   c->pos = malloc(sizeof(double) * imax(c->n, 1));
   for (int ci = 0; ci < c->n; ++ci) {
@@ -171,7 +192,9 @@ static void axis_coarsen(const axis_t* f, axis_t* c) {
   }
   cplx last = 0;
   for (int j = 2 * c->n; j <= f->n; ++j) last += f->gap[j];
-  c->gap[c->n] = last;
+  /* a Sommerfeld axis is coarsened only with an even n, so the fine boundary node 2c+1 = n-1 is
+   * the last coarse node; its ghost width mirrors the last coarse width */
+  c->gap[c->n] = c->somm ? c->gap[c->n - 1] : last;
   axis_coeffs(c);
 }
 
@@ -235,8 +258,13 @@ static cplx diag_at(const level_t* L, int i, int j, int l) {
   if (L->st9) return L->st9[9 * lidx(L, i, j, l) + 4];
   int ix[3] = {i, j, l};
   cplx d = 0;
-  for (int a = 0; a < L->dim; ++a) d += L->ax[a].a0[ix[a]];
-  return d - L->s * L->phi[lidx(L, i, j, l)];
+  double ph = L->phi[lidx(L, i, j, l)];
+  for (int a = 0; a < L->dim; ++a) {
+    d += L->ax[a].a0[ix[a]];
+    /* Sommerfeld boundary node: + 2 i k / h_l with k = sqrt(phi), the unshifted wave number */
+    if (L->ax[a].somm && ix[a] == L->ax[a].n - 1) d += L->ax[a].bt * sqrt(ph);
+  }
+  return d - L->s * ph;
 }
 
 /* Off-diagonal part of row (i,j,l) applied to x (Dirichlet neighbours contribute 0). */
@@ -421,7 +449,11 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_p
       if (F->n[d] > pc->coarse_max) all_small = 0;
       if (F->n[d] < min_n) min_n = F->n[d];
     }
-    if (all_small || min_n < 3) break;
+    /* a Sommerfeld axis keeps its boundary node only when its unknown count is even */
+    int odd_somm = 0;
+    for (int d = 0; d < F->dim; ++d)
+      if (F->ax[d].somm && (F->n[d] & 1)) odd_somm = 1;
+    if (all_small || min_n < 3 || odd_somm) break;
     level_coarse(F, &c->M[c->nlev]);
     if (pc->galerkin && g->dim == 2) level_galerkin(F, &c->M[c->nlev]);
     c->nlev++;

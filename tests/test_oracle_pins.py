@@ -742,3 +742,67 @@ def test_right_preconditioned_gmres_minimises_over_the_preconditioned_space():
         assert np.all(np.diff(cyc) <= 1e-12 * cyc[0])
     xd = o.dense_solve(p.b)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+
+
+# ---- first-order Sommerfeld boundary (Section 2, eq. "sommerfeld1") ----------------------------
+
+def test_sommerfeld_row_is_consistent_with_the_outgoing_wave():
+    """u = e^{-i k x} satisfies du/dn = -i k u at the high end exactly; the interior rows leave
+    (2 - 2 cos kh)/h^2 - k^2 = O(k^4 h^2), and the ghost-node boundary row leaves
+    i k^3 h / 3 - k^4 h^2 / 12 + O(h^3) (Taylor expansion of its three terms) -- on every level of
+    the hierarchy, whose coarse grids keep the boundary node."""
+    n_int, k = 97, 9.0
+    p = _prob(1, n_int, (0, -1), theta=0.5, k0=k, rhs="zero")
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1.0, smoother=hi.SM_JACOBI, max_levels=4, coarse_max=2)
+    o = Oracle(p, pc)
+    assert o.nlev == 4
+    for lvl in range(o.nlev):
+        t = o.axis_tables(1, lvl, 0)
+        x = t["pos"]
+        h = float(np.real(t["gap"][-2]))
+        assert x[-1] == 1.0 and t["gap"][-1] == t["gap"][-2]  # boundary node kept, ghost mirrored
+        u = np.exp(-1j * k * x)
+        r = o.apply(u, 1, lvl) / u  # CSL with shift 1 is H on this level
+        inner = (2 - 2 * np.cos(k * h)) / h ** 2 - k ** 2
+        assert np.allclose(r[1:-1], inner, atol=1e-9 * k ** 2)
+        lead = 1j * k ** 3 * h / 3 - k ** 4 * h ** 2 / 12
+        assert abs(r[-1] - lead) <= 0.2 * k ** 5 * h ** 3 + 1e-9 * k ** 2
+
+
+def test_sommerfeld_weighted_operator_is_complex_symmetric():
+    """With the half cell w_N = h_l / 2 at a Sommerfeld node (full cells elsewhere) W H is complex
+    symmetric: the ghost doubles the boundary row's left weight and nothing else is off."""
+    p = _prob(2, (9, 10), ((2, -1), (0, -1)), theta=0.5, k0=4.0)
+    o = Oracle(p)
+    w = []
+    for a in range(2):
+        g = o.axis_tables(0, 0, a)["gap"]
+        wa = (g[:-1] + g[1:]) / 2
+        wa[-1] = g[-2] / 2
+        w.append(wa)
+    W = np.multiply.outer(w[1], w[0]).ravel()
+    A = o.dense()
+    WA = W[:, None] * A
+    assert np.abs(WA - WA.T).max() <= 1e-12 * np.abs(WA).max()
+
+
+def test_sommerfeld_spectrum_in_the_upper_half_plane():
+    """The boundary term 2 i k / h is the only non-real part of W^{1/2} H W^{-1/2} (complex
+    symmetric, real off the boundary) and it is positive imaginary, so every eigenvalue of H has
+    Im >= 0 (Bendixson) -- the 'first quadrant' spectrum the paper contrasts with ECS -- and the
+    boundary makes some strictly positive."""
+    p = _prob(2, (12, 13), ((0, -1), (0, -1)), theta=0.0, k0=7.0)
+    lam = np.linalg.eigvals(Oracle(p).dense())
+    assert lam.imag.min() >= -1e-10 * np.abs(lam).max()
+    assert lam.imag.max() > 1.0
+
+
+def test_sommerfeld_mg_preconditioned_solve_reaches_direct_solution():
+    p = _prob(2, (33, 32), ((0, -1), (4, -1)), theta=0.5, k0=10.0)  # 32 x 36 unknowns: 3 levels
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    assert o.nlev >= 3
+    x, info = o.solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-11, maxmv=2000))
+    assert info["status"] == 0
+    xd = o.dense_solve(p.b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
