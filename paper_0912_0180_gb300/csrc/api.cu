@@ -52,11 +52,11 @@ static helm_status check_grid(const helm_grid* g) {
   long total = 1;
   for (int a = 0; a < g->dim; ++a) {
     int lo = g->n_layer[a][0], hi = g->n_layer[a][1];
-    if (lo < 0 || hi < 0 || g->n_int[a] < 2 || !(g->extent[a] > 0.0) || !std::isfinite(g->extent[a])) {
-      set_error("invalid n_int / n_layer / extent");
+    if (lo < 0 || hi < -1 || g->n_int[a] < 2 || !(g->extent[a] > 0.0) || !std::isfinite(g->extent[a])) {
+      set_error("invalid n_int / n_layer / extent (low sides >= 0, high sides >= -1)");
       return HELM_ERR_ARG;
     }
-    long n = (long)g->n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+    long n = axis_unknowns(g->n_int[a], lo, hi);
     if (n < 1 || n > 65535) { set_error("an axis has no unknowns or more than 65535"); return HELM_ERR_ARG; }
     total *= n;
     if (total > (1L << 34)) { set_error("grid too large"); return HELM_ERR_ARG; }
@@ -153,14 +153,16 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   cudaGetDevice(&c->dev);
   cudaStream_t st = (cudaStream_t)stream;
   c->alloc_stream = st;
+  bool somm = false;
+  for (int a = 0; a < grid->dim; ++a) somm = somm || grid->n_layer[a][1] < 0;
   if (k->phi) {
     long n = 1;
-    for (int a = 0; a < grid->dim; ++a) {
-      int lo = grid->n_layer[a][0], hi = grid->n_layer[a][1];
-      n *= (long)grid->n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
-    }
-    for (long i = 0; i < n; ++i)
+    for (int a = 0; a < grid->dim; ++a) n *= axis_unknowns(grid->n_int[a], grid->n_layer[a][0], grid->n_layer[a][1]);
+    for (long i = 0; i < n; ++i) {
       if (!std::isfinite(k->phi[i])) { delete c; set_error("phi has a non-finite entry"); return HELM_ERR_ARG; }
+      // a Sommerfeld boundary needs the real wave number k = sqrt(phi)
+      if (somm && k->phi[i] < 0.0) { delete c; set_error("phi < 0 with a Sommerfeld side"); return HELM_ERR_ARG; }
+    }
   }
   if ((s = build_operator(c, k, st)) != HELM_OK) { ctx_release(c); return s; }
   if ((s = build_hierarchy(c, st)) != HELM_OK) { ctx_release(c); return s; }

@@ -80,7 +80,32 @@ template <typename T> struct OpView {
   const cx<T>* st9;   // Galerkin level (2D): weight k = 3 (dj + 1) + (di + 1) of unknown p at
                       // st9[k * ntot + p]; nullptr for a Shortley-Weller level
   long ntot;
+  int somm;           // bit a: the last unknown of axis a is a Sommerfeld boundary node
+  double2 bt[3];      // its boundary weight 2i / h_l (the diagonal gains bt * sqrt(phi))
 };
+
+// Sommerfeld boundary part of the diagonal at (i, j, l) (Section 2, eq. "sommerfeld1", by a
+// mirrored ghost node): sum over the axes whose last unknown this is of 2 i k / h_l, with
+// k = sqrt(phi) the unshifted wave number.  FP64; zero away from such nodes.
+template <typename T>
+__host__ __device__ inline double2 somm_diag(const OpView<T>& op, int i, int j, int l, double ph) {
+  double2 d = {0.0, 0.0};
+  if (!op.somm) return d;
+  const int idx[3] = {i, j, l};
+  for (int a = 0; a < 3; ++a)
+    if (((op.somm >> a) & 1) && idx[a] == op.n[a] - 1) {
+      const double k = sqrt(ph);
+      d.x += op.bt[a].x * k;
+      d.y += op.bt[a].y * k;
+    }
+  return d;
+}
+
+// Unknowns along one axis: interior nodes minus Dirichlet walls, plus m + 1 per ECS layer of m
+// nodes, plus the boundary node of a Sommerfeld high side (hi = -1).
+inline long axis_unknowns(int n_int, int lo, int hi) {
+  return (long)n_int - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
+}
 
 // ---- owned device storage of one level ---------------------------------------------------
 struct LevelHost {
@@ -108,6 +133,9 @@ struct LevelHost {
   // Galerkin coarse operator (2D, 9-point), [9][ntot]; FP64 always, FP32 copy for FP32 multigrid
   double2* st9_64 = nullptr;
   float2* st9_32 = nullptr;
+  // Sommerfeld high sides: bit a set when the last unknown of axis a is the boundary node
+  int somm = 0;
+  double2 bt[3] = {};
   // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, -1 by the block-count rule
   int tile_down = -1, tile_up = -1;
   // work vectors (MG type), allocated for multigrid levels

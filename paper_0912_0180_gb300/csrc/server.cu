@@ -39,8 +39,7 @@ static double now_s() {
 }
 
 static long axis_n(const helm_grid& g, int a) {
-  int lo = g.n_layer[a][0], hi = g.n_layer[a][1];
-  return (long)g.n_int[a] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+  return axis_unknowns(g.n_int[a], g.n_layer[a][0], g.n_layer[a][1]);
 }
 
 }  // namespace helm

@@ -19,10 +19,11 @@ namespace helm {
 // last ones) are h e^{i theta_gamma} * scale_ly, except, with a ramp of R > 1 widths, the m-th
 // layer width from the turning point for m < R, which turns by only theta_gamma * m / R.
 __global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_layer,
-                            double2 w_int, int ramp, double h, double theta_g, double2 scale_ly) {
+                            double2 w_int, int ramp, double h, double theta_g, double2 scale_ly,
+                            int somm) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ngap) return;
-  if (j >= nlo && j < nlo + nin) {
+  if ((j >= nlo && j < nlo + nin) || (somm && j == ngap - 1)) {  // a Sommerfeld ghost mirrors h
     gap[j] = w_int;
     return;
   }
@@ -38,11 +39,13 @@ __global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_
 // coarse width c = fine widths 2c and 2c+1; the last coarse width reaches the fine Dirichlet
 // node and gathers the remaining one or two fine widths.
 __global__ void k_axis_coarsen(const double2* __restrict__ gf, int nf, double2* __restrict__ gc,
-                               int nc) {
+                               int nc, int somm) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c > nc) return;
   if (c < nc) {
     gc[c] = cadd<double>(gf[2 * c], gf[2 * c + 1]);
+  } else if (somm) {  // the ghost width mirrors the last coarse width (nf even: 2nc = nf)
+    gc[c] = cadd<double>(gf[2 * c - 2], gf[2 * c - 1]);
   } else {
     double2 acc = mkc<double>(0.0, 0.0);
     for (int j = 2 * nc; j <= nf; ++j) acc = cadd<double>(acc, gf[j]);
@@ -52,8 +55,11 @@ __global__ void k_axis_coarsen(const double2* __restrict__ gf, int nf, double2* 
 
 // Shortley-Weller row of -d^2/dz^2 at unknown j with left width hl, right width hr:
 //   am = -2 / (hl (hl + hr)),  a0 = 2 / (hl hr),  ap = -2 / (hr (hl + hr)).
+// A Sommerfeld boundary node (somm, last row): the mirrored ghost u_g = u_{N-1} - 2 i k h_l u_N
+// folds into the row, doubling the left weight and removing the right one (its diagonal part
+// 2 i k / h_l is added where the diagonal is formed).
 __global__ void k_axis_coeffs(const double2* __restrict__ gap, int n, double2* am, double2* a0,
-                              double2* ap, float2* am32, float2* a032, float2* ap32) {
+                              double2* ap, float2* am32, float2* a032, float2* ap32, int somm) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double2 hl = gap[j], hr = gap[j + 1];
@@ -65,6 +71,10 @@ __global__ void k_axis_coeffs(const double2* __restrict__ gap, int n, double2* a
   am[j] = mkc<double>(-m.x, -m.y);
   a0[j] = c;
   ap[j] = mkc<double>(-p.x, -p.y);
+  if (somm && j == n - 1) {
+    am[j] = mkc<double>(-2.0 * m.x, -2.0 * m.y);
+    ap[j] = mkc<double>(0.0, 0.0);
+  }
   if (am32) {
     am32[j] = cconv<float, double>(am[j]);
     a032[j] = cconv<float, double>(c);
@@ -103,6 +113,7 @@ __global__ void k_dinv(OpView<double> op, double omega_s, double2* d64, float2* 
   if (DIM > 1) d = cadd<double>(d, op.a0[1][j]);
   if (DIM > 2) d = cadd<double>(d, op.a0[2][l]);
   double ph = op.phi ? op.phi[p] : op.phi0;
+  d = cadd<double>(d, somm_diag(op, i, j, l, ph));
   d = csub<double>(d, cscale<double>(ph, op.s));
   double2 r = cscale<double>(omega_s, crecip<double>(d));
   if (d64) d64[p] = r;
@@ -134,6 +145,7 @@ __global__ void k_dense_assemble(OpView<double> op, int dim, double2* A, int n) 
   double2 d = op.a0[0][i];
   if (dim > 1) d = cadd<double>(d, op.a0[1][j]);
   if (dim > 2) d = cadd<double>(d, op.a0[2][l]);
+  d = cadd<double>(d, somm_diag(op, i, j, l, ph));
   d = csub<double>(d, cscale<double>(ph, op.s));
   row[p] = d;
   if (i > 0) row[p - 1] = op.am[0][i];
@@ -225,7 +237,8 @@ __device__ double2 fine_entry(const OpView<double>& F, int i, int j, int ii, int
   if (F.st9) return F.st9[(long)(3 * (dj + 1) + (di + 1)) * F.ntot + p];
   if (di == 0 && dj == 0) {
     double ph = F.phi ? F.phi[p] : F.phi0;
-    return csub<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), cscale<double>(ph, F.s));
+    double2 d = cadd<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), somm_diag(F, i, j, 0, ph));
+    return csub<double>(d, cscale<double>(ph, F.s));
   }
   if (di != 0 && dj != 0) return mkc<double>(0.0, 0.0);  // a 5-point row has no corner weights
   if (dj == 0) return di < 0 ? F.am[0][i] : F.ap[0][i];
@@ -406,7 +419,8 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
   for (int a = 0; a < 3; ++a) L.n[a] = 1;
   for (int a = 0; a < g.dim; ++a) {
     int lo = g.n_layer[a][0], hi = g.n_layer[a][1];
-    int nlo = lo > 0 ? lo + 1 : 0, nhi = hi > 0 ? hi + 1 : 0;
+    const int somm = hi < 0;  // Sommerfeld high side: one mirrored width to the ghost node
+    int nlo = lo > 0 ? lo + 1 : 0, nhi = hi > 0 ? hi + 1 : (somm ? 1 : 0);
     int nin = g.n_int[a] - 1;
     int ngap = nlo + nin + nhi;
     int n = ngap - 1;
@@ -421,10 +435,14 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
       if (want32 && (s = ctx_alloc(c, (void**)&L.coef32[a][k], sizeof(float2) * n)) != HELM_OK) return s;
     }
     k_axis_gaps<<<ceil_div(ngap, 256), 256, 0, st>>>(L.gap[a], ngap, nlo, nin, wl, wi, g.ecs_ramp, h,
-                                                     g.theta_gamma, scale_ly);
+                                                     g.theta_gamma, scale_ly, somm);
     k_axis_coeffs<<<ceil_div(n, 256), 256, 0, st>>>(L.gap[a], n, L.coef64[a][0], L.coef64[a][1],
                                                     L.coef64[a][2], L.coef32[a][0], L.coef32[a][1],
-                                                    L.coef32[a][2]);
+                                                    L.coef32[a][2], somm);
+    if (somm) {  // boundary weight 2i / h_l, h_l = the last (interior) width
+      L.somm |= 1 << a;
+      L.bt[a] = cdiv<double>(mkc<double>(0.0, 2.0), wi);
+    }
     HELM_CUDA(cudaGetLastError());
     L.n[a] = n;
     L.ntot *= n;
@@ -504,6 +522,8 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.dg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dg64 : (const cx<T>*)(const void*)dg32;
   v.st9 = std::is_same<T, double>::value ? (const cx<T>*)(const void*)st9_64 : (const cx<T>*)(const void*)st9_32;
   v.ntot = ntot;
+  v.somm = somm;
+  for (int a = 0; a < 3; ++a) v.bt[a] = bt[a];
   return v;
 }
 template OpView<double> LevelHost::view<double>() const;
@@ -572,21 +592,29 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       if (F.n[a] > pc.coarse_max) all_small = false;
       if (F.n[a] < min_n) min_n = F.n[a];
     }
-    if (all_small || min_n < 3) break;
+    // a Sommerfeld axis keeps its boundary node (fine 2c+1 = n-1) only when n is even
+    bool odd_somm = false;
+    for (int a = 0; a < F.dim; ++a)
+      if (((F.somm >> a) & 1) && (F.n[a] & 1)) odd_somm = true;
+    if (all_small || min_n < 3 || odd_somm) break;
     LevelHost C;
     C.dim = F.dim;
     C.ntot = 1;
+    C.somm = F.somm;
     for (int a = 0; a < F.dim; ++a) {
       int nf = F.n[a], nc = nf / 2;
+      const int somm = (F.somm >> a) & 1;
       if ((rc = ctx_alloc(c, (void**)&C.gap[a], sizeof(double2) * (nc + 1))) != HELM_OK) return rc;
       for (int k = 0; k < 3; ++k) {
         if ((rc = ctx_alloc(c, (void**)&C.coef64[a][k], sizeof(double2) * nc)) != HELM_OK) return rc;
         if (f32 && (rc = ctx_alloc(c, (void**)&C.coef32[a][k], sizeof(float2) * nc)) != HELM_OK) return rc;
       }
-      k_axis_coarsen<<<ceil_div(nc + 1, 256), 256, 0, st>>>(F.gap[a], nf, C.gap[a], nc);
+      k_axis_coarsen<<<ceil_div(nc + 1, 256), 256, 0, st>>>(F.gap[a], nf, C.gap[a], nc, somm);
       k_axis_coeffs<<<ceil_div(nc, 256), 256, 0, st>>>(C.gap[a], nc, C.coef64[a][0], C.coef64[a][1],
                                                        C.coef64[a][2], C.coef32[a][0],
-                                                       C.coef32[a][1], C.coef32[a][2]);
+                                                       C.coef32[a][1], C.coef32[a][2], somm);
+      // the last coarse width is the sum of the two last fine ones, both h_l: 2i / (2 h_l)
+      C.bt[a] = somm ? mkc<double>(0.5 * F.bt[a].x, 0.5 * F.bt[a].y) : mkc<double>(0.0, 0.0);
       C.n[a] = nc;
       C.ntot *= nc;
     }
@@ -642,7 +670,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
   // constant phi on a large coarsest level: the separable exact solve, no dense inverse
-  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.st9_64) {
+  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.st9_64 && !Cst.somm) {
     if ((rc = fdm_build(c, Cst, f32, st)) != HELM_OK) return rc;
     if (c->fdm.on) {
       c->nco = 0;

@@ -639,3 +639,111 @@ def test_gmres_full_and_batch():
         hs[0].solve(cu(p.b), method=hi.GMRES, s=129)
     for h in hs:
         h.close()
+
+
+# First-order Sommerfeld condition on high sides (n_layer = -1): unknown counts even over
+# several levels so that coarsening keeps the boundary node (fine 2c+1 = n-1), ragged shapes,
+# ECS layers on some low sides, a bump k.
+SOMM_CASES = [
+    # dim, n_int, layers, theta, k0, phi kind
+    (1, 48, (6, -1), 0.5, 9.0, "bump"),                                   # 54 unknowns
+    (2, (44, 49), ((4, -1), (0, -1)), 0.5, 12.0, "bump"),                 # 48 x 48
+    (2, (65, 33), ((0, -1), (7, 0)), 0.4, 14.0, "const"),                 # 64 x 39
+    (3, (13, 14, 12), ((0, -1), (2, -1), (0, 0)), 0.5, 5.0, "bump"),      # 12 x 16 x 10
+]
+SOMM_PCS = [
+    hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5),
+    hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=-0.3, smoother=hi.SM_RBGS),
+]
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("pci", range(len(SOMM_PCS)))
+@pytest.mark.parametrize("case", SOMM_CASES)
+def test_sommerfeld_operator_levels_and_vcycle(case, pci, mg):
+    """The Sommerfeld boundary rows: H itself, every level's operator (the ghost-node row with its
+    2 i k / h_l diagonal on each coarse grid), the smoother, and the whole V-cycle, fused and
+    one kernel per component, against the oracle."""
+    p = _problem(case)
+    pc = SOMM_PCS[pci]
+    o = Oracle(p, pc)
+    if mg == "c128":
+        h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+        x = hi.random_vector(p.n, 3)
+        assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+        h0.close()
+    h = Helm(p, pc, mg_dtype=mg)
+    assert h.nlev == o.nlev and o.nlev >= 2
+    dt = torch.complex128 if mg == "c128" else torch.complex64
+    tol = 1e-11 if mg == "c128" else 2e-5
+    for lvl in range(o.nlev - 1):
+        n = o.level_size(1, lvl)
+        a = hi.random_vector(n, 9 + lvl).astype(np.complex64).astype(np.complex128)
+        b = hi.random_vector(n, 19 + lvl).astype(np.complex64).astype(np.complex128)
+        out = torch.empty(n, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
+        assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+        u = cu(a, dt)
+        h.level_op(L.HELM_OP_SMOOTH, lvl, u, cu(b, dt), None, count=2)
+        assert rel(u.cpu().numpy(), o.smooth(lvl, a, b, 2)) < tol
+    nco = o.level_size(1, o.nlev - 1)
+    a = hi.random_vector(nco, 5)
+    out = torch.empty(nco, dtype=dt, device="cuda")
+    h.level_op(L.HELM_OP_COARSE, o.nlev - 1, cu(a, dt), None, out)
+    assert rel(out.cpu().numpy(), o.coarse_solve(a)) < (1e-10 if mg == "c128" else 1e-4)
+    r = hi.random_vector(p.n, 21)
+    for fused in (True, False):
+        hf = h if fused else Helm(p, pc, mg_dtype=mg, fused=False)
+        z = hf.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
+        assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+        if not fused:
+            hf.close()
+    h.close()
+
+
+@pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR, hi.GMRES])
+@pytest.mark.parametrize("case", SOMM_CASES[1:3])
+def test_sommerfeld_solve_matches_oracle(case, method):
+    """FP64 solves of Sommerfeld problems against the oracle (matvecs within 2, solution to 1e-9),
+    the FP32-multigrid path certified by its FP64 true residual, and Galerkin coarse operators
+    built from the Sommerfeld rows (2D)."""
+    p = _problem(case, rhs="gauss", seed=29)
+    pc = SOMM_PCS[0]
+    o = Oracle(p, pc)
+    sh = hi.shadow_space(p.n, 4) if method == hi.IDR else None
+    s = 60 if method == hi.GMRES else 4  # few GMRES cycles, so that the matvec counts stay close
+    xo, io = o.solve(p.b, hi.SolveOpts(method=method, s=s, tol=1e-10, maxmv=3000), shadow=sh)
+    h = Helm(p, pc, mg_dtype="c128")
+    x, info = h.solve(cu(p.b), method=method, s=s, tol=1e-10, maxmv=3000, shadow=sh)
+    assert info.status == 0 and io["status"] == 0
+    assert abs(info.matvecs - io["matvecs"]) <= 2
+    assert rel(x.cpu().numpy(), xo) < 1e-9
+    h.close()
+    h32 = Helm(p, pc, mg_dtype="c64")
+    x3, i3 = h32.solve(cu(p.b), method=method, s=s, tol=1e-7, maxmv=3000, shadow=sh)
+    assert i3.status == 0 and i3.rel_res_true < 1e-7
+    h32.close()
+    if method == hi.BICGSTAB:
+        pg = hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5, galerkin=True)
+        og = Oracle(p, pg)
+        hg = Helm(p, pg, mg_dtype="c128")
+        for lvl in range(og.nlev):
+            xx = hi.random_vector(og.level_size(1, lvl), 40 + lvl)
+            y = hg.level_op(L.HELM_OP_APPLY, lvl, cu(xx), None, torch.empty(len(xx), dtype=torch.complex128, device="cuda"))
+            assert rel(y.cpu().numpy(), og.apply(xx, 1, lvl)) < 1e-12
+        xg, ig = hg.solve(cu(p.b), tol=1e-10, maxmv=3000)
+        xgo, igo = og.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
+        assert ig.status == 0 and igo["status"] == 0 and rel(xg.cpu().numpy(), xgo) < 1e-9
+        hg.close()
+
+
+def test_sommerfeld_arguments():
+    """A Sommerfeld low side and a negative phi at a Sommerfeld grid are refused."""
+    from paper_0912_0180_gb300.helm import HelmError
+    p = hi.make_problem(2, 17, ((-1, 0), (0, 0)), k0=3.0, rhs="zero")
+    with pytest.raises(HelmError):
+        Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+    q = hi.make_problem(2, 17, ((0, -1), (0, 0)), k0=3.0, rhs="zero")
+    q.phi = np.full(q.n, -1.0)
+    with pytest.raises(HelmError):
+        Helm(q, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
