@@ -15,6 +15,9 @@
             once, {Bi-CGSTAB, IDR(4), IDR(8)} x {CSL, CSG} with the shift and angle of the paper's
             ECS rows and its Galerkin coarse operators (omega-Jacobi V(1,1) here, not the paper's
             ILU(0) V(0,1), so the paper's matvec counts, reported beside ours, are context).
+  mp2som, mp3som  the same problems with the first-order Sommerfeld condition on the east / north
+            edges instead of layers (the paper's Sommerfeld rows: shift 1 - 0.35i / 1 - 0.38i, angle
+            -pi/20 / -pi/17).
   mp2s      mp2 on the smooth ECS contour of the paper's Section 7 remark (the layer widths turn by
             theta_gamma / 128 per width over the whole 128-node layer).
   gmres     the paper's GMRES remark: MP2 (nu = 1, k = 4, ECS) to 1e-7 with GMRES(128), GMRES(30),
@@ -81,6 +84,7 @@ def run(args):
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
     fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+          "mp2som": run_mp, "mp3som": run_mp,
           "select": run_select, "gmres": run_gmres}[args.workload]
     line = fn(args, torch, ranks, dev, local)
     if rank == 0:
@@ -449,6 +453,14 @@ MP_CASES = {
     "mp3": {"problem": lambda: hi.workload_mp3(), "csl": 1 + 0.38j, "csg": np.pi / 17,
             "paper_matvecs": {"csl": {"bicgstab": 142, "idr4": 145, "idr8": 141},
                               "csg": {"bicgstab": 139, "idr4": 139, "idr8": 134}}},
+    # the Sommerfeld rows: first-order condition on the east / north edges instead of layers; the
+    # spectrum sits in the first quadrant, so the shift's imaginary part and the angle flip sign
+    "mp2som": {"problem": lambda: hi.workload_mp2(n_l=-1), "csl": 1 - 0.35j, "csg": -np.pi / 20,
+               "paper_matvecs": {"csl": {"bicgstab": 123, "idr4": 120, "idr8": 122},
+                                 "csg": {"bicgstab": 113, "idr4": 115, "idr8": 115}}},
+    "mp3som": {"problem": lambda: hi.workload_mp3(n_l=-1), "csl": 1 - 0.38j, "csg": -np.pi / 17,
+               "paper_matvecs": {"csl": {"bicgstab": 207, "idr4": 214, "idr8": 232},
+                                 "csg": {"bicgstab": 205, "idr4": 207, "idr8": 207}}},
 }
 
 
@@ -501,7 +513,9 @@ def run_mp(args, torch, ranks, dev, local):
            "solves": "{Bi-CGSTAB, IDR(4), IDR(8)} x {CSL shift %s, CSG theta_beta %.4f}, run at once"
                      % (case["csl"], case["csg"]),
            "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, Galerkin coarse operators R A P",
-           "boundaries": "Dirichlet south / west, ECS layers east / north (theta_gamma = pi/6)",
+           "boundaries": "Dirichlet south / west, " + ("first-order Sommerfeld east / north"
+                                                        if args.workload.endswith("som") else
+                                                        "ECS layers east / north (theta_gamma = pi/6)"),
            "l2": "flushed (512 MiB device write) before every timed step"}
     line = _base(args, ranks.job_rate(done(res["c128"][1]), res["c128"][0]), res["c128"][0], ranks.world, cfg, "c128")
     line.update({

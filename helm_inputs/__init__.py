@@ -201,10 +201,13 @@ def workload_mp2(nu: float = 7.0, k: float = 2.0, n_int: int = 385, n_l: int = 1
                  theta_gamma: float = np.pi / 6, ecs_ramp: int = 0) -> Problem:
     """The paper's model problem 2 (Section 4, eq. "MP2"): phi = nu (e^{-x^2} + e^{-y^2}) + k^2,
     source chi = e^{-(x^2 + y^2)} on [0, r]^2, Dirichlet on the south / west edges (x = 0, y = 0) and
-    ECS layers of n_l nodes on the east / north edges.  Defaults: the paper's 384^2 interior grid
-    with 128 layer nodes (512^2 unknowns).  ecs_ramp > 1 turns the contour gradually (Section 7's
-    smooth ECS transition)."""
+    ECS layers of n_l nodes on the east / north edges (n_l = -1: the first-order Sommerfeld
+    condition there instead, eq. "BC").  Defaults: the paper's 384^2 interior grid with 128 layer
+    nodes (512^2 unknowns; 384^2 with Sommerfeld edges).  ecs_ramp > 1 turns the contour gradually
+    (Section 7's smooth ECS transition)."""
     tag = f"-ramp{ecs_ramp}" if ecs_ramp > 1 else ""
+    if n_l < 0:
+        tag += "-sommerfeld"
     return make_problem(2, n_int, ((0, n_l), (0, n_l)), extent=r, theta_gamma=theta_gamma, k0=k,
                         ecs_ramp=ecs_ramp,
                         phi_kind="field", rhs="field", name=f"mp2-nu{nu:g}-k{k:g}-{n_int - 1}sq-L{n_l}{tag}",
@@ -216,10 +219,11 @@ def workload_mp3(r: float = 90.0, k: float = 2.0, n_int: int = 1025, n_l: int = 
                  theta_gamma: float = np.pi / 6) -> Problem:
     """The paper's model problem 3 (Section 4, eq. "MP3"): phi = 1/x + 1/y + k^2 (singular at the
     origin, which is a Dirichlet node here, so no unknown sits on it), chi = e^{-(x^2 + y^2)} on
-    [0, r]^2, Dirichlet south / west, ECS layers east / north.  Defaults: r = 90 with the paper's
-    1024^2 interior grid and 256 layer nodes (1280^2 unknowns)."""
+    [0, r]^2, Dirichlet south / west, ECS layers east / north (n_l = -1: Sommerfeld edges).
+    Defaults: r = 90 with the paper's 1024^2 interior grid and 256 layer nodes (1280^2 unknowns)."""
+    tag = "-sommerfeld" if n_l < 0 else ""
     return make_problem(2, n_int, ((0, n_l), (0, n_l)), extent=r, theta_gamma=theta_gamma, k0=k,
-                        phi_kind="field", rhs="field", name=f"mp3-r{r:g}-k{k:g}-{n_int - 1}sq-L{n_l}",
+                        phi_kind="field", rhs="field", name=f"mp3-r{r:g}-k{k:g}-{n_int - 1}sq-L{n_l}{tag}",
                         phi_fn=lambda x, y: 1.0 / x + 1.0 / y + k * k,
                         rhs_fn=lambda x, y: np.exp(-(x * x + y * y)))
 
