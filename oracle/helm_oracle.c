@@ -100,6 +100,7 @@ typedef struct {
   cplx s;         /* sigma = s * phi; 1 for H and CSG, beta^2 for CSL */
   cplx* st9;      /* Galerkin levels (2D): row p is st9[9p + 3(dj+1) + (di+1)], the weight of the
                      unknown (i+di, j+dj); NULL for a Shortley-Weller level */
+  cplx* st27;     /* Galerkin levels (3D): row p is st27[27p + 9(dl+1) + 3(dj+1) + (di+1)] */
 } level_t;
 
 typedef struct orc_ctx {
@@ -204,6 +205,7 @@ static void axis_free(axis_t* a) {
 
 static void level_free(level_t* L) {
   free(L->st9);
+  free(L->st27);
   for (int d = 0; d < L->dim; ++d) axis_free(&L->ax[d]);
   free(L->phi);
 }
@@ -256,6 +258,7 @@ static void level_coarse(const level_t* F, level_t* C) {
  * (a Galerkin level: its stencil's centre weight). */
 static cplx diag_at(const level_t* L, int i, int j, int l) {
   if (L->st9) return L->st9[9 * lidx(L, i, j, l) + 4];
+  if (L->st27) return L->st27[27 * lidx(L, i, j, l) + 13];
   int ix[3] = {i, j, l};
   cplx d = 0;
   double ph = L->phi[lidx(L, i, j, l)];
@@ -279,6 +282,19 @@ static cplx offdiag_at(const level_t* L, const cplx* x, int i, int j, int l) {
         if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) continue;
         acc += w[3 * (dj + 1) + (di + 1)] * x[lidx(L, ii, jj, 0)];
       }
+    return acc;
+  }
+  if (L->st27) {  /* the 26 neighbours of a 3D Galerkin stencil */
+    cplx acc = 0;
+    const cplx* w = L->st27 + 27 * lidx(L, i, j, l);
+    for (int dl = -1; dl <= 1; ++dl)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if (di == 0 && dj == 0 && dl == 0) continue;
+          int ii = i + di, jj = j + dj, ll = l + dl;
+          if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1] || ll < 0 || ll >= L->n[2]) continue;
+          acc += w[9 * (dl + 1) + 3 * (dj + 1) + (di + 1)] * x[lidx(L, ii, jj, ll)];
+        }
     return acc;
   }
   int ix[3] = {i, j, l};
@@ -350,6 +366,20 @@ static void level_dense(const level_t* L, cplx* A) {
             if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) continue;
             A[lidx(L, i, j, 0) * n + lidx(L, ii, jj, 0)] = L->st9[9 * lidx(L, i, j, 0) + 3 * (dj + 1) + (di + 1)];
           }
+    return;
+  }
+  if (L->st27) {
+    for (int l = 0; l < L->n[2]; ++l)
+      for (int j = 0; j < L->n[1]; ++j)
+        for (int i = 0; i < L->n[0]; ++i)
+          for (int dl = -1; dl <= 1; ++dl)
+            for (int dj = -1; dj <= 1; ++dj)
+              for (int di = -1; di <= 1; ++di) {
+                int ii = i + di, jj = j + dj, ll = l + dl;
+                if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1] || ll < 0 || ll >= L->n[2]) continue;
+                A[lidx(L, i, j, l) * n + lidx(L, ii, jj, ll)] =
+                    L->st27[27 * lidx(L, i, j, l) + 9 * (dl + 1) + 3 * (dj + 1) + (di + 1)];
+              }
     return;
   }
   for (int l = 0; l < L->n[2]; ++l)
@@ -426,6 +456,55 @@ static void level_galerkin(const level_t* F, level_t* C) {
         }
 }
 
+/* Entry (row p, column q) of a 3D level's operator, by its definition. */
+static cplx entry3d(const level_t* L, int i, int j, int l, int ii, int jj, int ll) {
+  if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1] || ll < 0 || ll >= L->n[2]) return 0;
+  int di = ii - i, dj = jj - j, dl = ll - l;
+  if (L->st27) {
+    if (di < -1 || di > 1 || dj < -1 || dj > 1 || dl < -1 || dl > 1) return 0;
+    return L->st27[27 * lidx(L, i, j, l) + 9 * (dl + 1) + 3 * (dj + 1) + (di + 1)];
+  }
+  if (di == 0 && dj == 0 && dl == 0) return diag_at(L, i, j, l);
+  if (dj == 0 && dl == 0 && di == -1) return L->ax[0].am[i];
+  if (dj == 0 && dl == 0 && di == 1) return L->ax[0].ap[i];
+  if (di == 0 && dl == 0 && dj == -1) return L->ax[1].am[j];
+  if (di == 0 && dl == 0 && dj == 1) return L->ax[1].ap[j];
+  if (di == 0 && dj == 0 && dl == -1) return L->ax[2].am[l];
+  if (di == 0 && dj == 0 && dl == 1) return L->ax[2].ap[l];
+  return 0;
+}
+
+/* Galerkin coarse operator (3D): C = R F P as in 2D, with the full weighting and the trilinear
+ * interpolation tensorised over three axes; only coarse neighbours within one index on every
+ * axis can be non-zero (the 27-point result).  (I,J,L) = (ci,cj,cl), (K,M,N) = (ck,cm,cn). */
+static void level_galerkin3d(const level_t* F, level_t* C) {
+  C->st27 = calloc(27 * (size_t)imax(C->ntot, 1), sizeof(cplx));
+  for (int cl = 0; cl < C->n[2]; ++cl)
+    for (int cj = 0; cj < C->n[1]; ++cj)
+      for (int ci = 0; ci < C->n[0]; ++ci)
+        for (int dn = -1; dn <= 1; ++dn)
+          for (int dm = -1; dm <= 1; ++dm)
+            for (int dk = -1; dk <= 1; ++dk) {
+              int ck = ci + dk, cm = cj + dm, cn = cl + dn;
+              if (ck < 0 || ck >= C->n[0] || cm < 0 || cm >= C->n[1] || cn < 0 || cn >= C->n[2]) continue;
+              cplx acc = 0;
+              for (int e = 2 * cl; e <= 2 * cl + 2; ++e)
+                for (int b = 2 * cj; b <= 2 * cj + 2; ++b)
+                  for (int a = 2 * ci; a <= 2 * ci + 2; ++a) {
+                    if (a >= F->n[0] || b >= F->n[1] || e >= F->n[2]) continue;
+                    double r = fw_weight(a, ci) * fw_weight(b, cj) * fw_weight(e, cl);
+                    for (int g = e - 1; g <= e + 1; ++g)
+                      for (int d = b - 1; d <= b + 1; ++d)
+                        for (int c2 = a - 1; c2 <= a + 1; ++c2) {
+                          double pw = lin_weight(c2, ck) * lin_weight(d, cm) * lin_weight(g, cn);
+                          if (pw == 0.0) continue;
+                          acc += r * entry3d(F, a, b, e, c2, d, g) * pw;
+                        }
+                  }
+              C->st27[27 * lidx(C, ci, cj, cl) + 9 * (dn + 1) + 3 * (dm + 1) + (dk + 1)] = acc;
+            }
+}
+
 /* ---- context ------------------------------------------------------------------------- */
 orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_precond* pc) {
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
@@ -456,6 +535,7 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_p
     if (all_small || min_n < 3 || odd_somm) break;
     level_coarse(F, &c->M[c->nlev]);
     if (pc->galerkin && g->dim == 2) level_galerkin(F, &c->M[c->nlev]);
+    if (pc->galerkin && g->dim == 3) level_galerkin3d(F, &c->M[c->nlev]);
     c->nlev++;
   }
   level_t* C = &c->M[c->nlev - 1];
@@ -507,6 +587,11 @@ void orc_level_st9(const orc_ctx* c, int lvl, cplx* out) {
   const level_t* L = pick(c, 1, lvl);
   if (L->st9) memcpy(out, L->st9, sizeof(cplx) * 9 * L->ntot);
   else memset(out, 0, sizeof(cplx) * 9 * L->ntot);
+}
+void orc_level_st27(const orc_ctx* c, int lvl, cplx* out) {
+  const level_t* L = pick(c, 1, lvl);
+  if (L->st27) memcpy(out, L->st27, sizeof(cplx) * 27 * L->ntot);
+  else memset(out, 0, sizeof(cplx) * 27 * L->ntot);
 }
 
 void orc_apply(const orc_ctx* c, int which, int lvl, const cplx* x, cplx* y) {

@@ -71,6 +71,7 @@ def _load():
         lib.orc_axis_tables.argtypes = [vp, ip, ip, ip, vp, vp, vp, vp, vp]
         lib.orc_level_phi.argtypes = [vp, ip, ip, vp, vp]
         lib.orc_level_st9.argtypes = [vp, ip, vp]
+        lib.orc_level_st27.argtypes = [vp, ip, vp]
         lib.orc_apply.argtypes = [vp, ip, ip, vp, vp]
         lib.orc_dense.argtypes = [vp, ip, ip, vp]
         lib.orc_vcycle.argtypes = [vp, vp, vp]
@@ -193,6 +194,14 @@ class Oracle:
         out = np.zeros(9 * m, np.complex128)
         _lib.orc_level_st9(self._h, lvl, _ptr(out))
         return out.reshape(m, 3, 3)
+
+    def level_stencil27(self, lvl):
+        """Galerkin 27-point stencil of preconditioner level lvl (3D), shape (ntot, 3, 3, 3)
+        indexed [p, dl+1, dj+1, di+1]; zeros for a Shortley-Weller level."""
+        m = self.level_size(1, lvl)
+        out = np.zeros(27 * m, np.complex128)
+        _lib.orc_level_st27(self._h, lvl, _ptr(out))
+        return out.reshape(m, 3, 3, 3)
 
     def apply(self, x, which=0, lvl=0):
         x = _c128(x)

@@ -806,3 +806,60 @@ def test_sommerfeld_mg_preconditioned_solve_reaches_direct_solution():
     assert info["status"] == 0
     xd = o.dense_solve(p.b)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+# ---- 3D Galerkin coarse operators (27-point R A P) ---------------------------------------------
+
+def _stencil27_to_dense(st, n0, n1, n2):
+    n = n0 * n1 * n2
+    A = np.zeros((n, n), np.complex128)
+    for l in range(n2):
+        for j in range(n1):
+            for i in range(n0):
+                p = i + n0 * (j + n1 * l)
+                for dl in (-1, 0, 1):
+                    for dj in (-1, 0, 1):
+                        for di in (-1, 0, 1):
+                            ii, jj, ll = i + di, j + dj, l + dl
+                            if 0 <= ii < n0 and 0 <= jj < n1 and 0 <= ll < n2:
+                                A[p, ii + n0 * (jj + n1 * ll)] = st[p, dl + 1, dj + 1, di + 1]
+    return A
+
+
+def test_galerkin3d_coarse_operator_is_R_A_P():
+    """3D: every Galerkin level equals R A P with R, P the Kronecker products of the 1D full
+    weighting and linear interpolation (x fastest), on a complex CSG / ECS grid with one-sided
+    layers, a Sommerfeld side and a variable k; level 2 is the operator of a 27-point level."""
+    p = hi.make_problem(3, (13, 11, 13), ((2, 0), (0, 3), (0, -1)), theta_gamma=0.5, k0=4.0,
+                        phi_kind="bump", rhs="zero")  # 14 x 13 x 12 unknowns
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, galerkin=True,
+                    coarse_max=2)
+    o = Oracle(p, pc)
+    assert o.nlev >= 3
+    for lvl in range(1, o.nlev):
+        nf = o.level_shape(1, lvl - 1)
+        nc = o.level_shape(1, lvl)
+        R = np.kron(_fw_matrix(nf[2], nc[2]), np.kron(_fw_matrix(nf[1], nc[1]), _fw_matrix(nf[0], nc[0])))
+        P = np.kron(_lin_matrix(nf[2], nc[2]), np.kron(_lin_matrix(nf[1], nc[1]), _lin_matrix(nf[0], nc[0])))
+        RAP = R @ o.dense(1, lvl - 1) @ P
+        C = _stencil27_to_dense(o.level_stencil27(lvl), *nc)
+        assert np.abs(C - RAP).max() <= 1e-12 * np.abs(RAP).max()
+        assert np.abs(o.dense(1, lvl) - C).max() == 0.0
+
+
+def test_galerkin3d_laplacian_closed_form():
+    """Uniform Dirichlet cube, k = 0: the 3D Galerkin Laplacian is A (x) M (x) M + M (x) A (x) M +
+    M (x) M (x) A with the 1D Galerkin rows a = R a1 P and mass m = R P."""
+    n = 7
+    p = hi.make_problem(3, n + 2, 0, theta_gamma=0.0, k0=0.0, rhs="zero")
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1.0, smoother=hi.SM_JACOBI, galerkin=True, max_levels=2,
+                    coarse_max=2)
+    o = Oracle(p, pc)
+    assert o.nlev == 2
+    h = 1.0 / (n + 1)
+    a1 = (np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)) / h ** 2
+    R, P = _fw_matrix(n, n // 2), _lin_matrix(n, n // 2)
+    ac, mc = R @ a1 @ P, R @ P
+    kron3 = lambda z, y, x: np.kron(z, np.kron(y, x))
+    ref = kron3(mc, mc, ac) + kron3(mc, ac, mc) + kron3(ac, mc, mc)
+    assert np.allclose(o.dense(1, 1), ref, rtol=1e-12, atol=1e-9)
