@@ -130,10 +130,11 @@ typedef struct {
  * change the speed only (every point is computed by the same formulas); the tail depth also
  * changes the summation order inside the small levels, i.e. the rounding. */
 enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4, HELM_PF_GALERKIN = 8 };
-/* HELM_PF_GALERKIN (2D, omega-Jacobi only; else helm_create: HELM_ERR_ARG): every coarse level's
- * operator is R A P -- the full weighting R times the finer level's operator A times the linear
- * interpolation P of the V-cycle, a 9-point stencil built at helm_create in FP64 -- instead of the
- * Shortley-Weller operator rediscretised on the coarse widths (Section 6.1 lists both). */
+/* HELM_PF_GALERKIN (2D or 3D, omega-Jacobi only; else helm_create: HELM_ERR_ARG): every coarse
+ * level's operator is R A P -- the full weighting R times the finer level's operator A times the
+ * (bi/tri)linear interpolation P of the V-cycle, a 9-point (2D) or 27-point (3D) stencil built at
+ * helm_create in FP64 -- instead of the Shortley-Weller operator rediscretised on the coarse widths
+ * (Section 6.1 lists both). */
 
 /* Krylov solve options.  The stopping rule is ||r_m|| / ||b|| < tol on the recurrence
  * residual (Section 6.2, with d_0 = b since x_0 = 0), then b - H x is recomputed in FP64;

@@ -137,8 +137,8 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   helm_status s;
   if ((s = check_grid(grid)) != HELM_OK) return s;
   if ((s = check_precond(pc)) != HELM_OK) return s;
-  if ((pc->flags & HELM_PF_GALERKIN) && pc->kind != HELM_PC_NONE && grid->dim != 2) {
-    set_error("Galerkin coarse operators need a 2D grid");
+  if ((pc->flags & HELM_PF_GALERKIN) && pc->kind != HELM_PC_NONE && grid->dim < 2) {
+    set_error("Galerkin coarse operators need a 2D or 3D grid");
     return HELM_ERR_ARG;
   }
   if (!k || !std::isfinite(k->k0)) { set_error("kspec missing or k0 not finite"); return HELM_ERR_ARG; }

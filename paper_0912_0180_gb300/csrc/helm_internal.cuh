@@ -77,8 +77,9 @@ template <typename T> struct OpView {
   const cx<T>* dinv;  // omega/D (damped Jacobi) or 1/D (Gauss-Seidel) at every point of a
                       // multigrid level; nullptr otherwise
   const cx<T>* dg;    // the diagonal itself (multigrid levels; nullptr otherwise)
-  const cx<T>* st9;   // Galerkin level (2D): weight k = 3 (dj + 1) + (di + 1) of unknown p at
-                      // st9[k * ntot + p]; nullptr for a Shortley-Weller level
+  const cx<T>* stg;   // Galerkin level: weight k of unknown p at stg[k * ntot + p], with
+                      // k = 3 (dj + 1) + (di + 1) in 2D (9 weights) and k = 9 (dl + 1) + 3 (dj + 1)
+                      // + (di + 1) in 3D (27); nullptr for a Shortley-Weller level
   long ntot;
   int somm;           // bit a: the last unknown of axis a is a Sommerfeld boundary node
   double2 bt[3];      // its boundary weight 2i / h_l (the diagonal gains bt * sqrt(phi))
@@ -130,9 +131,10 @@ struct LevelHost {
   float2* dinv32 = nullptr;
   double2* dg64 = nullptr;   // the diagonal itself, same precision
   float2* dg32 = nullptr;
-  // Galerkin coarse operator (2D, 9-point), [9][ntot]; FP64 always, FP32 copy for FP32 multigrid
-  double2* st9_64 = nullptr;
-  float2* st9_32 = nullptr;
+  // Galerkin coarse operator (9-point in 2D, 27-point in 3D), [9 or 27][ntot]; FP64 always, FP32
+  // copy for FP32 multigrid
+  double2* stg64 = nullptr;
+  float2* stg32 = nullptr;
   // Sommerfeld high sides: bit a set when the last unknown of axis a is the boundary node
   int somm = 0;
   double2 bt[3] = {};

@@ -141,7 +141,7 @@ __device__ __forceinline__ cx<T> off9(const OpView<T>& op, const cx<T>* __restri
       if (di == 0 && dj == 0) continue;
       const int ii = i + di, jj = j + dj;
       if (ii < 0 || ii >= op.n[0] || jj < 0 || jj >= op.n[1]) continue;
-      acc = cfma<T>(op.st9[(long)(3 * (dj + 1) + (di + 1)) * op.ntot + p], x[p + di + (long)dj * op.n[0]], acc);
+      acc = cfma<T>(op.stg[(long)(3 * (dj + 1) + (di + 1)) * op.ntot + p], x[p + di + (long)dj * op.n[0]], acc);
     }
   return acc;
 }
@@ -154,7 +154,7 @@ __global__ void k_apply9(OpView<T> op, const cx<T>* __restrict__ x, const cx<T>*
   if (skip && *skip) return;
   POINT_INDEX(op);
   (void)l;
-  cx<T> v = cfma<T>(op.st9[4 * op.ntot + p], x[p], off9<T>(op, x, i, j, p));
+  cx<T> v = cfma<T>(op.stg[4 * op.ntot + p], x[p], off9<T>(op, x, i, j, p));
   y[p] = f ? csub<T>(f[p], v) : v;
 }
 
@@ -186,6 +186,81 @@ __global__ void k_resid0_9(OpView<T> op, const cx<T>* __restrict__ u, const cx<T
   POINT_INDEX(op);
   (void)l;
   cx<T> acc = off9<T>(op, u, i, j, p);
+  cx<T> fv = f[p];
+  const T om1 = T(1) - omega;
+  r[p] = mkc<T>(fma(om1, fv.x, -acc.x), fma(om1, fv.y, -acc.y));
+}
+
+// ---- Galerkin (27-point) levels, 3D ---------------------------------------------------------
+
+// Off-diagonal part of a 27-point row: the 26 neighbours' weights times their values.
+template <typename T>
+__device__ __forceinline__ cx<T> off27(const OpView<T>& op, const cx<T>* __restrict__ x, int i, int j, int l,
+                                       long p) {
+  cx<T> acc = mkc<T>(T(0), T(0));
+  const long sy = op.n[0], sz = (long)op.n[0] * op.n[1];
+#pragma unroll
+  for (int dl = -1; dl <= 1; ++dl) {
+    const int ll = l + dl;
+    if (ll < 0 || ll >= op.n[2]) continue;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= op.n[1]) continue;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        if (di == 0 && dj == 0 && dl == 0) continue;
+        const int ii = i + di;
+        if (ii < 0 || ii >= op.n[0]) continue;
+        acc = cfma<T>(op.stg[(long)(9 * (dl + 1) + 3 * (dj + 1) + (di + 1)) * op.ntot + p],
+                      x[p + di + dj * sy + dl * sz], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// y = M x, or y = f - M x when f is given, on a 27-point level.
+template <typename T>
+__global__ void k_apply27(OpView<T> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ f,
+                          cx<T>* __restrict__ y, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  POINT_INDEX(op);
+  cx<T> v = cfma<T>(op.stg[13 * op.ntot + p], x[p], off27<T>(op, x, i, j, l, p));
+  y[p] = f ? csub<T>(f[p], v) : v;
+}
+
+// Damped-Jacobi sweep on a 27-point level (u == nullptr: zero guess); `wide` also receives the
+// result in complex128 (the last sweep of an FP32 V-cycle).
+template <typename T>
+__global__ void k_jacobi27(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
+                           cx<T>* __restrict__ un, T omega, double2* wide, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  POINT_INDEX(op);
+  cx<T> di = op.dinv[p];  // omega / D
+  cx<T> r;
+  if (!u) {
+    r = cmul<T>(f[p], di);
+  } else {
+    cx<T> g = cmul<T>(csub<T>(f[p], off27<T>(op, u, i, j, l, p)), di);
+    cx<T> u0 = u[p];
+    const T om1 = T(1) - omega;
+    r = mkc<T>(fma(om1, u0.x, g.x), fma(om1, u0.y, g.y));
+  }
+  un[p] = r;
+  if (wide) wide[p] = cconv<double, T>(r);
+}
+
+// Residual after the single Jacobi sweep from zero on a 27-point level: (1 - omega) f - offdiag(u).
+template <typename T>
+__global__ void k_resid0_27(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
+                            cx<T>* __restrict__ r, T omega, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  POINT_INDEX(op);
+  cx<T> acc = off27<T>(op, u, i, j, l, p);
   cx<T> fv = f[p];
   const T om1 = T(1) - omega;
   r[p] = mkc<T>(fma(om1, fv.x, -acc.x), fma(om1, fv.y, -acc.y));
@@ -313,18 +388,22 @@ template <typename T>
 static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const int* skip, cudaStream_t st,
                            double2* wide = nullptr);
 
-template <typename T> static bool is9(const LevelHost& L) { return L.st9_64 != nullptr; }
+// a Galerkin level: 9-point in 2D, 27-point in 3D
+template <typename T> static bool is9(const LevelHost& L) { return L.stg64 != nullptr; }
 
 template <typename T, int DIM> struct Launch {
   static void apply(const LevelHost& L, const cx<T>* x, const cx<T>* f, cx<T>* y, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
     if (DIM == 2 && is9<T>(L)) launch_pdl(k_apply9<T>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
+    else if (DIM == 3 && is9<T>(L)) launch_pdl(k_apply27<T>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
     else launch_pdl(k_mg_apply<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
   }
   static void jacobi(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* un, T omega, double2* wide,
                      const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
     if (DIM == 2 && is9<T>(L)) launch_pdl(k_jacobi9<T>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, skip);
+    else if (DIM == 3 && is9<T>(L))
+      launch_pdl(k_jacobi27<T>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, wide, skip);
     else launch_pdl(k_jacobi<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, un, omega, wide, skip);
   }
   static void rbgs(const LevelHost& L, cx<T>* u, const cx<T>* f, int colour, int zero, double2* wide,
@@ -343,6 +422,8 @@ template <typename T, int DIM> struct Launch {
     } else {
       cfg<DIM>(L.n, g, b);
       if (DIM == 2 && is9<T>(L)) launch_pdl(k_resid0_9<T>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+      else if (DIM == 3 && is9<T>(L))
+        launch_pdl(k_resid0_27<T>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
       else launch_pdl(k_resid0<T, DIM, false>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
     }
   }
@@ -432,7 +513,7 @@ template <typename T>
 static bool fused_applies(const helm_ctx* c, int l) {
   const helm_precond& pcf = c->pc;
   if (pcf.flags & HELM_PF_UNFUSED) return false;
-  if (c->lv[l].st9_64) return false;  // 9-point Galerkin levels run the per-component kernels
+  if (c->lv[l].stg64) return false;  // 9-point Galerkin levels run the per-component kernels
   if (l >= c->tail_first) return true;
   return c->lv[l].dim == 2 && pcf.nu1 == 1 && pcf.nu2 == 1 && l < (int)c->lv.size() - 1;
 }
@@ -533,7 +614,7 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
     case HELM_OP_PROLONG: if (lvl >= nl - 1 || !A || !B) return HELM_ERR_ARG; prolong_any<T>(L, c->lv[lvl + 1], B, A, 0, nullptr, st); break;
     case HELM_OP_COARSE: if (lvl != nl - 1 || !A || !O) return HELM_ERR_ARG; coarse_solve<T>(c, A, O, nullptr, st); break;
     case HELM_OP_DOWN:
-      if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || L.st9_64 || !A || !B || !O) return HELM_ERR_ARG;
+      if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || L.stg64 || !A || !B || !O) return HELM_ERR_ARG;
       fused_down2d<T>(c, lvl, B, A, O, nullptr, st);
       break;
     default: return HELM_ERR_ARG;

@@ -487,7 +487,7 @@ constexpr size_t TAIL_INVERSE_BYTES = 1 << 20;
 template <typename T> int tail_first_level(const helm_ctx* c, long point_budget) {
   int nl = (int)c->lv.size();
   if (c->fdm.on) return nl;  // the one-block tail needs the dense coarsest inverse
-  if (c->lv[nl - 1].st9_64) return nl;  // ... and runs 5-point rows only
+  if (c->lv[nl - 1].stg64) return nl;  // ... and runs 5-point rows only
   long pts = c->lv[nl - 1].ntot;
   size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
   if (bytes > TAIL_SMEM_BUDGET) return nl;  // the coarsest level alone is too big: no tail
@@ -710,7 +710,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   if (fused2d) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (int l = 0; l < nl - 1; ++l) {
-      if (c->lv[l].st9_64) continue;  // Galerkin levels do not run the fused kernels
+      if (c->lv[l].stg64) continue;  // Galerkin levels do not run the fused kernels
       auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
       auto valid = [](int t) { return t == TILE_BIG || t == TILE_SMALL || t == TILE_TINY; };
       if (it != g_tune.end() && valid(it->second.first) && valid(it->second.second)) {

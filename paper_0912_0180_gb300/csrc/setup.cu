@@ -234,7 +234,7 @@ __device__ double2 fine_entry(const OpView<double>& F, int i, int j, int ii, int
   if (ii < 0 || ii >= F.n[0] || jj < 0 || jj >= F.n[1]) return mkc<double>(0.0, 0.0);
   const int di = ii - i, dj = jj - j;
   const long p = i + (long)F.n[0] * j;
-  if (F.st9) return F.st9[(long)(3 * (dj + 1) + (di + 1)) * F.ntot + p];
+  if (F.stg) return F.stg[(long)(3 * (dj + 1) + (di + 1)) * F.ntot + p];
   if (di == 0 && dj == 0) {
     double ph = F.phi ? F.phi[p] : F.phi0;
     double2 d = cadd<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), somm_diag(F, i, j, 0, ph));
@@ -295,12 +295,90 @@ __global__ void k_galerkin2d(OpView<double> F, int nc0, int nc1, double2* __rest
   }
 }
 
-// omega / D and D of a Galerkin level (D = the stencil's centre weight).
-__global__ void k_dinv9(const double2* __restrict__ st9, long n, double omega_s, double2* d64, float2* d32,
-                        double2* g64, float2* g32) {
+// ---- Galerkin coarse operators (3D) ---------------------------------------------------------
+// Entry of a finer 3D operator between fine unknowns (i, j, l) and (ii, jj, ll): its 27-point
+// stencil when it is a Galerkin level, else its Shortley-Weller row.
+__device__ double2 fine_entry3(const OpView<double>& F, int i, int j, int l, int ii, int jj, int ll) {
+  if (ii < 0 || ii >= F.n[0] || jj < 0 || jj >= F.n[1] || ll < 0 || ll >= F.n[2]) return mkc<double>(0.0, 0.0);
+  const int di = ii - i, dj = jj - j, dl = ll - l;
+  const long p = i + (long)F.n[0] * (j + (long)F.n[1] * l);
+  if (F.stg) return F.stg[(long)(9 * (dl + 1) + 3 * (dj + 1) + (di + 1)) * F.ntot + p];
+  const int nz = (di != 0) + (dj != 0) + (dl != 0);
+  if (nz == 0) {
+    double ph = F.phi ? F.phi[p] : F.phi0;
+    double2 d = cadd<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), F.a0[2][l]);
+    d = cadd<double>(d, somm_diag(F, i, j, l, ph));
+    return csub<double>(d, cscale<double>(ph, F.s));
+  }
+  if (nz > 1) return mkc<double>(0.0, 0.0);  // a 7-point row has only axis neighbours
+  if (di) return di < 0 ? F.am[0][i] : F.ap[0][i];
+  if (dj) return dj < 0 ? F.am[1][j] : F.ap[1][j];
+  return dl < 0 ? F.am[2][l] : F.ap[2][l];
+}
+
+// C = R F P in 3D for one coarse unknown (I, J, L) per thread: R gathers the 27 fine unknowns
+// 2I+{0,1,2} x 2J+{0,1,2} x 2L+{0,1,2} with the full-weighting weights; each entry of F reaches a
+// fine unknown g, which the trilinear interpolation takes from the coarse unknowns K with
+// |g - (2K+1)| <= 1 on every axis (weight 1 or 1/2 per axis); only |K - I| <= 1 per axis survive.
+__global__ void k_galerkin3d(OpView<double> F, int nc0, int nc1, int nc2, double2* __restrict__ c64,
+                             float2* __restrict__ c32) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y, L = blockIdx.z;
+  if (I >= nc0) return;
+  const long ncs = (long)nc0 * nc1 * nc2;
+  const long q = I + (long)nc0 * (J + (long)nc1 * L);
+  const double wr[3] = {0.25, 0.5, 0.25};
+  double2 acc[27];
+  for (int k = 0; k < 27; ++k) acc[k] = mkc<double>(0.0, 0.0);
+  for (int c = 0; c < 3; ++c) {
+    const int fl = 2 * L + c;
+    if (fl >= F.n[2]) continue;
+    for (int b = 0; b < 3; ++b) {
+      const int fj = 2 * J + b;
+      if (fj >= F.n[1]) continue;
+      for (int a = 0; a < 3; ++a) {
+        const int fi = 2 * I + a;
+        if (fi >= F.n[0]) continue;
+        const double r = wr[a] * wr[b] * wr[c];
+        for (int dl = -1; dl <= 1; ++dl)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              const double2 e = fine_entry3(F, fi, fj, fl, fi + di, fj + dj, fl + dl);
+              if (e.x == 0.0 && e.y == 0.0) continue;
+              const int gi = fi + di, gj = fj + dj, gl = fl + dl;
+              for (int dN = -1; dN <= 1; ++dN) {
+                const int N = L + dN, tz = gl - (2 * N + 1);
+                if (N < 0 || N >= nc2 || tz < -1 || tz > 1) continue;
+                const double pz = tz == 0 ? 1.0 : 0.5;
+                for (int dM = -1; dM <= 1; ++dM) {
+                  const int M = J + dM, ty = gj - (2 * M + 1);
+                  if (M < 0 || M >= nc1 || ty < -1 || ty > 1) continue;
+                  const double py = ty == 0 ? 1.0 : 0.5;
+                  for (int dK = -1; dK <= 1; ++dK) {
+                    const int K = I + dK, tx = gi - (2 * K + 1);
+                    if (K < 0 || K >= nc0 || tx < -1 || tx > 1) continue;
+                    const double w = r * pz * py * (tx == 0 ? 1.0 : 0.5);
+                    double2& o = acc[9 * (dN + 1) + 3 * (dM + 1) + (dK + 1)];
+                    o = mkc<double>(fma(w, e.x, o.x), fma(w, e.y, o.y));
+                  }
+                }
+              }
+            }
+      }
+    }
+  }
+  for (int k = 0; k < 27; ++k) {
+    c64[k * ncs + q] = acc[k];
+    if (c32) c32[k * ncs + q] = cconv<float, double>(acc[k]);
+  }
+}
+
+// omega / D and D of a Galerkin level (D = the stencil's centre weight, index `centre`).
+__global__ void k_dinvg(const double2* __restrict__ stg, long n, int centre, double omega_s, double2* d64,
+                        float2* d32, double2* g64, float2* g32) {
   long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  double2 d = st9[4 * n + p];
+  double2 d = stg[(long)centre * n + p];
   double2 r = cscale<double>(omega_s, crecip<double>(d));
   if (d64) d64[p] = r;
   if (g64) g64[p] = d;
@@ -308,19 +386,24 @@ __global__ void k_dinv9(const double2* __restrict__ st9, long n, double omega_s,
   if (g32) g32[p] = cconv<float, double>(d);
 }
 
-// Dense matrix of a Galerkin coarsest level (row-major, FP64), one thread per row.
-__global__ void k_dense_assemble9(const double2* __restrict__ st9, int n0, int n1, double2* A, int n) {
+// Dense matrix of a Galerkin coarsest level (row-major, FP64), one thread per row; n2 = 1 in 2D
+// (9 weights), > 1 in 3D (27 weights).
+__global__ void k_dense_assembleg(const double2* __restrict__ stg, int n0, int n1, int n2, int dim, double2* A,
+                                  int n) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  int i = p % n0, j = p / n0;
+  int i = p % n0, j = (p / n0) % n1, l = p / (n0 * n1);
   double2* row = A + (long)p * n;
   for (int c = 0; c < n; ++c) row[c] = mkc<double>(0.0, 0.0);
-  for (int dj = -1; dj <= 1; ++dj)
-    for (int di = -1; di <= 1; ++di) {
-      int ii = i + di, jj = j + dj;
-      if (ii < 0 || ii >= n0 || jj < 0 || jj >= n1) continue;
-      row[ii + n0 * jj] = st9[(long)(3 * (dj + 1) + (di + 1)) * n + p];
-    }
+  const int lr = dim == 3 ? 1 : 0;
+  for (int dl = -lr; dl <= lr; ++dl)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        int ii = i + di, jj = j + dj, ll = l + dl;
+        if (ii < 0 || ii >= n0 || jj < 0 || jj >= n1 || ll < 0 || ll >= n2) continue;
+        const int k = dim == 3 ? 9 * (dl + 1) + 3 * (dj + 1) + (di + 1) : 3 * (dj + 1) + (di + 1);
+        row[ii + n0 * (jj + n1 * ll)] = stg[(long)k * n + p];
+      }
 }
 
 
@@ -520,7 +603,7 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.uniform_iso = iso ? 1 : 0;
   v.dinv = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dinv64 : (const cx<T>*)(const void*)dinv32;
   v.dg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)dg64 : (const cx<T>*)(const void*)dg32;
-  v.st9 = std::is_same<T, double>::value ? (const cx<T>*)(const void*)st9_64 : (const cx<T>*)(const void*)st9_32;
+  v.stg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)stg64 : (const cx<T>*)(const void*)stg32;
   v.ntot = ntot;
   v.somm = somm;
   for (int a = 0; a < 3; ++a) v.bt[a] = bt[a];
@@ -631,10 +714,16 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     if (galerkin) {
       // R F P replaces the rediscretised row; its uniform-interior shortcut does not apply
       for (int a = 0; a < 3; ++a) { C.ulo[a] = 1; C.uhi[a] = 0; }
-      if ((rc = ctx_alloc(c, (void**)&C.st9_64, sizeof(double2) * 9 * C.ntot)) != HELM_OK) return rc;
-      if (f32 && (rc = ctx_alloc(c, (void**)&C.st9_32, sizeof(float2) * 9 * C.ntot)) != HELM_OK) return rc;
-      dim3 gg(ceil_div(C.n[0], 128), C.n[1]);
-      k_galerkin2d<<<gg, 128, 0, st>>>(F.view<double>(), C.n[0], C.n[1], C.st9_64, C.st9_32);
+      const int nw = C.dim == 3 ? 27 : 9;
+      if ((rc = ctx_alloc(c, (void**)&C.stg64, sizeof(double2) * nw * C.ntot)) != HELM_OK) return rc;
+      if (f32 && (rc = ctx_alloc(c, (void**)&C.stg32, sizeof(float2) * nw * C.ntot)) != HELM_OK) return rc;
+      if (C.dim == 3) {
+        dim3 gg(ceil_div(C.n[0], 64), C.n[1], C.n[2]);
+        k_galerkin3d<<<gg, 64, 0, st>>>(F.view<double>(), C.n[0], C.n[1], C.n[2], C.stg64, C.stg32);
+      } else {
+        dim3 gg(ceil_div(C.n[0], 128), C.n[1]);
+        k_galerkin2d<<<gg, 128, 0, st>>>(F.view<double>(), C.n[0], C.n[1], C.stg64, C.stg32);
+      }
       HELM_CUDA(cudaGetLastError());
     }
     c->lv.push_back(C);
@@ -654,7 +743,9 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       OpView<double> v = L.view<double>();
       dim3 g((L.n[0] + 127) / 128, L.n[1], L.n[2]);
       double om = pc.smoother == HELM_SM_JACOBI ? pc.omega : 1.0;
-      if (L.st9_64) k_dinv9<<<ceil_div(L.ntot, 256), 256, 0, st>>>(L.st9_64, L.ntot, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
+      if (L.stg64)
+        k_dinvg<<<ceil_div(L.ntot, 256), 256, 0, st>>>(L.stg64, L.ntot, L.dim == 3 ? 13 : 4, om, L.dinv64, L.dinv32,
+                                                       L.dg64, L.dg32);
       else if (L.dim == 1) k_dinv<1><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       else if (L.dim == 2) k_dinv<2><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
       else k_dinv<3><<<g, 128, 0, st>>>(v, om, L.dinv64, L.dinv32, L.dg64, L.dg32);
@@ -670,7 +761,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
   // constant phi on a large coarsest level: the separable exact solve, no dense inverse
-  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.st9_64 && !Cst.somm) {
+  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.stg64 && !Cst.somm) {
     if ((rc = fdm_build(c, Cst, f32, st)) != HELM_OK) return rc;
     if (c->fdm.on) {
       c->nco = 0;
@@ -704,7 +795,8 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     return cuda_check(e2, "cudaMallocAsync(coarse)");
   }
   cudaMemsetAsync(flag, 0, sizeof(int), st);
-  if (Cst.st9_64) k_dense_assemble9<<<ceil_div(n, 128), 128, 0, st>>>(Cst.st9_64, Cst.n[0], Cst.n[1], A, n);
+  if (Cst.stg64)
+    k_dense_assembleg<<<ceil_div(n, 128), 128, 0, st>>>(Cst.stg64, Cst.n[0], Cst.n[1], Cst.n[2], Cst.dim, A, n);
   else k_dense_assemble<<<ceil_div(n, 128), 128, 0, st>>>(Cst.view<double>(), Cst.dim, A, n);
   const double2* inv = X;
   if (one_block) {
