@@ -6,6 +6,7 @@
             20^3 = 8000 unknowns, dense inverse).  `value` is the all-FP64 path; `fp32_mg` is the
             complex-FP32 V-cycle under FP64 Bi-CGSTAB and FP64 true residual, with its solution's
             relative difference from the FP64 path's.
+  3d160g    the same 3D solve with 27-point Galerkin coarse operators (omega-Jacobi V(1,1)).
   batch256  256 independent 2D instances (interior 63..511 per axis, 16..32-node layers, kh in
             [0.3, 0.6], constant or bump k, seeded point sources); one step solves all of them with
             helm_solve_batch (Bi-CGSTAB, CSG omega-Jacobi V(1,1), 1e-6).
@@ -83,7 +84,7 @@ def run(args):
     g.build()
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
-    fn = {"3d160": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+    fn = {"3d160": run_3d, "3d160g": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
           "mp2som": run_mp, "mp3som": run_mp,
           "select": run_select, "gmres": run_gmres}[args.workload]
     line = fn(args, torch, ranks, dev, local)
@@ -95,7 +96,10 @@ def run(args):
 
 # ---- 3D ------------------------------------------------------------------------------------
 
-def _pc3d():
+def _pc3d(galerkin=False):
+    if galerkin:  # Galerkin operators take the Jacobi smoother (red-black is no 2-colouring of 27 points)
+        return hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5, max_levels=4,
+                          galerkin=True)
     return hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS, max_levels=4)
 
 
@@ -104,12 +108,13 @@ def run_3d(args, torch, ranks, dev, local):
     from paper_0912_0180_gb300 import _lib as L
     from paper_0912_0180_gb300.helm import Helm
     p = hi.workload_3d_128()
+    galerkin = args.workload == "3d160g"
     b_dev = torch.from_numpy(p.b).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx, create_s = {}, {}
     for mg in ("c128", "c64"):
         t = time.perf_counter()
-        ctx[mg] = Helm(p, _pc3d(), mg_dtype=mg)
+        ctx[mg] = Helm(p, _pc3d(galerkin), mg_dtype=mg)
         torch.cuda.synchronize()
         create_s[mg] = time.perf_counter() - t
 
@@ -161,11 +166,13 @@ def run_3d(args, torch, ranks, dev, local):
     err = _errors_vs_reference(torch, ctx, b_dev)
     step64 = ranks.max(statistics.mean(ms64))
     step32 = ranks.max(statistics.mean(ms32))
-    kern = _kernels_3d(torch, L, ctx, p, dev, flush)
-    cfg = {"workload": p.name, "grid": "128^3 interior + 16 ECS nodes per side (160^3 unknowns)",
+    kern = None if galerkin else _kernels_3d(torch, L, ctx, p, dev, flush)
+    cfg = {"workload": p.name + ("-galerkin" if galerkin else ""),
+           "grid": "128^3 interior + 16 ECS nodes per side (160^3 unknowns)",
            "n_unknowns": p.n, "solves_per_step": 1, "solver": "Bi-CGSTAB, tol 1e-6 (FP64 true residual)",
-           "multigrid": "CSG theta_beta=0.3, V(1,1) red-black Gauss-Seidel, 4 levels, FW, trilinear, "
-                        "dense inverse of the 20^3 coarsest level",
+           "multigrid": ("CSG theta_beta=0.3, V(1,1) omega-Jacobi 0.5 on 27-point Galerkin coarse operators R A P, "
+                         if galerkin else "CSG theta_beta=0.3, V(1,1) red-black Gauss-Seidel, ") +
+                        "4 levels, FW, trilinear, dense inverse of the 20^3 coarsest level",
            "l2": "flushed (512 MiB device write) before every timed step"}
     line = _base(args, ranks.job_rate(1, step64), step64, ranks.world, cfg, "c128")
     line.update({
@@ -183,8 +190,9 @@ def run_3d(args, torch, ranks, dev, local):
                 "path": "fp32_mg through helm_solve with pinned host b and x",
                 "h2d_bytes_per_step": p.n * 16, "d2h_bytes_per_step": p.n * 16},
         "gpu_launches": int(sum(i.kernels for i in inf64) + sum(i.kernels for i in inf32)),
-        "roofline": kern["dominant"], "kernels": kern["table"],
     })
+    if kern is not None:
+        line.update({"roofline": kern["dominant"], "kernels": kern["table"]})
     for h in ctx.values():
         h.close()
     return line
