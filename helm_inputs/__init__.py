@@ -43,6 +43,7 @@ class Problem:
     b: np.ndarray              # right-hand side (complex128, x fastest)
     name: str = ""
     ecs_ramp: int = 0          # > 1: the layer contour turns over this many widths (smooth ECS)
+    phi_im: Optional[np.ndarray] = None  # imaginary part of phi (k at complex node positions)
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -77,6 +78,35 @@ def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray
     return np.asarray(xs, dtype=np.float64)
 
 
+def axis_positions_complex(n_int: int, nl: Tuple[int, int], extent: float, theta: float,
+                           ramp: int = 0) -> np.ndarray:
+    """Complex coordinates of the unknowns along one axis: real in the interior, and in a layer of
+    m nodes the turning point plus the sum of the layer widths h e^{i theta min(q, R) / R} (R the
+    ramp, sharp contour for R <= 1) up to the node -- the ECS map of Section 2."""
+    h = extent / (n_int - 1)
+    lo, hi = nl
+
+    def depth(m):
+        if ramp > 1:
+            return sum(h * np.exp(1j * theta * min(q, ramp) / ramp) for q in range(1, m + 1))
+        return m * h * np.exp(1j * theta)
+
+    zs: List[complex] = [-depth(m) for m in range(lo, 0, -1)]
+    first = 0 if lo > 0 else 1
+    last = n_int - 1 if hi != 0 else n_int - 2
+    zs += [complex(j * h) for j in range(first, last + 1)]
+    zs += [extent + depth(m) for m in range(1, hi + 1)] if hi > 0 else []
+    return np.asarray(zs, dtype=np.complex128)
+
+
+def mesh_complex(p: Problem) -> List[np.ndarray]:
+    """Like mesh(), with the complex node coordinates of the layers."""
+    axes = [axis_positions_complex(p.n_int[a], p.n_layer[a], p.extent[a], p.theta_gamma, p.ecs_ramp)
+            for a in range(p.dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return grids[::-1]
+
+
 def mesh(p: Problem) -> List[np.ndarray]:
     """Broadcastable real coordinate arrays, ordered so that arr.ravel() is x-fastest."""
     axes = [axis_positions(p.n_int[a], p.n_layer[a], p.extent[a]) for a in range(p.dim)]
@@ -100,7 +130,7 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
                  theta_gamma=0.5, k0: float = 0.0, phi_kind: str = "const", bump_amp=0.3,
                  bump_width2=0.02, bump_centre=(0.5, 0.5, 0.5), rhs: str = "point",
                  rhs_width_h: float = 2.0, seed: int = BASE_SEED, name: str = "",
-                 phi_fn=None, rhs_fn=None, ecs_ramp: int = 0) -> Problem:
+                 phi_fn=None, rhs_fn=None, ecs_ramp: int = 0, complex_z: bool = False) -> Problem:
     """Build a seeded synthetic instance shaped like the paper's model problems.
 
     n_l: int (all sides), one (lo, hi) pair for every axis, or per-axis (lo, hi) pairs.
@@ -108,6 +138,9 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
          (phi = phi_fn(x, y[, z]) at the real node positions).
     ecs_ramp: 0 = sharp ECS contour; R > 1 = the contour turns by theta_gamma / R per layer width
          over the first R widths (the smooth transition of the paper's Section 7 remark).
+    complex_z: evaluate the "bump" / "field" phi at the complex node coordinates of the layers (the
+         analytic continuation of k; |x - c|^2 becomes sum (z - c)^2), giving phi_im; False reads k
+         at the real positions.
     rhs: "point" (value 1 at the interior node floor((n_int-1)/2) per axis, as in MP1),
          "gauss" (exp(-|x - x_s|^2 / (2 sigma^2)), sigma = rhs_width_h * h, x_s uniform in
          [0.1, 0.9]^d from the seed), "random" (complex normal entries), "zero", "field"
@@ -129,14 +162,19 @@ def make_problem(dim: int, n_int: int | Sequence[int], n_l: int | Sequence, *, e
                 ecs_ramp=int(ecs_ramp))
     shape = p.shape
     X = mesh(p)
+    Z = mesh_complex(p) if complex_z else X
     if phi_kind == "bump":
-        r2 = sum((X[a] - bump_centre[a] * ext[a]) ** 2 for a in range(dim))
+        r2 = sum((Z[a] - bump_centre[a] * ext[a]) ** 2 for a in range(dim))
         k = k0 * (1.0 + bump_amp * np.exp(-r2 / bump_width2))
-        p.phi = np.ascontiguousarray((k * k).ravel(), dtype=np.float64)
+        ph = (k * k).ravel()
     elif phi_kind == "field":
-        p.phi = np.ascontiguousarray(np.broadcast_to(phi_fn(*X[:dim]), shape[::-1]).ravel(), dtype=np.float64)
+        ph = np.broadcast_to(phi_fn(*Z[:dim]), shape[::-1]).ravel()
     elif phi_kind != "const":
         raise ValueError(phi_kind)
+    if phi_kind != "const":
+        p.phi = np.ascontiguousarray(np.real(ph), dtype=np.float64)
+        if complex_z:
+            p.phi_im = np.ascontiguousarray(np.imag(ph), dtype=np.float64)
     n = int(np.prod(shape))
     if rhs == "point":
         b = np.zeros(shape[::-1], np.complex128)

@@ -97,6 +97,7 @@ typedef struct {
   long ntot;
   axis_t ax[3];
   double* phi;    /* k(x)^2 at every unknown */
+  double* phi_im; /* imaginary part of phi (k evaluated at complex node positions); NULL = real */
   cplx s;         /* sigma = s * phi; 1 for H and CSG, beta^2 for CSL */
   cplx* st9;      /* Galerkin levels (2D): row p is st9[9p + 3(dj+1) + (di+1)], the weight of the
                      unknown (i+di, j+dj); NULL for a Shortley-Weller level */
@@ -208,6 +209,7 @@ static void level_free(level_t* L) {
   free(L->st27);
   for (int d = 0; d < L->dim; ++d) axis_free(&L->ax[d]);
   free(L->phi);
+  free(L->phi_im);
 }
 
 static long lidx(const level_t* L, int i, int j, int l) {
@@ -215,7 +217,7 @@ static long lidx(const level_t* L, int i, int j, int l) {
 }
 
 /* Fine level: gaps for the requested operator, phi sampled (or constant). */
-static void level_fine(level_t* L, const orc_grid* g, const double* phi, double k0,
+static void level_fine(level_t* L, const orc_grid* g, const double* phi, const double* phi_im, double k0,
                        cplx scale_in, cplx scale_ly, cplx s) {
   memset(L, 0, sizeof(*L));
   L->dim = g->dim;
@@ -230,6 +232,10 @@ static void level_fine(level_t* L, const orc_grid* g, const double* phi, double 
   }
   L->phi = malloc(sizeof(double) * imax(L->ntot, 1));
   for (long p = 0; p < L->ntot; ++p) L->phi[p] = phi ? phi[p] : k0 * k0;
+  if (phi_im) {
+    L->phi_im = malloc(sizeof(double) * imax(L->ntot, 1));
+    memcpy(L->phi_im, phi_im, sizeof(double) * L->ntot);
+  }
   L->s = s;
 }
 
@@ -251,6 +257,15 @@ static void level_coarse(const level_t* F, level_t* C) {
         int fi = 2 * i + 1, fj = F->dim > 1 ? 2 * j + 1 : 0, fl = F->dim > 2 ? 2 * l + 1 : 0;
         C->phi[lidx(C, i, j, l)] = F->phi[lidx(F, fi, fj, fl)];
       }
+  if (F->phi_im) {  /* injected like the real part */
+    C->phi_im = malloc(sizeof(double) * imax(C->ntot, 1));
+    for (int l = 0; l < C->n[2]; ++l)
+      for (int j = 0; j < C->n[1]; ++j)
+        for (int i = 0; i < C->n[0]; ++i) {
+          int fi = 2 * i + 1, fj = F->dim > 1 ? 2 * j + 1 : 0, fl = F->dim > 2 ? 2 * l + 1 : 0;
+          C->phi_im[lidx(C, i, j, l)] = F->phi_im[lidx(F, fi, fj, fl)];
+        }
+  }
   C->s = F->s;
 }
 
@@ -267,7 +282,8 @@ static cplx diag_at(const level_t* L, int i, int j, int l) {
     /* Sommerfeld boundary node: + 2 i k / h_l with k = sqrt(phi), the unshifted wave number */
     if (L->ax[a].somm && ix[a] == L->ax[a].n - 1) d += L->ax[a].bt * sqrt(ph);
   }
-  return d - L->s * ph;
+  cplx phc = ph + I * (L->phi_im ? L->phi_im[lidx(L, i, j, l)] : 0.0);
+  return d - L->s * phc;
 }
 
 /* Off-diagonal part of row (i,j,l) applied to x (Dirichlet neighbours contribute 0). */
@@ -506,11 +522,15 @@ static void level_galerkin3d(const level_t* F, level_t* C) {
 }
 
 /* ---- context ------------------------------------------------------------------------- */
-orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_precond* pc) {
+/* phi_im (optional): the imaginary part of phi at every unknown, for k evaluated at the complex
+ * node positions of the layers (the alternative to reading k at real positions); the Sommerfeld
+ * boundary term keeps sqrt of the real part (its nodes are real). */
+orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, double k0,
+                    const orc_precond* pc) {
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
   c->grid = *g;
   c->pc = *pc;
-  level_fine(&c->H, g, phi, k0, 1.0, 1.0, 1.0);
+  level_fine(&c->H, g, phi, phi_im, k0, 1.0, 1.0, 1.0);
   if (pc->kind == 0) return c; /* identity preconditioner: no hierarchy */
   cplx beta = cexp(I * pc->theta_beta);
   cplx scale_in = 1.0, scale_ly = 1.0, s = 1.0;
@@ -519,7 +539,7 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, double k0, const orc_p
   else if (pc->kind == 3) { scale_in = beta; }                       /* CSG, interior widths */
   int maxl = pc->max_levels < 1 ? 1 : pc->max_levels;
   c->M = calloc(maxl, sizeof(level_t));
-  level_fine(&c->M[0], g, phi, k0, scale_in, scale_ly, s);
+  level_fine(&c->M[0], g, phi, phi_im, k0, scale_in, scale_ly, s);
   c->nlev = 1;
   while (c->nlev < maxl) {
     const level_t* F = &c->M[c->nlev - 1];
@@ -1139,7 +1159,8 @@ int orc_mg_iterate(const orc_ctx* c, const cplx* f, int max_cycles, double reduc
  * with right-hand side f); *out receives the last preconditioner that converged.  params[t] and
  * cycles[t] record each trial (cycles -1 = did not converge).  Returns the number of trials run;
  * *status = 0 when the start converged, else 5 and *out = the start. */
-int orc_select_precond(const orc_grid* g, const double* phi, double k0, const orc_precond* start,
+int orc_select_precond(const orc_grid* g, const double* phi, const double* phi_im, double k0,
+                       const orc_precond* start,
                        const cplx* f, int max_cycles, double reduction, double factor,
                        int max_trials, orc_precond* out, double* params, int* cycles, int* status) {
   *out = *start;
@@ -1156,7 +1177,7 @@ int orc_select_precond(const orc_grid* g, const double* phi, double k0, const or
   for (; t < max_trials; ++t) {
     if (t > 0) p *= factor;
     if (pc.kind == 1) pc.shift_im = p; else pc.theta_beta = p;
-    orc_ctx* c = orc_create(g, phi, k0, &pc);
+    orc_ctx* c = orc_create(g, phi, phi_im, k0, &pc);
     int k = orc_mg_iterate(c, f, max_cycles, reduction, u, NULL);
     orc_destroy(c);
     params[t] = p;

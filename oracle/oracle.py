@@ -64,7 +64,7 @@ def _load():
         lib = C.CDLL(_LIB)
         vp, ip, dp = C.c_void_p, C.c_int, C.c_double
         lib.orc_create.restype = vp
-        lib.orc_create.argtypes = [C.POINTER(_Grid), vp, dp, C.POINTER(_Precond)]
+        lib.orc_create.argtypes = [C.POINTER(_Grid), vp, vp, dp, C.POINTER(_Precond)]
         lib.orc_destroy.argtypes = [vp]
         lib.orc_num_levels.argtypes = [vp]
         lib.orc_level_shape.argtypes = [vp, ip, ip, vp]
@@ -85,7 +85,7 @@ def _load():
         lib.orc_solve.restype = ip
         lib.orc_mg_iterate.argtypes = [vp, vp, ip, dp, vp, vp]
         lib.orc_mg_iterate.restype = ip
-        lib.orc_select_precond.argtypes = [C.POINTER(_Grid), vp, dp, C.POINTER(_Precond), vp, ip, dp, dp, ip,
+        lib.orc_select_precond.argtypes = [C.POINTER(_Grid), vp, vp, dp, C.POINTER(_Precond), vp, ip, dp, dp, ip,
                                            C.POINTER(_Precond), vp, vp, C.POINTER(C.c_int)]
         lib.orc_select_precond.restype = ip
         _lib = lib
@@ -113,6 +113,12 @@ def _grid(problem) -> "_Grid":
     return g
 
 
+def _phi_im(problem):
+    """The imaginary part of phi (k at complex node positions), or None when phi is real."""
+    v = getattr(problem, "phi_im", None)
+    return None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+
+
 def _precond(pc) -> "_Precond":
     return _Precond(pc.kind, pc.theta_beta, complex(pc.shift).real, complex(pc.shift).imag,
                     pc.nu1, pc.nu2, pc.smoother, pc.omega, pc.max_levels, pc.coarse_max,
@@ -127,12 +133,14 @@ def select_precond(problem, start, f, max_cycles=20, reduction=1e-6, factor=0.8,
     g = _grid(problem)
     p = _precond(start)
     phi = None if problem.phi is None else np.ascontiguousarray(problem.phi, dtype=np.float64)
+    phi_im = _phi_im(problem)
     f = _c128(f)
     out = _Precond()
     params = np.zeros(max_trials, np.float64)
     cycles = np.zeros(max_trials, np.int32)
     status = C.c_int(0)
-    t = lib.orc_select_precond(C.byref(g), _ptr(phi) if phi is not None else None, problem.k0, C.byref(p),
+    t = lib.orc_select_precond(C.byref(g), _ptr(phi) if phi is not None else None,
+                               _ptr(phi_im) if phi_im is not None else None, problem.k0, C.byref(p),
                                _ptr(f), max_cycles, reduction, factor, max_trials, C.byref(out),
                                _ptr(params), _ptr(cycles), C.byref(status))
     chosen = out.shift_im if start.kind == 1 else out.theta_beta
@@ -155,7 +163,9 @@ class Oracle:
         self._phi = None
         if problem.phi is not None:
             self._phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
+        self._phi_im = _phi_im(problem)
         self._h = lib.orc_create(C.byref(g), _ptr(self._phi) if self._phi is not None else None,
+                                 _ptr(self._phi_im) if self._phi_im is not None else None,
                                  problem.k0, C.byref(p))
         self.n = problem.n
         self.nlev = lib.orc_num_levels(self._h)

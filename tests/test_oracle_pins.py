@@ -863,3 +863,39 @@ def test_galerkin3d_laplacian_closed_form():
     kron3 = lambda z, y, x: np.kron(z, np.kron(y, x))
     ref = kron3(mc, mc, ac) + kron3(mc, ac, mc) + kron3(ac, mc, mc)
     assert np.allclose(o.dense(1, 1), ref, rtol=1e-12, atol=1e-9)
+
+
+# ---- k evaluated at complex node positions ------------------------------------------------------
+
+@pytest.mark.parametrize("dim,ramp", [(1, 0), (2, 0), (2, 4)])
+def test_complex_z_potential_exact_for_quadratics(dim, ramp):
+    """phi(z) = alpha z_x + beta (analytic, complex in the layers) sampled at the generator's complex
+    node coordinates: for u = prod_a (z_a - zlo_a)(z_a - zhi_a), H u = -Laplacian u - phi(z) u
+    exactly, with z built independently above; with phi_im = 0 the operator is the real-k one bit
+    for bit."""
+    n_int, nl, theta = (11, 4, 0.5) if dim == 1 else (9, 3, 0.5)
+    alpha, beta = 3.0, 5.0
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=theta, phi_kind="field", rhs="zero", ecs_ramp=ramp,
+                        complex_z=True, phi_fn=lambda *z: alpha * z[0] + beta)
+    assert p.phi_im is not None and np.abs(p.phi_im).max() > 0
+    o = Oracle(p)
+    zs = [_node_z(n_int, (nl, nl), 1.0, theta, ramp) for _ in range(dim)]
+    q = [(z - zlo) * (z - zhi) for (z, zlo, zhi) in zs]
+
+    def outer(vs):
+        v = vs[0]
+        for a in range(1, dim):
+            v = np.multiply.outer(vs[a], v)
+        return v.ravel()
+
+    u = outer(q)
+    lap = np.zeros_like(u)
+    for a in range(dim):
+        lap += outer([q[b] if b != a else 2 * np.ones_like(q[a]) for b in range(dim)])
+    zx = outer([zs[0][0]] + [np.ones_like(zs[b][0]) for b in range(1, dim)])
+    expect = -lap - (alpha * zx + beta) * u
+    assert np.abs(o.apply(u) - expect).max() <= 1e-10 * np.abs(expect).max()
+    r = dataclasses.replace(p, phi_im=np.zeros_like(p.phi_im))
+    s = dataclasses.replace(p, phi_im=None)
+    x = hi.random_vector(p.n, 3)
+    assert np.array_equal(Oracle(r).apply(x), Oracle(s).apply(x))
