@@ -86,6 +86,10 @@ typedef struct {
 typedef struct {
   double k0;
   const double* phi;    /* HOST pointer to N real values (x fastest), read during helm_create only */
+  const double* phi_im; /* HOST pointer to N values or NULL: the imaginary part of phi, for k read at
+                           the complex node positions of the layers (the analytic continuation of
+                           k); it must come with phi.  The uniform-interior shortcut of a level is
+                           kept only where it vanishes (the interior nodes are real) */
 } helm_kspec;
 
 /* Preconditioner M and the V(nu1, nu2)-cycle that approximates M^{-1} (Section 5;

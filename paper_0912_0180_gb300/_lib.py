@@ -23,7 +23,7 @@ class Grid(C.Structure):
 
 
 class KSpec(C.Structure):
-    _fields_ = [("k0", C.c_double), ("phi", C.c_void_p)]
+    _fields_ = [("k0", C.c_double), ("phi", C.c_void_p), ("phi_im", C.c_void_p)]
 
 
 class Precond(C.Structure):

@@ -155,10 +155,12 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   c->alloc_stream = st;
   bool somm = false;
   for (int a = 0; a < grid->dim; ++a) somm = somm || grid->n_layer[a][1] < 0;
+  if (k->phi_im && !k->phi) { delete c; set_error("phi_im needs phi"); return HELM_ERR_ARG; }
   if (k->phi) {
     long n = 1;
     for (int a = 0; a < grid->dim; ++a) n *= axis_unknowns(grid->n_int[a], grid->n_layer[a][0], grid->n_layer[a][1]);
     for (long i = 0; i < n; ++i) {
+      if (k->phi_im && !std::isfinite(k->phi_im[i])) { delete c; set_error("phi_im has a non-finite entry"); return HELM_ERR_ARG; }
       if (!std::isfinite(k->phi[i])) { delete c; set_error("phi has a non-finite entry"); return HELM_ERR_ARG; }
       // a Sommerfeld boundary needs the real wave number k = sqrt(phi)
       if (somm && k->phi[i] < 0.0) { delete c; set_error("phi < 0 with a Sommerfeld side"); return HELM_ERR_ARG; }

@@ -83,7 +83,15 @@ template <typename T> struct OpView {
   long ntot;
   int somm;           // bit a: the last unknown of axis a is a Sommerfeld boundary node
   double2 bt[3];      // its boundary weight 2i / h_l (the diagonal gains bt * sqrt(phi))
+  const double* phim; // imaginary part of phi (k at complex node positions; zero in the uniform
+                      // interior) or nullptr
 };
+
+// The potential term s * phi of the diagonal at p in FP64, phi complex when phim is given.
+inline __host__ __device__ double2 sigma64(const OpView<double>& op, long p, double ph) {
+  if (op.phim) return cmul<double>(op.s, mkc<double>(ph, op.phim[p]));
+  return cscale<double>(ph, op.s);
+}
 
 // Sommerfeld boundary part of the diagonal at (i, j, l) (Section 2, eq. "sommerfeld1", by a
 // mirrored ghost node): sum over the axes whose last unknown this is of 2 i k / h_l, with
@@ -138,6 +146,7 @@ struct LevelHost {
   // Sommerfeld high sides: bit a set when the last unknown of axis a is the boundary node
   int somm = 0;
   double2 bt[3] = {};
+  double* phim64 = nullptr;  // imaginary part of phi (FP64), nullptr when phi is real
   // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, -1 by the block-count rule
   int tile_down = -1, tile_up = -1;
   // work vectors (MG type), allocated for multigrid levels

@@ -56,7 +56,7 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
   for (int a = 0; a < g->dim; ++a) { n[a] = axis_n(*g, a); N *= n[a]; }
   size_t bytes = 0;
   for (int a = 0; a < g->dim; ++a) bytes += (size_t)(n[a] + 1) * 16 * 4;  // H tables
-  bytes += (size_t)N * 8;                                                 // phi
+  bytes += (size_t)N * 8 * 2;                                             // phi and its imaginary part
   bytes += (size_t)N * 16;                                                // diagonal of H
   bool pcon = pc->kind != HELM_PC_NONE;
   size_t esz = pcon && pc->mg_dtype == HELM_C64 ? 8 : 16;
@@ -69,6 +69,8 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
       ++levels;
       for (int a = 0; a < g->dim; ++a) bytes += (size_t)(m[a] + 1) * (16 * 4 + 8 * 3);
       bytes += (size_t)Nl * (8 + 4 + 2 * esz + (levels == 1 ? 1 : 3) * esz);
+      if (levels > 1 && (pc->flags & HELM_PF_GALERKIN))  // the stencil, FP64 and the V-cycle precision
+        bytes += (size_t)Nl * (g->dim == 3 ? 27 : 9) * (16 + (esz == 8 ? 8 : 0)) + (size_t)Nl * 8;
       last = Nl;
       bool all_small = true;
       long min_n = 1L << 40;
@@ -100,7 +102,7 @@ struct helm_server {
     helm_precond pc{};
     helm_solve_opts opts{};
     double k0 = 0.0;
-    std::vector<double> phi;
+    std::vector<double> phi, phi_im;
     std::vector<std::complex<double>> b, shadow;
     void* x_host = nullptr;
     long n = 0;
@@ -230,7 +232,7 @@ struct helm_server {
   helm_status start(Req* r) {
     r->stream = streams[(size_t)r->slot * prio_levels + prio_level(r)];
     cudaStream_t s = r->stream;
-    helm_kspec k{r->k0, r->phi.empty() ? nullptr : r->phi.data()};
+    helm_kspec k{r->k0, r->phi.empty() ? nullptr : r->phi.data(), r->phi_im.empty() ? nullptr : r->phi_im.data()};
     helm_status st = helm_create(&r->grid, &k, &r->pc, (void*)s, &r->ctx);
     if (st != HELM_OK) return st;
     size_t vb = sizeof(double2) * r->n;
@@ -353,6 +355,7 @@ helm_status helm_server_submit(helm_server* s, const helm_request* rq, uint64_t*
   for (int a = 0; a < rq->grid.dim; ++a) r->n *= axis_n(rq->grid, a);
   if (r->n < 1) { delete r; set_error("helm_server_submit: empty grid"); return HELM_ERR_ARG; }
   if (rq->k.phi) r->phi.assign(rq->k.phi, rq->k.phi + r->n);
+  if (rq->k.phi_im) r->phi_im.assign(rq->k.phi_im, rq->k.phi_im + r->n);
   r->nrhs = rq->nrhs < 1 ? 1 : rq->nrhs;
   if (r->nrhs > HELM_MAX_RHS) { delete r; set_error("helm_server_submit: nrhs"); return HELM_ERR_ARG; }
   const std::complex<double>* b = (const std::complex<double>*)rq->b;

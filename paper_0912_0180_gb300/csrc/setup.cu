@@ -114,7 +114,7 @@ __global__ void k_dinv(OpView<double> op, double omega_s, double2* d64, float2* 
   if (DIM > 2) d = cadd<double>(d, op.a0[2][l]);
   double ph = op.phi ? op.phi[p] : op.phi0;
   d = cadd<double>(d, somm_diag(op, i, j, l, ph));
-  d = csub<double>(d, cscale<double>(ph, op.s));
+  d = csub<double>(d, sigma64(op, p, ph));
   double2 r = cscale<double>(omega_s, crecip<double>(d));
   if (d64) d64[p] = r;
   if (g64) g64[p] = d;
@@ -146,7 +146,7 @@ __global__ void k_dense_assemble(OpView<double> op, int dim, double2* A, int n) 
   if (dim > 1) d = cadd<double>(d, op.a0[1][j]);
   if (dim > 2) d = cadd<double>(d, op.a0[2][l]);
   d = cadd<double>(d, somm_diag(op, i, j, l, ph));
-  d = csub<double>(d, cscale<double>(ph, op.s));
+  d = csub<double>(d, sigma64(op, p, ph));
   row[p] = d;
   if (i > 0) row[p - 1] = op.am[0][i];
   if (i < op.n[0] - 1) row[p + 1] = op.ap[0][i];
@@ -238,7 +238,7 @@ __device__ double2 fine_entry(const OpView<double>& F, int i, int j, int ii, int
   if (di == 0 && dj == 0) {
     double ph = F.phi ? F.phi[p] : F.phi0;
     double2 d = cadd<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), somm_diag(F, i, j, 0, ph));
-    return csub<double>(d, cscale<double>(ph, F.s));
+    return csub<double>(d, sigma64(F, p, ph));
   }
   if (di != 0 && dj != 0) return mkc<double>(0.0, 0.0);  // a 5-point row has no corner weights
   if (dj == 0) return di < 0 ? F.am[0][i] : F.ap[0][i];
@@ -308,7 +308,7 @@ __device__ double2 fine_entry3(const OpView<double>& F, int i, int j, int l, int
     double ph = F.phi ? F.phi[p] : F.phi0;
     double2 d = cadd<double>(cadd<double>(F.a0[0][i], F.a0[1][j]), F.a0[2][l]);
     d = cadd<double>(d, somm_diag(F, i, j, l, ph));
-    return csub<double>(d, cscale<double>(ph, F.s));
+    return csub<double>(d, sigma64(F, p, ph));
   }
   if (nz > 1) return mkc<double>(0.0, 0.0);  // a 7-point row has only axis neighbours
   if (di) return di < 0 ? F.am[0][i] : F.ap[0][i];
@@ -571,6 +571,27 @@ static helm_status find_uniform(LevelHost& L, cudaStream_t st) {
   return HELM_OK;
 }
 
+// The uniform-interior rows take a real phi (the diagonal ud - s phi without an imaginary part).
+// With a complex phi -- k read at complex node positions, which are real in the interior -- the
+// shortcut stays only if the imaginary part vanishes on the whole uniform box; else it is dropped
+// for this level and every row reads its stored diagonal.
+static helm_status uniform_needs_real_phi(LevelHost& L, cudaStream_t st) {
+  if (!L.phim64 || L.uhi[0] < L.ulo[0]) return HELM_OK;
+  std::vector<double> im(L.ntot);
+  HELM_CUDA(cudaMemcpyAsync(im.data(), L.phim64, sizeof(double) * L.ntot, cudaMemcpyDeviceToHost, st));
+  HELM_CUDA(cudaStreamSynchronize(st));
+  const int lo1 = L.dim > 1 ? L.ulo[1] : 0, hi1 = L.dim > 1 ? L.uhi[1] : 0;
+  const int lo2 = L.dim > 2 ? L.ulo[2] : 0, hi2 = L.dim > 2 ? L.uhi[2] : 0;
+  for (int l = lo2; l <= hi2; ++l)
+    for (int j = lo1; j <= hi1; ++j)
+      for (int i = L.ulo[0]; i <= L.uhi[0]; ++i)
+        if (im[i + (long)L.n[0] * (j + (long)L.n[1] * l)] != 0.0) {
+          for (int a = 0; a < 3; ++a) { L.ulo[a] = 1; L.uhi[a] = 0; }
+          return HELM_OK;
+        }
+  return HELM_OK;
+}
+
 template <typename T> OpView<T> LevelHost::view() const {
   OpView<T> v{};
   for (int a = 0; a < 3; ++a) {
@@ -607,6 +628,7 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.ntot = ntot;
   v.somm = somm;
   for (int a = 0; a < 3; ++a) v.bt[a] = bt[a];
+  v.phim = phim64;
   return v;
 }
 template OpView<double> LevelHost::view<double>() const;
@@ -623,6 +645,11 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
   if (k->phi) {
     if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
     HELM_CUDA(cudaMemcpyAsync(H.phi64, k->phi, sizeof(double) * H.ntot, cudaMemcpyHostToDevice, st));
+  }
+  if (k->phi_im) {
+    if ((s = ctx_alloc(c, (void**)&H.phim64, sizeof(double) * H.ntot)) != HELM_OK) return s;
+    HELM_CUDA(cudaMemcpyAsync(H.phim64, k->phi_im, sizeof(double) * H.ntot, cudaMemcpyHostToDevice, st));
+    if ((s = uniform_needs_real_phi(H, st)) != HELM_OK) return s;
   }
   // the diagonal of H at every point: outside the uniform interior the stencil kernels read it
   // instead of summing the axes' centre coefficients and subtracting phi (FP64 operations are
@@ -662,6 +689,8 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     L0.s = s;
     L0.phi0 = c->H.phi0;
     L0.phi64 = c->H.phi64;  // same field, shared
+    L0.phim64 = c->H.phim64;
+    if (L0.phim64 && (rc = uniform_needs_real_phi(L0, st)) != HELM_OK) return rc;
     if (L0.phi64 && f32) {
       if ((rc = ctx_alloc(c, (void**)&L0.phi32, sizeof(float) * L0.ntot)) != HELM_OK) return rc;
       k_to_f32<<<ceil_div(L0.ntot, 256), 256, 0, st>>>(L0.phi64, L0.phi32, L0.ntot);
@@ -709,8 +738,14 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       k_phi_inject<<<ceil_div(C.ntot, 256), 256, 0, st>>>(F.phi64, F.n[0], F.n[1], F.dim, C.phi64,
                                                           C.phi32, C.n[0], C.n[1], C.n[2]);
     }
+    if (F.phim64) {  // the imaginary part is injected like the real part
+      if ((rc = ctx_alloc(c, (void**)&C.phim64, sizeof(double) * C.ntot)) != HELM_OK) return rc;
+      k_phi_inject<<<ceil_div(C.ntot, 256), 256, 0, st>>>(F.phim64, F.n[0], F.n[1], F.dim, C.phim64,
+                                                          nullptr, C.n[0], C.n[1], C.n[2]);
+    }
     HELM_CUDA(cudaGetLastError());
     if ((rc = find_uniform(C, st)) != HELM_OK) return rc;
+    if (C.phim64 && (rc = uniform_needs_real_phi(C, st)) != HELM_OK) return rc;
     if (galerkin) {
       // R F P replaces the rediscretised row; its uniform-interior shortcut does not apply
       for (int a = 0; a < 3; ++a) { C.ulo[a] = 1; C.uhi[a] = 0; }

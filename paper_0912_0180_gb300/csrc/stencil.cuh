@@ -100,7 +100,7 @@ __device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __res
     if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
     if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
     d = cadd<T>(d, cconv<T, double>(somm_diag(op, i, j, l, (double)ph)));
-    d = csub<T>(d, cscale<T>(ph, op.s));
+    d = op.phim ? csub<T>(d, cmul<T>(op.s, mkc<T>(ph, (T)op.phim[p]))) : csub<T>(d, cscale<T>(ph, op.s));
   }
   return cfma<T>(d, xp, op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p));
 }

@@ -62,14 +62,19 @@ def _grid(problem) -> "L.Grid":
 
 
 def _kspec(problem):
-    """The k specification and the host array it points to (keep it alive while in use)."""
+    """The k specification and the host arrays it points to (keep them alive while in use)."""
     k = L.KSpec()
     k.k0 = problem.k0
-    phi = None
+    keep = []
     if problem.phi is not None:
         phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
         k.phi = phi.ctypes.data
-    return k, phi
+        keep.append(phi)
+    if getattr(problem, "phi_im", None) is not None:
+        im = np.ascontiguousarray(problem.phi_im, dtype=np.float64)
+        k.phi_im = im.ctypes.data
+        keep.append(im)
+    return k, keep
 
 
 def _precond(precond, mg_dtype: str = "c64", flags: int = 0) -> "L.Precond":
@@ -230,24 +235,9 @@ class Server:
         """Queues one request; `rhs` (nrhs x N complex128) replaces problem.b when given, and
         wait() then returns x with the same shape."""
         rq = L.Request()
-        g = rq.grid
-        g.dim = problem.dim
-        for a in range(3):
-            g.n_int[a] = problem.n_int[a]
-            g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
-            g.extent[a] = problem.extent[a]
-        g.theta_gamma = problem.theta_gamma
-        g.ecs_ramp = getattr(problem, "ecs_ramp", 0)
-        rq.k.k0 = problem.k0
-        phi = None
-        if problem.phi is not None:
-            phi = np.ascontiguousarray(problem.phi, dtype=np.float64)
-            rq.k.phi = phi.ctypes.data
-        rq.pc = L.Precond(precond.kind, precond.theta_beta, complex(precond.shift).real,
-                          complex(precond.shift).imag, precond.nu1, precond.nu2, precond.smoother,
-                          precond.omega, precond.max_levels, precond.coarse_max,
-                          L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128,
-                          L.HELM_PF_GALERKIN if getattr(precond, "galerkin", False) else 0)
+        rq.grid = _grid(problem)
+        rq.k, phi = _kspec(problem)  # the server copies the arrays at submission
+        rq.pc = _precond(precond, mg_dtype)
         rq.opts = L.SolveOpts(method, s, tol, maxmv, max_restarts, None, None, 0)
         sh = None
         if shadow is not None:
@@ -318,14 +308,7 @@ def select_precond(problem, start, f: torch.Tensor, max_cycles: int = 20, reduct
 
 def estimate_bytes(problem, precond, mg_dtype: str = "c64", method: int = 0, s: int = 4) -> int:
     lib = L.load()
-    g = L.Grid()
-    g.dim = problem.dim
-    for a in range(3):
-        g.n_int[a] = problem.n_int[a]
-        g.n_layer[a][0], g.n_layer[a][1] = problem.n_layer[a]
-        g.extent[a] = problem.extent[a]
-    pc = L.Precond(precond.kind, precond.theta_beta, 0.0, 0.0, precond.nu1, precond.nu2, precond.smoother,
-                   precond.omega, precond.max_levels, precond.coarse_max,
-                   L.HELM_C64 if mg_dtype == "c64" else L.HELM_C128, 0)
+    g = _grid(problem)
+    pc = _precond(precond, mg_dtype)
     o = L.SolveOpts(method, s, 1e-6, 1000, 3, None, None, 0)
     return int(lib.helm_estimate_bytes(C.byref(g), C.byref(pc), C.byref(o)))

@@ -778,3 +778,67 @@ def test_galerkin3d_levels_vcycle_and_solve(shape, mg):
         assert abs(info.matvecs - io["matvecs"]) <= 2
         assert rel(x.cpu().numpy(), xo) < 1e-9
     h.close()
+
+
+CZ_CASES = [
+    # dim, n_int, layers, ramp, k0, preconditioner index into PCS
+    (2, (40, 29), ((5, 0), (3, 8)), 0, 12.0, 0),
+    (2, 64, 16, 6, 20.0, 2),
+    (3, (12, 9, 10), ((2, 3), (0, 2), (3, 0)), 0, 5.0, 0),
+]
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("ci", range(len(CZ_CASES)))
+def test_complex_z_potential_parity(ci, mg):
+    """k read at the complex node positions of the layers (phi complex there): H, every level's
+    operator, the V-cycle fused and unfused, and an FP64 solve against the oracle."""
+    dim, n_int, nl, ramp, k0, pci = CZ_CASES[ci]
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=k0, phi_kind="bump", rhs="gauss", seed=41,
+                        bump_centre=(0.15, 0.8, 0.5), bump_width2=0.05, ecs_ramp=ramp, complex_z=True)
+    assert np.abs(p.phi_im).max() > 1e-3
+    pc = PCS[pci]
+    o = Oracle(p, pc)
+    x = hi.random_vector(p.n, 4)
+    if mg == "c128":
+        h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+        assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+        h0.close()
+    dt = torch.complex128 if mg == "c128" else torch.complex64
+    tol = 1e-11 if mg == "c128" else 2e-5
+    for fused in (True, False):
+        h = Helm(p, pc, mg_dtype=mg, fused=fused)
+        assert h.nlev == o.nlev
+        if fused:
+            for lvl in range(o.nlev - 1):
+                a = hi.random_vector(o.level_size(1, lvl), 9 + lvl).astype(np.complex64).astype(np.complex128)
+                out = torch.empty(len(a), dtype=dt, device="cuda")
+                h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
+                assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+        z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
+        assert rel(z, o.vcycle(x)) < (1e-10 if mg == "c128" else 5e-5)
+        if mg == "c128" and fused:
+            xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
+            xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
+            assert info.status == 0 and io["status"] == 0
+            assert abs(info.matvecs - io["matvecs"]) <= 2
+            assert rel(xs.cpu().numpy(), xo) < 1e-9
+        h.close()
+
+
+def test_complex_phi_inside_the_uniform_interior():
+    """An imaginary part of phi inside the interior (not what complex node positions give, but
+    allowed) drops the uniform-interior shortcut rather than being ignored there."""
+    p = _problem(CASES[3])
+    p.phi = np.full(p.n, 20.0 ** 2)
+    p.phi_im = 0.3 * np.random.default_rng(3).standard_normal(p.n)
+    o = Oracle(p, PCS[0])
+    x = hi.random_vector(p.n, 5)
+    h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+    assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    h0.close()
+    for mg in ("c128", "c64"):
+        h = Helm(p, PCS[0], mg_dtype=mg)
+        z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
+        assert rel(z, o.vcycle(x)) < (1e-10 if mg == "c128" else 5e-5)
+        h.close()
