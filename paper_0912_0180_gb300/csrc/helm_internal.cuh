@@ -147,7 +147,8 @@ struct LevelHost {
   int somm = 0;
   double2 bt[3] = {};
   double* phim64 = nullptr;  // imaginary part of phi (FP64), nullptr when phi is real
-  // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, -1 by the block-count rule
+  // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, 2 one warp, 3 square, -1 by the
+  // block-count rule
   int tile_down = -1, tile_up = -1;
   // work vectors (MG type), allocated for multigrid levels
   void* u = nullptr;

@@ -34,12 +34,14 @@ namespace helm {
 // levels with at least two blocks per SM; otherwise quarter / half tiles of 128 threads, so
 // that a small level still spreads over most SMs (in FP64 one block's arithmetic on one SM
 // otherwise sets the level's time).  The autotuner chooses among these and a one-warp tile.
-constexpr int DN_CX = 16, DN_CY = 8, DN_SCX = 8, DN_SCY = 4, DN_TCX = 4, DN_TCY = 2;
-constexpr int UP_FX = 32, UP_FY = 8, UP_SFX = 16, UP_SFY = 8, UP_TFX = 8, UP_TFY = 4;
+constexpr int DN_CX = 16, DN_CY = 8, DN_SCX = 8, DN_SCY = 4, DN_TCX = 4, DN_TCY = 2, DN_QCX = 8, DN_QCY = 8;
+constexpr int UP_FX = 32, UP_FY = 8, UP_SFX = 16, UP_SFY = 8, UP_TFX = 8, UP_TFY = 4, UP_QFX = 16, UP_QFY = 16;
 constexpr int FUSED_THREADS = 256, FUSED_SMALL_THREADS = 128, FUSED_TINY_THREADS = 32;
 // tile choices (LevelHost::tile_down / tile_up): the autotuner also tries a tiny tile of one warp,
-// which spreads a small FP64 level over many more SMs
-enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2 };
+// which spreads a small FP64 level over many more SMs, and a square tile of 128 threads (8 x 8
+// coarse / 16 x 16 fine), whose halo is smaller than the small tile's and whose block count falls
+// between the small and the large tile's (for an even spread over the SMs)
+enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2, TILE_SQUARE = 3 };
 
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
@@ -578,6 +580,7 @@ static void down_tile(int tile, const LevelHost& F, const LevelHost& C, const cx
                       const int* skip, cudaStream_t st) {
   if (tile == TILE_BIG) down_launch<T, RB, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else if (tile == TILE_TINY) down_launch<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  else if (tile == TILE_SQUARE) down_launch<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
 }
 
@@ -605,6 +608,7 @@ static void up_tile(int tile, const LevelHost& F, const LevelHost& C, const cx<T
                     const cx<T>* f, TO* o, T om, const int* skip, cudaStream_t st) {
   if (tile == TILE_BIG) up_launch<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
   else if (tile == TILE_TINY) up_launch<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  else if (tile == TILE_SQUARE) up_launch<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
   else up_launch<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
 }
 
@@ -629,7 +633,7 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
 }
 
 // ---- autotuner ------------------------------------------------------------------------------
-// On every fused 2D level the large, small and one-warp tiles of k_down2d and k_up2d are timed with
+// On every fused 2D level the large, small, square and one-warp tiles of k_down2d and k_up2d are timed with
 // CUDA events (mean of three launches after one warm-up) on zeroed buffers of the level's shape,
 // and the fastest is kept; then whole V-cycles are timed for every admissible depth of the
 // one-block tail (from the deepest that fits its budgets to none) and the fastest depth is kept.
@@ -712,7 +716,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     for (int l = 0; l < nl - 1; ++l) {
       if (c->lv[l].stg64) continue;  // Galerkin levels do not run the fused kernels
       auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
-      auto valid = [](int t) { return t == TILE_BIG || t == TILE_SMALL || t == TILE_TINY; };
+      auto valid = [](int t) { return t == TILE_BIG || t == TILE_SMALL || t == TILE_TINY || t == TILE_SQUARE; };
       if (it != g_tune.end() && valid(it->second.first) && valid(it->second.second)) {
         c->lv[l].tile_down = it->second.first;
         c->lv[l].tile_up = it->second.second;
@@ -754,7 +758,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     const LevelHost& C = c->lv[l + 1];
     int best_d = TILE_BIG, best_u = TILE_BIG;
     float td = 1e30f, tu = 1e30f;
-    for (int tile : {TILE_BIG, TILE_SMALL, TILE_TINY}) {
+    for (int tile : {TILE_BIG, TILE_SMALL, TILE_TINY, TILE_SQUARE}) {
       float a = time_variant([&] { down_tile<T, RB>(tile, F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
       float b = time_variant([&] { up_tile<T, RB, T>(tile, F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
       if (a < td) { td = a; best_d = tile; }
