@@ -899,3 +899,14 @@ def test_complex_z_potential_exact_for_quadratics(dim, ramp):
     s = dataclasses.replace(p, phi_im=None)
     x = hi.random_vector(p.n, 3)
     assert np.array_equal(Oracle(r).apply(x), Oracle(s).apply(x))
+
+
+@pytest.mark.parametrize("ramp", [0, 5])
+def test_complex_coordinates_agree_with_the_oracle_widths(ramp):
+    """The generator's complex node coordinates (used to sample k at complex positions) step by the
+    oracle's own layer widths: z_{j+1} - z_j = gap_{j+1} between consecutive unknowns."""
+    p = hi.make_problem(1, 21, (6, 7), theta_gamma=0.6, k0=1.0, rhs="zero", ecs_ramp=ramp)
+    z = hi.axis_positions_complex(21, (6, 7), 1.0, 0.6, ramp)
+    gap = Oracle(p).axis_tables(0, 0, 0)["gap"]
+    assert len(z) == p.n
+    assert np.allclose(np.diff(z), gap[1:-1], rtol=0, atol=1e-14)
