@@ -635,7 +635,8 @@ def run_gmres(args, torch, ranks, dev, local):
         for mg in ("c128", "c64"):
             h = Helm(p, pc, mg_dtype=mg)
             for name, meth, s in methods:
-                kw = dict(method=meth, s=s, tol=tol, maxmv=MP_MAXMV, shadow=shadow if meth == hi.IDR else None)
+                kw = dict(method=meth, s=s, tol=tol, maxmv=MP_MAXMV, shadow=shadow if meth == hi.IDR else None,
+                          host_loop=args.host_loop)
                 for _ in range(args.warmup):
                     h.solve(b, **kw)
                 ms, info = [], None
