@@ -694,14 +694,20 @@ __global__ void k_gm_w(const KrylovState* S, OpView<double> H, const double2* __
 // h_i = v_i^H w for i = 0..j: each block takes a contiguous slice of the points, so that its
 // slice of w stays in cache over the chunks of 8 basis vectors; the last block to finish adds
 // the per-block partials in block order (deterministic).
+// The block's 8 sums of a chunk go through shared memory, one warp per sum (8 sequential terms
+// per lane, then 5 shuffle levels): a slice holds only a few points per thread, and a shuffle
+// reduction of all 8 sums on every lane would cost as many FP64 additions as the products.
 __global__ void k_gm_dots(KrylovState* S, const double2* __restrict__ V, const double2* __restrict__ w, long n,
                           double2* partials, double2* h, int tk) {
+  static_assert(KT == 256, "one warp per chunk sum");
   pdl_entry();
   if (S->done) return;
+  __shared__ double2 red[8][KT];
   const int j = S->k;
   const int G = gridDim.x;
   const long L = (n + G - 1) / G;
   const long beg = blockIdx.x * L, end = beg + L < n ? beg + L : n;
+  const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i0 = 0; i0 <= j; i0 += 8) {
     double2 acc[8];
 #pragma unroll
@@ -712,12 +718,26 @@ __global__ void k_gm_dots(KrylovState* S, const double2* __restrict__ V, const d
       for (int q = 0; q < 8; ++q)
         if (i0 + q <= j) acc[q] = cfmac<double>(V[(size_t)(i0 + q) * n + p], wp, acc[q]);
     }
-    block_sum<8>(acc);
-    if (threadIdx.x == 0)
+    __syncthreads();  // the previous chunk's readers are done with red
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (i0 + q <= j) partials[(size_t)(i0 + q) * G + blockIdx.x] = acc[q];
+    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    double2 t = mkc<double>(0.0, 0.0);
+#pragma unroll
+    for (int k = lane; k < KT; k += 32) {
+      t.x += red[wq][k].x;
+      t.y += red[wq][k].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_down_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_down_sync(0xffffffffu, t.y, o);
+    }
+    if (lane == 0 && i0 + wq <= j) partials[(size_t)(i0 + wq) * G + blockIdx.x] = t;
   }
+  // the partials were written by lane 0 of every warp: each fences its own writes, and the block
+  // barrier orders them before the ticket
+  __threadfence();
+  __syncthreads();
   __shared__ bool last;
   if (threadIdx.x == 0) {
     __threadfence();
