@@ -910,3 +910,21 @@ def test_complex_coordinates_agree_with_the_oracle_widths(ramp):
     gap = Oracle(p).axis_tables(0, 0, 0)["gap"]
     assert len(z) == p.n
     assert np.allclose(np.diff(z), gap[1:-1], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("pck", [hi.PC_NONE, hi.PC_CSL])
+def test_idr1_reproduces_bicgstab_every_second_matvec(pck):
+    """Sonneveld & van Gijzen (IDR(s), the method of Section 6.2): IDR(1) with the shadow space
+    spanned by r_0 produces the Bi-CGSTAB residuals (shadow r^ = r_0) at every second matvec, with
+    or without the right preconditioner; the odd-step residuals differ (IDR's extra minimal-residual
+    steps), which also shows the comparison is not vacuous."""
+    p = _prob(2, 12, 3, theta=0.5, k0=6.0, seed=3)
+    pc = hi.Precond(kind=pck, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, pc)
+    _, ib = o.solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-12, maxmv=200), history=True)
+    _, ii = o.solve(p.b, hi.SolveOpts(method=hi.IDR, s=1, tol=1e-12, maxmv=200),
+                    shadow=p.b.reshape(1, -1).copy(), history=True)
+    hb, hI = ib["history"], ii["history"]
+    even = np.arange(1, 20, 2)  # matvecs 2, 4, ..., 20
+    assert np.allclose(hI[even], hb[even], rtol=1e-8, atol=0)
+    assert not np.allclose(hI[even - 1], hb[even - 1], rtol=1e-3, atol=0)
