@@ -928,3 +928,40 @@ def test_idr1_reproduces_bicgstab_every_second_matvec(pck):
     even = np.arange(1, 20, 2)  # matvecs 2, 4, ..., 20
     assert np.allclose(hI[even], hb[even], rtol=1e-8, atol=0)
     assert not np.allclose(hI[even - 1], hb[even - 1], rtol=1e-3, atol=0)
+
+
+# ---- the model problems' resolution (Section 6, mesh-width tables) -------------------------------
+
+def _hmax_tables():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "model_problem_hmax.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        rows[(f[0], f[1])] = [float(v) for v in f[2:]]
+    return rows
+
+
+def test_model_problem_mesh_widths_follow_the_accuracy_rule():
+    """The paper's maximum mesh widths are the accuracy rule k_max h < 0.625 at the supremum of the
+    wave number, printed to three decimals (some entries rounded, some cut): for MP2 the supremum
+    sqrt(2 nu + k^2) sits at the origin; for MP3 the largest discrete value is at (h/2, h/2), where
+    phi = 4/h + k^2 turns the rule into k^2 h^2 + 4 h - 0.625^2 = 0 (independent of r).  A wrong
+    supremum (nu + k^2, or the MP3 value at (h, h)) misses most entries by far more than the
+    printed precision.  The generators' default grids respect the printed limits."""
+    t = _hmax_tables()
+    for nu in range(11):
+        for k in range(1, 6):
+            assert abs(0.625 / np.sqrt(2 * nu + k * k) - t[("mp2", str(nu))][k - 1]) <= 1.0e-3 + 1e-12
+    for k in range(1, 6):
+        h = (-4 + np.sqrt(16 + 4 * k * k * 0.625 ** 2)) / (2 * k * k)
+        assert abs(h - t[("mp3", "any")][k - 1]) <= 1.0e-3 + 1e-12
+    for nu, k in ((7.0, 2.0), (1.0, 4.0)):
+        p = hi.workload_mp2(nu=nu, k=k)
+        assert p.h(0) <= t[("mp2", str(int(nu)))][int(k) - 1]
+        # the largest phi on the grid sits at the node (h, h) next to the origin:
+        # 2 nu e^{-h^2} + k^2, between 2 nu (1 - h^2) + k^2 and the supremum 2 nu + k^2
+        h = p.h(0)
+        assert 2 * nu * (1 - h * h) + k * k <= p.phi.max() <= 2 * nu + k * k
+    p = hi.workload_mp3()  # r = 90, k = 2
+    assert p.h(0) <= t[("mp3", "any")][1]
