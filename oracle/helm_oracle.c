@@ -35,7 +35,44 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 typedef double complex cplx;
+
+/* Point-wise loops (stencil, smoothers, transfers, vector updates) may run on several threads:
+ * every element is computed by the same expression in the same order whatever the thread count,
+ * and every inner product and norm is a single-threaded sum in index order, so results are
+ * bitwise the same on one thread and on many.  PAR_FOR2 splits the two outer loops of a grid
+ * sweep, PAR_FOR a flat loop over unknowns; both stay serial up to 4096 unknowns. */
+#define PAR_PRAGMA(x) _Pragma(#x)
+#ifdef _OPENMP
+#define PAR_FOR2(n) PAR_PRAGMA(omp parallel for collapse(2) schedule(static) if ((n) > 4096))
+#define PAR_FOR(n) PAR_PRAGMA(omp parallel for schedule(static) if ((n) > 4096))
+#else
+#define PAR_FOR2(n)
+#define PAR_FOR(n)
+#endif
+
+/* Threads used by the point-wise loops (1 = serial); returns the previous value. */
+int orc_set_threads(int t) {
+#ifdef _OPENMP
+  int old = omp_get_max_threads();
+  if (t >= 1) omp_set_num_threads(t);
+  return old;
+#else
+  (void)t;
+  return 1;
+#endif
+}
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ---- public structs (mirrored by the ctypes wrapper in oracle.py) -------------------- */
 typedef struct {
@@ -329,6 +366,7 @@ static cplx offdiag_at(const level_t* L, const cplx* x, int i, int j, int l) {
 /* y = A x for the operator of a level: the d-fold sum of Shortley-Weller rows minus
  * sigma = s * phi (eq. "helmctu0" / "Helgen"; CSL eq. "helmctucsl"). */
 static void level_apply(const level_t* L, const cplx* x, cplx* y) {
+  PAR_FOR2(L->ntot)
   for (int l = 0; l < L->n[2]; ++l)
     for (int j = 0; j < L->n[1]; ++j)
       for (int i = 0; i < L->n[0]; ++i) {
@@ -348,6 +386,7 @@ static int lu_factor(cplx* A, int* piv, long n) {
     if (best == 0.0) return -1;
     if (p != k)
       for (long c = 0; c < n; ++c) { cplx t = A[k * n + c]; A[k * n + c] = A[p * n + c]; A[p * n + c] = t; }
+    PAR_FOR((n - k) * (n - k))
     for (long r = k + 1; r < n; ++r) {
       cplx m = A[r * n + k] / A[k * n + k];
       A[r * n + k] = m;
@@ -525,6 +564,10 @@ static void level_galerkin3d(const level_t* F, level_t* C) {
 /* phi_im (optional): the imaginary part of phi at every unknown, for k evaluated at the complex
  * node positions of the layers (the alternative to reading k at real positions); the Sommerfeld
  * boundary term keeps sqrt of the real part (its nodes are real). */
+void orc_destroy(orc_ctx* c);
+
+/* Returns NULL when the coarsest preconditioner level is singular (its dense LU meets a zero
+ * pivot). */
 orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, double k0,
                     const orc_precond* pc) {
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
@@ -563,7 +606,12 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, 
   c->lu = malloc(sizeof(cplx) * c->nco * c->nco);
   c->piv = malloc(sizeof(int) * c->nco);
   level_dense(C, c->lu);
-  if (lu_factor(c->lu, c->piv, c->nco) != 0) { /* singular coarsest operator */ }
+  if (lu_factor(c->lu, c->piv, c->nco) != 0) {
+    /* singular coarsest operator (a coarse grid at a resonance of M, Section 5.1): no
+     * preconditioner can be built, so the caller gets no context rather than NaNs later */
+    orc_destroy(c);
+    return NULL;
+  }
   return c;
 }
 
@@ -625,6 +673,7 @@ void orc_dense(const orc_ctx* c, int which, int lvl, cplx* A) { level_dense(pick
 /* One damped-Jacobi sweep: u <- u + omega D^{-1} (f - A u). */
 static void jacobi_sweep(const level_t* L, double omega, cplx* u, const cplx* f, cplx* tmp) {
   level_apply(L, u, tmp);
+  PAR_FOR2(L->ntot)
   for (int l = 0; l < L->n[2]; ++l)
     for (int j = 0; j < L->n[1]; ++j)
       for (int i = 0; i < L->n[0]; ++i) {
@@ -637,7 +686,9 @@ static void jacobi_sweep(const level_t* L, double omega, cplx* u, const cplx* f,
 /* One red-black Gauss-Seidel sweep: red points ((i+j+l) even) then black points, each
  * solving its own row with the current neighbour values. */
 static void rbgs_sweep(const level_t* L, cplx* u, const cplx* f) {
-  for (int colour = 0; colour < 2; ++colour)
+  for (int colour = 0; colour < 2; ++colour) {
+    /* the points of one colour read only the other colour: any order gives the same values */
+    PAR_FOR2(L->ntot)
     for (int l = 0; l < L->n[2]; ++l)
       for (int j = 0; j < L->n[1]; ++j)
         for (int i = 0; i < L->n[0]; ++i) {
@@ -645,6 +696,7 @@ static void rbgs_sweep(const level_t* L, cplx* u, const cplx* f) {
           long p = lidx(L, i, j, l);
           u[p] = (f[p] - offdiag_at(L, u, i, j, l)) / diag_at(L, i, j, l);
         }
+  }
 }
 
 static void smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps, cplx* tmp) {
@@ -659,6 +711,7 @@ static void smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps
  * with weights 1/4, 1/2, 1/4 per axis (tensor product); missing neighbours are Dirichlet. */
 static void restrict_fw(const level_t* F, const level_t* C, const cplx* r, cplx* fc) {
   static const double w[3] = {0.25, 0.5, 0.25};
+  PAR_FOR2(C->ntot)
   for (int cl = 0; cl < C->n[2]; ++cl)
     for (int cj = 0; cj < C->n[1]; ++cj)
       for (int Ii = 0; Ii < C->n[0]; ++Ii) {
@@ -688,6 +741,7 @@ static int interp1(int i, int nc, int* ci, double* w) {
 
 /* u_f += P e_c, bilinear / trilinear interpolation (tensor product of 1D linear). */
 static void prolong_add(const level_t* F, const level_t* C, const cplx* ec, cplx* u) {
+  PAR_FOR2(F->ntot)
   for (int l = 0; l < F->n[2]; ++l)
     for (int j = 0; j < F->n[1]; ++j)
       for (int i = 0; i < F->n[0]; ++i) {
@@ -718,6 +772,7 @@ static void vcycle_rec(const orc_ctx* c, int lvl, const cplx* f, cplx* u) {
   memset(u, 0, sizeof(cplx) * n);
   smooth(c, lvl, u, f, c->pc.nu1, tmp);
   level_apply(L, u, tmp);
+  PAR_FOR(n)
   for (long p = 0; p < n; ++p) r[p] = f[p] - tmp[p];
   restrict_fw(L, C, r, fc);
   vcycle_rec(c, lvl + 1, fc, ec);
@@ -791,6 +846,7 @@ static int bicgstab_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, doubl
     if (!finite_c(rho)) { st = ST_NAN; break; }
     if (rho == 0) { st = ST_BREAKDOWN; break; }
     cplx beta = (rho / rho_old) * (alpha / omega);
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
     orc_vcycle(c, p, ph);
     level_apply(&c->H, ph, v);
@@ -800,18 +856,21 @@ static int bicgstab_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, doubl
     if (!finite_c(rv)) { st = ST_NAN; break; }
     if (rv == 0) { st = ST_BREAKDOWN; break; }
     alpha = rho / rv;
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) sv[i] = r[i] - alpha * v[i];
     double sn = nrm2(sv, n) / bn;
     if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = sn;
     info->rel_res_recur = sn;
     if (!isfinite(sn)) { st = ST_NAN; break; }
     if (sn < o->tol) {
+      PAR_FOR(n)
       for (long i = 0; i < n; ++i) x[i] += alpha * ph[i];
       memcpy(r, sv, sizeof(cplx) * n);
       st = ST_OK;
       break;
     }
     if (info->matvecs >= o->maxmv) {
+      PAR_FOR(n)
       for (long i = 0; i < n; ++i) x[i] += alpha * ph[i];
       memcpy(r, sv, sizeof(cplx) * n);
       st = ST_MAXMV;
@@ -825,6 +884,7 @@ static int bicgstab_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, doubl
     if (!isfinite(tt) || !finite_c(ts)) { st = ST_NAN; break; }
     if (tt == 0) { st = ST_BREAKDOWN; break; }
     omega = ts / tt;
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) {
       x[i] += alpha * ph[i] + omega * sh[i];
       r[i] = sv[i] - omega * t[i];
@@ -898,6 +958,7 @@ static int idr_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
     if (!isfinite(tt)) { st = ST_NAN; goto done; }
     if (tt == 0) { st = ST_BREAKDOWN; goto done; }
     omega = dotc(t, r, n) / tt;
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) {
       dX[k * n + i] = omega * z[i];
       dR[k * n + i] = -omega * t[i];
@@ -919,6 +980,7 @@ static int idr_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
     for (int k = 0; k <= s; ++k) {
       if (info->matvecs >= o->maxmv) { st = ST_MAXMV; goto done; }
       if (small_solve(Mk, m, cc, s) != 0) { st = ST_BREAKDOWN; goto done; }
+      PAR_FOR(n)
       for (long i = 0; i < n; ++i) {
         cplx acc = 0;
         for (int j = 0; j < s; ++j) acc -= dR[(long)j * n + i] * cc[j];
@@ -927,6 +989,7 @@ static int idr_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
       }
       orc_vcycle(c, v, z);
       /* new x-space difference: -dX c + omega z */
+      PAR_FOR(n)
       for (long i = 0; i < n; ++i) {
         cplx acc = 0;
         for (int j = 0; j < s; ++j) acc -= dX[(long)j * n + i] * cc[j];
@@ -940,17 +1003,21 @@ static int idr_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double bn,
         if (!isfinite(tt)) { st = ST_NAN; goto done; }
         if (tt == 0) { st = ST_BREAKDOWN; goto done; }
         omega = dotc(t, v, n) / tt;
+        PAR_FOR(n)
         for (long i = 0; i < n; ++i) {
           dRo[i] = q[i] - omega * t[i];
           dXo[i] = xs[i] + omega * z[i];
         }
       } else {
+        PAR_FOR(n)
         for (long i = 0; i < n; ++i) dXo[i] = xs[i] + omega * z[i];
         level_apply(&c->H, dXo, t);
+        PAR_FOR(n)
         for (long i = 0; i < n; ++i) dRo[i] = -t[i];
       }
       info->matvecs++;
       info->iters++;
+      PAR_FOR(n)
       for (long i = 0; i < n; ++i) { r[i] += dRo[i]; x[i] += dXo[i]; }
       rn = nrm2(r, n) / bn;
       if (hist && info->matvecs - 1 < hist_cap) hist[info->matvecs - 1] = rn;
@@ -974,9 +1041,11 @@ static void orthonormalise(cplx* P, int s, long n) {
     for (int i = 0; i < j; ++i) {
       cplx* pi = &P[(long)i * n];
       cplx h = dotc(pi, pj, n);
+      PAR_FOR(n)
       for (long k = 0; k < n; ++k) pj[k] -= h * pi[k];
     }
     double nn = nrm2(pj, n);
+    PAR_FOR(n)
     for (long k = 0; k < n; ++k) pj[k] /= nn;
   }
 }
@@ -1007,6 +1076,7 @@ static int gmres_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double b
     if (!isfinite(beta)) { st = ST_NAN; break; }
     if (beta / bn < o->tol) { st = ST_OK; break; }
     if (info->matvecs >= o->maxmv) { st = ST_MAXMV; break; }
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) V[i] = r[i] / beta;
     for (int i = 0; i <= m; ++i) g[i] = 0;
     g[0] = beta;
@@ -1023,6 +1093,7 @@ static int gmres_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double b
       for (int i = 0; i <= j; ++i) col[i] = 0;
       for (int pass = 0; pass < 2; ++pass) {
         for (int i = 0; i <= j; ++i) h[i] = dotc(V + (size_t)i * n, w, n);
+        PAR_FOR(n)
         for (long q = 0; q < n; ++q) {
           cplx acc = 0;
           for (int i = 0; i <= j; ++i) acc += h[i] * V[(size_t)i * n + q];
@@ -1056,6 +1127,7 @@ static int gmres_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double b
       info->rel_res_recur = est;
       if (!isfinite(est) || !isfinite(hn)) { st = ST_NAN; done = 1; break; }
       if (est < o->tol || hn == 0) { st = ST_OK; done = 1; break; }
+      PAR_FOR(n)
       for (long q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
     }
     /* x += M^{-1} V y, R y = g (upper triangular k x k) */
@@ -1065,15 +1137,18 @@ static int gmres_run(const orc_ctx* c, const cplx* b, cplx* x, cplx* r, double b
       y[i] = acc / Hs[i + (size_t)(m + 1) * i];
     }
     if (k > 0) {
+      PAR_FOR(n)
       for (long q = 0; q < n; ++q) {
         cplx acc = 0;
         for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * n + q];
         w[q] = acc;
       }
       orc_vcycle(c, w, z);
+      PAR_FOR(n)
       for (long q = 0; q < n; ++q) x[q] += z[q];
     }
     level_apply(&c->H, x, r);
+    PAR_FOR(n)
     for (long q = 0; q < n; ++q) r[q] = b[q] - r[q];
     if (done) break;
   }
@@ -1109,6 +1184,7 @@ int orc_solve(const orc_ctx* c, const cplx* b, cplx* x, const orc_solve_opts* o,
                         : gmres_run(c, b, x, r, bn, o, info, hist, hist_cap);
     /* true residual */
     level_apply(&c->H, x, r);
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) r[i] = b[i] - r[i];
     info->rel_res_true = nrm2(r, n) / bn;
     if (st != ST_OK) break;
@@ -1141,8 +1217,10 @@ int orc_mg_iterate(const orc_ctx* c, const cplx* f, int max_cycles, double reduc
   int result = -1;
   for (int k = 1; k <= max_cycles; ++k) {
     vcycle_rec(c, 0, r, z);
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) u[i] += z[i];
     level_apply(&c->M[0], u, r);
+    PAR_FOR(n)
     for (long i = 0; i < n; ++i) r[i] = f[i] - r[i];
     double rel = nrm2(r, n) / fn;
     if (hist) hist[k - 1] = rel;
@@ -1168,7 +1246,7 @@ int orc_select_precond(const orc_grid* g, const double* phi, const double* phi_i
   long n = 1;
   for (int d = 0; d < g->dim; ++d) {
     int lo = g->n_layer[d][0], hi = g->n_layer[d][1];
-    n *= g->n_int[d] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : 0);
+    n *= g->n_int[d] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : hi < 0 ? 1 : 0);
   }
   cplx* u = malloc(sizeof(cplx) * n);
   orc_precond pc = *start;
@@ -1178,7 +1256,7 @@ int orc_select_precond(const orc_grid* g, const double* phi, const double* phi_i
     if (t > 0) p *= factor;
     if (pc.kind == 1) pc.shift_im = p; else pc.theta_beta = p;
     orc_ctx* c = orc_create(g, phi, phi_im, k0, &pc);
-    int k = orc_mg_iterate(c, f, max_cycles, reduction, u, NULL);
+    int k = c ? orc_mg_iterate(c, f, max_cycles, reduction, u, NULL) : -1; /* singular: no M */
     orc_destroy(c);
     params[t] = p;
     cycles[t] = k;

@@ -24,14 +24,31 @@ def lib_path() -> str:
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile helm_oracle.c into oracle/liboracle.so (portable flags, no FMA contraction)."""
+    """Compile helm_oracle.c into oracle/liboracle.so (portable flags, no FMA contraction), with
+    OpenMP for its point-wise loops when the compiler has it (results are bitwise the same on
+    any number of threads; without OpenMP the library is single-threaded)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                   "-o", _LIB + ".tmp", _SRC, "-lm"]
-            subprocess.run(cmd, check=True)
+            base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-o", _LIB + ".tmp", _SRC, "-lm"]
+            r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+            if r.returncode != 0:
+                subprocess.run(base, check=True)
             os.replace(_LIB + ".tmp", _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's point-wise loops (1 = serial); returns the previous count."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
+
+
+class OracleError(RuntimeError):
+    pass
 
 
 class _Grid(C.Structure):
@@ -88,6 +105,10 @@ def _load():
         lib.orc_select_precond.argtypes = [C.POINTER(_Grid), vp, vp, dp, C.POINTER(_Precond), vp, ip, dp, dp, ip,
                                            C.POINTER(_Precond), vp, vp, C.POINTER(C.c_int)]
         lib.orc_select_precond.restype = ip
+        lib.orc_set_threads.argtypes = [ip]
+        lib.orc_set_threads.restype = ip
+        lib.orc_get_threads.argtypes = []
+        lib.orc_get_threads.restype = ip
         _lib = lib
     return _lib
 
@@ -167,6 +188,8 @@ class Oracle:
         self._h = lib.orc_create(C.byref(g), _ptr(self._phi) if self._phi is not None else None,
                                  _ptr(self._phi_im) if self._phi_im is not None else None,
                                  problem.k0, C.byref(p))
+        if not self._h:
+            raise OracleError("singular coarsest preconditioner level (zero pivot in its dense LU)")
         self.n = problem.n
         self.nlev = lib.orc_num_levels(self._h)
 

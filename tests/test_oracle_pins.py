@@ -965,3 +965,47 @@ def test_model_problem_mesh_widths_follow_the_accuracy_rule():
         assert 2 * nu * (1 - h * h) + k * k <= p.phi.max() <= 2 * nu + k * k
     p = hi.workload_mp3()  # r = 90, k = 2
     assert p.h(0) <= t[("mp3", "any")][1]
+
+
+# ---- the oracle's threading and its failure on a singular coarsest level ------------------
+
+def test_threads_do_not_change_results():
+    """The point-wise loops run on several threads while every inner product is a serial sum in
+    index order: a solve (Bi-CGSTAB, IDR(4), GMRES) with each smoother gives bitwise the same
+    iterates, histories and counts on one thread and on four."""
+    import oracle
+    p = hi.make_problem(2, (90, 71), ((6, 4), (5, 7)), theta_gamma=0.5, k0=25.0, phi_kind="bump",
+                        rhs="gauss", seed=4, bump_centre=(0.4, 0.6))
+    assert p.n > 4096  # above the size at which the loops split
+    sh = hi.shadow_space(p.n, 4)
+    old = oracle.get_threads()
+    try:
+        for pc in (hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5),
+                   hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_RBGS)):
+            o = Oracle(p, pc)
+            for method, s in ((hi.BICGSTAB, 4), (hi.IDR, 4), (hi.GMRES, 12)):
+                opts = hi.SolveOpts(method=method, s=s, tol=1e-12, maxmv=40, max_restarts=0)
+                out = []
+                for t in (1, 4):
+                    oracle.set_threads(t)
+                    out.append(o.solve(p.b, opts, shadow=sh if method == hi.IDR else None, history=True))
+                (x1, i1), (x4, i4) = out
+                assert np.array_equal(x1, x4)
+                assert np.array_equal(i1["history"], i4["history"]) and i1["matvecs"] == i4["matvecs"]
+    finally:
+        oracle.set_threads(old)
+
+
+def test_singular_coarsest_level_is_an_error():
+    """One unknown, no layer (h = 1/2, so the Shortley-Weller centre weight is 8) and phi = 8
+    with the real CSL shift 1: the only (coarsest) level of M is exactly zero.  The oracle
+    refuses to build it instead of returning NaNs from the first V-cycle."""
+    import oracle
+    p = _prob(1, 3, 0, theta=0.0, k0=0.0, phi=np.array([8.0]))
+    assert p.n == 1
+    with pytest.raises(oracle.OracleError):
+        Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=1.0 + 0.0j))
+    # the same grid with a complex shift is regular and solves exactly
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=1.0 + 0.5j))
+    z = o.vcycle(np.array([1.0 + 0j]))
+    assert abs(z[0] - 1.0 / (8.0 - 8.0 * (1.0 + 0.5j))) < 1e-15

@@ -32,7 +32,8 @@ def _worker(rank, world, port, out):
 def test_two_replicas_take_the_slowest_rank():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    # the manager process is spawned, not forked: this process may already run OpenMP threads
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
