@@ -31,6 +31,10 @@
             solve server (150 GB budget); reports right-hand-side solves/s and the server's
             submit-to-completion latencies.
 
+  c1        64^2 interior + 16-node ECS layers, k = 20, centre point source, Bi-CGSTAB with the CSG
+            red-black Gauss-Seidel V(1,1) preconditioner to 1e-8: one solve per step, its p50 / p99
+            latency, the omega-Jacobi and FP32-multigrid variants, and the oracle's count and time.
+
 Every timed solve is certified by the FP64 true residual; a step whose solves did not all reach
 1e-6 aborts the run.
 """
@@ -84,7 +88,7 @@ def run(args):
     g.build()
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
-    fn = {"3d160": run_3d, "3d160g": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+    fn = {"c1": run_c1, "3d160": run_3d, "3d160g": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
           "mp2som": run_mp, "mp3som": run_mp,
           "select": run_select, "gmres": run_gmres}[args.workload]
     line = fn(args, torch, ranks, dev, local)
@@ -92,6 +96,102 @@ def run(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---- C1: the small single-solve latency case -------------------------------------------------
+
+def run_c1(args, torch, ranks, dev, local):
+    """64^2 interior + 16-node ECS layers (96^2 = 9216 unknowns), theta_gamma = 0.5, k = 20, unit
+    point source at the centre; Bi-CGSTAB preconditioned by one CSG (theta_beta = 0.3) V(1,1) cycle
+    with red-black Gauss-Seidel, to 1e-8, FP64 -- a single solve per step, latency-bound (its
+    vectors live in L2), so the line reports the solve's latency rather than a roofline.  Beside it:
+    the same solve with omega-Jacobi and with the FP32 V-cycle, the end-to-end time through pinned
+    host buffers, and the oracle's matvec count, solution error and time on this host."""
+    import bench
+    import oracle
+    from paper_0912_0180_gb300.helm import Helm
+    p = hi.workload_small_2d()
+    tol = 1e-8
+    pcs = {"rbgs": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS),
+           "jacobi": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)}
+    b = torch.from_numpy(p.b).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    nlat = max(args.steps, 200)
+
+    def latencies(h, count, host=None):
+        for _ in range(args.warmup):
+            h.solve(b, tol=tol, maxmv=2000)
+        ms, infos = [], []
+        for _ in range(count):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bi = host["b"].to(dev, non_blocking=True) if host else b
+            x, info = h.solve(bi, tol=tol, maxmv=2000)
+            if host:
+                host["x"].copy_(x, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        _check_tol(infos, "c1", tol)
+        return ms, infos
+
+    ctx = {"rbgs64": Helm(p, pcs["rbgs"], mg_dtype="c128"), "rbgs32": Helm(p, pcs["rbgs"], mg_dtype="c64"),
+           "jacobi64": Helm(p, pcs["jacobi"], mg_dtype="c128")}
+    with bench.ClockSampler(local) as clk:
+        ms, inf = latencies(ctx["rbgs64"], nlat)
+        other = {k: latencies(ctx[k], nlat) for k in ("rbgs32", "jacobi64")}
+    host = {"b": torch.from_numpy(p.b).pin_memory(), "x": torch.empty(p.n, dtype=torch.complex128).pin_memory()}
+    e2e_ms, _ = latencies(ctx["rbgs64"], args.steps, host)
+    # the oracle: same solve, its matvec count and solution, timed on this host's cores
+    cores = bench.host_cores()
+    oracle.set_threads(cores)
+    o = oracle.Oracle(p, pcs["rbgs"])
+    t = time.perf_counter()
+    reps = 0
+    while True:
+        xo, io = o.solve(p.b, hi.SolveOpts(tol=tol, maxmv=2000))
+        reps += 1
+        if time.perf_counter() - t > 2.0:
+            break
+    cpu_s = (time.perf_counter() - t) / reps
+    x12, _ = o.solve(p.b, hi.SolveOpts(tol=1e-12, maxmv=4000))
+    nref = np.linalg.norm(x12)
+    errs = {}
+    for k, h in ctx.items():
+        x, _ = h.solve(b, tol=tol, maxmv=2000)
+        errs[k] = float(np.linalg.norm(x.cpu().numpy() - x12) / nref)
+    step = ranks.max(statistics.mean(ms))
+    cfg = {"workload": p.name, "grid": "64^2 interior + 16 ECS nodes per side (96^2 unknowns)", "n_unknowns": p.n,
+           "solver": "Bi-CGSTAB, tol 1e-8 (FP64 true residual), one solve per step",
+           "multigrid": "CSG theta_beta=0.3, V(1,1) red-black Gauss-Seidel, FW, bilinear, rediscretised levels",
+           "l2": "flushed (256 MiB device write) before every timed solve"}
+    line = _base(args, ranks.job_rate(1, step), step, ranks.world, cfg, "c128")
+    line.update({
+        "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "solves": len(ms)},
+        "matvecs": inf[-1].matvecs, "oracle_matvecs": io["matvecs"],
+        "variants": {k: {"latency_ms": {"p50": _pct(v[0], 50), "p99": _pct(v[0], 99)}, "matvecs": v[1][-1].matvecs}
+                     for k, v in other.items()},
+        "error_vs_reference": {"reference": "FP64 oracle at tol 1e-12", **errs},
+        "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"the same solve, {reps} times, on all {cores} host cores"},
+        "clocks": clk.summary(),
+        "e2e": {"value": 1000.0 / statistics.mean(e2e_ms), "unit": "solves/s",
+                "path": "helm_solve with b copied in from pinned host memory and x copied out, every solve",
+                "h2d_bytes_per_step": p.n * 16, "d2h_bytes_per_step": p.n * 16},
+        "gpu_launches": int(sum(i.kernels for i in inf[:args.steps])),
+    })
+    for h in ctx.values():
+        h.close()
+    return line
+
+
+def _check_tol(infos, what, tol):
+    for i in infos:
+        if i.status != 0 or not i.rel_res_true < tol:
+            raise SystemExit(f"{what}: a timed solve did not converge: {i}")
 
 
 # ---- 3D ------------------------------------------------------------------------------------
@@ -598,6 +698,25 @@ def run_select(args, torch, ranks, dev, local):
                          "trials": [{"param": float(a), "cycles": int(c)} for a, c in zip(params, cycles)],
                          "solve_default": {"param": par(default), "matvecs": info_def.matvecs, "ms": ms_def},
                          "solve_chosen": {"param": par(chosen), "matvecs": info_ch.matvecs, "ms": ms_ch}}
+        # the CSL shift's sign (the paper's "1 - 0.5i" read literally, beta^2 = 1 - 0.5i, against the
+        # sign matched to the fourth-quadrant ECS spectrum, 1 + 0.5i): the multigrid factor of
+        # omega-Jacobi V(1,1) on M (30 cycles of the stationary iteration, FP64 hierarchy) and a
+        # preconditioned Bi-CGSTAB solve (FP32 V-cycle) each
+        sign = {}
+        for tag, sh_ in (("1+0.5i", 1 + 0.5j), ("1-0.5i", 1 - 0.5j)):
+            pc = hi.Precond(kind=hi.PC_CSL, shift=sh_, smoother=hi.SM_JACOBI, omega=0.5)
+            hm = Helm(p, pc, mg_dtype="c128")
+            k, _, hist = hm.mg_iterate(f, max_cycles=30, reduction=1e-12)
+            hm.close()
+            hs = Helm(p, pc, mg_dtype="c64")
+            xs_, inf = hs.solve(b, tol=TOL, maxmv=4000)
+            hs.close()
+            launches += inf.kernels
+            fac = float(hist[-1] ** (1.0 / len(hist))) if len(hist) else None
+            sign[tag] = {"mg_factor": fac, "mg_cycles_run": int(len(hist)), "mg_residual_ratio_last": float(hist[-1]),
+                         "bicgstab_status": int(inf.status), "bicgstab_matvecs": int(inf.matvecs),
+                         "bicgstab_true_rel_res": float(inf.rel_res_true)}
+        out["csl_shift_sign"] = sign
     total = sum(seconds)
     cfg = {"workload": "select-" + p.name, "n_unknowns": p.n,
            "rule": "parameter x 0.8 per trial (at most 16) while omega-Jacobi V(1,1) on M reaches 1e-6 in "
@@ -607,7 +726,7 @@ def run_select(args, torch, ranks, dev, local):
             "unit": "selections/s", "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / len(seconds), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": cfg}
-    line.update({"csl": out["csl"], "csg": out["csg"], "clocks": clk.summary(),
+    line.update({"csl": out["csl"], "csg": out["csg"], "csl_shift_sign": out["csl_shift_sign"], "clocks": clk.summary(),
                  "e2e": {"value": None, "unit": "selections/s", "path": "not measured in this mode",
                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                  "gpu_launches": int(launches)})

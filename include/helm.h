@@ -81,15 +81,31 @@ typedef struct {
   int ecs_ramp;         /* 0..1048576 */
 } helm_grid;
 
-/* Wave number: phi = k(x)^2 at the real node positions (the layers continue the real
- * coordinate).  phi == NULL means the constant k0. */
+/* Wave number k(x) (Section 2, eq. "helmctu0"; variable k: Section 4, eq. "Helgen"): the operator
+ * uses phi = k(x)^2 at the real node positions (the layers continue the real coordinate: along axis
+ * a the unknown with interior-node index j sits at j h, layer nodes at -m h and extent + m h).
+ * When phi (a HOST array) is given it is used as it stands; otherwise `kind` says how to form it on
+ * the device during helm_create:
+ *   HELM_K_CONST       k = k0 everywhere (a zero-initialised struct);
+ *   HELM_K_GAUSS_BUMP  k = k0 (1 + amp exp(-|x - centre|^2 / width2)), centre in the same absolute
+ *                      coordinates as the nodes (width2 > 0);
+ *   HELM_K_FIELD       k = field[p], a DEVICE array of N real values (x fastest, 8-byte aligned)
+ *                      borrowed during helm_create only; a non-finite entry makes helm_create return
+ *                      HELM_ERR_ARG.  The solve server does not take this kind (its requests are
+ *                      built later, on its own thread): pass phi instead. */
+enum { HELM_K_CONST = 0, HELM_K_GAUSS_BUMP = 1, HELM_K_FIELD = 2 };
 typedef struct {
   double k0;
-  const double* phi;    /* HOST pointer to N real values (x fastest), read during helm_create only */
+  const double* phi;    /* HOST pointer to N real values of k^2 (x fastest), read during helm_create
+                           only; NULL: see kind */
   const double* phi_im; /* HOST pointer to N values or NULL: the imaginary part of phi, for k read at
                            the complex node positions of the layers (the analytic continuation of
                            k); it must come with phi.  The uniform-interior shortcut of a level is
                            kept only where it vanishes (the interior nodes are real) */
+  int kind;             /* HELM_K_*, used when phi is NULL */
+  double amp, width2;   /* HELM_K_GAUSS_BUMP */
+  double centre[3];     /* HELM_K_GAUSS_BUMP */
+  const double* field;  /* HELM_K_FIELD: DEVICE pointer to N values of k */
 } helm_kspec;
 
 /* Preconditioner M and the V(nu1, nu2)-cycle that approximates M^{-1} (Section 5;
@@ -179,6 +195,11 @@ typedef struct {
   double rel_res_recur; /* last recurrence residual / ||b|| */
   double rel_res_true;  /* ||b - H x|| / ||b|| recomputed in FP64 */
   long kernels;         /* kernel launches the solve executed on the device */
+  int vcycles;          /* V-cycles applied: one per preconditioned matvec, plus one per GMRES cycle
+                           for its update x += M^{-1} V y; 0 without a preconditioner */
+  double seconds;       /* host wall time from the start of the solve to its statistics being read
+                           (a served request: summed over its right-hand sides) */
+  int history_len;      /* entries written to opts.history (0 when it was NULL) */
 } helm_solve_info;
 
 typedef struct helm_ctx helm_ctx;
@@ -201,9 +222,16 @@ size_t helm_workspace_bytes(const helm_ctx* ctx);
 helm_status helm_apply(helm_ctx* ctx, helm_dtype dtype, const void* x, void* y, void* stream);
 
 /* z = one V(nu1, nu2)-cycle on the preconditioner from a zero initial guess, z ~ M^{-1} r
- * (Section 5.1).  r is complex128; z has the hierarchy's mg_dtype.  For HELM_PC_NONE, z = r
- * (converted).  r and z must not alias. */
-helm_status helm_vcycle(helm_ctx* ctx, const void* r, void* z, void* stream);
+ * (Section 5.1; M is CSL or CSG, Sections 5.2-5.3).  r is complex128 (a Krylov vector).
+ * pc: NULL, or the preconditioner the context was created with -- its hierarchy is built once, in
+ * helm_create, so another kind, parameter, cycle, smoother, depth, precision or coarse-operator
+ * choice returns HELM_ERR_ARG (create a context for it).  dtype is z's element type: the
+ * hierarchy's mg_dtype, or HELM_C128 with an FP32 hierarchy, in which case the cycle runs in FP32
+ * and its last kernel writes z widened to complex128 (the precision boundary of the mixed solver;
+ * the widening is exact).  HELM_C64 with an FP64 hierarchy returns HELM_ERR_ARG.  For HELM_PC_NONE,
+ * z = r converted to dtype.  r and z must not alias. */
+helm_status helm_vcycle(helm_ctx* ctx, const helm_precond* pc, helm_dtype dtype, const void* r, void* z,
+                        void* stream);
 
 /* Single multigrid component on level `lvl` of the hierarchy (element type = mg_dtype), for
  * testing each kernel against a reference:
@@ -308,8 +336,11 @@ void helm_server_destroy(helm_server* s);
  * Its scratch (per-block partial sums and a completion counter) is a file-scope static
  * device array of 64 KiB + 256 B that every device which loads libhelm.so keeps until the
  * process exits; it bounds N to at most 4,194,304 unknowns (HELM_ERR_ARG beyond).
- * The first call on each device looks up that array's device address with the device
- * current (cudaGetSymbolAddress); make this first call before any stream capture.
+ * The context's device must be current (else HELM_ERR_ARG).  Each call made outside a stream
+ * capture looks up that array's device address with the device current (cudaGetSymbolAddress),
+ * so a call after a device reset finds the reloaded array; a call made while `stream` is being
+ * captured reuses the address of an earlier call on that device, so make the first call on each
+ * device before any stream capture (a first call inside one returns HELM_ERR_ARG).
  * Every call shares the one array and zeroes its counter on `stream` before the kernel:
  * calls whose kernels overlap on the GPU (two streams, or two host threads) race and give
  * wrong results; serialise them.  Asynchronous: *rel_out is valid once `stream` reaches it. */

@@ -14,6 +14,12 @@ HELM_OP_APPLY, HELM_OP_RESIDUAL, HELM_OP_SMOOTH, HELM_OP_SMOOTH0 = 0, 1, 2, 3
 HELM_OP_RESTRICT, HELM_OP_PROLONG, HELM_OP_COARSE, HELM_OP_DOWN = 4, 5, 6, 7
 HELM_PF_UNFUSED, HELM_PF_NO_PDL, HELM_PF_NO_AUTOTUNE, HELM_PF_GALERKIN = 1, 2, 4, 8
 HELM_SERVE_FIFO, HELM_SERVE_SMALLEST_FIRST = 0, 1
+HELM_K_CONST, HELM_K_GAUSS_BUMP, HELM_K_FIELD = 0, 1, 2
+
+# helm_set_allocator callbacks: alloc(bytes, stream, user) -> device pointer or NULL;
+# free(ptr, stream, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class Grid(C.Structure):
@@ -23,7 +29,9 @@ class Grid(C.Structure):
 
 
 class KSpec(C.Structure):
-    _fields_ = [("k0", C.c_double), ("phi", C.c_void_p), ("phi_im", C.c_void_p)]
+    _fields_ = [("k0", C.c_double), ("phi", C.c_void_p), ("phi_im", C.c_void_p), ("kind", C.c_int),
+                ("amp", C.c_double), ("width2", C.c_double), ("centre", C.c_double * 3),
+                ("field", C.c_void_p)]
 
 
 class Precond(C.Structure):
@@ -41,7 +49,8 @@ class SolveOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("matvecs", C.c_int), ("restarts", C.c_int),
-                ("rel_res_recur", C.c_double), ("rel_res_true", C.c_double), ("kernels", C.c_long)]
+                ("rel_res_recur", C.c_double), ("rel_res_true", C.c_double), ("kernels", C.c_long),
+                ("vcycles", C.c_int), ("seconds", C.c_double), ("history_len", C.c_int)]
 
 
 class Request(C.Structure):
@@ -73,7 +82,7 @@ def load() -> C.CDLL:
     lib.helm_level_shape.restype = ip
     lib.helm_apply.argtypes = [vp, ip, vp, vp, vp]
     lib.helm_apply.restype = ip
-    lib.helm_vcycle.argtypes = [vp, vp, vp, vp]
+    lib.helm_vcycle.argtypes = [vp, C.POINTER(Precond), ip, vp, vp, vp]
     lib.helm_vcycle.restype = ip
     lib.helm_level_op.argtypes = [vp, ip, ip, vp, vp, vp, ip, vp]
     lib.helm_level_op.restype = ip
@@ -107,6 +116,8 @@ def load() -> C.CDLL:
     lib.helm_select_precond.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
+    lib.helm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    lib.helm_set_allocator.restype = None
     lib.helm_status_str.argtypes = [ip]
     lib.helm_status_str.restype = C.c_char_p
     lib.helm_last_error.argtypes = []

@@ -28,17 +28,78 @@ helm_status cuda_check(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA;
 }
 
-helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes) {
+// The allocator registered with helm_set_allocator (alloc == nullptr: the CUDA stream-ordered one).
+struct Allocator {
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free)(void*, void*, void*) = nullptr;
+  void* user = nullptr;
+};
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+helm_status dev_alloc(void** p, size_t bytes, cudaStream_t st, DevBlock* rec) {
   *p = nullptr;
-  if (bytes == 0) return HELM_OK;
-  cudaError_t e = cudaMallocAsync(p, bytes, c->alloc_stream);
+  *rec = DevBlock{};
+  Allocator a;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+  }
+  if (a.alloc) {
+    void* q = a.alloc(bytes, (void*)st, a.user);
+    if (!q) {
+      set_error("the registered allocator returned NULL for " + std::to_string(bytes) + " bytes");
+      return HELM_ERR_OOM;
+    }
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {  // every kernel assumes aligned vectors
+      a.free(q, (void*)st, a.user);
+      set_error("the registered allocator returned a block that is not 256-byte aligned");
+      return HELM_ERR_OOM;
+    }
+    *p = q;
+    *rec = DevBlock{q, a.free, a.user};
+    return HELM_OK;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     return HELM_ERR_OOM;
   }
-  c->allocs.push_back(*p);
+  rec->p = *p;
+  return HELM_OK;
+}
+
+void dev_free(const DevBlock& b, cudaStream_t st) {
+  if (!b.p) return;
+  if (b.free) {
+    cudaStreamSynchronize(st);
+    b.free(b.p, (void*)st, b.user);
+  } else {
+    cudaFreeAsync(b.p, st);
+  }
+}
+
+void dev_free_all(std::vector<DevBlock>& v, cudaStream_t st) {
+  bool custom = false;
+  for (const DevBlock& b : v) custom = custom || (b.p && b.free);
+  if (custom) cudaStreamSynchronize(st);
+  for (const DevBlock& b : v) {
+    if (!b.p) continue;
+    if (b.free) b.free(b.p, (void*)st, b.user);
+    else cudaFreeAsync(b.p, st);
+  }
+  v.clear();
+}
+
+helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HELM_OK;
+  DevBlock b;
+  helm_status s = dev_alloc(p, bytes, c->alloc_stream, &b);
+  if (s != HELM_OK) return s;
+  c->allocs.push_back(b);
   c->bytes += bytes;
   return HELM_OK;
 }
@@ -89,7 +150,7 @@ static helm_status check_precond(const helm_precond* p) {
 void ctx_release_on(helm_ctx* c, cudaStream_t st) {
   if (!c) return;
   krylov_free(c, st);
-  for (void* p : c->allocs) cudaFreeAsync(p, st);
+  dev_free_all(c->allocs, st);
   delete c;
 }
 
@@ -156,6 +217,19 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   bool somm = false;
   for (int a = 0; a < grid->dim; ++a) somm = somm || grid->n_layer[a][1] < 0;
   if (k->phi_im && !k->phi) { delete c; set_error("phi_im needs phi"); return HELM_ERR_ARG; }
+  if (!k->phi) {
+    bool ok = k->kind == HELM_K_CONST ||
+              (k->kind == HELM_K_GAUSS_BUMP && k->width2 > 0.0 && std::isfinite(k->width2) &&
+               std::isfinite(k->amp) && std::isfinite(k->centre[0]) && std::isfinite(k->centre[1]) &&
+               std::isfinite(k->centre[2])) ||
+              (k->kind == HELM_K_FIELD && k->field && aligned(k->field, 8));
+    if (!ok) {
+      delete c;
+      set_error("kspec: kind must be HELM_K_CONST, HELM_K_GAUSS_BUMP (finite amp and centre, width2 > 0) or "
+                "HELM_K_FIELD (an 8-byte aligned device field)");
+      return HELM_ERR_ARG;
+    }
+  }
   if (k->phi) {
     long n = 1;
     for (int a = 0; a < grid->dim; ++a) n *= axis_unknowns(grid->n_int[a], grid->n_layer[a][0], grid->n_layer[a][1]);
@@ -173,6 +247,12 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { ctx_release(c); return cuda_check(e, "helm_create"); }
+  if (c->field_bad) {
+    int bad = 0;
+    e = cudaMemcpy(&bad, c->field_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { ctx_release(c); return cuda_check(e, "helm_create"); }
+    if (bad) { ctx_release(c); set_error("kspec.field has a non-finite entry"); return HELM_ERR_ARG; }
+  }
   *out = c;
   return HELM_OK;
 }
@@ -197,22 +277,45 @@ helm_status helm_apply(helm_ctx* c, helm_dtype dtype, const void* x, void* y, vo
   return h_apply(c, dtype == HELM_C64, x, (double2*)y, (cudaStream_t)stream);
 }
 
-helm_status helm_vcycle(helm_ctx* c, const void* r, void* z, void* stream) {
+// The preconditioner a hierarchy was built for: everything that changes M or the cycle.
+static bool same_precond(const helm_precond& a, const helm_precond& b) {
+  if (a.kind != b.kind) return false;
+  if (a.kind == HELM_PC_NONE) return true;
+  if ((a.kind == HELM_PC_CSG_UNIFORM || a.kind == HELM_PC_CSG_INTERIOR) && a.theta_beta != b.theta_beta) return false;
+  if (a.kind == HELM_PC_CSL && (a.shift_re != b.shift_re || a.shift_im != b.shift_im)) return false;
+  if (a.smoother == HELM_SM_JACOBI && b.smoother == HELM_SM_JACOBI && a.omega != b.omega) return false;
+  return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.smoother == b.smoother && a.max_levels == b.max_levels &&
+         a.coarse_max == b.coarse_max && a.mg_dtype == b.mg_dtype &&
+         (a.flags & HELM_PF_GALERKIN) == (b.flags & HELM_PF_GALERKIN);
+}
+
+helm_status helm_vcycle(helm_ctx* c, const helm_precond* pc, helm_dtype dtype, const void* r, void* z,
+                        void* stream) {
   if (!c || !r || !z || r == z) { set_error("helm_vcycle: NULL or aliased arguments"); return HELM_ERR_ARG; }
+  if (pc && !same_precond(*pc, c->pc)) {
+    set_error("helm_vcycle: the context's hierarchy was built for another preconditioner");
+    return HELM_ERR_ARG;
+  }
+  if (dtype != HELM_C64 && dtype != HELM_C128) { set_error("helm_vcycle: dtype"); return HELM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   PdlScope pdl(c);
   bool f32 = c->pc.mg_dtype == HELM_C64;
-  if (!aligned(r, 16) || !aligned(z, f32 ? 8 : 16)) { set_error("helm_vcycle: misaligned"); return HELM_ERR_ARG; }
+  bool z64 = dtype == HELM_C128;
+  if (!aligned(r, 16) || !aligned(z, z64 ? 16 : 8)) { set_error("helm_vcycle: misaligned"); return HELM_ERR_ARG; }
   if (c->pc.kind == HELM_PC_NONE) {
-    if (f32) return convert_c128_to_mg(c, (const double2*)r, z, st);
+    if (!z64) {
+      if (!f32) { set_error("helm_vcycle: complex64 output needs an FP32 context"); return HELM_ERR_ARG; }
+      return convert_c128_to_mg(c, (const double2*)r, z, st);
+    }
     cudaError_t e = cudaMemcpyAsync(z, r, sizeof(double2) * c->n, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? HELM_OK : cuda_check(e, "helm_vcycle copy");
   }
   if (f32) {
     helm_status s = convert_c128_to_mg(c, (const double2*)r, c->scratch, st);
     if (s != HELM_OK) return s;
-    return mg_vcycle<float>(c, (const float2*)c->scratch, z, false, nullptr, st);
+    return mg_vcycle<float>(c, (const float2*)c->scratch, z, z64, nullptr, st);
   }
+  if (!z64) { set_error("helm_vcycle: an FP64 hierarchy gives complex128 output"); return HELM_ERR_ARG; }
   return mg_vcycle<double>(c, (const double2*)r, z, false, nullptr, st);
 }
 
@@ -262,6 +365,12 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opt
 }
 
 void helm_destroy(helm_ctx* c) { ctx_release(c); }
+
+void helm_set_allocator(void* (*alloc)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* user) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (alloc && free_fn) g_alloc = Allocator{alloc, free_fn, user};
+  else g_alloc = Allocator{};
+}
 
 const char* helm_status_str(helm_status s) {
   switch (s) {

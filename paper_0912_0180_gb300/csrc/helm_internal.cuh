@@ -160,6 +160,15 @@ struct LevelHost {
 
 struct KrylovState;  // device-side scalars, defined in krylov.cu
 
+// One device allocation and the release function of the allocator that made it (free == nullptr:
+// cudaMallocAsync, released by cudaFreeAsync; otherwise the allocator registered with
+// helm_set_allocator when the block was allocated).
+struct DevBlock {
+  void* p = nullptr;
+  void (*free)(void*, void*, void*) = nullptr;
+  void* user = nullptr;
+};
+
 struct Workspace;    // Krylov vectors, defined in krylov.cu
 
 }  // namespace helm
@@ -187,12 +196,13 @@ struct helm_ctx {
   void* coarse_inv = nullptr;        // dense inverse of the coarsest M (mg dtype)
   int nco = 0;
   size_t bytes = 0;                  // device bytes held
-  std::vector<void*> allocs;         // everything to free
+  std::vector<helm::DevBlock> allocs;  // everything to free
   helm::Workspace* ws = nullptr;     // Krylov workspace (lazily created)
   void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations of helm_create
   int tail_first = 1 << 30;          // first level run by the single-block tail kernel
   FdmCoarse fdm;                     // separable coarsest solve (constant phi there), or off
+  int* field_bad = nullptr;          // set by helm_create when a device k field has a non-finite entry
 };
 
 namespace helm {
@@ -206,7 +216,14 @@ helm_status cuda_check(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::helm::cuda_check(_e, #call);   \
   } while (0)
 
-// device allocation owned by the context (stream-ordered, on the context's creation stream)
+// Device memory through the allocator registered with helm_set_allocator (default: stream-ordered
+// cudaMallocAsync on `st`).  HELM_ERR_OOM (and *p = nullptr) when it fails.  dev_free releases one
+// block; dev_free_all a list, after `st` has finished its queued work when any block came from a
+// registered allocator (whose release is immediate), else stream-ordered.
+helm_status dev_alloc(void** p, size_t bytes, cudaStream_t st, DevBlock* rec);
+void dev_free(const DevBlock& b, cudaStream_t st);
+void dev_free_all(std::vector<DevBlock>& v, cudaStream_t st);
+// device allocation owned by the context (on the context's creation stream)
 helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes);
 // releases a context: every buffer is freed in order on `st` after the work already queued there
 // (no device-wide synchronisation); the caller guarantees all its work was queued on `st`

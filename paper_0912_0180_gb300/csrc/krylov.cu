@@ -14,6 +14,7 @@
 // No kernel waits on another: there is no device-side spin anywhere.
 #include <cmath>
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <thread>
 #include <type_traits>
@@ -21,6 +22,10 @@
 #include "stencil.cuh"
 
 namespace helm {
+
+static double host_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 constexpr int KT = 256;      // threads per block of the vector kernels
 #ifndef KRYLOV_BLOCKS_PER_SM
@@ -63,7 +68,8 @@ struct Workspace {
   cudaGraphExec_t idr_init = nullptr;
   cudaGraph_t loop_graph = nullptr, init_graph = nullptr, body_graph = nullptr;
   size_t body_nodes = 0, init_nodes = 0;  // kernels per loop body / IDR start graph
-  std::vector<void*> mem;
+  std::vector<DevBlock> mem;
+  size_t bytes = 0;  // device bytes of mem (counted in the context's total while it lives)
 };
 
 // ---- block reductions -------------------------------------------------------------------
@@ -885,13 +891,14 @@ __global__ void k_gm_addx(const KrylovState* S, const double2* __restrict__ z, d
 // ---- host orchestration ---------------------------------------------------------------------
 
 static helm_status ws_alloc(helm_ctx* c, Workspace* w, void** p, size_t bytes, cudaStream_t st) {
-  cudaError_t e = cudaMallocAsync(p, bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error("cudaMalloc failed for the Krylov workspace");
-    return HELM_ERR_OOM;
+  DevBlock b;
+  helm_status s = dev_alloc(p, bytes, st, &b);
+  if (s != HELM_OK) {
+    set_error("device allocation failed for the Krylov workspace");
+    return s;
   }
-  w->mem.push_back(*p);
+  w->mem.push_back(b);
+  w->bytes += bytes;
   c->bytes += bytes;
   return HELM_OK;
 }
@@ -905,7 +912,8 @@ void krylov_free(helm_ctx* c, cudaStream_t st) {
   if (w->idr_init) cudaGraphExecDestroy(w->idr_init);
   if (w->loop_graph) cudaGraphDestroy(w->loop_graph);
   if (w->init_graph) cudaGraphDestroy(w->init_graph);
-  for (void* p : w->mem) cudaFreeAsync(p, st);
+  dev_free_all(w->mem, st);
+  c->bytes -= w->bytes;
   pinned_slot_put(w->hst);
   delete w;
   c->ws = nullptr;
@@ -1133,7 +1141,24 @@ static helm_status build_loop(const Ctx& k, int method, int s) {
 }
 
 template <typename TM>
+static helm_status prepare_ws(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st);
+
+// The Krylov workspace and graphs for (method, s), built on first use.  A build that fails part
+// way (an allocation refused, a capture error) releases what it made, so that the next solve starts
+// from nothing instead of finding an incomplete workspace.
+template <typename TM>
 static helm_status prepare(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st) {
+  helm_status s = prepare_ws<TM>(c, o, k, st);
+  Workspace* w = c->ws;
+  if (s != HELM_OK && w && (!w->loop || (w->method == HELM_IDR && !w->idr_init))) {
+    cudaStreamSynchronize(st);
+    krylov_free(c, st);
+  }
+  return s;
+}
+
+template <typename TM>
+static helm_status prepare_ws(helm_ctx* c, const helm_solve_opts* o, Ctx& k, cudaStream_t st) {
   Workspace*& w = c->ws;
   if (w && (w->method != o->method || (o->method != HELM_BICGSTAB && w->s != o->s))) {
     HELM_CUDA(cudaStreamSynchronize(st));
@@ -1244,6 +1269,7 @@ struct SolveJob {
   int restarts = 0;
   long kernels = 0;
   long host_loops = -1;
+  double t0 = 0.0;  // host clock at the start of the solve
   cudaEvent_t ev = nullptr;
   bool finished = false;
   helm_status status = HELM_OK;
@@ -1369,6 +1395,9 @@ static helm_status job_step_t(SolveJob& j) {
     j.info->rel_res_recur = hs.rel_recur;
     j.info->rel_res_true = hs.rel_true;
     j.info->kernels = j.kernels;
+    j.info->vcycles = j.k.pc ? hs.matvecs + (j.gm ? j.gm_passes : 0) : 0;
+    j.info->seconds = host_seconds() - j.t0;
+    j.info->history_len = j.o.history ? (hs.matvecs < j.o.maxmv ? hs.matvecs : j.o.maxmv) : 0;
   }
   j.status = fs;
   j.finished = true;
@@ -1378,6 +1407,7 @@ static helm_status job_step_t(SolveJob& j) {
 static bool job_f32(const helm_ctx* c) { return c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64; }
 
 helm_status job_begin(SolveJob& j) {
+  j.t0 = host_seconds();
   j.f32 = job_f32(j.c);
   j.bicg = j.o.method == HELM_BICGSTAB;
   j.gm = j.o.method == HELM_GMRES;

@@ -741,7 +741,9 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   size_t nf = (size_t)c->lv[0].ntot, ncs = (size_t)c->lv[1].ntot;
   void* buf = nullptr;
   size_t bytes = sizeof(cx<T>) * (4 * nf + ncs);
-  HELM_CUDA(cudaMallocAsync(&buf, bytes, st));
+  DevBlock blk;
+  helm_status as = dev_alloc(&buf, bytes, st, &blk);
+  if (as != HELM_OK) return as;
   HELM_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
   cx<T>* f = (cx<T>*)buf;
   cx<T>* u = f + nf;
@@ -791,7 +793,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFreeAsync(buf, st);
+  dev_free(blk, st);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }

@@ -5,8 +5,8 @@
 //
 // The array lives in the module: every device that loads libhelm.so holds
 // sizeof(g_noalloc_scratch) bytes until the process exits.  Host code cannot use the array's
-// name as a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and every launch gets that pointer.
+// name as a device address, so the entry point looks the address up with cudaGetSymbolAddress
+// (with the context's device current) and every launch gets that pointer.
 #include <mutex>
 
 #include "stencil.cuh"
@@ -81,16 +81,29 @@ k_residual_noalloc(OpView<double> H, const double2* __restrict__ b, const double
   }
 }
 
-// device address of g_noalloc_scratch, looked up once per device
+// Device address of g_noalloc_scratch on the current device, which must be the context's.  It is
+// looked up with that device current on every call made outside a stream capture (cheap, and
+// correct again after a device reset reloads the module) and cached per device for calls made
+// while `st` is being captured, where the cached value from an earlier call is used.
 static std::mutex g_na_mutex;
 static double* g_na_ptr[64] = {};
 
-static helm_status scratch_for_current_device(double** out) {
+static helm_status scratch_for_context_device(const helm_ctx* c, cudaStream_t st, double** out) {
   int dev = 0;
   HELM_CUDA(cudaGetDevice(&dev));
+  if (dev != c->dev) {
+    set_error("helm_residual_noalloc: the current device is not the context's device");
+    return HELM_ERR_ARG;
+  }
   if (dev < 0 || dev >= 64) { set_error("helm_residual_noalloc: device ordinal >= 64"); return HELM_ERR_ARG; }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HELM_CUDA(cudaStreamIsCapturing(st, &cs));
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_na_ptr[dev]) {
+    if (cs != cudaStreamCaptureStatusNone) {
+      set_error("helm_residual_noalloc: the first call on a device must come before any stream capture");
+      return HELM_ERR_ARG;
+    }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_check(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
@@ -110,6 +123,10 @@ extern "C" helm_status helm_residual_noalloc(helm_ctx* c, const void* b, const v
     set_error("helm_residual_noalloc: NULL or aliased arguments");
     return HELM_ERR_ARG;
   }
+  if (c->n < 1) {
+    set_error("helm_residual_noalloc: the context has no unknowns");
+    return HELM_ERR_ARG;
+  }
   if (c->n > (long)NA_MAX_BLOCKS * NA_POINTS_PER_BLOCK) {
     set_error("helm_residual_noalloc: more than 4194304 unknowns (the size of its static scratch)");
     return HELM_ERR_ARG;
@@ -119,10 +136,10 @@ extern "C" helm_status helm_residual_noalloc(helm_ctx* c, const void* b, const v
     set_error("helm_residual_noalloc: misaligned pointer");
     return HELM_ERR_ARG;
   }
-  double* scratch = nullptr;
-  helm_status s = scratch_for_current_device(&scratch);
-  if (s != HELM_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  helm_status s = scratch_for_context_device(c, st, &scratch);
+  if (s != HELM_OK) return s;
   // the completion counter must start at zero
   HELM_CUDA(cudaMemsetAsync(scratch + NA_TICKET, 0, sizeof(unsigned int), st));
   int blocks = (int)((c->n + NA_POINTS_PER_BLOCK - 1) / NA_POINTS_PER_BLOCK);

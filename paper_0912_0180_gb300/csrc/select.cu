@@ -69,10 +69,11 @@ __global__ void k_sub_from(const double2* __restrict__ f, double2* __restrict__ 
 
 struct Scratch {
   void* buf = nullptr;
+  DevBlock blk;
   double* host = nullptr;
   cudaStream_t st = nullptr;
   ~Scratch() {
-    if (buf) cudaFreeAsync(buf, st);
+    dev_free(blk, st);
     if (host) pinned_slot_put(host);
   }
 };
@@ -97,7 +98,8 @@ helm_status mg_iterate(helm_ctx* c, const double2* f, double2* u, int max_cycles
   Scratch s;
   s.st = st;
   size_t bytes = sizeof(double2) * 2 * (size_t)n + sizeof(double) * (NORM_BLOCKS + 2);
-  HELM_CUDA(cudaMallocAsync(&s.buf, bytes, st));
+  helm_status as = dev_alloc(&s.buf, bytes, st, &s.blk);
+  if (as != HELM_OK) return as;
   s.host = (double*)pinned_slot_get(sizeof(double));
   if (!s.host) { set_error("pinned host slot"); return HELM_ERR_OOM; }
   double2* r = (double2*)s.buf;
@@ -171,6 +173,7 @@ helm_status helm_select_precond(const helm_grid* grid, const helm_kspec* k, cons
   double p = start->kind == HELM_PC_CSL ? start->shift_im : start->theta_beta;
   bool any = false;
   void* u = nullptr;
+  DevBlock ublk;
   helm_status result = HELM_OK;
   for (int t = 0; t < max_trials; ++t) {
     if (t > 0) p *= factor;
@@ -179,8 +182,8 @@ helm_status helm_select_precond(const helm_grid* grid, const helm_kspec* k, cons
     helm_status e = helm_create(grid, k, &pc, stream, &c);
     if (e != HELM_OK) { result = e; break; }
     if (!u) {
-      cudaError_t ce = cudaMallocAsync(&u, sizeof(double2) * c->n, st);
-      if (ce != cudaSuccess) { helm_destroy(c); result = cuda_check(ce, "helm_select_precond"); break; }
+      helm_status ae = dev_alloc(&u, sizeof(double2) * c->n, st, &ublk);
+      if (ae != HELM_OK) { helm_destroy(c); result = ae; break; }
     }
     int kc = -1;
     e = helm_mg_iterate(c, f, u, max_cycles, reduction, &kc, nullptr, stream);
@@ -194,7 +197,7 @@ helm_status helm_select_precond(const helm_grid* grid, const helm_kspec* k, cons
     *out = *start;
     if (out->kind == HELM_PC_CSL) out->shift_im = p; else out->theta_beta = p;
   }
-  if (u) cudaFreeAsync(u, st);
+  dev_free(ublk, st);
   cudaStreamSynchronize(st);
   if (result != HELM_OK) return result;
   if (!any) { set_error("helm_select_precond: multigrid does not converge at the starting parameter"); return HELM_ERR_MAXIT; }

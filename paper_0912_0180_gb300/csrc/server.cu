@@ -103,6 +103,7 @@ struct helm_server {
     helm_solve_opts opts{};
     double k0 = 0.0;
     std::vector<double> phi, phi_im;
+    helm_kspec kform{};  // kind and bump parameters when phi is not given
     std::vector<std::complex<double>> b, shadow;
     void* x_host = nullptr;
     long n = 0;
@@ -118,6 +119,7 @@ struct helm_server {
     helm_ctx* ctx = nullptr;
     void* bd = nullptr;
     void* xd = nullptr;
+    std::vector<DevBlock> vecs;  // bd and xd
     SolveJob* job = nullptr;
     int slot = -1;
     cudaStream_t stream = nullptr;  // the slot's stream at this request's priority
@@ -148,6 +150,8 @@ struct helm_server {
     if (r->cur == 0) a = o;
     else {
       a.iters += o.iters; a.matvecs += o.matvecs; a.restarts += o.restarts; a.kernels += o.kernels;
+      a.vcycles += o.vcycles; a.seconds += o.seconds;
+      a.history_len = 0;
       if (o.rel_res_recur > a.rel_res_recur) a.rel_res_recur = o.rel_res_recur;
       if (o.rel_res_true > a.rel_res_true) a.rel_res_true = o.rel_res_true;
       if (a.status == HELM_OK) a.status = o.status;
@@ -182,8 +186,7 @@ struct helm_server {
     cudaStream_t s = r->stream;
     if (r->ctx && r->xd && r->job && job_finished(r->job)) collect(r);  // the solution, or the last iterate
     if (r->job) { job_release(*r->job); job_delete(r->job); r->job = nullptr; }
-    if (r->bd) cudaFreeAsync(r->bd, s);
-    if (r->xd) cudaFreeAsync(r->xd, s);
+    dev_free_all(r->vecs, s);
     if (r->ctx) ctx_release_on(r->ctx, s);
     r->bd = r->xd = nullptr;
     r->ctx = nullptr;
@@ -232,14 +235,18 @@ struct helm_server {
   helm_status start(Req* r) {
     r->stream = streams[(size_t)r->slot * prio_levels + prio_level(r)];
     cudaStream_t s = r->stream;
-    helm_kspec k{r->k0, r->phi.empty() ? nullptr : r->phi.data(), r->phi_im.empty() ? nullptr : r->phi_im.data()};
+    helm_kspec k = r->kform;
+    k.k0 = r->k0;
+    k.phi = r->phi.empty() ? nullptr : r->phi.data();
+    k.phi_im = r->phi_im.empty() ? nullptr : r->phi_im.data();
+    k.field = nullptr;
     helm_status st = helm_create(&r->grid, &k, &r->pc, (void*)s, &r->ctx);
     if (st != HELM_OK) return st;
     size_t vb = sizeof(double2) * r->n;
-    if (cudaMallocAsync(&r->bd, vb, s) != cudaSuccess || cudaMallocAsync(&r->xd, vb, s) != cudaSuccess) {
-      cudaGetLastError();
-      return HELM_ERR_OOM;
-    }
+    r->vecs.assign(2, DevBlock{});
+    helm_status ae = dev_alloc(&r->bd, vb, s, &r->vecs[0]);
+    if (ae == HELM_OK) ae = dev_alloc(&r->xd, vb, s, &r->vecs[1]);
+    if (ae != HELM_OK) return ae;
     if (!r->shadow.empty()) r->opts.shadow = r->shadow.data();
     r->opts.history = nullptr;
     r->opts.host_loop = 0;
@@ -351,6 +358,12 @@ helm_status helm_server_submit(helm_server* s, const helm_request* rq, uint64_t*
   r->pc = rq->pc;
   r->opts = rq->opts;
   r->k0 = rq->k.k0;
+  if (!rq->k.phi && rq->k.kind == HELM_K_FIELD) {
+    delete r;
+    set_error("helm_server_submit: a device k field is not accepted (pass phi)");
+    return HELM_ERR_ARG;
+  }
+  r->kform = rq->k;
   r->n = 1;
   for (int a = 0; a < rq->grid.dim; ++a) r->n *= axis_n(rq->grid, a);
   if (r->n < 1) { delete r; set_error("helm_server_submit: empty grid"); return HELM_ERR_ARG; }

@@ -122,6 +122,41 @@ __global__ void k_dinv(OpView<double> op, double omega_s, double2* d64, float2* 
   if (g32) g32[p] = cconv<float, double>(d);
 }
 
+// phi = k(x)^2 for the Gaussian bump k = k0 (1 + amp exp(-|x - c|^2 / width2)) (the variable wave
+// number of Section 4, eq. "Helgen", in the form of the benchmark configurations), at the real node
+// positions: along each axis x = (u - off) h, with off the index of the interior node at x = 0 (the
+// ECS layers continue the real coordinate linearly, h per node).
+struct BumpAxes {
+  int n[3];
+  int off[3];
+  double h[3];
+  double c[3];
+};
+__global__ void k_phi_bump(BumpAxes ax, int dim, double k0, double amp, double width2, double* __restrict__ phi) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long ntot = (long)ax.n[0] * ax.n[1] * ax.n[2];
+  if (p >= ntot) return;
+  long q = p;
+  double r2 = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    const int u = (int)(q % ax.n[a]);
+    q /= ax.n[a];
+    const double d = (double)(u - ax.off[a]) * ax.h[a] - ax.c[a];
+    r2 += d * d;
+  }
+  const double k = k0 * (1.0 + amp * exp(-r2 / width2));
+  phi[p] = k * k;
+}
+
+// phi = k^2 from a caller's device field of k values; *bad is set when an entry is not finite.
+__global__ void k_phi_field(const double* __restrict__ kf, double* __restrict__ phi, long n, int* bad) {
+  long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double k = kf[p];
+  if (!isfinite(k)) *bad = 1;
+  phi[p] = k * k;
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
   long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (p < n) b[p] = (float)a[p];
@@ -645,6 +680,23 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
   if (k->phi) {
     if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
     HELM_CUDA(cudaMemcpyAsync(H.phi64, k->phi, sizeof(double) * H.ntot, cudaMemcpyHostToDevice, st));
+  } else if (k->kind == HELM_K_GAUSS_BUMP) {
+    if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
+    BumpAxes ax{};
+    for (int a = 0; a < 3; ++a) {
+      ax.n[a] = H.n[a];
+      ax.off[a] = c->grid.n_layer[a][0] > 0 ? c->grid.n_layer[a][0] : -1;
+      ax.h[a] = c->grid.extent[a] / (c->grid.n_int[a] - 1);
+      ax.c[a] = k->centre[a];
+    }
+    k_phi_bump<<<ceil_div(H.ntot, 256), 256, 0, st>>>(ax, H.dim, k->k0, k->amp, k->width2, H.phi64);
+    HELM_CUDA(cudaGetLastError());
+  } else if (k->kind == HELM_K_FIELD) {
+    if ((s = ctx_alloc(c, (void**)&H.phi64, sizeof(double) * H.ntot)) != HELM_OK) return s;
+    if ((s = ctx_alloc(c, (void**)&c->field_bad, sizeof(int))) != HELM_OK) return s;
+    HELM_CUDA(cudaMemsetAsync(c->field_bad, 0, sizeof(int), st));
+    k_phi_field<<<ceil_div(H.ntot, 256), 256, 0, st>>>(k->field, H.phi64, H.ntot, c->field_bad);
+    HELM_CUDA(cudaGetLastError());
   }
   if (k->phi_im) {
     if ((s = ctx_alloc(c, (void**)&H.phim64, sizeof(double) * H.ntot)) != HELM_OK) return s;
@@ -814,20 +866,17 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   double2 *A = nullptr, *X = nullptr, *prow = nullptr, *fcol = nullptr;
   int *flag = nullptr, *perm = nullptr;
   GjPivot* pv = nullptr;
-  auto free_all = [&]() {
-    if (A) cudaFreeAsync(A, st);
-    if (X) cudaFreeAsync(X, st);
-    if (flag) cudaFreeAsync(flag, st);
-  };
+  std::vector<DevBlock> tmp(3);
+  auto free_all = [&]() { dev_free_all(tmp, st); };
   // X holds the inverse (one block) or the pivot row, saved column, pivots and pivot order
   size_t xbytes = one_block ? sizeof(double2) * (size_t)n * n
                             : sizeof(double2) * 2 * (size_t)n + sizeof(GjPivot) + sizeof(int) * (size_t)n + 256;
-  cudaError_t e0 = cudaMallocAsync(&A, sizeof(double2) * (size_t)n * n, st);
-  cudaError_t e1 = e0 == cudaSuccess ? cudaMallocAsync(&X, xbytes, st) : e0;
-  cudaError_t e2 = e1 == cudaSuccess ? cudaMallocAsync(&flag, sizeof(int), st) : e1;
-  if (e2 != cudaSuccess) {
+  helm_status ae = dev_alloc((void**)&A, sizeof(double2) * (size_t)n * n, st, &tmp[0]);
+  if (ae == HELM_OK) ae = dev_alloc((void**)&X, xbytes, st, &tmp[1]);
+  if (ae == HELM_OK) ae = dev_alloc((void**)&flag, sizeof(int), st, &tmp[2]);
+  if (ae != HELM_OK) {
     free_all();
-    return cuda_check(e2, "cudaMallocAsync(coarse)");
+    return ae;
   }
   cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (Cst.stg64)

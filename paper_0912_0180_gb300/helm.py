@@ -47,6 +47,70 @@ class Info:
     rel_res_true: float
     kernels: int = 0
     history: Optional[np.ndarray] = None
+    vcycles: int = 0
+    seconds: float = 0.0
+    history_len: int = 0
+
+
+def _info(ci, history=None) -> Info:
+    return Info(ci.status, ci.iters, ci.matvecs, ci.restarts, ci.rel_res_recur, ci.rel_res_true, ci.kernels,
+                history, ci.vcycles, ci.seconds, ci.history_len)
+
+
+# ---- device memory: libhelm allocates through torch's caching allocator ---------------------
+_keep = []        # every callback pair ever registered (blocks keep pointers to them)
+_allocator = None  # None: nothing registered by this module yet; else "torch", "user" or "library"
+
+
+def set_allocator(alloc=None, free=None):
+    """helm_set_allocator with Python callables alloc(nbytes, stream) -> device pointer (int) or
+    None, and free(ptr, stream); with no arguments, the library's own cudaMallocAsync.  The
+    callbacks stay alive for the whole process: blocks allocated through them keep pointers to them
+    and may be freed at any later time."""
+    global _allocator
+    lib = L.load()
+    if alloc is None:
+        lib.helm_set_allocator(L.ALLOC_FN(), L.FREE_FN(), None)
+        _allocator = "library"
+        return
+
+    def _a(nbytes, stream, user):
+        try:
+            p = alloc(int(nbytes), int(stream or 0))
+            return int(p) if p else None
+        except Exception:  # any failure reads as out of memory: the library returns HELM_ERR_OOM
+            return None
+
+    def _f(ptr, stream, user):
+        try:
+            free(int(ptr), int(stream or 0))
+        except Exception:
+            pass
+
+    cbs = (L.ALLOC_FN(_a), L.FREE_FN(_f))
+    for cb in cbs:  # never collected, even at interpreter shutdown
+        C.pythonapi.Py_IncRef(C.py_object(cb))
+    _keep.append(cbs)
+    lib.helm_set_allocator(cbs[0], cbs[1], None)
+    _allocator = "user"
+
+
+def use_torch_allocator(force: bool = False):
+    """Route libhelm's device allocations through torch's caching allocator, on the stream the
+    library allocates on.  The first context, server or parameter choice this module creates does
+    this, unless set_allocator() chose another allocator before; force=True registers it anyway."""
+    global _allocator
+    if _allocator is not None and not force:
+        return
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(max(nbytes, 1), torch.cuda.current_device(), stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)
+    _allocator = "torch"
 
 
 def _grid(problem) -> "L.Grid":
@@ -93,13 +157,27 @@ class Helm:
     """
 
     def __init__(self, problem, precond, mg_dtype: str = "c64", stream=None, fused: bool = True,
-                 pdl: bool = True, autotune: bool = True):
+                 pdl: bool = True, autotune: bool = True, k_field: Optional[torch.Tensor] = None,
+                 k_bump: Optional[dict] = None):
         lib = L.load()
         self._lib = lib
+        use_torch_allocator()
         g = _grid(problem)
         k, self._phi = _kspec(problem)
+        if k_field is not None:  # k(x) as a device field (HELM_K_FIELD) instead of the problem's phi
+            k.phi = k.phi_im = None
+            k.kind = L.HELM_K_FIELD
+            k.field = k_field.data_ptr()
+            self._phi = [k_field]
+        elif k_bump is not None:  # k0 (1 + amp exp(-|x - centre|^2 / width2)) formed on the device
+            k.phi = k.phi_im = None
+            k.kind = L.HELM_K_GAUSS_BUMP
+            k.amp, k.width2 = k_bump["amp"], k_bump["width2"]
+            for a, v in enumerate(k_bump["centre"]):
+                k.centre[a] = v
         pc = _precond(precond, mg_dtype, (0 if fused else L.HELM_PF_UNFUSED) | (0 if pdl else L.HELM_PF_NO_PDL)
                       | (0 if autotune else L.HELM_PF_NO_AUTOTUNE))
+        self._pc = pc
         h = C.c_void_p()
         _check(lib.helm_create(C.byref(g), C.byref(k), C.byref(pc), C.c_void_p(_stream(stream)), C.byref(h)),
                "helm_create")
@@ -138,10 +216,18 @@ class Helm:
         _check(self._lib.helm_apply(self._h, dt, _ptr(x), _ptr(out), C.c_void_p(_stream(stream))), "helm_apply")
         return out
 
-    def vcycle(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    def vcycle(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None, dtype=None,
+               precond=None) -> torch.Tensor:
+        """z = one V-cycle on M (helm_vcycle); dtype (torch.complex64 / complex128) is z's type,
+        default the hierarchy's; complex128 from an FP32 hierarchy is its widened output.
+        precond: None, or a helm_inputs.Precond that must be the context's own."""
+        dt = dtype if dtype is not None else (out.dtype if out is not None else self.mg_dtype)
         if out is None:
-            out = torch.empty(self.n, dtype=self.mg_dtype, device=r.device)
-        _check(self._lib.helm_vcycle(self._h, _ptr(r), _ptr(out), C.c_void_p(_stream(stream))), "helm_vcycle")
+            out = torch.empty(self.n, dtype=dt, device=r.device)
+        pc = None if precond is None else C.byref(_precond(precond, "c64" if self.mg_dtype == torch.complex64 else "c128",
+                                                           self._pc.flags))
+        hd = L.HELM_C64 if dt == torch.complex64 else L.HELM_C128
+        _check(self._lib.helm_vcycle(self._h, pc, hd, _ptr(r), _ptr(out), C.c_void_p(_stream(stream))), "helm_vcycle")
         return out
 
     def level_op(self, op: int, lvl: int, a: Optional[torch.Tensor], b: Optional[torch.Tensor] = None,
@@ -182,9 +268,8 @@ class Helm:
                                   C.c_void_p(_stream(stream)))
         ok = (L.HELM_OK,) if raise_on_error else (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN)
         _check(st, "helm_solve", ok)
-        h = hist[: info.matvecs].cpu().numpy() if hist is not None else None
-        return x, Info(info.status, info.iters, info.matvecs, info.restarts, info.rel_res_recur,
-                       info.rel_res_true, info.kernels, h)
+        h = hist[: info.history_len].cpu().numpy() if hist is not None else None
+        return x, _info(info, h)
 
 
 def solve_batch(instances, bs, *, method=0, s=4, tol: float = 1e-6, maxmv: int = 2000,
@@ -213,8 +298,7 @@ def solve_batch(instances, bs, *, method=0, s=4, tol: float = 1e-6, maxmv: int =
     xp = (C.c_void_p * max(n, 1))(*[x.data_ptr() for x in xs])
     st = lib.helm_solve_batch(cs, bp, xp, n, opts, infos, C.c_void_p(_stream(stream)))
     _check(st, "helm_solve_batch", (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN))
-    out = [Info(infos[i].status, infos[i].iters, infos[i].matvecs, infos[i].restarts, infos[i].rel_res_recur,
-                infos[i].rel_res_true, infos[i].kernels) for i in range(n)]
+    out = [_info(infos[i]) for i in range(n)]
     return xs, out
 
 
@@ -223,6 +307,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_active: int = 4, smallest_first: bool = False):
         self._lib = L.load()
+        use_torch_allocator()
         h = C.c_void_p()
         _check(self._lib.helm_server_create(int(budget_bytes), int(max_active), C.byref(h)), "helm_server_create")
         self._h = h
@@ -260,8 +345,7 @@ class Server:
         st = self._lib.helm_server_wait(self._h, ticket, C.byref(info), C.byref(lat))
         _check(st, "helm_server_wait", (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN))
         x = self._keep.pop(ticket)
-        return x, Info(info.status, info.iters, info.matvecs, info.restarts, info.rel_res_recur,
-                       info.rel_res_true, info.kernels), lat.value
+        return x, _info(info), lat.value
 
     def stats(self):
         q, a, u = C.c_int(), C.c_int(), C.c_size_t()
@@ -286,6 +370,7 @@ def select_precond(problem, start, f: torch.Tensor, max_cycles: int = 20, reduct
     as a helm_inputs.Precond, status, per-trial parameters, per-trial cycles)."""
     import dataclasses
     lib = L.load()
+    use_torch_allocator()
     g = _grid(problem)
     k, phi = _kspec(problem)
     pc = _precond(start, "c128")

@@ -39,6 +39,45 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def relmax(a, b):
+    """Element-wise: max_i |a_i - b_i| / max_i |b_i|."""
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300) if len(b) else 0.0
+
+
+def check(a, ref, tol, rows=None):
+    """a matches ref within tol both as a relative 2-norm and element by element
+    (max |a_i - ref_i| / max |ref_i|); with `rows` (boolean mask) also on those rows alone,
+    against their own largest reference entry, so that a wrong boundary or turning-point row
+    cannot hide among the many interior rows."""
+    a = np.asarray(a).astype(np.complex128)
+    ref = np.asarray(ref).astype(np.complex128)
+    assert rel(a, ref) < tol, ("2-norm", rel(a, ref), tol)
+    assert relmax(a, ref) < tol, ("max-norm", relmax(a, ref), tol)
+    if rows is not None and rows.any():
+        assert relmax(a[rows], ref[rows]) < tol, ("edge rows", relmax(a[rows], ref[rows]), tol)
+
+
+def edge_rows(o, lvl, which=1):
+    """Rows of level `lvl` whose Shortley-Weller row is not the uniform interior one on some axis:
+    the ECS layer rows, the turning points, the rows next to a coarse width that sums an uneven
+    number of fine widths, and the Sommerfeld boundary rows (from the oracle's own tables)."""
+    shape = o.level_shape(which, lvl)
+    masks = []
+    for a, n in enumerate(shape):
+        t = o.axis_tables(which, lvl, a)
+        mid = n // 2
+        uni = (np.isclose(t["am"], t["am"][mid], rtol=1e-12, atol=0) &
+               np.isclose(t["ap"], t["ap"][mid], rtol=1e-12, atol=0) &
+               np.isclose(t["a0"], t["a0"][mid], rtol=1e-12, atol=0))
+        masks.append(~uni)
+    m = np.zeros(shape[::-1], bool)  # indexed [l][j][i], x fastest when flattened
+    for a, ma in enumerate(masks):
+        sh = [1] * len(shape)
+        sh[len(shape) - 1 - a] = len(ma)
+        m |= ma.reshape(sh)
+    return m.reshape(-1)
+
+
 CASES = [
     # dim, n_int, layers, theta, k0, phi kind
     (1, 50, (7, 5), 0.5, 9.0, "const"),
@@ -64,11 +103,11 @@ def test_helmholtz_apply_fp64(case):
     x = hi.random_vector(p.n, 3)
     y = h.apply(cu(x)).cpu().numpy()
     ref = o.apply(x)
-    assert rel(y, ref) < 1e-12
+    check(y, ref, 1e-12, edge_rows(o, 0, which=0))
     # complex64 input: exact upcast, then FP64 arithmetic
     x32 = x.astype(np.complex64)
     y32 = h.apply(cu(x32, torch.complex64)).cpu().numpy()
-    assert rel(y32, o.apply(x32.astype(np.complex128))) < 1e-12
+    check(y32, o.apply(x32.astype(np.complex128)), 1e-12)
     h.close()
 
 
@@ -105,29 +144,30 @@ def test_multigrid_components(case, pci, mg):
         if lvl == o.nlev - 1:
             out = torch.empty(n, dtype=dt, device="cuda")
             h.level_op(L.HELM_OP_COARSE, lvl, cu(a, dt), None, out)
-            assert rel(out.cpu().numpy(), o.coarse_solve(a)) < (1e-10 if mg == "c128" else 1e-4)
+            check(out.cpu().numpy(), o.coarse_solve(a), (1e-10 if mg == "c128" else 1e-4))
             continue
+        edge = edge_rows(o, lvl)
         out = torch.empty(n, dtype=dt, device="cuda")
         h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
-        assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+        check(out.cpu().numpy(), o.apply(a, 1, lvl), tol, edge)
         h.level_op(L.HELM_OP_RESIDUAL, lvl, cu(a, dt), cu(b, dt), out)
-        assert rel(out.cpu().numpy(), b - o.apply(a, 1, lvl)) < tol
+        check(out.cpu().numpy(), b - o.apply(a, 1, lvl), tol, edge)
         u = cu(a, dt)
         h.level_op(L.HELM_OP_SMOOTH, lvl, u, cu(b, dt), None, count=2)
-        assert rel(u.cpu().numpy(), o.smooth(lvl, a, b, 2)) < tol
+        check(u.cpu().numpy(), o.smooth(lvl, a, b, 2), tol, edge)
         u = cu(a, dt)
         h.level_op(L.HELM_OP_SMOOTH0, lvl, u, cu(b, dt), None, count=2)
-        assert rel(u.cpu().numpy(), o.smooth(lvl, np.zeros(n), b, 2)) < tol
+        check(u.cpu().numpy(), o.smooth(lvl, np.zeros(n), b, 2), tol, edge)
         nc = o.level_size(1, lvl + 1)
         fc = torch.empty(nc, dtype=dt, device="cuda")
         h.level_op(L.HELM_OP_RESTRICT, lvl, cu(a, dt), None, fc)
-        assert rel(fc.cpu().numpy(), o.restrict(lvl, a)) < tol
+        check(fc.cpu().numpy(), o.restrict(lvl, a), tol)
         ec = rng.standard_normal(nc) + 1j * rng.standard_normal(nc)
         if mg == "c64":
             ec = ec.astype(np.complex64).astype(np.complex128)
         u = cu(a, dt)
         h.level_op(L.HELM_OP_PROLONG, lvl, u, cu(ec, dt))
-        assert rel(u.cpu().numpy(), o.prolong_add(lvl, ec, a)) < tol
+        check(u.cpu().numpy(), o.prolong_add(lvl, ec, a), tol, edge)
     h.close()
 
 
@@ -154,8 +194,8 @@ def test_fused_down_kernel(case, pci, mg):
         h.level_op(L.HELM_OP_DOWN, lvl, u, cu(f, dt), fc)
         u_ref = o.smooth(lvl, np.zeros(n), f, 1)
         fc_ref = o.restrict(lvl, f - o.apply(u_ref, 1, lvl))
-        assert rel(u.cpu().numpy(), u_ref) < tol
-        assert rel(fc.cpu().numpy(), fc_ref) < (10 * tol)
+        check(u.cpu().numpy(), u_ref, tol)
+        check(fc.cpu().numpy(), fc_ref, (10 * tol))
     h.close()
 
 
@@ -174,7 +214,7 @@ def test_vcycle(case, pci, mg, fused):
     r = hi.random_vector(p.n, 21)
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
     ref = o.vcycle(r)
-    assert rel(z, ref) < (1e-10 if mg == "c128" else 5e-5)
+    check(z, ref, (1e-10 if mg == "c128" else 5e-5))
     h.close()
 
 
@@ -194,7 +234,7 @@ def test_vcycle_fused_levels_large(shape, sm, mg):
     h = Helm(p, pc, mg_dtype=mg)
     r = hi.random_vector(p.n, 2)
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
-    assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+    check(z, o.vcycle(r), (1e-10 if mg == "c128" else 5e-5))
     h.close()
 
 
@@ -206,28 +246,13 @@ SOLVE_CASES = [
 ]
 
 
-def _oracle_counts(o, b, opts, sh):
-    """Matvec counts of the oracle on b perturbed at rounding level (ten draws, relative
-    1e-15 .. 1e-11): near a tight tolerance the Bi-CGSTAB/IDR residual history is not
-    monotone (on the 64^2, k = 20 case it bounces between 1e-10 and 5e-10 for about ten
-    matvecs), and the count at which it first crosses tol moves by several matvecs under such
-    perturbations; the spread is the method's own rounding sensitivity."""
-    counts = []
-    rng = np.random.default_rng(99)
-    for eps in (1e-15, 1e-14, 1e-13, 1e-12, 1e-11, 1e-15, 1e-14, 1e-13, 1e-12, 1e-11):
-        bp = b * (1 + eps * rng.standard_normal(b.shape))
-        counts.append(o.solve(bp, opts, shadow=sh)[1]["matvecs"])
-    return counts
-
-
 @pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
 @pytest.mark.parametrize("pci", [0, 2])
 @pytest.mark.parametrize("case", SOLVE_CASES)
 def test_fp64_solve_matches_oracle(case, pci, method):
     """FP64 path vs the oracle at tol 1e-10: the same residual history until rounding drift
     (first 8 matvecs to 1e-9 relative), relative solution difference <= 1e-9, and a matvec
-    count within 2 of the oracle's -- or, where rounding-level perturbations of b move the
-    oracle's own count by more than that, within 2 of the range they span."""
+    count within 2 of the oracle's."""
     p = _problem(case, rhs="point")
     pc = PCS[pci]
     o = Oracle(p, pc)
@@ -240,10 +265,8 @@ def test_fp64_solve_matches_oracle(case, pci, method):
     assert info.rel_res_true < 1e-10
     m = min(8, info.matvecs, info_ref["matvecs"])
     assert np.allclose(info.history[:m], info_ref["history"][:m], rtol=1e-9, atol=0)
-    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
-    if abs(info.matvecs - info_ref["matvecs"]) > 2:
-        counts = _oracle_counts(o, p.b, opts, sh) + [info_ref["matvecs"]]
-        assert min(counts) - 2 <= info.matvecs <= max(counts) + 2, (info.matvecs, counts)
+    check(x.cpu().numpy(), x_ref, 1e-9)
+    assert abs(info.matvecs - info_ref["matvecs"]) <= 2, (info.matvecs, info_ref["matvecs"])
     h.close()
 
 
@@ -251,16 +274,17 @@ def test_fp64_solve_matches_oracle(case, pci, method):
 @pytest.mark.parametrize("case", SOLVE_CASES)
 def test_mixed_precision_solve_error(case, method):
     """FP32 V-cycle, FP64 Krylov: true residual below tol and the error against the oracle's
-    solution at 1e-12 within 1e-5 (at tol 1e-7)."""
+    solution at 1e-12 within 1e-5 at the operating tolerance 1e-6 (and within 1e-6 at 1e-7)."""
     p = _problem(case, rhs="point")
     pc = PCS[0]
     o = Oracle(p, pc)
     sh = hi.shadow_space(p.n, 4)
     x_ref, _ = o.solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-12, maxmv=3000))
     h = Helm(p, pc, mg_dtype="c64")
-    x, info = h.solve(cu(p.b), method=method, s=4, tol=1e-7, maxmv=1500, shadow=sh)
-    assert info.status == 0 and info.rel_res_true < 1e-7
-    assert rel(x.cpu().numpy(), x_ref) < 1e-5
+    for tol, bar in ((1e-6, 1e-5), (1e-7, 1e-6)):
+        x, info = h.solve(cu(p.b), method=method, s=4, tol=tol, maxmv=1500, shadow=sh)
+        assert info.status == 0 and info.rel_res_true < tol
+        assert rel(x.cpu().numpy(), x_ref) < bar, (tol, rel(x.cpu().numpy(), x_ref))
     h.close()
 
 
@@ -274,11 +298,8 @@ def test_idr_other_shadow_dimensions(s):
     h = Helm(p, pc, mg_dtype="c128")
     x, info = h.solve(cu(p.b), method=hi.IDR, s=s, tol=1e-10, maxmv=1500, shadow=sh)
     assert info.status == 0
-    if abs(info.matvecs - info_ref["matvecs"]) > 2:
-        counts = _oracle_counts(o, p.b, hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=1500), sh)
-        counts.append(info_ref["matvecs"])
-        assert min(counts) - 2 <= info.matvecs <= max(counts) + 2, (info.matvecs, counts)
-    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
+    assert abs(info.matvecs - info_ref["matvecs"]) <= 2, (info.matvecs, info_ref["matvecs"])
+    check(x.cpu().numpy(), x_ref, 1e-9)
     h.close()
 
 
@@ -289,7 +310,8 @@ def test_unpreconditioned_and_edge_cases():
     h = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
     for method in (hi.BICGSTAB, hi.IDR):
         x, info = h.solve(cu(p.b), method=method, tol=1e-12, maxmv=5000, shadow=hi.shadow_space(p.n, 4))
-        assert info.status == 0 and rel(x.cpu().numpy(), x_ref) < 1e-9
+        assert info.status == 0
+        check(x.cpu().numpy(), x_ref, 1e-9)
     # zero right-hand side: x = 0 without a matvec
     x, info = h.solve(torch.zeros(p.n, dtype=torch.complex128, device="cuda"))
     assert info.status == 0 and info.matvecs == 0 and not torch.any(x)
@@ -302,7 +324,8 @@ def test_unpreconditioned_and_edge_cases():
     x, info = h.solve(cu(p.b), tol=1e-14, maxmv=7)
     assert info.status == L.HELM_ERR_MAXIT and info.matvecs == 7
     xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-14, maxmv=7, max_restarts=0))
-    assert io["status"] == 5 and rel(x.cpu().numpy(), xo) < 1e-10
+    assert io["status"] == 5
+    check(x.cpu().numpy(), xo, 1e-10)
     h.close()
 
 
@@ -314,7 +337,7 @@ def test_single_unknown_and_single_level():
     o = Oracle(p, pc)
     h = Helm(p, pc, mg_dtype="c128")
     assert h.nlev == 1
-    assert rel(h.vcycle(cu(p.b)).cpu().numpy(), o.vcycle(p.b)) < 1e-13
+    check(h.vcycle(cu(p.b)).cpu().numpy(), o.vcycle(p.b), 1e-13)
     x, info = h.solve(cu(p.b), tol=1e-12)
     assert info.status == 0 and info.matvecs <= 2
     h.close()
@@ -343,9 +366,9 @@ def test_large_2d_workload_sampled():
     o = Oracle(p, pc)
     h = Helm(p, pc, mg_dtype="c64")
     x = hi.random_vector(p.n, 4)
-    assert rel(h.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    check(h.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
     z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
-    assert rel(z, o.vcycle(x)) < 5e-5
+    check(z, o.vcycle(x), 5e-5)
     for method in (hi.BICGSTAB, hi.IDR):
         xs, info = h.solve(cu(p.b), method=method, s=4, tol=1e-6, maxmv=3000,
                            shadow=hi.shadow_space(p.n, 4))
@@ -353,6 +376,50 @@ def test_large_2d_workload_sampled():
         r = p.b - o.apply(xs.cpu().numpy())
         assert np.linalg.norm(r) / np.linalg.norm(p.b) < 1e-6
     h.close()
+
+
+def test_full_size_2d_solves_match_oracle():
+    """The benchmark's 640^2 problem (512^2 interior + 64-node ECS layers, kh = 0.5, bump k,
+    Gaussian source) at full size.  (1) Bi-CGSTAB with the CSG omega-Jacobi V(1,1) preconditioner,
+    FP64 path at tol 1e-10, against the oracle's own solve at 1e-10: relative solution difference
+    <= 1e-9 (2-norm and element-wise) and the matvec count within 2 of the oracle's, or of the
+    counts the oracle gives for b perturbed by 1e-15 and 1e-14 relative.  (2) The benchmark's four solves
+    ({Bi-CGSTAB, IDR(4)} x {CSG, CSL}) at its tolerance 1e-6 in both precisions, against the
+    oracle's solution at 1e-12 (the discrete solution does not depend on the preconditioner):
+    every error below 1e-5."""
+    p = hi.workload_2d_512()
+    csg = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    csl = hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    o = Oracle(p, csg)
+    x10, i10 = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=6000))
+    x12, i12 = o.solve(p.b, hi.SolveOpts(tol=1e-12, maxmv=8000))
+    assert i10["status"] == 0 and i12["status"] == 0 and i12["rel_res_true"] < 1e-12
+    h = Helm(p, csg, mg_dtype="c128")
+    x, info = h.solve(cu(p.b), tol=1e-10, maxmv=6000)
+    assert info.status == 0 and info.rel_res_true < 1e-10
+    check(x.cpu().numpy(), x10, 1e-9)
+    if abs(info.matvecs - i10["matvecs"]) > 2:
+        # Over ~800 matvecs two FP64 runs that round differently (reduction order, fused
+        # multiply-adds) follow different Bi-CGSTAB histories near 1e-10, and the count at which
+        # the recurrence first crosses tol moves; the oracle's own count moves the same way when b
+        # changes by 1e-15 .. 1e-14 relative (10 to 100 units of its rounding).  The GPU count
+        # must lie within 2 of the range those runs span.
+        rng = np.random.default_rng(99)
+        counts = [i10["matvecs"]]
+        for eps in (1e-15, 1e-15, 1e-14, 1e-14):
+            bp = p.b * (1 + eps * rng.standard_normal(p.n))
+            counts.append(o.solve(bp, hi.SolveOpts(tol=1e-10, maxmv=6000))[1]["matvecs"])
+        assert min(counts) - 2 <= info.matvecs <= max(counts) + 2, (info.matvecs, counts)
+    h.close()
+    sh = hi.shadow_space(p.n, 4)
+    for mg in ("c128", "c64"):
+        for pc in (csg, csl):
+            h = Helm(p, pc, mg_dtype=mg)
+            for method in (hi.BICGSTAB, hi.IDR):
+                xs, inf = h.solve(cu(p.b), method=method, s=4, tol=1e-6, maxmv=4000, shadow=sh)
+                assert inf.status == 0 and inf.rel_res_true < 1e-6
+                assert rel(xs.cpu().numpy(), x12) < 1e-5, (mg, pc.kind, method, rel(xs.cpu().numpy(), x12))
+            h.close()
 
 
 @pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR])
@@ -394,7 +461,7 @@ def test_vcycle_large_coarsest(shape, kind, mg):
     assert int(np.prod(shp[:dim])) > 512
     r = hi.random_vector(p.n, 4)
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
-    assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+    check(z, o.vcycle(r), (1e-10 if mg == "c128" else 5e-5))
     h.close()
 
 
@@ -411,9 +478,9 @@ def test_autotuned_tiles_give_the_same_vcycle(sm, mg):
     ha = Helm(p, pc, mg_dtype=mg, autotune=True)
     hb = Helm(p, pc, mg_dtype=mg, autotune=False)
     za, zb = ha.vcycle(r), hb.vcycle(r)
-    assert rel(za.cpu().numpy(), zb.cpu().numpy()) < (1e-13 if mg == "c128" else 2e-6)
+    check(za.cpu().numpy(), zb.cpu().numpy(), (1e-13 if mg == "c128" else 2e-6))
     ref = Oracle(p, pc).vcycle(r.cpu().numpy())
-    assert rel(za.cpu().numpy().astype(np.complex128), ref) < (1e-10 if mg == "c128" else 5e-5)
+    check(za.cpu().numpy().astype(np.complex128), ref, (1e-10 if mg == "c128" else 5e-5))
     ha.close()
     hb.close()
 
@@ -431,12 +498,12 @@ def test_large_3d_workload_sampled():
     assert h64.nlev == 4 and tuple(h64.level_shape(3)[:3]) == (20, 20, 20)
     x = hi.random_vector(p.n, 4)
     y = hi.random_vector(p.n, 5)
-    assert rel(h64.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    check(h64.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
     a, b = 0.7 - 0.2j, -1.3 + 0.4j
     vx, vy = h64.vcycle(cu(x)), h64.vcycle(cu(y))
     vxy = h64.vcycle(cu(a * x + b * y))
-    assert rel(vxy.cpu().numpy(), (a * vx + b * vy).cpu().numpy()) < 1e-12
-    assert rel(h32.vcycle(cu(x)).cpu().numpy().astype(np.complex128), vx.cpu().numpy()) < 5e-5
+    check(vxy.cpu().numpy(), (a * vx + b * vy).cpu().numpy(), 1e-12)
+    check(h32.vcycle(cu(x)).cpu().numpy().astype(np.complex128), vx.cpu().numpy(), 5e-5)
     for h in (h64, h32):
         xs, info = h.solve(cu(p.b), tol=1e-6, maxmv=3000)
         assert info.status == 0 and info.rel_res_true < 1e-6
@@ -478,12 +545,12 @@ def test_model_problems_small(which):
     o = Oracle(p, pc)
     r = hi.random_vector(p.n, 3)
     h64 = Helm(p, pc, mg_dtype="c128")
-    assert rel(h64.apply(cu(r)).cpu().numpy(), o.apply(r)) < 1e-12
-    assert rel(h64.vcycle(cu(r)).cpu().numpy(), o.vcycle(r)) < 1e-10
+    check(h64.apply(cu(r)).cpu().numpy(), o.apply(r), 1e-12)
+    check(h64.vcycle(cu(r)).cpu().numpy(), o.vcycle(r), 1e-10)
     x, info = h64.solve(cu(p.b), tol=1e-10, maxmv=4000)
     xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=4000))
     assert info.status == 0 and io["status"] == 0
-    assert rel(x.cpu().numpy(), xo) < 1e-9
+    check(x.cpu().numpy(), xo, 1e-9)
     h32 = Helm(p, pc, mg_dtype="c64")
     x32, i32 = h32.solve(cu(p.b), tol=1e-7, maxmv=4000)
     assert i32.status == 0
@@ -508,10 +575,10 @@ def test_galerkin_vcycle(shape, mg):
     for lvl in range(h.nlev):
         x = hi.random_vector(o.level_size(1, lvl), 30 + lvl)
         y = h.level_op(L.HELM_OP_APPLY, lvl, cu(x, dt), None, torch.empty(len(x), dtype=dt, device="cuda"))
-        assert rel(y.cpu().numpy().astype(np.complex128), o.apply(x, 1, lvl)) < (1e-12 if mg == "c128" else 2e-5)
+        check(y.cpu().numpy().astype(np.complex128), o.apply(x, 1, lvl), (1e-12 if mg == "c128" else 2e-5))
     r = hi.random_vector(p.n, 2)
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
-    assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+    check(z, o.vcycle(r), (1e-10 if mg == "c128" else 5e-5))
     h.close()
 
 
@@ -524,7 +591,7 @@ def test_galerkin_solve_matches_oracle():
     x, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
     xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
     assert info.status == 0 and io["status"] == 0
-    assert rel(x.cpu().numpy(), xo) < 1e-9
+    check(x.cpu().numpy(), xo, 1e-9)
     with pytest.raises(Exception):  # Galerkin levels need the Jacobi smoother
         Helm(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_RBGS, galerkin=True))
     h.close()
@@ -553,22 +620,22 @@ def test_smooth_contour_parity(case):
         h = Helm(p, pc, mg_dtype=mg)
         assert h.nlev == o.nlev
         if mg == "c128":
-            assert rel(h.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+            check(h.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
         dt = torch.complex128 if mg == "c128" else torch.complex64
         for lvl in range(o.nlev - 1):
             n = o.level_size(1, lvl)
             a = hi.random_vector(n, 9 + lvl).astype(np.complex64).astype(np.complex128)
             out = torch.empty(n, dtype=dt, device="cuda")
             h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
-            assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < (1e-12 if mg == "c128" else 2e-5)
+            check(out.cpu().numpy(), o.apply(a, 1, lvl), (1e-12 if mg == "c128" else 2e-5))
         z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
-        assert rel(z, o.vcycle(x)) < (1e-11 if mg == "c128" else 2e-5)
+        check(z, o.vcycle(x), (1e-11 if mg == "c128" else 2e-5))
         if mg == "c128":
             xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=2000)
             xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=2000))
             assert info.status == 0 and io["status"] == 0
             assert abs(info.matvecs - io["matvecs"]) <= 2
-            assert rel(xs.cpu().numpy(), xo) < 1e-9
+            check(xs.cpu().numpy(), xo, 1e-9)
         h.close()
 
 
@@ -597,7 +664,7 @@ def test_gmres_solve_matches_oracle(gi):
     assert info.status == 0 and io["status"] == 0, (info, io)
     assert info.rel_res_true < 1e-10
     assert abs(info.matvecs - io["matvecs"]) <= 2
-    assert rel(x.cpu().numpy(), xo) < 1e-9
+    check(x.cpu().numpy(), xo, 1e-9)
     hg = info.history[: min(info.matvecs, io["matvecs"])]
     ho = io["history"][: len(hg)]
     far = ho > 1e-6
@@ -625,7 +692,7 @@ def test_gmres_full_and_batch():
     x, info = hs[0].solve(cu(p.b), method=hi.GMRES, s=128, tol=1e-10, maxmv=128)
     assert io["status"] == 0 and info.status == 0 and info.restarts == 0
     assert abs(info.matvecs - io["matvecs"]) <= 1
-    assert rel(x.cpu().numpy(), xo) < 1e-9
+    check(x.cpu().numpy(), xo, 1e-9)
     from paper_0912_0180_gb300.helm import solve_batch
     shadow = hi.shadow_space(p.n, 4)
     lone = [hs[0].solve(cu(p.b), method=hi.GMRES, s=20, tol=1e-8)[0],
@@ -670,7 +737,7 @@ def test_sommerfeld_operator_levels_and_vcycle(case, pci, mg):
     if mg == "c128":
         h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
         x = hi.random_vector(p.n, 3)
-        assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+        check(h0.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
         h0.close()
     h = Helm(p, pc, mg_dtype=mg)
     assert h.nlev == o.nlev and o.nlev >= 2
@@ -681,21 +748,22 @@ def test_sommerfeld_operator_levels_and_vcycle(case, pci, mg):
         a = hi.random_vector(n, 9 + lvl).astype(np.complex64).astype(np.complex128)
         b = hi.random_vector(n, 19 + lvl).astype(np.complex64).astype(np.complex128)
         out = torch.empty(n, dtype=dt, device="cuda")
+        edge = edge_rows(o, lvl)
         h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
-        assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+        check(out.cpu().numpy(), o.apply(a, 1, lvl), tol, edge)
         u = cu(a, dt)
         h.level_op(L.HELM_OP_SMOOTH, lvl, u, cu(b, dt), None, count=2)
-        assert rel(u.cpu().numpy(), o.smooth(lvl, a, b, 2)) < tol
+        check(u.cpu().numpy(), o.smooth(lvl, a, b, 2), tol, edge)
     nco = o.level_size(1, o.nlev - 1)
     a = hi.random_vector(nco, 5)
     out = torch.empty(nco, dtype=dt, device="cuda")
     h.level_op(L.HELM_OP_COARSE, o.nlev - 1, cu(a, dt), None, out)
-    assert rel(out.cpu().numpy(), o.coarse_solve(a)) < (1e-10 if mg == "c128" else 1e-4)
+    check(out.cpu().numpy(), o.coarse_solve(a), (1e-10 if mg == "c128" else 1e-4))
     r = hi.random_vector(p.n, 21)
     for fused in (True, False):
         hf = h if fused else Helm(p, pc, mg_dtype=mg, fused=False)
         z = hf.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
-        assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+        check(z, o.vcycle(r), (1e-10 if mg == "c128" else 5e-5))
         if not fused:
             hf.close()
     h.close()
@@ -717,7 +785,7 @@ def test_sommerfeld_solve_matches_oracle(case, method):
     x, info = h.solve(cu(p.b), method=method, s=s, tol=1e-10, maxmv=3000, shadow=sh)
     assert info.status == 0 and io["status"] == 0
     assert abs(info.matvecs - io["matvecs"]) <= 2
-    assert rel(x.cpu().numpy(), xo) < 1e-9
+    check(x.cpu().numpy(), xo, 1e-9)
     h.close()
     h32 = Helm(p, pc, mg_dtype="c64")
     x3, i3 = h32.solve(cu(p.b), method=method, s=s, tol=1e-7, maxmv=3000, shadow=sh)
@@ -730,10 +798,11 @@ def test_sommerfeld_solve_matches_oracle(case, method):
         for lvl in range(og.nlev):
             xx = hi.random_vector(og.level_size(1, lvl), 40 + lvl)
             y = hg.level_op(L.HELM_OP_APPLY, lvl, cu(xx), None, torch.empty(len(xx), dtype=torch.complex128, device="cuda"))
-            assert rel(y.cpu().numpy(), og.apply(xx, 1, lvl)) < 1e-12
+            check(y.cpu().numpy(), og.apply(xx, 1, lvl), 1e-12)
         xg, ig = hg.solve(cu(p.b), tol=1e-10, maxmv=3000)
         xgo, igo = og.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
-        assert ig.status == 0 and igo["status"] == 0 and rel(xg.cpu().numpy(), xgo) < 1e-9
+        assert ig.status == 0 and igo["status"] == 0
+        check(xg.cpu().numpy(), xgo, 1e-9)
         hg.close()
 
 
@@ -767,16 +836,16 @@ def test_galerkin3d_levels_vcycle_and_solve(shape, mg):
     for lvl in range(h.nlev):
         x = hi.random_vector(o.level_size(1, lvl), 30 + lvl).astype(np.complex64).astype(np.complex128)
         y = h.level_op(L.HELM_OP_APPLY, lvl, cu(x, dt), None, torch.empty(len(x), dtype=dt, device="cuda"))
-        assert rel(y.cpu().numpy().astype(np.complex128), o.apply(x, 1, lvl)) < (1e-12 if mg == "c128" else 2e-5)
+        check(y.cpu().numpy().astype(np.complex128), o.apply(x, 1, lvl), (1e-12 if mg == "c128" else 2e-5))
     r = hi.random_vector(p.n, 2)
     z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
-    assert rel(z, o.vcycle(r)) < (1e-10 if mg == "c128" else 5e-5)
+    check(z, o.vcycle(r), (1e-10 if mg == "c128" else 5e-5))
     if mg == "c128":
         x, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
         xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
         assert info.status == 0 and io["status"] == 0
         assert abs(info.matvecs - io["matvecs"]) <= 2
-        assert rel(x.cpu().numpy(), xo) < 1e-9
+        check(x.cpu().numpy(), xo, 1e-9)
     h.close()
 
 
@@ -802,7 +871,7 @@ def test_complex_z_potential_parity(ci, mg):
     x = hi.random_vector(p.n, 4)
     if mg == "c128":
         h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
-        assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+        check(h0.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
         h0.close()
     dt = torch.complex128 if mg == "c128" else torch.complex64
     tol = 1e-11 if mg == "c128" else 2e-5
@@ -814,15 +883,15 @@ def test_complex_z_potential_parity(ci, mg):
                 a = hi.random_vector(o.level_size(1, lvl), 9 + lvl).astype(np.complex64).astype(np.complex128)
                 out = torch.empty(len(a), dtype=dt, device="cuda")
                 h.level_op(L.HELM_OP_APPLY, lvl, cu(a, dt), None, out)
-                assert rel(out.cpu().numpy(), o.apply(a, 1, lvl)) < tol
+                check(out.cpu().numpy(), o.apply(a, 1, lvl), tol)
         z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
-        assert rel(z, o.vcycle(x)) < (1e-10 if mg == "c128" else 5e-5)
+        check(z, o.vcycle(x), (1e-10 if mg == "c128" else 5e-5))
         if mg == "c128" and fused:
             xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
             xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
             assert info.status == 0 and io["status"] == 0
             assert abs(info.matvecs - io["matvecs"]) <= 2
-            assert rel(xs.cpu().numpy(), xo) < 1e-9
+            check(xs.cpu().numpy(), xo, 1e-9)
         h.close()
 
 
@@ -835,10 +904,10 @@ def test_complex_phi_inside_the_uniform_interior():
     o = Oracle(p, PCS[0])
     x = hi.random_vector(p.n, 5)
     h0 = Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
-    assert rel(h0.apply(cu(x)).cpu().numpy(), o.apply(x)) < 1e-12
+    check(h0.apply(cu(x)).cpu().numpy(), o.apply(x), 1e-12)
     h0.close()
     for mg in ("c128", "c64"):
         h = Helm(p, PCS[0], mg_dtype=mg)
         z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
-        assert rel(z, o.vcycle(x)) < (1e-10 if mg == "c128" else 5e-5)
+        check(z, o.vcycle(x), (1e-10 if mg == "c128" else 5e-5))
         h.close()
