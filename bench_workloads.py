@@ -381,7 +381,7 @@ def _pc2d():
 
 def run_batch(args, torch, ranks, dev, local):
     import bench
-    from paper_0912_0180_gb300.helm import Helm, solve_batch
+    from paper_0912_0180_gb300.helm import Helm, solve_batch, solve_group
     inst = hi.workload_batch_2d(256)
     bs = [torch.from_numpy(p.b).to(dev) for p in inst]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -406,6 +406,26 @@ def run_batch(args, torch, ranks, dev, local):
                 ms.append(e0.elapsed_time(e1))
                 infos += inf
             _check(infos, "batch256")
+            # the same step as ONE group (helm_solve_group): every kernel of an iteration is one launch
+            # over all 256 instances
+            for _ in range(args.warmup):
+                solve_group(hs, bs, tol=TOL, maxmv=4000)
+            gms, ginfos = [], []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                ranks.barrier()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gxs, ginf = solve_group(hs, bs, tol=TOL, maxmv=4000)
+                e1.record()
+                ranks.barrier()
+                torch.cuda.synchronize()
+                gms.append(e0.elapsed_time(e1))
+                ginfos += ginf
+            _check(ginfos, "batch256 grouped")
+            same = all(torch.equal(a, b_) for a, b_ in zip(gxs, xs))
             one = None
             if mg == "c64":  # the same instances one after another, for the batching gain
                 torch.cuda.synchronize()
@@ -434,7 +454,8 @@ def run_batch(args, torch, ranks, dev, local):
                     torch.cuda.synchronize()
                     e2e.append(e0.elapsed_time(e1))
                 res["e2e_ms"] = statistics.mean(e2e)
-            res[mg] = {"ms": ranks.max(statistics.mean(ms)), "infos": infos, "one_by_one_ms": one}
+            res[mg] = {"ms": ranks.max(statistics.mean(ms)), "infos": infos, "one_by_one_ms": one,
+                       "group_ms": ranks.max(statistics.mean(gms)), "group_infos": ginfos, "group_same": same}
             for h in hs:
                 h.close()
     nb = len(inst)
@@ -452,6 +473,13 @@ def run_batch(args, torch, ranks, dev, local):
                     "one_by_one_solves_per_s": nb / (r32["one_by_one_ms"] / 1000),
                     "max_true_rel_res": max(i.rel_res_true for i in r32["infos"])},
         "max_true_rel_res": max(i.rel_res_true for i in r64["infos"]),
+        "grouped": {mg: {"solves_per_s": nb * ranks.world / (res[mg]["group_ms"] / 1000),
+                         "ms_per_step": res[mg]["group_ms"],
+                         "launches_per_step": int(res[mg]["group_infos"][0].kernels),
+                         "bitwise_equal_to_streams": bool(res[mg]["group_same"])}
+                    for mg in ("c128", "c64")},
+        "grouped_what": "helm_solve_group: the 256 instances as one group, each kernel of an iteration one launch "
+                        "over all instances (per-instance descriptors), one captured loop graph",
         "clocks": clk.summary(),
         "e2e": {"value": nb / (res["e2e_ms"] / 1000), "unit": "solves/s",
                 "path": "fp32_mg batch with pinned host right-hand sides and solutions",

@@ -60,9 +60,9 @@ class Problem:
 
 def axis_unknowns(n_int: int, nl: Tuple[int, int]) -> int:
     """Number of unknowns along one axis (interior nodes, minus Dirichlet walls, plus layers; a
-    high side of -1 is a Sommerfeld boundary whose node is an unknown)."""
+    side of -1 is a Sommerfeld boundary whose node is an unknown)."""
     lo, hi = nl
-    return n_int - 2 + (lo + 1 if lo > 0 else 0) + (hi + 1 if hi > 0 else (1 if hi < 0 else 0))
+    return n_int - 2 + (lo + 1 if lo > 0 else (1 if lo < 0 else 0)) + (hi + 1 if hi > 0 else (1 if hi < 0 else 0))
 
 
 def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray:
@@ -71,7 +71,7 @@ def axis_positions(n_int: int, nl: Tuple[int, int], extent: float) -> np.ndarray
     lo, hi = nl
     xs: List[float] = []
     xs += [-m * h for m in range(lo, 0, -1)]
-    first = 0 if lo > 0 else 1
+    first = 0 if lo != 0 else 1
     last = n_int - 1 if hi != 0 else n_int - 2
     xs += [j * h for j in range(first, last + 1)]
     xs += [extent + m * h for m in range(1, hi + 1)]
@@ -92,7 +92,7 @@ def axis_positions_complex(n_int: int, nl: Tuple[int, int], extent: float, theta
         return m * h * np.exp(1j * theta)
 
     zs: List[complex] = [-depth(m) for m in range(lo, 0, -1)]
-    first = 0 if lo > 0 else 1
+    first = 0 if lo != 0 else 1
     last = n_int - 1 if hi != 0 else n_int - 2
     zs += [complex(j * h) for j in range(first, last + 1)]
     zs += [extent + depth(m) for m in range(1, hi + 1)] if hi > 0 else []
@@ -118,7 +118,7 @@ def mesh(p: Problem) -> List[np.ndarray]:
 def interior_node_index(p: Problem, axis: int, j: int) -> int:
     """0-based unknown index along `axis` of interior grid node j (0..n_int-1)."""
     lo = p.n_layer[axis][0]
-    return j + lo if lo > 0 else j - 1
+    return j + lo if lo > 0 else (j if lo < 0 else j - 1)
 
 
 def _dims3(dim, v):

@@ -276,6 +276,24 @@ helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, const helm_solve_o
 helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* b, void* const* x, int n,
                              const helm_solve_opts* opts, helm_solve_info* infos, void* stream);
 
+/* Solves n independent instances H_i x_i = b_i with Bi-CGSTAB (opts->method must be HELM_BICGSTAB;
+ * one opts for all; no history) as ONE group: every kernel of an iteration -- the Krylov updates
+ * and inner products, and each level of the V-cycles -- is a single launch over all instances'
+ * blocks, driven by a device table of per-instance descriptors (operator, buffers, the blocks each
+ * instance owns).  The instances iterate in lockstep in one captured loop graph whose WHILE node
+ * runs while any of them is unfinished; an instance that has converged skips the later launches
+ * (one flag read per block).  Launches per iteration: 6 Krylov kernels, 2 x (2 L + up to 3)
+ * V-cycle kernels (L = the largest number of fused levels) and one condition kernel, whatever n.
+ * Requirements (else HELM_ERR_ARG, checked on the host): n >= 1 distinct contexts on the current
+ * device, 2D grids, a CSL or CSG preconditioner with V(1,1) cycles on rediscretised fused levels
+ * (no HELM_PF_UNFUSED or HELM_PF_GALERKIN) and a dense coarsest inverse, one smoother kind and one
+ * mg_dtype for all.  Grids, k fields, preconditioner parameters and sizes may all differ.
+ * Each instance keeps its own block decomposition and reduction order, so its iterates, statistics
+ * and solution are bitwise those helm_solve gives it alone; infos[i].kernels is the group's total
+ * launch count.  Synchronises `stream` at the end. */
+helm_status helm_solve_group(helm_ctx* const* ctxs, const void* const* b, void* const* x, int n,
+                             const helm_solve_opts* opts, helm_solve_info* infos, void* stream);
+
 /* ---- serving --------------------------------------------------------------------------------
  * A server admits solve requests of any grid, k field and preconditioner against a device-memory
  * budget and runs up to max_active of them at once, each on its own stream with its own context

@@ -126,6 +126,10 @@ typedef struct {
   cplx *am, *a0, *ap; /* Shortley-Weller row of -d^2/dz^2 at each unknown */
   int somm;       /* 1: the last unknown is a Sommerfeld boundary node */
   cplx bt;        /* its boundary weight 2i / h_l: the diagonal gains bt * k */
+  int somm_lo;    /* 1: the first unknown is a Sommerfeld boundary node (low side) */
+  cplx bt_lo;     /* its boundary weight 2i / h_r */
+  int off;        /* coarsening offset: coarse unknown c is fine unknown 2c + off (0 with a
+                     Sommerfeld low side, whose boundary node 0 every level keeps; else 1) */
 } axis_t;
 
 typedef struct {
@@ -169,15 +173,18 @@ static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, dou
                        int ramp, cplx scale_in, cplx scale_ly) {
   double h = extent / (n_int - 1);
   int lo = nl[0], hi = nl[1];
-  /* a Sommerfeld high side adds one width: the mirror of the last one, to the ghost node */
-  int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
+  /* a Sommerfeld side adds one width: the mirror of the adjacent interior one, to the ghost node */
+  int ngap = (n_int - 1) + (lo > 0 ? lo + 1 : (lo < 0 ? 1 : 0)) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
   a->n = ngap - 1;
   a->somm = hi < 0;
+  a->somm_lo = lo < 0;
+  a->off = lo < 0 ? 0 : 1;
   a->gap = malloc(sizeof(cplx) * ngap);
   a->pos = malloc(sizeof(double) * imax(a->n, 1));
   int g = 0;
   if (lo > 0)  /* outermost first: gap m = lo + 1 down to 1 */
     for (int m = lo + 1; m >= 1; --m) a->gap[g++] = layer_width(h, theta_g, ramp, m) * scale_ly;
+  if (lo < 0) a->gap[g++] = h * scale_in;
   for (int m = 0; m < n_int - 1; ++m) a->gap[g++] = h * scale_in;
   if (hi > 0)
     for (int m = 1; m <= hi + 1; ++m) a->gap[g++] = layer_width(h, theta_g, ramp, m) * scale_ly;
@@ -185,7 +192,7 @@ static void axis_build(axis_t* a, int n_int, const int nl[2], double extent, dou
   /* real positions: the layers continue the real coordinate */
   int u = 0;
   for (int m = lo; m >= 1; --m) a->pos[u++] = -m * h;
-  int first = lo > 0 ? 0 : 1, last = hi != 0 ? n_int - 1 : n_int - 2;
+  int first = lo != 0 ? 0 : 1, last = hi != 0 ? n_int - 1 : n_int - 2;
   for (int j = first; j <= last; ++j) a->pos[u++] = j * h;
   for (int m = 1; m <= hi; ++m) a->pos[u++] = extent + m * h;
 }
@@ -215,24 +222,43 @@ static void axis_coeffs(axis_t* a) {
     a->am[N] *= 2.0;
     a->ap[N] = 0;
   }
+  a->bt_lo = 0;
+  if (a->somm_lo && a->n > 0) {
+    /* Sommerfeld node 0 on the low side (outward normal -x, so du/dx = i k u there): the centred
+     * difference (u_1 - u_g) / (2 h_r) = i k u_0 gives the ghost u_g = u_1 - 2 i k h_r u_0, so the
+     * right weight doubles, the left one vanishes and the diagonal gains -2 i k h_r am = 2 i k / h_r
+     * (the gap to the ghost mirrors h_r) */
+    cplx hr = a->gap[0];
+    a->bt_lo = -2.0 * I * hr * a->am[0];
+    a->ap[0] *= 2.0;
+    a->am[0] = 0;
+  }
 }
 
 /* Index-even coarsening: coarse unknown c is fine unknown 2c+1 (0-based), i.e. coarse node
  * c+1 is fine node 2(c+1); coarse widths are the sums of the fine widths between coarse
- * nodes; the last one reaches the fine Dirichlet node and spans one or two fine widths. */
+ * nodes; the last one reaches the fine Dirichlet node and spans one or two fine widths.
+ * With a Sommerfeld low side the offset is 0 instead (coarse c is fine 2c), so that the boundary
+ * node 0 stays a node of every level; its ghost width mirrors the first coarse width. */
 static void axis_coarsen(const axis_t* f, axis_t* c) {
-  c->n = f->n / 2;
+  const int o = f->off;
+  c->n = o ? f->n / 2 : (f->n + 1) / 2;
   c->somm = f->somm;
+  c->somm_lo = f->somm_lo;
+  c->off = f->off;
   c->gap = malloc(sizeof(cplx) * (c->n + 1));
   c->pos = malloc(sizeof(double) * imax(c->n, 1));
   for (int ci = 0; ci < c->n; ++ci) {
-    c->gap[ci] = f->gap[2 * ci] + f->gap[2 * ci + 1];
-    c->pos[ci] = f->pos[2 * ci + 1];
+    /* the widths between fine nodes 2(ci-1)+o and 2ci+o; before the first coarse node, those
+     * from the low end (its Dirichlet node, or the ghost) */
+    c->gap[ci] = (2 * ci + o - 1 >= 0 ? f->gap[2 * ci + o - 1] : 0) + f->gap[2 * ci + o];
+    c->pos[ci] = f->pos[2 * ci + o];
   }
+  if (c->somm_lo && c->n > 1) c->gap[0] = c->gap[1];
   cplx last = 0;
-  for (int j = 2 * c->n; j <= f->n; ++j) last += f->gap[j];
-  /* a Sommerfeld axis is coarsened only with an even n, so the fine boundary node 2c+1 = n-1 is
-   * the last coarse node; its ghost width mirrors the last coarse width */
+  for (int j = 2 * (c->n - 1) + o + 1; j <= f->n; ++j) last += f->gap[j];
+  /* a Sommerfeld high side is coarsened only when its boundary node n-1 is a coarse node; its
+   * ghost width mirrors the last coarse width */
   c->gap[c->n] = c->somm ? c->gap[c->n - 1] : last;
   axis_coeffs(c);
 }
@@ -291,7 +317,8 @@ static void level_coarse(const level_t* F, level_t* C) {
   for (int l = 0; l < C->n[2]; ++l)
     for (int j = 0; j < C->n[1]; ++j)
       for (int i = 0; i < C->n[0]; ++i) {
-        int fi = 2 * i + 1, fj = F->dim > 1 ? 2 * j + 1 : 0, fl = F->dim > 2 ? 2 * l + 1 : 0;
+        int fi = 2 * i + F->ax[0].off, fj = F->dim > 1 ? 2 * j + F->ax[1].off : 0;
+        int fl = F->dim > 2 ? 2 * l + F->ax[2].off : 0;
         C->phi[lidx(C, i, j, l)] = F->phi[lidx(F, fi, fj, fl)];
       }
   if (F->phi_im) {  /* injected like the real part */
@@ -299,7 +326,8 @@ static void level_coarse(const level_t* F, level_t* C) {
     for (int l = 0; l < C->n[2]; ++l)
       for (int j = 0; j < C->n[1]; ++j)
         for (int i = 0; i < C->n[0]; ++i) {
-          int fi = 2 * i + 1, fj = F->dim > 1 ? 2 * j + 1 : 0, fl = F->dim > 2 ? 2 * l + 1 : 0;
+          int fi = 2 * i + F->ax[0].off, fj = F->dim > 1 ? 2 * j + F->ax[1].off : 0;
+          int fl = F->dim > 2 ? 2 * l + F->ax[2].off : 0;
           C->phi_im[lidx(C, i, j, l)] = F->phi_im[lidx(F, fi, fj, fl)];
         }
   }
@@ -318,6 +346,7 @@ static cplx diag_at(const level_t* L, int i, int j, int l) {
     d += L->ax[a].a0[ix[a]];
     /* Sommerfeld boundary node: + 2 i k / h_l with k = sqrt(phi), the unshifted wave number */
     if (L->ax[a].somm && ix[a] == L->ax[a].n - 1) d += L->ax[a].bt * sqrt(ph);
+    if (L->ax[a].somm_lo && ix[a] == 0) d += L->ax[a].bt_lo * sqrt(ph);
   }
   cplx phc = ph + I * (L->phi_im ? L->phi_im[lidx(L, i, j, l)] : 0.0);
   return d - L->s * phc;
@@ -567,7 +596,7 @@ static void level_galerkin3d(const level_t* F, level_t* C) {
 void orc_destroy(orc_ctx* c);
 
 /* Returns NULL when the coarsest preconditioner level is singular (its dense LU meets a zero
- * pivot). */
+ * pivot), or for Galerkin coarse operators on a grid with a Sommerfeld low side. */
 orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, double k0,
                     const orc_precond* pc) {
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
@@ -575,6 +604,9 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, 
   c->pc = *pc;
   level_fine(&c->H, g, phi, phi_im, k0, 1.0, 1.0, 1.0);
   if (pc->kind == 0) return c; /* identity preconditioner: no hierarchy */
+  if (pc->galerkin)  /* the Galerkin products are written for the offset-1 coarsening only */
+    for (int d = 0; d < g->dim; ++d)
+      if (g->n_layer[d][0] < 0) { orc_destroy(c); return NULL; }
   cplx beta = cexp(I * pc->theta_beta);
   cplx scale_in = 1.0, scale_ly = 1.0, s = 1.0;
   if (pc->kind == 1) s = pc->shift_re + I * pc->shift_im;           /* CSL: sigma = beta^2 phi */
@@ -591,10 +623,11 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, 
       if (F->n[d] > pc->coarse_max) all_small = 0;
       if (F->n[d] < min_n) min_n = F->n[d];
     }
-    /* a Sommerfeld axis keeps its boundary node only when its unknown count is even */
+    /* a Sommerfeld high side keeps its boundary node n-1 only when n-1-o is even (o the axis's
+     * coarsening offset: an even n with o = 1, an odd n with o = 0) */
     int odd_somm = 0;
     for (int d = 0; d < F->dim; ++d)
-      if (F->ax[d].somm && (F->n[d] & 1)) odd_somm = 1;
+      if (F->ax[d].somm && ((F->n[d] - 1 - F->ax[d].off) & 1)) odd_somm = 1;
     if (all_small || min_n < 3 || odd_somm) break;
     level_coarse(F, &c->M[c->nlev]);
     if (pc->galerkin && g->dim == 2) level_galerkin(F, &c->M[c->nlev]);
@@ -707,8 +740,9 @@ static void smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps
   }
 }
 
-/* Full weighting in index space: coarse unknown c gathers fine unknowns 2c, 2c+1, 2c+2
- * with weights 1/4, 1/2, 1/4 per axis (tensor product); missing neighbours are Dirichlet. */
+/* Full weighting in index space: coarse unknown c gathers fine unknowns 2c+o-1, 2c+o, 2c+o+1
+ * (o the axis's coarsening offset, 1 unless a Sommerfeld low side makes it 0) with weights
+ * 1/4, 1/2, 1/4 per axis (tensor product); missing neighbours are Dirichlet. */
 static void restrict_fw(const level_t* F, const level_t* C, const cplx* r, cplx* fc) {
   static const double w[3] = {0.25, 0.5, 0.25};
   PAR_FOR2(C->ntot)
@@ -719,9 +753,9 @@ static void restrict_fw(const level_t* F, const level_t* C, const cplx* r, cplx*
         for (int dl = (F->dim > 2 ? -1 : 0); dl <= (F->dim > 2 ? 1 : 0); ++dl)
           for (int dj = (F->dim > 1 ? -1 : 0); dj <= (F->dim > 1 ? 1 : 0); ++dj)
             for (int di = -1; di <= 1; ++di) {
-              int fi = 2 * Ii + 1 + di;
-              int fj = F->dim > 1 ? 2 * cj + 1 + dj : 0;
-              int fl = F->dim > 2 ? 2 * cl + 1 + dl : 0;
+              int fi = 2 * Ii + F->ax[0].off + di;
+              int fj = F->dim > 1 ? 2 * cj + F->ax[1].off + dj : 0;
+              int fl = F->dim > 2 ? 2 * cl + F->ax[2].off + dl : 0;
               if (fi < 0 || fi >= F->n[0] || fj < 0 || fj >= F->n[1] || fl < 0 || fl >= F->n[2]) continue;
               double wt = w[di + 1] * (F->dim > 1 ? w[dj + 1] : 1.0) * (F->dim > 2 ? w[dl + 1] : 1.0);
               acc += wt * r[lidx(F, fi, fj, fl)];
@@ -730,12 +764,17 @@ static void restrict_fw(const level_t* F, const level_t* C, const cplx* r, cplx*
       }
 }
 
-/* Linear interpolation weights of fine index i from coarse indices (per axis). */
-static int interp1(int i, int nc, int* ci, double* w) {
-  if (i & 1) { ci[0] = (i - 1) / 2; w[0] = 1.0; return 1; }
+/* Linear interpolation weights of fine index i from coarse indices (per axis): fine 2c + o is
+ * coarse c itself, a fine index between two coarse ones takes half of each (o the coarsening
+ * offset; a coarse index outside 0..nc-1 is a Dirichlet zero). */
+static int interp1(int i, int nc, int o, int* ci, double* w) {
+  int r = i - o;
+  if (r >= 0 && !(r & 1)) { ci[0] = r / 2; w[0] = 1.0; return 1; }
   int k = 0;
-  if (i / 2 - 1 >= 0) { ci[k] = i / 2 - 1; w[k] = 0.5; ++k; }
-  if (i / 2 < nc) { ci[k] = i / 2; w[k] = 0.5; ++k; }
+  int left = (r - 1) / 2, right = (r + 1) / 2;  /* r odd (or -1): its coarse neighbours */
+  if (r < 0) { left = -1; right = 0; }
+  if (left >= 0 && left < nc) { ci[k] = left; w[k] = 0.5; ++k; }
+  if (right >= 0 && right < nc) { ci[k] = right; w[k] = 0.5; ++k; }
   return k;
 }
 
@@ -747,9 +786,9 @@ static void prolong_add(const level_t* F, const level_t* C, const cplx* ec, cplx
       for (int i = 0; i < F->n[0]; ++i) {
         int ci[2], cj[2] = {0}, cl[2] = {0};
         double wi[2], wj[2] = {1.0}, wl[2] = {1.0};
-        int ni = interp1(i, C->n[0], ci, wi);
-        int nj = F->dim > 1 ? interp1(j, C->n[1], cj, wj) : 1;
-        int nl = F->dim > 2 ? interp1(l, C->n[2], cl, wl) : 1;
+        int ni = interp1(i, C->n[0], F->ax[0].off, ci, wi);
+        int nj = F->dim > 1 ? interp1(j, C->n[1], F->ax[1].off, cj, wj) : 1;
+        int nl = F->dim > 2 ? interp1(l, C->n[2], F->ax[2].off, cl, wl) : 1;
         cplx acc = 0;
         for (int c3 = 0; c3 < nl; ++c3)
           for (int c2 = 0; c2 < nj; ++c2)
@@ -1246,7 +1285,7 @@ int orc_select_precond(const orc_grid* g, const double* phi, const double* phi_i
   long n = 1;
   for (int d = 0; d < g->dim; ++d) {
     int lo = g->n_layer[d][0], hi = g->n_layer[d][1];
-    n *= g->n_int[d] - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : hi < 0 ? 1 : 0);
+    n *= g->n_int[d] - 2 + (lo > 0 ? lo + 1 : lo < 0 ? 1 : 0) + (hi > 0 ? hi + 1 : hi < 0 ? 1 : 0);
   }
   cplx* u = malloc(sizeof(cplx) * n);
   orc_precond pc = *start;

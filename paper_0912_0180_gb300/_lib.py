@@ -90,6 +90,8 @@ def load() -> C.CDLL:
     lib.helm_solve.restype = ip
     lib.helm_solve_batch.argtypes = [vp, vp, vp, ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.helm_solve_batch.restype = ip
+    lib.helm_solve_group.argtypes = [vp, vp, vp, ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+    lib.helm_solve_group.restype = ip
     lib.helm_estimate_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Precond), C.POINTER(SolveOpts)]
     lib.helm_estimate_bytes.restype = C.c_size_t
     lib.helm_server_create.argtypes = [C.c_size_t, ip, C.POINTER(vp)]

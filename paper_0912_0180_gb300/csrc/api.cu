@@ -353,6 +353,20 @@ helm_status helm_solve_batch(helm_ctx* const* cs, const void* const* b, void* co
   return s;
 }
 
+helm_status helm_solve_group(helm_ctx* const* cs, const void* const* b, void* const* x, int n,
+                             const helm_solve_opts* o, helm_solve_info* infos, void* stream) {
+  if (infos && n > 0) std::memset(infos, 0, sizeof(*infos) * n);
+  if (n < 1 || !cs || !b || !x || !o) { set_error("helm_solve_group: bad arrays"); return HELM_ERR_ARG; }
+  for (int i = 0; i < n; ++i) {
+    helm_status s = check_solve_args(cs[i], b[i], x[i], o);
+    if (s != HELM_OK) return s;
+    for (int j = 0; j < i; ++j)
+      if (cs[j] == cs[i]) { set_error("helm_solve_group: a context appears twice"); return HELM_ERR_ARG; }
+  }
+  PdlScope pdl(cs[0]);
+  return krylov_solve_group(cs, (const double2* const*)b, (double2* const*)x, n, o, infos, (cudaStream_t)stream);
+}
+
 helm_status helm_solve(helm_ctx* c, const void* b, void* x, const helm_solve_opts* o, helm_solve_info* info,
                        void* stream) {
   if (info) std::memset(info, 0, sizeof(*info));

@@ -210,6 +210,7 @@ namespace helm {
 // error bookkeeping (per thread)
 void set_error(const std::string& msg);
 helm_status cuda_check(cudaError_t e, const char* what);
+inline helm_status cuda_err(cudaError_t e) { return e == cudaSuccess ? HELM_OK : cuda_check(e, "CUDA call"); }
 #define HELM_CUDA(call)                                            \
   do {                                                             \
     cudaError_t _e = (call);                                       \
@@ -250,6 +251,17 @@ helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaSt
 
 // mg_fused.cu
 helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);
+// Grouped V-cycles (mg_fused.cu): the V-cycles of ni contexts (2D, fused V(1,1) levels, dense
+// coarsest inverse, one smoother kind, multigrid precision T) enqueued as one launch per level and
+// kernel kind.  in[i] (cx<T>) is instance i's right-hand side, out[i] its complex128 result,
+// skip[i] its skip flag; the plan keeps device descriptors until group_vcycle_free.
+struct GroupVcycle;
+template <typename T>
+helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* in, double2* const* out,
+                               const int* const* skip, cudaStream_t st, GroupVcycle** plan);
+template <typename T> void group_vcycle_enqueue(const GroupVcycle* plan, cudaStream_t st);
+long group_vcycle_launches(const GroupVcycle* plan);
+void group_vcycle_free(GroupVcycle* plan, cudaStream_t st);
 // coarse_fdm.cu
 helm_status fdm_build(helm_ctx* c, const LevelHost& L, bool f32, cudaStream_t st);
 template <typename T>
@@ -269,6 +281,9 @@ helm_status krylov_solve(helm_ctx* c, const double2* b, double2* x, const helm_s
                          helm_solve_info* info, cudaStream_t st);
 helm_status krylov_solve_batch(helm_ctx* const* cs, const double2* const* b, double2* const* x, int n,
                                const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t user);
+// grouped Bi-CGSTAB (group.cu): arguments already checked per instance
+helm_status krylov_solve_group(helm_ctx* const* cs, const double2* const* b, double2* const* x, int n,
+                               const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t st);
 // resumable solves (used by the batch and the server)
 struct SolveJob;
 void krylov_free(helm_ctx* c, cudaStream_t st);

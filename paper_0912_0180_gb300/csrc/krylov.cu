@@ -20,57 +20,13 @@
 #include <type_traits>
 
 #include "stencil.cuh"
+#include "krylov_state.cuh"
 
 namespace helm {
 
 static double host_seconds() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
-
-constexpr int KT = 256;      // threads per block of the vector kernels
-#ifndef KRYLOV_BLOCKS_PER_SM
-#define KRYLOV_BLOCKS_PER_SM 2
-#endif
-constexpr int SMAX = 8;      // largest IDR shadow dimension
-constexpr int NRED = SMAX + 2;
-constexpr int GMRES_MMAX = HELM_GMRES_MAX_M;  // largest GMRES restart length
-
-struct KrylovState {
-  double2 rho, rho_old, alpha, omega, beta;
-  double bnorm, tol, rel_recur, rel_true;
-  int done, status, half, matvecs, iters, maxmv;
-  int k, oldest, s, loops;  // loops: body executions of the WHILE node in this solve
-  double2 M[SMAX * SMAX];  // IDR: P^H dR, column-major M[i + s*j]
-  double2 m[SMAX];         // IDR: P^H r
-  double2 c[SMAX];         // IDR: M^{-1} m
-  unsigned int ticket[8];  // last-block counters, one per reduction site
-  double* hist;            // optional residual history (device), capacity maxmv
-  double hn;               // GMRES: norm of the last orthogonalised vector, h_{j+1,j}
-  int gmm;                 // GMRES: restart length m
-  double2* gm;             // GMRES: Hessenberg matrix, rotations, g, y and the two h passes
-};
-
-struct Workspace {
-  int method = -1, s = 0;
-  int G = 0;                   // blocks of the vector kernels (fixed -> fixed reduction order)
-  KrylovState* st = nullptr;   // device
-  KrylovState* hst = nullptr;  // pinned host copy
-  double2* partials = nullptr; // [NRED][G]
-  double2 *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *sv = nullptr, *t = nullptr, *q = nullptr;
-  void *pmg = nullptr, *smg = nullptr;  // V-cycle inputs in the multigrid precision
-  double2 *ph = nullptr, *sh = nullptr; // V-cycle outputs, widened to complex128
-  double2 *P = nullptr, *dR = nullptr, *dX = nullptr;                  // IDR, s vectors each
-  double2 *V = nullptr, *gm = nullptr;  // GMRES: m + 1 basis vectors; its small dense arrays
-  int nred = NRED;                      // partial-sum slots per block
-  const void* shadow_key = nullptr;
-  cudaGraphExec_t loop = nullptr;
-  cudaGraphExec_t body = nullptr;       // host-driven loop: one iteration per launch
-  cudaGraphExec_t idr_init = nullptr;
-  cudaGraph_t loop_graph = nullptr, init_graph = nullptr, body_graph = nullptr;
-  size_t body_nodes = 0, init_nodes = 0;  // kernels per loop body / IDR start graph
-  std::vector<DevBlock> mem;
-  size_t bytes = 0;  // device bytes of mem (counted in the context's total while it lives)
-};
 
 // ---- block reductions -------------------------------------------------------------------
 
@@ -104,15 +60,18 @@ __device__ __forceinline__ void block_sum(double2 (&v)[K]) {
 
 // Stores this block's K partial sums, then returns true in the last block to arrive, where
 // `tot` holds the grand totals (summed in a fixed order) on every thread.
+// vb / vg: this block's index and the number of blocks among which the sum is split (the launch's
+// grid, or the instance's share of a grouped launch).
 template <int K>
-__device__ bool reduce_last(double2 (&v)[K], double2* partials, unsigned int* ticket, double2 (&tot)[K]) {
+__device__ bool reduce_last(double2 (&v)[K], double2* partials, unsigned int* ticket, double2 (&tot)[K], int vb,
+                            int vg) {
   __shared__ bool last;
   __shared__ double2 res[K];
   block_sum<K>(v);
-  int G = gridDim.x;
+  int G = vg;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) partials[k * G + blockIdx.x] = v[k];
+    for (int k = 0; k < K; ++k) partials[k * G + vb] = v[k];
     __threadfence();
     unsigned int t = atomicAdd(ticket, 1u);
     last = (t == (unsigned int)G - 1);
@@ -159,15 +118,20 @@ template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i,
   if (dst) reinterpret_cast<cx<TM>*>(dst)[i] = cconv<TM, double>(v);
 }
 
-#define GRID_LOOP(i, n) for (long i = blockIdx.x * (long)KT + threadIdx.x; i < (n); i += (long)gridDim.x * KT)
+// vb_ / vg_: the block's index and the block count of the instance (see VBLK and the bodies)
+#define GRID_LOOP(i, n) for (long i = vb_ * (long)KT + threadIdx.x; i < (n); i += (long)vg_ * KT)
+#define VBLK                                          \
+  const int vb_ = blockIdx.x, vg_ = gridDim.x;        \
+  (void)vb_;                                          \
+  (void)vg_
 
 // Stencil kernels walk warp-sized chunks of grid rows: a warp takes 32 consecutive points of
 // one row (fixed j, l), so its loads are coalesced, only the last chunk of a row has idle lanes,
 // and the index arithmetic costs one div/mod per chunk.
 #define ROW_LOOP(H, i, j, l, p)                                                              \
-  for (long ch_ = (blockIdx.x * (long)KT + threadIdx.x) >> 5, nch_ = ((H).n[0] + 31) >> 5,    \
+  for (long ch_ = (vb_ * (long)KT + threadIdx.x) >> 5, nch_ = ((H).n[0] + 31) >> 5,          \
             nc_ = nch_ * (H).n[1] * (H).n[2];                                                 \
-       ch_ < nc_; ch_ += ((long)gridDim.x * KT) >> 5)                                         \
+       ch_ < nc_; ch_ += ((long)vg_ * KT) >> 5)                                               \
     for (long row_ = ch_ / nch_, once_ = 1; once_; once_ = 0)                                 \
       for (int i = (int)(ch_ - row_ * nch_) * 32 + (threadIdx.x & 31), j = (int)(row_ % (H).n[1]), \
                l = (int)(row_ / (H).n[1]);                                                    \
@@ -182,6 +146,7 @@ __global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* 
                         double2* p, double2* v, void* rmg, int mg32, long n, int first,
                         double2* partials) {
   pdl_entry();
+  VBLK;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
     double2 ri = first ? b[i] : r[i];
@@ -192,7 +157,7 @@ __global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* 
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double rr = tot[0].x;
   if (first) {
@@ -216,6 +181,7 @@ template <int DIM>
 __global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __restrict__ b,
                            const double2* __restrict__ x, double2* __restrict__ r, long n, double2* partials) {
   pdl_entry();
+  VBLK;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
     double2 ri = csub<double>(b[p], op_row<double, double, DIM>(H, x, i, j, l, p));
@@ -223,7 +189,7 @@ __global__ void k_true_res(KrylovState* S, OpView<double> H, const double2* __re
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[1], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[1], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   S->rel_true = S->bnorm > 0.0 ? sqrt(tot[0].x) / S->bnorm : 0.0;
 }
@@ -244,9 +210,8 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, KrylovState* S, int in_
 
 // p = r + beta (p - omega v); its copy in multigrid precision feeds the V-cycle.
 template <typename TM>
-__global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ p,
+__device__ __forceinline__ void bicg_p_body(int vb_, int vg_, const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ p,
                          const double2* __restrict__ v, void* pmg, long n) {
-  pdl_entry();
   if (S->done) return;
   const double2 beta = S->beta;
   const double2 mbw = cmul<double>(mkc<double>(-beta.x, -beta.y), S->omega);  // -beta omega
@@ -256,12 +221,17 @@ __global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, do
     put_mg<TM>(pmg, i, pi);
   }
 }
+template <typename TM>
+__global__ void k_bicg_p(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ p,
+                         const double2* __restrict__ v, void* pmg, long n) {
+  pdl_entry();
+  bicg_p_body<TM>(blockIdx.x, gridDim.x, S, r, p, v, pmg, n);
+}
 
 // v = H p^ and alpha = rho / (r^H v).
 template <int DIM>
-__global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __restrict__ ph,
+__device__ __forceinline__ void bicg_v_body(int vb_, int vg_, KrylovState* S, const OpView<double>& H, const double2* __restrict__ ph,
                          const double2* __restrict__ rh, double2* __restrict__ v, long n, double2* partials) {
-  pdl_entry();
   if (S->done) return;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -270,7 +240,7 @@ __global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __rest
     acc[0] = cfmac<double>(rh[p], vi, acc[0]);
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[2], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[2], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   S->matvecs += 1;
   S->iters += 1;
@@ -279,12 +249,17 @@ __global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __rest
   if (is_zero(rv)) { finish(S, HELM_ERR_BREAKDOWN); return; }
   S->alpha = cdiv<double>(S->rho, rv);
 }
+template <int DIM>
+__global__ void k_bicg_v(KrylovState* S, OpView<double> H, const double2* __restrict__ ph,
+                         const double2* __restrict__ rh, double2* __restrict__ v, long n, double2* partials) {
+  pdl_entry();
+  bicg_v_body<DIM>(blockIdx.x, gridDim.x, S, H, ph, rh, v, n, partials);
+}
 
 // s = r - alpha v, ||s||; stop after the half step if ||s|| / ||b|| < tol (or at the cap).
 template <typename TM>
-__global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const double2* __restrict__ v,
+__device__ __forceinline__ void bicg_s_body(int vb_, int vg_, KrylovState* S, const double2* __restrict__ r, const double2* __restrict__ v,
                          double2* __restrict__ sv, void* smg, long n, double2* partials) {
-  pdl_entry();
   if (S->done) return;
   const double2 mal = mkc<double>(-S->alpha.x, -S->alpha.y);
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
@@ -295,7 +270,7 @@ __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const do
     acc[0].x = fma(si.x, si.x, fma(si.y, si.y, acc[0].x));
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double sn = sqrt(tot[0].x) / S->bnorm;
   record(S, sn);
@@ -303,20 +278,28 @@ __global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const do
   if (sn < S->tol) { S->half = 1; finish(S, HELM_OK); return; }
   if (S->matvecs >= S->maxmv) { S->half = 1; finish(S, HELM_ERR_MAXIT); }
 }
+template <typename TM>
+__global__ void k_bicg_s(KrylovState* S, const double2* __restrict__ r, const double2* __restrict__ v,
+                         double2* __restrict__ sv, void* smg, long n, double2* partials) {
+  pdl_entry();
+  bicg_s_body<TM>(blockIdx.x, gridDim.x, S, r, v, sv, smg, n, partials);
+}
 
 // x += alpha p^ after a half-step exit.
-__global__ void k_bicg_xhalf(KrylovState* S, const double2* __restrict__ ph, double2* __restrict__ x, long n) {
-  pdl_entry();
-  if (!S->half) return;
+__device__ __forceinline__ void bicg_xhalf_body(int vb_, int vg_, KrylovState* S, const double2* __restrict__ ph, double2* __restrict__ x, long n) {
+  if (S->half != 1) return;  // 2: a grouped loop applied it in an earlier body
   double2 al = S->alpha;
   GRID_LOOP(i, n) x[i] = cfma<double>(al, ph[i], x[i]);
+}
+__global__ void k_bicg_xhalf(KrylovState* S, const double2* __restrict__ ph, double2* __restrict__ x, long n) {
+  pdl_entry();
+  bicg_xhalf_body(blockIdx.x, gridDim.x, S, ph, x, n);
 }
 
 // t = H s^, omega = (t^H s) / (t^H t).
 template <int DIM>
-__global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __restrict__ sh,
+__device__ __forceinline__ void bicg_t_body(int vb_, int vg_, KrylovState* S, const OpView<double>& H, const double2* __restrict__ sh,
                          const double2* __restrict__ sv, double2* __restrict__ t, long n, double2* partials) {
-  pdl_entry();
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -326,7 +309,7 @@ __global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __rest
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
-  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot)) return;
+  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   S->matvecs += 1;
   double tt = tot[1].x;
@@ -334,13 +317,18 @@ __global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __rest
   if (tt == 0.0) { finish(S, HELM_ERR_BREAKDOWN); return; }
   S->omega = cscale<double>(1.0 / tt, tot[0]);
 }
+template <int DIM>
+__global__ void k_bicg_t(KrylovState* S, OpView<double> H, const double2* __restrict__ sh,
+                         const double2* __restrict__ sv, double2* __restrict__ t, long n, double2* partials) {
+  pdl_entry();
+  bicg_t_body<DIM>(blockIdx.x, gridDim.x, S, H, sh, sv, t, n, partials);
+}
 
 // x += alpha p^ + omega s^; r = s - omega t; ||r||, rho = r^H r and the next beta.
-__global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const double2* __restrict__ sh,
+__device__ __forceinline__ void bicg_xr_body(int vb_, int vg_, KrylovState* S, const double2* __restrict__ ph, const double2* __restrict__ sh,
                           const double2* __restrict__ sv, const double2* __restrict__ t,
                           const double2* __restrict__ rh, double2* __restrict__ x, double2* __restrict__ r,
                           long n, double2* partials) {
-  pdl_entry();
   if (S->done) return;
   double2 al = S->alpha, om = S->omega;
   const double2 mom = mkc<double>(-om.x, -om.y);
@@ -353,7 +341,7 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
     acc[1] = cfmac<double>(rh[i], ri, acc[1]);
   }
   double2 tot[2];
-  if (!reduce_last<2>(acc, partials, &S->ticket[5], tot)) return;
+  if (!reduce_last<2>(acc, partials, &S->ticket[5], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double rn = sqrt(tot[0].x) / S->bnorm;
   record(S, rn);
@@ -367,6 +355,125 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
   S->rho_old = S->rho;
   S->rho = rho;
   S->beta = cmul<double>(cdiv<double>(rho, S->rho_old), cdiv<double>(S->alpha, om));
+}
+__global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const double2* __restrict__ sh,
+                          const double2* __restrict__ sv, const double2* __restrict__ t,
+                          const double2* __restrict__ rh, double2* __restrict__ x, double2* __restrict__ r,
+                          long n, double2* partials) {
+  pdl_entry();
+  bicg_xr_body(blockIdx.x, gridDim.x, S, ph, sh, sv, t, rh, x, r, n, partials);
+}
+
+// ---- grouped Bi-CGSTAB: one launch per kernel for many instances ---------------------------
+// Block b of a grouped launch belongs to the instance with the largest `first` <= b; inside it the
+// block plays block b - first of the instance's own G-block launch, so every point, partial sum and
+// reduction order is the one the instance has alone.
+
+__device__ __forceinline__ const GroupBicg& group_member(const GroupBicg* __restrict__ A, int ni) {
+  __shared__ int s_i;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = ni - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {  // largest i with A[i].first <= b
+      const int mid = (lo + hi + 1) >> 1;
+      if (A[mid].first <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_i = lo;
+  }
+  __syncthreads();
+  return A[s_i];
+}
+
+template <typename TM>
+__global__ void kg_bicg_p(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  const int vb = blockIdx.x - g.first;
+  // the loop body runs for this instance: count it (the single-instance loop does this in its
+  // condition kernel)
+  if (vb == 0 && threadIdx.x == 0 && !g.S->done) g.S->loops += 1;
+  bicg_p_body<TM>(vb, g.G, g.S, g.r, g.p, g.v, g.pmg, g.n);
+}
+
+template <int DIM>
+__global__ void kg_bicg_v(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  bicg_v_body<DIM>(blockIdx.x - g.first, g.G, g.S, g.H, g.ph, g.rh, g.v, g.n, g.partials);
+}
+
+template <typename TM>
+__global__ void kg_bicg_s(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  bicg_s_body<TM>(blockIdx.x - g.first, g.G, g.S, g.r, g.v, g.sv, g.smg, g.n, g.partials);
+}
+
+__global__ void kg_bicg_xhalf(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  bicg_xhalf_body(blockIdx.x - g.first, g.G, g.S, g.ph, g.x, g.n);
+}
+
+template <int DIM>
+__global__ void kg_bicg_t(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  bicg_t_body<DIM>(blockIdx.x - g.first, g.G, g.S, g.H, g.sh, g.sv, g.t, g.n, g.partials);
+}
+
+__global__ void kg_bicg_xr(const GroupBicg* __restrict__ A, int ni) {
+  pdl_entry();
+  const GroupBicg& g = group_member(A, ni);
+  bicg_xr_body(blockIdx.x - g.first, g.G, g.S, g.ph, g.sh, g.sv, g.t, g.rh, g.x, g.r, g.n, g.partials);
+}
+
+// The WHILE condition of the grouped loop: continue while any instance is running.  At the end of
+// the body it also counts the group's bodies and, as the single-instance loop does, ends a loop
+// that ran more bodies than the largest matvec cap allows (HELM_ERR_TIMEOUT for the instances
+// still running).
+__global__ void kg_cond(cudaGraphConditionalHandle h, const GroupBicg* __restrict__ A, int ni, int* loops,
+                        int cap, int in_body) {
+  pdl_entry();
+  __shared__ int any;
+  if (threadIdx.x == 0) {
+    any = 0;
+    if (in_body) *loops += 1;
+  }
+  __syncthreads();
+  const bool over = in_body && *loops > cap;
+  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+    KrylovState* S = A[i].S;
+    // an instance that ended on a half step had x += alpha p^ applied in this body; the bodies
+    // that run on for the other instances must not apply it again
+    if (in_body && S->half == 1) S->half = 2;
+    if (!S->done) {
+      if (over) finish(S, HELM_ERR_TIMEOUT);
+      else any = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+template <typename TM>
+void group_krylov_launch(int which, const GroupBicg* A, int ni, int blocks, cudaStream_t st) {
+  switch (which) {
+    case GK_P: launch_pdl(kg_bicg_p<TM>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    case GK_V: launch_pdl(kg_bicg_v<2>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    case GK_S: launch_pdl(kg_bicg_s<TM>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    case GK_XHALF: launch_pdl(kg_bicg_xhalf, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    case GK_T: launch_pdl(kg_bicg_t<2>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    default: launch_pdl(kg_bicg_xr, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+  }
+}
+template void group_krylov_launch<float>(int, const GroupBicg*, int, int, cudaStream_t);
+template void group_krylov_launch<double>(int, const GroupBicg*, int, int, cudaStream_t);
+
+void group_cond_launch(cudaGraphConditionalHandle h, const GroupBicg* A, int ni, int* loops, int cap, int in_body,
+                       cudaStream_t st) {
+  launch_pdl(kg_cond, dim3(1), dim3(256), 0, st, h, A, ni, loops, cap, in_body);
 }
 
 // ---- IDR(s) -------------------------------------------------------------------------------
@@ -383,6 +490,7 @@ template <int DIM>
 __global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                            const double2* __restrict__ r, double2* __restrict__ t, long n, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -392,7 +500,7 @@ __global__ void k_idr_mr_t(KrylovState* S, OpView<double> H, const double2* __re
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
-  if (!reduce_last<2>(acc, partials, &S->ticket[2], tot)) return;
+  if (!reduce_last<2>(acc, partials, &S->ticket[2], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   S->matvecs += 1;
   S->iters += 1;
@@ -408,6 +516,7 @@ __global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict
                              double2* __restrict__ dX, double2* __restrict__ dR, double2* __restrict__ x,
                              double2* __restrict__ r, void* rmg, long n, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   double2 om = S->omega;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
@@ -424,7 +533,7 @@ __global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[3], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double rn = sqrt(tot[0].x) / S->bnorm;
   record(S, rn);
@@ -438,13 +547,14 @@ template <int S_>
 __global__ void k_idr_proj(KrylovState* S, const double2* __restrict__ P, const double2* __restrict__ y,
                            int col, long n, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   double2 acc[S_];
 #pragma unroll
   for (int k = 0; k < S_; ++k) acc[k] = mkc<double>(0.0, 0.0);
   GRID_LOOP(i, n) proj_acc<S_>(P, n, i, y[i], acc);
   double2 tot[S_];
-  if (!reduce_last<S_>(acc, partials, &S->ticket[6], tot)) return;
+  if (!reduce_last<S_>(acc, partials, &S->ticket[6], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   for (int k = 0; k < S_; ++k) {
     if (col >= 0) S->M[k + S_ * col] = tot[k];
@@ -490,6 +600,7 @@ template <typename TM, int S_>
 __global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, const double2* __restrict__ r,
                         double2* __restrict__ q, void* vmg, long n) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   double2 c[S_];
 #pragma unroll
@@ -509,6 +620,7 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __rest
                          const double2* __restrict__ r, const double2* __restrict__ q,
                          double2* __restrict__ t, long n, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done || S->k != 0) return;
   double2 acc[2] = {mkc<double>(0.0, 0.0), mkc<double>(0.0, 0.0)};
   ROW_LOOP(H, i, j, l, p) {
@@ -518,7 +630,7 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __rest
     acc[1].x = fma(ti.x, ti.x, fma(ti.y, ti.y, acc[1].x));
   }
   double2 tot[2];
-  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot)) return;
+  if (!reduce_last<2>(acc, partials, &S->ticket[4], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double tt = tot[1].x;
   if (!isfinite(tt) || !finite2(tot[0])) { finish(S, HELM_ERR_NAN); return; }
@@ -530,6 +642,7 @@ __global__ void k_idr_t0(KrylovState* S, OpView<double> H, const double2* __rest
 template <int S_>
 __global__ void k_idr_dx(const KrylovState* S, double2* __restrict__ dX, const double2* __restrict__ z, long n) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   double2 c[S_];
 #pragma unroll
@@ -549,6 +662,7 @@ template <int DIM>
 __global__ void k_idr_tk(const KrylovState* S, OpView<double> H, const double2* __restrict__ dX,
                          double2* __restrict__ t, long n) {
   pdl_entry();
+  VBLK;
   if (S->done || S->k == 0) return;
   const double2* d = dX + S->oldest * n;
   ROW_LOOP(H, i, j, l, p) {
@@ -564,6 +678,7 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
                           const double2* __restrict__ t, double2* __restrict__ x, double2* __restrict__ r,
                           long n, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   int o = S->oldest;
   bool first = S->k == 0;
@@ -582,7 +697,7 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
     proj_acc<S_>(P, n, i, dr, acc);
   }
   double2 tot[S_ + 1];
-  if (!reduce_last<S_ + 1>(acc, partials, &S->ticket[5], tot)) return;
+  if (!reduce_last<S_ + 1>(acc, partials, &S->ticket[5], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   S->matvecs += 1;
   S->iters += 1;
@@ -602,15 +717,17 @@ __global__ void k_idr_upd(KrylovState* S, const double2* __restrict__ P, double2
 __global__ void k_dot1(KrylovState* S, const double2* __restrict__ a, const double2* __restrict__ b,
                        long n, double2* partials, double2* out) {
   pdl_entry();
+  VBLK;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) acc[0] = cfmac<double>(a[i], b[i], acc[0]);
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[7], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[7], tot, vb_, vg_)) return;
   if (threadIdx.x == 0) *out = tot[0];
 }
 // ... P_j -= h P_i  (mode 0)  or  P_j /= sqrt(h)  (mode 1, h = P_j^H P_j)
 __global__ void k_mgs_upd(double2* __restrict__ pj, const double2* __restrict__ pi, const double2* h, int mode, long n) {
   pdl_entry();
+  VBLK;
   double2 hv = *h;
   double sc = mode ? 1.0 / sqrt(hv.x) : 0.0;
   GRID_LOOP(i, n) {
@@ -647,6 +764,7 @@ inline size_t gm_elems(int m) { return (size_t)(m + 1) * m + 6 * (size_t)m + 3; 
 __global__ void k_gm_start(KrylovState* S, const double2* __restrict__ b, double2* r, long n, int first,
                            double2* partials) {
   pdl_entry();
+  VBLK;
   double2 acc[1] = {mkc<double>(0.0, 0.0)};
   GRID_LOOP(i, n) {
     double2 ri = first ? b[i] : r[i];
@@ -654,7 +772,7 @@ __global__ void k_gm_start(KrylovState* S, const double2* __restrict__ b, double
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[0], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   double beta = sqrt(tot[0].x);
   if (first) {
@@ -679,6 +797,7 @@ template <typename TM>
 __global__ void k_gm_v0(const KrylovState* S, const double2* __restrict__ r, double2* __restrict__ V, void* vmg,
                         long n) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   const double beta = S->beta.x;
   GRID_LOOP(i, n) {
@@ -693,6 +812,7 @@ template <int DIM>
 __global__ void k_gm_w(const KrylovState* S, OpView<double> H, const double2* __restrict__ z,
                        double2* __restrict__ w, long n) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   ROW_LOOP(H, i, j, l, p) w[p] = op_row<double, double, DIM>(H, z, i, j, l, p);
 }
@@ -815,6 +935,7 @@ __device__ void gm_step_end(KrylovState* S, double hn) {
 __global__ void k_gm_sub(KrylovState* S, const double2* __restrict__ V, double2* __restrict__ w,
                          const double2* __restrict__ h, long n, int final, double2* partials) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   __shared__ double2 hs[GMRES_MMAX + 1];
   const int j = S->k;
@@ -830,7 +951,7 @@ __global__ void k_gm_sub(KrylovState* S, const double2* __restrict__ V, double2*
   }
   if (!final) return;
   double2 tot[1];
-  if (!reduce_last<1>(acc, partials, &S->ticket[5], tot)) return;
+  if (!reduce_last<1>(acc, partials, &S->ticket[5], tot, vb_, vg_)) return;
   if (threadIdx.x) return;
   gm_step_end(S, sqrt(tot[0].x));
 }
@@ -840,6 +961,7 @@ template <typename TM>
 __global__ void k_gm_next(const KrylovState* S, const double2* __restrict__ w, double2* __restrict__ V, void* vmg,
                           long n) {
   pdl_entry();
+  VBLK;
   if (S->done) return;
   const double hn = S->hn;
   double2* vk = V + (size_t)S->k * n;
@@ -868,6 +990,7 @@ __global__ void k_gm_y(KrylovState* S) {
 template <typename TM>
 __global__ void k_gm_comb(const KrylovState* S, const double2* __restrict__ V, void* umg, double2* u64, long n) {
   pdl_entry();
+  VBLK;
   __shared__ double2 ys[GMRES_MMAX];
   const int k = S->k;
   GmView G = gm_view(S->gm, S->gmm);
@@ -884,6 +1007,7 @@ __global__ void k_gm_comb(const KrylovState* S, const double2* __restrict__ V, v
 // x += z
 __global__ void k_gm_addx(const KrylovState* S, const double2* __restrict__ z, double2* __restrict__ x, long n) {
   pdl_entry();
+  VBLK;
   if (S->k == 0) return;
   GRID_LOOP(i, n) x[i] = cadd<double>(x[i], z[i]);
 }
@@ -1402,6 +1526,44 @@ static helm_status job_step_t(SolveJob& j) {
   j.status = fs;
   j.finished = true;
   return HELM_OK;
+}
+
+// ---- helpers of the grouped solve (group.cu): one instance's part outside the grouped loop ----
+
+template <typename TM>
+static helm_status group_member_begin_t(helm_ctx* c, const helm_solve_opts* o, cudaStream_t st) {
+  Ctx k{};
+  helm_status s = prepare<TM>(c, o, k, st);
+  if (s != HELM_OK) return s;
+  Workspace* w = c->ws;
+  const double tol = o->tol;
+  const int maxmv = o->maxmv, sdim = o->s;
+  double* hist = nullptr;
+  HELM_CUDA(cudaMemcpyAsync(&w->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemcpyAsync(&w->st->maxmv, &maxmv, sizeof(int), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemcpyAsync(&w->st->s, &sdim, sizeof(int), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * c->n, st));
+  return HELM_OK;
+}
+
+helm_status group_member_begin(helm_ctx* c, const helm_solve_opts* o, cudaStream_t st) {
+  const bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
+  return f32 ? group_member_begin_t<float>(c, o, st) : group_member_begin_t<double>(c, o, st);
+}
+
+void group_member_start(helm_ctx* c, const double2* b, bool first, cudaStream_t st) {
+  Workspace* w = c->ws;
+  const bool f32 = c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64;
+  launch_pdl(k_start, dim3(w->G), dim3(KT), 0, st, w->st, b, w->r, w->rh, w->p, w->v, (void*)nullptr,
+             f32 ? 1 : 0, c->n, first ? 1 : 0, w->partials);
+}
+
+void group_member_true_res(helm_ctx* c, const double2* b, cudaStream_t st) {
+  Workspace* w = c->ws;
+  OpView<double> H = c->H.view<double>();
+  launch_pdl(k_true_res<2>, dim3(w->G), dim3(KT), 0, st, w->st, H, b, w->x, w->r, c->n, w->partials);
+  cudaMemcpyAsync(w->hst, w->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, st);
 }
 
 static bool job_f32(const helm_ctx* c) { return c->pc.kind != HELM_PC_NONE && c->pc.mg_dtype == HELM_C64; }

@@ -46,11 +46,8 @@ enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2, TILE_SQUARE = 3 };
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
 template <typename T, bool RBGS, int CX, int CY, int NT>
-__global__ void __launch_bounds__(NT)
-k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
-         cx<T>* __restrict__ fc, T omega, const int* skip) {
-  pdl_entry();
-  if (skip && *skip) return;
+__device__ __forceinline__ void down2d_body(int bx_, int by_, const OpView<T>& op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
+         cx<T>* __restrict__ fc, T omega) {
   constexpr int HF = RBGS ? 2 : 1;
   constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;  // residual region
   constexpr int FX = RX + 2 * HF, FY = RY + 2 * HF;      // staged f / u region
@@ -58,7 +55,7 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
   __shared__ cx<T> su[FY][FX];
   __shared__ cx<T> sr[RY][RX];
   const int n0 = op.n[0], n1 = op.n[1];
-  const int I0 = blockIdx.x * CX, J0 = blockIdx.y * CY;
+  const int I0 = bx_ * CX, J0 = by_ * CY;
   const int fx0 = 2 * I0 - HF, fy0 = 2 * J0 - HF;  // origin of the staged region
   const int tid = threadIdx.x;
   // stage f; Jacobi: u = omega D^-1 f; RB-GS: red u = D^-1 f, black 0.  All loads of a
@@ -145,21 +142,26 @@ k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __r
     fc[I + nc0 * J] = cscale<T>(T(0.0625), acc);
   }
 }
+template <typename T, bool RBGS, int CX, int CY, int NT>
+__global__ void __launch_bounds__(NT)
+k_down2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
+         cx<T>* __restrict__ fc, T omega, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  down2d_body<T, RBGS, CX, CY, NT>(blockIdx.x, blockIdx.y, op, nc0, nc1, f, u_out, fc, omega);
+}
 
 // ---- up: prolongation + correction + post-smoothing (2D, nu2 = 1), out of place --------------
 template <typename T, bool RBGS, typename TO, int FX, int FY, int NT>
-__global__ void __launch_bounds__(NT)
-k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
-       const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega, const int* skip) {
-  pdl_entry();
-  if (skip && *skip) return;
+__device__ __forceinline__ void up2d_body(int bx_, int by_, const OpView<T>& op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
+       const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega) {
   constexpr int HU = RBGS ? 2 : 1;                 // halo of the corrected iterate
   constexpr int UX = FX + 2 * HU, UY = FY + 2 * HU;
   constexpr int CXN = UX / 2 + 3, CYN = UY / 2 + 3;  // coarse values covering the region
   __shared__ cx<T> su[UY][UX];
   __shared__ cx<T> se[CYN][CXN];
   const int n0 = op.n[0], n1 = op.n[1];
-  const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY;
+  const int i0 = bx_ * FX, j0 = by_ * FY;
   const int ux0 = i0 - HU, uy0 = j0 - HU;
   const int cx0 = (ux0 >> 1) - 1, cy0 = (uy0 >> 1) - 1;  // floor division for negatives
   const int tid = threadIdx.x;
@@ -245,6 +247,14 @@ k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<
       u_out[p] = cconv<TO, T>(v);
     }
   }
+}
+template <typename T, bool RBGS, typename TO, int FX, int FY, int NT>
+__global__ void __launch_bounds__(NT)
+k_up2d(OpView<T> op, int nc0, int nc1, const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
+       const cx<T>* __restrict__ f, cx<TO>* __restrict__ u_out, T omega, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  up2d_body<T, RBGS, TO, FX, FY, NT>(blockIdx.x, blockIdx.y, op, nc0, nc1, u_in, ec, f, u_out, omega);
 }
 
 // ---- tail: the coarsest levels in one block ------------------------------------------------
@@ -337,11 +347,8 @@ __device__ __forceinline__ int tail_lin(int x, int nc, int* c, T* w) {
 }
 
 template <typename T, int DIM, typename TO>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ TailArgs<T> a,
-                                                       const cx<T>* __restrict__ f_in,
-                                                       cx<TO>* __restrict__ u_outg, const int* skip) {
-  pdl_entry();
-  if (skip && *skip) return;
+__device__ __forceinline__ void tail_body(const TailArgs<T>& a, const cx<T>* __restrict__ f_in,
+                                          cx<TO>* __restrict__ u_outg) {
   extern __shared__ unsigned char tail_smem[];
   // every level's operator with its coefficient tables redirected to shared-memory copies, so
   // that no phase waits on a global load
@@ -477,6 +484,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ T
   }
 }
 
+template <typename T, int DIM, typename TO>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ TailArgs<T> a,
+                                                       const cx<T>* __restrict__ f_in,
+                                                       cx<TO>* __restrict__ u_outg, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  tail_body<T, DIM, TO>(a, f_in, u_outg);
+}
+
 // ---- host side ----------------------------------------------------------------------------
 
 // Points handled by the single block: its phases cost a fraction of a microsecond each only while
@@ -527,10 +543,10 @@ static helm_status tail_launch(const TailArgs<T>& a, int dim, size_t smem, const
   return HELM_OK;
 }
 
+// The tail's arguments for levels first.. of c, and the dynamic shared memory it needs.
 template <typename T>
-helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,
-                        cudaStream_t st) {
-  TailArgs<T> a{};
+static size_t tail_args(const helm_ctx* c, int first, TailArgs<T>& a) {
+  a = TailArgs<T>{};
   int nl = (int)c->lv.size();
   a.count = nl - first;
   int off = 0;
@@ -557,7 +573,14 @@ helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool 
   a.nu2 = c->pc.nu2;
   a.smoother = c->pc.smoother;
   a.omega = (T)c->pc.omega;
-  size_t smem = (size_t)off * sizeof(cx<T>);
+  return (size_t)off * sizeof(cx<T>);
+}
+
+template <typename T>
+helm_status tail_vcycle(helm_ctx* c, int first, const cx<T>* f, void* out, bool out_f64, const int* skip,
+                        cudaStream_t st) {
+  TailArgs<T> a;
+  const size_t smem = tail_args<T>(c, first, a);
   if (out_f64) return tail_launch<T, double>(a, c->grid.dim, smem, f, (double2*)out, skip, st);
   return tail_launch<T, T>(a, c->grid.dim, smem, f, (cx<T>*)out, skip, st);
 }
@@ -582,6 +605,26 @@ static void down_tile(int tile, const LevelHost& F, const LevelHost& C, const cx
   else if (tile == TILE_TINY) down_launch<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else if (tile == TILE_SQUARE) down_launch<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
+}
+
+// The tile a level's fused kernels use (the autotuner's choice, else the block-count rule) and its
+// coarse (down) or fine (up) extent.
+static int down_tile_of(const helm_ctx* c, int l, int* tx, int* ty) {
+  const LevelHost& F = c->lv[l];
+  const LevelHost& C = c->lv[l + 1];
+  long nb = (long)((C.n[0] + DN_CX - 1) / DN_CX) * ((C.n[1] + DN_CY - 1) / DN_CY);
+  int tile = F.tile_down >= 0 ? F.tile_down : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
+  *tx = tile == TILE_BIG ? DN_CX : tile == TILE_TINY ? DN_TCX : tile == TILE_SQUARE ? DN_QCX : DN_SCX;
+  *ty = tile == TILE_BIG ? DN_CY : tile == TILE_TINY ? DN_TCY : tile == TILE_SQUARE ? DN_QCY : DN_SCY;
+  return tile;
+}
+static int up_tile_of(const helm_ctx* c, int l, int* tx, int* ty) {
+  const LevelHost& F = c->lv[l];
+  long nb = (long)((F.n[0] + UP_FX - 1) / UP_FX) * ((F.n[1] + UP_FY - 1) / UP_FY);
+  int tile = F.tile_up >= 0 ? F.tile_up : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
+  *tx = tile == TILE_BIG ? UP_FX : tile == TILE_TINY ? UP_TFX : tile == TILE_SQUARE ? UP_QFX : UP_SFX;
+  *ty = tile == TILE_BIG ? UP_FY : tile == TILE_TINY ? UP_TFY : tile == TILE_SQUARE ? UP_QFY : UP_SFY;
+  return tile;
 }
 
 template <typename T>
@@ -631,6 +674,319 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
   if (out_f64) up_dispatch<T, double>(c, F, C, u_in, ec, f, out, skip, st);
   else up_dispatch<T, T>(c, F, C, u_in, ec, f, out, skip, st);
 }
+
+// ---- grouped V-cycle: one launch per level for many instances --------------------------------
+// The instances of a group (2D, V(1,1), fused levels) run their V-cycles together: level l of
+// every instance that still has a fused level there goes out in one k_down2d launch (and one
+// k_up2d launch on the way up), each instance's one-block tail in one launch with a block per
+// instance, and the coarsest dense solves of the others in one launch.  Each instance's work,
+// point by point, is what its own V-cycle does, so the results are bitwise those of the instance
+// alone.  A descriptor per instance and launch (device array) gives its operator, buffers and
+// the first block it owns; block b belongs to the descriptor with the largest `first` <= b.
+
+template <typename T> struct GDown {
+  OpView<T> op;
+  int nc0, nc1;
+  const cx<T>* f;
+  cx<T>* u_out;
+  cx<T>* fc;
+  T omega;
+  const int* skip;
+  int first, tiles_x;
+};
+template <typename T> struct GUp {
+  OpView<T> op;
+  int nc0, nc1;
+  const cx<T>* u_in;
+  const cx<T>* ec;
+  const cx<T>* f;
+  void* u_out;  // cx<T>, or complex128 on the finest level
+  T omega;
+  const int* skip;
+  int first, tiles_x;
+};
+template <typename T> struct GCoarse {
+  const cx<T>* ainv;
+  int n;
+  const cx<T>* f;
+  cx<T>* z;
+  const int* skip;
+  int first;
+};
+template <typename T> struct GTail {  // one block per instance
+  TailArgs<T> a;
+  const cx<T>* f;
+  void* out;
+  const int* skip;
+};
+
+template <typename D>
+__device__ __forceinline__ const D& group_pick(const D* __restrict__ A, int ni) {
+  __shared__ int s_i;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = ni - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (A[mid].first <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_i = lo;
+  }
+  __syncthreads();
+  return A[s_i];
+}
+
+template <typename T, bool RBGS, int CX, int CY, int NT>
+__global__ void __launch_bounds__(NT) kg_down2d(const GDown<T>* __restrict__ A, int ni) {
+  pdl_entry();
+  const GDown<T>& g = group_pick(A, ni);
+  if (g.skip && *g.skip) return;
+  const int t = blockIdx.x - g.first;
+  down2d_body<T, RBGS, CX, CY, NT>(t % g.tiles_x, t / g.tiles_x, g.op, g.nc0, g.nc1, g.f, g.u_out, g.fc, g.omega);
+}
+
+template <typename T, bool RBGS, typename TO, int FX, int FY, int NT>
+__global__ void __launch_bounds__(NT) kg_up2d(const GUp<T>* __restrict__ A, int ni) {
+  pdl_entry();
+  const GUp<T>& g = group_pick(A, ni);
+  if (g.skip && *g.skip) return;
+  const int t = blockIdx.x - g.first;
+  up2d_body<T, RBGS, TO, FX, FY, NT>(t % g.tiles_x, t / g.tiles_x, g.op, g.nc0, g.nc1, g.u_in, g.ec, g.f,
+                                     (cx<TO>*)g.u_out, g.omega);
+}
+
+// z = A^{-1} f with the dense coarsest inverse, one warp per row (as k_coarse)
+template <typename T>
+__global__ void kg_coarse(const GCoarse<T>* __restrict__ A, int ni) {
+  pdl_entry();
+  const GCoarse<T>& g = group_pick(A, ni);
+  if (g.skip && *g.skip) return;
+  const int warp = ((blockIdx.x - g.first) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= g.n) return;
+  const cx<T>* row = g.ainv + (long)warp * g.n;
+  cx<T> acc = mkc<T>(T(0), T(0));
+  for (int c = lane; c < g.n; c += 32) acc = cfma<T>(row[c], g.f[c], acc);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) g.z[warp] = acc;
+}
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(TAIL_THREADS) kg_tail(const GTail<T>* __restrict__ A) {
+  pdl_entry();
+  const GTail<T>& g = A[blockIdx.x];
+  if (g.skip && *g.skip) return;
+  tail_body<T, 2, TO>(g.a, g.f, (cx<TO>*)g.out);
+}
+
+struct GroupVcycle {
+  bool rb = false;
+  struct Launch {
+    void* args = nullptr;  // device array of descriptors
+    int ni = 0, blocks = 0;
+    size_t smem = 0;
+    int tile = 0;  // fused levels: the tile shape of every instance in this launch
+  };
+  // per level, one launch per tile shape in use there (each instance keeps the tile its own
+  // V-cycle uses, so that its arithmetic is exactly that of its lone cycle); up[0] writes the
+  // complex128 result
+  std::vector<std::vector<Launch>> down, up;
+  Launch tail0, tailk, coarse;    // tails from the finest level / from a coarser one; dense coarsest solves
+  std::vector<DevBlock> mem;
+};
+
+template <typename D>
+static helm_status group_upload(GroupVcycle* P, const std::vector<D>& v, int blocks, GroupVcycle::Launch* L,
+                                cudaStream_t st) {
+  L->ni = (int)v.size();
+  L->blocks = blocks;
+  if (v.empty()) return HELM_OK;
+  DevBlock b;
+  helm_status s = dev_alloc(&L->args, sizeof(D) * v.size(), st, &b);
+  if (s != HELM_OK) return s;
+  P->mem.push_back(b);
+  HELM_CUDA(cudaMemcpyAsync(L->args, v.data(), sizeof(D) * v.size(), cudaMemcpyHostToDevice, st));
+  return HELM_OK;
+}
+
+template <typename T>
+helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* in, double2* const* out,
+                               const int* const* skip, cudaStream_t st, GroupVcycle** plan) {
+  *plan = nullptr;
+  auto* P = new GroupVcycle();
+  P->rb = cs[0]->pc.smoother == HELM_SM_RBGS;
+  std::vector<int> tf(ni), stop(ni);
+  int lmax = 0;
+  for (int i = 0; i < ni; ++i) {
+    const int nl = (int)cs[i]->lv.size();
+    tf[i] = std::min(cs[i]->tail_first, nl);
+    stop[i] = std::min(tf[i], nl - 1);  // fused levels above the tail or the coarsest
+    lmax = std::max(lmax, stop[i]);
+  }
+  helm_status s = HELM_OK;
+  P->down.resize(lmax);
+  P->up.resize(lmax);
+  for (int l = 0; l < lmax && s == HELM_OK; ++l) {
+    for (int tile = 0; tile < 4 && s == HELM_OK; ++tile) {
+      std::vector<GDown<T>> dv;
+      std::vector<GUp<T>> uv;
+      int bd = 0, bu = 0;
+      for (int i = 0; i < ni; ++i) {
+        if (l >= stop[i]) continue;
+        const helm_ctx* c = cs[i];
+        const LevelHost& F = c->lv[l];
+        const LevelHost& C = c->lv[l + 1];
+        int cx_, cy_, fx_, fy_;
+        if (down_tile_of(c, l, &cx_, &cy_) == tile) {
+          const cx<T>* f = l == 0 ? (const cx<T>*)in[i] : (const cx<T>*)F.f;
+          GDown<T> d{F.view<T>(), C.n[0], C.n[1], f, (cx<T>*)F.w, (cx<T>*)C.f, (T)c->pc.omega, skip[i], bd,
+                     (C.n[0] + cx_ - 1) / cx_};
+          bd += d.tiles_x * ((C.n[1] + cy_ - 1) / cy_);
+          dv.push_back(d);
+        }
+        if (up_tile_of(c, l, &fx_, &fy_) == tile) {
+          const cx<T>* f = l == 0 ? (const cx<T>*)in[i] : (const cx<T>*)F.f;
+          GUp<T> u{F.view<T>(), C.n[0], C.n[1], (const cx<T>*)F.w, (const cx<T>*)C.u, f,
+                   l == 0 ? (void*)out[i] : F.u, (T)c->pc.omega, skip[i], bu, (F.n[0] + fx_ - 1) / fx_};
+          bu += u.tiles_x * ((F.n[1] + fy_ - 1) / fy_);
+          uv.push_back(u);
+        }
+      }
+      GroupVcycle::Launch ld, lu;
+      ld.tile = lu.tile = tile;
+      s = group_upload(P, dv, bd, &ld, st);
+      if (s == HELM_OK) s = group_upload(P, uv, bu, &lu, st);
+      if (ld.ni) P->down[l].push_back(ld);
+      if (lu.ni) P->up[l].push_back(lu);
+    }
+  }
+  std::vector<GTail<T>> t0, tk;
+  std::vector<GCoarse<T>> co;
+  size_t smem0 = 0, smemk = 0;
+  int bc = 0;
+  for (int i = 0; i < ni && s == HELM_OK; ++i) {
+    helm_ctx* c = cs[i];
+    const int nl = (int)c->lv.size();
+    if (tf[i] < nl) {
+      GTail<T> g;
+      const size_t sm = tail_args<T>(c, tf[i], g.a);
+      g.skip = skip[i];
+      if (tf[i] == 0) {
+        g.f = (const cx<T>*)in[i];
+        g.out = out[i];
+        t0.push_back(g);
+        smem0 = std::max(smem0, sm);
+      } else {
+        g.f = (const cx<T>*)c->lv[tf[i]].f;
+        g.out = c->lv[tf[i]].u;
+        tk.push_back(g);
+        smemk = std::max(smemk, sm);
+      }
+    } else {
+      const LevelHost& Lc = c->lv[nl - 1];
+      GCoarse<T> g{(const cx<T>*)c->coarse_inv, c->nco, (const cx<T>*)Lc.f, (cx<T>*)Lc.u, skip[i], bc};
+      bc += (c->nco * 32 + 255) / 256;
+      co.push_back(g);
+    }
+  }
+  if (s == HELM_OK) s = group_upload(P, t0, (int)t0.size(), &P->tail0, st);
+  if (s == HELM_OK) s = group_upload(P, tk, (int)tk.size(), &P->tailk, st);
+  if (s == HELM_OK) s = group_upload(P, co, bc, &P->coarse, st);
+  P->tail0.smem = smem0;
+  P->tailk.smem = smemk;
+  if (s == HELM_OK && smem0)
+    s = cuda_err(cudaFuncSetAttribute(kg_tail<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0));
+  if (s == HELM_OK && smemk)
+    s = cuda_err(cudaFuncSetAttribute(kg_tail<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemk));
+  if (s != HELM_OK) {
+    group_vcycle_free(P, st);
+    return s;
+  }
+  *plan = P;
+  return HELM_OK;
+}
+
+template <typename T, bool RB>
+static void group_down_launch(const GroupVcycle::Launch& L, cudaStream_t st) {
+  const GDown<T>* a = (const GDown<T>*)L.args;
+  if (L.tile == TILE_BIG)
+    launch_pdl(kg_down2d<T, RB, DN_CX, DN_CY, FUSED_THREADS>, dim3(L.blocks), dim3(FUSED_THREADS), 0, st, a, L.ni);
+  else if (L.tile == TILE_TINY)
+    launch_pdl(kg_down2d<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>, dim3(L.blocks), dim3(FUSED_TINY_THREADS), 0, st,
+               a, L.ni);
+  else if (L.tile == TILE_SQUARE)
+    launch_pdl(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, L.ni);
+  else
+    launch_pdl(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, L.ni);
+}
+
+template <typename T, bool RB, typename TO>
+static void group_up_launch(const GroupVcycle::Launch& L, cudaStream_t st) {
+  const GUp<T>* a = (const GUp<T>*)L.args;
+  if (L.tile == TILE_BIG)
+    launch_pdl(kg_up2d<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>, dim3(L.blocks), dim3(FUSED_THREADS), 0, st, a, L.ni);
+  else if (L.tile == TILE_TINY)
+    launch_pdl(kg_up2d<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>, dim3(L.blocks), dim3(FUSED_TINY_THREADS), 0,
+               st, a, L.ni);
+  else if (L.tile == TILE_SQUARE)
+    launch_pdl(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, L.ni);
+  else
+    launch_pdl(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, L.ni);
+}
+
+template <typename T, bool RB>
+static void group_vcycle_enqueue_t(const GroupVcycle* P, cudaStream_t st) {
+  for (size_t l = 0; l < P->down.size(); ++l)
+    for (const auto& L : P->down[l]) group_down_launch<T, RB>(L, st);
+  if (P->tail0.ni)
+    launch_pdl(kg_tail<T, double>, dim3(P->tail0.ni), dim3(TAIL_THREADS), P->tail0.smem, st,
+               (const GTail<T>*)P->tail0.args);
+  if (P->tailk.ni)
+    launch_pdl(kg_tail<T, T>, dim3(P->tailk.ni), dim3(TAIL_THREADS), P->tailk.smem, st,
+               (const GTail<T>*)P->tailk.args);
+  if (P->coarse.ni)
+    launch_pdl(kg_coarse<T>, dim3(P->coarse.blocks), dim3(256), 0, st, (const GCoarse<T>*)P->coarse.args,
+               P->coarse.ni);
+  for (size_t l = P->up.size(); l-- > 0;)
+    for (const auto& L : P->up[l]) {
+      if (l == 0) group_up_launch<T, RB, double>(L, st);
+      else group_up_launch<T, RB, T>(L, st);
+    }
+}
+
+template <typename T>
+void group_vcycle_enqueue(const GroupVcycle* P, cudaStream_t st) {
+  if (P->rb) group_vcycle_enqueue_t<T, true>(P, st);
+  else group_vcycle_enqueue_t<T, false>(P, st);
+}
+
+long group_vcycle_launches(const GroupVcycle* P) {
+  long k = (P->tail0.ni > 0) + (P->tailk.ni > 0) + (P->coarse.ni > 0);
+  for (const auto& v : P->down) k += (long)v.size();
+  for (const auto& v : P->up) k += (long)v.size();
+  return k;
+}
+
+void group_vcycle_free(GroupVcycle* P, cudaStream_t st) {
+  if (!P) return;
+  dev_free_all(P->mem, st);
+  delete P;
+}
+
+template helm_status group_vcycle_build<float>(helm_ctx* const*, int, const void* const*, double2* const*,
+                                               const int* const*, cudaStream_t, GroupVcycle**);
+template helm_status group_vcycle_build<double>(helm_ctx* const*, int, const void* const*, double2* const*,
+                                                const int* const*, cudaStream_t, GroupVcycle**);
+template void group_vcycle_enqueue<float>(const GroupVcycle*, cudaStream_t);
+template void group_vcycle_enqueue<double>(const GroupVcycle*, cudaStream_t);
 
 // ---- autotuner ------------------------------------------------------------------------------
 // On every fused 2D level the large, small, square and one-warp tiles of k_down2d and k_up2d are timed with

@@ -302,6 +302,24 @@ def solve_batch(instances, bs, *, method=0, s=4, tol: float = 1e-6, maxmv: int =
     return xs, out
 
 
+def solve_group(instances, bs, *, tol: float = 1e-6, maxmv: int = 2000, max_restarts: int = 3, stream=None,
+                xs=None):
+    """helm_solve_group: Bi-CGSTAB on every (Helm instance, rhs) pair as one group, each kernel of an
+    iteration one launch over all instances; returns (xs, infos)."""
+    lib = L.load()
+    n = len(instances)
+    if xs is None:
+        xs = [torch.empty(h.n, dtype=torch.complex128, device=b.device) for h, b in zip(instances, bs)]
+    o = L.SolveOpts(0, 4, tol, maxmv, max_restarts, None, None, 0)
+    infos = (L.SolveInfo * max(n, 1))()
+    cs = (C.c_void_p * max(n, 1))(*[h._h.value for h in instances])
+    bp = (C.c_void_p * max(n, 1))(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * max(n, 1))(*[x.data_ptr() for x in xs])
+    st = lib.helm_solve_group(cs, bp, xp, n, C.byref(o), infos, C.c_void_p(_stream(stream)))
+    _check(st, "helm_solve_group", (L.HELM_OK, L.HELM_ERR_BREAKDOWN, L.HELM_ERR_MAXIT, L.HELM_ERR_NAN))
+    return xs, [_info(infos[i]) for i in range(n)]
+
+
 class Server:
     """helm_server_*: continuous-batching solve server (requests from host memory)."""
 

@@ -209,3 +209,81 @@ def test_gmres_in_batch_and_server():
     srv.close()
     for h in hs:
         h.close()
+
+
+def _group_instances(smoother):
+    """Uneven 2D instances for one group: sizes (from a one-level tail to many fused levels), ragged
+    and one-sided layers, constant and bump k, CSG / CSL / interior-CSG with different parameters."""
+    specs = [
+        (33, 6, 10.0, "const", hi.PC_CSG_UNIFORM, 0.3),
+        (96, 16, 25.0, "bump", hi.PC_CSL, 0.3),
+        ((70, 33), ((6, 0), (4, 9)), 12.0, "bump", hi.PC_CSG_UNIFORM, 0.25),
+        (130, 20, 30.0, "const", hi.PC_CSG_INTERIOR, 0.3),
+        ((161, 120), ((0, 9), (5, 5)), 40.0, "bump", hi.PC_CSL, 0.3),
+        (12, 2, 4.0, "const", hi.PC_CSG_UNIFORM, 0.3),
+    ]
+    out = []
+    for i, (n_int, nl, k0, kind, pck, th) in enumerate(specs):
+        p = hi.make_problem(2, n_int, nl, theta_gamma=0.5, k0=k0, phi_kind=kind, rhs="gauss", seed=200 + i,
+                            bump_centre=(0.45, 0.55))
+        pc = hi.Precond(kind=pck, theta_beta=th, shift=1 + 0.5j + 0.1j * i, smoother=smoother, omega=0.5 + 0.05 * i)
+        out.append((p, pc))
+    return out
+
+
+@pytest.mark.parametrize("smoother", [hi.SM_JACOBI, hi.SM_RBGS])
+@pytest.mark.parametrize("mg", ["c64", "c128"])
+def test_group_equals_lone_solves(mg, smoother):
+    """helm_solve_group runs every kernel of an iteration as one launch over all instances; each
+    instance's solution, matvec count and residuals are bitwise its lone helm_solve's, and the group
+    issues far fewer launches than the instances would one by one."""
+    from paper_0912_0180_gb300.helm import Helm, solve_group
+    inst = _group_instances(smoother)
+    for autotune in (True, False):  # the tuner's tail depths and the rule's
+        hs = [Helm(p, pc, mg_dtype=mg, autotune=autotune) for p, pc in inst]
+        bs = [torch.from_numpy(p.b).cuda() for p, _ in inst]
+        alone = []
+        for h, b in zip(hs, bs):
+            x, info = h.solve(b, tol=1e-8, maxmv=3000)
+            alone.append((x.clone(), info))
+        xs, infos = solve_group(hs, bs, tol=1e-8, maxmv=3000)
+        for (xa, ia), xg, ig in zip(alone, xs, infos):
+            assert ia.status == 0 and ig.status == 0
+            assert torch.equal(xa, xg)
+            assert ia.matvecs == ig.matvecs and ia.iters == ig.iters
+            assert ia.rel_res_true == ig.rel_res_true and ia.rel_res_recur == ig.rel_res_recur
+        assert infos[0].kernels < sum(ia.kernels for _, ia in alone) / 2
+        # a second call on the same contexts gives the same results again
+        xs2, _ = solve_group(hs, bs, tol=1e-8, maxmv=3000)
+        assert all(torch.equal(a, b_) for a, b_ in zip(xs, xs2))
+        for h in hs:
+            h.close()
+
+
+def test_group_against_the_oracle_and_its_refusals():
+    """A group's FP64-multigrid solutions against the oracle's own solves; instances that the grouped
+    kernels do not cover are refused on the host."""
+    from paper_0912_0180_gb300.helm import Helm, HelmError, solve_group
+    inst = _group_instances(hi.SM_JACOBI)[:4]
+    hs = [Helm(p, pc, mg_dtype="c128") for p, pc in inst]
+    bs = [torch.from_numpy(p.b).cuda() for p, _ in inst]
+    xs, infos = solve_group(hs, bs, tol=1e-10, maxmv=3000)
+    for (p, pc), x, inf in zip(inst, xs, infos):
+        xo, io = Oracle(p, pc).solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
+        assert inf.status == 0 and io["status"] == 0
+        assert abs(inf.matvecs - io["matvecs"]) <= 2
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) < 1e-9
+    p3 = hi.make_problem(3, 15, 3, theta_gamma=0.5, k0=6.0, rhs="gauss", seed=3)
+    pc3 = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
+    bad = [Helm(p3, pc3, mg_dtype="c64"),
+           Helm(inst[0][0], hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_JACOBI, galerkin=True), mg_dtype="c64"),
+           Helm(inst[0][0], hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_JACOBI, nu1=2), mg_dtype="c64"),
+           Helm(inst[0][0], hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")]
+    for hb in bad:
+        with pytest.raises(HelmError):
+            solve_group([hs[0], hb], [bs[0], torch.from_numpy(hb.problem.b).cuda()], tol=1e-8)
+    with pytest.raises(HelmError):  # one smoother kind per group
+        hr = Helm(inst[1][0], hi.Precond(kind=hi.PC_CSL, shift=1 + 0.5j, smoother=hi.SM_RBGS), mg_dtype="c128")
+        solve_group([hs[0], hr], bs[:2], tol=1e-8)
+    for h in hs + bad:
+        h.close()

@@ -808,6 +808,89 @@ def test_sommerfeld_mg_preconditioned_solve_reaches_direct_solution():
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
 
 
+# ---- Sommerfeld condition on low sides (coarsening with offset 0 keeps node 0) -----------------
+
+def test_low_sommerfeld_row_is_consistent_with_the_outgoing_wave():
+    """At the low end the outgoing wave is e^{+i k x}: du/dn = -du/dx = -i k u there exactly.  The
+    ghost-node row leaves i k^3 h / 3 - k^4 h^2 / 12 + O(h^3), the interior rows the usual
+    O(k^4 h^2), on every level -- each coarse grid keeps node 0 and mirrors its first width."""
+    n_int, k = 97, 9.0
+    for nl in ((-1, 0), (-1, -1)):
+        p = _prob(1, n_int, nl, theta=0.5, k0=k, rhs="zero")
+        pc = hi.Precond(kind=hi.PC_CSL, shift=1.0, smoother=hi.SM_JACOBI, max_levels=4, coarse_max=2)
+        o = Oracle(p, pc)
+        assert o.nlev == 4
+        for lvl in range(o.nlev):
+            t = o.axis_tables(1, lvl, 0)
+            x = t["pos"]
+            h = float(np.real(t["gap"][1]))
+            assert x[0] == 0.0 and t["gap"][0] == t["gap"][1]  # boundary node kept, ghost mirrored
+            u = np.exp(1j * k * x)
+            r = o.apply(u, 1, lvl) / u
+            inner = (2 - 2 * np.cos(k * h)) / h ** 2 - k ** 2
+            last = -1 if nl[1] == 0 else -2
+            assert np.allclose(r[1:last], inner, atol=1e-9 * k ** 2)
+            lead = 1j * k ** 3 * h / 3 - k ** 4 * h ** 2 / 12
+            assert abs(r[0] - lead) <= 0.2 * k ** 5 * h ** 3 + 1e-9 * k ** 2
+
+
+def test_low_sommerfeld_is_the_mirror_of_the_high_side():
+    """Reversing an axis turns a grid with a Sommerfeld low side into one with a Sommerfeld high
+    side (layers and Dirichlet ends swapped too): the operator is J H J, and so are every level of
+    the multigrid hierarchy and the whole V-cycle -- coarsening with offset 0 from the low end
+    keeps exactly the reversed nodes that offset 1 keeps from the high end -- and the solves take
+    the same matvec counts."""
+    for shape in (((31,), ((-1, 5),)), ((33,), ((-1, 0),))):
+        (n_int,), ((lo, hi_),) = shape
+        p_lo = _prob(1, n_int, (lo, hi_), theta=0.5, k0=11.0, rhs="random", seed=3)
+        p_hi = _prob(1, n_int, (hi_, lo), theta=0.5, k0=11.0, rhs="random", seed=3)
+        # as deep as the high side coarsens (while its unknown count stays even); the low side
+        # alone could go on, keeping node 0 on odd counts too
+        pc = hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.6, coarse_max=3,
+                        max_levels=3)
+        o_lo, o_hi = Oracle(p_lo, pc), Oracle(p_hi, pc)
+        assert o_lo.nlev == o_hi.nlev == 3
+        for lvl in range(o_lo.nlev):
+            A_lo, A_hi = o_lo.dense(1, lvl), o_hi.dense(1, lvl)
+            assert np.abs(A_lo - A_hi[::-1, ::-1]).max() <= 1e-12 * np.abs(A_hi).max()
+        r = hi.random_vector(p_lo.n, 5)
+        z_lo, z_hi = o_lo.vcycle(r), o_hi.vcycle(r[::-1].copy())
+        assert np.abs(z_lo - z_hi[::-1]).max() <= 1e-11 * np.abs(z_hi).max()
+        b = hi.random_vector(p_lo.n, 6)
+        _, i_lo = o_lo.solve(b, hi.SolveOpts(tol=1e-9, maxmv=400))
+        _, i_hi = o_hi.solve(b[::-1].copy(), hi.SolveOpts(tol=1e-9, maxmv=400))
+        assert i_lo["status"] == 0 and abs(i_lo["matvecs"] - i_hi["matvecs"]) <= 2
+
+
+def test_four_sided_sommerfeld_symmetry_spectrum_and_solve():
+    """The paper's model problem 1 with Sommerfeld edges: all four sides.  W H is complex symmetric
+    with half cells at both ends of each axis, every eigenvalue lies in the upper half plane, and the
+    multigrid-preconditioned Bi-CGSTAB solve reaches the dense solution."""
+    p = _prob(2, (17, 19), ((-1, -1), (-1, -1)), theta=0.0, k0=6.0, rhs="random", seed=8)
+    o = Oracle(p)
+    w = []
+    for a in range(2):
+        g = o.axis_tables(0, 0, a)["gap"]
+        wa = (g[:-1] + g[1:]) / 2
+        wa[0] = g[1] / 2
+        wa[-1] = g[-2] / 2
+        w.append(wa)
+    W = np.multiply.outer(w[1], w[0]).ravel()
+    A = o.dense()
+    WA = W[:, None] * A
+    assert np.abs(WA - WA.T).max() <= 1e-12 * np.abs(WA).max()
+    lam = np.linalg.eigvals(A)
+    assert lam.imag.min() >= -1e-10 * np.abs(lam).max() and lam.imag.max() > 1.0
+    q = _prob(2, 65, ((-1, -1), (-1, -1)), theta=0.0, k0=12.0, rhs="point")
+    pc = hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5)
+    oq = Oracle(q, pc)
+    assert oq.nlev >= 4 and oq.level_shape(1, 1) == (33, 33)
+    x, info = oq.solve(q.b, hi.SolveOpts(tol=1e-11, maxmv=2000))
+    assert info["status"] == 0
+    xd = oq.dense_solve(q.b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
 # ---- 3D Galerkin coarse operators (27-point R A P) ---------------------------------------------
 
 def _stencil27_to_dense(st, n0, n1, n2):
