@@ -89,6 +89,7 @@ def run(args):
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
     fn = {"c1": run_c1, "3d160": run_3d, "3d160g": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+          "mp3b": run_mp, "mp3bsom": run_mp, "mp1": run_mp, "mp1som": run_mp,
           "mp2som": run_mp, "mp3som": run_mp,
           "select": run_select, "gmres": run_gmres}[args.workload]
     line = fn(args, torch, ranks, dev, local)
@@ -597,6 +598,26 @@ MP_CASES = {
     "mp3som": {"problem": lambda: hi.workload_mp3(n_l=-1), "csl": 1 - 0.38j, "csg": -np.pi / 17,
                "paper_matvecs": {"csl": {"bicgstab": 207, "idr4": 214, "idr8": 232},
                                  "csg": {"bicgstab": 205, "idr4": 207, "idr8": 207}}},
+    # MP3's second case of the paper's table: r = 150, k = 4 on 2048^2 interior nodes (+ 512 layer
+    # nodes on the east / north edges), ECS and Sommerfeld rows
+    "mp3b": {"problem": lambda: hi.workload_mp3(r=150.0, k=4.0, n_int=2049, n_l=512), "csl": 1 + 0.40j,
+             "csg": np.pi / 17,
+             "paper_matvecs": {"csl": {"bicgstab": 436, "idr4": 413, "idr8": 423},
+                               "csg": {"bicgstab": 390, "idr4": 387, "idr8": 392}}},
+    "mp3bsom": {"problem": lambda: hi.workload_mp3(r=150.0, k=4.0, n_int=2049, n_l=-1), "csl": 1 - 0.40j,
+                "csg": -np.pi / 17,
+                "paper_matvecs": {"csl": {"bicgstab": 681, "idr4": 682, "idr8": 669},
+                                  "csg": {"bicgstab": 620, "idr4": 650, "idr8": 652}}},
+    # MP1 (constant k = 160, centre point source, unit square), absorbing on all four edges: ECS
+    # layers of 64 nodes, or the first-order Sommerfeld condition on every edge -- two of them low
+    # sides, whose coarsening keeps node 0 and runs the per-component V-cycle with rediscretised
+    # levels (no Galerkin operators there)
+    "mp1": {"problem": lambda: hi.workload_mp1(), "csl": 1 + 0.2j, "csg": np.pi / 28,
+            "paper_matvecs": {"csl": {"bicgstab": 59, "idr4": 62, "idr8": 60},
+                              "csg": {"bicgstab": 58, "idr4": 62, "idr8": 56}}},
+    "mp1som": {"problem": lambda: hi.workload_mp1(n_l=-1), "csl": 1 - 0.2j, "csg": -np.pi / 28, "galerkin": False,
+               "paper_matvecs": {"csl": {"bicgstab": 79, "idr4": 72, "idr8": 76},
+                                 "csg": {"bicgstab": 74, "idr4": 70, "idr8": 72}}},
 }
 
 
@@ -611,9 +632,10 @@ def run_mp(args, torch, ranks, dev, local):
     b_dev = torch.from_numpy(p.b).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     solves = [(m, s, pcn) for pcn in ("csl", "csg") for (m, s) in (("bicgstab", 0), ("idr4", 4), ("idr8", 8))]
-    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], smoother=hi.SM_JACOBI, omega=0.5, galerkin=True),
+    gal = case.get("galerkin", True)
+    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], smoother=hi.SM_JACOBI, omega=0.5, galerkin=gal),
            "csg": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=case["csg"], smoother=hi.SM_JACOBI, omega=0.5,
-                             galerkin=True)}
+                             galerkin=gal)}
     methods = [hi.BICGSTAB if s == 0 else hi.IDR for (_, s, _) in solves]
     svals = [max(s, 1) for (_, s, _) in solves]
     shadows = [hi.shadow_space(p.n, s) if s else None for (_, s, _) in solves]
@@ -648,10 +670,13 @@ def run_mp(args, torch, ranks, dev, local):
     cfg = {"workload": p.name, "n_unknowns": p.n, "solves_per_step": ns,
            "solves": "{Bi-CGSTAB, IDR(4), IDR(8)} x {CSL shift %s, CSG theta_beta %.4f}, run at once"
                      % (case["csl"], case["csg"]),
-           "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, Galerkin coarse operators R A P",
-           "boundaries": "Dirichlet south / west, " + ("first-order Sommerfeld east / north"
+           "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, " + ("Galerkin coarse operators R A P" if gal else
+                                                                      "rediscretised coarse operators"),
+           "boundaries": (("first-order Sommerfeld on all four edges" if args.workload.endswith("som") else
+                           "ECS layers on all four edges (theta_gamma = pi/6)") if args.workload.startswith("mp1") else
+                          "Dirichlet south / west, " + ("first-order Sommerfeld east / north"
                                                         if args.workload.endswith("som") else
-                                                        "ECS layers east / north (theta_gamma = pi/6)"),
+                                                        "ECS layers east / north (theta_gamma = pi/6)")),
            "l2": "flushed (512 MiB device write) before every timed step"}
     line = _base(args, ranks.job_rate(done(res["c128"][1]), res["c128"][0]), res["c128"][0], ranks.world, cfg, "c128")
     line.update({

@@ -235,6 +235,17 @@ def workload_3d_128(seed: int = BASE_SEED) -> Problem:
                         name="3d-128cube-L16-k40-point")
 
 
+def workload_mp1(k: float = 160.0, n_int: int = 257, n_l: int = 64, theta_gamma: float = np.pi / 6) -> Problem:
+    """The paper's model problem 1 (Section 4, eq. "MP1"): constant k on the unit square with a unit
+    point source at the centre node, absorbing on all four edges -- ECS layers of n_l nodes per side
+    (theta_gamma = pi/6), or, with n_l = -1, the first-order Sommerfeld condition on every edge (the
+    boundary nodes are unknowns).  Defaults: k = 160 on 257 nodes per axis (h = 1/256, kh = 0.625,
+    the accuracy limit; the paper's 256 cell-centred points, its Table MP1)."""
+    tag = "-sommerfeld" if n_l < 0 else f"-L{n_l}"
+    return make_problem(2, n_int, n_l, theta_gamma=theta_gamma, k0=k, rhs="point",
+                        name=f"mp1-k{k:g}-{n_int - 1}sq{tag}")
+
+
 def workload_mp2(nu: float = 7.0, k: float = 2.0, n_int: int = 385, n_l: int = 128, r: float = 50.0,
                  theta_gamma: float = np.pi / 6, ecs_ramp: int = 0) -> Problem:
     """The paper's model problem 2 (Section 4, eq. "MP2"): phi = nu (e^{-x^2} + e^{-y^2}) + k^2,

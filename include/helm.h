@@ -61,13 +61,17 @@ enum { HELM_BICGSTAB = 0, HELM_IDR = 1, HELM_GMRES = 2 };
  * interior holds n_int[a] nodes at 0, h, ..., extent[a] (h = extent/(n_int-1)); a side with
  * n_layer[a][side] = m > 0 continues with m ECS nodes of width h e^{i theta_gamma} and a
  * Dirichlet node after them; a side with m = 0 is a Dirichlet wall (its end node is not an
- * unknown).  A HIGH side with m = -1 carries the first-order Sommerfeld condition du/dn = -i k u
- * (Section 2, eq. "sommerfeld1"; the paper's east / north edges of MP2 and MP3): its end node is
- * an unknown whose row takes a mirrored ghost node, u_g = u_{N-1} - 2 i k h u_N, with k =
- * sqrt(phi) >= 0 there (also in the preconditioner, whose shift or stretch applies as elsewhere);
- * coarsening then keeps that node and stops at the first level where such an axis has an odd
- * number of unknowns.  Unknowns per axis: n_int - 2 + (m_lo ? m_lo + 1 : 0) + (m_hi > 0 ? m_hi + 1
- * : m_hi < 0 ? 1 : 0).
+ * unknown).  A side with m = -1 carries the first-order Sommerfeld condition du/dn = -i k u
+ * (Section 2, eq. "sommerfeld1"; the paper's east / north edges of MP2 and MP3, all four edges of
+ * MP1's Sommerfeld rows): its end node is an unknown whose row takes a mirrored ghost node,
+ * u_g = u_{N-1} - 2 i k h u_N on a high side and u_g = u_1 - 2 i k h u_0 on a low side, with
+ * k = sqrt(phi) >= 0 there (also in the preconditioner, whose shift or stretch applies as
+ * elsewhere).  Coarsening keeps those nodes: coarse unknown c is fine unknown 2c + 1, or 2c on an
+ * axis with a Sommerfeld low side, and it stops at the first level where a Sommerfeld high side's
+ * node would not be kept (n - 1 - offset odd).  Levels coarsened with offset 0 run the
+ * one-kernel-per-component V-cycle and take no Galerkin operators (HELM_ERR_ARG).  Unknowns per
+ * axis: n_int - 2 + (m_lo > 0 ? m_lo + 1 : m_lo < 0 ? 1 : 0) + (m_hi > 0 ? m_hi + 1 : m_hi < 0 ? 1
+ * : 0).
  * ecs_ramp = R > 1 replaces the sharp turn by a gradual one (the smooth ECS transition of the
  * paper's remark in Section 7): the m-th layer width counted from the turning point (m = 1, 2,
  * ...) is h e^{i theta_gamma min(m, R) / R}, so the contour turns by theta_gamma / R per width over
@@ -75,7 +79,7 @@ enum { HELM_BICGSTAB = 0, HELM_IDR = 1, HELM_GMRES = 2 };
 typedef struct {
   int dim;              /* 1, 2 or 3 */
   int n_int[3];         /* >= 2 (>= 3 for a side without layer); unused axes ignored */
-  int n_layer[3][2];    /* low sides >= 0, high sides >= -1 (-1: Sommerfeld) */
+  int n_layer[3][2];    /* every side >= -1 (-1: Sommerfeld) */
   double extent[3];     /* > 0 */
   double theta_gamma;   /* ECS angle in radians, 0 <= theta_gamma < pi/2 */
   int ecs_ramp;         /* 0..1048576 */

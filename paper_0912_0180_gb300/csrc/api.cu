@@ -113,8 +113,8 @@ static helm_status check_grid(const helm_grid* g) {
   long total = 1;
   for (int a = 0; a < g->dim; ++a) {
     int lo = g->n_layer[a][0], hi = g->n_layer[a][1];
-    if (lo < 0 || hi < -1 || g->n_int[a] < 2 || !(g->extent[a] > 0.0) || !std::isfinite(g->extent[a])) {
-      set_error("invalid n_int / n_layer / extent (low sides >= 0, high sides >= -1)");
+    if (lo < -1 || hi < -1 || g->n_int[a] < 2 || !(g->extent[a] > 0.0) || !std::isfinite(g->extent[a])) {
+      set_error("invalid n_int / n_layer / extent (every side >= -1)");
       return HELM_ERR_ARG;
     }
     long n = axis_unknowns(g->n_int[a], lo, hi);
@@ -215,7 +215,16 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   cudaStream_t st = (cudaStream_t)stream;
   c->alloc_stream = st;
   bool somm = false;
-  for (int a = 0; a < grid->dim; ++a) somm = somm || grid->n_layer[a][1] < 0;
+  bool somm_lo = false;
+  for (int a = 0; a < grid->dim; ++a) {
+    somm = somm || grid->n_layer[a][1] < 0 || grid->n_layer[a][0] < 0;
+    somm_lo = somm_lo || grid->n_layer[a][0] < 0;
+  }
+  if (somm_lo && (pc->flags & HELM_PF_GALERKIN) && pc->kind != HELM_PC_NONE) {
+    delete c;
+    set_error("Galerkin coarse operators are not built for a grid with a Sommerfeld low side");
+    return HELM_ERR_ARG;
+  }
   if (k->phi_im && !k->phi) { delete c; set_error("phi_im needs phi"); return HELM_ERR_ARG; }
   if (!k->phi) {
     bool ok = k->kind == HELM_K_CONST ||

@@ -45,6 +45,7 @@ const char* group_refusal(const helm_ctx* c, const helm_ctx* c0, int dev) {
   if (c->pc.nu1 != 1 || c->pc.nu2 != 1) return "grouped solves run V(1,1) cycles";
   if (c->pc.flags & (HELM_PF_UNFUSED | HELM_PF_GALERKIN)) return "grouped solves need the fused rediscretised levels";
   if (c->fdm.on) return "grouped solves need a dense coarsest inverse";
+  if (!c->lv.empty() && c->lv[0].any_offset0()) return "grouped solves do not take Sommerfeld low sides";
   if ((int)c->lv.size() < 2 && c->tail_first > 0) return "grouped solves need at least two levels";
   if (c->pc.smoother != c0->pc.smoother) return "the instances of a group share one smoother kind";
   if (c->pc.mg_dtype != c0->pc.mg_dtype) return "the instances of a group share one multigrid precision";

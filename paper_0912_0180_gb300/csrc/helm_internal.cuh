@@ -81,8 +81,10 @@ template <typename T> struct OpView {
                       // k = 3 (dj + 1) + (di + 1) in 2D (9 weights) and k = 9 (dl + 1) + 3 (dj + 1)
                       // + (di + 1) in 3D (27); nullptr for a Shortley-Weller level
   long ntot;
-  int somm;           // bit a: the last unknown of axis a is a Sommerfeld boundary node
-  double2 bt[3];      // its boundary weight 2i / h_l (the diagonal gains bt * sqrt(phi))
+  int somm;           // bit a: the last unknown of axis a is a Sommerfeld boundary node; bit a + 3:
+                      // the first one is (a low side)
+  double2 bt[3];      // the last node's boundary weight 2i / h_l (the diagonal gains bt * sqrt(phi))
+  double2 btl[3];     // the first node's, 2i / h_r
   const double* phim; // imaginary part of phi (k at complex node positions; zero in the uniform
                       // interior) or nullptr
 };
@@ -94,26 +96,32 @@ inline __host__ __device__ double2 sigma64(const OpView<double>& op, long p, dou
 }
 
 // Sommerfeld boundary part of the diagonal at (i, j, l) (Section 2, eq. "sommerfeld1", by a
-// mirrored ghost node): sum over the axes whose last unknown this is of 2 i k / h_l, with
-// k = sqrt(phi) the unshifted wave number.  FP64; zero away from such nodes.
+// mirrored ghost node): sum over the axes whose last (or, on a low side, first) unknown this is of
+// 2 i k / h, with k = sqrt(phi) the unshifted wave number.  FP64; zero away from such nodes.
 template <typename T>
 __host__ __device__ inline double2 somm_diag(const OpView<T>& op, int i, int j, int l, double ph) {
   double2 d = {0.0, 0.0};
   if (!op.somm) return d;
   const int idx[3] = {i, j, l};
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) {
     if (((op.somm >> a) & 1) && idx[a] == op.n[a] - 1) {
       const double k = sqrt(ph);
       d.x += op.bt[a].x * k;
       d.y += op.bt[a].y * k;
     }
+    if (((op.somm >> (a + 3)) & 1) && idx[a] == 0) {
+      const double k = sqrt(ph);
+      d.x += op.btl[a].x * k;
+      d.y += op.btl[a].y * k;
+    }
+  }
   return d;
 }
 
 // Unknowns along one axis: interior nodes minus Dirichlet walls, plus m + 1 per ECS layer of m
-// nodes, plus the boundary node of a Sommerfeld high side (hi = -1).
+// nodes, plus the boundary node of each Sommerfeld side (-1).
 inline long axis_unknowns(int n_int, int lo, int hi) {
-  return (long)n_int - 2 + (lo > 0 ? lo + 1 : 0) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
+  return (long)n_int - 2 + (lo > 0 ? lo + 1 : (lo < 0 ? 1 : 0)) + (hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0));
 }
 
 // ---- owned device storage of one level ---------------------------------------------------
@@ -143,9 +151,14 @@ struct LevelHost {
   // copy for FP32 multigrid
   double2* stg64 = nullptr;
   float2* stg32 = nullptr;
-  // Sommerfeld high sides: bit a set when the last unknown of axis a is the boundary node
+  // Sommerfeld sides: bit a set when the last unknown of axis a is the boundary node, bit a + 3 when
+  // the first one is (a low side: that axis coarsens with offset 0, keeping node 0)
   int somm = 0;
   double2 bt[3] = {};
+  double2 btl[3] = {};
+  // coarsening offset of axis a: coarse unknown c is fine unknown 2c + offset(a)
+  int offset(int a) const { return ((somm >> (a + 3)) & 1) ? 0 : 1; }
+  bool any_offset0() const { return (somm >> 3) != 0; }
   double* phim64 = nullptr;  // imaginary part of phi (FP64), nullptr when phi is real
   // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, 2 one warp, 3 square, -1 by the
   // block-count rule

@@ -266,10 +266,12 @@ __global__ void k_resid0_27(OpView<T> op, const cx<T>* __restrict__ u, const cx<
   r[p] = mkc<T>(fma(om1, fv.x, -acc.x), fma(om1, fv.y, -acc.y));
 }
 
-struct Dims { int f[3]; int c[3]; };
+// fine and coarse unknowns per axis, and the coarsening offsets (coarse c is fine 2c + o[a]:
+// o = 1, or 0 on an axis with a Sommerfeld low side)
+struct Dims { int f[3]; int c[3]; int o[3]; };
 
-// Full weighting in index space: coarse unknown c gathers fine unknowns 2c, 2c+1, 2c+2 per
-// axis with weights 1/4, 1/2, 1/4 (tensor product); indices past the grid are Dirichlet.  The
+// Full weighting in index space: coarse unknown c gathers fine unknowns 2c+o-1, 2c+o, 2c+o+1 per
+// axis with weights 1/4, 1/2, 1/4 (tensor product); indices outside the grid are Dirichlet.  The
 // weights are applied one axis at a time, (a + c) + 2 b, and the factor 4^-DIM once at the end.
 template <typename T, int DIM>
 __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restrict__ fc, const int* skip) {
@@ -283,32 +285,39 @@ __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restric
   auto w3 = [](cx<T> a, cx<T> b, cx<T> c) {
     return mkc<T>(fma(T(2), b.x, a.x + c.x), fma(T(2), b.y, a.y + c.y));
   };
-  const int fi = 2 * I;  // fine 2I .. 2I+2; 2I+2 may lie past a ragged edge
+  // fine fi .. fi+2 along x: fi = -1 (offset 0, first coarse node) and fi + 2 past a ragged edge
+  // are outside the grid
+  const int fi = 2 * I + d.o[0] - 1;
   auto row_sum = [&](int fj, int fl) -> cx<T> {
-    if ((DIM > 1 && fj >= d.f[1]) || (DIM > 2 && fl >= d.f[2])) return zero;
+    if ((DIM > 1 && (fj < 0 || fj >= d.f[1])) || (DIM > 2 && (fl < 0 || fl >= d.f[2]))) return zero;
     const cx<T>* row = r + (long)d.f[0] * (fj + (long)d.f[1] * fl);
-    return w3(row[fi], row[fi + 1], fi + 2 < d.f[0] ? row[fi + 2] : zero);
+    return w3(fi >= 0 ? row[fi] : zero, row[fi + 1], fi + 2 < d.f[0] ? row[fi + 2] : zero);
   };
   auto plane_sum = [&](int fl) -> cx<T> {
     if (DIM == 1) return row_sum(0, 0);
-    const int fj = 2 * J;
+    const int fj = 2 * J + d.o[1] - 1;
     return w3(row_sum(fj, fl), row_sum(fj + 1, fl), row_sum(fj + 2, fl));
   };
   cx<T> acc;
   if (DIM < 3) acc = plane_sum(0);
-  else acc = w3(plane_sum(2 * L), plane_sum(2 * L + 1), plane_sum(2 * L + 2));
+  else {
+    const int fl = 2 * L + d.o[2] - 1;
+    acc = w3(plane_sum(fl), plane_sum(fl + 1), plane_sum(fl + 2));
+  }
   const T sc = DIM == 1 ? T(0.25) : (DIM == 2 ? T(0.0625) : T(0.015625));
   fc[I + (long)d.c[0] * (J + (long)d.c[1] * L)] = cscale<T>(sc, acc);
 }
 
-// Linear interpolation along one axis: an odd fine index i takes coarse node (i - 1) / 2 with
-// weight 1, an even one the coarse nodes i/2 - 1 and i/2 with weight 1/2 each (nodes outside
-// the coarse grid are Dirichlet zeros).  Returns the count of coarse nodes and their indices.
-__device__ __forceinline__ int interp1(int i, int nc, int* ci) {
-  if (i & 1) { ci[0] = (i - 1) >> 1; return 1; }
+// Linear interpolation along one axis: fine index i = 2c + o is coarse node c (weight 1); one
+// between two coarse nodes takes both with weight 1/2 (nodes outside the coarse grid are
+// Dirichlet zeros).  Returns the count of coarse nodes and their indices.
+__device__ __forceinline__ int interp1(int i, int nc, int o, int* ci) {
+  const int r = i - o;
+  if (r >= 0 && !(r & 1)) { ci[0] = r >> 1; return 1; }
   int k = 0;
-  if ((i >> 1) - 1 >= 0) ci[k++] = (i >> 1) - 1;
-  if ((i >> 1) < nc) ci[k++] = i >> 1;
+  const int left = (r - 1) >> 1, right = (r + 1) >> 1;  // r odd or -1
+  if (left >= 0 && left < nc) ci[k++] = left;
+  if (right >= 0 && right < nc) ci[k++] = right;
   return k;
 }
 
@@ -324,12 +333,13 @@ __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restric
   int l = blockIdx.z;
   if (i >= d.f[0] || j >= d.f[1]) return;
   int ci[2], cj[2] = {0, 0}, cl[2] = {0, 0};
-  int ni = interp1(i, d.c[0], ci);
-  int nj = DIM > 1 ? interp1(j, d.c[1], cj) : 1;
-  int nl = DIM > 2 ? interp1(l, d.c[2], cl) : 1;
-  T w = (i & 1) ? T(1) : T(0.5);
-  if (DIM > 1 && !(j & 1)) w *= T(0.5);
-  if (DIM > 2 && !(l & 1)) w *= T(0.5);
+  int ni = interp1(i, d.c[0], d.o[0], ci);
+  int nj = DIM > 1 ? interp1(j, d.c[1], d.o[1], cj) : 1;
+  int nl = DIM > 2 ? interp1(l, d.c[2], d.o[2], cl) : 1;
+  auto on_coarse = [](int x, int o) { return x - o >= 0 && !((x - o) & 1); };
+  T w = on_coarse(i, d.o[0]) ? T(1) : T(0.5);
+  if (DIM > 1 && !on_coarse(j, d.o[1])) w *= T(0.5);
+  if (DIM > 2 && !on_coarse(l, d.o[2])) w *= T(0.5);
   cx<T> acc = mkc<T>(T(0), T(0));
   for (int c3 = 0; c3 < nl; ++c3)
     for (int c2 = 0; c2 < nj; ++c2) {
@@ -428,12 +438,12 @@ template <typename T, int DIM> struct Launch {
     }
   }
   static void restrict_(const LevelHost& F, const LevelHost& C, const cx<T>* r, cx<T>* fc, const int* skip, cudaStream_t st) {
-    Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; }
+    Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
     dim3 g, b; cfg<DIM>(C.n, g, b);
     launch_pdl(k_restrict<T, DIM>, dim3(g), dim3(b), 0, st, d, r, fc, skip);
   }
   static void prolong(const LevelHost& F, const LevelHost& C, const cx<T>* ec, cx<T>* u, int overwrite, const int* skip, cudaStream_t st) {
-    Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; }
+    Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
     dim3 g, b; cfg<DIM>(F.n, g, b);
     launch_pdl(k_prolong<T, DIM>, dim3(g), dim3(b), 0, st, d, ec, u, overwrite, skip);
   }
@@ -514,6 +524,7 @@ static bool fused_applies(const helm_ctx* c, int l) {
   const helm_precond& pcf = c->pc;
   if (pcf.flags & HELM_PF_UNFUSED) return false;
   if (c->lv[l].stg64) return false;  // 9-point Galerkin levels run the per-component kernels
+  if (c->lv[l].any_offset0()) return false;  // the fused tiles assume coarse c = fine 2c + 1
   if (l >= c->tail_first) return true;
   return c->lv[l].dim == 2 && pcf.nu1 == 1 && pcf.nu2 == 1 && l < (int)c->lv.size() - 1;
 }
@@ -614,7 +625,8 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
     case HELM_OP_PROLONG: if (lvl >= nl - 1 || !A || !B) return HELM_ERR_ARG; prolong_any<T>(L, c->lv[lvl + 1], B, A, 0, nullptr, st); break;
     case HELM_OP_COARSE: if (lvl != nl - 1 || !A || !O) return HELM_ERR_ARG; coarse_solve<T>(c, A, O, nullptr, st); break;
     case HELM_OP_DOWN:
-      if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || L.stg64 || !A || !B || !O) return HELM_ERR_ARG;
+      if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || L.stg64 || L.any_offset0() || !A || !B || !O)
+        return HELM_ERR_ARG;
       fused_down2d<T>(c, lvl, B, A, O, nullptr, st);
       break;
     default: return HELM_ERR_ARG;

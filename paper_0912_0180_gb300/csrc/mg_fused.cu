@@ -505,6 +505,7 @@ constexpr size_t TAIL_INVERSE_BYTES = 1 << 20;
 template <typename T> int tail_first_level(const helm_ctx* c, long point_budget) {
   int nl = (int)c->lv.size();
   if (c->fdm.on) return nl;  // the one-block tail needs the dense coarsest inverse
+  if (c->lv[0].any_offset0()) return nl;  // ... and coarsens with offset 1
   if (c->lv[nl - 1].stg64) return nl;  // ... and runs 5-point rows only
   long pts = c->lv[nl - 1].ntot;
   size_t bytes = TAIL_VECS * sizeof(cx<T>) * c->lv[nl - 1].ntot;
@@ -1060,7 +1061,8 @@ template <typename T, bool RB>
 static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
   int nl = (int)c->lv.size();
   if (nl < 2) return HELM_OK;
-  const bool fused2d = c->lv[0].dim == 2 && c->pc.nu1 == 1 && c->pc.nu2 == 1;
+  // levels coarsened with offset 0 (a Sommerfeld low side) run the per-component kernels only
+  const bool fused2d = c->lv[0].dim == 2 && c->pc.nu1 == 1 && c->pc.nu2 == 1 && !c->lv[0].any_offset0();
   // 1. tiles of every level that can run the fused 2D kernels
   std::vector<int> todo;
   {

@@ -18,12 +18,14 @@ namespace helm {
 // One thread per width: interior widths are h * scale_in; layer widths (the first nlo and the
 // last ones) are h e^{i theta_gamma} * scale_ly, except, with a ramp of R > 1 widths, the m-th
 // layer width from the turning point for m < R, which turns by only theta_gamma * m / R.
+// somm: bit 0 a Sommerfeld high side, bit 1 a Sommerfeld low side (its ghost width is width 0).
 __global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_layer,
                             double2 w_int, int ramp, double h, double theta_g, double2 scale_ly,
                             int somm) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ngap) return;
-  if ((j >= nlo && j < nlo + nin) || (somm && j == ngap - 1)) {  // a Sommerfeld ghost mirrors h
+  if ((j >= nlo && j < nlo + nin) || ((somm & 1) && j == ngap - 1) || ((somm & 2) && j == 0)) {
+    // interior widths; a Sommerfeld ghost mirrors h
     gap[j] = w_int;
     return;
   }
@@ -36,19 +38,26 @@ __global__ void k_axis_gaps(double2* gap, int ngap, int nlo, int nin, double2 w_
   }
 }
 
-// coarse width c = fine widths 2c and 2c+1; the last coarse width reaches the fine Dirichlet
-// node and gathers the remaining one or two fine widths.
+// Coarse unknown c is fine unknown 2c + o (o = 1; o = 0 on an axis with a Sommerfeld low side, so
+// that its boundary node 0 stays a node).  Coarse width c (c >= 1, or c = 0 with o = 1) spans the
+// fine widths 2c+o-1 and 2c+o; with o = 0 width 0 leads to the low ghost and mirrors width 1.  The
+// last coarse width reaches the fine Dirichlet node and gathers the remaining fine widths, or, on
+// a Sommerfeld high side (whose boundary node n-1 is then a coarse node), mirrors the last coarse
+// width.  somm: bit 0 high side, bit 1 low side.  The hierarchy coarsens only axes of >= 3
+// unknowns, so nc >= 2 when o = 0.
 __global__ void k_axis_coarsen(const double2* __restrict__ gf, int nf, double2* __restrict__ gc,
                                int nc, int somm) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c > nc) return;
+  const int o = (somm & 2) ? 0 : 1;
   if (c < nc) {
-    gc[c] = cadd<double>(gf[2 * c], gf[2 * c + 1]);
-  } else if (somm) {  // the ghost width mirrors the last coarse width (nf even: 2nc = nf)
-    gc[c] = cadd<double>(gf[2 * c - 2], gf[2 * c - 1]);
+    const int ci = (o == 0 && c == 0) ? 1 : c;
+    gc[c] = cadd<double>(gf[2 * ci + o - 1], gf[2 * ci + o]);
+  } else if (somm & 1) {
+    gc[c] = cadd<double>(gf[2 * (nc - 1) + o - 1], gf[2 * (nc - 1) + o]);
   } else {
     double2 acc = mkc<double>(0.0, 0.0);
-    for (int j = 2 * nc; j <= nf; ++j) acc = cadd<double>(acc, gf[j]);
+    for (int j = 2 * (nc - 1) + o + 1; j <= nf; ++j) acc = cadd<double>(acc, gf[j]);
     gc[c] = acc;
   }
 }
@@ -71,9 +80,13 @@ __global__ void k_axis_coeffs(const double2* __restrict__ gap, int n, double2* a
   am[j] = mkc<double>(-m.x, -m.y);
   a0[j] = c;
   ap[j] = mkc<double>(-p.x, -p.y);
-  if (somm && j == n - 1) {
+  if ((somm & 1) && j == n - 1) {
     am[j] = mkc<double>(-2.0 * m.x, -2.0 * m.y);
     ap[j] = mkc<double>(0.0, 0.0);
+  }
+  if ((somm & 2) && j == 0) {  // low side: the ghost u_g = u_1 - 2 i k h_r u_0 mirrors the other way
+    ap[j] = mkc<double>(-2.0 * p.x, -2.0 * p.y);
+    am[j] = mkc<double>(0.0, 0.0);
   }
   if (am32) {
     am32[j] = cconv<float, double>(am[j]);
@@ -82,10 +95,11 @@ __global__ void k_axis_coeffs(const double2* __restrict__ gap, int n, double2* a
   }
 }
 
-// phi on the coarse level: value of the fine node that coincides with the coarse node.
+// phi on the coarse level: value of the fine node that coincides with the coarse node (fine
+// index 2c + o per axis, o = offs bit clear ? 1 : 0 -- bit a set: offset 0 on axis a).
 __global__ void k_phi_inject(const double* __restrict__ pf, int f0, int f1, int dim,
                              double* __restrict__ pc, float* __restrict__ pc32, int c0, int c1,
-                             int c2) {
+                             int c2, int offs) {
   long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long nc = (long)c0 * c1 * c2;
   if (p >= nc) return;
@@ -93,7 +107,8 @@ __global__ void k_phi_inject(const double* __restrict__ pf, int f0, int f1, int 
   long q = p / c0;
   int j = (int)(q % c1);
   int l = (int)(q / c1);
-  int fi = 2 * i + 1, fj = dim > 1 ? 2 * j + 1 : 0, fl = dim > 2 ? 2 * l + 1 : 0;
+  const int o0 = (offs & 1) ? 0 : 1, o1 = (offs & 2) ? 0 : 1, o2 = (offs & 4) ? 0 : 1;
+  int fi = 2 * i + o0, fj = dim > 1 ? 2 * j + o1 : 0, fl = dim > 2 ? 2 * l + o2 : 0;
   double v = pf[fi + (long)f0 * (fj + (long)f1 * fl)];
   pc[p] = v;
   if (pc32) pc32[p] = (float)v;
@@ -537,8 +552,9 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
   for (int a = 0; a < 3; ++a) L.n[a] = 1;
   for (int a = 0; a < g.dim; ++a) {
     int lo = g.n_layer[a][0], hi = g.n_layer[a][1];
-    const int somm = hi < 0;  // Sommerfeld high side: one mirrored width to the ghost node
-    int nlo = lo > 0 ? lo + 1 : 0, nhi = hi > 0 ? hi + 1 : (somm ? 1 : 0);
+    // Sommerfeld sides (bit 0 high, bit 1 low): one mirrored width each, to the ghost node
+    const int somm = (hi < 0 ? 1 : 0) | (lo < 0 ? 2 : 0);
+    int nlo = lo > 0 ? lo + 1 : (lo < 0 ? 1 : 0), nhi = hi > 0 ? hi + 1 : (hi < 0 ? 1 : 0);
     int nin = g.n_int[a] - 1;
     int ngap = nlo + nin + nhi;
     int n = ngap - 1;
@@ -557,9 +573,13 @@ static helm_status build_axes(helm_ctx* c, LevelHost& L, double2 scale_in, doubl
     k_axis_coeffs<<<ceil_div(n, 256), 256, 0, st>>>(L.gap[a], n, L.coef64[a][0], L.coef64[a][1],
                                                     L.coef64[a][2], L.coef32[a][0], L.coef32[a][1],
                                                     L.coef32[a][2], somm);
-    if (somm) {  // boundary weight 2i / h_l, h_l = the last (interior) width
+    if (somm & 1) {  // boundary weight 2i / h_l, h_l = the last (interior) width
       L.somm |= 1 << a;
       L.bt[a] = cdiv<double>(mkc<double>(0.0, 2.0), wi);
+    }
+    if (somm & 2) {  // boundary weight 2i / h_r, h_r = the first (interior) width
+      L.somm |= 8 << a;
+      L.btl[a] = cdiv<double>(mkc<double>(0.0, 2.0), wi);
     }
     HELM_CUDA(cudaGetLastError());
     L.n[a] = n;
@@ -662,7 +682,10 @@ template <typename T> OpView<T> LevelHost::view() const {
   v.stg = std::is_same<T, double>::value ? (const cx<T>*)(const void*)stg64 : (const cx<T>*)(const void*)stg32;
   v.ntot = ntot;
   v.somm = somm;
-  for (int a = 0; a < 3; ++a) v.bt[a] = bt[a];
+  for (int a = 0; a < 3; ++a) {
+    v.bt[a] = bt[a];
+    v.btl[a] = btl[a];
+  }
   v.phim = phim64;
   return v;
 }
@@ -685,7 +708,8 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
     BumpAxes ax{};
     for (int a = 0; a < 3; ++a) {
       ax.n[a] = H.n[a];
-      ax.off[a] = c->grid.n_layer[a][0] > 0 ? c->grid.n_layer[a][0] : -1;
+      const int lo = c->grid.n_layer[a][0];
+      ax.off[a] = lo > 0 ? lo : (lo < 0 ? 0 : -1);  // index of the unknown at x = 0
       ax.h[a] = c->grid.extent[a] / (c->grid.n_int[a] - 1);
       ax.c[a] = k->centre[a];
     }
@@ -756,18 +780,19 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       if (F.n[a] > pc.coarse_max) all_small = false;
       if (F.n[a] < min_n) min_n = F.n[a];
     }
-    // a Sommerfeld axis keeps its boundary node (fine 2c+1 = n-1) only when n is even
+    // a Sommerfeld high side keeps its boundary node (fine 2c+o = n-1) only when n-1-o is even
     bool odd_somm = false;
     for (int a = 0; a < F.dim; ++a)
-      if (((F.somm >> a) & 1) && (F.n[a] & 1)) odd_somm = true;
+      if (((F.somm >> a) & 1) && ((F.n[a] - 1 - F.offset(a)) & 1)) odd_somm = true;
     if (all_small || min_n < 3 || odd_somm) break;
     LevelHost C;
     C.dim = F.dim;
     C.ntot = 1;
     C.somm = F.somm;
     for (int a = 0; a < F.dim; ++a) {
-      int nf = F.n[a], nc = nf / 2;
-      const int somm = (F.somm >> a) & 1;
+      const int o = F.offset(a);
+      int nf = F.n[a], nc = o ? nf / 2 : (nf + 1) / 2;
+      const int somm = ((F.somm >> a) & 1) | (((F.somm >> (a + 3)) & 1) << 1);
       if ((rc = ctx_alloc(c, (void**)&C.gap[a], sizeof(double2) * (nc + 1))) != HELM_OK) return rc;
       for (int k = 0; k < 3; ++k) {
         if ((rc = ctx_alloc(c, (void**)&C.coef64[a][k], sizeof(double2) * nc)) != HELM_OK) return rc;
@@ -778,7 +803,8 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
                                                        C.coef64[a][2], C.coef32[a][0],
                                                        C.coef32[a][1], C.coef32[a][2], somm);
       // the last coarse width is the sum of the two last fine ones, both h_l: 2i / (2 h_l)
-      C.bt[a] = somm ? mkc<double>(0.5 * F.bt[a].x, 0.5 * F.bt[a].y) : mkc<double>(0.0, 0.0);
+      C.bt[a] = (somm & 1) ? mkc<double>(0.5 * F.bt[a].x, 0.5 * F.bt[a].y) : mkc<double>(0.0, 0.0);
+      C.btl[a] = (somm & 2) ? mkc<double>(0.5 * F.btl[a].x, 0.5 * F.btl[a].y) : mkc<double>(0.0, 0.0);
       C.n[a] = nc;
       C.ntot *= nc;
     }
@@ -788,12 +814,12 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       if ((rc = ctx_alloc(c, (void**)&C.phi64, sizeof(double) * C.ntot)) != HELM_OK) return rc;
       if (f32 && (rc = ctx_alloc(c, (void**)&C.phi32, sizeof(float) * C.ntot)) != HELM_OK) return rc;
       k_phi_inject<<<ceil_div(C.ntot, 256), 256, 0, st>>>(F.phi64, F.n[0], F.n[1], F.dim, C.phi64,
-                                                          C.phi32, C.n[0], C.n[1], C.n[2]);
+                                                          C.phi32, C.n[0], C.n[1], C.n[2], F.somm >> 3);
     }
     if (F.phim64) {  // the imaginary part is injected like the real part
       if ((rc = ctx_alloc(c, (void**)&C.phim64, sizeof(double) * C.ntot)) != HELM_OK) return rc;
       k_phi_inject<<<ceil_div(C.ntot, 256), 256, 0, st>>>(F.phim64, F.n[0], F.n[1], F.dim, C.phim64,
-                                                          nullptr, C.n[0], C.n[1], C.n[2]);
+                                                          nullptr, C.n[0], C.n[1], C.n[2], F.somm >> 3);
     }
     HELM_CUDA(cudaGetLastError());
     if ((rc = find_uniform(C, st)) != HELM_OK) return rc;
@@ -848,7 +874,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
   // constant phi on a large coarsest level: the separable exact solve, no dense inverse
-  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.stg64 && !Cst.somm) {
+  if (Cst.ntot > FDM_MIN_UNKNOWNS && !Cst.phi64 && !Cst.stg64 && !Cst.somm) {  // (somm: either side)
     if ((rc = fdm_build(c, Cst, f32, st)) != HELM_OK) return rc;
     if (c->fdm.on) {
       c->nco = 0;

@@ -46,7 +46,7 @@ def test_status_strings_and_argument_errors_without_gpu():
 
 
 def test_argument_errors_of_the_newer_entry_points_without_gpu():
-    """Sommerfeld low sides, a bad ramp, GMRES restart lengths and the parameter choice's
+    """A side below -1, a bad ramp, GMRES restart lengths and the parameter choice's
     arguments are refused on the host (no device is touched)."""
     import helm_inputs as hi
     import paper_0912_0180_gb300 as P
@@ -54,7 +54,7 @@ def test_argument_errors_of_the_newer_entry_points_without_gpu():
     from paper_0912_0180_gb300.helm import _grid, _kspec, _precond
     lib = P.load()
     out = ctypes.c_void_p()
-    p = hi.make_problem(2, 17, ((-1, 0), (0, 0)), k0=3.0, rhs="zero")  # Sommerfeld on a low side
+    p = hi.make_problem(2, 17, ((-2, 0), (0, 0)), k0=3.0, rhs="zero")  # a side below -1
     k, keep = _kspec(p)
     pc = _precond(hi.Precond(kind=hi.PC_NONE), "c128")
     assert lib.helm_create(ctypes.byref(_grid(p)), ctypes.byref(k), ctypes.byref(pc), None, ctypes.byref(out)) \

@@ -718,6 +718,14 @@ SOMM_CASES = [
     (2, (65, 33), ((0, -1), (7, 0)), 0.4, 14.0, "const"),                 # 64 x 39
     (3, (13, 14, 12), ((0, -1), (2, -1), (0, 0)), 0.5, 5.0, "bump"),      # 12 x 16 x 10
 ]
+# Sommerfeld low sides (n_layer = -1 on a low side; MP1's edges): the axis coarsens with offset 0,
+# keeping node 0; both sides on one axis (odd counts), low side with layers on the high side, 3D
+SOMM_LO_CASES = [
+    (1, 49, (-1, 6), 0.5, 9.0, "bump"),                                    # 55 unknowns
+    (2, (45, 49), ((-1, -1), (-1, 0)), 0.5, 12.0, "bump"),                 # 45 x 48
+    (2, (33, 40), ((-1, 4), (6, -1)), 0.4, 11.0, "const"),                 # 37 x 46
+    (3, (13, 13, 12), ((-1, -1), (2, 0), (-1, 2)), 0.5, 5.0, "bump"),      # 13 x 14 x 14
+]
 SOMM_PCS = [
     hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5),
     hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=-0.3, smoother=hi.SM_RBGS),
@@ -726,7 +734,7 @@ SOMM_PCS = [
 
 @pytest.mark.parametrize("mg", ["c128", "c64"])
 @pytest.mark.parametrize("pci", range(len(SOMM_PCS)))
-@pytest.mark.parametrize("case", SOMM_CASES)
+@pytest.mark.parametrize("case", SOMM_CASES + SOMM_LO_CASES)
 def test_sommerfeld_operator_levels_and_vcycle(case, pci, mg):
     """The Sommerfeld boundary rows: H itself, every level's operator (the ghost-node row with its
     2 i k / h_l diagonal on each coarse grid), the smoother, and the whole V-cycle, fused and
@@ -770,7 +778,7 @@ def test_sommerfeld_operator_levels_and_vcycle(case, pci, mg):
 
 
 @pytest.mark.parametrize("method", [hi.BICGSTAB, hi.IDR, hi.GMRES])
-@pytest.mark.parametrize("case", SOMM_CASES[1:3])
+@pytest.mark.parametrize("case", SOMM_CASES[1:3] + SOMM_LO_CASES[1:3])
 def test_sommerfeld_solve_matches_oracle(case, method):
     """FP64 solves of Sommerfeld problems against the oracle (matvecs within 2, solution to 1e-9),
     the FP32-multigrid path certified by its FP64 true residual, and Galerkin coarse operators
@@ -791,7 +799,7 @@ def test_sommerfeld_solve_matches_oracle(case, method):
     x3, i3 = h32.solve(cu(p.b), method=method, s=s, tol=1e-7, maxmv=3000, shadow=sh)
     assert i3.status == 0 and i3.rel_res_true < 1e-7
     h32.close()
-    if method == hi.BICGSTAB:
+    if method == hi.BICGSTAB and min(lo for lo, _ in p.n_layer[: p.dim]) >= 0:  # Galerkin: no low sides
         pg = hi.Precond(kind=hi.PC_CSL, shift=1 - 0.5j, smoother=hi.SM_JACOBI, omega=0.5, galerkin=True)
         og = Oracle(p, pg)
         hg = Helm(p, pg, mg_dtype="c128")
@@ -807,11 +815,13 @@ def test_sommerfeld_solve_matches_oracle(case, method):
 
 
 def test_sommerfeld_arguments():
-    """A Sommerfeld low side and a negative phi at a Sommerfeld grid are refused."""
+    """A side below -1, Galerkin operators with a Sommerfeld low side, and a negative phi at a
+    Sommerfeld grid are refused."""
     from paper_0912_0180_gb300.helm import HelmError
     p = hi.make_problem(2, 17, ((-1, 0), (0, 0)), k0=3.0, rhs="zero")
+    Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128").close()
     with pytest.raises(HelmError):
-        Helm(p, hi.Precond(kind=hi.PC_NONE), mg_dtype="c128")
+        Helm(p, hi.Precond(kind=hi.PC_CSL, smoother=hi.SM_JACOBI, galerkin=True), mg_dtype="c128")
     q = hi.make_problem(2, 17, ((0, -1), (0, 0)), k0=3.0, rhs="zero")
     q.phi = np.full(q.n, -1.0)
     with pytest.raises(HelmError):
