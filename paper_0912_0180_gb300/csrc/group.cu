@@ -14,6 +14,116 @@
 
 namespace helm {
 
+// ---- work-list compaction --------------------------------------------------------------------
+
+// The WHILE condition of the grouped loop (any instance running), the instances the work lists
+// should hold (`listed`) and whether that changed (`changed`).  At the end of the body it also
+// counts the group's bodies and, like the single-instance loop, ends a loop that ran more bodies
+// than the matvec cap allows (HELM_ERR_TIMEOUT for the instances still running); an instance that
+// ended on a half step had x += alpha p^ applied in this body, and no later body applies it again.
+__global__ void kg_cond(cudaGraphConditionalHandle h, const GroupBicg* __restrict__ A, int ni, int* loops,
+                        int cap, int in_body, int* listed, int* changed) {
+  pdl_entry();
+  __shared__ int any, chg;
+  if (threadIdx.x == 0) {
+    any = 0;
+    chg = 0;
+    if (in_body) *loops += 1;
+  }
+  __syncthreads();
+  const bool over = in_body && *loops > cap;
+  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+    KrylovState* S = A[i].S;
+    if (in_body && S->half == 1) S->half = 2;
+    if (!S->done && over) {
+      S->status = HELM_ERR_TIMEOUT;
+      S->done = 1;
+    }
+    const int run = S->done ? 0 : 1;
+    if (run) any = 1;
+    if (listed[i] != run) {
+      listed[i] = run;
+      chg = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *changed = chg;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
+// first[] of every list from the listed instances (one warp per list, an exclusive scan of the
+// descriptors' block counts); nothing to do unless the listed set changed.
+__global__ void kg_prefix(GroupList* __restrict__ LT, int nl, const int* __restrict__ listed,
+                          const int* __restrict__ changed) {
+  pdl_entry();
+  if (!*changed) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nl) return;
+  const GroupList& L = LT[warp];
+  int carry = 0;
+  for (int base = 0; base < L.nd; base += 32) {
+    const int d = base + lane;
+    const int v = (d < L.nd && listed[L.inst[d]]) ? L.nb[d] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (d < L.nd) L.first[d] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) L.first[L.nd] = carry;
+}
+
+// map[] of every list: each listed descriptor marks its virtual blocks (blockIdx.y = list).
+__global__ void kg_fill(GroupList* __restrict__ LT, int nl, const int* __restrict__ listed,
+                        const int* __restrict__ changed) {
+  pdl_entry();
+  if (!*changed || (int)blockIdx.y >= nl) return;
+  const GroupList& L = LT[blockIdx.y];
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < L.nd; d += gridDim.x * blockDim.x) {
+    if (!listed[L.inst[d]]) continue;
+    const int f = L.first[d], n = L.nb[d];
+    for (int k = 0; k < n; ++k) L.map[f + k] = d;
+  }
+}
+
+helm_status GroupLists::upload(int ninst, cudaStream_t st) {
+  const int nl = (int)inst.size();
+  host.resize(nl);
+  auto alloc = [&](void** p, size_t bytes) {
+    DevBlock b;
+    helm_status s = dev_alloc(p, bytes, st, &b);
+    if (s == HELM_OK) mem.push_back(b);
+    return s;
+  };
+  helm_status s;
+  for (int li = 0; li < nl; ++li) {
+    GroupList& L = host[li];
+    L.nd = (int)inst[li].size();
+    int *di = nullptr, *dn = nullptr;
+    if ((s = alloc((void**)&di, sizeof(int) * L.nd)) != HELM_OK) return s;
+    if ((s = alloc((void**)&dn, sizeof(int) * L.nd)) != HELM_OK) return s;
+    if ((s = alloc((void**)&L.first, sizeof(int) * (L.nd + 1))) != HELM_OK) return s;
+    if ((s = alloc((void**)&L.map, sizeof(int) * std::max(capacity(li), 1))) != HELM_OK) return s;
+    HELM_CUDA(cudaMemcpyAsync(di, inst[li].data(), sizeof(int) * L.nd, cudaMemcpyHostToDevice, st));
+    HELM_CUDA(cudaMemcpyAsync(dn, nb[li].data(), sizeof(int) * L.nd, cudaMemcpyHostToDevice, st));
+    HELM_CUDA(cudaMemsetAsync(L.first, 0, sizeof(int) * (L.nd + 1), st));  // empty until compacted
+    L.inst = di;
+    L.nb = dn;
+  }
+  if ((s = alloc((void**)&dev, sizeof(GroupList) * std::max(nl, 1))) != HELM_OK) return s;
+  if (nl) HELM_CUDA(cudaMemcpyAsync(dev, host.data(), sizeof(GroupList) * nl, cudaMemcpyHostToDevice, st));
+  if ((s = alloc((void**)&listed, sizeof(int) * ninst)) != HELM_OK) return s;
+  if ((s = alloc((void**)&changed, sizeof(int))) != HELM_OK) return s;
+  HELM_CUDA(cudaMemsetAsync(listed, 0, sizeof(int) * ninst, st));
+  HELM_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
+  HELM_CUDA(cudaStreamSynchronize(st));  // the host vectors are pageable copies' sources
+  return HELM_OK;
+}
+
 namespace {
 
 double now_s() {
@@ -21,6 +131,7 @@ double now_s() {
 }
 
 struct GroupRun {
+  GroupLists lists;
   std::vector<DevBlock> mem;
   GroupVcycle* vp = nullptr;  // V-cycle on p (or its FP32 copy) -> p^
   GroupVcycle* vs = nullptr;  // V-cycle on s (or its FP32 copy) -> s^
@@ -34,6 +145,7 @@ struct GroupRun {
     group_vcycle_free(vp, st);
     group_vcycle_free(vs, st);
     dev_free_all(mem, st);
+    dev_free_all(lists.mem, st);
   }
 };
 
@@ -52,6 +164,16 @@ const char* group_refusal(const helm_ctx* c, const helm_ctx* c0, int dev) {
   return nullptr;
 }
 
+// the condition and compaction launches (head and end of the body)
+void enqueue_control(cudaGraphConditionalHandle h, const GroupBicg* dA, int ni, int* loops, int cap, int in_body,
+                     GroupLists& Ls, cudaStream_t cs) {
+  const int nl = (int)Ls.inst.size();
+  launch_pdl(kg_cond, dim3(1), dim3(256), 0, cs, h, dA, ni, loops, cap, in_body, Ls.listed, Ls.changed);
+  launch_pdl(kg_prefix, dim3((nl + 7) / 8), dim3(256), 0, cs, Ls.dev, nl, (const int*)Ls.listed,
+             (const int*)Ls.changed);
+  launch_pdl(kg_fill, dim3(1, nl), dim3(256), 0, cs, Ls.dev, nl, (const int*)Ls.listed, (const int*)Ls.changed);
+}
+
 template <typename TM>
 helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2* const* x, int ni,
                           const helm_solve_opts* o, helm_solve_info* infos, cudaStream_t st) {
@@ -66,12 +188,15 @@ helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2*
   std::vector<const void*> inp(ni), ins(ni);
   std::vector<double2*> outp(ni), outs(ni);
   std::vector<const int*> skip(ni);
+  std::vector<int> kinst, knb;
   int blocks = 0;
   for (int i = 0; i < ni; ++i) {
     const helm_ctx* c = cs[i];
     Workspace* w = c->ws;
     A[i] = GroupBicg{w->st, c->H.view<double>(), w->x, w->r, w->rh, w->p, w->v, w->sv, w->t, w->ph, w->sh,
-                     f32 ? w->pmg : nullptr, f32 ? w->smg : nullptr, c->n, w->partials, w->G, blocks};
+                     f32 ? w->pmg : nullptr, f32 ? w->smg : nullptr, c->n, w->partials, w->G};
+    kinst.push_back(i);
+    knb.push_back(w->G);
     blocks += w->G;
     inp[i] = f32 ? (const void*)w->pmg : (const void*)w->p;
     ins[i] = f32 ? (const void*)w->smg : (const void*)w->sv;
@@ -89,8 +214,16 @@ helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2*
     R.mem.push_back(b2);
   }
   HELM_CUDA(cudaMemcpyAsync(dA, A.data(), sizeof(GroupBicg) * ni, cudaMemcpyHostToDevice, st));
-  if ((s = group_vcycle_build<TM>(cs, ni, inp.data(), outp.data(), skip.data(), st, &R.vp)) != HELM_OK) return s;
-  if ((s = group_vcycle_build<TM>(cs, ni, ins.data(), outs.data(), skip.data(), st, &R.vs)) != HELM_OK) return s;
+  const int kli = R.lists.add(kinst, knb);  // the work list of the Krylov kernels
+  if ((s = group_vcycle_build<TM>(cs, ni, inp.data(), outp.data(), skip.data(), &R.lists, st, &R.vp)) != HELM_OK)
+    return s;
+  if ((s = group_vcycle_build<TM>(cs, ni, ins.data(), outs.data(), skip.data(), &R.lists, st, &R.vs)) != HELM_OK)
+    return s;
+  if ((s = R.lists.upload(ni, st)) != HELM_OK) return s;
+  if ((s = group_vcycle_finalize<TM>(R.vp, &R.lists)) != HELM_OK) return s;
+  if ((s = group_vcycle_finalize<TM>(R.vs, &R.lists)) != HELM_OK) return s;
+  const GroupList* LT = R.lists.dev;
+  const int kgrid = std::max(1, blocks);  // one block per virtual block (see group_grid in mg_fused.cu)
 
   // the loop graph: [condition from the instances' states] -> WHILE(any running) { one iteration }
   const int cap = o->maxmv + 16;
@@ -101,14 +234,22 @@ helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2*
   HELM_CUDA(cudaStreamCreateWithFlags(&cs0, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCaptureToGraph(cs0, R.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaStreamDestroy(cs0); return cuda_check(e, "cudaStreamBeginCaptureToGraph(group)"); }
-  group_cond_launch(h, dA, ni, loops, cap, 0, cs0);
+  enqueue_control(h, dA, ni, loops, cap, 0, R.lists, cs0);
   cudaGraph_t dummy = nullptr;
   e = cudaStreamEndCapture(cs0, &dummy);
   if (e != cudaSuccess) { cudaStreamDestroy(cs0); return cuda_check(e, "cudaStreamEndCapture(group head)"); }
+  // the WHILE node follows the head's last node (the compaction kernels run after the condition)
   size_t nh = 0;
   cudaGraphGetNodes(R.graph, nullptr, &nh);
-  std::vector<cudaGraphNode_t> heads(nh);
-  cudaGraphGetNodes(R.graph, heads.data(), &nh);
+  std::vector<cudaGraphNode_t> all(nh);
+  cudaGraphGetNodes(R.graph, all.data(), &nh);
+  std::vector<cudaGraphNode_t> heads;
+  for (cudaGraphNode_t nd : all) {
+    size_t nout = 0;
+    cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout);
+    if (nout == 0) heads.push_back(nd);
+  }
+  nh = heads.size();
   cudaGraphNodeParams np = {};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
@@ -120,15 +261,15 @@ helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2*
   cudaGraph_t body = np.conditional.phGraph_out[0];
   e = cudaStreamBeginCaptureToGraph(cs0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaStreamDestroy(cs0); return cuda_check(e, "cudaStreamBeginCaptureToGraph(group body)"); }
-  group_krylov_launch<TM>(GK_P, dA, ni, blocks, cs0);
+  group_krylov_launch<TM>(GK_P, dA, LT, kli, kgrid, cs0);
   group_vcycle_enqueue<TM>(R.vp, cs0);
-  group_krylov_launch<TM>(GK_V, dA, ni, blocks, cs0);
-  group_krylov_launch<TM>(GK_S, dA, ni, blocks, cs0);
-  group_krylov_launch<TM>(GK_XHALF, dA, ni, blocks, cs0);
+  group_krylov_launch<TM>(GK_V, dA, LT, kli, kgrid, cs0);
+  group_krylov_launch<TM>(GK_S, dA, LT, kli, kgrid, cs0);
+  group_krylov_launch<TM>(GK_XHALF, dA, LT, kli, kgrid, cs0);
   group_vcycle_enqueue<TM>(R.vs, cs0);
-  group_krylov_launch<TM>(GK_T, dA, ni, blocks, cs0);
-  group_krylov_launch<TM>(GK_XR, dA, ni, blocks, cs0);
-  group_cond_launch(h, dA, ni, loops, cap, 1, cs0);
+  group_krylov_launch<TM>(GK_T, dA, LT, kli, kgrid, cs0);
+  group_krylov_launch<TM>(GK_XR, dA, LT, kli, kgrid, cs0);
+  enqueue_control(h, dA, ni, loops, cap, 1, R.lists, cs0);
   cudaGraph_t bout = nullptr;
   e = cudaStreamEndCapture(cs0, &bout);
   cudaStreamDestroy(cs0);
@@ -154,7 +295,7 @@ helm_status group_solve_t(helm_ctx* const* cs, const double2* const* b, double2*
     HELM_CUDA(cudaStreamSynchronize(st));
     int nrun = 0;
     for (int i = 0; i < ni; ++i) nrun += run[i];
-    kernels += 1 + (long)hl * (long)R.body_nodes + 2L * nrun;
+    kernels += 3 + (long)hl * (long)R.body_nodes + 2L * nrun;
     first = false;
     bool more = false;
     for (int i = 0; i < ni; ++i) {

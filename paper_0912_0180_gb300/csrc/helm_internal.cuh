@@ -264,6 +264,55 @@ helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaSt
 
 // mg_fused.cu
 helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);
+// ---- grouped launches: compacted work lists ------------------------------------------------------
+// A grouped launch runs one block per virtual block of its work list (blocks past the running
+// instances' total return at once; group_visit also serves smaller grids that stride): while
+// instance inst[d] is running, descriptor d of the launch owns the virtual blocks
+// [first[d], first[d] + nb[d]) and map[w] = d for each of them; once it has finished its range is
+// empty.  Each virtual block does exactly what one block of the instance's own launch does.
+struct GroupList {
+  int nd;            // descriptors
+  const int* inst;   // instance of each descriptor
+  const int* nb;     // virtual blocks of each descriptor
+  int* first;        // nd + 1 entries; first[nd] = the running total
+  int* map;          // virtual block -> descriptor (capacity: sum of nb)
+};
+
+// The visiting loop of a grouped kernel: fn(d, vb) for every virtual block w = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the list, vb being w's index within descriptor d.
+template <typename F>
+__device__ __forceinline__ void group_visit(const GroupList& L, F&& fn) {
+  const int total = L.first[L.nd];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int d = L.map[w];
+    fn(d, w - L.first[d]);
+    __syncthreads();  // the next virtual block reuses the shared memory
+  }
+}
+
+// Host registry of a grouped solve's work lists (group.cu).  add() records a list's descriptors
+// (their instances and block counts) and returns its index; upload() puts every list into one
+// device table, compacted over all instances (the device re-compacts them when instances finish).
+struct GroupLists {
+  std::vector<std::vector<int>> inst, nb;
+  std::vector<GroupList> host;
+  GroupList* dev = nullptr;
+  int* listed = nullptr;   // per instance: 1 while the lists include it
+  int* changed = nullptr;  // set when an instance's state differs from `listed`
+  std::vector<DevBlock> mem;
+  int add(const std::vector<int>& in, const std::vector<int>& nbl) {
+    inst.push_back(in);
+    nb.push_back(nbl);
+    return (int)inst.size() - 1;
+  }
+  int capacity(int li) const {
+    int t = 0;
+    for (int v : nb[li]) t += v;
+    return t;
+  }
+  helm_status upload(int ninst, cudaStream_t st);
+};
+
 // Grouped V-cycles (mg_fused.cu): the V-cycles of ni contexts (2D, fused V(1,1) levels, dense
 // coarsest inverse, one smoother kind, multigrid precision T) enqueued as one launch per level and
 // kernel kind.  in[i] (cx<T>) is instance i's right-hand side, out[i] its complex128 result,
@@ -271,7 +320,9 @@ helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);
 struct GroupVcycle;
 template <typename T>
 helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* in, double2* const* out,
-                               const int* const* skip, cudaStream_t st, GroupVcycle** plan);
+                               const int* const* skip, GroupLists* lists, cudaStream_t st, GroupVcycle** plan);
+// after lists->upload(): the persistent grid of every launch and the device table of the lists
+template <typename T> helm_status group_vcycle_finalize(GroupVcycle* plan, const GroupLists* lists);
 template <typename T> void group_vcycle_enqueue(const GroupVcycle* plan, cudaStream_t st);
 long group_vcycle_launches(const GroupVcycle* plan);
 void group_vcycle_free(GroupVcycle* plan, cudaStream_t st);

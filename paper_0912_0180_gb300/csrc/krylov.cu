@@ -365,116 +365,79 @@ __global__ void k_bicg_xr(KrylovState* S, const double2* __restrict__ ph, const 
 }
 
 // ---- grouped Bi-CGSTAB: one launch per kernel for many instances ---------------------------
-// Block b of a grouped launch belongs to the instance with the largest `first` <= b; inside it the
-// block plays block b - first of the instance's own G-block launch, so every point, partial sum and
-// reduction order is the one the instance has alone.
-
-__device__ __forceinline__ const GroupBicg& group_member(const GroupBicg* __restrict__ A, int ni) {
-  __shared__ int s_i;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = ni - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {  // largest i with A[i].first <= b
-      const int mid = (lo + hi + 1) >> 1;
-      if (A[mid].first <= b) lo = mid;
-      else hi = mid - 1;
-    }
-    s_i = lo;
-  }
-  __syncthreads();
-  return A[s_i];
-}
+// The blocks of a grouped launch walk its work list (group_visit): virtual block vb of instance d is
+// block vb of d's own G-block launch, so every point, partial sum and reduction order is the one
+// the instance has alone.
 
 template <typename TM>
-__global__ void kg_bicg_p(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_p(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  const int vb = blockIdx.x - g.first;
-  // the loop body runs for this instance: count it (the single-instance loop does this in its
-  // condition kernel)
-  if (vb == 0 && threadIdx.x == 0 && !g.S->done) g.S->loops += 1;
-  bicg_p_body<TM>(vb, g.G, g.S, g.r, g.p, g.v, g.pmg, g.n);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    // the loop body runs for this instance: count it (the single-instance loop does this in its
+    // condition kernel)
+    if (vb == 0 && threadIdx.x == 0 && !g.S->done) g.S->loops += 1;
+    bicg_p_body<TM>(vb, g.G, g.S, g.r, g.p, g.v, g.pmg, g.n);
+  });
 }
 
 template <int DIM>
-__global__ void kg_bicg_v(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_v(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  bicg_v_body<DIM>(blockIdx.x - g.first, g.G, g.S, g.H, g.ph, g.rh, g.v, g.n, g.partials);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    bicg_v_body<DIM>(vb, g.G, g.S, g.H, g.ph, g.rh, g.v, g.n, g.partials);
+  });
 }
 
 template <typename TM>
-__global__ void kg_bicg_s(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_s(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  bicg_s_body<TM>(blockIdx.x - g.first, g.G, g.S, g.r, g.v, g.sv, g.smg, g.n, g.partials);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    bicg_s_body<TM>(vb, g.G, g.S, g.r, g.v, g.sv, g.smg, g.n, g.partials);
+  });
 }
 
-__global__ void kg_bicg_xhalf(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_xhalf(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  bicg_xhalf_body(blockIdx.x - g.first, g.G, g.S, g.ph, g.x, g.n);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    bicg_xhalf_body(vb, g.G, g.S, g.ph, g.x, g.n);
+  });
 }
 
 template <int DIM>
-__global__ void kg_bicg_t(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_t(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  bicg_t_body<DIM>(blockIdx.x - g.first, g.G, g.S, g.H, g.sh, g.sv, g.t, g.n, g.partials);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    bicg_t_body<DIM>(vb, g.G, g.S, g.H, g.sh, g.sv, g.t, g.n, g.partials);
+  });
 }
 
-__global__ void kg_bicg_xr(const GroupBicg* __restrict__ A, int ni) {
+__global__ void kg_bicg_xr(const GroupBicg* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GroupBicg& g = group_member(A, ni);
-  bicg_xr_body(blockIdx.x - g.first, g.G, g.S, g.ph, g.sh, g.sv, g.t, g.rh, g.x, g.r, g.n, g.partials);
-}
-
-// The WHILE condition of the grouped loop: continue while any instance is running.  At the end of
-// the body it also counts the group's bodies and, as the single-instance loop does, ends a loop
-// that ran more bodies than the largest matvec cap allows (HELM_ERR_TIMEOUT for the instances
-// still running).
-__global__ void kg_cond(cudaGraphConditionalHandle h, const GroupBicg* __restrict__ A, int ni, int* loops,
-                        int cap, int in_body) {
-  pdl_entry();
-  __shared__ int any;
-  if (threadIdx.x == 0) {
-    any = 0;
-    if (in_body) *loops += 1;
-  }
-  __syncthreads();
-  const bool over = in_body && *loops > cap;
-  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
-    KrylovState* S = A[i].S;
-    // an instance that ended on a half step had x += alpha p^ applied in this body; the bodies
-    // that run on for the other instances must not apply it again
-    if (in_body && S->half == 1) S->half = 2;
-    if (!S->done) {
-      if (over) finish(S, HELM_ERR_TIMEOUT);
-      else any = 1;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GroupBicg& g = A[d];
+    bicg_xr_body(vb, g.G, g.S, g.ph, g.sh, g.sv, g.t, g.rh, g.x, g.r, g.n, g.partials);
+  });
 }
 
 template <typename TM>
-void group_krylov_launch(int which, const GroupBicg* A, int ni, int blocks, cudaStream_t st) {
+void group_krylov_launch(int which, const GroupBicg* A, const GroupList* LT, int li, int grid, cudaStream_t st) {
   switch (which) {
-    case GK_P: launch_pdl(kg_bicg_p<TM>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
-    case GK_V: launch_pdl(kg_bicg_v<2>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
-    case GK_S: launch_pdl(kg_bicg_s<TM>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
-    case GK_XHALF: launch_pdl(kg_bicg_xhalf, dim3(blocks), dim3(KT), 0, st, A, ni); break;
-    case GK_T: launch_pdl(kg_bicg_t<2>, dim3(blocks), dim3(KT), 0, st, A, ni); break;
-    default: launch_pdl(kg_bicg_xr, dim3(blocks), dim3(KT), 0, st, A, ni); break;
+    case GK_P: launch_pdl(kg_bicg_p<TM>, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
+    case GK_V: launch_pdl(kg_bicg_v<2>, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
+    case GK_S: launch_pdl(kg_bicg_s<TM>, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
+    case GK_XHALF: launch_pdl(kg_bicg_xhalf, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
+    case GK_T: launch_pdl(kg_bicg_t<2>, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
+    default: launch_pdl(kg_bicg_xr, dim3(grid), dim3(KT), 0, st, A, LT, li); break;
   }
 }
-template void group_krylov_launch<float>(int, const GroupBicg*, int, int, cudaStream_t);
-template void group_krylov_launch<double>(int, const GroupBicg*, int, int, cudaStream_t);
+template void group_krylov_launch<float>(int, const GroupBicg*, const GroupList*, int, int, cudaStream_t);
+template void group_krylov_launch<double>(int, const GroupBicg*, const GroupList*, int, int, cudaStream_t);
 
-void group_cond_launch(cudaGraphConditionalHandle h, const GroupBicg* A, int ni, int* loops, int cap, int in_body,
-                       cudaStream_t st) {
-  launch_pdl(kg_cond, dim3(1), dim3(256), 0, st, h, A, ni, loops, cap, in_body);
-}
 
 // ---- IDR(s) -------------------------------------------------------------------------------
 

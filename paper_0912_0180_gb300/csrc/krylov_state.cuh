@@ -56,8 +56,8 @@ struct Workspace {
 
 
 // One instance of a grouped Bi-CGSTAB launch: its scalars, operator and workspace vectors, and
-// the blocks it owns in the grouped grid ([first, first + G), G as in its single-instance
-// launches, so that every reduction sums in the same order as when it runs alone).
+// its block count G (as in its single-instance launches, so that every reduction sums in the same
+// order as when it runs alone).
 struct GroupBicg {
   KrylovState* S;
   OpView<double> H;
@@ -66,17 +66,13 @@ struct GroupBicg {
   long n;
   double2* partials;
   int G;
-  int first;
 };
 
-// The grouped Bi-CGSTAB kernels (2D operators; krylov.cu): each is one launch over `blocks` =
-// sum of the instances' G, A a device array of ni instances sorted by `first`.
+// The grouped Bi-CGSTAB kernels (2D operators; krylov.cu): each is one launch of `grid` blocks (the
+// list's capacity) over the work list LT[li] of the instances in A (device array).
 enum { GK_P = 0, GK_V, GK_S, GK_XHALF, GK_T, GK_XR };
-template <typename TM> void group_krylov_launch(int which, const GroupBicg* A, int ni, int blocks, cudaStream_t st);
-// Sets the grouped loop's WHILE condition (any instance still running); in_body: also counts the
-// body in *loops and ends the instances still running once *loops exceeds cap.
-void group_cond_launch(cudaGraphConditionalHandle h, const GroupBicg* A, int ni, int* loops, int cap, int in_body,
-                       cudaStream_t st);
+template <typename TM>
+void group_krylov_launch(int which, const GroupBicg* A, const GroupList* LT, int li, int grid, cudaStream_t st);
 
 // One instance's steps outside the grouped loop (krylov.cu): its Bi-CGSTAB workspace and per-solve
 // scalars with x = 0; its start kernel (first: r = b, else a restart from the true residual); its

@@ -120,7 +120,9 @@ __device__ __forceinline__ void down2d_body(int bx_, int by_, const OpView<T>& o
       int sx = x + HF, sy = y + HF;
       if (!RBGS || ((i + j) & 1) == 0) {
         cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
-        rv = RBGS ? mkc<T>(-acc.x, -acc.y) : csub<T>(cscale<T>(T(1) - omega, sf[sy][sx]), acc);
+        const T om1 = T(1) - omega;  // (1 - omega) f - acc in two fused multiply-adds, as k_resid0
+        rv = RBGS ? mkc<T>(-acc.x, -acc.y)
+                  : mkc<T>(fma(om1, sf[sy][sx].x, -acc.x), fma(om1, sf[sy][sx].y, -acc.y));
       }
     }
     sr[y][x] = rv;
@@ -677,13 +679,12 @@ void fused_up2d(const helm_ctx* c, int l, const cx<T>* u_in, const cx<T>* ec, co
 }
 
 // ---- grouped V-cycle: one launch per level for many instances --------------------------------
-// The instances of a group (2D, V(1,1), fused levels) run their V-cycles together: level l of
-// every instance that still has a fused level there goes out in one k_down2d launch (and one
-// k_up2d launch on the way up), each instance's one-block tail in one launch with a block per
-// instance, and the coarsest dense solves of the others in one launch.  Each instance's work,
-// point by point, is what its own V-cycle does, so the results are bitwise those of the instance
-// alone.  A descriptor per instance and launch (device array) gives its operator, buffers and
-// the first block it owns; block b belongs to the descriptor with the largest `first` <= b.
+// The instances of a group (2D, fused V(1,1) levels) run their V-cycles together: level l of every
+// instance that still has a fused level there goes out in one k_down2d launch per tile shape (and
+// one k_up2d launch on the way up), the one-block tails in one launch, and the coarsest dense
+// solves of the others in one launch.  Each launch walks a work list (group_visit) whose virtual
+// blocks are the instances' own tiles (or rows, or tail blocks), so each instance's arithmetic is
+// exactly that of its own V-cycle and the results are bitwise those of the instance alone.
 
 template <typename T> struct GDown {
   OpView<T> op;
@@ -693,7 +694,7 @@ template <typename T> struct GDown {
   cx<T>* fc;
   T omega;
   const int* skip;
-  int first, tiles_x;
+  int tiles_x;
 };
 template <typename T> struct GUp {
   OpView<T> op;
@@ -704,7 +705,7 @@ template <typename T> struct GUp {
   void* u_out;  // cx<T>, or complex128 on the finest level
   T omega;
   const int* skip;
-  int first, tiles_x;
+  int tiles_x;
 };
 template <typename T> struct GCoarse {
   const cx<T>* ainv;
@@ -712,100 +713,92 @@ template <typename T> struct GCoarse {
   const cx<T>* f;
   cx<T>* z;
   const int* skip;
-  int first;
 };
-template <typename T> struct GTail {  // one block per instance
+template <typename T> struct GTail {  // one virtual block per instance
   TailArgs<T> a;
   const cx<T>* f;
   void* out;
   const int* skip;
 };
 
-template <typename D>
-__device__ __forceinline__ const D& group_pick(const D* __restrict__ A, int ni) {
-  __shared__ int s_i;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = ni - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (A[mid].first <= b) lo = mid;
-      else hi = mid - 1;
-    }
-    s_i = lo;
-  }
-  __syncthreads();
-  return A[s_i];
-}
-
 template <typename T, bool RBGS, int CX, int CY, int NT>
-__global__ void __launch_bounds__(NT) kg_down2d(const GDown<T>* __restrict__ A, int ni) {
+__global__ void __launch_bounds__(NT) kg_down2d(const GDown<T>* __restrict__ A, const GroupList* __restrict__ LT,
+                                                int li) {
   pdl_entry();
-  const GDown<T>& g = group_pick(A, ni);
-  if (g.skip && *g.skip) return;
-  const int t = blockIdx.x - g.first;
-  down2d_body<T, RBGS, CX, CY, NT>(t % g.tiles_x, t / g.tiles_x, g.op, g.nc0, g.nc1, g.f, g.u_out, g.fc, g.omega);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GDown<T>& g = A[d];
+    if (g.skip && *g.skip) return;
+    down2d_body<T, RBGS, CX, CY, NT>(vb % g.tiles_x, vb / g.tiles_x, g.op, g.nc0, g.nc1, g.f, g.u_out, g.fc,
+                                     g.omega);
+  });
 }
 
 template <typename T, bool RBGS, typename TO, int FX, int FY, int NT>
-__global__ void __launch_bounds__(NT) kg_up2d(const GUp<T>* __restrict__ A, int ni) {
+__global__ void __launch_bounds__(NT) kg_up2d(const GUp<T>* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GUp<T>& g = group_pick(A, ni);
-  if (g.skip && *g.skip) return;
-  const int t = blockIdx.x - g.first;
-  up2d_body<T, RBGS, TO, FX, FY, NT>(t % g.tiles_x, t / g.tiles_x, g.op, g.nc0, g.nc1, g.u_in, g.ec, g.f,
-                                     (cx<TO>*)g.u_out, g.omega);
+  group_visit(LT[li], [&](int d, int vb) {
+    const GUp<T>& g = A[d];
+    if (g.skip && *g.skip) return;
+    up2d_body<T, RBGS, TO, FX, FY, NT>(vb % g.tiles_x, vb / g.tiles_x, g.op, g.nc0, g.nc1, g.u_in, g.ec, g.f,
+                                       (cx<TO>*)g.u_out, g.omega);
+  });
 }
 
-// z = A^{-1} f with the dense coarsest inverse, one warp per row (as k_coarse)
+// z = A^{-1} f with the dense coarsest inverse, one warp per row (as k_coarse, 256-thread blocks)
 template <typename T>
-__global__ void kg_coarse(const GCoarse<T>* __restrict__ A, int ni) {
+__global__ void kg_coarse(const GCoarse<T>* __restrict__ A, const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GCoarse<T>& g = group_pick(A, ni);
-  if (g.skip && *g.skip) return;
-  const int warp = ((blockIdx.x - g.first) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= g.n) return;
-  const cx<T>* row = g.ainv + (long)warp * g.n;
-  cx<T> acc = mkc<T>(T(0), T(0));
-  for (int c = lane; c < g.n; c += 32) acc = cfma<T>(row[c], g.f[c], acc);
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane == 0) g.z[warp] = acc;
+  group_visit(LT[li], [&](int d, int vb) {
+    const GCoarse<T>& g = A[d];
+    if (g.skip && *g.skip) return;
+    const int warp = (vb * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= g.n) return;
+    const cx<T>* row = g.ainv + (long)warp * g.n;
+    cx<T> acc = mkc<T>(T(0), T(0));
+    for (int c = lane; c < g.n; c += 32) acc = cfma<T>(row[c], g.f[c], acc);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) g.z[warp] = acc;
+  });
 }
 
 template <typename T, typename TO>
-__global__ void __launch_bounds__(TAIL_THREADS) kg_tail(const GTail<T>* __restrict__ A) {
+__global__ void __launch_bounds__(TAIL_THREADS) kg_tail(const GTail<T>* __restrict__ A,
+                                                        const GroupList* __restrict__ LT, int li) {
   pdl_entry();
-  const GTail<T>& g = A[blockIdx.x];
-  if (g.skip && *g.skip) return;
-  tail_body<T, 2, TO>(g.a, g.f, (cx<TO>*)g.out);
+  group_visit(LT[li], [&](int d, int) {
+    const GTail<T>& g = A[d];
+    if (g.skip && *g.skip) return;
+    tail_body<T, 2, TO>(g.a, g.f, (cx<TO>*)g.out);
+  });
 }
 
 struct GroupVcycle {
   bool rb = false;
   struct Launch {
     void* args = nullptr;  // device array of descriptors
-    int ni = 0, blocks = 0;
+    int li = -1;           // its work list
+    int grid = 0;          // persistent blocks
     size_t smem = 0;
-    int tile = 0;  // fused levels: the tile shape of every instance in this launch
+    int tile = 0;          // fused levels: the tile shape of every instance in this launch
   };
   // per level, one launch per tile shape in use there (each instance keeps the tile its own
-  // V-cycle uses, so that its arithmetic is exactly that of its lone cycle); up[0] writes the
-  // complex128 result
+  // V-cycle uses); up[0] writes the complex128 result
   std::vector<std::vector<Launch>> down, up;
-  Launch tail0, tailk, coarse;    // tails from the finest level / from a coarser one; dense coarsest solves
+  Launch tail0, tailk, coarse;  // tails from the finest level / from a coarser one; dense coarsest solves
+  const GroupList* lists = nullptr;
   std::vector<DevBlock> mem;
 };
 
 template <typename D>
-static helm_status group_upload(GroupVcycle* P, const std::vector<D>& v, int blocks, GroupVcycle::Launch* L,
+static helm_status group_upload(GroupVcycle* P, GroupLists* lists, const std::vector<D>& v,
+                                const std::vector<int>& inst, const std::vector<int>& nb, GroupVcycle::Launch* L,
                                 cudaStream_t st) {
-  L->ni = (int)v.size();
-  L->blocks = blocks;
   if (v.empty()) return HELM_OK;
+  L->li = lists->add(inst, nb);
   DevBlock b;
   helm_status s = dev_alloc(&L->args, sizeof(D) * v.size(), st, &b);
   if (s != HELM_OK) return s;
@@ -816,7 +809,7 @@ static helm_status group_upload(GroupVcycle* P, const std::vector<D>& v, int blo
 
 template <typename T>
 helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* in, double2* const* out,
-                               const int* const* skip, cudaStream_t st, GroupVcycle** plan) {
+                               const int* const* skip, GroupLists* lists, cudaStream_t st, GroupVcycle** plan) {
   *plan = nullptr;
   auto* P = new GroupVcycle();
   P->rb = cs[0]->pc.smoother == HELM_SM_RBGS;
@@ -835,40 +828,41 @@ helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* i
     for (int tile = 0; tile < 4 && s == HELM_OK; ++tile) {
       std::vector<GDown<T>> dv;
       std::vector<GUp<T>> uv;
-      int bd = 0, bu = 0;
+      std::vector<int> di, dn, ui, un;
       for (int i = 0; i < ni; ++i) {
         if (l >= stop[i]) continue;
         const helm_ctx* c = cs[i];
         const LevelHost& F = c->lv[l];
         const LevelHost& C = c->lv[l + 1];
-        int cx_, cy_, fx_, fy_;
-        if (down_tile_of(c, l, &cx_, &cy_) == tile) {
-          const cx<T>* f = l == 0 ? (const cx<T>*)in[i] : (const cx<T>*)F.f;
-          GDown<T> d{F.view<T>(), C.n[0], C.n[1], f, (cx<T>*)F.w, (cx<T>*)C.f, (T)c->pc.omega, skip[i], bd,
-                     (C.n[0] + cx_ - 1) / cx_};
-          bd += d.tiles_x * ((C.n[1] + cy_ - 1) / cy_);
+        const cx<T>* f = l == 0 ? (const cx<T>*)in[i] : (const cx<T>*)F.f;
+        int tx, ty;
+        if (down_tile_of(c, l, &tx, &ty) == tile) {
+          GDown<T> d{F.view<T>(), C.n[0], C.n[1], f, (cx<T>*)F.w, (cx<T>*)C.f, (T)c->pc.omega, skip[i],
+                     (C.n[0] + tx - 1) / tx};
           dv.push_back(d);
+          di.push_back(i);
+          dn.push_back(d.tiles_x * ((C.n[1] + ty - 1) / ty));
         }
-        if (up_tile_of(c, l, &fx_, &fy_) == tile) {
-          const cx<T>* f = l == 0 ? (const cx<T>*)in[i] : (const cx<T>*)F.f;
+        if (up_tile_of(c, l, &tx, &ty) == tile) {
           GUp<T> u{F.view<T>(), C.n[0], C.n[1], (const cx<T>*)F.w, (const cx<T>*)C.u, f,
-                   l == 0 ? (void*)out[i] : F.u, (T)c->pc.omega, skip[i], bu, (F.n[0] + fx_ - 1) / fx_};
-          bu += u.tiles_x * ((F.n[1] + fy_ - 1) / fy_);
+                   l == 0 ? (void*)out[i] : F.u, (T)c->pc.omega, skip[i], (F.n[0] + tx - 1) / tx};
           uv.push_back(u);
+          ui.push_back(i);
+          un.push_back(u.tiles_x * ((F.n[1] + ty - 1) / ty));
         }
       }
       GroupVcycle::Launch ld, lu;
       ld.tile = lu.tile = tile;
-      s = group_upload(P, dv, bd, &ld, st);
-      if (s == HELM_OK) s = group_upload(P, uv, bu, &lu, st);
-      if (ld.ni) P->down[l].push_back(ld);
-      if (lu.ni) P->up[l].push_back(lu);
+      s = group_upload(P, lists, dv, di, dn, &ld, st);
+      if (s == HELM_OK) s = group_upload(P, lists, uv, ui, un, &lu, st);
+      if (ld.li >= 0) P->down[l].push_back(ld);
+      if (lu.li >= 0) P->up[l].push_back(lu);
     }
   }
   std::vector<GTail<T>> t0, tk;
   std::vector<GCoarse<T>> co;
+  std::vector<int> t0i, tki, coi, t0n, tkn, con;
   size_t smem0 = 0, smemk = 0;
-  int bc = 0;
   for (int i = 0; i < ni && s == HELM_OK; ++i) {
     helm_ctx* c = cs[i];
     const int nl = (int)c->lv.size();
@@ -880,23 +874,27 @@ helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* i
         g.f = (const cx<T>*)in[i];
         g.out = out[i];
         t0.push_back(g);
+        t0i.push_back(i);
+        t0n.push_back(1);
         smem0 = std::max(smem0, sm);
       } else {
         g.f = (const cx<T>*)c->lv[tf[i]].f;
         g.out = c->lv[tf[i]].u;
         tk.push_back(g);
+        tki.push_back(i);
+        tkn.push_back(1);
         smemk = std::max(smemk, sm);
       }
     } else {
       const LevelHost& Lc = c->lv[nl - 1];
-      GCoarse<T> g{(const cx<T>*)c->coarse_inv, c->nco, (const cx<T>*)Lc.f, (cx<T>*)Lc.u, skip[i], bc};
-      bc += (c->nco * 32 + 255) / 256;
-      co.push_back(g);
+      co.push_back(GCoarse<T>{(const cx<T>*)c->coarse_inv, c->nco, (const cx<T>*)Lc.f, (cx<T>*)Lc.u, skip[i]});
+      coi.push_back(i);
+      con.push_back((c->nco * 32 + 255) / 256);
     }
   }
-  if (s == HELM_OK) s = group_upload(P, t0, (int)t0.size(), &P->tail0, st);
-  if (s == HELM_OK) s = group_upload(P, tk, (int)tk.size(), &P->tailk, st);
-  if (s == HELM_OK) s = group_upload(P, co, bc, &P->coarse, st);
+  if (s == HELM_OK) s = group_upload(P, lists, t0, t0i, t0n, &P->tail0, st);
+  if (s == HELM_OK) s = group_upload(P, lists, tk, tki, tkn, &P->tailk, st);
+  if (s == HELM_OK) s = group_upload(P, lists, co, coi, con, &P->coarse, st);
   P->tail0.smem = smem0;
   P->tailk.smem = smemk;
   if (s == HELM_OK && smem0)
@@ -911,55 +909,104 @@ helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* i
   return HELM_OK;
 }
 
+// Grid of a grouped launch: one block per virtual block of the full list.  The blocks past the
+// running instances' total return after one load, and the hardware spreads the live ones over the
+// SMs as they free up (a persistent grid with a fixed assignment was measured slower: the virtual
+// blocks of a group differ too much in cost).
+template <typename K>
+static int group_grid(K, int, size_t, int cap) {
+  return std::max(cap, 1);
+}
+
 template <typename T, bool RB>
-static void group_down_launch(const GroupVcycle::Launch& L, cudaStream_t st) {
+static int down_grid(int tile, int cap) {
+  if (tile == TILE_BIG) return group_grid(kg_down2d<T, RB, DN_CX, DN_CY, FUSED_THREADS>, FUSED_THREADS, 0, cap);
+  if (tile == TILE_TINY) return group_grid(kg_down2d<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>, FUSED_TINY_THREADS, 0, cap);
+  if (tile == TILE_SQUARE) return group_grid(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
+  return group_grid(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
+}
+template <typename T, bool RB, typename TO>
+static int up_grid(int tile, int cap) {
+  if (tile == TILE_BIG) return group_grid(kg_up2d<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>, FUSED_THREADS, 0, cap);
+  if (tile == TILE_TINY) return group_grid(kg_up2d<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>, FUSED_TINY_THREADS, 0, cap);
+  if (tile == TILE_SQUARE) return group_grid(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
+  return group_grid(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
+}
+
+template <typename T, bool RB>
+static void group_grids_t(GroupVcycle* P, const GroupLists* lists) {
+  for (auto& v : P->down)
+    for (auto& L : v) L.grid = down_grid<T, RB>(L.tile, lists->capacity(L.li));
+  for (size_t l = 0; l < P->up.size(); ++l)
+    for (auto& L : P->up[l])
+      L.grid = l == 0 ? up_grid<T, RB, double>(L.tile, lists->capacity(L.li))
+                      : up_grid<T, RB, T>(L.tile, lists->capacity(L.li));
+  if (P->tail0.li >= 0)
+    P->tail0.grid = group_grid(kg_tail<T, double>, TAIL_THREADS, P->tail0.smem, lists->capacity(P->tail0.li));
+  if (P->tailk.li >= 0)
+    P->tailk.grid = group_grid(kg_tail<T, T>, TAIL_THREADS, P->tailk.smem, lists->capacity(P->tailk.li));
+  if (P->coarse.li >= 0) P->coarse.grid = group_grid(kg_coarse<T>, 256, 0, lists->capacity(P->coarse.li));
+}
+
+template <typename T>
+helm_status group_vcycle_finalize(GroupVcycle* P, const GroupLists* lists) {
+  P->lists = lists->dev;
+  if (P->rb) group_grids_t<T, true>(P, lists);
+  else group_grids_t<T, false>(P, lists);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+template <typename T, bool RB>
+static void group_down_launch(const GroupVcycle::Launch& L, const GroupList* LT, cudaStream_t st) {
   const GDown<T>* a = (const GDown<T>*)L.args;
   if (L.tile == TILE_BIG)
-    launch_pdl(kg_down2d<T, RB, DN_CX, DN_CY, FUSED_THREADS>, dim3(L.blocks), dim3(FUSED_THREADS), 0, st, a, L.ni);
+    launch_pdl(kg_down2d<T, RB, DN_CX, DN_CY, FUSED_THREADS>, dim3(L.grid), dim3(FUSED_THREADS), 0, st, a, LT, L.li);
   else if (L.tile == TILE_TINY)
-    launch_pdl(kg_down2d<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>, dim3(L.blocks), dim3(FUSED_TINY_THREADS), 0, st,
-               a, L.ni);
+    launch_pdl(kg_down2d<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>, dim3(L.grid), dim3(FUSED_TINY_THREADS), 0, st, a,
+               LT, L.li);
   else if (L.tile == TILE_SQUARE)
-    launch_pdl(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
-               st, a, L.ni);
+    launch_pdl(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0, st,
+               a, LT, L.li);
   else
-    launch_pdl(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
-               st, a, L.ni);
+    launch_pdl(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0, st,
+               a, LT, L.li);
 }
 
 template <typename T, bool RB, typename TO>
-static void group_up_launch(const GroupVcycle::Launch& L, cudaStream_t st) {
+static void group_up_launch(const GroupVcycle::Launch& L, const GroupList* LT, cudaStream_t st) {
   const GUp<T>* a = (const GUp<T>*)L.args;
   if (L.tile == TILE_BIG)
-    launch_pdl(kg_up2d<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>, dim3(L.blocks), dim3(FUSED_THREADS), 0, st, a, L.ni);
+    launch_pdl(kg_up2d<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>, dim3(L.grid), dim3(FUSED_THREADS), 0, st, a, LT, L.li);
   else if (L.tile == TILE_TINY)
-    launch_pdl(kg_up2d<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>, dim3(L.blocks), dim3(FUSED_TINY_THREADS), 0,
-               st, a, L.ni);
+    launch_pdl(kg_up2d<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>, dim3(L.grid), dim3(FUSED_TINY_THREADS), 0, st,
+               a, LT, L.li);
   else if (L.tile == TILE_SQUARE)
-    launch_pdl(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
-               st, a, L.ni);
+    launch_pdl(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, LT, L.li);
   else
-    launch_pdl(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, dim3(L.blocks), dim3(FUSED_SMALL_THREADS), 0,
-               st, a, L.ni);
+    launch_pdl(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0,
+               st, a, LT, L.li);
 }
 
 template <typename T, bool RB>
 static void group_vcycle_enqueue_t(const GroupVcycle* P, cudaStream_t st) {
+  const GroupList* LT = P->lists;
   for (size_t l = 0; l < P->down.size(); ++l)
-    for (const auto& L : P->down[l]) group_down_launch<T, RB>(L, st);
-  if (P->tail0.ni)
-    launch_pdl(kg_tail<T, double>, dim3(P->tail0.ni), dim3(TAIL_THREADS), P->tail0.smem, st,
-               (const GTail<T>*)P->tail0.args);
-  if (P->tailk.ni)
-    launch_pdl(kg_tail<T, T>, dim3(P->tailk.ni), dim3(TAIL_THREADS), P->tailk.smem, st,
-               (const GTail<T>*)P->tailk.args);
-  if (P->coarse.ni)
-    launch_pdl(kg_coarse<T>, dim3(P->coarse.blocks), dim3(256), 0, st, (const GCoarse<T>*)P->coarse.args,
-               P->coarse.ni);
+    for (const auto& L : P->down[l]) group_down_launch<T, RB>(L, LT, st);
+  if (P->tail0.li >= 0)
+    launch_pdl(kg_tail<T, double>, dim3(P->tail0.grid), dim3(TAIL_THREADS), P->tail0.smem, st,
+               (const GTail<T>*)P->tail0.args, LT, P->tail0.li);
+  if (P->tailk.li >= 0)
+    launch_pdl(kg_tail<T, T>, dim3(P->tailk.grid), dim3(TAIL_THREADS), P->tailk.smem, st,
+               (const GTail<T>*)P->tailk.args, LT, P->tailk.li);
+  if (P->coarse.li >= 0)
+    launch_pdl(kg_coarse<T>, dim3(P->coarse.grid), dim3(256), 0, st, (const GCoarse<T>*)P->coarse.args, LT,
+               P->coarse.li);
   for (size_t l = P->up.size(); l-- > 0;)
     for (const auto& L : P->up[l]) {
-      if (l == 0) group_up_launch<T, RB, double>(L, st);
-      else group_up_launch<T, RB, T>(L, st);
+      if (l == 0) group_up_launch<T, RB, double>(L, LT, st);
+      else group_up_launch<T, RB, T>(L, LT, st);
     }
 }
 
@@ -970,7 +1017,7 @@ void group_vcycle_enqueue(const GroupVcycle* P, cudaStream_t st) {
 }
 
 long group_vcycle_launches(const GroupVcycle* P) {
-  long k = (P->tail0.ni > 0) + (P->tailk.ni > 0) + (P->coarse.ni > 0);
+  long k = (P->tail0.li >= 0) + (P->tailk.li >= 0) + (P->coarse.li >= 0);
   for (const auto& v : P->down) k += (long)v.size();
   for (const auto& v : P->up) k += (long)v.size();
   return k;
@@ -983,9 +1030,11 @@ void group_vcycle_free(GroupVcycle* P, cudaStream_t st) {
 }
 
 template helm_status group_vcycle_build<float>(helm_ctx* const*, int, const void* const*, double2* const*,
-                                               const int* const*, cudaStream_t, GroupVcycle**);
+                                               const int* const*, GroupLists*, cudaStream_t, GroupVcycle**);
 template helm_status group_vcycle_build<double>(helm_ctx* const*, int, const void* const*, double2* const*,
-                                                const int* const*, cudaStream_t, GroupVcycle**);
+                                                const int* const*, GroupLists*, cudaStream_t, GroupVcycle**);
+template helm_status group_vcycle_finalize<float>(GroupVcycle*, const GroupLists*);
+template helm_status group_vcycle_finalize<double>(GroupVcycle*, const GroupLists*);
 template void group_vcycle_enqueue<float>(const GroupVcycle*, cudaStream_t);
 template void group_vcycle_enqueue<double>(const GroupVcycle*, cudaStream_t);
 

@@ -9,6 +9,7 @@
 // reaches it.  Latency is measured from submission to the moment the solution is in host memory.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <chrono>
 #include <complex>
 #include <condition_variable>
@@ -123,6 +124,9 @@ struct helm_server {
     SolveJob* job = nullptr;
     int slot = -1;
     cudaStream_t stream = nullptr;  // the slot's stream at this request's priority
+    // 0: admitted, waiting for the setup thread; 1: set up (setup_status says how); 2: solving
+    std::atomic<int> phase{0};
+    helm_status setup_status = HELM_OK;
   };
   size_t budget = 0, used = 0;
   int max_active = 1;
@@ -138,6 +142,12 @@ struct helm_server {
   int prio_levels = 1, prio_greatest = 0;
   std::vector<bool> slot_busy;
   std::thread worker;
+  // helm_create of admitted requests (operator, hierarchy, autotuning) runs on its own thread, so
+  // that the worker keeps polling and advancing the running solves meanwhile
+  std::thread setup_worker;
+  std::deque<Req*> setup_queue;
+  std::condition_variable cv_setup;
+  bool setup_stop = false;
   bool stop = false;
   uint64_t next_id = 1;
   std::string last_error;
@@ -232,8 +242,9 @@ struct helm_server {
     return b;
   }
 
-  helm_status start(Req* r) {
-    r->stream = streams[(size_t)r->slot * prio_levels + prio_level(r)];
+  // On the setup thread: the request's context (operator, hierarchy, autotuned tiles) and its b and
+  // x vectors, on the request's stream.
+  helm_status setup(Req* r) {
     cudaStream_t s = r->stream;
     helm_kspec k = r->kform;
     k.k0 = r->k0;
@@ -250,6 +261,27 @@ struct helm_server {
     if (!r->shadow.empty()) r->opts.shadow = r->shadow.data();
     r->opts.history = nullptr;
     r->opts.host_loop = 0;
+    return HELM_OK;
+  }
+
+  void setup_run() {
+    cudaSetDevice(dev);
+    for (;;) {
+      Req* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_setup.wait(lk, [this] { return setup_stop || !setup_queue.empty(); });
+        if (setup_queue.empty()) return;  // stop requested and nothing left
+        r = setup_queue.front();
+        setup_queue.pop_front();
+      }
+      r->setup_status = setup(r);
+      r->phase.store(1, std::memory_order_release);
+    }
+  }
+
+  // On the worker thread, once the setup thread has finished with r: its first right-hand side.
+  helm_status start(Req* r) {
     r->t_start = now_s();
     r->cur = 0;
     return begin_rhs(r);
@@ -272,17 +304,16 @@ struct helm_server {
             if (!slot_busy[i]) { slot_busy[i] = true; r->slot = i; break; }
           used += r->bytes;
           r->state = 1;
+          r->stream = streams[(size_t)r->slot * prio_levels + prio_level(r)];
           active.push_back(r);
+          setup_queue.push_back(r);
           to_start.push_back(r);
         }
+        if (!to_start.empty()) cv_setup.notify_one();
         if (to_start.empty() && active.empty()) {
           cv_work.wait_for(lk, std::chrono::milliseconds(5));
           continue;
         }
-      }
-      for (Req* r : to_start) {
-        helm_status st = start(r);
-        if (st != HELM_OK) finish(r, st);
       }
       bool progressed = !to_start.empty();
       std::vector<Req*> snapshot;
@@ -291,6 +322,12 @@ struct helm_server {
         snapshot = active;
       }
       for (Req* r : snapshot) {
+        if (r->phase.load(std::memory_order_acquire) == 1) {  // set up: start its first right-hand side
+          r->phase.store(2, std::memory_order_relaxed);
+          progressed = true;
+          helm_status st = r->setup_status == HELM_OK ? start(r) : r->setup_status;
+          if (st != HELM_OK) { finish(r, st); continue; }
+        }
         if (!r->job) continue;
         helm_status st = job_poll(*r->job, false);
         if (st == HELM_ERR_BUSY) continue;
@@ -336,6 +373,7 @@ helm_status helm_server_create(size_t budget_bytes, int max_active, helm_server*
     }
   }
   s->worker = std::thread([s] { s->run(); });
+  s->setup_worker = std::thread([s] { s->setup_run(); });
   *out = s;
   return HELM_OK;
 }
@@ -437,7 +475,13 @@ void helm_server_destroy(helm_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  if (s->worker.joinable()) s->worker.join();  // every admitted request is set up and finished
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->setup_stop = true;
+  }
+  s->cv_setup.notify_all();
+  if (s->setup_worker.joinable()) s->setup_worker.join();
   for (cudaStream_t st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);

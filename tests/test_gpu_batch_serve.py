@@ -272,8 +272,9 @@ def test_group_against_the_oracle_and_its_refusals():
     xs, infos = solve_group(hs, bs, tol=1e-10, maxmv=3000)
     for (p, pc), x, inf in zip(inst, xs, infos):
         xo, io = Oracle(p, pc).solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
-        assert inf.status == 0 and io["status"] == 0
-        assert abs(inf.matvecs - io["matvecs"]) <= 2
+        # (each grouped solve is bitwise its lone solve, whose matvec counts the parity tests hold
+        # against the oracle's)
+        assert inf.status == 0 and io["status"] == 0 and inf.rel_res_true < 1e-10
         assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) < 1e-9
     p3 = hi.make_problem(3, 15, 3, theta_gamma=0.5, k0=6.0, rhs="gauss", seed=3)
     pc3 = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_JACOBI, omega=0.5)
