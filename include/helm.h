@@ -144,7 +144,7 @@ typedef struct {
 /* helm_precond.flags: HELM_PF_UNFUSED runs every V-cycle component as its own kernel (the
  * same arithmetic as the default fused kernels; for testing the fusion); HELM_PF_NO_PDL
  * launches the solve-path kernels without programmatic dependent launch (same kernels);
- * HELM_PF_NO_AUTOTUNE skips the autotuner of helm_create, which times the large, small, square
+ * HELM_PF_NO_AUTOTUNE skips the autotuner of helm_create, which times the large, small, square, wide
  * and one-warp tiles of the fused 2D kernels on every fused level and then whole V-cycles for every
  * admissible depth of the one-block tail kernel, keeps the fastest, and caches the choices for the
  * process (tiles by precision, smoother and level shape; depth by precision, smoother and

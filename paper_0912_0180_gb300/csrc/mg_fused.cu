@@ -41,7 +41,11 @@ constexpr int FUSED_THREADS = 256, FUSED_SMALL_THREADS = 128, FUSED_TINY_THREADS
 // which spreads a small FP64 level over many more SMs, and a square tile of 128 threads (8 x 8
 // coarse / 16 x 16 fine), whose halo is smaller than the small tile's and whose block count falls
 // between the small and the large tile's (for an even spread over the SMs)
-enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2, TILE_SQUARE = 3 };
+// and a wide tile of 256 threads (16 x 12 coarse / 32 x 24 fine), whose halo is the smallest (the
+// recomputed sweep and residual cost most in FP64, where the fine levels are bound by the FP64 pipe)
+enum { TILE_SMALL = 0, TILE_BIG = 1, TILE_TINY = 2, TILE_SQUARE = 3, TILE_WIDE = 4 };
+constexpr int NUM_TILES = 5;
+constexpr int DN_WCX = 16, DN_WCY = 12, UP_WFX = 32, UP_WFY = 24;
 
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
@@ -607,6 +611,7 @@ static void down_tile(int tile, const LevelHost& F, const LevelHost& C, const cx
   if (tile == TILE_BIG) down_launch<T, RB, DN_CX, DN_CY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else if (tile == TILE_TINY) down_launch<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else if (tile == TILE_SQUARE) down_launch<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
+  else if (tile == TILE_WIDE) down_launch<T, RB, DN_WCX, DN_WCY, FUSED_THREADS>(F, C, f, u_out, fc, om, skip, st);
   else down_launch<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>(F, C, f, u_out, fc, om, skip, st);
 }
 
@@ -617,16 +622,20 @@ static int down_tile_of(const helm_ctx* c, int l, int* tx, int* ty) {
   const LevelHost& C = c->lv[l + 1];
   long nb = (long)((C.n[0] + DN_CX - 1) / DN_CX) * ((C.n[1] + DN_CY - 1) / DN_CY);
   int tile = F.tile_down >= 0 ? F.tile_down : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
-  *tx = tile == TILE_BIG ? DN_CX : tile == TILE_TINY ? DN_TCX : tile == TILE_SQUARE ? DN_QCX : DN_SCX;
-  *ty = tile == TILE_BIG ? DN_CY : tile == TILE_TINY ? DN_TCY : tile == TILE_SQUARE ? DN_QCY : DN_SCY;
+  *tx = tile == TILE_BIG ? DN_CX : tile == TILE_TINY ? DN_TCX : tile == TILE_SQUARE ? DN_QCX
+      : tile == TILE_WIDE ? DN_WCX : DN_SCX;
+  *ty = tile == TILE_BIG ? DN_CY : tile == TILE_TINY ? DN_TCY : tile == TILE_SQUARE ? DN_QCY
+      : tile == TILE_WIDE ? DN_WCY : DN_SCY;
   return tile;
 }
 static int up_tile_of(const helm_ctx* c, int l, int* tx, int* ty) {
   const LevelHost& F = c->lv[l];
   long nb = (long)((F.n[0] + UP_FX - 1) / UP_FX) * ((F.n[1] + UP_FY - 1) / UP_FY);
   int tile = F.tile_up >= 0 ? F.tile_up : (big_tiles(c, nb) ? TILE_BIG : TILE_SMALL);
-  *tx = tile == TILE_BIG ? UP_FX : tile == TILE_TINY ? UP_TFX : tile == TILE_SQUARE ? UP_QFX : UP_SFX;
-  *ty = tile == TILE_BIG ? UP_FY : tile == TILE_TINY ? UP_TFY : tile == TILE_SQUARE ? UP_QFY : UP_SFY;
+  *tx = tile == TILE_BIG ? UP_FX : tile == TILE_TINY ? UP_TFX : tile == TILE_SQUARE ? UP_QFX
+      : tile == TILE_WIDE ? UP_WFX : UP_SFX;
+  *ty = tile == TILE_BIG ? UP_FY : tile == TILE_TINY ? UP_TFY : tile == TILE_SQUARE ? UP_QFY
+      : tile == TILE_WIDE ? UP_WFY : UP_SFY;
   return tile;
 }
 
@@ -655,6 +664,7 @@ static void up_tile(int tile, const LevelHost& F, const LevelHost& C, const cx<T
   if (tile == TILE_BIG) up_launch<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
   else if (tile == TILE_TINY) up_launch<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
   else if (tile == TILE_SQUARE) up_launch<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
+  else if (tile == TILE_WIDE) up_launch<T, RB, TO, UP_WFX, UP_WFY, FUSED_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
   else up_launch<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>(F, C, u_in, ec, f, o, om, skip, st);
 }
 
@@ -825,7 +835,7 @@ helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* i
   P->down.resize(lmax);
   P->up.resize(lmax);
   for (int l = 0; l < lmax && s == HELM_OK; ++l) {
-    for (int tile = 0; tile < 4 && s == HELM_OK; ++tile) {
+    for (int tile = 0; tile < NUM_TILES && s == HELM_OK; ++tile) {
       std::vector<GDown<T>> dv;
       std::vector<GUp<T>> uv;
       std::vector<int> di, dn, ui, un;
@@ -913,39 +923,16 @@ helm_status group_vcycle_build(helm_ctx* const* cs, int ni, const void* const* i
 // running instances' total return after one load, and the hardware spreads the live ones over the
 // SMs as they free up (a persistent grid with a fixed assignment was measured slower: the virtual
 // blocks of a group differ too much in cost).
-template <typename K>
-static int group_grid(K, int, size_t, int cap) {
-  return std::max(cap, 1);
-}
-
-template <typename T, bool RB>
-static int down_grid(int tile, int cap) {
-  if (tile == TILE_BIG) return group_grid(kg_down2d<T, RB, DN_CX, DN_CY, FUSED_THREADS>, FUSED_THREADS, 0, cap);
-  if (tile == TILE_TINY) return group_grid(kg_down2d<T, RB, DN_TCX, DN_TCY, FUSED_TINY_THREADS>, FUSED_TINY_THREADS, 0, cap);
-  if (tile == TILE_SQUARE) return group_grid(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
-  return group_grid(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
-}
-template <typename T, bool RB, typename TO>
-static int up_grid(int tile, int cap) {
-  if (tile == TILE_BIG) return group_grid(kg_up2d<T, RB, TO, UP_FX, UP_FY, FUSED_THREADS>, FUSED_THREADS, 0, cap);
-  if (tile == TILE_TINY) return group_grid(kg_up2d<T, RB, TO, UP_TFX, UP_TFY, FUSED_TINY_THREADS>, FUSED_TINY_THREADS, 0, cap);
-  if (tile == TILE_SQUARE) return group_grid(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
-  return group_grid(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, FUSED_SMALL_THREADS, 0, cap);
-}
+static int group_grid(int cap) { return std::max(cap, 1); }
 
 template <typename T, bool RB>
 static void group_grids_t(GroupVcycle* P, const GroupLists* lists) {
   for (auto& v : P->down)
-    for (auto& L : v) L.grid = down_grid<T, RB>(L.tile, lists->capacity(L.li));
-  for (size_t l = 0; l < P->up.size(); ++l)
-    for (auto& L : P->up[l])
-      L.grid = l == 0 ? up_grid<T, RB, double>(L.tile, lists->capacity(L.li))
-                      : up_grid<T, RB, T>(L.tile, lists->capacity(L.li));
-  if (P->tail0.li >= 0)
-    P->tail0.grid = group_grid(kg_tail<T, double>, TAIL_THREADS, P->tail0.smem, lists->capacity(P->tail0.li));
-  if (P->tailk.li >= 0)
-    P->tailk.grid = group_grid(kg_tail<T, T>, TAIL_THREADS, P->tailk.smem, lists->capacity(P->tailk.li));
-  if (P->coarse.li >= 0) P->coarse.grid = group_grid(kg_coarse<T>, 256, 0, lists->capacity(P->coarse.li));
+    for (auto& L : v) L.grid = group_grid(lists->capacity(L.li));
+  for (auto& v : P->up)
+    for (auto& L : v) L.grid = group_grid(lists->capacity(L.li));
+  for (GroupVcycle::Launch* L : {&P->tail0, &P->tailk, &P->coarse})
+    if (L->li >= 0) L->grid = group_grid(lists->capacity(L->li));
 }
 
 template <typename T>
@@ -968,6 +955,8 @@ static void group_down_launch(const GroupVcycle::Launch& L, const GroupList* LT,
   else if (L.tile == TILE_SQUARE)
     launch_pdl(kg_down2d<T, RB, DN_QCX, DN_QCY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0, st,
                a, LT, L.li);
+  else if (L.tile == TILE_WIDE)
+    launch_pdl(kg_down2d<T, RB, DN_WCX, DN_WCY, FUSED_THREADS>, dim3(L.grid), dim3(FUSED_THREADS), 0, st, a, LT, L.li);
   else
     launch_pdl(kg_down2d<T, RB, DN_SCX, DN_SCY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0, st,
                a, LT, L.li);
@@ -984,6 +973,9 @@ static void group_up_launch(const GroupVcycle::Launch& L, const GroupList* LT, c
   else if (L.tile == TILE_SQUARE)
     launch_pdl(kg_up2d<T, RB, TO, UP_QFX, UP_QFY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0,
                st, a, LT, L.li);
+  else if (L.tile == TILE_WIDE)
+    launch_pdl(kg_up2d<T, RB, TO, UP_WFX, UP_WFY, FUSED_THREADS>, dim3(L.grid), dim3(FUSED_THREADS), 0, st, a, LT,
+               L.li);
   else
     launch_pdl(kg_up2d<T, RB, TO, UP_SFX, UP_SFY, FUSED_SMALL_THREADS>, dim3(L.grid), dim3(FUSED_SMALL_THREADS), 0,
                st, a, LT, L.li);
@@ -1039,8 +1031,9 @@ template void group_vcycle_enqueue<float>(const GroupVcycle*, cudaStream_t);
 template void group_vcycle_enqueue<double>(const GroupVcycle*, cudaStream_t);
 
 // ---- autotuner ------------------------------------------------------------------------------
-// On every fused 2D level the large, small, square and one-warp tiles of k_down2d and k_up2d are timed with
-// CUDA events (mean of three launches after one warm-up) on zeroed buffers of the level's shape,
+// On every fused 2D level the large, small, square, wide and one-warp tiles of k_down2d and k_up2d are timed
+// with CUDA events (the fastest of three rounds of three launches, after one warm-up) on zeroed buffers of
+// the level's shape,
 // and the fastest is kept; then whole V-cycles are timed for every admissible depth of the
 // one-block tail (from the deepest that fits its budgets to none) and the fastest depth is kept.
 // Choices are cached for the process (tiles by precision, smoother and level shape; depth by
@@ -1097,13 +1090,17 @@ static void tune_cache_append(const char* line) {
 template <typename F_>
 static float time_variant(F_ launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   launch();
-  cudaEventRecord(e0, st);
-  for (int r = 0; r < 3; ++r) launch();
-  cudaEventRecord(e1, st);
-  cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  return ms;
+  float best = 1e30f;
+  for (int round = 0; round < 3; ++round) {  // the fastest of three rounds: tiles often differ by
+    cudaEventRecord(e0, st);                 // less than one round's noise
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = ms < best ? ms : best;
+  }
+  return best;
 }
 
 template <typename T, bool RB>
@@ -1123,7 +1120,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     for (int l = 0; l < nl - 1; ++l) {
       if (c->lv[l].stg64) continue;  // Galerkin levels do not run the fused kernels
       auto it = g_tune.find(std::make_tuple((int)sizeof(T), (int)RB, c->lv[l].n[0], c->lv[l].n[1]));
-      auto valid = [](int t) { return t == TILE_BIG || t == TILE_SMALL || t == TILE_TINY || t == TILE_SQUARE; };
+      auto valid = [](int t) { return t >= 0 && t < NUM_TILES; };
       if (it != g_tune.end() && valid(it->second.first) && valid(it->second.second)) {
         c->lv[l].tile_down = it->second.first;
         c->lv[l].tile_up = it->second.second;
@@ -1167,7 +1164,7 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
     const LevelHost& C = c->lv[l + 1];
     int best_d = TILE_BIG, best_u = TILE_BIG;
     float td = 1e30f, tu = 1e30f;
-    for (int tile : {TILE_BIG, TILE_SMALL, TILE_TINY, TILE_SQUARE}) {
+    for (int tile : {TILE_BIG, TILE_SMALL, TILE_TINY, TILE_SQUARE, TILE_WIDE}) {
       float a = time_variant([&] { down_tile<T, RB>(tile, F, C, f, u, fc, om, nullptr, st); }, st, e0, e1);
       float b = time_variant([&] { up_tile<T, RB, T>(tile, F, C, u, fc, f, (T*)o, om, nullptr, st); }, st, e0, e1);
       if (a < td) { td = a; best_d = tile; }
