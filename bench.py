@@ -496,7 +496,7 @@ DOWN_FP64_OPS_PER_POINT = 4 + 12 + 18 / 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level launch of the fused
 # down kernel on this workload, from an ncu --set full capture of the current kernels (FP64, FP32);
 # set back to None whenever k_down2d changes.
-DOWN_TRAFFIC_BYTES = {"c128": None, "c64": None}
+DOWN_TRAFFIC_BYTES = {"c128": 13134336, "c64": None}
 
 
 def down_bytes_per_point(esz: int) -> float:
@@ -571,7 +571,8 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
                 "frac": d64["T_op/s"] / fp64_ops_peak, "traffic": DOWN_TRAFFIC_BYTES["c128"],
                 "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
                 "fp64_ops_per_launch": d64["fp64_ops"], "launch_us": d64["us"],
-                "note": "DADD, DMUL and DFMA each take one FP64-pipe slot; ncu: the pipe is 82% busy"}
+                "note": "DADD, DMUL and DFMA each take one FP64-pipe slot; ncu: the FP64 pipe is 76% busy over "
+                        "active cycles, DRAM reads = the algorithmic reads (f and omega/D; writes stay in L2)"}
     fp32 = {"kernel": "k_down2d<float> (same kernel in the FP32 V-cycle)", "bound": "hbm",
             "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm,
             "traffic": DOWN_TRAFFIC_BYTES["c64"],
