@@ -358,7 +358,9 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
         hh = ctx[mg]
         f = torch.randn(n, dtype=dt, device=dev)
         u = torch.zeros(n, dtype=dt, device=dev)
-        t = _time_cold(torch, flush, lambda: hh.level_op(L.HELM_OP_SMOOTH, 0, u, f, u), name=f"rbgs_sweep_{mg}_3d")
+        # u and f in the level's storage order (x-split rows on the FP32 levels), as inside the V-cycle
+        t = _time_cold(torch, flush, lambda: hh.level_op(L.HELM_OP_SMOOTH | L.HELM_OP_STORED, 0, u, f, u),
+                       name=f"rbgs_sweep_{mg}_3d")
         table[f"rbgs_sweep_{mg}"] = {"us": t * 1e6, "bytes": n * 4 * esz, "GB/s": n * 4 * esz / t / 1e9}
         r = torch.randn(n, dtype=torch.complex128, device=dev)
         z = torch.empty(n, dtype=dt, device=dev)

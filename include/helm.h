@@ -248,9 +248,18 @@ helm_status helm_vcycle(helm_ctx* ctx, const helm_precond* pc, helm_dtype dtype,
  *   HELM_OP_COARSE    out = M_coarsest^{-1} a (lvl must be the coarsest level)
  *   HELM_OP_DOWN      the fused first half of a V(1,1) level (2D, nu1 = 1, not the coarsest):
  *                     a = one smoothing sweep from the zero guess on M_lvl a = b, and
- *                     out (level lvl+1) = full weighting of b - M_lvl a, in one kernel */
+ *                     out (level lvl+1) = full weighting of b - M_lvl a, in one kernel
+ *   HELM_OP_TO_STORED   out = a (natural order) in level lvl's storage order
+ *   HELM_OP_FROM_STORED out = a (in level lvl's storage order) in natural order
+ * Vectors are in natural order (x fastest), unless HELM_OP_STORED is or'ed into `op` (SMOOTH,
+ * SMOOTH0, APPLY, RESIDUAL, RESTRICT, PROLONG: every vector in its level's storage order).  The
+ * storage order is natural except on the red-black levels of a 3D FP32 hierarchy above the
+ * coarsest level (and above the one-block tail): there each row of n0 points holds its even x
+ * indices first, then its odd ones ("x-split"), so that the points of one colour in a row are
+ * contiguous.  The V-cycle converts at its boundary; this interface is for tests and timing. */
 enum { HELM_OP_APPLY = 0, HELM_OP_RESIDUAL = 1, HELM_OP_SMOOTH = 2, HELM_OP_SMOOTH0 = 3,
-       HELM_OP_RESTRICT = 4, HELM_OP_PROLONG = 5, HELM_OP_COARSE = 6, HELM_OP_DOWN = 7 };
+       HELM_OP_RESTRICT = 4, HELM_OP_PROLONG = 5, HELM_OP_COARSE = 6, HELM_OP_DOWN = 7,
+       HELM_OP_TO_STORED = 8, HELM_OP_FROM_STORED = 9, HELM_OP_STORED = 0x100 };
 helm_status helm_level_op(helm_ctx* ctx, int op, int lvl, void* a, const void* b, void* out,
                           int count, void* stream);
 

@@ -12,6 +12,7 @@ HELM_ERR_BREAKDOWN, HELM_ERR_MAXIT, HELM_ERR_NAN, HELM_ERR_TIMEOUT, HELM_ERR_BUS
 HELM_C64, HELM_C128 = 0, 1
 HELM_OP_APPLY, HELM_OP_RESIDUAL, HELM_OP_SMOOTH, HELM_OP_SMOOTH0 = 0, 1, 2, 3
 HELM_OP_RESTRICT, HELM_OP_PROLONG, HELM_OP_COARSE, HELM_OP_DOWN = 4, 5, 6, 7
+HELM_OP_TO_STORED, HELM_OP_FROM_STORED, HELM_OP_STORED = 8, 9, 0x100
 HELM_PF_UNFUSED, HELM_PF_NO_PDL, HELM_PF_NO_AUTOTUNE, HELM_PF_GALERKIN = 1, 2, 4, 8
 HELM_SERVE_FIFO, HELM_SERVE_SMALLEST_FIRST = 0, 1
 HELM_K_CONST, HELM_K_GAUSS_BUMP, HELM_K_FIELD = 0, 1, 2

@@ -252,7 +252,8 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
   if ((s = build_operator(c, k, st)) != HELM_OK) { ctx_release(c); return s; }
   if ((s = build_hierarchy(c, st)) != HELM_OK) { ctx_release(c); return s; }
   if (pc->kind != HELM_PC_NONE && pc->mg_dtype == HELM_C64) {
-    if ((s = ctx_alloc(c, &c->scratch, sizeof(float2) * c->n)) != HELM_OK) { ctx_release(c); return s; }
+    // two vectors: the V-cycle's level-0 output before widening, and helm_vcycle's converted input
+    if ((s = ctx_alloc(c, &c->scratch, 2 * sizeof(float2) * c->n)) != HELM_OK) { ctx_release(c); return s; }
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { ctx_release(c); return cuda_check(e, "helm_create"); }
@@ -320,9 +321,10 @@ helm_status helm_vcycle(helm_ctx* c, const helm_precond* pc, helm_dtype dtype, c
     return e == cudaSuccess ? HELM_OK : cuda_check(e, "helm_vcycle copy");
   }
   if (f32) {
-    helm_status s = convert_c128_to_mg(c, (const double2*)r, c->scratch, st);
+    float2* in = (float2*)c->scratch + c->n;  // not the first half: the unfused cycle's output goes there
+    helm_status s = mg_input_from_c128(c, (const double2*)r, in, st);
     if (s != HELM_OK) return s;
-    return mg_vcycle<float>(c, (const float2*)c->scratch, z, z64, nullptr, st);
+    return mg_vcycle<float>(c, in, z, z64, nullptr, st);
   }
   if (!z64) { set_error("helm_vcycle: an FP64 hierarchy gives complex128 output"); return HELM_ERR_ARG; }
   return mg_vcycle<double>(c, (const double2*)r, z, false, nullptr, st);

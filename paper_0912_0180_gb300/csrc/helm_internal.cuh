@@ -163,6 +163,11 @@ struct LevelHost {
   // fused 2D kernel tiles picked by the autotuner: 1 large, 0 small, 2 one warp, 3 square, -1 by the
   // block-count rule
   int tile_down = -1, tile_up = -1;
+  // x-split storage (FP32 red-black levels of a 3D hierarchy above the coarsest and the one-block
+  // tail): u, f, the spare vector and dinv32 store each row's even x indices first, then the odd
+  // ones, so that a half-sweep reads only its own colour's sectors.  phi32 and dg32 stay natural.
+  int xs = 0;
+  int xs_half() const { return xs ? (n[0] + 1) / 2 : 0; }
   // work vectors (MG type), allocated for multigrid levels
   void* u = nullptr;
   void* f = nullptr;
@@ -211,7 +216,8 @@ struct helm_ctx {
   size_t bytes = 0;                  // device bytes held
   std::vector<helm::DevBlock> allocs;  // everything to free
   helm::Workspace* ws = nullptr;     // Krylov workspace (lazily created)
-  void* scratch = nullptr;           // conversion buffer for helm_vcycle (mg dtype, N)
+  void* scratch = nullptr;           // FP32 hierarchies: 2N complex64, the unfused V-cycle's level-0
+                                     // output before widening, then helm_vcycle's converted input
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations of helm_create
   int tail_first = 1 << 30;          // first level run by the single-block tail kernel
   FdmCoarse fdm;                     // separable coarsest solve (constant phi there), or off
@@ -261,6 +267,10 @@ helm_status mg_level_op(helm_ctx* c, int op, int lvl, void* a, const void* b, vo
 // y = H x (FP64 arithmetic); x of type TX; optional fused partial inner products handled in krylov.cu
 helm_status h_apply(helm_ctx* c, bool x_is_f32, const void* x, double2* y, cudaStream_t st);
 helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st);
+// the same in level 0's storage order (the V-cycle's input)
+helm_status mg_input_from_c128(helm_ctx* c, const double2* in, void* out, cudaStream_t st);
+// out = in (natural order, complex64) with level L's rows x-split
+helm_status xs_permute_c64(const LevelHost& L, const float2* in, float2* out, cudaStream_t st);
 
 // mg_fused.cu
 helm_status autotune_tiles(helm_ctx* c, cudaStream_t st);

@@ -13,6 +13,7 @@
 // whose condition the last kernel of the iteration sets, so a whole solve is one graph launch.
 // No kernel waits on another: there is no device-side spin anywhere.
 #include <cmath>
+#include <cstddef>
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -114,8 +115,21 @@ __device__ __forceinline__ void finish(KrylovState* S, int status) {
   S->done = 1;
 }
 
-template <typename TM> __device__ __forceinline__ void put_mg(void* dst, long i, double2 v) {
-  if (dst) reinterpret_cast<cx<TM>*>(dst)[i] = cconv<TM, double>(v);
+// Element i (natural order) of a V-cycle input in the multigrid precision, stored in level 0's
+// order: x-split rows for an FP32 hierarchy whose finest level is x-split.
+template <typename TM>
+__device__ __forceinline__ void put_mg(const KrylovState* S, void* dst, long i, double2 v) {
+  if (!dst) return;
+  long q = i;
+  if (std::is_same<TM, float>::value) {
+    const int n0 = S->xs_n0;
+    if (n0) {
+      const long row = i < 0x7fffffffL ? (long)((unsigned)i / (unsigned)n0) : i / n0;
+      const int x = (int)(i - row * n0);
+      q = row * n0 + ((x & 1) ? S->xs_h + (x >> 1) : (x >> 1));
+    }
+  }
+  reinterpret_cast<cx<TM>*>(dst)[q] = cconv<TM, double>(v);
 }
 
 // vb_ / vg_: the block's index and the block count of the instance (see VBLK and the bodies)
@@ -153,7 +167,7 @@ __global__ void k_start(KrylovState* S, const double2* __restrict__ b, double2* 
     if (first) r[i] = ri;
     if (rh) rh[i] = ri;
     if (p) { p[i] = mkc<double>(0.0, 0.0); v[i] = mkc<double>(0.0, 0.0); }
-    if (rmg) { if (mg32) put_mg<float>(rmg, i, ri); else put_mg<double>(rmg, i, ri); }
+    if (rmg) { if (mg32) put_mg<float>(S, rmg, i, ri); else put_mg<double>(S, rmg, i, ri); }
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
@@ -218,7 +232,7 @@ __device__ __forceinline__ void bicg_p_body(int vb_, int vg_, const KrylovState*
   GRID_LOOP(i, n) {
     double2 pi = cfma<double>(mbw, v[i], cfma<double>(beta, p[i], r[i]));  // r + beta (p - omega v)
     p[i] = pi;
-    put_mg<TM>(pmg, i, pi);
+    put_mg<TM>(S, pmg, i, pi);
   }
 }
 template <typename TM>
@@ -266,7 +280,7 @@ __device__ __forceinline__ void bicg_s_body(int vb_, int vg_, KrylovState* S, co
   GRID_LOOP(i, n) {
     double2 si = cfma<double>(mal, v[i], r[i]);  // r - alpha v
     sv[i] = si;
-    put_mg<TM>(smg, i, si);
+    put_mg<TM>(S, smg, i, si);
     acc[0].x = fma(si.x, si.x, fma(si.y, si.y, acc[0].x));
   }
   double2 tot[1];
@@ -492,7 +506,7 @@ __global__ void k_idr_mr_upd(KrylovState* S, int kcol, const double2* __restrict
     x[i] = cadd<double>(x[i], dx);
     double2 ri = cadd<double>(r[i], dr);
     r[i] = ri;
-    put_mg<TM>(rmg, i, ri);
+    put_mg<TM>(S, rmg, i, ri);
     acc[0].x = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0].x));
   }
   double2 tot[1];
@@ -573,7 +587,7 @@ __global__ void k_idr_v(const KrylovState* S, const double2* __restrict__ dR, co
 #pragma unroll
     for (int k = 0; k < S_; ++k) acc = cfms<double>(dR[k * n + i], c[k], acc);
     q[i] = acc;
-    put_mg<TM>(vmg, i, cadd<double>(r[i], acc));
+    put_mg<TM>(S, vmg, i, cadd<double>(r[i], acc));
   }
 }
 
@@ -766,7 +780,7 @@ __global__ void k_gm_v0(const KrylovState* S, const double2* __restrict__ r, dou
   GRID_LOOP(i, n) {
     double2 v = mkc<double>(r[i].x / beta, r[i].y / beta);
     V[i] = v;
-    put_mg<TM>(vmg, i, v);
+    put_mg<TM>(S, vmg, i, v);
   }
 }
 
@@ -931,7 +945,7 @@ __global__ void k_gm_next(const KrylovState* S, const double2* __restrict__ w, d
   GRID_LOOP(i, n) {
     double2 v = mkc<double>(w[i].x / hn, w[i].y / hn);
     vk[i] = v;
-    put_mg<TM>(vmg, i, v);
+    put_mg<TM>(S, vmg, i, v);
   }
 }
 
@@ -962,7 +976,7 @@ __global__ void k_gm_comb(const KrylovState* S, const double2* __restrict__ V, v
   GRID_LOOP(p, n) {
     double2 u = mkc<double>(0.0, 0.0);
     for (int i = 0; i < k; ++i) u = cfma<double>(ys[i], V[(size_t)i * n + p], u);
-    put_mg<TM>(umg, p, u);
+    put_mg<TM>(S, umg, p, u);
     if (u64) u64[p] = u;
   }
 }
@@ -1413,6 +1427,17 @@ static helm_status job_pass(SolveJob& j) {
   return HELM_OK;
 }
 
+// the storage order of the V-cycle inputs the kernels write (level 0's)
+static cudaError_t upload_mg_layout(const helm_ctx* c, Workspace* w, cudaStream_t st) {
+  int xs[2] = {0, 0};
+  if (c->pc.kind != HELM_PC_NONE && !c->lv.empty() && c->lv[0].xs) {
+    xs[0] = c->lv[0].n[0];
+    xs[1] = c->lv[0].xs_half();
+  }
+  static_assert(offsetof(KrylovState, xs_h) == offsetof(KrylovState, xs_n0) + sizeof(int), "adjacent");
+  return cudaMemcpyAsync(&w->st->xs_n0, xs, sizeof(xs), cudaMemcpyHostToDevice, st);
+}
+
 template <typename TM>
 static helm_status job_begin_t(SolveJob& j) {
   helm_status s = prepare<TM>(j.c, &j.o, j.k, j.st);
@@ -1430,6 +1455,7 @@ static helm_status job_begin_t(SolveJob& j) {
   HELM_CUDA(cudaMemcpyAsync(&w->st->s, &init.s, sizeof(int), cudaMemcpyHostToDevice, st));
   double* hist = j.o.history;
   HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(upload_mg_layout(j.c, w, st));
   if (j.gm) {
     init.gmm = j.o.s;
     init.gm = w->gm;
@@ -1506,6 +1532,7 @@ static helm_status group_member_begin_t(helm_ctx* c, const helm_solve_opts* o, c
   HELM_CUDA(cudaMemcpyAsync(&w->st->maxmv, &maxmv, sizeof(int), cudaMemcpyHostToDevice, st));
   HELM_CUDA(cudaMemcpyAsync(&w->st->s, &sdim, sizeof(int), cudaMemcpyHostToDevice, st));
   HELM_CUDA(cudaMemcpyAsync(&w->st->hist, &hist, sizeof(double*), cudaMemcpyHostToDevice, st));
+  HELM_CUDA(upload_mg_layout(c, w, st));
   HELM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double2) * c->n, st));
   return HELM_OK;
 }

@@ -30,6 +30,8 @@ struct KrylovState {
   double hn;               // GMRES: norm of the last orthogonalised vector, h_{j+1,j}
   int gmm;                 // GMRES: restart length m
   double2* gm;             // GMRES: Hessenberg matrix, rotations, g, y and the two h passes
+  int xs_n0, xs_h;         // level 0 of an FP32 hierarchy stored x-split: row length and even
+                           // x indices per row (xs_n0 = 0: natural order)
 };
 
 struct Workspace {

@@ -6,7 +6,9 @@
 // Kernels take an optional `skip` flag: when it points to a non-zero word the kernel returns
 // at once.  Inside a captured Krylov iteration this lets the remaining work of a converged
 // solve cost one flag read per thread.
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "stencil.cuh"
 
@@ -29,13 +31,20 @@ template <int DIM> static void cfg(const int n[3], dim3& g, dim3& b) {
   if (i >= (op).n[0] || j >= (op).n[1]) return;                                \
   long p = i + (long)(op).n[0] * (j + (long)(op).n[1] * l);
 
-// y = M x, or y = f - M x when f is given.
-template <typename T, int DIM>
+// y = M x, or y = f - M x when f is given.  XS: x, f and y are stored x-split (h = (n0 + 1) / 2).
+template <typename T, int DIM, bool XS = false>
 __global__ void k_mg_apply(OpView<T> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ f,
                            cx<T>* __restrict__ y, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
   POINT_INDEX(op);
+  if (XS) {
+    const int h = (op.n[0] + 1) >> 1;
+    const long row = p - i, ps = row + xs_pos(i, h);
+    cx<T> v = op_row_at<T, T, DIM>(op, x, i, j, l, ps, p, row + xs_pos(i - 1, h), row + xs_pos(i + 1, h));
+    y[ps] = f ? csub<T>(f[ps], v) : v;
+    return;
+  }
   cx<T> v = op_row<T, T, DIM>(op, x, i, j, l, p);
   y[p] = f ? csub<T>(f[p], v) : v;
 }
@@ -68,8 +77,10 @@ __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
 // thread per point of the colour (thread t of a row takes i = 2t or 2t + 1) and every lane of a
 // warp does arithmetic.  zero_guess (colour 0) writes the red points from a zero guess, f / D; the
 // black sweep that always follows it reads only red neighbours and writes every black point.
-// `wide` (black sweeps only): also write the pair of points of this thread, widened to complex128.
-template <typename T, int DIM>
+// `wide` (black sweeps only): also write the pair of points of this thread, widened to complex128
+// in natural order.  XS: u, f and dinv are stored x-split, so that the points of the colour in a
+// row (thread t: stored at t, or h + t when the colour's x indices are odd) are contiguous.
+template <typename T, int DIM, bool XS = false>
 __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restrict__ f, int colour,
                        int zero_guess, double2* __restrict__ wide, const int* skip) {
   pdl_entry();
@@ -79,28 +90,31 @@ __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restr
   int l = blockIdx.z;
   if (j >= op.n[1]) return;
   const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
-  const int i = 2 * t + ((j + l + colour) & 1);
+  const int h = (op.n[0] + 1) >> 1;
+  const int par = (j + l + colour) & 1;
+  const int i = 2 * t + par;
   if (i < op.n[0]) {
-    const long p = row + i;
+    const long p = XS ? row + (par ? h + t : t) : row + i;
     if (zero_guess) {
       u[p] = cmul<T>(f[p], op.dinv[p]);
       return;
     }
-    cx<T> v = cmul<T>(csub<T>(f[p], op_offdiag<T, T, DIM>(op, u, i, j, l, p)), op.dinv[p]);
+    const cx<T> off = XS ? op_offdiag_xs<T, T, DIM>(op, u, i, j, l, row, h) : op_offdiag<T, T, DIM>(op, u, i, j, l, p);
+    cx<T> v = cmul<T>(csub<T>(f[p], off), op.dinv[p]);
     u[p] = v;
-    if (wide) wide[p] = cconv<double, T>(v);
+    if (wide) wide[row + i] = cconv<double, T>(v);
   }
   // the other point of the pair [2t, 2t + 1] is already final; it is in the grid even when this
   // thread's point lies past an odd row end
-  const int i2 = 2 * t + ((j + l + colour + 1) & 1);
-  if (wide && i2 < op.n[0]) wide[row + i2] = cconv<double, T>(u[row + i2]);
+  const int i2 = 2 * t + 1 - par;
+  if (wide && i2 < op.n[0]) wide[row + i2] = cconv<double, T>(u[XS ? row + (par ? t : h + t) : row + i2]);
 }
 
 // Residual right after the single pre-smoothing sweep from the zero guess, without the diagonal:
 // damped Jacobi left D u = omega f, so r = (1 - omega) f - offdiag(u); red-black Gauss-Seidel
 // left r = 0 on the black points and r = -offdiag(u) on the red ones (their neighbours are all
 // black and were updated last).  RB: one thread per red/black pair of a row.
-template <typename T, int DIM, bool RB>
+template <typename T, int DIM, bool RB, bool XS = false>
 __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ r, T omega, const int* skip) {
   pdl_entry();
@@ -111,12 +125,14 @@ __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
   if (j >= op.n[1]) return;
   const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
   if (RB) {
-    int par = (j + l) & 1;
+    const int par = (j + l) & 1, h = (op.n[0] + 1) >> 1;
     int ir = 2 * t + par, ib = 2 * t + 1 - par;
-    if (ib < op.n[0]) r[row + ib] = mkc<T>(T(0), T(0));
+    // XS: the red point of the pair is stored at t or h + t, the black one in the other half
+    const long pr = XS ? row + (par ? h + t : t) : row + ir, pb = XS ? row + (par ? t : h + t) : row + ib;
+    if (ib < op.n[0]) r[pb] = mkc<T>(T(0), T(0));
     if (ir < op.n[0]) {
-      cx<T> acc = op_offdiag<T, T, DIM>(op, u, ir, j, l, row + ir);
-      r[row + ir] = mkc<T>(-acc.x, -acc.y);
+      cx<T> acc = XS ? op_offdiag_xs<T, T, DIM>(op, u, ir, j, l, row, h) : op_offdiag<T, T, DIM>(op, u, ir, j, l, pr);
+      r[pr] = mkc<T>(-acc.x, -acc.y);
     }
   } else {
     if (t >= op.n[0]) return;
@@ -267,8 +283,10 @@ __global__ void k_resid0_27(OpView<T> op, const cx<T>* __restrict__ u, const cx<
 }
 
 // fine and coarse unknowns per axis, and the coarsening offsets (coarse c is fine 2c + o[a]:
-// o = 1, or 0 on an axis with a Sommerfeld low side)
-struct Dims { int f[3]; int c[3]; int o[3]; };
+// o = 1, or 0 on an axis with a Sommerfeld low side); fh / ch: the fine / coarse level is stored
+// x-split with that many even x indices per row (0: natural order)
+struct Dims { int f[3]; int c[3]; int o[3]; int fh = 0, ch = 0; };
+__device__ __forceinline__ int xpos(int i, int h) { return h ? xs_pos(i, h) : i; }
 
 // Full weighting in index space: coarse unknown c gathers fine unknowns 2c+o-1, 2c+o, 2c+o+1 per
 // axis with weights 1/4, 1/2, 1/4 (tensor product); indices outside the grid are Dirichlet.  The
@@ -291,7 +309,8 @@ __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restric
   auto row_sum = [&](int fj, int fl) -> cx<T> {
     if ((DIM > 1 && (fj < 0 || fj >= d.f[1])) || (DIM > 2 && (fl < 0 || fl >= d.f[2]))) return zero;
     const cx<T>* row = r + (long)d.f[0] * (fj + (long)d.f[1] * fl);
-    return w3(fi >= 0 ? row[fi] : zero, row[fi + 1], fi + 2 < d.f[0] ? row[fi + 2] : zero);
+    return w3(fi >= 0 ? row[xpos(fi, d.fh)] : zero, row[xpos(fi + 1, d.fh)],
+              fi + 2 < d.f[0] ? row[xpos(fi + 2, d.fh)] : zero);
   };
   auto plane_sum = [&](int fl) -> cx<T> {
     if (DIM == 1) return row_sum(0, 0);
@@ -305,7 +324,7 @@ __global__ void k_restrict(Dims d, const cx<T>* __restrict__ r, cx<T>* __restric
     acc = w3(plane_sum(fl), plane_sum(fl + 1), plane_sum(fl + 2));
   }
   const T sc = DIM == 1 ? T(0.25) : (DIM == 2 ? T(0.0625) : T(0.015625));
-  fc[I + (long)d.c[0] * (J + (long)d.c[1] * L)] = cscale<T>(sc, acc);
+  fc[xpos(I, d.ch) + (long)d.c[0] * (J + (long)d.c[1] * L)] = cscale<T>(sc, acc);
 }
 
 // Linear interpolation along one axis: fine index i = 2c + o is coarse node c (weight 1); one
@@ -344,9 +363,9 @@ __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restric
   for (int c3 = 0; c3 < nl; ++c3)
     for (int c2 = 0; c2 < nj; ++c2) {
       const cx<T>* row = ec + (long)d.c[0] * (cj[c2] + (long)d.c[1] * cl[c3]);
-      for (int c1 = 0; c1 < ni; ++c1) acc = cadd<T>(acc, row[ci[c1]]);
+      for (int c1 = 0; c1 < ni; ++c1) acc = cadd<T>(acc, row[xpos(ci[c1], d.ch)]);
     }
-  long p = i + (long)d.f[0] * (j + (long)d.f[1] * l);
+  long p = xpos(i, d.fh) + (long)d.f[0] * (j + (long)d.f[1] * l);
   if (overwrite) u[p] = cscale<T>(w, acc);
   else {
     cx<T> uo = u[p];
@@ -388,10 +407,39 @@ __global__ void k_widen(const float2* __restrict__ a, double2* __restrict__ b, l
   if (p < n) b[p] = cconv<double, float>(a[p]);
 }
 
+// Between natural and x-split order (h even x indices per row of n0), converting the element type
+// on the way: TO_XS reads natural and writes x-split, otherwise the reverse.  One thread per point
+// of a row, so both sides are coalesced.
+template <typename TI, typename TO, bool TO_XS>
+__global__ void k_xs_convert(const cx<TI>* __restrict__ a, cx<TO>* __restrict__ b, int n0, long rows,
+                             const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const long r = blockIdx.y + (long)gridDim.y * blockIdx.z;
+  if (i >= n0 || r >= rows) return;
+  const long row = r * n0;
+  const long q = row + xs_pos(i, (n0 + 1) >> 1);
+  if (TO_XS) b[q] = cconv<TO, TI>(a[row + i]);
+  else b[row + i] = cconv<TO, TI>(a[q]);
+}
+
 // ---- host side -------------------------------------------------------------------------
 
 static void widen_c64(const helm_ctx*, const float2* a, double2* b, long n, const int* skip, cudaStream_t st) {
   launch_pdl(k_widen, dim3((int)((n + 255) / 256)), dim3(256), 0, st, a, b, n, skip);
+}
+
+// a (level L, natural order when to_xs, else x-split) -> b in the other order, element type TO
+template <typename TI, typename TO>
+static void xs_convert(const LevelHost& L, const cx<TI>* a, cx<TO>* b, bool to_xs, const int* skip, cudaStream_t st) {
+  const long rows = L.ntot / L.n[0];
+  const int gy = (int)std::min<long>(rows, 65535);
+  const int gz = (int)((rows + gy - 1) / gy);
+  const int thr = std::min(256, (L.n[0] + 31) / 32 * 32);
+  dim3 g((L.n[0] + thr - 1) / thr, gy, gz);
+  if (to_xs) launch_pdl(k_xs_convert<TI, TO, true>, g, dim3(thr), 0, st, a, b, L.n[0], rows, skip);
+  else launch_pdl(k_xs_convert<TI, TO, false>, g, dim3(thr), 0, st, a, b, L.n[0], rows, skip);
 }
 
 template <typename T>
@@ -406,6 +454,7 @@ template <typename T, int DIM> struct Launch {
     dim3 g, b; cfg<DIM>(L.n, g, b);
     if (DIM == 2 && is9<T>(L)) launch_pdl(k_apply9<T>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
     else if (DIM == 3 && is9<T>(L)) launch_pdl(k_apply27<T>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
+    else if (DIM == 3 && L.xs) launch_pdl(k_mg_apply<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
     else launch_pdl(k_mg_apply<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), x, f, y, skip);
   }
   static void jacobi(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* un, T omega, double2* wide,
@@ -420,7 +469,8 @@ template <typename T, int DIM> struct Launch {
                    const int* skip, cudaStream_t st) {
     int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
     dim3 g, b; cfg<DIM>(half, g, b);
-    launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
+    if (DIM == 3 && L.xs) launch_pdl(k_rbgs<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
+    else launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
   }
   static void resid0(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* r, T omega, bool rb, const int* skip,
                      cudaStream_t st) {
@@ -428,7 +478,8 @@ template <typename T, int DIM> struct Launch {
     dim3 g, b;
     if (rb) {
       cfg<DIM>(half, g, b);
-      launch_pdl(k_resid0<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+      if (DIM == 3 && L.xs) launch_pdl(k_resid0<T, DIM, true, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+      else launch_pdl(k_resid0<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
     } else {
       cfg<DIM>(L.n, g, b);
       if (DIM == 2 && is9<T>(L)) launch_pdl(k_resid0_9<T>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
@@ -439,11 +490,13 @@ template <typename T, int DIM> struct Launch {
   }
   static void restrict_(const LevelHost& F, const LevelHost& C, const cx<T>* r, cx<T>* fc, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
+    d.fh = F.xs_half(); d.ch = C.xs_half();
     dim3 g, b; cfg<DIM>(C.n, g, b);
     launch_pdl(k_restrict<T, DIM>, dim3(g), dim3(b), 0, st, d, r, fc, skip);
   }
   static void prolong(const LevelHost& F, const LevelHost& C, const cx<T>* ec, cx<T>* u, int overwrite, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
+    d.fh = F.xs_half(); d.ch = C.xs_half();
     dim3 g, b; cfg<DIM>(F.n, g, b);
     launch_pdl(k_prolong<T, DIM>, dim3(g), dim3(b), 0, st, d, ec, u, overwrite, skip);
   }
@@ -587,12 +640,37 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
   vcycle_level<T>(c, l + 1, fc, C.u, false, skip, st);
   prolong_any<T>(L, C, (const cx<T>*)C.u, b[cur], pc.nu1 > 0 ? 0 : 1, skip, st);
   smooth<T>(c, L, b, &cur, f, pc.nu2, false, skip, st, wide);
-  if (wide && pc.nu2 == 0) widen_c64(c, (const float2*)b[cur], wide, L.ntot, skip, st);
+  if (wide && pc.nu2 == 0) {
+    if (L.xs) xs_convert<float, double>(L, (const float2*)b[cur], wide, false, skip, st);
+    else widen_c64(c, (const float2*)b[cur], wide, L.ntot, skip, st);
+  }
 }
 
 template <typename T>
 helm_status mg_vcycle(helm_ctx* c, const cx<T>* f0, void* u0, bool u0_f64, const int* skip, cudaStream_t st) {
-  vcycle_level<T>(c, 0, f0, u0, u0_f64 && !std::is_same<T, double>::value, skip, st);
+  const bool wide = u0_f64 && !std::is_same<T, double>::value;
+  vcycle_level<T>(c, 0, f0, u0, wide, skip, st);
+  const LevelHost& L = c->lv[0];
+  if (L.xs && !wide) {  // an x-split result in the multigrid precision: back to natural order
+    HELM_CUDA(cudaMemcpyAsync(L.w, u0, sizeof(cx<T>) * L.ntot, cudaMemcpyDeviceToDevice, st));
+    xs_convert<T, T>(L, (const cx<T>*)L.w, (cx<T>*)u0, false, skip, st);
+  }
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status xs_permute_c64(const LevelHost& L, const float2* in, float2* out, cudaStream_t st) {
+  xs_convert<float, float>(L, in, out, true, nullptr, st);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+// the V-cycle input on level 0 from a complex128 vector: converted to the multigrid precision, in
+// the level's storage order
+helm_status mg_input_from_c128(helm_ctx* c, const double2* in, void* out, cudaStream_t st) {
+  const LevelHost& L = c->lv[0];
+  if (!L.xs) return convert_c128_to_mg(c, in, out, st);
+  xs_convert<double, float>(L, in, (float2*)out, true, nullptr, st);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
@@ -604,8 +682,14 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
                               cudaStream_t st) {
   int nl = (int)c->lv.size();
   if (lvl < 0 || lvl >= nl) return HELM_ERR_ARG;
+  const bool stored = (op & HELM_OP_STORED) != 0;
+  op &= ~HELM_OP_STORED;
   const LevelHost& L = c->lv[lvl];
-  Ops<T> o{L, L.dim};
+  // vectors in natural order: the index-only kernels run on a natural view of the levels (the
+  // tables they read, phi and the stored diagonal, are natural on every level)
+  LevelHost Ln = L, Cn = lvl + 1 < nl ? c->lv[lvl + 1] : L;
+  if (!stored) Ln.xs = Cn.xs = 0;
+  Ops<T> o{Ln, Ln.dim};
   cx<T>* A = (cx<T>*)a;
   const cx<T>* B = (const cx<T>*)bb;
   cx<T>* O = (cx<T>*)out;
@@ -615,15 +699,42 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
     case HELM_OP_SMOOTH:
     case HELM_OP_SMOOTH0: {
       if (!A || !B || count < 0) return HELM_ERR_ARG;
-      cx<T>* b2[2] = {A, (cx<T>*)L.w};
+      // the sweeps read the level's reciprocal diagonal in its storage order: natural vectors of
+      // an x-split level go through two x-split copies
+      const bool conv = L.xs && !stored;
+      std::vector<DevBlock> tmp(2);
+      cx<T>* ua = A;
+      const cx<T>* fb = B;
+      if (conv) {
+        void *t0 = nullptr, *t1 = nullptr;
+        helm_status as = dev_alloc(&t0, sizeof(cx<T>) * L.ntot, st, &tmp[0]);
+        if (as == HELM_OK) as = dev_alloc(&t1, sizeof(cx<T>) * L.ntot, st, &tmp[1]);
+        if (as != HELM_OK) { dev_free_all(tmp, st); return as; }
+        ua = (cx<T>*)t0;
+        fb = (const cx<T>*)t1;
+        xs_convert<T, T>(L, A, ua, true, nullptr, st);
+        xs_convert<T, T>(L, B, (cx<T>*)t1, true, nullptr, st);
+      }
+      cx<T>* b2[2] = {ua, (cx<T>*)L.w};
       int cur = 0;
-      smooth<T>(c, L, b2, &cur, B, count, op == HELM_OP_SMOOTH0, nullptr, st);
-      if (cur == 1) HELM_CUDA(cudaMemcpyAsync(A, L.w, sizeof(cx<T>) * L.ntot, cudaMemcpyDeviceToDevice, st));
+      smooth<T>(c, L, b2, &cur, fb, count, op == HELM_OP_SMOOTH0, nullptr, st);
+      if (cur == 1) HELM_CUDA(cudaMemcpyAsync(ua, L.w, sizeof(cx<T>) * L.ntot, cudaMemcpyDeviceToDevice, st));
+      if (conv) {
+        xs_convert<T, T>(L, ua, A, false, nullptr, st);
+        HELM_CUDA(cudaGetLastError());
+        dev_free_all(tmp, st);
+      }
       break;
     }
-    case HELM_OP_RESTRICT: if (lvl >= nl - 1 || !A || !O) return HELM_ERR_ARG; restrict_any<T>(L, c->lv[lvl + 1], A, O, nullptr, st); break;
-    case HELM_OP_PROLONG: if (lvl >= nl - 1 || !A || !B) return HELM_ERR_ARG; prolong_any<T>(L, c->lv[lvl + 1], B, A, 0, nullptr, st); break;
+    case HELM_OP_RESTRICT: if (lvl >= nl - 1 || !A || !O) return HELM_ERR_ARG; restrict_any<T>(Ln, Cn, A, O, nullptr, st); break;
+    case HELM_OP_PROLONG: if (lvl >= nl - 1 || !A || !B) return HELM_ERR_ARG; prolong_any<T>(Ln, Cn, B, A, 0, nullptr, st); break;
     case HELM_OP_COARSE: if (lvl != nl - 1 || !A || !O) return HELM_ERR_ARG; coarse_solve<T>(c, A, O, nullptr, st); break;
+    case HELM_OP_TO_STORED:
+    case HELM_OP_FROM_STORED:
+      if (!A || !O || A == O) return HELM_ERR_ARG;
+      if (!L.xs) HELM_CUDA(cudaMemcpyAsync(O, A, sizeof(cx<T>) * L.ntot, cudaMemcpyDeviceToDevice, st));
+      else xs_convert<T, T>(L, A, O, op == HELM_OP_TO_STORED, nullptr, st);
+      break;
     case HELM_OP_DOWN:
       if (lvl >= nl - 1 || L.dim != 2 || c->pc.nu1 != 1 || L.stg64 || L.any_offset0() || !A || !B || !O)
         return HELM_ERR_ARG;

@@ -85,7 +85,7 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
     }
     bytes += (size_t)last * last * esz;     // coarse inverse
     bytes += (size_t)last * last * 32 + 4;  // its FP64 factorisation (transient)
-    if (esz == 8) bytes += (size_t)N * 8;   // conversion buffer
+    if (esz == 8) bytes += (size_t)N * 16;  // the two-vector scratch of an FP32 hierarchy
   }
   // Krylov workspace
   if (o->method == HELM_IDR) bytes += (size_t)N * ((5 + 3 * (size_t)o->s) * 16 + esz);

@@ -742,6 +742,8 @@ helm_status build_operator(helm_ctx* c, const helm_kspec* k, cudaStream_t st) {
   return HELM_OK;
 }
 
+static helm_status tune_and_lay_out(helm_ctx* c, cudaStream_t st);
+
 helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   const helm_precond& pc = c->pc;
   if (pc.kind == HELM_PC_NONE) return HELM_OK;
@@ -879,7 +881,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
     if (c->fdm.on) {
       c->nco = 0;
       c->tail_first = (int)c->lv.size();  // the one-block tail needs the dense inverse
-      return autotune_tiles(c, st);
+      return tune_and_lay_out(c, st);
     }
   }
   if (Cst.ntot > HELM_COARSE_MAX_UNKNOWNS) {
@@ -944,7 +946,37 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   }
   c->tail_first = f32 ? tail_first_level<float>(c) : tail_first_level<double>(c);
   if (galerkin) c->tail_first = (int)c->lv.size();  // the one-block tail runs 5-point rows only
-  return autotune_tiles(c, st);
+  return tune_and_lay_out(c, st);
+}
+
+// Storage order of the levels, fixed once the tail depth is known: on a 3D FP32 hierarchy with
+// red-black Gauss-Seidel, every 7-point level above the coarsest one and the one-block tail stores
+// its rows x-split (even x indices first), its reciprocal diagonal permuted to match.
+static helm_status assign_layouts(helm_ctx* c, cudaStream_t st) {
+  const helm_precond& pc = c->pc;
+  if (pc.kind == HELM_PC_NONE || pc.mg_dtype != HELM_C64 || pc.smoother != HELM_SM_RBGS) return HELM_OK;
+  const int nl = (int)c->lv.size();
+  const int tail = (pc.flags & HELM_PF_UNFUSED) ? nl : c->tail_first;  // unfused: no level runs in the tail
+  for (int l = 0; l < nl - 1 && l < tail; ++l) {
+    LevelHost& L = c->lv[l];
+    if (L.dim != 3 || L.stg64 || L.xs) continue;
+    void* tmp = nullptr;
+    DevBlock blk;
+    helm_status s = dev_alloc(&tmp, sizeof(float2) * L.ntot, st, &blk);
+    if (s != HELM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(tmp, L.dinv32, sizeof(float2) * L.ntot, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) s = xs_permute_c64(L, (const float2*)tmp, L.dinv32, st);
+    dev_free(blk, st);
+    HELM_CUDA(e);
+    if (s != HELM_OK) return s;
+    L.xs = 1;
+  }
+  return HELM_OK;
+}
+
+static helm_status tune_and_lay_out(helm_ctx* c, cudaStream_t st) {
+  helm_status s = autotune_tiles(c, st);
+  return s == HELM_OK ? assign_layouts(c, st) : s;
 }
 
 helm_status convert_c128_to_mg(helm_ctx* c, const double2* in, void* out, cudaStream_t st) {

@@ -16,9 +16,17 @@ __device__ __forceinline__ bool op_uniform(const OpView<T>& op, int i, int j, in
   return u;
 }
 
+// Position of x index i in a row stored x-split (the red-black levels of 3D FP32 hierarchies):
+// the even indices first, then the odd ones, h = (n0 + 1) / 2 of them even, so that the points of
+// one colour in a row are contiguous.
+__device__ __forceinline__ int xs_pos(int i, int h) { return (i & 1) ? h + (i >> 1) : (i >> 1); }
+
+// Off-diagonal sum in the uniform interior; the x neighbours sit at pxm / pxp (p - 1 / p + 1 in
+// natural order), the y and z neighbours one row or plane away.
 template <typename T, typename TX, int DIM>
-__device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const cx<TX>* __restrict__ x, long p) {
-  cx<T> sx = cadd<T>(cconv<T, TX>(x[p - 1]), cconv<T, TX>(x[p + 1]));
+__device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const cx<TX>* __restrict__ x, long p,
+                                                    long pxm, long pxp) {
+  cx<T> sx = cadd<T>(cconv<T, TX>(x[pxm]), cconv<T, TX>(x[pxp]));
   cx<T> sy, sz;
   if (DIM > 1) {
     long st = op.n[0];
@@ -44,29 +52,39 @@ __device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const c
   if (DIM > 2) acc = cfma<T>(op.ua[2], sz, acc);
   return acc;
 }
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_offdiag_uniform(const OpView<T>& op, const cx<TX>* __restrict__ x, long p) {
+  return op_offdiag_uniform<T, TX, DIM>(op, x, p, p - 1, p + 1);
+}
 
 // Off-diagonal sum of a point outside the uniform interior.  Axes along which the point still
 // lies in the uniform run take the shared coefficient on the neighbour pair (one product instead
 // of two); the others read their Shortley-Weller row, skipping Dirichlet neighbours.
 template <typename T, typename TX, int DIM>
 __device__ __forceinline__ cx<T> op_offdiag_general(const OpView<T>& op, const cx<TX>* __restrict__ x,
-                                                    int i, int j, int l, long p) {
+                                                    int i, int j, int l, long p, long pxm, long pxp) {
   cx<T> acc = mkc<T>(T(0), T(0));
   const int idx[3] = {i, j, l};
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     const long st = a == 0 ? 1 : (a == 1 ? (long)op.n[0] : (long)op.n[0] * op.n[1]);
+    const long qm = a == 0 ? pxm : p - st, qp = a == 0 ? pxp : p + st;
     const int q = idx[a];
     if (q >= op.ulo[a] && q <= op.uhi[a]) {
-      cx<T> pr = cadd<T>(cconv<T, TX>(x[p - st]), cconv<T, TX>(x[p + st]));
+      cx<T> pr = cadd<T>(cconv<T, TX>(x[qm]), cconv<T, TX>(x[qp]));
       acc = op.uniform_real ? mkc<T>(fma(op.ua[a].x, pr.x, acc.x), fma(op.ua[a].x, pr.y, acc.y))
                             : cfma<T>(op.ua[a], pr, acc);
     } else {
-      if (q > 0) acc = cfma<T>(op.am[a][q], cconv<T, TX>(x[p - st]), acc);
-      if (q < op.n[a] - 1) acc = cfma<T>(op.ap[a][q], cconv<T, TX>(x[p + st]), acc);
+      if (q > 0) acc = cfma<T>(op.am[a][q], cconv<T, TX>(x[qm]), acc);
+      if (q < op.n[a] - 1) acc = cfma<T>(op.ap[a][q], cconv<T, TX>(x[qp]), acc);
     }
   }
   return acc;
+}
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_offdiag_general(const OpView<T>& op, const cx<TX>* __restrict__ x,
+                                                    int i, int j, int l, long p) {
+  return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p, p - 1, p + 1);
 }
 
 template <typename T, typename TX, int DIM>
@@ -76,16 +94,28 @@ __device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* _
   return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p);
 }
 
+// The same on an x-split row: the point is stored at p = row + xs_pos(i, h).  A neighbour index
+// outside the row (i = 0 or n0 - 1) maps to a position that is never read.
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_offdiag_xs(const OpView<T>& op, const cx<TX>* __restrict__ x, int i, int j,
+                                               int l, long row, int h) {
+  const long p = row + xs_pos(i, h), pxm = row + xs_pos(i - 1, h), pxp = row + xs_pos(i + 1, h);
+  if (op_uniform<DIM>(op, i, j, l)) return op_offdiag_uniform<T, TX, DIM>(op, x, p, pxm, pxp);
+  return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p, pxm, pxp);
+}
+
 // (A x)_P.  In the uniform interior of an operator with real coefficients (H) the diagonal
 // ud - s phi_P is real and multiplies x_P with two FMAs; elsewhere the stored diagonal is read
 // when the operator has one.
+// x is read at p (its x neighbours at pxm / pxp), the level's per-point tables (phi, the stored
+// diagonal) at pn: p = pn in natural order.
 template <typename T, typename TX, int DIM>
-__device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __restrict__ x, int i,
-                                        int j, int l, long p) {
+__device__ __forceinline__ cx<T> op_row_at(const OpView<T>& op, const cx<TX>* __restrict__ x, int i, int j,
+                                           int l, long p, long pn, long pxm, long pxp) {
   const cx<T> xp = cconv<T, TX>(x[p]);
-  const T ph = op.phi ? op.phi[p] : op.phi0;
+  const T ph = op.phi ? op.phi[pn] : op.phi0;
   if (op_uniform<DIM>(op, i, j, l)) {
-    const cx<T> off = op_offdiag_uniform<T, TX, DIM>(op, x, p);
+    const cx<T> off = op_offdiag_uniform<T, TX, DIM>(op, x, p, pxm, pxp);
     if (op.uniform_real) {
       const T d = fma(-ph, op.s.x, op.ud.x);
       return mkc<T>(fma(d, xp.x, off.x), fma(d, xp.y, off.y));
@@ -94,15 +124,20 @@ __device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __res
   }
   cx<T> d;
   if (op.dg) {
-    d = op.dg[p];  // the stored diagonal
+    d = op.dg[pn];  // the stored diagonal
   } else {
     d = op.a0[0][i];
     if (DIM > 1) d = cadd<T>(d, op.a0[1][j]);
     if (DIM > 2) d = cadd<T>(d, op.a0[2][l]);
     d = cadd<T>(d, cconv<T, double>(somm_diag(op, i, j, l, (double)ph)));
-    d = op.phim ? csub<T>(d, cmul<T>(op.s, mkc<T>(ph, (T)op.phim[p]))) : csub<T>(d, cscale<T>(ph, op.s));
+    d = op.phim ? csub<T>(d, cmul<T>(op.s, mkc<T>(ph, (T)op.phim[pn]))) : csub<T>(d, cscale<T>(ph, op.s));
   }
-  return cfma<T>(d, xp, op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p));
+  return cfma<T>(d, xp, op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p, pxm, pxp));
+}
+template <typename T, typename TX, int DIM>
+__device__ __forceinline__ cx<T> op_row(const OpView<T>& op, const cx<TX>* __restrict__ x, int i,
+                                        int j, int l, long p) {
+  return op_row_at<T, TX, DIM>(op, x, i, j, l, p, p, p - 1, p + 1);
 }
 
 // 2D off-diagonal part from the four neighbour values (staged in shared memory by the fused

@@ -513,6 +513,94 @@ def test_large_3d_workload_sampled():
     h32.close()
 
 
+XS_CASES = [
+    ((41, 30, 27), ((3, 4), (2, 0), (5, 1)), "bump"),   # 48 x 32 x 33 unknowns: even row length
+    ((26, 19, 22), ((2, 3), (1, 2), (0, 3)), "const"),  # 31 x 22 x 25: odd row length
+]
+
+
+def _xsplit(v, shape):
+    """Rows of shape[0] points with their even x indices first, then the odd ones."""
+    a = np.asarray(v).reshape(-1, shape[0])
+    return np.concatenate([a[:, 0::2], a[:, 1::2]], axis=1).reshape(-1)
+
+
+@pytest.mark.parametrize("shape", XS_CASES)
+def test_xsplit_levels_3d_fp32(shape):
+    """The FP32 red-black levels of a 3D hierarchy above the coarsest store their rows x-split:
+    the storage order is exactly that permutation on each such level (the coarsest stays natural),
+    the level kernels on stored vectors give bitwise the natural results permuted, and the
+    V-cycle (complex64 and widened output) and mixed-precision solves match the oracle."""
+    n_int, nl, kind = shape
+    p = hi.make_problem(3, n_int, nl, theta_gamma=0.5, k0=5.0, phi_kind=kind, rhs="point", seed=4,
+                        bump_centre=(0.4, 0.6, 0.5))
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_RBGS)
+    o = Oracle(p, pc)
+    h = Helm(p, pc, mg_dtype="c64", fused=False)
+    assert h.nlev >= 3
+    dt = torch.complex64
+    rng = np.random.default_rng(9)
+    rnd = lambda n: (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    S = L.HELM_OP_STORED
+    for lvl in range(h.nlev):
+        shp = h.level_shape(lvl)
+        n = int(np.prod(shp))
+        split = lvl < h.nlev - 1
+        perm = (lambda v, s=shp: _xsplit(v, s)) if split else (lambda v: np.asarray(v))
+        a, b = rnd(n), rnd(n)
+        st = torch.empty(n, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_TO_STORED, lvl, cu(a, dt), None, st)
+        assert np.array_equal(st.cpu().numpy(), perm(a)), lvl
+        back = torch.empty_like(st)
+        h.level_op(L.HELM_OP_FROM_STORED, lvl, st, None, back)
+        assert np.array_equal(back.cpu().numpy(), a)
+        if not split:
+            continue
+        for op in (L.HELM_OP_SMOOTH, L.HELM_OP_SMOOTH0):
+            un, us = cu(a, dt), cu(perm(a), dt)
+            h.level_op(op, lvl, un, cu(b, dt), None, count=2)
+            h.level_op(op | S, lvl, us, cu(perm(b), dt), None, count=2)
+            assert np.array_equal(us.cpu().numpy(), perm(un.cpu().numpy())), (lvl, op)
+        for op, bb in ((L.HELM_OP_APPLY, None), (L.HELM_OP_RESIDUAL, b)):
+            on, os_ = torch.empty(n, dtype=dt, device="cuda"), torch.empty(n, dtype=dt, device="cuda")
+            h.level_op(op, lvl, cu(a, dt), None if bb is None else cu(bb, dt), on)
+            h.level_op(op | S, lvl, cu(perm(a), dt), None if bb is None else cu(perm(bb), dt), os_)
+            assert np.array_equal(os_.cpu().numpy(), perm(on.cpu().numpy())), (lvl, op)
+        shc = h.level_shape(lvl + 1)
+        nc = int(np.prod(shc))
+        permc = (lambda v, s=shc: _xsplit(v, s)) if lvl + 1 < h.nlev - 1 else (lambda v: np.asarray(v))
+        fn, fs = torch.empty(nc, dtype=dt, device="cuda"), torch.empty(nc, dtype=dt, device="cuda")
+        h.level_op(L.HELM_OP_RESTRICT, lvl, cu(a, dt), None, fn)
+        h.level_op(L.HELM_OP_RESTRICT | S, lvl, cu(perm(a), dt), None, fs)
+        assert np.array_equal(fs.cpu().numpy(), permc(fn.cpu().numpy())), lvl
+        check(fn.cpu().numpy(), o.restrict(lvl, a.astype(np.complex128)), 2e-5)
+        ec = rnd(nc)
+        un, us = cu(a, dt), cu(perm(a), dt)
+        h.level_op(L.HELM_OP_PROLONG, lvl, un, cu(ec, dt))
+        h.level_op(L.HELM_OP_PROLONG | S, lvl, us, cu(permc(ec), dt))
+        assert np.array_equal(us.cpu().numpy(), perm(un.cpu().numpy())), lvl
+        check(un.cpu().numpy(), o.prolong_add(lvl, ec.astype(np.complex128), a.astype(np.complex128)), 2e-5)
+    r = hi.random_vector(p.n, 21)
+    ref = o.vcycle(r)
+    check(h.vcycle(cu(r)).cpu().numpy().astype(np.complex128), ref, 5e-5)
+    check(h.vcycle(cu(r), dtype=torch.complex128).cpu().numpy(), ref, 5e-5)
+    # every Krylov method feeds the cycle through its x-split input: the solution matches the
+    # oracle's, and the matvec count is that of the natural-order FP64 hierarchy up to rounding
+    x_ref, _ = o.solve(p.b, hi.SolveOpts(method=hi.BICGSTAB, tol=1e-12, maxmv=3000))
+    sh = hi.shadow_space(p.n, 4)
+    h64 = Helm(p, pc, mg_dtype="c128", fused=False)
+    for method in (hi.BICGSTAB, hi.IDR, hi.GMRES):
+        kw = dict(method=method, s=(4 if method == hi.IDR else 30), tol=1e-8, maxmv=1500,
+                  shadow=sh if method == hi.IDR else None)
+        x, info = h.solve(cu(p.b), **kw)
+        _, info64 = h64.solve(cu(p.b), **kw)
+        assert info.status == 0 and info.rel_res_true < 1e-8
+        assert rel(x.cpu().numpy(), x_ref) < 1e-6, (method, rel(x.cpu().numpy(), x_ref))
+        assert abs(info.matvecs - info64.matvecs) <= max(3, info64.matvecs // 10), (method, info.matvecs, info64.matvecs)
+    h64.close()
+    h.close()
+
+
 def test_batch256_workload_sampled():
     """All 256 instances of the uneven batch in one helm_solve_batch call (FP32 multigrid, the
     benchmark's configuration); a seeded sample of them certified by the oracle's own residual."""
