@@ -110,6 +110,130 @@ __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restr
   if (wide && i2 < op.n[0]) wide[row + i2] = cconv<double, T>(u[XS ? row + (par ? t : h + t) : row + i2]);
 }
 
+// Red-black half-sweep on an x-split 3D level, marching along z: a thread owns the pair of
+// columns (2t, 2t + 1) of row j and walks the planes [l0, l0 + lz).  In plane p the colour's
+// point is column cur(p) = (j + p + colour) & 1 of the pair, and the pair's other-colour value
+// V(p) (column 1 - cur(p)) is the point's in-pair x neighbour and, since the colour flips from
+// plane to plane, the z neighbour of the colour's points in planes p - 1 and p + 1: a window of
+// three V values in registers serves both, one new load per plane.  The other x neighbour is
+// the V of the adjacent thread of the row segment (a shuffle; the segment's end lanes load it),
+// the y neighbours are read from the rows j -+ 1, and every neighbour enters through its axis
+// table (a neighbour outside the grid has value zero; its table entry is finite).  A row is a
+// segment of W lanes (W = 32 or 16); the two segments of a 16-lane warp take rows of equal parity
+// (j and j + 4), so cur is uniform over the warp and each plane's step is compiled for its column.
+// RESID: instead of updating u, write the residual after the zero-guess sweep to r (-offdiag(u)
+// on the colour, zero on the other one).  WIDE (sweeps only): both points of the pair also written
+// widened to complex128 in natural order.  Every load of plane p + 1 (f, 1/D, the y neighbours, an
+// end lane's x neighbour, V(p + 2)) is issued before plane p is computed: they read the other
+// colour or read-only data, which this half-sweep never writes.  IDX: the offset type (int when
+// N < 2^31).
+template <typename T, bool RESID, bool WIDE, int W, typename IDX>
+__global__ void __launch_bounds__(128) k_rbgs3z(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
+                                                cx<T>* __restrict__ r, int colour, int lz,
+                                                double2* __restrict__ wide, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  constexpr int SEGS = 32 / W;  // rows per warp
+  const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
+  const int h = (n0 + 1) >> 1;
+  const int sl = threadIdx.x % W, seg = threadIdx.x / W;
+  const int t = blockIdx.x * W + sl;
+  const int j = blockIdx.y * (4 * SEGS) + seg * 4 + threadIdx.y;
+  const int l0 = blockIdx.z * lz, l1 = min(l0 + lz, n2);
+  const cx<T> zero = mkc<T>(T(0), T(0));
+  const bool row_ok = j < n1;
+  const bool has0 = row_ok && 2 * t < n0, has1 = row_ok && 2 * t + 1 < n0;
+  const bool ylo = j > 0, yhi = j < n1 - 1;
+  const bool xlo = row_ok && t > 0 && t - 1 < h && sl == 0, xhi = row_ok && 2 * t + 2 < n0 && sl == W - 1;
+  const cx<T> axm0 = has0 ? op.am[0][2 * t] : zero, axp0 = has0 ? op.ap[0][2 * t] : zero;
+  const cx<T> axm1 = has1 ? op.am[0][2 * t + 1] : zero, axp1 = has1 ? op.ap[0][2 * t + 1] : zero;
+  const cx<T> aym = row_ok ? op.am[1][j] : zero, ayp = row_ok ? op.ap[1][j] : zero;
+  const IDX P = (IDX)n0 * n1;
+  const IDX rowoff = (IDX)n0 * (row_ok ? j : 0);
+  // the pair's two columns in this row (x-split positions t and h + t)
+  cx<T>* const ue = u + rowoff + t;
+  cx<T>* const uo = u + rowoff + h + t;
+  const cx<T>* const fe = RESID ? nullptr : f + rowoff + t;
+  const cx<T>* const fo = RESID ? nullptr : f + rowoff + h + t;
+  const cx<T>* const de = op.dinv + rowoff + t;
+  const cx<T>* const dd = op.dinv + rowoff + h + t;
+  auto vload = [&](int q) -> cx<T> {  // V(q): the other colour's column of plane q
+    if (q < 0 || q >= n2) return zero;
+    const bool odd = ((j + q + colour) & 1) == 0;
+    return (odd ? has1 : has0) ? (odd ? uo : ue)[(IDX)q * P] : zero;
+  };
+  // the operands of the colour's point of a plane (offset oo, column C)
+  struct Pre { cx<T> f, d, ym, yp, xe; };
+  auto prefetch = [&](auto cc, IDX oo) -> Pre {
+    constexpr int C = decltype(cc)::value;
+    const cx<T>* const uc = C ? uo : ue;
+    const bool hc = C ? has1 : has0;
+    Pre q;
+    q.f = !RESID && hc ? (C ? fo : fe)[oo] : zero;
+    q.d = !RESID && hc ? (C ? dd : de)[oo] : zero;
+    q.ym = hc && ylo ? uc[oo - n0] : zero;
+    q.yp = hc && yhi ? uc[oo + n0] : zero;
+    if (C == 0) q.xe = xlo ? uo[oo - 1] : zero;  // column 2t - 1
+    else q.xe = xhi ? ue[oo + 1] : zero;         // column 2t + 2
+    return q;
+  };
+  int cur = (j + l0 + colour) & 1;
+  IDX o = (IDX)l0 * P;
+  cx<T> vm = vload(l0 - 1), v0 = vload(l0), vp = vload(l0 + 1);
+  Pre pre = cur ? prefetch(std::integral_constant<int, 1>(), o) : prefetch(std::integral_constant<int, 0>(), o);
+  auto step = [&](auto cc, int p) {
+    constexpr int C = decltype(cc)::value;
+    cx<T>* const uc = C ? uo : ue;  // the colour's column
+    const bool hc = C ? has1 : has0, ho = C ? has0 : has1;
+    // next plane: its operands, and V(p + 2) (in the other column, like V(p))
+    Pre nx = pre;
+    cx<T> vpp = zero;
+    if (p + 1 < l1) {
+      nx = prefetch(std::integral_constant<int, 1 - C>(), o + P);
+      if (p + 2 < n2 && ho) vpp = (C ? ue : uo)[o + 2 * P];
+    }
+    cx<T> xo;  // the x neighbour outside the pair
+    if (C == 0) {
+      xo.x = __shfl_up_sync(0xffffffffu, v0.x, 1, W);
+      xo.y = __shfl_up_sync(0xffffffffu, v0.y, 1, W);
+      if (sl == 0) xo = pre.xe;
+    } else {
+      xo.x = __shfl_down_sync(0xffffffffu, v0.x, 1, W);
+      xo.y = __shfl_down_sync(0xffffffffu, v0.y, 1, W);
+      if (sl == W - 1) xo = pre.xe;
+    }
+    if (hc) {
+      cx<T> off = cmul<T>(C ? axm1 : axm0, C ? v0 : xo);
+      off = cfma<T>(C ? axp1 : axp0, C ? xo : v0, off);
+      off = cfma<T>(aym, pre.ym, off);
+      off = cfma<T>(ayp, pre.yp, off);
+      off = cfma<T>(op.am[2][p], vm, off);
+      off = cfma<T>(op.ap[2][p], vp, off);
+      if (RESID) {
+        r[(uc - u) + o] = mkc<T>(-off.x, -off.y);
+      } else {
+        const cx<T> v = cmul<T>(csub<T>(pre.f, off), pre.d);
+        uc[o] = v;
+        if (WIDE) wide[rowoff + 2 * t + C + o] = cconv<double, T>(v);
+      }
+    }
+    if (ho) {
+      if (RESID) r[((C ? ue : uo) - u) + o] = zero;
+      else if (WIDE) wide[rowoff + 2 * t + 1 - C + o] = cconv<double, T>(v0);
+    }
+    vm = v0;
+    v0 = vp;
+    vp = vpp;
+    pre = nx;
+  };
+  for (int p = l0; p < l1; ++p) {
+    if (cur) step(std::integral_constant<int, 1>(), p);
+    else step(std::integral_constant<int, 0>(), p);
+    cur ^= 1;
+    o += P;
+  }
+}
+
 // Residual right after the single pre-smoothing sweep from the zero guess, without the diagonal:
 // damped Jacobi left D u = omega f, so r = (1 - omega) f - offdiag(u); red-black Gauss-Seidel
 // left r = 0 on the black points and r = -offdiag(u) on the red ones (their neighbours are all
@@ -449,6 +573,45 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
 // a Galerkin level: 9-point in 2D, 27-point in 3D
 template <typename T> static bool is9(const LevelHost& L) { return L.stg64 != nullptr; }
 
+// the z-marching sweep: row segments of 32 or 16 pairs (whichever idles fewer lanes), 4 warps a
+// block; planes per thread chosen so that the grid holds about 48 warps per SM (fewer planes per
+// thread re-read more window values at the chunk ends)
+template <typename T, bool RESID, bool WIDE, int W, typename IDX>
+static void launch_rbgs3z_g(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
+                            const int* skip, cudaStream_t st);
+template <typename T, bool RESID, int W, typename IDX>
+static void launch_rbgs3z_w(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
+                            const int* skip, cudaStream_t st) {
+  if (wide) {
+    launch_rbgs3z_g<T, RESID, true, W, IDX>(L, u, f, r, colour, wide, skip, st);
+    return;
+  }
+  launch_rbgs3z_g<T, RESID, false, W, IDX>(L, u, f, r, colour, wide, skip, st);
+}
+template <typename T, bool RESID, bool WIDE, int W, typename IDX>
+static void launch_rbgs3z_g(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
+                            const int* skip, cudaStream_t st) {
+  const int h = (L.n[0] + 1) / 2;
+  const int rows_per_block = 4 * (32 / W);
+  const long gx = (h + W - 1) / W, gy = (L.n[1] + rows_per_block - 1) / rows_per_block;
+  const long warps_per_chunk = gx * gy * 4;
+  int lz = 32;
+  while (lz > 2 && warps_per_chunk * ((L.n[2] + lz - 1) / lz) < 152L * 48) lz /= 2;
+  dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((L.n[2] + lz - 1) / lz));
+  launch_pdl(k_rbgs3z<T, RESID, WIDE, W, IDX>, g, dim3(32, 4), 0, st, L.view<T>(), u, f, r, colour, lz, wide, skip);
+}
+template <typename T, bool RESID>
+static void launch_rbgs3z(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
+                          const int* skip, cudaStream_t st) {
+  const int h = (L.n[0] + 1) / 2;
+  const bool w16 = (h + 15) / 16 * 16 < (h + 31) / 32 * 32;
+  const bool i64 = L.ntot >= 0x7fffffffL;
+  if (w16 && !i64) launch_rbgs3z_w<T, RESID, 16, int>(L, u, f, r, colour, wide, skip, st);
+  else if (!i64) launch_rbgs3z_w<T, RESID, 32, int>(L, u, f, r, colour, wide, skip, st);
+  else if (w16) launch_rbgs3z_w<T, RESID, 16, long>(L, u, f, r, colour, wide, skip, st);
+  else launch_rbgs3z_w<T, RESID, 32, long>(L, u, f, r, colour, wide, skip, st);
+}
+
 template <typename T, int DIM> struct Launch {
   static void apply(const LevelHost& L, const cx<T>* x, const cx<T>* f, cx<T>* y, const int* skip, cudaStream_t st) {
     dim3 g, b; cfg<DIM>(L.n, g, b);
@@ -469,7 +632,8 @@ template <typename T, int DIM> struct Launch {
                    const int* skip, cudaStream_t st) {
     int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
     dim3 g, b; cfg<DIM>(half, g, b);
-    if (DIM == 3 && L.xs) launch_pdl(k_rbgs<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
+    if (DIM == 3 && L.xs && !zero) launch_rbgs3z<T, false>(L, u, f, nullptr, colour, wide, skip, st);
+    else if (DIM == 3 && L.xs) launch_pdl(k_rbgs<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
     else launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
   }
   static void resid0(const LevelHost& L, const cx<T>* u, const cx<T>* f, cx<T>* r, T omega, bool rb, const int* skip,
@@ -478,7 +642,7 @@ template <typename T, int DIM> struct Launch {
     dim3 g, b;
     if (rb) {
       cfg<DIM>(half, g, b);
-      if (DIM == 3 && L.xs) launch_pdl(k_resid0<T, DIM, true, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
+      if (DIM == 3 && L.xs) launch_rbgs3z<T, true>(L, const_cast<cx<T>*>(u), nullptr, r, 0, nullptr, skip, st);
       else launch_pdl(k_resid0<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
     } else {
       cfg<DIM>(L.n, g, b);
