@@ -224,7 +224,7 @@ def run_3d(args, torch, ranks, dev, local):
         for h in ctx.values():
             h.close()
         return {"metric": bench.METRIC, "phase": "kernels", "config": {"workload": p.name},
-                "roofline": kern["dominant"], "kernels": kern["table"]}
+                "roofline": kern["dominant"], "roofline_fp32_mg": kern["fp32_mg"], "kernels": kern["table"]}
 
     def step(mg, host=None):
         h = ctx[mg]
@@ -293,7 +293,7 @@ def run_3d(args, torch, ranks, dev, local):
         "gpu_launches": int(sum(i.kernels for i in inf64) + sum(i.kernels for i in inf32)),
     })
     if kern is not None:
-        line.update({"roofline": kern["dominant"], "kernels": kern["table"]})
+        line.update({"roofline": kern["dominant"], "roofline_fp32_mg": kern["fp32_mg"], "kernels": kern["table"]})
     for h in ctx.values():
         h.close()
     return line
@@ -373,7 +373,29 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
            "frac": achieved / fp64_ops_peak, "traffic": H3D_TRAFFIC_BYTES,
            "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
            "launch_us": a["us"]}
-    return {"dominant": dom, "table": table}
+    # the FP32 sweep against the measured copy bandwidth: per point and sweep, f, 1/D and the
+    # other colour's u read and u written, 8 bytes each (x-split rows: no other sector comes along)
+    hbm, hbm_src = _hbm_peak()
+    rb = table["rbgs_sweep_c64"]
+    fp32 = {"kernel": "k_rbgs3z<float> (red and black half-sweeps of the finest level, x-split rows, marching along z)",
+            "bound": "hbm", "achieved": rb["GB/s"], "peak": hbm, "unit": "GB/s", "frac": rb["GB/s"] / hbm,
+            "traffic": RBGS3Z_TRAFFIC_BYTES, "peak_source": hbm_src, "bytes_per_launch": rb["bytes"] / 2,
+            "launch_us": rb["us"] / 2}
+    return {"dominant": dom, "fp32_mg": fp32, "table": table}
+
+
+# DRAM bytes (read + write) of one k_rbgs3z<float> half-sweep on the 160^3 level, from an ncu
+# capture of the current kernel; None whenever it changes.
+RBGS3Z_TRAFFIC_BYTES = 49202176 + 528896
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        peaks = {}
+    return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
 
 
 # ---- batch ---------------------------------------------------------------------------------

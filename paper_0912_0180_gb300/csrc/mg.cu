@@ -151,47 +151,60 @@ __global__ void __launch_bounds__(128) k_rbgs3z(OpView<T> op, cx<T>* __restrict_
   const IDX P = (IDX)n0 * n1;
   const IDX rowoff = (IDX)n0 * (row_ok ? j : 0);
   // the pair's two columns in this row (x-split positions t and h + t)
-  cx<T>* const ue = u + rowoff + t;
-  cx<T>* const uo = u + rowoff + h + t;
-  const cx<T>* const fe = RESID ? nullptr : f + rowoff + t;
-  const cx<T>* const fo = RESID ? nullptr : f + rowoff + h + t;
-  const cx<T>* const de = op.dinv + rowoff + t;
-  const cx<T>* const dd = op.dinv + rowoff + h + t;
+  const IDX ce = rowoff + t, co = rowoff + h + t;
+  const cx<T>* const dv = op.dinv;
   auto vload = [&](int q) -> cx<T> {  // V(q): the other colour's column of plane q
     if (q < 0 || q >= n2) return zero;
     const bool odd = ((j + q + colour) & 1) == 0;
-    return (odd ? has1 : has0) ? (odd ? uo : ue)[(IDX)q * P] : zero;
+    return (odd ? has1 : has0) ? u[(odd ? co : ce) + (IDX)q * P] : zero;
   };
-  // the operands of the colour's point of a plane (offset oo, column C)
-  struct Pre { cx<T> f, d, ym, yp, xe; };
-  auto prefetch = [&](auto cc, IDX oo) -> Pre {
+  // f and 1/D of the colour's point of a plane (offset oo, column C): the streams from DRAM,
+  // fetched two planes ahead
+  auto fd = [&](auto cc, IDX oo, cx<T>& fv, cx<T>& dvv) {
     constexpr int C = decltype(cc)::value;
-    const cx<T>* const uc = C ? uo : ue;
+    const IDX pc = (C ? co : ce) + oo;
     const bool hc = C ? has1 : has0;
-    Pre q;
-    q.f = !RESID && hc ? (C ? fo : fe)[oo] : zero;
-    q.d = !RESID && hc ? (C ? dd : de)[oo] : zero;
-    q.ym = hc && ylo ? uc[oo - n0] : zero;
-    q.yp = hc && yhi ? uc[oo + n0] : zero;
-    if (C == 0) q.xe = xlo ? uo[oo - 1] : zero;  // column 2t - 1
-    else q.xe = xhi ? ue[oo + 1] : zero;         // column 2t + 2
+    fv = !RESID && hc ? f[pc] : zero;
+    dvv = !RESID && hc ? dv[pc] : zero;
+  };
+  // the y neighbours and an end lane's outer x neighbour (mostly cache hits), one plane ahead
+  struct Nb { cx<T> ym, yp, xe; };
+  auto nb = [&](auto cc, IDX oo) -> Nb {
+    constexpr int C = decltype(cc)::value;
+    const IDX pc = (C ? co : ce) + oo;
+    const bool hc = C ? has1 : has0;
+    Nb q;
+    q.ym = hc && ylo ? u[pc - n0] : zero;
+    q.yp = hc && yhi ? u[pc + n0] : zero;
+    if (C == 0) q.xe = xlo ? u[co + oo - 1] : zero;  // column 2t - 1
+    else q.xe = xhi ? u[ce + oo + 1] : zero;         // column 2t + 2
     return q;
   };
   int cur = (j + l0 + colour) & 1;
   IDX o = (IDX)l0 * P;
-  cx<T> vm = vload(l0 - 1), v0 = vload(l0), vp = vload(l0 + 1);
-  Pre pre = cur ? prefetch(std::integral_constant<int, 1>(), o) : prefetch(std::integral_constant<int, 0>(), o);
+  cx<T> vm = vload(l0 - 1), v0 = vload(l0), vp = vload(l0 + 1), vpp = vload(l0 + 2);
+  cx<T> f0, d0, f1 = zero, d1 = zero;
+  Nb pre;
+  if (cur) {
+    fd(std::integral_constant<int, 1>(), o, f0, d0);
+    if (l0 + 1 < l1) fd(std::integral_constant<int, 0>(), o + P, f1, d1);
+    pre = nb(std::integral_constant<int, 1>(), o);
+  } else {
+    fd(std::integral_constant<int, 0>(), o, f0, d0);
+    if (l0 + 1 < l1) fd(std::integral_constant<int, 1>(), o + P, f1, d1);
+    pre = nb(std::integral_constant<int, 0>(), o);
+  }
   auto step = [&](auto cc, int p) {
     constexpr int C = decltype(cc)::value;
-    cx<T>* const uc = C ? uo : ue;  // the colour's column
+    const IDX pc = (C ? co : ce) + o, po = (C ? ce : co) + o;  // the colour's point, the other one
     const bool hc = C ? has1 : has0, ho = C ? has0 : has1;
-    // next plane: its operands, and V(p + 2) (in the other column, like V(p))
-    Pre nx = pre;
-    cx<T> vpp = zero;
-    if (p + 1 < l1) {
-      nx = prefetch(std::integral_constant<int, 1 - C>(), o + P);
-      if (p + 2 < n2 && ho) vpp = (C ? ue : uo)[o + 2 * P];
-    }
+    // plane p + 2 (its colour's column is C again): f, 1/D and V(p + 3) (also column C); plane
+    // p + 1: the neighbours
+    cx<T> f2 = zero, d2 = zero, v3 = zero;
+    if (p + 2 < l1) fd(cc, o + 2 * P, f2, d2);
+    if (p + 3 < n2 && p + 1 < l1 && hc) v3 = u[pc + 3 * P];
+    Nb nx = pre;
+    if (p + 1 < l1) nx = nb(std::integral_constant<int, 1 - C>(), o + P);
     cx<T> xo;  // the x neighbour outside the pair
     if (C == 0) {
       xo.x = __shfl_up_sync(0xffffffffu, v0.x, 1, W);
@@ -210,20 +223,25 @@ __global__ void __launch_bounds__(128) k_rbgs3z(OpView<T> op, cx<T>* __restrict_
       off = cfma<T>(op.am[2][p], vm, off);
       off = cfma<T>(op.ap[2][p], vp, off);
       if (RESID) {
-        r[(uc - u) + o] = mkc<T>(-off.x, -off.y);
+        r[pc] = mkc<T>(-off.x, -off.y);
       } else {
-        const cx<T> v = cmul<T>(csub<T>(pre.f, off), pre.d);
-        uc[o] = v;
+        const cx<T> v = cmul<T>(csub<T>(f0, off), d0);
+        u[pc] = v;
         if (WIDE) wide[rowoff + 2 * t + C + o] = cconv<double, T>(v);
       }
     }
     if (ho) {
-      if (RESID) r[((C ? ue : uo) - u) + o] = zero;
+      if (RESID) r[po] = zero;
       else if (WIDE) wide[rowoff + 2 * t + 1 - C + o] = cconv<double, T>(v0);
     }
     vm = v0;
     v0 = vp;
     vp = vpp;
+    vpp = v3;
+    f0 = f1;
+    d0 = d1;
+    f1 = f2;
+    d1 = d2;
     pre = nx;
   };
   for (int p = l0; p < l1; ++p) {
@@ -497,6 +515,150 @@ __global__ void k_prolong(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restric
   }
 }
 
+// The 3D transfers onto / from an x-split fine level, marching along z (one thread per coarse
+// point or fine pair, consecutive planes in registers).  Both keep the exact arithmetic of
+// k_restrict / k_prolong, so either kernel gives bitwise the same result.
+//
+// Full weighting: thread (I, J) walks the coarse planes [L0, L1); the plane sum PS(fl) (rows and
+// columns weighted first) of fine plane fl = 2L + o - 1 is the last one of coarse plane L - 1, so
+// two new plane sums per coarse plane.
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(128) k_restrict3z(Dims d, const cx<T>* __restrict__ r, cx<T>* __restrict__ fc,
+                                                    int lz, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int L0 = blockIdx.z * lz, L1 = min(L0 + lz, d.c[2]);
+  if (I >= d.c[0] || J >= d.c[1]) return;
+  const cx<T> zero = mkc<T>(T(0), T(0));
+  auto w3 = [](cx<T> a, cx<T> b, cx<T> c) {
+    return mkc<T>(fma(T(2), b.x, a.x + c.x), fma(T(2), b.y, a.y + c.y));
+  };
+  const int fi = 2 * I + d.o[0] - 1, fj = 2 * J + d.o[1] - 1;
+  const bool xl = fi >= 0, xh = fi + 2 < d.f[0];
+  const IDX qa = xl ? xpos(fi, d.fh) : 0, qb = xpos(fi + 1, d.fh), qc = xh ? xpos(fi + 2, d.fh) : 0;
+  const IDX P = (IDX)d.f[0] * d.f[1];
+  auto plane_sum = [&](int fl) -> cx<T> {
+    if (fl < 0 || fl >= d.f[2]) return zero;
+    cx<T> rs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int y = fj + k;
+      if (y < 0 || y >= d.f[1]) {
+        rs[k] = zero;
+        continue;
+      }
+      const cx<T>* row = r + (IDX)fl * P + (IDX)d.f[0] * y;
+      rs[k] = w3(xl ? row[qa] : zero, row[qb], xh ? row[qc] : zero);
+    }
+    return w3(rs[0], rs[1], rs[2]);
+  };
+  cx<T> prev = plane_sum(2 * L0 + d.o[2] - 1);
+  const IDX cq = (IDX)xpos(I, d.ch) + (IDX)d.c[0] * J;
+  const IDX CP = (IDX)d.c[0] * d.c[1];
+  for (int L = L0; L < L1; ++L) {
+    const int fl = 2 * L + d.o[2] - 1;
+    const cx<T> mid = plane_sum(fl + 1), last = plane_sum(fl + 2);
+    fc[cq + CP * L] = cscale<T>(T(0.015625), w3(prev, mid, last));
+    prev = last;
+  }
+}
+
+// Trilinear prolongation onto an x-split fine level: thread (t, j) owns the fine pair (2t, 2t + 1)
+// of row j and walks fine planes [l0, l1).  The pair reads coarse columns a = t - o and a + 1, the
+// row coarse rows jA (and jB); the coarse values of the two coarse planes a fine plane can need
+// stay in registers.  Every fine point sums its coarse values in k_prolong's order (lower plane,
+// row, column first) and scales once.
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(128) k_prolong3z(Dims d, const cx<T>* __restrict__ ec, cx<T>* __restrict__ u,
+                                                   int overwrite, int lz, const int* skip) {
+  pdl_entry();
+  if (skip && *skip) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int l0 = blockIdx.z * lz, l1 = min(l0 + lz, d.f[2]);
+  if (j >= d.f[1] || 2 * t >= d.f[0]) return;
+  const cx<T> zero = mkc<T>(T(0), T(0));
+  const bool has1 = 2 * t + 1 < d.f[0];
+  // x: coarse columns a, a + 1; with o = 1 the even fine column lies between them and the odd one
+  // on a + 1, with o = 0 the even one on a and the odd one between them
+  const int o0 = d.o[0], a = t - o0;
+  const bool va = a >= 0 && a < d.c[0], vb = a + 1 < d.c[0];
+  const IDX pa = va ? xpos(a, d.ch) : 0, pb = vb ? xpos(a + 1, d.ch) : 0;
+  // y: coarse rows
+  const int ry = j - d.o[1];
+  const bool yon = ry >= 0 && !(ry & 1);
+  const int jA = yon ? ry >> 1 : (ry - 1) >> 1, jB = jA + 1;
+  const bool vjA = jA >= 0 && jA < d.c[1], vjB = !yon && jB < d.c[1];
+  const IDX CP = (IDX)d.c[0] * d.c[1];
+  // coarse values of plane L: [row A / B][column a / a + 1]
+  struct Cp { cx<T> e[2][2]; bool v; };
+  auto load_plane = [&](int L) -> Cp {
+    Cp q;
+    q.v = L >= 0 && L < d.c[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const bool vr = q.v && (rr ? vjB : vjA);
+      const IDX rb = (IDX)L * CP + (IDX)d.c[0] * (rr ? jB : jA);
+      q.e[rr][0] = vr && va ? ec[rb + pa] : zero;
+      q.e[rr][1] = vr && vb ? ec[rb + pb] : zero;
+    }
+    return q;
+  };
+  const T wy = yon ? T(1) : T(0.5);
+  const T wxe = o0 ? T(0.5) : T(1), wxo = o0 ? T(1) : T(0.5);
+  // the coarse values of one fine point in k_prolong's order: planes, rows, columns ascending
+  auto point = [&](const Cp& A, const Cp& B, bool two, bool odd) -> cx<T> {
+    cx<T> acc = zero;
+    // the even column uses {a, a + 1} when o = 1, {a} when o = 0; the odd one {a + 1} / {a, a + 1}
+    const bool ca = odd ? (o0 == 0) : true, cb = odd ? true : (o0 == 1);
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      const Cp& Q = z ? B : A;
+      if ((z && !two) || !Q.v) continue;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        if (!(rr ? vjB : vjA)) continue;
+        if (ca && va) acc = cadd<T>(acc, Q.e[rr][0]);
+        if (cb && vb) acc = cadd<T>(acc, Q.e[rr][1]);
+      }
+    }
+    return acc;
+  };
+  const IDX P = (IDX)d.f[0] * d.f[1];
+  const IDX ce = (IDX)d.f[0] * j + t, co = (IDX)d.f[0] * j + d.fh + t;
+  int rz = l0 - d.o[2];
+  int Lc = rz >> 1;  // floor
+  Cp A = load_plane(Lc), B = load_plane(Lc + 1);
+  for (int l = l0; l < l1; ++l, ++rz) {
+    if ((rz >> 1) != Lc) {  // the next coarse plane pair
+      ++Lc;
+      A = B;
+      B = load_plane(Lc + 1);
+    }
+    const bool zon = !(rz & 1);  // on coarse plane Lc; otherwise between Lc and Lc + 1
+    const T wz = zon ? T(1) : T(0.5);
+    const IDX oe = ce + (IDX)l * P, oo = co + (IDX)l * P;
+    const cx<T> se = point(A, B, !zon, false);
+    const T we = wxe * wy * wz;
+    if (overwrite) u[oe] = cscale<T>(we, se);
+    else {
+      const cx<T> uo = u[oe];
+      u[oe] = mkc<T>(fma(we, se.x, uo.x), fma(we, se.y, uo.y));
+    }
+    if (has1) {
+      const cx<T> so = point(A, B, !zon, true);
+      const T wo = wxo * wy * wz;
+      if (overwrite) u[oo] = cscale<T>(wo, so);
+      else {
+        const cx<T> uo = u[oo];
+        u[oo] = mkc<T>(fma(wo, so.x, uo.x), fma(wo, so.y, uo.y));
+      }
+    }
+  }
+}
+
 // z = Ainv f, one warp per row of the dense inverse of the coarsest operator.
 template <typename T>
 __global__ void k_coarse(const cx<T>* __restrict__ Ainv, int n, const cx<T>* __restrict__ f,
@@ -573,9 +735,17 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
 // a Galerkin level: 9-point in 2D, 27-point in 3D
 template <typename T> static bool is9(const LevelHost& L) { return L.stg64 != nullptr; }
 
+// planes per thread of a z-marching kernel whose x-y grid has `warps` warps: the most (up to 32)
+// that still leave about 24 warps per SM (fewer planes per thread re-read more window values at
+// the chunk ends)
+static int plane_chunk(long warps, int nz) {
+  int lz = 32;
+  while (lz > 2 && warps * ((nz + lz - 1) / lz) < 152L * 24) lz /= 2;
+  return lz;
+}
+
 // the z-marching sweep: row segments of 32 or 16 pairs (whichever idles fewer lanes), 4 warps a
-// block; planes per thread chosen so that the grid holds about 48 warps per SM (fewer planes per
-// thread re-read more window values at the chunk ends)
+// block
 template <typename T, bool RESID, bool WIDE, int W, typename IDX>
 static void launch_rbgs3z_g(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
                             const int* skip, cudaStream_t st);
@@ -594,9 +764,7 @@ static void launch_rbgs3z_g(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>*
   const int h = (L.n[0] + 1) / 2;
   const int rows_per_block = 4 * (32 / W);
   const long gx = (h + W - 1) / W, gy = (L.n[1] + rows_per_block - 1) / rows_per_block;
-  const long warps_per_chunk = gx * gy * 4;
-  int lz = 32;
-  while (lz > 2 && warps_per_chunk * ((L.n[2] + lz - 1) / lz) < 152L * 48) lz /= 2;
+  const int lz = plane_chunk(gx * gy * 4, L.n[2]);
   dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((L.n[2] + lz - 1) / lz));
   launch_pdl(k_rbgs3z<T, RESID, WIDE, W, IDX>, g, dim3(32, 4), 0, st, L.view<T>(), u, f, r, colour, lz, wide, skip);
 }
@@ -655,12 +823,28 @@ template <typename T, int DIM> struct Launch {
   static void restrict_(const LevelHost& F, const LevelHost& C, const cx<T>* r, cx<T>* fc, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
     d.fh = F.xs_half(); d.ch = C.xs_half();
+    if (DIM == 3 && F.xs) {  // marching along z over the coarse planes
+      const long gx = (C.n[0] + 31) / 32, gy = (C.n[1] + 3) / 4;
+      const int lz = plane_chunk(gx * gy * 4, C.n[2]);
+      dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((C.n[2] + lz - 1) / lz));
+      if (F.ntot < 0x7fffffffL) launch_pdl(k_restrict3z<T, int>, g, dim3(32, 4), 0, st, d, r, fc, lz, skip);
+      else launch_pdl(k_restrict3z<T, long>, g, dim3(32, 4), 0, st, d, r, fc, lz, skip);
+      return;
+    }
     dim3 g, b; cfg<DIM>(C.n, g, b);
     launch_pdl(k_restrict<T, DIM>, dim3(g), dim3(b), 0, st, d, r, fc, skip);
   }
   static void prolong(const LevelHost& F, const LevelHost& C, const cx<T>* ec, cx<T>* u, int overwrite, const int* skip, cudaStream_t st) {
     Dims d; for (int a = 0; a < 3; ++a) { d.f[a] = F.n[a]; d.c[a] = C.n[a]; d.o[a] = F.offset(a); }
     d.fh = F.xs_half(); d.ch = C.xs_half();
+    if (DIM == 3 && F.xs) {  // marching along z over the fine planes, one thread per fine pair
+      const long gx = (d.fh + 31) / 32, gy = (F.n[1] + 3) / 4;
+      const int lz = plane_chunk(gx * gy * 4, F.n[2]);
+      dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((F.n[2] + lz - 1) / lz));
+      if (F.ntot < 0x7fffffffL) launch_pdl(k_prolong3z<T, int>, g, dim3(32, 4), 0, st, d, ec, u, overwrite, lz, skip);
+      else launch_pdl(k_prolong3z<T, long>, g, dim3(32, 4), 0, st, d, ec, u, overwrite, lz, skip);
+      return;
+    }
     dim3 g, b; cfg<DIM>(F.n, g, b);
     launch_pdl(k_prolong<T, DIM>, dim3(g), dim3(b), 0, st, d, ec, u, overwrite, skip);
   }
