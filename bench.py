@@ -571,8 +571,9 @@ def kernel_rooflines(torch, L, ctxs, p, dev, flush) -> dict:
                 "frac": d64["T_op/s"] / fp64_ops_peak, "traffic": DOWN_TRAFFIC_BYTES["c128"],
                 "peak_source": "derived: 152 SMs x 2 FP64 operations/clk (ncu peak_sustained) x 2.07 GHz",
                 "fp64_ops_per_launch": d64["fp64_ops"], "launch_us": d64["us"],
-                "note": "DADD, DMUL and DFMA each take one FP64-pipe slot; ncu: the FP64 pipe is 76% busy over "
-                        "active cycles, DRAM reads = the algorithmic reads (f and omega/D; writes stay in L2)"}
+                "note": "DADD, DMUL and DFMA each take one FP64-pipe slot; ncu: the FP64 pipe is 76-80% busy over "
+                        "active cycles, DRAM reads = the algorithmic reads (f and omega/D; writes stay in L2); "
+                        "executed FP64 lane slots 22-33 per fine point against 20.5 algorithmic (halo, partial warps)"}
     fp32 = {"kernel": "k_down2d<float> (same kernel in the FP32 V-cycle)", "bound": "hbm",
             "achieved": d32["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d32["GB/s"] / hbm,
             "traffic": DOWN_TRAFFIC_BYTES["c64"],
