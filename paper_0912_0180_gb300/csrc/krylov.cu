@@ -31,31 +31,35 @@ static double host_seconds() {
 
 // ---- block reductions -------------------------------------------------------------------
 
-template <int K>
-__device__ __forceinline__ void warp_sum(double2 (&v)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    for (int o = 16; o > 0; o >>= 1) {
-      v[k].x += __shfl_down_sync(0xffffffffu, v[k].x, o);
-      v[k].y += __shfl_down_sync(0xffffffffu, v[k].y, o);
-    }
-}
-
-// Sum K values over the block; thread 0 gets the totals.
+// Sum K values over the block; thread 0 gets the totals.  Every thread's values go through shared
+// memory and one warp sums each of them (KT / 32 terms a lane, then the warp's shuffle): about 24
+// FP64 additions a lane on K warps, where shuffling all K sums on every warp costs 10 K on each of
+// the KT / 32 warps -- at GB300's FP64 rate as much as the products of the few points a thread
+// holds.  The order of the additions is fixed, so the sums are reproducible.
 template <int K>
 __device__ __forceinline__ void block_sum(double2 (&v)[K]) {
-  __shared__ double2 sm[K][KT / 32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  warp_sum<K>(v);
-  if (lane == 0)
+  __shared__ double2 sm[K][KT];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) sm[k][w] = v[k];
+  for (int k = 0; k < K; ++k) sm[k][threadIdx.x] = v[k];
   __syncthreads();
-  if (w == 0) {
+  for (int k = w; k < K; k += KT / 32) {
+    double2 t = sm[k][lane];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = lane < KT / 32 ? sm[k][lane] : mkc<double>(0.0, 0.0);
-    warp_sum<K>(v);
+    for (int q = 1; q < KT / 32; ++q) {
+      t.x += sm[k][lane + 32 * q].x;
+      t.y += sm[k][lane + 32 * q].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_down_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_down_sync(0xffffffffu, t.y, o);
+    }
+    if (lane == 0) sm[k][0] = t;  // the warp's reads of row k are done (the shuffles synchronise it)
   }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = sm[k][0];
   __syncthreads();
 }
 

@@ -10,6 +10,8 @@ Tolerances, derived from the arithmetic:
     first steps and then drift; the solutions both satisfy ||b - Hx|| <= tol ||b||, so they
     agree to about cond * tol; at tol 1e-10 the bar is 1e-9 relative, matvec counts within 2.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -76,6 +78,33 @@ def edge_rows(o, lvl, which=1):
         sh[len(shape) - 1 - a] = len(ma)
         m |= ma.reshape(sh)
     return m.reshape(-1)
+
+
+# Cases whose GPU matvec count differs from the oracle's by more than 2 and is checked against
+# the oracle's own count range under rounding-level perturbations of b (printed with -s).
+SPREAD_CASES = []
+
+
+def counts_match(o, b, opts, gpu, ref, shadow=None, eps=(1e-16,) * 15 + (1e-15,) * 15 + (1e-14,) * 15, seed=99):
+    """Matvec-count bar of a solve at a tight tolerance: within 2 of the oracle's count, or else
+    within 2 of the range of counts the oracle itself reaches when b changes by 1e-16 .. 1e-14
+    relative (1 to 100 units of its rounding; 15 runs each).  Near the stopping tolerance two FP64
+    runs that round differently (another summation order, fused multiply-adds) follow different
+    Krylov histories, and the step at which the recurrence first crosses tol moves; the perturbed
+    oracle runs measure how far it moves for this problem (on the most sensitive case, a
+    Sommerfeld Bi-CGSTAB solve, by +-25 around 230 already at 1e-16)."""
+    if abs(gpu - ref) <= 2:
+        return
+    rng = np.random.default_rng(seed)
+    counts = [ref]
+    for e in eps:
+        bp = b * (1 + e * rng.standard_normal(len(b)))
+        counts.append(o.solve(bp, opts, shadow=shadow)[1]["matvecs"])
+    where = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    SPREAD_CASES.append((where, gpu, ref, min(counts), max(counts)))
+    print(f"\ncount bar by the oracle's spread: {where}: GPU {gpu}, oracle {ref}, "
+          f"perturbed {min(counts)}..{max(counts)} ({len(counts) - 1} runs)")
+    assert min(counts) - 2 <= gpu <= max(counts) + 2, (gpu, counts)
 
 
 CASES = [
@@ -252,7 +281,7 @@ SOLVE_CASES = [
 def test_fp64_solve_matches_oracle(case, pci, method):
     """FP64 path vs the oracle at tol 1e-10: the same residual history until rounding drift
     (first 8 matvecs to 1e-9 relative), relative solution difference <= 1e-9, and a matvec
-    count within 2 of the oracle's."""
+    count within 2 of the oracle's (or of its spread under rounding-level changes of b)."""
     p = _problem(case, rhs="point")
     pc = PCS[pci]
     o = Oracle(p, pc)
@@ -266,7 +295,7 @@ def test_fp64_solve_matches_oracle(case, pci, method):
     m = min(8, info.matvecs, info_ref["matvecs"])
     assert np.allclose(info.history[:m], info_ref["history"][:m], rtol=1e-9, atol=0)
     check(x.cpu().numpy(), x_ref, 1e-9)
-    assert abs(info.matvecs - info_ref["matvecs"]) <= 2, (info.matvecs, info_ref["matvecs"])
+    counts_match(o, p.b, opts, info.matvecs, info_ref["matvecs"], shadow=sh)
     h.close()
 
 
@@ -294,11 +323,12 @@ def test_idr_other_shadow_dimensions(s):
     pc = PCS[0]
     o = Oracle(p, pc)
     sh = hi.shadow_space(p.n, s, seed=77)
-    x_ref, info_ref = o.solve(p.b, hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=1500), shadow=sh)
+    opts = hi.SolveOpts(method=hi.IDR, s=s, tol=1e-10, maxmv=1500)
+    x_ref, info_ref = o.solve(p.b, opts, shadow=sh)
     h = Helm(p, pc, mg_dtype="c128")
     x, info = h.solve(cu(p.b), method=hi.IDR, s=s, tol=1e-10, maxmv=1500, shadow=sh)
     assert info.status == 0
-    assert abs(info.matvecs - info_ref["matvecs"]) <= 2, (info.matvecs, info_ref["matvecs"])
+    counts_match(o, p.b, opts, info.matvecs, info_ref["matvecs"], shadow=sh)
     check(x.cpu().numpy(), x_ref, 1e-9)
     h.close()
 
@@ -398,18 +428,9 @@ def test_full_size_2d_solves_match_oracle():
     x, info = h.solve(cu(p.b), tol=1e-10, maxmv=6000)
     assert info.status == 0 and info.rel_res_true < 1e-10
     check(x.cpu().numpy(), x10, 1e-9)
-    if abs(info.matvecs - i10["matvecs"]) > 2:
-        # Over ~800 matvecs two FP64 runs that round differently (reduction order, fused
-        # multiply-adds) follow different Bi-CGSTAB histories near 1e-10, and the count at which
-        # the recurrence first crosses tol moves; the oracle's own count moves the same way when b
-        # changes by 1e-15 .. 1e-14 relative (10 to 100 units of its rounding).  The GPU count
-        # must lie within 2 of the range those runs span.
-        rng = np.random.default_rng(99)
-        counts = [i10["matvecs"]]
-        for eps in (1e-15, 1e-15, 1e-14, 1e-14):
-            bp = p.b * (1 + eps * rng.standard_normal(p.n))
-            counts.append(o.solve(bp, hi.SolveOpts(tol=1e-10, maxmv=6000))[1]["matvecs"])
-        assert min(counts) - 2 <= info.matvecs <= max(counts) + 2, (info.matvecs, counts)
+    # over ~800 matvecs: four perturbed oracle runs at most (each takes seconds at this size)
+    counts_match(o, p.b, hi.SolveOpts(tol=1e-10, maxmv=6000), info.matvecs, i10["matvecs"],
+                 eps=(1e-15, 1e-15, 1e-14, 1e-14))
     h.close()
     sh = hi.shadow_space(p.n, 4)
     for mg in ("c128", "c64"):
@@ -722,7 +743,7 @@ def test_smooth_contour_parity(case):
             xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=2000)
             xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=2000))
             assert info.status == 0 and io["status"] == 0
-            assert abs(info.matvecs - io["matvecs"]) <= 2
+            counts_match(o, p.b, hi.SolveOpts(tol=1e-10, maxmv=2000), info.matvecs, io["matvecs"])
             check(xs.cpu().numpy(), xo, 1e-9)
         h.close()
 
@@ -751,7 +772,7 @@ def test_gmres_solve_matches_oracle(gi):
     x, info = h.solve(cu(p.b), method=hi.GMRES, s=m, tol=1e-10, maxmv=maxmv, history=True)
     assert info.status == 0 and io["status"] == 0, (info, io)
     assert info.rel_res_true < 1e-10
-    assert abs(info.matvecs - io["matvecs"]) <= 2
+    counts_match(o, p.b, hi.SolveOpts(method=hi.GMRES, s=m, tol=1e-10, maxmv=maxmv), info.matvecs, io["matvecs"])
     check(x.cpu().numpy(), xo, 1e-9)
     hg = info.history[: min(info.matvecs, io["matvecs"])]
     ho = io["history"][: len(hg)]
@@ -880,7 +901,7 @@ def test_sommerfeld_solve_matches_oracle(case, method):
     h = Helm(p, pc, mg_dtype="c128")
     x, info = h.solve(cu(p.b), method=method, s=s, tol=1e-10, maxmv=3000, shadow=sh)
     assert info.status == 0 and io["status"] == 0
-    assert abs(info.matvecs - io["matvecs"]) <= 2
+    counts_match(o, p.b, hi.SolveOpts(method=method, s=s, tol=1e-10, maxmv=3000), info.matvecs, io["matvecs"], shadow=sh)
     check(x.cpu().numpy(), xo, 1e-9)
     h.close()
     h32 = Helm(p, pc, mg_dtype="c64")
@@ -942,7 +963,7 @@ def test_galerkin3d_levels_vcycle_and_solve(shape, mg):
         x, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
         xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
         assert info.status == 0 and io["status"] == 0
-        assert abs(info.matvecs - io["matvecs"]) <= 2
+        counts_match(o, p.b, hi.SolveOpts(tol=1e-10, maxmv=3000), info.matvecs, io["matvecs"])
         check(x.cpu().numpy(), xo, 1e-9)
     h.close()
 
@@ -988,7 +1009,7 @@ def test_complex_z_potential_parity(ci, mg):
             xs, info = h.solve(cu(p.b), tol=1e-10, maxmv=3000)
             xo, io = o.solve(p.b, hi.SolveOpts(tol=1e-10, maxmv=3000))
             assert info.status == 0 and io["status"] == 0
-            assert abs(info.matvecs - io["matvecs"]) <= 2
+            counts_match(o, p.b, hi.SolveOpts(tol=1e-10, maxmv=3000), info.matvecs, io["matvecs"])
             check(xs.cpu().numpy(), xo, 1e-9)
         h.close()
 
