@@ -49,6 +49,18 @@ constexpr int DN_WCX = 16, DN_WCY = 12, UP_WFX = 32, UP_WFY = 24;
 
 // ---- down: smooth from zero + residual + restriction (2D, nu1 = 1) ---------------------------
 // HF: halo of the staged region beyond the residual region (1 for Jacobi, 2 for RB-GS).
+// The k-th point of colour c ((i + j) & 1 == c) of a W x H block whose corner is the grid point
+// (gi0, gj0): row y = k / P, and in it the (k % P)-th point of that colour, P = ceil(W / 2) slots a
+// row.  False when the slot lies past the end of a row with fewer points of that colour.  A loop
+// over k < H P gives every lane of a warp a point of the colour, where a loop over all points
+// leaves half of them idle on the colour's arithmetic.
+__device__ __forceinline__ bool colour_item(int k, int W, int gi0, int gj0, int c, int& x, int& y) {
+  const int P = (W + 1) >> 1;
+  y = k / P;
+  x = 2 * (k - y * P) + ((gi0 + gj0 + y + c) & 1);
+  return x < W;
+}
+
 template <typename T, bool RBGS, int CX, int CY, int NT>
 __device__ __forceinline__ void down2d_body(int bx_, int by_, const OpView<T>& op, int nc0, int nc1, const cx<T>* __restrict__ f, cx<T>* __restrict__ u_out,
          cx<T>* __restrict__ fc, T omega) {
@@ -94,10 +106,14 @@ __device__ __forceinline__ void down2d_body(int bx_, int by_, const OpView<T>& o
   }
   __syncthreads();
   if (RBGS) {  // black points of the inner region from the red values just computed
-    for (int e = tid; e < (FX - 2) * (FY - 2); e += NT) {
-      int x = 1 + e % (FX - 2), y = 1 + e / (FX - 2);
+    constexpr int BW = FX - 2, BH = FY - 2;
+    for (int e = tid; e < BH * ((BW + 1) / 2); e += NT) {
+      int x, y;
+      if (!colour_item(e, BW, fx0 + 1, fy0 + 1, 1, x, y)) continue;
+      x += 1;
+      y += 1;
       int i = fx0 + x, j = fy0 + y;
-      if (i < 0 || i >= n0 || j < 0 || j >= n1 || ((i + j) & 1) == 0) continue;
+      if (i < 0 || i >= n0 || j < 0 || j >= n1) continue;
       cx<T> acc = off2d<T>(op, i, j, su[y][x - 1], su[y][x + 1], su[y - 1][x], su[y + 1][x]);
       su[y][x] = cmul<T>(csub<T>(sf[y][x], acc), op.dinv[i + n0 * j]);
     }
@@ -115,21 +131,37 @@ __device__ __forceinline__ void down2d_body(int bx_, int by_, const OpView<T>& o
       u_out[i + n0 * j] = su[y + HF][x + HF];
     }
   }
-  // residual on the restriction region (fine 2I0 .. 2I0 + 2CX), zero outside the grid
-  for (int e = tid; e < RX * RY; e += NT) {
-    int x = e % RX, y = e / RX;
-    int i = 2 * I0 + x, j = 2 * J0 + y;
-    cx<T> rv = mkc<T>(T(0), T(0));
-    if (i < n0 && j < n1) {
-      int sx = x + HF, sy = y + HF;
-      if (!RBGS || ((i + j) & 1) == 0) {
+  // residual on the restriction region (fine 2I0 .. 2I0 + 2CX), zero outside the grid; with
+  // red-black Gauss-Seidel only the red points have one, so the red points are one loop and the
+  // black ones (zero) another (colour_item)
+  if (!RBGS) {
+    for (int e = tid; e < RX * RY; e += NT) {
+      int x = e % RX, y = e / RX;
+      int i = 2 * I0 + x, j = 2 * J0 + y;
+      cx<T> rv = mkc<T>(T(0), T(0));
+      if (i < n0 && j < n1) {
+        int sx = x + HF, sy = y + HF;
         cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
         const T om1 = T(1) - omega;  // (1 - omega) f - acc in two fused multiply-adds, as k_resid0
-        rv = RBGS ? mkc<T>(-acc.x, -acc.y)
-                  : mkc<T>(fma(om1, sf[sy][sx].x, -acc.x), fma(om1, sf[sy][sx].y, -acc.y));
+        rv = mkc<T>(fma(om1, sf[sy][sx].x, -acc.x), fma(om1, sf[sy][sx].y, -acc.y));
       }
+      sr[y][x] = rv;
     }
-    sr[y][x] = rv;
+  } else {
+    constexpr int RQ = RY * ((RX + 1) / 2);
+    for (int e = tid; e < 2 * RQ; e += NT) {
+      const int c = e < RQ ? 0 : 1;
+      int x, y;
+      if (!colour_item(e - c * RQ, RX, 2 * I0, 2 * J0, c, x, y)) continue;
+      int i = 2 * I0 + x, j = 2 * J0 + y;
+      cx<T> rv = mkc<T>(T(0), T(0));
+      if (c == 0 && i < n0 && j < n1) {
+        int sx = x + HF, sy = y + HF;
+        cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
+        rv = mkc<T>(-acc.x, -acc.y);
+      }
+      sr[y][x] = rv;
+    }
   }
   __syncthreads();
   // full weighting (1/4, 1/2, 1/4 per axis)
@@ -177,20 +209,32 @@ __device__ __forceinline__ void up2d_body(int bx_, int by_, const OpView<T>& op,
     se[y][x] = (I >= 0 && I < nc0 && J >= 0 && J < nc1) ? ec[I + nc0 * J] : mkc<T>(T(0), T(0));
   }
   __syncthreads();
-  // corrected iterate u + P e on the tile and its halo (u loads issued up front)
+  // corrected iterate u + P e on the tile and its halo (u loads issued up front).  The region's
+  // points are taken parity class by parity class (local offsets (c & 1, c >> 1) on a 2 x 2
+  // lattice; UX and UY are even, so every class has the same number of points and its own fine
+  // (i, j) parities): a warp then takes one or two classes, not all four, and a class sums only the
+  // one, two or four coarse values it needs.
+  static_assert(UX % 2 == 0 && UY % 2 == 0, "parity classes of equal size");
+  constexpr int HX = UX / 2, QC = HX * (UY / 2);
+  auto item = [&](int e, int& x, int& y) {
+    const int c = e / QC, k = e - c * QC;
+    x = 2 * (k % HX) + (c & 1);
+    y = 2 * (k / HX) + (c >> 1);
+  };
   constexpr int NU = (UX * UY + NT - 1) / NT;
   cx<T> uold[NU];
 #pragma unroll
   for (int it = 0; it < NU; ++it) {
-    int e = tid + it * NT;
-    int i = ux0 + e % UX, j = uy0 + e / UX;
+    int e = tid + it * NT, x, y;
+    item(e, x, y);
+    int i = ux0 + x, j = uy0 + y;
     uold[it] = (e < UX * UY && i >= 0 && i < n0 && j >= 0 && j < n1) ? u_in[i + n0 * j] : mkc<T>(T(0), T(0));
   }
 #pragma unroll
   for (int it = 0; it < NU; ++it) {
-    int e = tid + it * NT;
+    int e = tid + it * NT, x, y;
     if (e >= UX * UY) break;
-    int x = e % UX, y = e / UX;
+    item(e, x, y);
     int i = ux0 + x, j = uy0 + y;
     cx<T> v = mkc<T>(T(0), T(0));
     if (i >= 0 && i < n0 && j >= 0 && j < n1) {
@@ -205,7 +249,9 @@ __device__ __forceinline__ void up2d_body(int bx_, int by_, const OpView<T>& op,
         acc = cadd<T>(acc, se[jb - cy0][ia - cx0]);
         if (ib != ia) acc = cadd<T>(acc, se[jb - cy0][ib - cx0]);
       }
-      v = cadd<T>(uold[it], cscale<T>(w, acc));
+      // the weight is a power of two, so w acc is exact and one FMA gives u + w acc as before
+      const cx<T> uo = uold[it];
+      v = mkc<T>(fma(w, acc.x, uo.x), fma(w, acc.y, uo.y));
     }
     su[y][x] = v;
   }
@@ -224,14 +270,18 @@ __device__ __forceinline__ void up2d_body(int bx_, int by_, const OpView<T>& op,
       u_out[p] = cconv<TO, T>(mkc<T>(fma(om1, uc.x, g.x), fma(om1, uc.y, g.y)));
     }
   } else {
-    // red points of the tile and one ring around it, from the corrected black values
+    // red points of the tile and one ring around it, from the corrected black values; the black
+    // ones are copied.  Each colour is its own loop (colour_item), so no lane idles on the update.
     __shared__ cx<T> sred[FY + 2][FX + 2];
-    for (int e = tid; e < (FX + 2) * (FY + 2); e += NT) {
-      int x = e % (FX + 2), y = e / (FX + 2);
+    constexpr int RW = FX + 2, RH = FY + 2, RQ = RH * ((RW + 1) / 2);
+    for (int e = tid; e < 2 * RQ; e += NT) {
+      const int c = e < RQ ? 0 : 1;  // red (updated), then black (copied)
+      int x, y;
+      if (!colour_item(e - c * RQ, RW, i0 - 1, j0 - 1, c, x, y)) continue;
       int i = i0 - 1 + x, j = j0 - 1 + y;
       int sx = x + 1, sy = y + 1;  // position in su (HU = 2)
       cx<T> v = su[sy][sx];
-      if (i >= 0 && i < n0 && j >= 0 && j < n1 && ((i + j) & 1) == 0) {
+      if (c == 0 && i >= 0 && i < n0 && j >= 0 && j < n1) {
         int p = i + n0 * j;
         cx<T> acc = off2d<T>(op, i, j, su[sy][sx - 1], su[sy][sx + 1], su[sy - 1][sx], su[sy + 1][sx]);
         v = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
@@ -239,14 +289,17 @@ __device__ __forceinline__ void up2d_body(int bx_, int by_, const OpView<T>& op,
       sred[y][x] = v;
     }
     __syncthreads();
-    for (int e = tid; e < FX * FY; e += NT) {
-      int x = e % FX, y = e / FX;
+    constexpr int BQ = FY * ((FX + 1) / 2);
+    for (int e = tid; e < 2 * BQ; e += NT) {
+      const int c = e < BQ ? 1 : 0;  // black (updated), then red (written as they are)
+      int x, y;
+      if (!colour_item(e - (1 - c) * BQ, FX, i0, j0, c, x, y)) continue;
       int i = i0 + x, j = j0 + y;
       if (i >= n0 || j >= n1) continue;
       int p = i + n0 * j;
       int sx = x + 1, sy = y + 1;  // position in sred
       cx<T> v = sred[sy][sx];
-      if ((i + j) & 1) {
+      if (c == 1) {
         cx<T> acc = off2d<T>(op, i, j, sred[sy][sx - 1], sred[sy][sx + 1], sred[sy - 1][sx], sred[sy + 1][sx]);
         v = cmul<T>(csub<T>(f[p], acc), op.dinv[p]);
       }
