@@ -537,6 +537,8 @@ def test_large_3d_workload_sampled():
 XS_CASES = [
     ((41, 30, 27), ((3, 4), (2, 0), (5, 1)), "bump"),   # 48 x 32 x 33 unknowns: even row length
     ((26, 19, 22), ((2, 3), (1, 2), (0, 3)), "const"),  # 31 x 22 x 25: odd row length
+    # Sommerfeld low sides on x and y (those axes coarsen with offset 0), a high one on z
+    ((26, 21, 22), ((-1, 3), (-1, 0), (2, -1)), "bump"),  # 29 x 20 x 24 unknowns, 3 levels
 ]
 
 
