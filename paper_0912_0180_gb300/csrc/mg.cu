@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(128) k_rbgs3z(OpView<T> op, cx<T>* __restrict_
 // damped Jacobi left D u = omega f, so r = (1 - omega) f - offdiag(u); red-black Gauss-Seidel
 // left r = 0 on the black points and r = -offdiag(u) on the red ones (their neighbours are all
 // black and were updated last).  RB: one thread per red/black pair of a row.
-template <typename T, int DIM, bool RB, bool XS = false>
+// (x-split 3D levels take k_rbgs3z<T, true> instead)
+template <typename T, int DIM, bool RB>
 __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ r, T omega, const int* skip) {
   pdl_entry();
@@ -267,14 +268,12 @@ __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
   if (j >= op.n[1]) return;
   const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
   if (RB) {
-    const int par = (j + l) & 1, h = (op.n[0] + 1) >> 1;
+    int par = (j + l) & 1;
     int ir = 2 * t + par, ib = 2 * t + 1 - par;
-    // XS: the red point of the pair is stored at t or h + t, the black one in the other half
-    const long pr = XS ? row + (par ? h + t : t) : row + ir, pb = XS ? row + (par ? t : h + t) : row + ib;
-    if (ib < op.n[0]) r[pb] = mkc<T>(T(0), T(0));
+    if (ib < op.n[0]) r[row + ib] = mkc<T>(T(0), T(0));
     if (ir < op.n[0]) {
-      cx<T> acc = XS ? op_offdiag_xs<T, T, DIM>(op, u, ir, j, l, row, h) : op_offdiag<T, T, DIM>(op, u, ir, j, l, pr);
-      r[pr] = mkc<T>(-acc.x, -acc.y);
+      cx<T> acc = op_offdiag<T, T, DIM>(op, u, ir, j, l, row + ir);
+      r[row + ir] = mkc<T>(-acc.x, -acc.y);
     }
   } else {
     if (t >= op.n[0]) return;

@@ -619,7 +619,13 @@ def test_xsplit_levels_3d_fp32(shape):
         _, info64 = h64.solve(cu(p.b), **kw)
         assert info.status == 0 and info.rel_res_true < 1e-8
         assert rel(x.cpu().numpy(), x_ref) < 1e-6, (method, rel(x.cpu().numpy(), x_ref))
-        assert abs(info.matvecs - info64.matvecs) <= max(3, info64.matvecs // 10), (method, info.matvecs, info64.matvecs)
+        # a broken input or output order would ruin the preconditioner and multiply the count; GMRES
+        # with an FP32 preconditioner may need one certification restart more at 1e-8 (its residual
+        # estimate assumes an exact preconditioner), which costs up to one more cycle
+        slack = max(3, info64.matvecs // 10)
+        if method == hi.GMRES and info.restarts != info64.restarts:
+            slack += kw["s"]
+        assert abs(info.matvecs - info64.matvecs) <= slack, (method, info.matvecs, info64.matvecs, info.restarts)
     h64.close()
     h.close()
 
