@@ -8,9 +8,20 @@
 
 namespace helm {
 
+// Along x the uniform-interior shortcut is decided for the aligned chunk of 32 points holding i:
+// the chunk must lie inside the uniform run, else all its points take the per-axis tables.  The
+// warps of the stencil kernels cover 32 consecutive x points from a multiple of 32, so a warp takes
+// one formula along x instead of running both where the run begins or ends inside it; y and z are
+// decided per point (a warp's points share them in the row-wise kernels).  The choice depends on a
+// point's indices alone, so every kernel computes the same value at a point.
+template <typename T>
+__device__ __forceinline__ bool op_uniform_x(const OpView<T>& op, int i) {
+  const int c0 = i & ~31;
+  return c0 >= op.ulo[0] && c0 + 31 <= op.uhi[0];
+}
 template <int DIM, typename T>
 __device__ __forceinline__ bool op_uniform(const OpView<T>& op, int i, int j, int l) {
-  bool u = i >= op.ulo[0] && i <= op.uhi[0];
+  bool u = op_uniform_x(op, i);
   if (DIM > 1) u = u && j >= op.ulo[1] && j <= op.uhi[1];
   if (DIM > 2) u = u && l >= op.ulo[2] && l <= op.uhi[2];
   return u;
@@ -70,7 +81,7 @@ __device__ __forceinline__ cx<T> op_offdiag_general(const OpView<T>& op, const c
     const long st = a == 0 ? 1 : (a == 1 ? (long)op.n[0] : (long)op.n[0] * op.n[1]);
     const long qm = a == 0 ? pxm : p - st, qp = a == 0 ? pxp : p + st;
     const int q = idx[a];
-    if (q >= op.ulo[a] && q <= op.uhi[a]) {
+    if (a == 0 ? op_uniform_x(op, q) : (q >= op.ulo[a] && q <= op.uhi[a])) {
       cx<T> pr = cadd<T>(cconv<T, TX>(x[qm]), cconv<T, TX>(x[qp]));
       acc = op.uniform_real ? mkc<T>(fma(op.ua[a].x, pr.x, acc.x), fma(op.ua[a].x, pr.y, acc.y))
                             : cfma<T>(op.ua[a], pr, acc);
@@ -158,7 +169,7 @@ __device__ __forceinline__ cx<T> off2d(const OpView<T>& op, int i, int j, cx<T> 
   }
   // per axis: the shared coefficient on the pair where the axis is still uniform
   cx<T> acc;
-  if (i >= op.ulo[0] && i <= op.uhi[0]) {
+  if (op_uniform_x(op, i)) {
     cx<T> pr = cadd<T>(xw, xe);
     acc = op.uniform_real ? cscale<T>(op.ua[0].x, pr) : cmul<T>(op.ua[0], pr);
   } else {
