@@ -23,6 +23,16 @@ template <int DIM> static void cfg(const int n[3], dim3& g, dim3& b) {
   b = dim3(Cfg<DIM>::BX, Cfg<DIM>::BY, 1);
   g = dim3((n[0] + b.x - 1) / b.x, (n[1] + b.y - 1) / b.y, n[2]);
 }
+// the colour-packed kernels (rb_pair_index): n[0] pairs a row; in 2D and 3D 16 pairs and two rows
+// a warp
+template <int DIM> static void rb_cfg(const int n[3], dim3& g, dim3& b) {
+  if (DIM == 1) {
+    cfg<DIM>(n, g, b);
+    return;
+  }
+  b = dim3(32, Cfg<DIM>::BY, 1);
+  g = dim3((n[0] + 15) / 16, (n[1] + 2 * b.y - 1) / (2 * b.y), n[2]);
+}
 
 #define POINT_INDEX(op)                                                        \
   int i = blockIdx.x * blockDim.x + threadIdx.x;                               \
@@ -80,13 +90,28 @@ __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
 // `wide` (black sweeps only): also write the pair of points of this thread, widened to complex128
 // in natural order.  XS: u, f and dinv are stored x-split, so that the points of the colour in a
 // row (thread t: stored at t, or h + t when the colour's x indices are odd) are contiguous.
+// Thread -> (pair t, row j) of the colour-packed kernels.  In 2D and 3D a warp takes 16 pairs --
+// 32 consecutive x points from a multiple of 32, one chunk of the uniform-interior rule -- of two
+// neighbouring rows, so its lanes share the formula along x (one pair per lane over 32 pairs would
+// span two chunks); launched by rb_cfg.
+template <int DIM>
+__device__ __forceinline__ void rb_pair_index(int& t, int& j) {
+  if (DIM == 1) {
+    t = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    return;
+  }
+  t = blockIdx.x * 16 + (threadIdx.x & 15);
+  j = (blockIdx.y * blockDim.y + threadIdx.y) * 2 + (threadIdx.x >> 4);
+}
+
 template <typename T, int DIM, bool XS = false>
 __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restrict__ f, int colour,
                        int zero_guess, double2* __restrict__ wide, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int t, j;
+  rb_pair_index<DIM>(t, j);
   int l = blockIdx.z;
   if (j >= op.n[1]) return;
   const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
@@ -262,8 +287,12 @@ __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
                          cx<T>* __restrict__ r, T omega, const int* skip) {
   pdl_entry();
   if (skip && *skip) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int t, j;
+  if (RB) rb_pair_index<DIM>(t, j);
+  else {
+    t = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+  }
   int l = blockIdx.z;
   if (j >= op.n[1]) return;
   const long row = (long)op.n[0] * (j + (long)op.n[1] * l);
@@ -798,7 +827,7 @@ template <typename T, int DIM> struct Launch {
   static void rbgs(const LevelHost& L, cx<T>* u, const cx<T>* f, int colour, int zero, double2* wide,
                    const int* skip, cudaStream_t st) {
     int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
-    dim3 g, b; cfg<DIM>(half, g, b);
+    dim3 g, b; rb_cfg<DIM>(half, g, b);
     if (DIM == 3 && L.xs && !zero) launch_rbgs3z<T, false>(L, u, f, nullptr, colour, wide, skip, st);
     else if (DIM == 3 && L.xs) launch_pdl(k_rbgs<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
     else launch_pdl(k_rbgs<T, DIM>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, colour, zero, wide, skip);
@@ -808,7 +837,7 @@ template <typename T, int DIM> struct Launch {
     int half[3] = {(L.n[0] + 1) / 2, L.n[1], L.n[2]};
     dim3 g, b;
     if (rb) {
-      cfg<DIM>(half, g, b);
+      rb_cfg<DIM>(half, g, b);
       if (DIM == 3 && L.xs) launch_rbgs3z<T, true>(L, const_cast<cx<T>*>(u), nullptr, r, 0, nullptr, skip, st);
       else launch_pdl(k_resid0<T, DIM, true>, dim3(g), dim3(b), 0, st, L.view<T>(), u, f, r, omega, skip);
     } else {
