@@ -496,7 +496,7 @@ DOWN_FP64_OPS_PER_POINT = 4 + 12 + 18 / 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level launch of the fused
 # down kernel on this workload, from an ncu --set full capture of the current kernels (FP64, FP32);
 # set back to None whenever k_down2d changes.
-DOWN_TRAFFIC_BYTES = {"c128": 13134336, "c64": None}
+DOWN_TRAFFIC_BYTES = {"c128": 13133568, "c64": None}
 
 
 def down_bytes_per_point(esz: int) -> float:

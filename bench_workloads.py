@@ -341,7 +341,7 @@ H3D_FP64_OPS_PER_POINT = 17
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_h_apply<double, 3> launch on
 # this workload, from an ncu --set full capture of the current kernel; None whenever it changes.
-H3D_TRAFFIC_BYTES = 102660864 + 35742720
+H3D_TRAFFIC_BYTES = 106760704 + 37031680
 
 
 def _kernels_3d(torch, L, ctx, p, dev, flush):
