@@ -88,8 +88,8 @@ __global__ void k_jacobi(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>*
 // warp does arithmetic.  zero_guess (colour 0) writes the red points from a zero guess, f / D; the
 // black sweep that always follows it reads only red neighbours and writes every black point.
 // `wide` (black sweeps only): also write the pair of points of this thread, widened to complex128
-// in natural order.  XS: u, f and dinv are stored x-split, so that the points of the colour in a
-// row (thread t: stored at t, or h + t when the colour's x indices are odd) are contiguous.
+// in natural order.  XS (the zero-guess sweep of an x-split level only): u, f and dinv are stored
+// x-split, the colour's point of thread t at t, or h + t when the colour's x indices are odd.
 // Thread -> (pair t, row j) of the colour-packed kernels.  In 2D and 3D a warp takes 16 pairs --
 // 32 consecutive x points from a multiple of 32, one chunk of the uniform-interior rule -- of two
 // neighbouring rows, so its lanes share the formula along x (one pair per lane over 32 pairs would
@@ -124,7 +124,10 @@ __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restr
       u[p] = cmul<T>(f[p], op.dinv[p]);
       return;
     }
-    const cx<T> off = XS ? op_offdiag_xs<T, T, DIM>(op, u, i, j, l, row, h) : op_offdiag<T, T, DIM>(op, u, i, j, l, p);
+    // x-split levels run every other sweep in k_rbgs3z; only the zero-guess sweep (no neighbours)
+    // comes here for them
+    if (XS) return;
+    const cx<T> off = op_offdiag<T, T, DIM>(op, u, i, j, l, p);
     cx<T> v = cmul<T>(csub<T>(f[p], off), op.dinv[p]);
     u[p] = v;
     if (wide) wide[row + i] = cconv<double, T>(v);

@@ -105,16 +105,6 @@ __device__ __forceinline__ cx<T> op_offdiag(const OpView<T>& op, const cx<TX>* _
   return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p);
 }
 
-// The same on an x-split row: the point is stored at p = row + xs_pos(i, h).  A neighbour index
-// outside the row (i = 0 or n0 - 1) maps to a position that is never read.
-template <typename T, typename TX, int DIM>
-__device__ __forceinline__ cx<T> op_offdiag_xs(const OpView<T>& op, const cx<TX>* __restrict__ x, int i, int j,
-                                               int l, long row, int h) {
-  const long p = row + xs_pos(i, h), pxm = row + xs_pos(i - 1, h), pxp = row + xs_pos(i + 1, h);
-  if (op_uniform<DIM>(op, i, j, l)) return op_offdiag_uniform<T, TX, DIM>(op, x, p, pxm, pxp);
-  return op_offdiag_general<T, TX, DIM>(op, x, i, j, l, p, pxm, pxp);
-}
-
 // (A x)_P.  In the uniform interior of an operator with real coefficients (H) the diagonal
 // ud - s phi_P is real and multiplies x_P with two FMAs; elsewhere the stored diagonal is read
 // when the operator has one.
