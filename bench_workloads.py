@@ -377,16 +377,16 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
     # other colour's u read and u written, 8 bytes each (x-split rows: no other sector comes along)
     hbm, hbm_src = _hbm_peak()
     rb = table["rbgs_sweep_c64"]
-    fp32 = {"kernel": "k_rbgs3z<float> (red and black half-sweeps of the finest level, x-split rows, marching along z)",
+    fp32 = {"kernel": "k_rbgs3z2 (red and black half-sweeps of the finest level, x-split rows, two pairs of columns a thread, marching along z)",
             "bound": "hbm", "achieved": rb["GB/s"], "peak": hbm, "unit": "GB/s", "frac": rb["GB/s"] / hbm,
             "traffic": RBGS3Z_TRAFFIC_BYTES, "peak_source": hbm_src, "bytes_per_launch": rb["bytes"] / 2,
             "launch_us": rb["us"] / 2}
     return {"dominant": dom, "fp32_mg": fp32, "table": table}
 
 
-# DRAM bytes (read + write) of one k_rbgs3z<float> half-sweep on the 160^3 level, from an ncu
-# capture of the current kernel; None whenever it changes.
-RBGS3Z_TRAFFIC_BYTES = 49202176 + 528896
+# DRAM bytes (read + write) of one k_rbgs3z2 half-sweep on the 160^3 level, from an ncu capture of
+# the current kernel; None whenever it changes.
+RBGS3Z_TRAFFIC_BYTES = 49200640 + 348672
 
 
 def _hbm_peak():

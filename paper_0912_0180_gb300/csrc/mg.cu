@@ -124,7 +124,7 @@ __global__ void k_rbgs(OpView<T> op, cx<T>* __restrict__ u, const cx<T>* __restr
       u[p] = cmul<T>(f[p], op.dinv[p]);
       return;
     }
-    // x-split levels run every other sweep in k_rbgs3z; only the zero-guess sweep (no neighbours)
+    // x-split levels run every other sweep in k_rbgs3z2 / k_rbgs3z; only the zero-guess sweep (no neighbours)
     // comes here for them
     if (XS) return;
     const cx<T> off = op_offdiag<T, T, DIM>(op, u, i, j, l, p);
@@ -280,11 +280,176 @@ __global__ void __launch_bounds__(128) k_rbgs3z(OpView<T> op, cx<T>* __restrict_
   }
 }
 
+// Two consecutive complex64 values, moved as one 16-byte access.
+struct c64x2 {
+  float2 a, b;
+};
+__device__ __forceinline__ c64x2 ld_x2(const float2* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return c64x2{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+__device__ __forceinline__ void st_x2(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// k_rbgs3z with two pairs of columns per thread (FP32 x-split levels with n0 a multiple of 4):
+// thread tt of a row owns columns 4tt .. 4tt + 3, so the colour's two points of a plane, the two
+// window values and their y neighbours sit at two consecutive x-split positions and each of them
+// is one 16-byte access; per point, the loads, their address arithmetic and the loop overhead are
+// half those of k_rbgs3z.  With n0 a multiple of 4 a thread has all four columns or none, and every
+// 16-byte access is aligned when the arrays are.  The per-point arithmetic is k_rbgs3z's, operation
+// for operation.  A row is a segment of W lanes (4, 8 or 16); the rows of a warp are blockDim.y
+// apart (even), so the colour's column is uniform over the warp.
+template <bool RESID, bool WIDE, int W, typename IDX>
+__global__ void __launch_bounds__(128) k_rbgs3z2(OpView<float> op, float2* __restrict__ u,
+                                                 const float2* __restrict__ f, float2* __restrict__ r,
+                                                 int colour, int lz, double2* __restrict__ wide,
+                                                 const int* skip) {
+  using T = float;
+  pdl_entry();
+  if (skip && *skip) return;
+  constexpr int SEGS = 32 / W;  // rows per warp
+  const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
+  const int h = n0 >> 1;
+  const int sl = threadIdx.x % W, seg = threadIdx.x / W;
+  const int tt = blockIdx.x * W + sl;
+  const int x0 = 4 * tt;
+  const int by = blockDim.y;
+  const int j = blockIdx.y * (by * SEGS) + seg * by + threadIdx.y;
+  const int l0 = blockIdx.z * lz, l1 = min(l0 + lz, n2);
+  const float2 zero = make_float2(0.f, 0.f);
+  const c64x2 zz{zero, zero};
+  const bool row_ok = j < n1;
+  const bool hp = row_ok && x0 < n0;  // all four columns
+  const bool ylo = j > 0, yhi = j < n1 - 1;
+  const bool xlo = hp && tt > 0 && sl == 0, xhi = hp && x0 + 4 < n0 && sl == W - 1;
+  // x coefficients of the four columns
+  float2 axm[4], axp[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    axm[c] = hp ? op.am[0][x0 + c] : zero;
+    axp[c] = hp ? op.ap[0][x0 + c] : zero;
+  }
+  const float2 aym = row_ok ? op.am[1][j] : zero, ayp = row_ok ? op.ap[1][j] : zero;
+  const IDX P = (IDX)n0 * n1;
+  const IDX rowoff = (IDX)n0 * (row_ok ? j : 0);
+  // the thread's positions in this row: even columns at ce, ce + 1, odd ones at co, co + 1
+  const IDX ce = rowoff + 2 * tt, co = rowoff + h + 2 * tt;
+  const float2* const dv = op.dinv;
+  auto vload = [&](int q) -> c64x2 {  // V(q): the other colour's columns of plane q
+    if (q < 0 || q >= n2 || !hp) return zz;
+    const bool odd = ((j + q + colour) & 1) == 0;
+    return ld_x2(u + (odd ? co : ce) + (IDX)q * P);
+  };
+  auto fd = [&](auto cc, IDX oo, c64x2& fv, c64x2& dvv) {
+    constexpr int C = decltype(cc)::value;
+    if (!RESID && hp) {
+      const IDX pc = (C ? co : ce) + oo;
+      fv = ld_x2(f + pc);
+      dvv = ld_x2(dv + pc);
+    }
+  };
+  struct Nb {
+    c64x2 ym, yp;
+    float2 xe;
+  };
+  auto nb = [&](auto cc, IDX oo) -> Nb {
+    constexpr int C = decltype(cc)::value;
+    const IDX pc = (C ? co : ce) + oo;
+    Nb q;
+    q.ym = hp && ylo ? ld_x2(u + pc - n0) : zz;
+    q.yp = hp && yhi ? ld_x2(u + pc + n0) : zz;
+    if (C == 0) q.xe = xlo ? u[co + oo - 1] : zero;  // column x0 - 1
+    else q.xe = xhi ? u[ce + oo + 2] : zero;         // column x0 + 4
+    return q;
+  };
+  int cur = (j + l0 + colour) & 1;
+  IDX o = (IDX)l0 * P;
+  c64x2 vm = vload(l0 - 1), v0 = vload(l0), vp = vload(l0 + 1), vpp = vload(l0 + 2);
+  c64x2 f0, d0, f1, d1;
+  Nb pre;
+  if (cur) {
+    fd(std::integral_constant<int, 1>(), o, f0, d0);
+    if (l0 + 1 < l1) fd(std::integral_constant<int, 0>(), o + P, f1, d1);
+    pre = nb(std::integral_constant<int, 1>(), o);
+  } else {
+    fd(std::integral_constant<int, 0>(), o, f0, d0);
+    if (l0 + 1 < l1) fd(std::integral_constant<int, 1>(), o + P, f1, d1);
+    pre = nb(std::integral_constant<int, 0>(), o);
+  }
+  // one point: k_rbgs3z's operation order
+  auto point = [&](float2 am_x, float2 ap_x, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm, float2 zp,
+                   float2 azm, float2 azp) {
+    float2 off = cmul<T>(am_x, xm);
+    off = cfma<T>(ap_x, xp, off);
+    off = cfma<T>(aym, ym, off);
+    off = cfma<T>(ayp, yp, off);
+    off = cfma<T>(azm, zm, off);
+    return cfma<T>(azp, zp, off);
+  };
+  auto step = [&](auto cc, int p) {
+    constexpr int C = decltype(cc)::value;
+    const IDX pc = (C ? co : ce) + o;  // the colour's points
+    c64x2 f2, d2, v3 = zz;
+    if (p + 2 < l1) fd(cc, o + 2 * P, f2, d2);
+    if (p + 3 < n2 && p + 1 < l1 && hp) v3 = ld_x2(u + pc + 3 * P);
+    Nb nx = pre;
+    if (p + 1 < l1) nx = nb(std::integral_constant<int, 1 - C>(), o + P);
+    float2 xo;  // the x neighbour outside the thread's columns
+    if (C == 0) {
+      xo.x = __shfl_up_sync(0xffffffffu, v0.b.x, 1, W);
+      xo.y = __shfl_up_sync(0xffffffffu, v0.b.y, 1, W);
+      if (sl == 0) xo = pre.xe;
+    } else {
+      xo.x = __shfl_down_sync(0xffffffffu, v0.a.x, 1, W);
+      xo.y = __shfl_down_sync(0xffffffffu, v0.a.y, 1, W);
+      if (sl == W - 1) xo = pre.xe;
+    }
+    if (hp) {
+      const float2 azm = op.am[2][p], azp = op.ap[2][p];
+      // colour columns x0 + C and x0 + 2 + C
+      const float2 oa = C ? point(axm[1], axp[1], v0.a, v0.b, pre.ym.a, pre.yp.a, vm.a, vp.a, azm, azp)
+                          : point(axm[0], axp[0], xo, v0.a, pre.ym.a, pre.yp.a, vm.a, vp.a, azm, azp);
+      const float2 ob = C ? point(axm[3], axp[3], v0.b, xo, pre.ym.b, pre.yp.b, vm.b, vp.b, azm, azp)
+                          : point(axm[2], axp[2], v0.a, v0.b, pre.ym.b, pre.yp.b, vm.b, vp.b, azm, azp);
+      if (RESID) {
+        st_x2(r + pc, make_float2(-oa.x, -oa.y), make_float2(-ob.x, -ob.y));
+        st_x2(r + (C ? ce : co) + o, zero, zero);  // the other colour's points
+      } else {
+        const float2 va = cmul<T>(csub<T>(f0.a, oa), d0.a), vb = cmul<T>(csub<T>(f0.b, ob), d0.b);
+        st_x2(u + pc, va, vb);
+        if (WIDE) {
+          double2* w = wide + rowoff + x0 + o;
+          w[C] = cconv<double, T>(va);
+          w[1 - C] = cconv<double, T>(v0.a);
+          w[2 + C] = cconv<double, T>(vb);
+          w[3 - C] = cconv<double, T>(v0.b);
+        }
+      }
+    }
+    vm = v0;
+    v0 = vp;
+    vp = vpp;
+    vpp = v3;
+    f0 = f1;
+    d0 = d1;
+    f1 = f2;
+    d1 = d2;
+    pre = nx;
+  };
+  for (int p = l0; p < l1; ++p) {
+    if (cur) step(std::integral_constant<int, 1>(), p);
+    else step(std::integral_constant<int, 0>(), p);
+    cur ^= 1;
+    o += P;
+  }
+}
+
 // Residual right after the single pre-smoothing sweep from the zero guess, without the diagonal:
 // damped Jacobi left D u = omega f, so r = (1 - omega) f - offdiag(u); red-black Gauss-Seidel
 // left r = 0 on the black points and r = -offdiag(u) on the red ones (their neighbours are all
 // black and were updated last).  RB: one thread per red/black pair of a row.
-// (x-split 3D levels take k_rbgs3z<T, true> instead)
+// (x-split 3D levels take the RESID form of k_rbgs3z2 / k_rbgs3z instead)
 template <typename T, int DIM, bool RB>
 __global__ void k_resid0(OpView<T> op, const cx<T>* __restrict__ u, const cx<T>* __restrict__ f,
                          cx<T>* __restrict__ r, T omega, const int* skip) {
@@ -799,9 +964,66 @@ static void launch_rbgs3z_g(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>*
   dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((L.n[2] + lz - 1) / lz));
   launch_pdl(k_rbgs3z<T, RESID, WIDE, W, IDX>, g, dim3(32, 4), 0, st, L.view<T>(), u, f, r, colour, lz, wide, skip);
 }
+// k_rbgs3z2: W lanes (two pairs each) per row segment, whichever of 16, 8, 4 idles the fewest
+// lanes; blockDim.y = 4 or 2 rows, whichever idles fewer; planes per thread: the fewest that still
+// fit the grid in one wave of resident blocks (a thread's planes run one after another, so the
+// kernel lasts about one chain of planes)
+template <bool RESID, bool WIDE, int W, typename IDX>
+static void launch_rbgs3z2_g(const LevelHost& L, float2* u, const float2* f, float2* r, int colour, double2* wide,
+                             const int* skip, cudaStream_t st) {
+  auto kern = k_rbgs3z2<RESID, WIDE, W, IDX>;
+  const int h = L.n[0] / 2;
+  const int segs = 32 / W;
+  const int by4 = (L.n[1] + 4 * segs - 1) / (4 * segs) * 4 * segs, by2 = (L.n[1] + 2 * segs - 1) / (2 * segs) * 2 * segs;
+  const int by = by2 < by4 ? 2 : 4;
+  const long gx = (h + 2 * W - 1) / (2 * W), gy = (L.n[1] + by * segs - 1) / (by * segs);
+  auto resident = [&](int rows) {  // blocks resident on the whole device
+    int dev = 0, b = 0, s = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * rows, 0);
+    return (long)(b > 0 ? b : 1) * (s > 0 ? s : 1);
+  };
+  static const long cap2 = resident(2), cap4 = resident(4);
+  const long cap = by == 2 ? cap2 : cap4;
+  int lz = 2;
+  while (lz < L.n[2] && gx * gy * ((L.n[2] + lz - 1) / lz) > cap) ++lz;
+  dim3 g((unsigned)gx, (unsigned)gy, (unsigned)((L.n[2] + lz - 1) / lz));
+  launch_pdl(kern, g, dim3(32, by), 0, st, L.view<float>(), u, f, r, colour, lz, wide, skip);
+}
+template <bool RESID, int W, typename IDX>
+static void launch_rbgs3z2_w(const LevelHost& L, float2* u, const float2* f, float2* r, int colour, double2* wide,
+                             const int* skip, cudaStream_t st) {
+  if (wide) launch_rbgs3z2_g<RESID, true, W, IDX>(L, u, f, r, colour, wide, skip, st);
+  else launch_rbgs3z2_g<RESID, false, W, IDX>(L, u, f, r, colour, wide, skip, st);
+}
+template <bool RESID, typename IDX>
+static void launch_rbgs3z2(const LevelHost& L, float2* u, const float2* f, float2* r, int colour, double2* wide,
+                           const int* skip, cudaStream_t st) {
+  const int h = L.n[0] / 2;
+  const int p16 = (h + 31) / 32 * 32, p8 = (h + 15) / 16 * 16, p4 = (h + 7) / 8 * 8;
+  if (p16 <= p8 && p16 <= p4) launch_rbgs3z2_w<RESID, 16, IDX>(L, u, f, r, colour, wide, skip, st);
+  else if (p8 <= p4) launch_rbgs3z2_w<RESID, 8, IDX>(L, u, f, r, colour, wide, skip, st);
+  else launch_rbgs3z2_w<RESID, 4, IDX>(L, u, f, r, colour, wide, skip, st);
+}
+// the two-pair kernel's conditions: n0 a multiple of 4 and 16-byte aligned arrays
+static bool rbgs3z2_fits(const LevelHost& L, const void* u, const void* f, const void* r) {
+  const uintptr_t a = (uintptr_t)u | (uintptr_t)f | (uintptr_t)r | (uintptr_t)L.dinv32;
+  return L.n[0] % 4 == 0 && (a & 15) == 0;
+}
+
+// x-split half-sweep or zero-guess residual: two pairs a thread where the row length and the
+// arrays allow, else one
 template <typename T, bool RESID>
 static void launch_rbgs3z(const LevelHost& L, cx<T>* u, const cx<T>* f, cx<T>* r, int colour, double2* wide,
                           const int* skip, cudaStream_t st) {
+  if constexpr (sizeof(cx<T>) == 8) {
+    if (rbgs3z2_fits(L, u, f, r)) {
+      if (L.ntot < 0x7fffffffL) launch_rbgs3z2<RESID, int>(L, (float2*)u, (const float2*)f, (float2*)r, colour, wide, skip, st);
+      else launch_rbgs3z2<RESID, long>(L, (float2*)u, (const float2*)f, (float2*)r, colour, wide, skip, st);
+      return;
+    }
+  }
   const int h = (L.n[0] + 1) / 2;
   const bool w16 = (h + 15) / 16 * 16 < (h + 31) / 32 * 32;
   const bool i64 = L.ntot >= 0x7fffffffL;
