@@ -366,6 +366,19 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
         z = torch.empty(n, dtype=dt, device=dev)
         t = _time_cold(torch, flush, lambda: hh.vcycle(r, out=z), name=f"vcycle_{mg}_3d")
         table[f"vcycle_{mg}"] = {"us": t * 1e6}
+    # The FP32 sweep pair's bytes moved as contiguous streams, timed the same way (L2 flushed by a
+    # write first): per colour three arrays of n/2 complex64 read and one written, the second pass
+    # reading the first one's output as the black half-sweep reads the red values.  A library
+    # elementwise kernel, used here only as the attainable rate for this many bytes in this regime.
+    a1, b1, c1, o1, a2, b2, o2 = (torch.randn(n, dtype=torch.float32, device=dev) for _ in range(7))
+
+    def streams():
+        torch.addcmul(c1, a1, b1, out=o1)
+        torch.addcmul(o1, a2, b2, out=o2)
+
+    t = _time_cold(torch, flush, streams, name="stream_same_bytes_3d")
+    table["stream_same_bytes_c64"] = {"us": t * 1e6, "bytes": n * 32, "GB/s": n * 32 / t / 1e9}
+    del a1, b1, c1, o1, a2, b2, o2
     a = table["k_h_apply_c128"]
     achieved = a["fp64_ops"] / (a["us"] / 1e6) / 1e12
     dom = {"kernel": "k_h_apply<double, 3> (FP64 Helmholtz matvec; the stencil of the Krylov kernels)",
@@ -381,6 +394,10 @@ def _kernels_3d(torch, L, ctx, p, dev, flush):
             "bound": "hbm", "achieved": rb["GB/s"], "peak": hbm, "unit": "GB/s", "frac": rb["GB/s"] / hbm,
             "traffic": RBGS3Z_TRAFFIC_BYTES, "peak_source": hbm_src, "bytes_per_launch": rb["bytes"] / 2,
             "launch_us": rb["us"] / 2}
+    sb = table["stream_same_bytes_c64"]
+    fp32["stream_same_bytes"] = {"what": "torch.addcmul over contiguous FP32 arrays moving the pair's bytes, L2 flushed the same way",
+                                 "us": sb["us"], "GB/s": sb["GB/s"], "frac_of_peak": sb["GB/s"] / hbm,
+                                 "sweep_frac_of_stream": rb["GB/s"] / sb["GB/s"]}
     return {"dominant": dom, "fp32_mg": fp32, "table": table}
 
 
