@@ -539,6 +539,8 @@ XS_CASES = [
     ((26, 19, 22), ((2, 3), (1, 2), (0, 3)), "const"),  # 31 x 22 x 25: odd row length
     # Sommerfeld low sides on x and y (those axes coarsen with offset 0), a high one on z
     ((26, 21, 22), ((-1, 3), (-1, 0), (2, -1)), "bump"),  # 29 x 20 x 24 unknowns, 3 levels
+    # rows of 128 and 64 points: the two-pair sweep with 16-lane row segments
+    ((120, 10, 12), ((4, 4), (2, 2), (2, 2)), "bump"),    # 128 x 14 x 16 unknowns
 ]
 
 
