@@ -25,7 +25,7 @@ BASE_SEED = 20091201
 
 # Preconditioner kinds and solver codes, mirrored by both the C-ABI and the oracle.
 PC_NONE, PC_CSL, PC_CSG_UNIFORM, PC_CSG_INTERIOR = 0, 1, 2, 3
-SM_JACOBI, SM_RBGS = 0, 1
+SM_JACOBI, SM_RBGS, SM_ILU = 0, 1, 2
 BICGSTAB, IDR, GMRES = 0, 1, 2  # GMRES: SolveOpts.s is the restart length m
 
 
@@ -345,7 +345,8 @@ class Precond:
 
     kind: PC_NONE (identity), PC_CSL (M = -(L + beta^2 k^2), beta^2 = shift),
     PC_CSG_UNIFORM (every mesh width times e^{i theta_beta}), PC_CSG_INTERIOR (interior
-    widths only).  V(nu1, nu2) cycles with damped Jacobi (omega) or red-black Gauss-Seidel.
+    widths only).  V(nu1, nu2) cycles with damped Jacobi (omega), red-black Gauss-Seidel or
+    ILU(0) (1D / 2D).
     """
 
     kind: int = PC_CSG_UNIFORM
@@ -357,7 +358,7 @@ class Precond:
     omega: float = 0.5
     max_levels: int = 32
     coarse_max: int = 8
-    galerkin: bool = False   # 2D, omega-Jacobi: coarse operators R A P instead of rediscretised
+    galerkin: bool = False   # 2D, omega-Jacobi or ILU(0): coarse operators R A P instead of rediscretised
 
 
 @dataclasses.dataclass

@@ -19,7 +19,8 @@
  *   - geometric multigrid on the preconditioner (Section 5.1, Section 6.1 components: full
  *     weighting restriction, bilinear prolongation, rediscretised ("direct") coarse operators
  *     or (2D) Galerkin coarse operators R A P, omega-Jacobi; red-black Gauss-Seidel as a
- *     second smoother; direct coarsest solve);
+ *     second smoother; ILU(0), the paper's smoother, on 1D and 2D levels; direct coarsest
+ *     solve);
  *   - right-preconditioned Bi-CGSTAB (van der Vorst 1992) and IDR(s) (Sonneveld & van Gijzen
  *     2008), the Krylov methods of Section 6.2, stopped on ||d_m|| / ||d_0|| < tol (the
  *     stopping rule of Section 6.2), followed by a true-residual check.
@@ -93,7 +94,7 @@ typedef struct {
   double theta_beta;    /* CSG angle */
   double shift_re, shift_im; /* CSL: beta^2 */
   int nu1, nu2;         /* pre / post smoothing sweeps */
-  int smoother;         /* 0 damped Jacobi, 1 red-black Gauss-Seidel */
+  int smoother;         /* 0 damped Jacobi, 1 red-black Gauss-Seidel, 2 ILU(0) (1D / 2D) */
   double omega;         /* Jacobi damping */
   int max_levels;       /* cap on the number of levels (>= 1) */
   int coarse_max;       /* stop coarsening once every axis has <= coarse_max unknowns */
@@ -143,6 +144,8 @@ typedef struct {
   cplx* st9;      /* Galerkin levels (2D): row p is st9[9p + 3(dj+1) + (di+1)], the weight of the
                      unknown (i+di, j+dj); NULL for a Shortley-Weller level */
   cplx* st27;     /* Galerkin levels (3D): row p is st27[27p + 9(dl+1) + 3(dj+1) + (di+1)] */
+  cplx* ilu;      /* ILU(0) factors (1D / 2D), laid out as st9: at the lower neighbours of row p
+                     the entries of L (unit diagonal implied), at p and its upper neighbours U */
 } level_t;
 
 typedef struct orc_ctx {
@@ -270,6 +273,7 @@ static void axis_free(axis_t* a) {
 static void level_free(level_t* L) {
   free(L->st9);
   free(L->st27);
+  free(L->ilu);
   for (int d = 0; d < L->dim; ++d) axis_free(&L->ax[d]);
   free(L->phi);
   free(L->phi_im);
@@ -594,6 +598,7 @@ static void level_galerkin3d(const level_t* F, level_t* C) {
  * node positions of the layers (the alternative to reading k at real positions); the Sommerfeld
  * boundary term keeps sqrt of the real part (its nodes are real). */
 void orc_destroy(orc_ctx* c);
+static void level_ilu(level_t* L);
 
 /* Returns NULL when the coarsest preconditioner level is singular (its dense LU meets a zero
  * pivot), or for Galerkin coarse operators on a grid with a Sommerfeld low side. */
@@ -604,6 +609,7 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, 
   c->pc = *pc;
   level_fine(&c->H, g, phi, phi_im, k0, 1.0, 1.0, 1.0);
   if (pc->kind == 0) return c; /* identity preconditioner: no hierarchy */
+  if (pc->smoother == 2 && g->dim > 2) { orc_destroy(c); return NULL; }  /* ILU(0): 1D / 2D */
   if (pc->galerkin)  /* the Galerkin products are written for the offset-1 coarsening only */
     for (int d = 0; d < g->dim; ++d)
       if (g->n_layer[d][0] < 0) { orc_destroy(c); return NULL; }
@@ -634,6 +640,8 @@ orc_ctx* orc_create(const orc_grid* g, const double* phi, const double* phi_im, 
     if (pc->galerkin && g->dim == 3) level_galerkin3d(F, &c->M[c->nlev]);
     c->nlev++;
   }
+  if (pc->smoother == 2)
+    for (int k = 0; k < c->nlev - 1; ++k) level_ilu(&c->M[k]);
   level_t* C = &c->M[c->nlev - 1];
   c->nco = C->ntot;
   c->lu = malloc(sizeof(cplx) * c->nco * c->nco);
@@ -701,6 +709,14 @@ void orc_apply(const orc_ctx* c, int which, int lvl, const cplx* x, cplx* y) {
 
 void orc_dense(const orc_ctx* c, int which, int lvl, cplx* A) { level_dense(pick(c, which, lvl), A); }
 
+/* The ILU(0) factors of preconditioner level lvl (9 entries per unknown, laid out as a Galerkin
+ * stencil); 0 when the hierarchy has none there (another smoother, or the coarsest level). */
+int orc_ilu_factors(const orc_ctx* c, int lvl, cplx* out) {
+  if (lvl < 0 || lvl >= c->nlev || !c->M[lvl].ilu) return 0;
+  memcpy(out, c->M[lvl].ilu, sizeof(cplx) * 9 * c->M[lvl].ntot);
+  return 1;
+}
+
 /* ---- multigrid components (Section 5.1 / 6.1) ----------------------------------------- */
 
 /* One damped-Jacobi sweep: u <- u + omega D^{-1} (f - A u). */
@@ -732,10 +748,85 @@ static void rbgs_sweep(const level_t* L, cplx* u, const cplx* f) {
   }
 }
 
+/* ---- ILU(0) smoothing (Section 6.1: the smoother of the paper's experiments) --------------
+ * Incomplete LU factorisation without fill: L (unit lower) and U (upper) keep the sparsity
+ * pattern of the level's matrix A, unknowns in lexicographic order (x fastest), and LU agrees
+ * with A at every position of that pattern.  The factors follow the row-wise ("IKJ") form of
+ * Gaussian elimination restricted to the pattern (Saad, Iterative Methods for Sparse Linear
+ * Systems, ILU(0)): for each row p, for each lower entry k of p in increasing column order,
+ * a_pk /= u_kk, then a_pq -= a_pk u_kq for every upper entry q of row k that lies in row p's
+ * pattern.  The pattern is the level's stencil: the 5-point Shortley-Weller cross (3 points in
+ * 1D), or the 9-point box of a Galerkin level.  One smoothing step is the defect correction
+ * u <- u + (LU)^{-1} (f - A u): a forward solve with L, then a backward solve with U. */
+static int ilu_in_pattern(const level_t* L, int i, int j, int di, int dj) {
+  int ii = i + di, jj = j + dj;
+  if (ii < 0 || ii >= L->n[0] || jj < 0 || jj >= L->n[1]) return 0;
+  if (di < -1 || di > 1 || dj < -1 || dj > 1) return 0;
+  return L->st9 ? 1 : (di == 0 || dj == 0);
+}
+
+static int ilu_slot(int di, int dj) { return 3 * (dj + 1) + (di + 1); }
+
+static void level_ilu(level_t* L) {
+  L->ilu = calloc(9 * (size_t)imax(L->ntot, 1), sizeof(cplx));
+  /* lower neighbours of a row in increasing column order, upper ones of a row */
+  static const int lo[4][2] = {{-1, -1}, {0, -1}, {1, -1}, {-1, 0}};
+  static const int up[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+  for (int j = 0; j < L->n[1]; ++j)
+    for (int i = 0; i < L->n[0]; ++i) {
+      cplx a[9] = {0};
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di)
+          if (ilu_in_pattern(L, i, j, di, dj)) a[ilu_slot(di, dj)] = entry2d(L, i, j, i + di, j + dj);
+      for (int t = 0; t < 4; ++t) {
+        int di = lo[t][0], dj = lo[t][1];
+        if (!ilu_in_pattern(L, i, j, di, dj)) continue;
+        const cplx* uk = L->ilu + 9 * lidx(L, i + di, j + dj, 0);  /* row k, already factored */
+        cplx lk = a[ilu_slot(di, dj)] / uk[4];
+        a[ilu_slot(di, dj)] = lk;
+        for (int v = 0; v < 4; ++v) {
+          int ei = up[v][0], ej = up[v][1];
+          if (!ilu_in_pattern(L, i + di, j + dj, ei, ej)) continue;   /* not in row k */
+          int ti = di + ei, tj = dj + ej;                             /* the column, seen from p */
+          if (!ilu_in_pattern(L, i, j, ti, tj)) continue;             /* not in row p: dropped */
+          a[ilu_slot(ti, tj)] -= lk * uk[ilu_slot(ei, ej)];
+        }
+      }
+      memcpy(L->ilu + 9 * lidx(L, i, j, 0), a, sizeof(a));
+    }
+}
+
+static void ilu_sweep(const level_t* L, cplx* u, const cplx* f, cplx* tmp) {
+  static const int lo[4][2] = {{-1, -1}, {0, -1}, {1, -1}, {-1, 0}};
+  static const int up[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+  level_apply(L, u, tmp);
+  for (long p = 0; p < L->ntot; ++p) tmp[p] = f[p] - tmp[p];
+  for (int j = 0; j < L->n[1]; ++j)       /* L y = r, rows in increasing order */
+    for (int i = 0; i < L->n[0]; ++i) {
+      const cplx* w = L->ilu + 9 * lidx(L, i, j, 0);
+      cplx y = tmp[lidx(L, i, j, 0)];
+      for (int t = 0; t < 4; ++t)
+        if (ilu_in_pattern(L, i, j, lo[t][0], lo[t][1]))
+          y -= w[ilu_slot(lo[t][0], lo[t][1])] * tmp[lidx(L, i + lo[t][0], j + lo[t][1], 0)];
+      tmp[lidx(L, i, j, 0)] = y;
+    }
+  for (int j = L->n[1] - 1; j >= 0; --j)  /* U z = y, rows in decreasing order */
+    for (int i = L->n[0] - 1; i >= 0; --i) {
+      const cplx* w = L->ilu + 9 * lidx(L, i, j, 0);
+      cplx z = tmp[lidx(L, i, j, 0)];
+      for (int v = 0; v < 4; ++v)
+        if (ilu_in_pattern(L, i, j, up[v][0], up[v][1]))
+          z -= w[ilu_slot(up[v][0], up[v][1])] * tmp[lidx(L, i + up[v][0], j + up[v][1], 0)];
+      tmp[lidx(L, i, j, 0)] = z / w[4];
+    }
+  for (long p = 0; p < L->ntot; ++p) u[p] += tmp[p];
+}
+
 static void smooth(const orc_ctx* c, int lvl, cplx* u, const cplx* f, int sweeps, cplx* tmp) {
   const level_t* L = &c->M[lvl];
   for (int k = 0; k < sweeps; ++k) {
     if (c->pc.smoother == 0) jacobi_sweep(L, c->pc.omega, u, f, tmp);
+    else if (c->pc.smoother == 2) ilu_sweep(L, u, f, tmp);
     else rbgs_sweep(L, u, f);
   }
 }

@@ -91,6 +91,8 @@ def _load():
         lib.orc_level_st27.argtypes = [vp, ip, vp]
         lib.orc_apply.argtypes = [vp, ip, ip, vp, vp]
         lib.orc_dense.argtypes = [vp, ip, ip, vp]
+        lib.orc_ilu_factors.argtypes = [vp, ip, vp]
+        lib.orc_ilu_factors.restype = ip
         lib.orc_vcycle.argtypes = [vp, vp, vp]
         lib.orc_smooth.argtypes = [vp, ip, vp, vp, ip]
         lib.orc_restrict.argtypes = [vp, ip, vp, vp]
@@ -241,6 +243,16 @@ class Oracle:
         y = np.empty(self.level_size(which, lvl), np.complex128)
         _lib.orc_apply(self._h, which, lvl, _ptr(x), _ptr(y))
         return y
+
+    def ilu_factors(self, lvl):
+        """ILU(0) factors of preconditioner level lvl, shape (ntot, 3, 3) indexed [p, dj+1, di+1]
+        like a Galerkin stencil: L at the lower neighbours (unit diagonal implied), U at p and its
+        upper neighbours; None when the level has none (another smoother or the coarsest)."""
+        m = self.level_size(1, lvl)
+        out = np.zeros(9 * m, np.complex128)
+        if not _lib.orc_ilu_factors(self._h, lvl, _ptr(out)):
+            return None
+        return out.reshape(m, 3, 3)
 
     def dense(self, which=0, lvl=0):
         m = self.level_size(which, lvl)

@@ -1092,3 +1092,83 @@ def test_singular_coarsest_level_is_an_error():
     o = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=1.0 + 0.5j))
     z = o.vcycle(np.array([1.0 + 0j]))
     assert abs(z[0] - 1.0 / (8.0 - 8.0 * (1.0 + 0.5j))) < 1e-15
+
+
+# ---- ILU(0) smoothing (Section 6.1, the smoother of the paper's experiments) -------------------
+
+def _ilu_dense(o, lvl):
+    """Dense L (unit diagonal) and U from the oracle's ILU(0) factors of level lvl."""
+    fac = o.ilu_factors(lvl)
+    sh = o.level_shape(1, lvl)
+    n0, n1 = sh[0], (sh[1] if len(sh) > 1 else 1)
+    m = n0 * n1
+    Lm, Um = np.eye(m, dtype=complex), np.zeros((m, m), complex)
+    for j in range(n1):
+        for i in range(n0):
+            p = i + n0 * j
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    ii, jj = i + di, j + dj
+                    if 0 <= ii < n0 and 0 <= jj < n1:
+                        q = ii + n0 * jj
+                        (Lm if q < p else Um)[p, q] = fac[p, dj + 1, di + 1]
+    return Lm, Um
+
+
+def test_ilu0_of_a_tridiagonal_level_is_its_lu():
+    """In 1D the level matrix is tridiagonal, Gaussian elimination makes no fill, so ILU(0) is the
+    exact LU and one smoothing step from any u solves M u = f."""
+    rng = np.random.default_rng(11)
+    p = hi.make_problem(1, 30, ((4, 5),), theta_gamma=0.5, k0=3.0, phi_kind="bump", rhs="point", seed=1)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_ILU))
+    A = o.dense(1, 0)
+    f = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    u0 = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    x = np.linalg.solve(A, f)
+    assert np.abs(o.smooth(0, u0, f, 1) - x).max() < 1e-10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("galerkin", [False, True])
+def test_ilu0_matches_the_matrix_on_its_pattern(galerkin):
+    """ILU(0)'s defining property: L U equals A at every position where A has an entry (the
+    5-point cross of a Shortley-Weller level, the 9-point box of a Galerkin level), and differs
+    from A only by the dropped fill; one smoothing step is u + (LU)^{-1} (f - A u)."""
+    rng = np.random.default_rng(12)
+    p = hi.make_problem(2, (13, 11), ((3, 4), (2, 3)), theta_gamma=0.5, k0=4.0, phi_kind="bump", rhs="point",
+                        seed=2)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_ILU, galerkin=galerkin,
+                             nu1=0, nu2=1))
+    assert o.nlev >= 3
+    assert o.ilu_factors(o.nlev - 1) is None  # the coarsest level is solved directly
+    for lvl in range(o.nlev - 1):
+        A = o.dense(1, lvl)
+        Lm, Um = _ilu_dense(o, lvl)
+        pattern = A != 0
+        E = Lm @ Um - A
+        assert np.abs(E[pattern]).max() < 1e-14 * np.abs(A).max(), lvl
+        assert np.abs(E[~pattern]).max() > 1e-3 * np.abs(A).max(), lvl  # fill was dropped
+        # the pattern of L and U is A's own
+        assert not np.any((Lm - np.eye(len(A)) != 0) & ~pattern) and not np.any((Um != 0) & ~pattern)
+        f = rng.standard_normal(len(A)) + 1j * rng.standard_normal(len(A))
+        u0 = rng.standard_normal(len(A)) + 1j * rng.standard_normal(len(A))
+        want = u0 + np.linalg.solve(Lm @ Um, f - A @ u0)
+        assert np.abs(o.smooth(lvl, u0, f, 1) - want).max() < 1e-11 * np.abs(want).max(), lvl
+    if galerkin:  # a 9-point level has corner entries, whose rows take corner updates
+        assert np.any(o.level_stencil9(1)[:, 0, 0] != 0)
+
+
+def test_ilu0_vcycle_is_a_contraction_on_a_model_problem():
+    """The V(0,1) cycle with ILU(0) and Galerkin coarse operators (the paper's multigrid) on a
+    CSG-preconditioned 2D problem reduces the residual of M u = f in every cycle."""
+    p = hi.make_problem(2, (31, 31), ((8, 8), (8, 8)), theta_gamma=0.5, k0=8.0, phi_kind="const", rhs="point",
+                        seed=3)
+    o = Oracle(p, hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.5, smoother=hi.SM_ILU, galerkin=True, nu1=0,
+                             nu2=1))
+    A = o.dense(1, 0)
+    f = np.asarray(p.b, np.complex128)
+    u = np.zeros_like(f)
+    res = [np.linalg.norm(f)]
+    for _ in range(6):
+        u = u + o.vcycle(f - A @ u)
+        res.append(np.linalg.norm(f - A @ u))
+    assert all(b < 0.7 * a for a, b in zip(res, res[1:])), res
