@@ -52,7 +52,7 @@ typedef enum {
 typedef enum { HELM_C64 = 0 /* complex float32 */, HELM_C128 = 1 /* complex float64 */ } helm_dtype;
 
 enum { HELM_PC_NONE = 0, HELM_PC_CSL = 1, HELM_PC_CSG_UNIFORM = 2, HELM_PC_CSG_INTERIOR = 3 };
-enum { HELM_SM_JACOBI = 0, HELM_SM_RBGS = 1 };
+enum { HELM_SM_JACOBI = 0, HELM_SM_RBGS = 1, HELM_SM_ILU = 2 };
 enum { HELM_BICGSTAB = 0, HELM_IDR = 1, HELM_GMRES = 2 };
 /* largest GMRES restart length (helm_solve_opts.s) */
 #define HELM_GMRES_MAX_M 128
@@ -123,7 +123,8 @@ typedef struct {
   double theta_beta;    /* CSG angle */
   double shift_re, shift_im; /* CSL shift beta^2 */
   int nu1, nu2;         /* 0..8 sweeps */
-  int smoother;         /* HELM_SM_JACOBI or HELM_SM_RBGS */
+  int smoother;         /* HELM_SM_JACOBI, HELM_SM_RBGS or HELM_SM_ILU (ILU(0), Section 6.1: 1D and
+                           2D grids, the one-kernel-per-component V-cycle; see helm_create) */
   double omega;         /* Jacobi damping, 0 < omega <= 1 */
   int max_levels;       /* >= 1; a coarsest level that needs the dense inverse (variable k) must
                            have at most HELM_COARSE_MAX_UNKNOWNS unknowns (else helm_create:
@@ -154,7 +155,7 @@ typedef struct {
  * change the speed only (every point is computed by the same formulas); the tail depth also
  * changes the summation order inside the small levels, i.e. the rounding. */
 enum { HELM_PF_UNFUSED = 1, HELM_PF_NO_PDL = 2, HELM_PF_NO_AUTOTUNE = 4, HELM_PF_GALERKIN = 8 };
-/* HELM_PF_GALERKIN (2D or 3D, omega-Jacobi only; else helm_create: HELM_ERR_ARG): every coarse
+/* HELM_PF_GALERKIN (2D or 3D, omega-Jacobi or ILU(0); else helm_create: HELM_ERR_ARG): every coarse
  * level's operator is R A P -- the full weighting R times the finer level's operator A times the
  * (bi/tri)linear interpolation P of the V-cycle, a 9-point (2D) or 27-point (3D) stencil built at
  * helm_create in FP64 -- instead of the Shortley-Weller operator rediscretised on the coarse widths
@@ -210,7 +211,14 @@ typedef struct helm_ctx helm_ctx;
 
 /* Builds the grid, the FP64 operator H and the preconditioner hierarchy on the current
  * device (setup kernels on `stream`, then synchronises).  Returns HELM_ERR_ARG for invalid
- * sizes/kinds, HELM_ERR_OOM if device memory runs out (nothing is leaked). */
+ * sizes/kinds, HELM_ERR_OOM if device memory runs out (nothing is leaked).
+ * HELM_SM_ILU: the ILU(0) factors of every level above the coarsest are computed here (FP64,
+ * stored in mg_dtype; the level's own stencil pattern, unknowns in natural order).  It takes 1D
+ * and 2D grids whose finest level has at most 7,264 (complex64) or 3,632 (complex128) rows along
+ * y (a ring of 4 values per row in one block's 227 KB of shared memory), else HELM_ERR_ARG; each
+ * smoothing step runs its two triangular solves as one single-block launch over the wavefronts
+ * i + 2j (their n0 + 2 n1 - 2 steps are sequential), so the V-cycle is far slower than with the
+ * point smoothers. */
 helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_precond* pc,
                         void* stream, helm_ctx** out);
 
@@ -299,7 +307,8 @@ helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* b, void* 
  * V-cycle kernels (L = the largest number of fused levels) and one condition kernel, whatever n.
  * Requirements (else HELM_ERR_ARG, checked on the host): n >= 1 distinct contexts on the current
  * device, 2D grids, a CSL or CSG preconditioner with V(1,1) cycles on rediscretised fused levels
- * (no HELM_PF_UNFUSED or HELM_PF_GALERKIN) and a dense coarsest inverse, one smoother kind and one
+ * (no HELM_PF_UNFUSED or HELM_PF_GALERKIN) and a dense coarsest inverse, one smoother kind (not
+ * HELM_SM_ILU) and one
  * mg_dtype for all.  Grids, k fields, preconditioner parameters and sizes may all differ.
  * Each instance keeps its own block decomposition and reduction order, so its iterates, statistics
  * and solution are bitwise those helm_solve gives it alone; infos[i].kernels is the group's total

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
-SOURCES = ["api.cu", "setup.cu", "mg.cu", "mg_fused.cu", "krylov.cu", "server.cu", "noalloc.cu", "coarse_fdm.cu", "select.cu", "group.cu"]
+SOURCES = ["api.cu", "setup.cu", "mg.cu", "mg_fused.cu", "krylov.cu", "server.cu", "noalloc.cu", "coarse_fdm.cu", "select.cu", "group.cu",
+           "ilu.cu"]
 HEADERS = ["helm_internal.cuh", "stencil.cuh", "krylov_state.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -130,14 +130,14 @@ static helm_status check_precond(const helm_precond* p) {
   if (p->kind < HELM_PC_NONE || p->kind > HELM_PC_CSG_INTERIOR) { set_error("precond.kind"); return HELM_ERR_ARG; }
   if (p->kind == HELM_PC_NONE) return HELM_OK;
   if (p->nu1 < 0 || p->nu1 > 8 || p->nu2 < 0 || p->nu2 > 8) { set_error("nu1/nu2 must be in 0..8"); return HELM_ERR_ARG; }
-  if (p->smoother != HELM_SM_JACOBI && p->smoother != HELM_SM_RBGS) { set_error("smoother"); return HELM_ERR_ARG; }
+  if (p->smoother != HELM_SM_JACOBI && p->smoother != HELM_SM_RBGS && p->smoother != HELM_SM_ILU) { set_error("smoother"); return HELM_ERR_ARG; }
   if (p->smoother == HELM_SM_JACOBI && !(p->omega > 0.0 && p->omega <= 1.0)) { set_error("omega must be in (0, 1]"); return HELM_ERR_ARG; }
   if (p->max_levels < 1 || p->max_levels > 32) { set_error("max_levels must be in 1..32"); return HELM_ERR_ARG; }
   if (p->coarse_max < 1) { set_error("coarse_max must be >= 1"); return HELM_ERR_ARG; }
   if (p->mg_dtype != HELM_C64 && p->mg_dtype != HELM_C128) { set_error("mg_dtype"); return HELM_ERR_ARG; }
   if (p->flags & ~(HELM_PF_UNFUSED | HELM_PF_NO_PDL | HELM_PF_NO_AUTOTUNE | HELM_PF_GALERKIN)) { set_error("unknown precond.flags bits"); return HELM_ERR_ARG; }
-  if ((p->flags & HELM_PF_GALERKIN) && p->smoother != HELM_SM_JACOBI) {
-    set_error("Galerkin coarse operators need the damped-Jacobi smoother");
+  if ((p->flags & HELM_PF_GALERKIN) && p->smoother == HELM_SM_RBGS) {
+    set_error("Galerkin coarse operators need the damped-Jacobi or the ILU(0) smoother");
     return HELM_ERR_ARG;
   }
   if (!std::isfinite(p->theta_beta) || !std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) {

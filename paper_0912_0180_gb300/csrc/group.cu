@@ -159,6 +159,7 @@ const char* group_refusal(const helm_ctx* c, const helm_ctx* c0, int dev) {
   if (c->fdm.on) return "grouped solves need a dense coarsest inverse";
   if (!c->lv.empty() && c->lv[0].any_offset0()) return "grouped solves do not take Sommerfeld low sides";
   if ((int)c->lv.size() < 2 && c->tail_first > 0) return "grouped solves need at least two levels";
+  if (c->pc.smoother == HELM_SM_ILU) return "grouped solves smooth with damped Jacobi or red-black Gauss-Seidel";
   if (c->pc.smoother != c0->pc.smoother) return "the instances of a group share one smoother kind";
   if (c->pc.mg_dtype != c0->pc.mg_dtype) return "the instances of a group share one multigrid precision";
   return nullptr;

@@ -151,6 +151,11 @@ struct LevelHost {
   // copy for FP32 multigrid
   double2* stg64 = nullptr;
   float2* stg32 = nullptr;
+  // ILU(0) factors (ILU smoothing, 1D / 2D levels above the coarsest), [ntot][9]: L at the slots
+  // of the lower neighbours, U at the point and its upper neighbours; FP64 always, FP32 copy for
+  // FP32 multigrid
+  double2* ilu64 = nullptr;
+  float2* ilu32 = nullptr;
   // Sommerfeld sides: bit a set when the last unknown of axis a is the boundary node, bit a + 3 when
   // the first one is (a low side: that axis coarsens with offset 0, keeping node 0)
   int somm = 0;
@@ -245,6 +250,15 @@ void dev_free(const DevBlock& b, cudaStream_t st);
 void dev_free_all(std::vector<DevBlock>& v, cudaStream_t st);
 // device allocation owned by the context (on the context's creation stream)
 helm_status ctx_alloc(helm_ctx* c, void** p, size_t bytes);
+
+// ILU(0) smoothing (ilu.cu).  ilu_check: whether a level of this shape can take it (1D / 2D, the
+// row ring within one block's shared memory); ilu_build: the factors of level L, at create;
+// ilu_solve: u += (L U)^{-1} in (u = (L U)^{-1} in when zero), y a level-sized buffer (may be in).
+constexpr size_t ILU_SMEM_MAX = 227 * 1024;
+helm_status ilu_check(int dim, const int n[3], bool f32);
+helm_status ilu_build(helm_ctx* c, LevelHost& L, bool f32, cudaStream_t st);
+template <typename T>
+void ilu_solve(const LevelHost& L, const cx<T>* in, cx<T>* y, cx<T>* u, bool zero, const int* skip, cudaStream_t st);
 // releases a context: every buffer is freed in order on `st` after the work already queued there
 // (no device-wide synchronisation); the caller guarantees all its work was queued on `st`
 void ctx_release_on(helm_ctx* c, cudaStream_t st);

@@ -1166,6 +1166,19 @@ static void smooth(helm_ctx* c, const LevelHost& L, cx<T>* b[2], int* cur, const
     if (c->pc.smoother == HELM_SM_JACOBI) {
       op.jacobi(z0 ? nullptr : b[*cur], f, b[1 - *cur], (T)c->pc.omega, skip, st, w);
       *cur = 1 - *cur;
+    } else if (c->pc.smoother == HELM_SM_ILU) {
+      // u += (L U)^{-1} (f - M u), the residual in the spare buffer; from u = 0 the residual is f
+      cx<T>* u = b[*cur];
+      cx<T>* r = b[1 - *cur];
+      if (z0) {
+        ilu_solve<T>(L, f, r, u, true, skip, st);
+      } else {
+        op.apply(u, f, r, skip, st);
+        ilu_solve<T>(L, r, r, u, false, skip, st);
+      }
+      if constexpr (sizeof(cx<T>) == 8) {
+        if (w) widen_c64(c, (const float2*)u, w, L.ntot, skip, st);
+      }
     } else {
       op.rbgs(b[*cur], f, 0, z0 ? 1 : 0, skip, st);
       op.rbgs(b[*cur], f, 1, 0, skip, st, w);
@@ -1177,6 +1190,7 @@ template <typename T>
 static bool fused_applies(const helm_ctx* c, int l) {
   const helm_precond& pcf = c->pc;
   if (pcf.flags & HELM_PF_UNFUSED) return false;
+  if (pcf.smoother == HELM_SM_ILU) return false;  // ILU(0) runs as its own kernels
   if (c->lv[l].stg64) return false;  // 9-point Galerkin levels run the per-component kernels
   if (c->lv[l].any_offset0()) return false;  // the fused tiles assume coarse c = fine 2c + 1
   if (l >= c->tail_first) return true;
@@ -1232,7 +1246,7 @@ static void vcycle_unfused(helm_ctx* c, int l, const cx<T>* f, cx<T>* out, const
   if (pc.nu1 > 0) {
     smooth<T>(c, L, b, &cur, f, pc.nu1, true, skip, st);
     // residual into the spare buffer; after a single sweep from zero without the diagonal
-    if (pc.nu1 == 1) op.resid0(b[cur], f, b[1 - cur], (T)pc.omega, !jac, skip, st);
+    if (pc.nu1 == 1 && pc.smoother != HELM_SM_ILU) op.resid0(b[cur], f, b[1 - cur], (T)pc.omega, !jac, skip, st);
     else op.apply(b[cur], f, b[1 - cur], skip, st);
     restrict_any<T>(L, C, b[1 - cur], fc, skip, st);
   } else {
@@ -1300,6 +1314,10 @@ static helm_status level_op_t(helm_ctx* c, int op, int lvl, void* a, const void*
     case HELM_OP_SMOOTH:
     case HELM_OP_SMOOTH0: {
       if (!A || !B || count < 0) return HELM_ERR_ARG;
+      if (c->pc.smoother == HELM_SM_ILU && !L.ilu64) {
+        set_error("the coarsest level is solved directly and has no ILU(0) factors");
+        return HELM_ERR_ARG;
+      }
       // the sweeps read the level's reciprocal diagonal in its storage order: natural vectors of
       // an x-split level go through two x-split copies
       const bool conv = L.xs && !stored;

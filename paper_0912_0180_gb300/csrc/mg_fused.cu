@@ -1256,7 +1256,8 @@ static helm_status autotune_t(helm_ctx* c, cudaStream_t st) {
 }
 
 helm_status autotune_tiles(helm_ctx* c, cudaStream_t st) {
-  if ((c->pc.flags & (HELM_PF_NO_AUTOTUNE | HELM_PF_UNFUSED)) || c->pc.kind == HELM_PC_NONE || c->lv.empty())
+  if ((c->pc.flags & (HELM_PF_NO_AUTOTUNE | HELM_PF_UNFUSED)) || c->pc.kind == HELM_PC_NONE || c->lv.empty() ||
+      c->pc.smoother == HELM_SM_ILU)  // ILU(0) hierarchies run no fused kernel
     return HELM_OK;
   bool f32 = c->pc.mg_dtype == HELM_C64, rb = c->pc.smoother == HELM_SM_RBGS;
   if (f32) return rb ? autotune_t<float, true>(c, st) : autotune_t<float, false>(c, st);

@@ -72,6 +72,8 @@ extern "C" size_t helm_estimate_bytes(const helm_grid* g, const helm_precond* pc
       bytes += (size_t)Nl * (8 + 4 + 2 * esz + (levels == 1 ? 1 : 3) * esz);
       if (levels > 1 && (pc->flags & HELM_PF_GALERKIN))  // the stencil, FP64 and the V-cycle precision
         bytes += (size_t)Nl * (g->dim == 3 ? 27 : 9) * (16 + (esz == 8 ? 8 : 0)) + (size_t)Nl * 8;
+      if (pc->smoother == HELM_SM_ILU)  // ILU(0) factors, FP64 and the V-cycle precision
+        bytes += (size_t)Nl * 9 * (16 + (esz == 8 ? 8 : 0));
       last = Nl;
       bool all_small = true;
       long min_n = 1L << 40;

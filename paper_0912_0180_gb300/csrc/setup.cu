@@ -872,6 +872,13 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
       if ((rc = ctx_alloc(c, &L.f, esz * L.ntot)) != HELM_OK) return rc;
     }
   }
+  // ILU(0) factors of every level above the coarsest (solved directly)
+  if (pc.smoother == HELM_SM_ILU) {
+    for (size_t l = 0; l + 1 < c->lv.size(); ++l) {
+      if ((rc = ilu_check(c->lv[l].dim, c->lv[l].n, f32)) != HELM_OK) return rc;
+      if ((rc = ilu_build(c, c->lv[l], f32, st)) != HELM_OK) return rc;
+    }
+  }
   // dense inverse of the coarsest operator, computed in FP64: one block for small levels,
   // the whole GPU (one launch sequence per pivot) above GJ_ONE_BLOCK_MAX unknowns
   LevelHost& Cst = c->lv.back();
@@ -946,6 +953,7 @@ helm_status build_hierarchy(helm_ctx* c, cudaStream_t st) {
   }
   c->tail_first = f32 ? tail_first_level<float>(c) : tail_first_level<double>(c);
   if (galerkin) c->tail_first = (int)c->lv.size();  // the one-block tail runs 5-point rows only
+  if (pc.smoother == HELM_SM_ILU) c->tail_first = (int)c->lv.size();  // nor does it smooth with ILU(0)
   return tune_and_lay_out(c, st);
 }
 

@@ -89,7 +89,7 @@ def test_argument_errors_of_the_newer_entry_points_without_gpu():
 
 def test_memory_estimate_counts_galerkin_stencils_and_gmres_basis():
     """helm_estimate_bytes (host only) grows by the stored Galerkin stencils (27 weights per coarse
-    unknown in 3D) and by the GMRES(m) basis of m + 1 vectors."""
+    unknown in 3D), by the GMRES(m) basis of m + 1 vectors and by the ILU(0) factors."""
     import helm_inputs as hi
     from paper_0912_0180_gb300.helm import estimate_bytes
     p = hi.make_problem(3, 66, 16, k0=10.0, rhs="zero")  # 80^3 unknowns
@@ -100,3 +100,8 @@ def test_memory_estimate_counts_galerkin_stencils_and_gmres_basis():
     assert gal - base >= 27 * 16 * n1
     g30, g60 = estimate_bytes(p, pc, "c128", method=2, s=30), estimate_bytes(p, pc, "c128", method=2, s=60)
     assert g60 - g30 >= 30 * 16 * p.n
+    # ILU(0) factors: 9 entries per unknown on every level above the coarsest (2D grid)
+    p2 = hi.make_problem(2, 300, 20, k0=10.0, rhs="zero")
+    pi = hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_ILU)
+    pj = hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_JACOBI)
+    assert estimate_bytes(p2, pi, "c64") - estimate_bytes(p2, pj, "c64") >= 9 * 24 * p2.n

@@ -1040,3 +1040,82 @@ def test_complex_phi_inside_the_uniform_interior():
         z = h.vcycle(cu(x)).cpu().numpy().astype(np.complex128)
         check(z, o.vcycle(x), (1e-10 if mg == "c128" else 5e-5))
         h.close()
+
+
+ILU_CASES = [
+    (1, 60, ((5, 6),)),                  # tridiagonal levels: ILU(0) is their exact LU
+    (2, (29, 23), ((4, 5), (3, 4))),     # odd sizes, uneven layers
+    (2, (40, 31), ((6, 0), (2, 7))),     # one-sided layers, an even row length
+]
+
+
+@pytest.mark.parametrize("mg", ["c128", "c64"])
+@pytest.mark.parametrize("galerkin", [False, True])
+@pytest.mark.parametrize("case", ILU_CASES)
+def test_ilu0_levels_vcycle_and_solve(case, galerkin, mg):
+    """ILU(0) smoothing (Section 6.1) on the GPU against the oracle: every non-coarsest level's
+    smoothing steps from a guess and from zero (Shortley-Weller cross levels and 9-point Galerkin
+    levels), the V(0,1) and V(1,1) cycles, and a right-preconditioned Bi-CGSTAB solve with the
+    paper's multigrid (Galerkin coarse operators, V(0,1), ILU(0))."""
+    dim, n_int, nl = case
+    if galerkin and dim == 1:
+        pytest.skip("Galerkin coarse operators are built in 2D and 3D")
+    p = hi.make_problem(dim, n_int, nl, theta_gamma=0.5, k0=6.0, phi_kind="bump", rhs="point", seed=7,
+                        bump_centre=(0.4, 0.6, 0.5))
+    dt = torch.complex128 if mg == "c128" else torch.complex64
+    tol = 1e-10 if mg == "c128" else 5e-5
+    rng = np.random.default_rng(17)
+    for nu1, nu2 in ((0, 1), (1, 1)):
+        pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.4, smoother=hi.SM_ILU, galerkin=galerkin, nu1=nu1,
+                        nu2=nu2)
+        o = Oracle(p, pc)
+        h = Helm(p, pc, mg_dtype=mg)
+        assert h.nlev == o.nlev >= 3
+        if nu1 == 0:
+            for lvl in range(o.nlev - 1):
+                n = o.level_size(1, lvl)
+                a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+                b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+                if mg == "c64":
+                    a = a.astype(np.complex64).astype(np.complex128)
+                    b = b.astype(np.complex64).astype(np.complex128)
+                u = cu(a, dt)
+                h.level_op(L.HELM_OP_SMOOTH, lvl, u, cu(b, dt), None, count=2)
+                check(u.cpu().numpy(), o.smooth(lvl, a, b, 2), tol)
+                u = cu(a, dt)
+                h.level_op(L.HELM_OP_SMOOTH0, lvl, u, cu(b, dt), None, count=1)
+                check(u.cpu().numpy(), o.smooth(lvl, np.zeros(n), b, 1), tol)
+        r = hi.random_vector(p.n, 23)
+        z = h.vcycle(cu(r)).cpu().numpy().astype(np.complex128)
+        check(z, o.vcycle(r), tol)
+        h.close()
+    if not galerkin or mg == "c64":
+        return
+    # the paper's multigrid in a solve: FP64 path against the oracle at a tight tolerance
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.4, smoother=hi.SM_ILU, galerkin=True, nu1=0, nu2=1)
+    o = Oracle(p, pc)
+    opts = hi.SolveOpts(method=hi.BICGSTAB, tol=1e-10, maxmv=1500)
+    x_ref, info_ref = o.solve(p.b, opts)
+    h = Helm(p, pc, mg_dtype="c128")
+    x, info = h.solve(cu(p.b), method=hi.BICGSTAB, tol=1e-10, maxmv=1500)
+    assert info.status == 0 and info_ref["status"] == 0 and info.rel_res_true < 1e-10
+    check(x.cpu().numpy(), x_ref, 1e-9)
+    counts_match(o, p.b, opts, info.matvecs, info_ref["matvecs"])
+    h.close()
+
+
+def test_ilu0_is_refused_where_it_does_not_run():
+    """ILU(0) smoothing is built for 1D and 2D levels: a 3D hierarchy is refused at create, and
+    the coarsest level (solved directly) has no factors to smooth with."""
+    p3 = hi.make_problem(3, (9, 9, 9), ((2, 2), (2, 2), (2, 2)), theta_gamma=0.5, k0=3.0)
+    pc = hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=0.3, smoother=hi.SM_ILU)
+    with pytest.raises(Exception, match="ILU"):
+        Helm(p3, pc, mg_dtype="c128")
+    p2 = hi.make_problem(2, (21, 17), ((3, 3), (3, 3)), theta_gamma=0.5, k0=4.0)
+    h = Helm(p2, pc, mg_dtype="c128")
+    lvl = h.nlev - 1
+    n = int(np.prod(h.level_shape(lvl)))
+    u = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    with pytest.raises(Exception, match="ILU"):
+        h.level_op(L.HELM_OP_SMOOTH, lvl, u, u.clone(), None, count=1)
+    h.close()
