@@ -263,7 +263,7 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the Krylov loop from the host (one graph launch per iteration) so that "
                          "a kernel profiler sees every launch; slower, for profiling only")
-    ap.add_argument("--workload", default="2d640", choices=["2d640", "c1", "3d160", "3d160g", "batch256", "serve", "mp2", "mp2s", "mp3", "mp2som", "mp3som", "mp3b", "mp3bsom", "mp1", "mp1som", "select", "gmres"],
+    ap.add_argument("--workload", default="2d640", choices=["2d640", "c1", "3d160", "3d160g", "batch256", "serve", "mp2", "mp2s", "mp3", "mp3ilu", "mp2som", "mp3som", "mp3b", "mp3bsom", "mp1", "mp1som", "select", "gmres"],
                     help="2d640 (default): the 512^2 + 64-layer four-solve step; 3d160: 128^3 + 16-layer "
                          "k = 40 mixed-precision solve; batch256: 256 uneven 2D instances per step; "
                          "serve: a Poisson-arrival request stream through the solve server; mp2 / mp3: "

@@ -19,6 +19,8 @@
   mp2som, mp3som  the same problems with the first-order Sommerfeld condition on the east / north
             edges instead of layers (the paper's Sommerfeld rows: shift 1 - 0.35i / 1 - 0.38i, angle
             -pi/20 / -pi/17).
+  mp3ilu    mp3 with the paper's own multigrid: ILU(0) smoothing (lexicographic order), Galerkin
+            coarse operators, V(0,1) cycles -- the configuration its matvec counts were measured with.
   mp2s      mp2 on the smooth ECS contour of the paper's Section 7 remark (the layer widths turn by
             theta_gamma / 128 per width over the whole 128-node layer).
   gmres     the paper's GMRES remark: MP2 (nu = 1, k = 4, ECS) to 1e-7 with GMRES(128), GMRES(30),
@@ -89,6 +91,7 @@ def run(args):
     dev = torch.device("cuda", local)
     ranks = bench.Ranks(dist if world > 1 else None, dev)
     fn = {"c1": run_c1, "3d160": run_3d, "3d160g": run_3d, "batch256": run_batch, "serve": run_serve, "mp2": run_mp, "mp2s": run_mp, "mp3": run_mp,
+          "mp3ilu": run_mp,
           "mp3b": run_mp, "mp3bsom": run_mp, "mp1": run_mp, "mp1som": run_mp,
           "mp2som": run_mp, "mp3som": run_mp,
           "select": run_select, "gmres": run_gmres}[args.workload]
@@ -656,6 +659,10 @@ MP_CASES = {
     "mp1": {"problem": lambda: hi.workload_mp1(), "csl": 1 + 0.2j, "csg": np.pi / 28,
             "paper_matvecs": {"csl": {"bicgstab": 59, "idr4": 62, "idr8": 60},
                               "csg": {"bicgstab": 58, "idr4": 62, "idr8": 56}}},
+    # MP3 with the paper's own multigrid: ILU(0) smoothing, Galerkin coarse operators, V(0,1)
+    "mp3ilu": {"problem": lambda: hi.workload_mp3(), "csl": 1 + 0.38j, "csg": np.pi / 17, "ilu": True,
+               "paper_matvecs": {"csl": {"bicgstab": 142, "idr4": 145, "idr8": 141},
+                                 "csg": {"bicgstab": 139, "idr4": 139, "idr8": 134}}},
     "mp1som": {"problem": lambda: hi.workload_mp1(n_l=-1), "csl": 1 - 0.2j, "csg": -np.pi / 28, "galerkin": False,
                "paper_matvecs": {"csl": {"bicgstab": 79, "idr4": 72, "idr8": 76},
                                  "csg": {"bicgstab": 74, "idr4": 70, "idr8": 72}}},
@@ -674,9 +681,10 @@ def run_mp(args, torch, ranks, dev, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     solves = [(m, s, pcn) for pcn in ("csl", "csg") for (m, s) in (("bicgstab", 0), ("idr4", 4), ("idr8", 8))]
     gal = case.get("galerkin", True)
-    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], smoother=hi.SM_JACOBI, omega=0.5, galerkin=gal),
-           "csg": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=case["csg"], smoother=hi.SM_JACOBI, omega=0.5,
-                             galerkin=gal)}
+    ilu = case.get("ilu", False)
+    sm = dict(smoother=hi.SM_ILU, nu1=0, nu2=1) if ilu else dict(smoother=hi.SM_JACOBI, omega=0.5)
+    pcs = {"csl": hi.Precond(kind=hi.PC_CSL, shift=case["csl"], galerkin=gal, **sm),
+           "csg": hi.Precond(kind=hi.PC_CSG_UNIFORM, theta_beta=case["csg"], galerkin=gal, **sm)}
     methods = [hi.BICGSTAB if s == 0 else hi.IDR for (_, s, _) in solves]
     svals = [max(s, 1) for (_, s, _) in solves]
     shadows = [hi.shadow_space(p.n, s) if s else None for (_, s, _) in solves]
@@ -711,8 +719,8 @@ def run_mp(args, torch, ranks, dev, local):
     cfg = {"workload": p.name, "n_unknowns": p.n, "solves_per_step": ns,
            "solves": "{Bi-CGSTAB, IDR(4), IDR(8)} x {CSL shift %s, CSG theta_beta %.4f}, run at once"
                      % (case["csl"], case["csg"]),
-           "multigrid": "V(1,1) omega-Jacobi 0.5, FW, bilinear, " + ("Galerkin coarse operators R A P" if gal else
-                                                                      "rediscretised coarse operators"),
+           "multigrid": ("V(0,1) ILU(0), FW, bilinear, " if ilu else "V(1,1) omega-Jacobi 0.5, FW, bilinear, ") +
+                        ("Galerkin coarse operators R A P" if gal else "rediscretised coarse operators"),
            "boundaries": (("first-order Sommerfeld on all four edges" if args.workload.endswith("som") else
                            "ECS layers on all four edges (theta_gamma = pi/6)") if args.workload.startswith("mp1") else
                           "Dirichlet south / west, " + ("first-order Sommerfeld east / north"
