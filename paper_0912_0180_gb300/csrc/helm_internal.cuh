@@ -152,8 +152,8 @@ struct LevelHost {
   double2* stg64 = nullptr;
   float2* stg32 = nullptr;
   // ILU(0) factors (ILU smoothing, 1D / 2D levels above the coarsest), [ntot][9]: L at the slots
-  // of the lower neighbours, U at the point and its upper neighbours; FP64 always, FP32 copy for
-  // FP32 multigrid
+  // of the lower neighbours, U at the upper neighbours and the reciprocal of U's pivot at the
+  // point's own slot; FP64 always, FP32 copy for FP32 multigrid
   double2* ilu64 = nullptr;
   float2* ilu32 = nullptr;
   // Sommerfeld sides: bit a set when the last unknown of axis a is the boundary node, bit a + 3 when

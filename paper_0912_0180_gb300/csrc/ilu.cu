@@ -16,7 +16,8 @@
 // The values of the last three wavefronts stay in a shared-memory ring indexed by row, so a point
 // reads its neighbours from shared memory.  The factors are computed once, in FP64, at create and
 // stored in the multigrid precision; a level's 9 factor entries of point p sit at [9p + s], slot
-// s = 3 (dj + 1) + (di + 1) of the neighbour (i + di, j + dj): L at the lower slots 0..3, U at 4..8.
+// s = 3 (dj + 1) + (di + 1) of the neighbour (i + di, j + dj): L at the lower slots 0..3, U at 5..8,
+// and at slot 4 the reciprocal of U's pivot (both the elimination and the solve multiply by it).
 #include <algorithm>
 #include <type_traits>
 
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(ILU_FACTOR_THREADS) k_ilu_factor(OpView<double
         if (!ilu_in_pattern(n0, n1, box, i, j, di, dj)) continue;
         const double2* uk = f64 + 9 * (p + di + (long)n0 * dj);  // row k, factored on an earlier wavefront
         const int sk = 3 * (dj + 1) + (di + 1);
-        const double2 l = cdiv<double>(a[sk], uk[4]);
+        const double2 l = cmul<double>(a[sk], uk[4]);  // uk[4]: 1 / row k's pivot
         a[sk] = l;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(ILU_FACTOR_THREADS) k_ilu_factor(OpView<double
           a[st] = csub<double>(a[st], cmul<double>(l, uk[3 * (ej + 1) + (ei + 1)]));
         }
       }
+      a[4] = crecip<double>(a[4]);
 #pragma unroll
       for (int s = 0; s < 9; ++s) {
         f64[9 * p + s] = a[s];
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(ILU_THREADS) k_ilu_solve(int n0, int n1, const
         v = csub<T>(v, cmul<T>(w[7], ring[((t + 2) & 3) * n1 + j + 1]));
         if (i < n0 - 1) v = csub<T>(v, cmul<T>(w[8], ring[((t + 3) & 3) * n1 + j + 1]));
       }
-      v = cdiv<T>(v, w[4]);
+      v = cmul<T>(v, w[4]);  // w[4]: 1 / the pivot
       ring[(t & 3) * n1 + j] = v;
       u[p] = zero ? v : cadd<T>(u[p], v);
     }
