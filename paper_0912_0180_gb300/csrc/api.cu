@@ -202,6 +202,10 @@ helm_status helm_create(const helm_grid* grid, const helm_kspec* k, const helm_p
     set_error("Galerkin coarse operators need a 2D or 3D grid");
     return HELM_ERR_ARG;
   }
+  if (pc->smoother == HELM_SM_ILU && pc->kind != HELM_PC_NONE && grid->dim > 2) {
+    set_error("ILU(0) smoothing runs on 1D and 2D levels");
+    return HELM_ERR_ARG;
+  }
   if (!k || !std::isfinite(k->k0)) { set_error("kspec missing or k0 not finite"); return HELM_ERR_ARG; }
   helm_ctx* c = new helm_ctx();
   c->grid = *grid;

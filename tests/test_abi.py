@@ -46,8 +46,8 @@ def test_status_strings_and_argument_errors_without_gpu():
 
 
 def test_argument_errors_of_the_newer_entry_points_without_gpu():
-    """A side below -1, a bad ramp, GMRES restart lengths and the parameter choice's
-    arguments are refused on the host (no device is touched)."""
+    """A side below -1, a bad ramp, ILU(0) on a 3D grid, an unknown smoother, GMRES restart lengths
+    and the parameter choice's arguments are refused on the host (no device is touched)."""
     import helm_inputs as hi
     import paper_0912_0180_gb300 as P
     from paper_0912_0180_gb300 import _lib as L
@@ -71,6 +71,17 @@ def test_argument_errors_of_the_newer_entry_points_without_gpu():
     im = (ctypes.c_double * q.n)()
     k.phi_im = ctypes.cast(im, ctypes.c_void_p)
     assert lib.helm_create(ctypes.byref(_grid(q)), ctypes.byref(k), ctypes.byref(pc), None, ctypes.byref(out)) \
+        == L.HELM_ERR_ARG
+    # ILU(0) smoothing on a 3D grid, and an unknown smoother kind
+    c = hi.make_problem(3, 9, 2, k0=3.0, rhs="zero")
+    k3, keep3 = _kspec(c)
+    pi = _precond(hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=hi.SM_ILU), "c128")
+    assert lib.helm_create(ctypes.byref(_grid(c)), ctypes.byref(k3), ctypes.byref(pi), None, ctypes.byref(out)) \
+        == L.HELM_ERR_ARG
+    assert b"ILU" in lib.helm_last_error()
+    pu = _precond(hi.Precond(kind=hi.PC_CSG_UNIFORM, smoother=7), "c128")
+    k, keep = _kspec(q)
+    assert lib.helm_create(ctypes.byref(_grid(q)), ctypes.byref(k), ctypes.byref(pu), None, ctypes.byref(out)) \
         == L.HELM_ERR_ARG
     # the parameter choice: factor outside (0, 1), identity preconditioner
     k, keep = _kspec(q)
