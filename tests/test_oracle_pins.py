@@ -1172,3 +1172,26 @@ def test_ilu0_vcycle_is_a_contraction_on_a_model_problem():
         u = u + o.vcycle(f - A @ u)
         res.append(np.linalg.norm(f - A @ u))
     assert all(b < 0.7 * a for a, b in zip(res, res[1:])), res
+
+
+def test_ilu0_triangular_solves_amplify_on_mp1_at_kh_1_25():
+    """The reading behind the MP1 / MP2 rows keeping omega-Jacobi: on MP1 (k = 160, 257^2 nodes,
+    64-node ECS layers) with the CSL shift 1 + 0.2i, one ILU(0) step from zero on the 192^2 level
+    (kH = 1.25) leaves a residual many orders of magnitude above the right-hand side, though every
+    pivot is far from zero; on the finest level and with a more damped shift (1 + 0.5i) the same step
+    reduces it."""
+    rng = np.random.default_rng(21)
+    p = hi.workload_mp1()
+
+    def step_ratio(shift, lvl):
+        o = Oracle(p, hi.Precond(kind=hi.PC_CSL, shift=shift, smoother=hi.SM_ILU, galerkin=True, nu1=0, nu2=1))
+        n = o.level_size(1, lvl)
+        f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        u = o.smooth(lvl, np.zeros(n, complex), f, 1)
+        piv = np.abs(o.ilu_factors(lvl)[:, 1, 1])
+        return np.linalg.norm(f - o.apply(u, 1, lvl)) / np.linalg.norm(f), piv.min() / piv.max()
+
+    bad, piv_ratio = step_ratio(1 + 0.2j, 1)
+    assert bad > 1e6 and piv_ratio > 0.1
+    assert step_ratio(1 + 0.2j, 0)[0] < 1
+    assert step_ratio(1 + 0.5j, 1)[0] < 1
